@@ -1,0 +1,214 @@
+"""Finite-element definitions of energy, residual, tangent and its action (Secs. 2-3, 5).
+
+Test infrastructure (see oracle/__init__.py). Everything is computed with the full
+tensor-product tables of oracle.basis (O(n^{2d}) per cell, no sum factorisation) and
+integrated in the reference configuration: the paper's division by J after integrating
+over the spatial configuration (Sec. 5) is the same integral, so it is absent here.
+
+Notation (per cell K, quadrature point q, node a, component c):
+  Grad N_a  = dN[q,a,:] / h           reference gradient of a shape function
+  F         = I + Grad u              (Sec. 2.1)
+  g_a       = F^{-T} Grad N_a         so that grad(N_a e_c) = e_c (x) g_a   (Sec. 2.1: grad = Grad . F^{-1})
+  residual  R_{a,c} = sum_q w_q h^d  tau : grad^s(N_a e_c)                    (Eq. weak_form)
+  tangent   A_{ac,be} = sum_q w_q h^d [ grad^s(N_a e_c) : JC : grad^s(N_b e_e)
+                                      + grad(N_a e_c) : (grad(N_b e_e) . tau) ] (Eq. algebraic_tangent)
+Dirichlet treatment (reading O9 / Sec. 3): the constrained operator is Z A Z + (I - Z) with
+Z the diagonal mask of free dofs; residual rows of constrained dofs are zero.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import material
+from .basis import CellTables
+
+
+class Problem:
+    """A uniform m^dim mesh of Q_k cells on the unit square/cube with per-cell materials.
+
+    ids: uint8 material id per cell (x fastest); mu_tab, lam_tab: per-id moduli;
+    masks: per-face bitmask of constrained components, faces (-x,+x,-y,+y,-z,+z).
+    """
+
+    def __init__(self, dim, k, m, ids, mu_tab, lam_tab, masks, chunk=512):
+        self.dim, self.k, self.m = dim, k, m
+        self.n = k + 1
+        self.h = 1.0 / m
+        self.L = k * m + 1
+        self.n_nodes = self.L**dim
+        self.n_dofs = dim * self.n_nodes
+        self.tab = CellTables(dim, k)
+        self.chunk = chunk
+        ids = np.asarray(ids)
+        self.mu = np.asarray(mu_tab, dtype=float)[ids]
+        self.lam = np.asarray(lam_tab, dtype=float)[ids]
+        self.masks = list(masks)
+        # connectivity: cell multi-index (c0,c1,..), local node multi-index (a0,a1,..), both x fastest
+        n, L = self.n, self.L
+        cells = np.indices((m,) * dim).reshape(dim, -1)[::-1]       # cells[i][K] = c_i
+        loc = np.indices((n,) * dim).reshape(dim, -1)[::-1]         # loc[i][a]  = a_i
+        gnode = np.zeros((m**dim, n**dim), dtype=np.int64)
+        for i in range(dim):
+            gnode += (k * cells[i][:, None] + loc[i][None, :]) * L**i
+        self.cell_nodes = gnode
+        self.cell_dofs = (gnode[:, :, None] * dim + np.arange(dim)[None, None, :]).reshape(m**dim, -1)
+        # constrained dofs from the face masks
+        lat = np.indices((L,) * dim).reshape(dim, -1)[::-1]
+        cons = np.zeros((self.n_nodes, dim), dtype=bool)
+        for a in range(dim):
+            for side, val in ((0, 0), (1, L - 1)):
+                for c in range(dim):
+                    if masks[2 * a + side] >> c & 1:
+                        cons[lat[a] == val, c] = True
+        self.constrained = cons.reshape(-1)
+        self.free = ~self.constrained
+
+    # ---- per-cell kinematics -------------------------------------------------------------
+    def _chunks(self):
+        nc = self.m**self.dim
+        for s in range(0, nc, self.chunk):
+            yield np.arange(s, min(nc, s + self.chunk))
+
+    def grad_at_qp(self, v, cells):
+        """Grad v[K,q,i,J] = sum_a v_{a,i} dN[q,a,J] / h for the given cells."""
+        vK = v[self.cell_dofs[cells]].reshape(len(cells), -1, self.dim)
+        return np.einsum("Kai,qaJ->KqiJ", vK, self.tab.dN) / self.h
+
+    def deformation(self, u, cells):
+        """F = I + Grad u at every quadrature point of the cells (Sec. 2.1); raises if J <= 0."""
+        F = np.eye(self.dim) + self.grad_at_qp(u, cells)
+        J = np.linalg.det(F)
+        if np.any(J <= 0):
+            raise FloatingPointError("J <= 0 at a quadrature point")
+        return F
+
+    def min_jacobian(self, u):
+        return min(np.linalg.det(np.eye(self.dim) + self.grad_at_qp(u, c)).min() for c in self._chunks())
+
+    def _qp_params(self, cells):
+        nq = self.n**self.dim
+        return (np.repeat(self.mu[cells][:, None], nq, axis=1), np.repeat(self.lam[cells][:, None], nq, axis=1))
+
+    def _g(self, F):
+        """g[K,q,a,j] = sum_J Grad N_a[J] F^{-1}[J,j]."""
+        Finv = np.linalg.inv(F)
+        return np.einsum("qaJ,KqJj->Kqaj", self.tab.dN / self.h, Finv)
+
+    # ---- energy, residual --------------------------------------------------------------------
+    def energy(self, u):
+        """E = sum_K sum_q psi(F_q) w_q h^d (Sec. 2.1 potential without traction term)."""
+        E = 0.0
+        for cells in self._chunks():
+            F = self.deformation(u, cells)
+            mu, lam = self._qp_params(cells)
+            E += np.einsum("Kq,q->", material.psi(F, mu, lam), self.tab.w) * self.h**self.dim
+        return E
+
+    def residual_raw(self, u):
+        """R_i = sum_K sum_q tau : grad^s N_i w_q h^d for every dof, constrained rows included (Eq. weak_form)."""
+        R = np.zeros(self.n_dofs)
+        for cells in self._chunks():
+            F = self.deformation(u, cells)
+            mu, lam = self._qp_params(cells)
+            tau = material.kirchhoff(F, mu, lam)
+            g = self._g(F)
+            # tau : grad^s(N_a e_c) = tau : grad(N_a e_c) (tau symmetric) = sum_j tau_cj g_a,j
+            RK = np.einsum("Kqcj,Kqaj,q->Kac", tau, g, self.tab.w) * self.h**self.dim
+            np.add.at(R, self.cell_dofs[cells].reshape(-1), RK.reshape(-1))
+        return R
+
+    def residual(self, u):
+        """Residual with constrained rows set to zero."""
+        R = self.residual_raw(u)
+        R[self.constrained] = 0.0
+        return R
+
+    # ---- tangent --------------------------------------------------------------------------------
+    def _local_tangent(self, u, cells):
+        """Element tangent matrices [K, a*d+c, b*d+e] from Eq. algebraic_tangent, literal double contractions."""
+        d = self.dim
+        F = self.deformation(u, cells)
+        mu, lam = self._qp_params(cells)
+        tau = material.kirchhoff(F, mu, lam)
+        JC = material.spatial_tangent(F, mu, lam)
+        ga = self._g(F)
+        I = np.eye(d)
+        G = np.einsum("ic,Kqaj->Kqacij", I, ga)                         # grad(N_a e_c)_{ij} = d_ic g_a,j
+        Gs = 0.5 * (G + np.swapaxes(G, -1, -2))                           # grad^s(N_a e_c)
+        w = self.tab.w * self.h**d
+        CGs = np.einsum("Kqijkl,Kqbekl->Kqijbe", JC, Gs)                # JC : grad^s(N_b e_e)
+        mat = np.einsum("Kqacij,Kqijbe,q->Kacbe", Gs, CGs, w)
+        Gt = np.einsum("Kqbeim,Kqmj->Kqbeij", G, tau)                   # grad(N_b e_e) . tau
+        geo = np.einsum("Kqacij,Kqbeij,q->Kacbe", G, Gt, w)
+        nloc = self.cell_dofs.shape[1]
+        return (mat + geo).reshape(len(cells), nloc, nloc)
+
+    def tangent_raw(self, u):
+        """Assembled tangent A (scipy CSR), no boundary conditions applied."""
+        rows, cols, vals = [], [], []
+        for cells in self._chunks():
+            AK = self._local_tangent(u, cells)
+            dofs = self.cell_dofs[cells]
+            rows.append(np.repeat(dofs[:, :, None], dofs.shape[1], axis=2).reshape(-1))
+            cols.append(np.repeat(dofs[:, None, :], dofs.shape[1], axis=1).reshape(-1))
+            vals.append(AK.reshape(-1))
+        A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                          shape=(self.n_dofs, self.n_dofs))
+        return A.tocsr()
+
+    def constrain(self, A):
+        """Z A Z + (I - Z): identity rows/columns on constrained dofs."""
+        z = self.free.astype(float)
+        Z = sp.diags(z)
+        return (Z @ A @ Z + sp.diags(1.0 - z)).tocsr()
+
+    def tangent(self, u):
+        return self.constrain(self.tangent_raw(u))
+
+    def apply(self, u, x, constrained=True):
+        """Element-by-element action y = A(u) x of Eq. mf_vmult (no assembled matrix).
+
+        Per cell and quadrature point: grad x = Grad x . F^{-1}; Q = grad x . tau + JC : grad^s x;
+        y_{a,c} += w_q h^d grad(N_a e_c) : Q = w_q h^d sum_j g_a,j Q_cj.
+        With constrained=True, x is read as zero on constrained dofs and y_c = x_c there.
+        """
+        d = self.dim
+        xin = np.where(self.constrained, 0.0, x) if constrained else np.asarray(x, dtype=float)
+        y = np.zeros(self.n_dofs)
+        for cells in self._chunks():
+            F = self.deformation(u, cells)
+            mu, lam = self._qp_params(cells)
+            tau = material.kirchhoff(F, mu, lam)
+            JC = material.spatial_tangent(F, mu, lam)
+            Finv = np.linalg.inv(F)
+            gx = np.einsum("KqiJ,KqJj->Kqij", self.grad_at_qp(xin, cells), Finv)
+            gxs = 0.5 * (gx + np.swapaxes(gx, -1, -2))
+            Q = np.einsum("Kqim,Kqmj->Kqij", gx, tau) + np.einsum("Kqijkl,Kqkl->Kqij", JC, gxs)
+            ga = self._g(F)
+            yK = np.einsum("Kqaj,Kqcj,q->Kac", ga, Q, self.tab.w) * self.h**d
+            np.add.at(y, self.cell_dofs[cells].reshape(-1), yK.reshape(-1))
+        if constrained:
+            y[self.constrained] = x[self.constrained]
+        return y
+
+    def diagonal(self, u):
+        """diag of the constrained tangent, summed element by element (1 on constrained dofs)."""
+        d = self.dim
+        D = np.zeros(self.n_dofs)
+        for cells in self._chunks():
+            F = self.deformation(u, cells)
+            mu, lam = self._qp_params(cells)
+            tau = material.kirchhoff(F, mu, lam)
+            JC = material.spatial_tangent(F, mu, lam)
+            ga = self._g(F)
+            I = np.eye(d)
+            G = np.einsum("ic,Kqaj->Kqacij", I, ga)
+            Gs = 0.5 * (G + np.swapaxes(G, -1, -2))
+            w = self.tab.w * self.h**d
+            mat = np.einsum("Kqacij,Kqijkl,Kqackl,q->Kac", Gs, JC, Gs, w)
+            geo = np.einsum("Kqaj,Kqmj,Kqam,q->Ka", ga, tau, ga, w)  # d_cc = 1: same for every c
+            DK = mat + geo[:, :, None]
+            np.add.at(D, self.cell_dofs[cells].reshape(-1), DK.reshape(-1))
+        D[self.constrained] = 1.0
+        return D

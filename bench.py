@@ -1,0 +1,373 @@
+"""Benchmark: matrix-free finite-strain tangent application on one GB300 (and GMG-CG solve latency).
+
+Workload (one step): the 3D compressible neo-Hookean unit cube with a spherical inclusion (r = 0.25,
+10x stiffer, mu = 1, nu = 0.3), uniform 32^3 Q2 hexahedra (823,875 dofs), 3^3 Gauss points, bottom
+face clamped, displacement state u = 0.05 * seeded smooth random field, source vector N(0,1). One
+step applies the FP64 tangent once in each of the three caching variants -- fourth-order tangent
+cached (T4, Algorithm 3), F cached with the stress recomputed (FC), nothing cached (NC).
+value = dofs processed / device time = 3 * 823,875 * K / sum of the K*3 kernel-event durations.
+Before every application the L2 cache is flushed by writing a 256 MB buffer (outside the timed
+events). Extra keys report every variant in FP64 and FP32 and the GMG-preconditioned CG solve
+latency (p50/p99) of the same problem with a 4-level hierarchy (32 -> 4), FP64 and mixed precision.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-solve]
+
+--impl reference times the CPU oracle (the test oracle of this repository, FP64 numpy) on the
+host cores on a bounded sample of the same workload (the same problem on a 16^3 Q2 mesh).
+"""
+import os
+
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+os.environ.setdefault("MKL_NUM_THREADS", "1")
+
+import argparse  # noqa: E402
+import json  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import time  # noqa: E402
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "tangent-apply GDoF/s (FP64 vs mixed) & GMG-CG solve p50/p99 latency, 1 GB300"
+UNIT = "GDoF/s"
+DIM, K, M = 3, 2, 32
+VARIANTS = ("T4", "FC", "NC")
+ALL_VARIANTS = ("T4", "T2", "FC", "SC", "NC")
+WORKLOAD = "3D neo-Hookean unit cube, spherical inclusion r=0.25 10x, 32^3 Q2 (823,875 dofs), FP64 tangent apply x {T4, FC, NC}"
+
+
+def flops_per_qp(var, dim=3, n=3):
+    """Algorithmic FP64 flops per Gauss point of one application, counted from the kernel's arithmetic
+    (FMA = 2): sum factorisation 4 d^2 (2n-1) + d(d-1); quadrature work per variant."""
+    sf = 4 * dim * dim * (2 * n - 1) + dim * (dim - 1)
+    g = dim * dim * (2 * dim - 1)          # g = G M
+    q = dim * dim * 2 * dim                # Q = S + g tau
+    p = dim * dim * (2 * dim - 1)          # P = Q M^T
+    ns = 6 if dim == 3 else 3
+    mat4 = ns * (2 * ns - 1) + 3           # Voigt J*C action
+    nh = 16                                # neo-Hooke action c1 sym(g) + c2 tr(g) I
+    state = 88                             # J, F^{-1}, ln J (counted as 1), b, tau, c1, c2 from F
+    ubar = 2 * dim * dim * (2 * n - 1) + 2 * dim * dim  # gradient of the displacement, F = I + Grad u
+    return {
+        "T4": sf + g + mat4 + q + p,
+        "T2": sf + g + nh + q + p,
+        "FC": sf + state + g + nh + q + p,
+        "SC": sf + ubar + state + g + nh + q + p,
+        "NC": sf + ubar + state + g + nh + q + p,
+    }[var]
+
+
+def bytes_per_apply(var, dtype_bytes, nqp, ndofs, dim=3):
+    """Algorithmic HBM bytes of one application: the cache once, x and the displacement once, y written once."""
+    nvals = {"T4": dim * dim + 6 + 21, "T2": dim * dim + 6 + 2, "FC": dim * dim, "SC": 1, "NC": 0}[var]
+    vec = 2 * ndofs * dtype_bytes + (ndofs * dtype_bytes if var in ("SC", "NC") else 0)
+    return nvals * nqp * dtype_bytes + vec
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm, src = 6800.0, "fallback"
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        hbm, src = float(d.get("hbm_gbs", hbm)), "measured"
+    # FP64 pipe: 2 DFMA per clock per SM x 152 SMs x 2.07 GHz (nominal 1.25 TFLOP/s)
+    fp64 = 2 * 2 * 152 * 2.07e9 / 1e12
+    return hbm, src, fp64
+
+
+class Clocks:
+    """Samples nvidia-smi clocks / throttle reasons while running (start before, stop after)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else f"/tmp/hy_clocks_{os.getpid()}.csv"
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def setup_contexts(torch, api, inputs, dev):
+    pr = inputs.problem(DIM, K, M, n_levels=1, top=0)  # bottom clamped, top free
+    u = torch.tensor(inputs.smooth_field(DIM, K, M, seed=0), device=dev)
+    x = torch.tensor(inputs.gaussian_vector(inputs.n_dofs(DIM, K, M), seed=1), device=dev)
+    ctxs = {}
+    for var in ALL_VARIANTS:
+        c = api.Context(dev.index)
+        c.setup_problem(pr)
+        c.set_solver_params(coarse_eig_iters=5)  # one-level hierarchy: the estimate is not used here
+        c.set_displacement(u, var, level_dtype=1)  # FP64 and FP32 caches
+        ctxs[var] = c
+    return pr, u, x, ctxs
+
+
+def time_applies(torch, ctxs, variants, x, dtype, steps, warmup, flush, stream):
+    """Per-(step, variant) CUDA-event durations in ms, L2 flushed before every application."""
+    xin = x if dtype == 0 else x.float()
+    ys = {v: torch.empty_like(xin) for v in variants}
+    for _ in range(warmup):
+        for v in variants:
+            ctxs[v].apply_tangent(xin, ys[v], dtype=dtype)
+    torch.cuda.synchronize()
+    launches0 = sum(ctxs[v].kernel_launches() for v in variants)
+    ev = []
+    for _ in range(steps):
+        row = []
+        for v in variants:
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctxs[v].apply_tangent(xin, ys[v], dtype=dtype)
+            e1.record(stream)
+            row.append((e0, e1))
+        ev.append(row)
+    torch.cuda.synchronize()
+    launches = sum(ctxs[v].kernel_launches() for v in variants) - launches0
+    return np.array([[a.elapsed_time(b) for a, b in row] for row in ev]), ys, launches
+
+
+def solve_latency(torch, api, inputs, dev, reps=5):
+    """GMG-PCG solves of A(u) du = b on the 32^3 Q2 problem with 4 levels (coarsest 4^3), rtol 1e-8, with the
+    boundary conditions of the Newton solves (bottom clamped, top normal component prescribed): with the top
+    free, the tangent at this non-equilibrium state is indefinite on the coarsest level."""
+    pr = inputs.problem(DIM, K, M, n_levels=4, top=inputs.normal_top_mask(DIM))
+    u = torch.tensor(inputs.smooth_field(DIM, K, M, seed=0), device=dev)
+    b = torch.tensor(inputs.gaussian_vector(inputs.n_dofs(DIM, K, M), seed=2), device=dev)
+    out = {}
+    with api.Context(dev.index) as c:
+        c.setup_problem(pr)
+        cons = torch.tensor(inputs.constrained_mask(DIM, K, M, pr["masks"]), device=dev)
+        b[cons] = 0.0
+        for name, ldt in (("fp64", 0), ("mixed", 1)):
+            t0 = time.perf_counter()
+            c.set_displacement(u, "T4", level_dtype=ldt)
+            torch.cuda.synchronize()
+            setup_ms = (time.perf_counter() - t0) * 1e3
+            lat, its = [], []
+            x, it = c.pcg(b, rtol=1e-8, max_iter=500)  # warm-up
+            for _ in range(reps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                x, it = c.pcg(b, x, rtol=1e-8, max_iter=500)
+                torch.cuda.synchronize()
+                lat.append((time.perf_counter() - t0) * 1e3)
+                its.append(it)
+            info = c.level_info(0)
+            out[name] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                         "cg_iterations": int(np.median(its)), "setup_ms": setup_ms, "levels": 4,
+                         "coarse_degree": info["coarse_degree"], "coarse_interval": [info["coarse_lo"], info["coarse_hi"]],
+                         "rtol": 1e-8, "reps": reps}
+    return out
+
+
+def cpu_oracle_rate(seconds=10.0):
+    """Oracle element-by-element application on the same problem at 16^3 Q2 (1/8 of the cells)."""
+    from oracle.fem import Problem
+    from paper_1904_13131_gb300 import inputs
+    m = 16
+    pr = inputs.problem(DIM, K, m, n_levels=1, top=0)
+    P = Problem(DIM, K, m, pr["ids"][0], pr["mu"], pr["lam"], pr["masks"])
+    u = inputs.smooth_field(DIM, K, m, seed=0)
+    x = inputs.gaussian_vector(P.n_dofs, seed=1)
+    n_done, t0 = 0, time.perf_counter()
+    while True:
+        P.apply(u, x)
+        n_done += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    # dofs per second on the sample, scaled to the full workload by cells (same cost per cell)
+    cells_ratio = (M / m) ** DIM
+    full_dofs = inputs.n_dofs(DIM, K, M)
+    t_full = el / n_done * cells_ratio
+    return full_dofs / t_full / 1e9, n_done, el, f"oracle apply on the 16^3 Q2 sample ({P.n_dofs} dofs, " \
+        f"{m**DIM} cells = 1/{int(cells_ratio)} of the workload), {n_done} applications in {el:.1f} s, scaled by cells"
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    rate, n, el, sample = cpu_oracle_rate(seconds=max(5.0, 2.0 * (args.steps + args.warmup)))
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 3 * inputs_ndofs() / (rate * 1e9) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def inputs_ndofs():
+    return DIM * (K * M + 1) ** DIM
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    from paper_1904_13131_gb300 import api, build, inputs
+    build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream(dev)
+    pr, u, x, ctxs = setup_contexts(torch, api, inputs, dev)
+    n = inputs.n_dofs(DIM, K, M)
+    ncells = M**DIM
+    nqp = ncells * (K + 1) ** DIM
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    # ---- timed region: K steps of {T4, FC, NC} FP64 applications --------------------------------
+    clk = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    t_wall = time.perf_counter()
+    ms, ys, launches_timed = time_applies(torch, ctxs, VARIANTS, x, 0, args.steps, args.warmup, flush, stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - t_wall
+    clocks = clk.stop()
+    total_ms = float(ms.sum())
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = 3 * n * args.steps * world / (total_ms * 1e-3) / 1e9
+    per_var_ms = {v: float(np.median(ms[:, i])) for i, v in enumerate(VARIANTS)}
+
+    # ---- per-variant FP64 / FP32 throughput (untimed for the headline) ---------------------------
+    ms64, _, _ = time_applies(torch, ctxs, ALL_VARIANTS, x, 0, 5, 2, flush, stream)
+    ms32, _, _ = time_applies(torch, ctxs, ALL_VARIANTS, x, 1, 5, 2, flush, stream)
+    hbm, hbm_src, fp64_peak = peaks()
+    variants = {}
+    for i, v in enumerate(ALL_VARIANTS):
+        t64, t32 = float(np.median(ms64[:, i])), float(np.median(ms32[:, i]))
+        variants[v] = {
+            "f64_gdofs": n / (t64 * 1e-3) / 1e9, "f64_ms": t64,
+            "f64_tflops": flops_per_qp(v) * nqp / (t64 * 1e-3) / 1e12,
+            "f32_gdofs": n / (t32 * 1e-3) / 1e9, "f32_ms": t32,
+            "f32_gbs": bytes_per_apply(v, 4, nqp, n) / (t32 * 1e-3) / 1e9,
+            "f32_hbm_frac": bytes_per_apply(v, 4, nqp, n) / (t32 * 1e-3) / 1e9 / hbm,
+        }
+    # dominant kernel of the step: the slowest variant's FP64 apply (FP64-pipe bound)
+    dom = max(per_var_ms, key=per_var_ms.get)
+    ach = flops_per_qp(dom) * nqp / (per_var_ms[dom] * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": f"apply_kernel<3,3,{dom},double>", "achieved": ach, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None,
+                "peak_source": "FP64 pipe: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (derived, nominal 1.25 TFLOP/s)",
+                "algorithmic_flops_per_launch": flops_per_qp(dom) * nqp}
+
+    # ---- end to end through the public API: pinned host x -> device, 3 applies, results -> host ----
+    xh = x.cpu().pin_memory()
+    yh = {v: torch.empty(n, dtype=torch.float64).pin_memory() for v in VARIANTS}
+    xd = torch.empty_like(x)
+    e2e_ms = []
+    for it in range(args.warmup + args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        xd.copy_(xh, non_blocking=True)
+        for v in VARIANTS:
+            ctxs[v].apply_tangent(xd, ys[v])
+            yh[v].copy_(ys[v], non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if it >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_total = float(np.sum(e2e_ms))
+    e2e = {"value": 3 * n * len(e2e_ms) * world / (e2e_total * 1e-3) / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": int(x.numel() * 8), "d2h_bytes_per_step": int(3 * n * 8)}
+
+    solve = None
+    if not args.no_solve and rank == 0:
+        for c in ctxs.values():
+            c.close()
+        try:
+            solve = solve_latency(torch, api, inputs, dev)
+        except api.HyError as e:
+            solve = {"error": str(e)}
+
+    cpu = None
+    if rank == 0 and world == 1:
+        rate, nd, el, sample = cpu_oracle_rate(args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "dofs": n, "cells": ncells, "degree": K, "dim": DIM,
+                           "variants_per_step": list(VARIANTS), "l2": "flushed (256 MB write) before every application",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": int(launches_timed),
+                "per_variant_ms_f64": per_var_ms, "variants": variants, "solve": solve,
+                "wall_s_timed_region": wall, "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * hyperelastic.h -- C ABI of libhyperelastic: matrix-free finite-strain hyperelasticity with
+ * geometric multigrid on one GB300 GPU (arXiv 1904.13131, "A matrix-free approach for finite-strain
+ * hyperelastic problems using geometric multigrid").
+ *
+ * Problem class: compressible neo-Hookean solid (Sec. 2.3) on the unit square (dim 2, plane strain)
+ * or unit cube (dim 3), uniform m^dim mesh of Q_k Lagrange cells (k = 1..4) with GLL nodes and the
+ * (k+1)^dim Gauss rule (Sec. 7, Tables 1-2: q = p + 1); homogeneous or prescribed Dirichlet values on
+ * selected components of selected faces.
+ *
+ * Conventions for every call:
+ *  - Vectors are caller-owned DEVICE buffers (e.g. a torch tensor's data pointer) on the context's
+ *    device, in the canonical layout: nodes of the (k m + 1)^dim lattice in lexicographic order with
+ *    x fastest, the dim displacement components of a node interleaved (dof = node * dim + comp).
+ *    "Level" l counts from 0 (coarsest, m / 2^(L-1) cells per direction) to L-1 (finest, m cells).
+ *  - The library owns everything else (caches, level vectors, hierarchy) and frees it in
+ *    hy_destroy. It never frees caller buffers.
+ *  - Work is enqueued on the stream given to hy_create (borrowed, not owned); calls that return
+ *    scalars or reports synchronise that stream before returning.
+ *  - Every call returns a hy_status, never throws across the ABI and never aborts the process.
+ *    On error, hy_last_error() holds a one-line description. A kernel-side failure (J <= 0, NaN)
+ *    is reported through the status of the call that checks it, with the device left usable.
+ *  - Faces are numbered (-x, +x, -y, +y, -z, +z); a face mask is a bitmask of constrained
+ *    components (bit c = component c).
+ */
+#ifndef HYPERELASTIC_H
+#define HYPERELASTIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hy_ctx hy_ctx;
+
+typedef enum {
+  HY_OK = 0,
+  HY_ERR_ARG = 1,          /* invalid argument (size, degree, pointer, NaN input, ...) */
+  HY_ERR_STATE = 2,        /* call out of order (e.g. apply before set_displacement) */
+  HY_ERR_OOM = 3,          /* device allocation failed */
+  HY_ERR_CUDA = 4,         /* a CUDA runtime call failed */
+  HY_ERR_JNEG = 5,         /* J = det F <= 0 at some Gauss point (Sec. 2.1 requires J > 0) */
+  HY_ERR_NOCONV = 6,       /* an iteration reached its cap */
+  HY_ERR_TIMEOUT = 7,      /* a bounded device wait gave up */
+  HY_ERR_UNSUPPORTED = 8   /* valid but not built (e.g. degree 5) */
+} hy_status;
+
+typedef enum { HY_F64 = 0, HY_F32 = 1 } hy_dtype;
+
+/* Tangent-operator variants (Sec. 5):
+ *   HY_T4  cache F^{-1}, tau and the fourth-order tangent J*C per Gauss point (Algorithm 3)
+ *   HY_T2  cache F^{-1}, tau and two scalars of the neo-Hooke action (Algorithm 2)
+ *   HY_FC  cache F only; J, ln J, tau and the action recomputed in every application
+ *   HY_SC  cache mu - 2 lambda ln J only; F recomputed from the displacement (Algorithm 1)
+ *   HY_NC  cache nothing; everything recomputed from the displacement */
+typedef enum { HY_T4 = 0, HY_T2 = 1, HY_FC = 2, HY_SC = 3, HY_NC = 4 } hy_variant;
+
+/* Create a context on CUDA device `device`, enqueuing all work on `cuda_stream` (a cudaStream_t;
+ * NULL = the legacy default stream). The stream is borrowed: it must outlive the context. */
+hy_status hy_create(hy_ctx **out, int device, void *cuda_stream);
+/* Free every device buffer the context owns. NULL is accepted. */
+void hy_destroy(hy_ctx *ctx);
+const char *hy_status_str(hy_status s);
+const char *hy_last_error(const hy_ctx *ctx);
+
+/* Mesh and level hierarchy (Sec. 6: a hierarchy of uniformly refined meshes; Sec. 3: Q_k space).
+ * dim 2|3, degree 1..4, cells_per_dir m >= 1; n_levels >= 1 levels with m / 2^(L-1-l) cells on level l
+ * (m must stay even while halving). face_masks[2*dim] gives the constrained components of each
+ * face; the same homogeneous constraints hold on every level (Sec. 6). Replaces any previous mesh. */
+hy_status hy_mesh_setup(hy_ctx *ctx, int dim, int degree, int cells_per_dir, int n_levels,
+                        const uint32_t *face_masks);
+
+/* Number of dofs of level `level` (-1 = finest). */
+hy_status hy_num_dofs(const hy_ctx *ctx, int level, int64_t *n);
+
+/* Materials of level `level` (-1 = finest): HOST arrays cell_mat[m_l^dim] (ids < n_mat, cells in
+ * lexicographic order, x fastest) and mu[n_mat], lambda[n_mat] (Sec. 2.3). Every level needs one
+ * call before hy_set_displacement; n_mat <= 16. */
+hy_status hy_set_material(hy_ctx *ctx, int level, const uint8_t *cell_mat, const double *mu,
+                          const double *lambda, int n_mat);
+
+/* Linearisation point (Sec. 6). u_dev: fine-level FP64 displacement (device). The displacement is
+ * carried down to every level by nodal interpolation and each level's Gauss-point cache is built
+ * for `variant` from FP64 kinematics (F, J, ln J). level_dtype = HY_F32 selects the mixed-precision
+ * V-cycle (FP32 caches, smoother, transfers on every level but the coarsest, which stays FP64; the
+ * finest level gets both an FP64 and an FP32 cache). Also builds the level diagonals and the
+ * smoother / coarse-solver eigenvalue estimates. Returns HY_ERR_JNEG if J <= 0 anywhere. */
+hy_status hy_set_displacement(hy_ctx *ctx, const double *u_dev, hy_variant variant, hy_dtype level_dtype);
+
+/* y = A(u) x on the finest level (Eq. algebraic_tangent applied as in Eq. mf_vmult), with the
+ * Dirichlet treatment A~ = Z A Z + (I - Z): x is read as zero on constrained dofs and y equals x
+ * there. dtype selects the FP64 or FP32 cache (the FP32 one exists after set_displacement with
+ * HY_F32). x_dev and y_dev are device arrays of n_dofs elements of that type; they must not alias. */
+hy_status hy_apply_tangent(hy_ctx *ctx, const void *x_dev, void *y_dev, hy_dtype dtype);
+
+/* Same on any level (the level operators of the V-cycle, Sec. 6). */
+hy_status hy_vmult(hy_ctx *ctx, int level, const void *x_dev, void *y_dev, hy_dtype dtype);
+
+/* r = F(u) of Eq. weak_form (no traction term), FP64, zero on constrained rows; u_dev and r_dev are
+ * fine-level FP64 device vectors. HY_ERR_JNEG if J <= 0 at a Gauss point. */
+hy_status hy_residual(hy_ctx *ctx, const double *u_dev, double *r_dev);
+
+/* Diagonal of the constrained level operator (1 on constrained dofs), as used by the Chebyshev
+ * smoother (Sec. 7); d_dev holds n_dofs(level) elements of dtype. */
+hy_status hy_diagonal(hy_ctx *ctx, int level, void *d_dev, hy_dtype dtype);
+
+/* One V-cycle of the geometric multigrid preconditioner (Secs. 6-7) on the finest level:
+ * z = V r for FP64 device vectors r, z (zero initial guess, constrained entries of z zero). */
+hy_status hy_gmg_vcycle(hy_ctx *ctx, const double *r_dev, double *z_dev);
+
+/* Solver knobs (Sec. 7 defaults in brackets). */
+typedef struct {
+  int cheb_degree;          /* [4]   Chebyshev degree of the level smoother */
+  int cheb_sweeps;          /* [1]   smoother applications per pre-/post-smoothing */
+  double cheb_lo;           /* [0.6] lower end of the smoothing range, times lambda_max */
+  double cheb_hi;           /* [1.2] upper end, times lambda_max */
+  int eig_iters;            /* [30]  CG iterations of the lambda_max estimate */
+  int coarse_eig_iters;     /* [0 = number of free coarse dofs] CG iterations on the coarsest level */
+  double coarse_reduction;  /* [1e-3] residual reduction of the coarse Chebyshev solve */
+} hy_solver_params;
+
+hy_status hy_set_solver_params(hy_ctx *ctx, const hy_solver_params *p);
+hy_status hy_get_solver_params(const hy_ctx *ctx, hy_solver_params *p);
+
+/* Estimates held by the context after set_displacement: lmax of level `level` (levels >= 1), and
+ * for the coarsest level its Chebyshev interval [lo, hi] and degree. Any output may be NULL. */
+hy_status hy_level_info(const hy_ctx *ctx, int level, double *lmax, double *coarse_lo, double *coarse_hi,
+                        int *coarse_degree);
+/* Override the estimates (levels >= 1: lmax; level 0: lo, hi), e.g. to mirror another solver. */
+hy_status hy_set_level_info(hy_ctx *ctx, int level, double lmax, double coarse_lo, double coarse_hi);
+
+/* Copy the level-`level` displacement (the carried-down linearisation point) into u_dev (FP64). */
+hy_status hy_level_displacement(const hy_ctx *ctx, int level, double *u_dev);
+
+/* Transfers between level l-1 (coarse) and l (fine), constrained entries zeroed (Sec. 6):
+ * fine += P coarse (prolongate_add) and coarse = P^T fine (restrict). dtype as for the level. */
+hy_status hy_prolongate_add(hy_ctx *ctx, int fine_level, const void *coarse_dev, void *fine_dev, hy_dtype dtype);
+hy_status hy_restrict(hy_ctx *ctx, int fine_level, const void *fine_dev, void *coarse_dev, hy_dtype dtype);
+
+/* Preconditioned CG (FP64) on the finest level: A~ x = b with the V-cycle preconditioner, zero
+ * initial guess, stop at ||r|| <= rtol ||b||. iterations may be NULL. HY_ERR_NOCONV at max_iter. */
+hy_status hy_pcg(hy_ctx *ctx, const double *b_dev, double *x_dev, double rtol, int max_iter, int *iterations);
+
+/* Newton-Raphson with load steps (Sec. 3, Sec. 7). */
+typedef struct {
+  int load_steps;            /* [5] prescribed values reached in equal increments */
+  int max_newton;            /* [25] per load step */
+  double newton_rtol;        /* [1e-10] ||R_free|| <= rtol * ||first right-hand side of the step|| */
+  double newton_atol;        /* [1e-14] or ||R_free|| <= atol */
+  double cg_rtol;            /* [1e-8] */
+  int cg_max_iter;           /* [1000] */
+  hy_variant variant;        /* [HY_T4] tangent variant of every level */
+  hy_dtype level_dtype;      /* [HY_F64] HY_F32 = mixed-precision V-cycle */
+  double face_values[6][3];  /* final prescribed displacement per face and component */
+} hy_newton_params;
+
+typedef struct {
+  int load_steps_done;
+  int newton_iterations[64];  /* per load step (first 64 steps) */
+  int cg_iterations_total;
+  int cg_iterations_max;
+  double final_residual;      /* ||R_free|| at the end */
+  int backtracks;             /* J <= 0 halvings taken */
+} hy_newton_report;
+
+void hy_newton_default_params(hy_newton_params *p);
+/* Solve for the equilibrium displacement: u_inout_dev (fine FP64, device) holds the start state on
+ * entry (its constrained values are overwritten by the load path) and the solution on return; on
+ * error it holds the last accepted iterate. rep may be NULL. */
+hy_status hy_newton_solve(hy_ctx *ctx, const hy_newton_params *p, double *u_inout_dev, hy_newton_report *rep);
+
+/* Deterministic FP64 dot product of two fine-level device vectors (fixed reduction order, so
+ * repeated calls give identical bits). Uses a scratch buffer owned by the context. */
+hy_status hy_dot(hy_ctx *ctx, const double *a_dev, const double *b_dev, int64_t n, double *result);
+
+/* Number of kernels this context has launched since creation (for accounting). */
+hy_status hy_kernel_launches(const hy_ctx *ctx, int64_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HYPERELASTIC_H */

@@ -170,6 +170,8 @@ class Hierarchy:
             it = nfree if self.coarse_eig_iters is None else min(nfree, self.coarse_eig_iters)
             ritz = self.estimate(0, it)
             self.coarse_lo, self.coarse_hi = ritz.min(), self.smooth_hi * ritz.max()
+            if not self.coarse_lo > 0:
+                raise ValueError("coarsest-level tangent is not positive definite")
         self.coarse_deg = coarse_degree(self.coarse_lo, self.coarse_hi, self.coarse_reduction)
 
     def start_vector(self, l):

@@ -1,0 +1,307 @@
+"""Thin ctypes binding of libhyperelastic (include/hyperelastic.h), same names as the C ABI.
+
+Argument marshalling only: torch tensors provide device memory and the CUDA stream; every step of
+the computation runs in the library's kernels. The library must be built (see build.py); loading
+fails loudly otherwise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhyperelastic.so")
+
+STATUS = {0: "HY_OK", 1: "HY_ERR_ARG", 2: "HY_ERR_STATE", 3: "HY_ERR_OOM", 4: "HY_ERR_CUDA", 5: "HY_ERR_JNEG",
+          6: "HY_ERR_NOCONV", 7: "HY_ERR_TIMEOUT", 8: "HY_ERR_UNSUPPORTED"}
+VARIANTS = {"T4": 0, "T2": 1, "FC": 2, "SC": 3, "NC": 4}
+F64, F32 = 0, 1
+
+# every symbol the header declares (checked by the CPU test suite)
+EXPORTED = ("hy_create", "hy_destroy", "hy_status_str", "hy_last_error", "hy_mesh_setup", "hy_num_dofs",
+            "hy_set_material", "hy_set_displacement", "hy_apply_tangent", "hy_vmult", "hy_residual", "hy_diagonal",
+            "hy_gmg_vcycle", "hy_set_solver_params", "hy_get_solver_params", "hy_level_info", "hy_set_level_info",
+            "hy_level_displacement", "hy_prolongate_add", "hy_restrict", "hy_pcg", "hy_newton_default_params",
+            "hy_newton_solve", "hy_dot", "hy_kernel_launches")
+
+
+class HyError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = STATUS.get(status, str(status))
+
+
+class SolverParams(ctypes.Structure):
+    _fields_ = [("cheb_degree", ctypes.c_int), ("cheb_sweeps", ctypes.c_int), ("cheb_lo", ctypes.c_double),
+                ("cheb_hi", ctypes.c_double), ("eig_iters", ctypes.c_int), ("coarse_eig_iters", ctypes.c_int),
+                ("coarse_reduction", ctypes.c_double)]
+
+
+class NewtonParams(ctypes.Structure):
+    _fields_ = [("load_steps", ctypes.c_int), ("max_newton", ctypes.c_int), ("newton_rtol", ctypes.c_double),
+                ("newton_atol", ctypes.c_double), ("cg_rtol", ctypes.c_double), ("cg_max_iter", ctypes.c_int),
+                ("variant", ctypes.c_int), ("level_dtype", ctypes.c_int),
+                ("face_values", (ctypes.c_double * 3) * 6)]
+
+
+class NewtonReport(ctypes.Structure):
+    _fields_ = [("load_steps_done", ctypes.c_int), ("newton_iterations", ctypes.c_int * 64),
+                ("cg_iterations_total", ctypes.c_int), ("cg_iterations_max", ctypes.c_int),
+                ("final_residual", ctypes.c_double), ("backtracks", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libhyperelastic.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_1904_13131_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "hy_create": [ctypes.POINTER(vp), i32, vp],
+        "hy_destroy": [vp],
+        "hy_status_str": [i32],
+        "hy_last_error": [vp],
+        "hy_mesh_setup": [vp, i32, i32, i32, i32, ctypes.POINTER(ctypes.c_uint32)],
+        "hy_num_dofs": [vp, i32, ctypes.POINTER(i64)],
+        "hy_set_material": [vp, i32, vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), i32],
+        "hy_set_displacement": [vp, vp, i32, i32],
+        "hy_apply_tangent": [vp, vp, vp, i32],
+        "hy_vmult": [vp, i32, vp, vp, i32],
+        "hy_residual": [vp, vp, vp],
+        "hy_diagonal": [vp, i32, vp, i32],
+        "hy_gmg_vcycle": [vp, vp, vp],
+        "hy_set_solver_params": [vp, ctypes.POINTER(SolverParams)],
+        "hy_get_solver_params": [vp, ctypes.POINTER(SolverParams)],
+        "hy_level_info": [vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(dbl),
+                          ctypes.POINTER(i32)],
+        "hy_set_level_info": [vp, i32, dbl, dbl, dbl],
+        "hy_level_displacement": [vp, i32, vp],
+        "hy_prolongate_add": [vp, i32, vp, vp, i32],
+        "hy_restrict": [vp, i32, vp, vp, i32],
+        "hy_pcg": [vp, vp, vp, dbl, i32, ctypes.POINTER(i32)],
+        "hy_newton_default_params": [ctypes.POINTER(NewtonParams)],
+        "hy_newton_solve": [vp, ctypes.POINTER(NewtonParams), vp, ctypes.POINTER(NewtonReport)],
+        "hy_dot": [vp, vp, vp, i64, ctypes.POINTER(dbl)],
+        "hy_kernel_launches": [vp, ctypes.POINTER(i64)],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = None if name in ("hy_destroy", "hy_newton_default_params") else ctypes.c_int
+    lib.hy_status_str.restype = ctypes.c_char_p
+    lib.hy_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One hy_ctx on a CUDA device, enqueuing on the given torch stream (default: the current one)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self._torch = torch
+        self.lib = load_library()
+        self.device = torch.device("cuda", device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        h = ctypes.c_void_p()
+        st = self.lib.hy_create(ctypes.byref(h), device, ctypes.c_void_p(stream.cuda_stream))
+        if st != 0:
+            raise HyError(st, "hy_create failed")
+        self.h = h
+        self.dim = self.degree = self.m = self.n_levels = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hy_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _ck(self, st):
+        if st != 0:
+            raise HyError(st, self.lib.hy_last_error(self.h).decode())
+
+    def _vec(self, t, n, dtype):
+        torch = self._torch
+        want = torch.float64 if dtype == F64 else torch.float32
+        if t.device != self.device or t.dtype != want or not t.is_contiguous() or t.numel() != n:
+            raise ValueError(f"expected a contiguous {want} tensor of {n} elements on {self.device}")
+        return _ptr(t)
+
+    def empty(self, level=-1, dtype=F64):
+        torch = self._torch
+        return torch.empty(self.num_dofs(level), dtype=torch.float64 if dtype == F64 else torch.float32,
+                           device=self.device)
+
+    # ---- mesh / material -------------------------------------------------------------------------
+    def mesh_setup(self, dim, degree, cells_per_dir, n_levels, face_masks):
+        fm = (ctypes.c_uint32 * (2 * dim))(*[int(x) for x in face_masks[: 2 * dim]])
+        self._ck(self.lib.hy_mesh_setup(self.h, dim, degree, cells_per_dir, n_levels, fm))
+        self.dim, self.degree, self.m, self.n_levels = dim, degree, cells_per_dir, n_levels
+
+    def num_dofs(self, level=-1):
+        n = ctypes.c_int64()
+        self._ck(self.lib.hy_num_dofs(self.h, level, ctypes.byref(n)))
+        return n.value
+
+    def set_material(self, level, cell_mat, mu, lam):
+        ids = np.ascontiguousarray(cell_mat, dtype=np.uint8)
+        mu = np.ascontiguousarray(mu, dtype=np.float64)
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        self._ck(self.lib.hy_set_material(self.h, level, ids.ctypes.data_as(ctypes.c_void_p),
+                                          mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                          lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(mu)))
+
+    def setup_problem(self, problem: dict, n_levels: int | None = None):
+        """mesh_setup + set_material on every level from an inputs.problem(...) bundle."""
+        L = len(problem["levels_m"]) if n_levels is None else n_levels
+        self.mesh_setup(problem["dim"], problem["k"], problem["m"], L, problem["masks"])
+        for l in range(L):
+            self.set_material(l, problem["ids"][l], problem["mu"], problem["lam"])
+
+    # ---- state / operators ----------------------------------------------------------------------
+    def set_displacement(self, u, variant="T4", level_dtype=F64):
+        self._ck(self.lib.hy_set_displacement(self.h, self._vec(u, self.num_dofs(), F64), VARIANTS[variant],
+                                              level_dtype))
+
+    def apply_tangent(self, x, y=None, dtype=F64):
+        n = self.num_dofs()
+        if y is None:
+            y = self.empty(-1, dtype)
+        self._ck(self.lib.hy_apply_tangent(self.h, self._vec(x, n, dtype), self._vec(y, n, dtype), dtype))
+        return y
+
+    def vmult(self, level, x, y=None, dtype=F64):
+        n = self.num_dofs(level)
+        if y is None:
+            y = self.empty(level, dtype)
+        self._ck(self.lib.hy_vmult(self.h, level, self._vec(x, n, dtype), self._vec(y, n, dtype), dtype))
+        return y
+
+    def residual(self, u, r=None):
+        n = self.num_dofs()
+        if r is None:
+            r = self.empty()
+        self._ck(self.lib.hy_residual(self.h, self._vec(u, n, F64), self._vec(r, n, F64)))
+        return r
+
+    def diagonal(self, level=-1, dtype=F64):
+        d = self.empty(level, dtype)
+        self._ck(self.lib.hy_diagonal(self.h, level, self._vec(d, self.num_dofs(level), dtype), dtype))
+        return d
+
+    def gmg_vcycle(self, r, z=None):
+        n = self.num_dofs()
+        if z is None:
+            z = self.empty()
+        self._ck(self.lib.hy_gmg_vcycle(self.h, self._vec(r, n, F64), self._vec(z, n, F64)))
+        return z
+
+    def set_solver_params(self, **kw):
+        p = self.get_solver_params()
+        for k, v in kw.items():
+            setattr(p, k, v)
+        self._ck(self.lib.hy_set_solver_params(self.h, ctypes.byref(p)))
+
+    def get_solver_params(self):
+        p = SolverParams()
+        self._ck(self.lib.hy_get_solver_params(self.h, ctypes.byref(p)))
+        return p
+
+    def level_info(self, level):
+        lm, lo, hi, dg = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        self._ck(self.lib.hy_level_info(self.h, level, ctypes.byref(lm), ctypes.byref(lo), ctypes.byref(hi),
+                                        ctypes.byref(dg)))
+        return {"lmax": lm.value, "coarse_lo": lo.value, "coarse_hi": hi.value, "coarse_degree": dg.value}
+
+    def set_level_info(self, level, lmax=0.0, coarse_lo=0.0, coarse_hi=0.0):
+        self._ck(self.lib.hy_set_level_info(self.h, level, lmax, coarse_lo, coarse_hi))
+
+    def level_displacement(self, level):
+        u = self.empty(level)
+        self._ck(self.lib.hy_level_displacement(self.h, level, self._vec(u, self.num_dofs(level), F64)))
+        return u
+
+    def prolongate_add(self, fine_level, coarse, fine, dtype=F64):
+        fl = fine_level if fine_level >= 0 else self.n_levels + fine_level
+        self._ck(self.lib.hy_prolongate_add(self.h, fl, self._vec(coarse, self.num_dofs(fl - 1), dtype),
+                                            self._vec(fine, self.num_dofs(fl), dtype), dtype))
+        return fine
+
+    def restrict(self, fine_level, fine, coarse=None, dtype=F64):
+        fl = fine_level if fine_level >= 0 else self.n_levels + fine_level
+        if coarse is None:
+            coarse = self.empty(fl - 1, dtype)
+        self._ck(self.lib.hy_restrict(self.h, fl, self._vec(fine, self.num_dofs(fl), dtype),
+                                      self._vec(coarse, self.num_dofs(fl - 1), dtype), dtype))
+        return coarse
+
+    def pcg(self, b, x=None, rtol=1e-8, max_iter=1000):
+        n = self.num_dofs()
+        if x is None:
+            x = self.empty()
+        its = ctypes.c_int()
+        self._ck(self.lib.hy_pcg(self.h, self._vec(b, n, F64), self._vec(x, n, F64), rtol, max_iter,
+                                 ctypes.byref(its)))
+        return x, its.value
+
+    @staticmethod
+    def newton_params(**kw):
+        p = NewtonParams()
+        load_library().hy_newton_default_params(ctypes.byref(p))
+        face_values = kw.pop("face_values", None)
+        for k, v in kw.items():
+            if k == "variant":
+                v = VARIANTS[v]
+            setattr(p, k, v)
+        if face_values is not None:
+            for f in range(6):
+                for c in range(3):
+                    p.face_values[f][c] = float(face_values[f][c]) if f < len(face_values) else 0.0
+        return p
+
+    def newton_solve(self, u, params: NewtonParams):
+        rep = NewtonReport()
+        st = self.lib.hy_newton_solve(self.h, ctypes.byref(params), self._vec(u, self.num_dofs(), F64),
+                                      ctypes.byref(rep))
+        report = {"load_steps_done": rep.load_steps_done,
+                  "newton_iterations": list(rep.newton_iterations[: max(rep.load_steps_done, params.load_steps)]),
+                  "cg_iterations_total": rep.cg_iterations_total, "cg_iterations_max": rep.cg_iterations_max,
+                  "final_residual": rep.final_residual, "backtracks": rep.backtracks}
+        self._ck(st)
+        return report
+
+    def dot(self, a, b):
+        n = a.numel()
+        out = ctypes.c_double()
+        self._ck(self.lib.hy_dot(self.h, self._vec(a, n, F64), self._vec(b, n, F64), n, ctypes.byref(out)))
+        return out.value
+
+    def kernel_launches(self):
+        c = ctypes.c_int64()
+        self._ck(self.lib.hy_kernel_launches(self.h, ctypes.byref(c)))
+        return c.value

@@ -1,0 +1,1251 @@
+// C ABI of libhyperelastic (include/hyperelastic.h): context, mesh hierarchy, Gauss-point state,
+// tangent action, residual, geometric multigrid (Secs. 6-7), PCG and Newton (Secs. 3, 7).
+// Host code orchestrates; every step on vectors runs in the kernels of this library.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/hyperelastic.h"
+#include "cell_kernels.cuh"
+#include "launch.cuh"
+
+using namespace hy;
+
+namespace {
+
+// ---------------------------------------------------------------------------------------------
+// 1D Q_k element tables from their definitions: Legendre recurrences for the GLL points (roots of
+// P_k' plus the end points) and the Gauss points (roots of P_n), Newton iteration to full precision,
+// Lagrange polynomials by their product formula.
+void legendre(int n, double x, double& p, double& dp) {
+  double p0 = 1.0, p1 = x;
+  if (n == 0) { p = 1.0; dp = 0.0; return; }
+  for (int j = 2; j <= n; ++j) {
+    const double p2 = ((2.0 * j - 1.0) * x * p1 - (j - 1.0) * p0) / j;
+    p0 = p1;
+    p1 = p2;
+  }
+  p = p1;
+  dp = n * (x * p1 - p0) / (x * x - 1.0);
+}
+
+std::vector<double> gauss_points(int n, std::vector<double>& w) {
+  std::vector<double> x(n);
+  w.assign(n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    double t = -std::cos(M_PI * (j + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double p, dp;
+      legendre(n, t, p, dp);
+      const double dt = p / dp;
+      t -= dt;
+      if (std::fabs(dt) < 1e-17) break;
+    }
+    double p, dp;
+    legendre(n, t, p, dp);
+    x[j] = 0.5 * (t + 1.0);
+    w[j] = 1.0 / ((1.0 - t * t) * dp * dp);  // 2/((1-t^2) P'^2) on [-1,1], halved for [0,1]
+  }
+  std::sort(x.begin(), x.end());
+  // weights are symmetric; recompute in sorted order
+  for (int j = 0; j < n; ++j) {
+    double p, dp;
+    const double t = 2.0 * x[j] - 1.0;
+    legendre(n, t, p, dp);
+    w[j] = 1.0 / ((1.0 - t * t) * dp * dp);
+  }
+  return x;
+}
+
+std::vector<double> gll_points(int k) {
+  std::vector<double> x(k + 1);
+  x[0] = 0.0;
+  x[k] = 1.0;
+  for (int j = 1; j < k; ++j) {
+    double t = -std::cos(M_PI * j / k);
+    for (int it = 0; it < 100; ++it) {
+      double p, dp;
+      legendre(k, t, p, dp);
+      const double d2p = (2.0 * t * dp - k * (k + 1.0) * p) / (1.0 - t * t);  // Legendre ODE
+      const double dt = dp / d2p;
+      t -= dt;
+      if (std::fabs(dt) < 1e-17) break;
+    }
+    x[j] = 0.5 * (t + 1.0);
+  }
+  std::sort(x.begin(), x.end());
+  return x;
+}
+
+double lagr(const std::vector<double>& nd, int j, double x) {
+  double v = 1.0;
+  for (size_t m = 0; m < nd.size(); ++m)
+    if ((int)m != j) v *= (x - nd[m]) / (nd[j] - nd[m]);
+  return v;
+}
+double dlagr(const std::vector<double>& nd, int j, double x) {
+  double s = 0.0;
+  for (size_t m = 0; m < nd.size(); ++m) {
+    if ((int)m == j) continue;
+    double t = 1.0 / (nd[j] - nd[m]);
+    for (size_t l = 0; l < nd.size(); ++l)
+      if ((int)l != j && l != m) t *= (x - nd[l]) / (nd[j] - nd[l]);
+    s += t;
+  }
+  return s;
+}
+
+// Extreme eigenvalues of the symmetric tridiagonal (diag a, off-diagonal b) by Sturm-count bisection.
+int sturm_count(const std::vector<double>& a, const std::vector<double>& b, double x) {
+  int cnt = 0;
+  double d = a[0] - x;
+  if (d < 0) ++cnt;
+  for (size_t i = 1; i < a.size(); ++i) {
+    if (d == 0.0) d = 1e-300;
+    d = a[i] - x - b[i - 1] * b[i - 1] / d;
+    if (d < 0) ++cnt;
+  }
+  return cnt;
+}
+void tridiag_extremes(const std::vector<double>& a, const std::vector<double>& b, double& lmin, double& lmax) {
+  const int n = (int)a.size();
+  double lo = a[0], hi = a[0];
+  for (int i = 0; i < n; ++i) {
+    const double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < n ? std::fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  double l = lo, h = hi;
+  for (int it = 0; it < 200 && h - l > 1e-16 * std::max(std::fabs(h), std::fabs(l)); ++it) {
+    const double mid = 0.5 * (l + h);
+    if (sturm_count(a, b, mid) >= n) h = mid; else l = mid;
+  }
+  lmax = h;
+  l = lo;
+  h = hi;
+  for (int it = 0; it < 200 && h - l > 1e-16 * std::max(std::fabs(h), std::fabs(l)); ++it) {
+    const double mid = 0.5 * (l + h);
+    if (sturm_count(a, b, mid) >= 1) h = mid; else l = mid;
+  }
+  lmin = h;
+}
+
+template <typename T> struct DT;
+template <> struct DT<double> { static constexpr hy_dtype v = HY_F64; };
+template <> struct DT<float> { static constexpr hy_dtype v = HY_F32; };
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+struct Level {
+  Geom g{};
+  long long nnodes = 0, ndofs = 0, nqp = 0;
+  uint8_t* d_mat = nullptr;
+  Mat<double> mt64{};
+  Mat<float> mt32{};
+  bool mat_set = false;
+  double* d_u64 = nullptr;
+  float* d_u32 = nullptr;
+  double* d_c64 = nullptr;
+  float* d_c32 = nullptr;
+  size_t c64_len = 0, c32_len = 0;
+  bool has64 = false, has32 = false;
+  double* d_diag = nullptr;
+  double* d_dinv64 = nullptr;
+  float* d_dinv32 = nullptr;
+  double lmax = 0.0;
+  double* w64[5] = {};  // V-cycle vectors b, x, r, d, t
+  float* w32[5] = {};
+};
+
+struct Transfer {  // level l-1 (coarse) <-> l (fine); the same 1D tables act along every axis
+  int Lc = 0, Lf = 0, Ep = 0, Er = 0, Ei = 0;
+  int *d_pstart = nullptr, *d_rstart = nullptr, *d_istart = nullptr;
+  double *d_pw64 = nullptr, *d_rw64 = nullptr, *d_iw64 = nullptr;
+  float *d_pw32 = nullptr, *d_rw32 = nullptr;
+};
+
+struct hy_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int dim = 0, k = 0, n = 0, nlev = 0;
+  uint32_t fm[6] = {0, 0, 0, 0, 0, 0};
+  std::vector<Level> lev;
+  std::vector<Transfer> tr;
+  Basis1D<double> b64{};
+  Basis1D<float> b32{};
+  hy_solver_params sp{4, 1, 0.6, 1.2, 30, 0, 1e-3};
+  int var = -1;
+  bool mixed = false;
+  bool state_ok = false;
+  double coarse_lo = 0, coarse_hi = 0;
+  int coarse_deg = 0;
+  unsigned* d_err = nullptr;
+  unsigned long long* d_jmin = nullptr;
+  double* d_partials = nullptr;
+  double* d_scal = nullptr;
+  double* d_face = nullptr;
+  double *tmp64a = nullptr, *tmp64b = nullptr;
+  float *tmp32a = nullptr, *tmp32b = nullptr, *tmp32c = nullptr;
+  size_t tmp_len = 0;
+  double* f64[10] = {};  // fine-level FP64 work vectors of PCG / Newton
+  long long launches = 0;
+  bool verbose = false;  // HY_VERBOSE=1: per-iteration diagnostics on stderr
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+#define HY_CK(call)                                                                                     \
+  do {                                                                                                  \
+    cudaError_t e_ = (call);                                                                            \
+    if (e_ != cudaSuccess) {                                                                            \
+      ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);                                     \
+      return e_ == cudaErrorMemoryAllocation ? HY_ERR_OOM : HY_ERR_CUDA;                                \
+    }                                                                                                   \
+  } while (0)
+#define HY_TRY(expr)                                                                                    \
+  do {                                                                                                  \
+    hy_status s_ = (expr);                                                                              \
+    if (s_ != HY_OK) return s_;                                                                         \
+  } while (0)
+
+hy_status fail(hy_ctx* ctx, hy_status s, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return s;
+}
+
+template <typename T>
+hy_status dalloc(hy_ctx* ctx, T** p, size_t n) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+  if (e != cudaSuccess) {
+    ctx->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? HY_ERR_OOM : HY_ERR_CUDA;
+  }
+  ctx->allocs.push_back(q);
+  *p = (T*)q;
+  return HY_OK;
+}
+
+void dfree(hy_ctx* ctx, void* p) {
+  if (!p) return;
+  auto it = std::find(ctx->allocs.begin(), ctx->allocs.end(), p);
+  if (it != ctx->allocs.end()) ctx->allocs.erase(it);
+  cudaFree(p);
+}
+
+hy_status check_launch(hy_ctx* ctx, int nlaunch) {
+  ctx->launches += nlaunch;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(ctx, HY_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  return HY_OK;
+}
+
+void free_mesh(hy_ctx* ctx) {
+  for (void* p : ctx->allocs) cudaFree(p);
+  ctx->allocs.clear();
+  ctx->lev.clear();
+  ctx->tr.clear();
+  ctx->d_err = nullptr;
+  ctx->d_jmin = nullptr;
+  ctx->d_partials = nullptr;
+  ctx->d_scal = nullptr;
+  ctx->d_face = nullptr;
+  ctx->tmp64a = ctx->tmp64b = nullptr;
+  ctx->tmp32a = ctx->tmp32b = ctx->tmp32c = nullptr;
+  for (auto& p : ctx->f64) p = nullptr;
+  ctx->state_ok = false;
+  ctx->var = -1;
+}
+
+int lev_index(const hy_ctx* ctx, int level) { return level < 0 ? ctx->nlev - 1 : level; }
+
+template <typename T>
+CellArgs<T> cell_args(hy_ctx* ctx, Level& L) {
+  CellArgs<T> a{};
+  a.mat = L.d_mat;
+  a.err = ctx->d_err;
+  a.jmin_bits = ctx->d_jmin;
+  a.g = L.g;
+  a.nqp = L.nqp;
+  if constexpr (sizeof(T) == 8) {
+    a.mt = L.mt64;
+    a.b = ctx->b64;
+  } else {
+    a.mt = L.mt32;
+    a.b = ctx->b32;
+  }
+  return a;
+}
+
+CellFn<double> apply_fn(hy_ctx* ctx, double*, int var) {
+  return ctx->dim == 2 ? apply_fn_f64_2d(ctx->n, var) : apply_fn_f64_3d(ctx->n, var);
+}
+CellFn<float> apply_fn(hy_ctx* ctx, float*, int var) {
+  return ctx->dim == 2 ? apply_fn_f32_2d(ctx->n, var) : apply_fn_f32_3d(ctx->n, var);
+}
+
+// y = A~ x on level l in precision T (x zero on constrained dofs on read, y = x there).
+template <typename T>
+hy_status vmult(hy_ctx* ctx, int l, const T* x, T* y, bool constrained_in = true) {
+  Level& L = ctx->lev[l];
+  const bool have = sizeof(T) == 8 ? L.has64 : L.has32;
+  if (!have) return fail(ctx, HY_ERR_STATE, "no Gauss-point cache of this precision on this level");
+  CellArgs<T> a = cell_args<T>(ctx, L);
+  a.x = x;
+  a.y = y;
+  if constexpr (sizeof(T) == 8) {
+    a.cache = L.d_c64;
+    a.ubar = L.d_u64;
+  } else {
+    a.cache = L.d_c32;
+    a.ubar = L.d_u32;
+  }
+  if (constrained_in) {
+    launch_prep_out<T>(x, y, L.nnodes, ctx->dim, L.g, ctx->stream);
+  } else {
+    // raw operator rows of the free dofs applied to x including its constrained entries
+    cudaMemsetAsync(y, 0, sizeof(T) * L.ndofs, ctx->stream);
+    a.g.fm[0] = a.g.fm[1] = a.g.fm[2] = a.g.fm[3] = a.g.fm[4] = a.g.fm[5] = 0;
+  }
+  CellFn<T> fn = apply_fn(ctx, (T*)nullptr, ctx->var);
+  if (!fn) return fail(ctx, HY_ERR_UNSUPPORTED, "no kernel for this dim/degree/variant");
+  fn(a, ctx->stream);
+  if (!constrained_in) launch_zero_constrained<T>(y, L.nnodes, ctx->dim, L.g, ctx->stream);
+  return check_launch(ctx, 2);
+}
+
+template <typename T>
+hy_status dot(hy_ctx* ctx, const T* a, const T* b, long long n, double* out) {
+  launch_dot<T>(a, b, n, ctx->d_partials, ctx->d_scal, ctx->stream);
+  HY_TRY(check_launch(ctx, 2));
+  HY_CK(cudaMemcpyAsync(out, ctx->d_scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  HY_CK(cudaStreamSynchronize(ctx->stream));
+  return HY_OK;
+}
+
+template <typename T> T* wvec(Level& L, int i);
+template <> double* wvec<double>(Level& L, int i) { return L.w64[i]; }
+template <> float* wvec<float>(Level& L, int i) { return L.w32[i]; }
+template <typename T> T* dinv_of(Level& L);
+template <> double* dinv_of<double>(Level& L) { return L.d_dinv64; }
+template <> float* dinv_of<float>(Level& L) { return L.d_dinv32; }
+template <typename T> T* pw_of(Transfer& t);
+template <> double* pw_of<double>(Transfer& t) { return t.d_pw64; }
+template <> float* pw_of<float>(Transfer& t) { return t.d_pw32; }
+template <typename T> T* rw_of(Transfer& t);
+template <> double* rw_of<double>(Transfer& t) { return t.d_rw64; }
+template <> float* rw_of<float>(Transfer& t) { return t.d_rw32; }
+template <typename T> T* tmp_of(hy_ctx* c, int i);
+template <> double* tmp_of<double>(hy_ctx* c, int i) { return i == 0 ? c->tmp64a : c->tmp64b; }
+template <> float* tmp_of<float>(hy_ctx* c, int i) { return i == 0 ? c->tmp32a : c->tmp32b; }
+
+// fine += P coarse (fine level l), constrained coarse entries read as zero, constrained fine rows zero.
+template <typename T>
+hy_status prolongate_add(hy_ctx* ctx, int l, const T* coarse, T* fine) {
+  Transfer& t = ctx->tr[l];
+  const int d = ctx->dim;
+  int Lin[3] = {t.Lc, t.Lc, t.Lc};
+  const T* src = coarse;
+  for (int ax = 0; ax < d; ++ax) {
+    int Lout[3] = {Lin[0], Lin[1], Lin[2]};
+    Lout[ax] = t.Lf;
+    const bool last = ax == d - 1;
+    T* dst = last ? fine : tmp_of<T>(ctx, ax & 1);
+    launch_sweep<T>(src, dst, d, Lin, Lout, ax, t.d_pstart, pw_of<T>(t), t.Ep, last, ax == 0 ? &ctx->lev[l - 1].g : nullptr,
+                    last ? &ctx->lev[l].g : nullptr, ctx->stream);
+    src = dst;
+    Lin[ax] = t.Lf;
+  }
+  return check_launch(ctx, d);
+}
+
+// coarse = P^T fine (fine level l), with the same constraint masks.
+template <typename T>
+hy_status restrict_to(hy_ctx* ctx, int l, const T* fine, T* coarse) {
+  Transfer& t = ctx->tr[l];
+  const int d = ctx->dim;
+  int Lin[3] = {t.Lf, t.Lf, t.Lf};
+  const T* src = fine;
+  for (int ax = 0; ax < d; ++ax) {
+    int Lout[3] = {Lin[0], Lin[1], Lin[2]};
+    Lout[ax] = t.Lc;
+    const bool last = ax == d - 1;
+    T* dst = last ? coarse : tmp_of<T>(ctx, ax & 1);
+    launch_sweep<T>(src, dst, d, Lin, Lout, ax, t.d_rstart, rw_of<T>(t), t.Er, false, ax == 0 ? &ctx->lev[l].g : nullptr,
+                    last ? &ctx->lev[l - 1].g : nullptr, ctx->stream);
+    src = dst;
+    Lin[ax] = t.Lc;
+  }
+  return check_launch(ctx, d);
+}
+
+// Level l-1 displacement = nodal interpolation of the level-l one (Sec. 6, carried down).
+hy_status interpolate_down(hy_ctx* ctx, int l) {
+  Transfer& t = ctx->tr[l];
+  const int d = ctx->dim;
+  int Lin[3] = {t.Lf, t.Lf, t.Lf};
+  const double* src = ctx->lev[l].d_u64;
+  for (int ax = 0; ax < d; ++ax) {
+    int Lout[3] = {Lin[0], Lin[1], Lin[2]};
+    Lout[ax] = t.Lc;
+    const bool last = ax == d - 1;
+    double* dst = last ? ctx->lev[l - 1].d_u64 : tmp_of<double>(ctx, ax & 1);
+    launch_sweep<double>(src, dst, d, Lin, Lout, ax, t.d_istart, t.d_iw64, t.Ei, false, nullptr, nullptr, ctx->stream);
+    src = dst;
+    Lin[ax] = t.Lc;
+  }
+  return check_launch(ctx, d);
+}
+
+// Chebyshev iteration of the given degree on [lo, hi] for A~ x = b on level l (Saad, Alg. 12.1),
+// Jacobi preconditioned; x0_zero starts from zero. Uses the level's r, d, t vectors.
+template <typename T>
+hy_status chebyshev(hy_ctx* ctx, int l, const T* b, T* x, bool x0_zero, int degree, double lo, double hi) {
+  Level& L = ctx->lev[l];
+  T* r = wvec<T>(L, 2);
+  T* dd = wvec<T>(L, 3);
+  T* t = wvec<T>(L, 4);
+  const T* dinv = dinv_of<T>(L);
+  const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
+  const double sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  if (!x0_zero) HY_TRY(vmult<T>(ctx, l, x, t));
+  launch_cheb_init<T>(b, t, dinv, r, dd, x, T(1.0 / theta), x0_zero, L.ndofs, ctx->stream);
+  HY_TRY(check_launch(ctx, 1));
+  for (int j = 1; j < degree; ++j) {
+    HY_TRY(vmult<T>(ctx, l, dd, t));
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    launch_cheb_step<T>(t, dinv, r, dd, x, T(rho_new * rho), T(2.0 * rho_new / delta), L.ndofs, ctx->stream);
+    HY_TRY(check_launch(ctx, 1));
+    rho = rho_new;
+  }
+  return HY_OK;
+}
+
+bool level_f32(const hy_ctx* ctx, int l) { return ctx->mixed && l > 0; }
+
+// V-cycle on level l for the level's b (w[0]) into x (w[1]), zero initial guess (Sec. 6, Sec. 7).
+hy_status vcycle_level(hy_ctx* ctx, int l);
+
+template <typename T>
+hy_status vcycle_typed(hy_ctx* ctx, int l) {
+  Level& L = ctx->lev[l];
+  T* b = wvec<T>(L, 0);
+  T* x = wvec<T>(L, 1);
+  const double lo = ctx->sp.cheb_lo * L.lmax, hi = ctx->sp.cheb_hi * L.lmax;
+  for (int s = 0; s < ctx->sp.cheb_sweeps; ++s) HY_TRY(chebyshev<T>(ctx, l, b, x, s == 0, ctx->sp.cheb_degree, lo, hi));
+  T* t = wvec<T>(L, 4);
+  T* r = wvec<T>(L, 2);
+  HY_TRY(vmult<T>(ctx, l, x, t));
+  launch_sub<T>(b, t, r, L.ndofs, ctx->stream);
+  HY_TRY(check_launch(ctx, 1));
+  Level& C = ctx->lev[l - 1];
+  const bool cf32 = level_f32(ctx, l - 1);
+  if ((sizeof(T) == 4) == cf32) {
+    HY_TRY(restrict_to<T>(ctx, l, r, wvec<T>(C, 0)));
+  } else {  // float fine level above the FP64 coarsest level
+    HY_TRY(restrict_to<T>(ctx, l, r, (T*)ctx->tmp32c));
+    launch_convert<float, double>((const float*)ctx->tmp32c, C.w64[0], C.ndofs, ctx->stream);
+    HY_TRY(check_launch(ctx, 1));
+  }
+  HY_TRY(vcycle_level(ctx, l - 1));
+  if ((sizeof(T) == 4) == cf32) {
+    HY_TRY(prolongate_add<T>(ctx, l, wvec<T>(C, 1), x));
+  } else {
+    launch_convert<double, float>(C.w64[1], ctx->tmp32c, C.ndofs, ctx->stream);
+    HY_TRY(check_launch(ctx, 1));
+    HY_TRY(prolongate_add<T>(ctx, l, (const T*)ctx->tmp32c, x));
+  }
+  for (int s = 0; s < ctx->sp.cheb_sweeps; ++s) HY_TRY(chebyshev<T>(ctx, l, b, x, false, ctx->sp.cheb_degree, lo, hi));
+  return HY_OK;
+}
+
+hy_status vcycle_level(hy_ctx* ctx, int l) {
+  if (l == 0) {
+    Level& L = ctx->lev[0];
+    return chebyshev<double>(ctx, 0, L.w64[0], L.w64[1], true, ctx->coarse_deg, ctx->coarse_lo, ctx->coarse_hi);
+  }
+  return level_f32(ctx, l) ? vcycle_typed<float>(ctx, l) : vcycle_typed<double>(ctx, l);
+}
+
+// z = V r on the finest level (FP64 in/out).
+hy_status vcycle_top(hy_ctx* ctx, const double* r, double* z) {
+  const int top = ctx->nlev - 1;
+  Level& L = ctx->lev[top];
+  if (level_f32(ctx, top)) {
+    launch_convert<double, float>(r, L.w32[0], L.ndofs, ctx->stream);
+    HY_TRY(check_launch(ctx, 1));
+    HY_TRY(vcycle_level(ctx, top));
+    launch_convert<float, double>(L.w32[1], z, L.ndofs, ctx->stream);
+    return check_launch(ctx, 1);
+  }
+  HY_CK(cudaMemcpyAsync(L.w64[0], r, sizeof(double) * L.ndofs, cudaMemcpyDeviceToDevice, ctx->stream));
+  HY_TRY(vcycle_level(ctx, top));
+  HY_CK(cudaMemcpyAsync(z, L.w64[1], sizeof(double) * L.ndofs, cudaMemcpyDeviceToDevice, ctx->stream));
+  return HY_OK;
+}
+
+// Ritz extremes of D^{-1} A~ on level l from `iters` Jacobi-PCG iterations (Lanczos tridiagonal from
+// the CG coefficients), start vector from SplitMix64 with seed l, constrained entries zero (Sec. 7).
+template <typename T>
+hy_status eig_estimate(hy_ctx* ctx, int l, int iters, double& lmin, double& lmax) {
+  Level& L = ctx->lev[l];
+  T* r = wvec<T>(L, 2);
+  T* z = wvec<T>(L, 3);
+  T* q = wvec<T>(L, 4);
+  T* p = wvec<T>(L, 1);
+  const T* dinv = dinv_of<T>(L);
+  launch_splitmix<T>(r, L.ndofs, (unsigned long long)l, ctx->stream);
+  launch_zero_constrained<T>(r, L.nnodes, ctx->dim, L.g, ctx->stream);
+  launch_mul<T>(dinv, r, z, L.ndofs, ctx->stream);
+  HY_CK(cudaMemcpyAsync(p, z, sizeof(T) * L.ndofs, cudaMemcpyDeviceToDevice, ctx->stream));
+  HY_TRY(check_launch(ctx, 3));
+  double rz, rz0;
+  HY_TRY(dot<T>(ctx, r, z, L.ndofs, &rz));
+  rz0 = rz;
+  std::vector<double> al, be;
+  for (int it = 0; it < iters; ++it) {
+    HY_TRY(vmult<T>(ctx, l, p, q));
+    double pq;
+    HY_TRY(dot<T>(ctx, p, q, L.ndofs, &pq));
+    const double alpha = rz / pq;
+    launch_axpby<T>(T(-alpha), q, T(1), r, L.ndofs, ctx->stream);  // r -= alpha q
+    launch_mul<T>(dinv, r, z, L.ndofs, ctx->stream);                 // z = D^{-1} r
+    HY_TRY(check_launch(ctx, 2));
+    double rzn;
+    HY_TRY(dot<T>(ctx, r, z, L.ndofs, &rzn));
+    const double beta = rzn / rz;
+    al.push_back(alpha);
+    be.push_back(beta);
+    if (rzn <= 1e-28 * rz0) break;
+    launch_xpay<T>(z, T(beta), p, p, L.ndofs, ctx->stream);  // p = z + beta p
+    HY_TRY(check_launch(ctx, 1));
+    rz = rzn;
+  }
+  const int m = (int)al.size();
+  if (m == 0) return fail(ctx, HY_ERR_STATE, "eigenvalue estimate: no iterations");
+  std::vector<double> diag(m), off(std::max(m - 1, 1));
+  for (int j = 0; j < m; ++j) {
+    diag[j] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
+    if (j + 1 < m) off[j] = std::sqrt(be[j]) / al[j];
+  }
+  tridiag_extremes(diag, off, lmin, lmax);
+  return HY_OK;
+}
+
+hy_status ensure_level_vectors(hy_ctx* ctx, int l, bool f32) {
+  Level& L = ctx->lev[l];
+  for (int i = 0; i < 5; ++i) {
+    if (f32) {
+      if (!L.w32[i]) HY_TRY(dalloc(ctx, &L.w32[i], L.ndofs));
+    } else {
+      if (!L.w64[i]) HY_TRY(dalloc(ctx, &L.w64[i], L.ndofs));
+    }
+  }
+  return HY_OK;
+}
+
+template <typename TOUT>
+hy_status build_cache(hy_ctx* ctx, int l, int var) {
+  Level& L = ctx->lev[l];
+  const size_t len = (size_t)cache_values(var, ctx->dim) * L.nqp;
+  TOUT*& buf = *reinterpret_cast<TOUT**>(sizeof(TOUT) == 8 ? (void*)&L.d_c64 : (void*)&L.d_c32);
+  size_t& cur = sizeof(TOUT) == 8 ? L.c64_len : L.c32_len;
+  if (cur < len) {
+    dfree(ctx, buf);
+    buf = nullptr;
+    HY_TRY(dalloc(ctx, &buf, len));
+    cur = len;
+  }
+  CellArgs<double> a = cell_args<double>(ctx, L);
+  a.u64 = L.d_u64;
+  StateFn<TOUT> fn;
+  if constexpr (sizeof(TOUT) == 8) fn = state_fn_f64(ctx->dim, ctx->n, var);
+  else fn = state_fn_f32(ctx->dim, ctx->n, var);
+  if (!fn) return fail(ctx, HY_ERR_UNSUPPORTED, "no state kernel");
+  fn(a, buf, ctx->stream);
+  return check_launch(ctx, 1);
+}
+
+hy_status check_error_word(hy_ctx* ctx, const char* where) {
+  unsigned h = 0;
+  HY_CK(cudaMemcpyAsync(&h, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+  HY_CK(cudaStreamSynchronize(ctx->stream));
+  if (h) {
+    HY_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
+    return fail(ctx, HY_ERR_JNEG, std::string(where) + ((h & ERRBIT_NAN) ? ": NaN in J" : ": J <= 0 at a Gauss point"));
+  }
+  return HY_OK;
+}
+
+hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
+  if (ctx->nlev == 0) return fail(ctx, HY_ERR_STATE, "mesh not set up");
+  for (int l = 0; l < ctx->nlev; ++l)
+    if (!ctx->lev[l].mat_set) return fail(ctx, HY_ERR_STATE, "material not set on level " + std::to_string(l));
+  if (var < 0 || var > 4) return fail(ctx, HY_ERR_ARG, "variant out of range");
+  ctx->state_ok = false;
+  ctx->var = var;
+  ctx->mixed = mixed;
+  const int top = ctx->nlev - 1;
+  HY_CK(cudaMemcpyAsync(ctx->lev[top].d_u64, u, sizeof(double) * ctx->lev[top].ndofs, cudaMemcpyDeviceToDevice,
+                        ctx->stream));
+  for (int l = top; l >= 1; --l) HY_TRY(interpolate_down(ctx, l));
+  HY_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
+  const unsigned long long one_bits = 0x7FF0000000000000ULL;  // +inf
+  HY_CK(cudaMemcpyAsync(ctx->d_jmin, &one_bits, sizeof(one_bits), cudaMemcpyHostToDevice, ctx->stream));
+  for (int l = 0; l < ctx->nlev; ++l) {
+    Level& L = ctx->lev[l];
+    const bool need64 = (l == top) || (l == 0) || !mixed;
+    const bool need32 = mixed && (l > 0 || l == top);
+    L.has64 = L.has32 = false;
+    if (need64) {
+      HY_TRY(build_cache<double>(ctx, l, var));
+      L.has64 = true;
+    }
+    if (need32) {
+      HY_TRY(build_cache<float>(ctx, l, var));
+      if (!L.d_u32) HY_TRY(dalloc(ctx, &L.d_u32, L.ndofs));
+      launch_convert<double, float>(L.d_u64, L.d_u32, L.ndofs, ctx->stream);
+      HY_TRY(check_launch(ctx, 1));
+      L.has32 = true;
+    }
+    // diagonal (FP64), inverse in the level precisions
+    HY_CK(cudaMemsetAsync(L.d_diag, 0, sizeof(double) * L.ndofs, ctx->stream));
+    CellArgs<double> a = cell_args<double>(ctx, L);
+    a.u64 = L.d_u64;
+    a.y = L.d_diag;
+    CellFn<double> dfn = diag_fn(ctx->dim, ctx->n);
+    dfn(a, ctx->stream);
+    launch_set_constrained_one<double>(L.d_diag, L.nnodes, ctx->dim, L.g, ctx->stream);
+    HY_TRY(check_launch(ctx, 2));
+    if (need64) {
+      if (!L.d_dinv64) HY_TRY(dalloc(ctx, &L.d_dinv64, L.ndofs));
+      launch_invert<double>(L.d_diag, L.d_dinv64, L.ndofs, ctx->stream);
+      HY_TRY(ensure_level_vectors(ctx, l, false));
+    }
+    if (need32) {
+      if (!L.d_dinv32) HY_TRY(dalloc(ctx, &L.d_dinv32, L.ndofs));
+      launch_invert<float>(L.d_diag, L.d_dinv32, L.ndofs, ctx->stream);
+      HY_TRY(ensure_level_vectors(ctx, l, true));
+    }
+    HY_TRY(check_launch(ctx, (int)need64 + (int)need32));
+  }
+  HY_TRY(check_error_word(ctx, "set_displacement"));
+  // eigenvalue estimates (level precision of the V-cycle)
+  for (int l = 1; l < ctx->nlev; ++l) {
+    double lmin, lmax;
+    if (level_f32(ctx, l)) HY_TRY(eig_estimate<float>(ctx, l, ctx->sp.eig_iters, lmin, lmax));
+    else HY_TRY(eig_estimate<double>(ctx, l, ctx->sp.eig_iters, lmin, lmax));
+    ctx->lev[l].lmax = lmax;
+  }
+  {
+    Level& C = ctx->lev[0];
+    long long nfree = 0;
+    {
+      // count free dofs on the coarsest level on the host from the face masks
+      const int Lc = C.g.L;
+      for (long long nd = 0; nd < C.nnodes; ++nd) {
+        const int i0 = (int)(nd % Lc), i1 = (int)((nd / Lc) % Lc), i2 = ctx->dim == 3 ? (int)(nd / ((long long)Lc * Lc)) : 0;
+        uint32_t cm = 0;
+        if (i0 == 0) cm |= C.g.fm[0];
+        if (i0 == Lc - 1) cm |= C.g.fm[1];
+        if (i1 == 0) cm |= C.g.fm[2];
+        if (i1 == Lc - 1) cm |= C.g.fm[3];
+        if (ctx->dim == 3 && i2 == 0) cm |= C.g.fm[4];
+        if (ctx->dim == 3 && i2 == Lc - 1) cm |= C.g.fm[5];
+        for (int c = 0; c < ctx->dim; ++c) nfree += ((cm >> c) & 1u) ? 0 : 1;
+      }
+    }
+    int it = ctx->sp.coarse_eig_iters > 0 ? (int)std::min<long long>(nfree, ctx->sp.coarse_eig_iters) : (int)nfree;
+    if (it < 1) it = 1;
+    double lmin, lmax;
+    HY_TRY(eig_estimate<double>(ctx, 0, it, lmin, lmax));
+    ctx->coarse_lo = lmin;
+    ctx->coarse_hi = ctx->sp.cheb_hi * lmax;
+    if (!(lmin > 0.0))
+      return fail(ctx, HY_ERR_NOCONV,
+                  "coarsest-level tangent is not positive definite (smallest Ritz value " + std::to_string(lmin) +
+                      "); the Chebyshev coarse solver needs an SPD operator");
+  }
+  {
+    const double sig = (ctx->coarse_hi + ctx->coarse_lo) / (ctx->coarse_hi - ctx->coarse_lo);
+    ctx->coarse_deg = std::max(1, (int)std::ceil(std::acosh(1.0 / ctx->sp.coarse_reduction) / std::acosh(sig) - 1e-12));
+  }
+  if (ctx->verbose) {
+    for (int l = 1; l < ctx->nlev; ++l) std::fprintf(stderr, "[hy] level %d lmax %.6e\n", l, ctx->lev[l].lmax);
+    std::fprintf(stderr, "[hy] coarse lo %.6e hi %.6e degree %d\n", ctx->coarse_lo, ctx->coarse_hi, ctx->coarse_deg);
+  }
+  ctx->state_ok = true;
+  return HY_OK;
+}
+
+hy_status residual(hy_ctx* ctx, const double* u, double* r) {
+  Level& L = ctx->lev[ctx->nlev - 1];
+  HY_CK(cudaMemsetAsync(r, 0, sizeof(double) * L.ndofs, ctx->stream));
+  CellArgs<double> a = cell_args<double>(ctx, L);
+  a.u64 = u;
+  a.y = r;
+  residual_fn(ctx->dim, ctx->n)(a, ctx->stream);
+  return check_launch(ctx, 1);
+}
+
+hy_status jacobian_ok(hy_ctx* ctx, const double* u, bool& ok) {
+  Level& L = ctx->lev[ctx->nlev - 1];
+  CellArgs<double> a = cell_args<double>(ctx, L);
+  a.u64 = u;
+  HY_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
+  state_fn_f64(ctx->dim, ctx->n, VAR_NONE)(a, nullptr, ctx->stream);
+  HY_TRY(check_launch(ctx, 1));
+  unsigned h = 0;
+  HY_CK(cudaMemcpyAsync(&h, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+  HY_CK(cudaStreamSynchronize(ctx->stream));
+  HY_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
+  ok = (h == 0);
+  return HY_OK;
+}
+
+hy_status pcg(hy_ctx* ctx, const double* b, double* x, double rtol, int max_iter, int* its_out) {
+  Level& L = ctx->lev[ctx->nlev - 1];
+  const long long n = L.ndofs;
+  double *r = ctx->f64[0], *z = ctx->f64[1], *p = ctx->f64[2], *q = ctx->f64[3];
+  if (its_out) *its_out = 0;
+  HY_CK(cudaMemsetAsync(x, 0, sizeof(double) * n, ctx->stream));
+  HY_CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  double bb;
+  HY_TRY(dot<double>(ctx, b, b, n, &bb));
+  const double nb = std::sqrt(bb);
+  if (nb == 0.0) return HY_OK;
+  if (!(nb == nb)) return fail(ctx, HY_ERR_ARG, "pcg: right-hand side has NaN");
+  HY_TRY(vcycle_top(ctx, r, z));
+  HY_CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  double rz;
+  HY_TRY(dot<double>(ctx, r, z, n, &rz));
+  for (int it = 1; it <= max_iter; ++it) {
+    HY_TRY(vmult<double>(ctx, ctx->nlev - 1, p, q));
+    double pq;
+    HY_TRY(dot<double>(ctx, p, q, n, &pq));
+    if (ctx->verbose) std::fprintf(stderr, "[hy] pcg it %d rz %.3e pAp %.3e\n", it, rz, pq);
+    if (!(pq > 0.0)) return fail(ctx, HY_ERR_NOCONV, "pcg: p^T A p <= 0 (operator not SPD)");
+    const double alpha = rz / pq;
+    launch_axpby<double>(alpha, p, 1.0, x, n, ctx->stream);
+    launch_axpby<double>(-alpha, q, 1.0, r, n, ctx->stream);
+    HY_TRY(check_launch(ctx, 2));
+    double rr;
+    HY_TRY(dot<double>(ctx, r, r, n, &rr));
+    if (its_out) *its_out = it;
+    if (std::sqrt(rr) <= rtol * nb) return HY_OK;
+    HY_TRY(vcycle_top(ctx, r, z));
+    double rzn;
+    HY_TRY(dot<double>(ctx, r, z, n, &rzn));
+    launch_xpay<double>(z, rzn / rz, p, p, n, ctx->stream);
+    HY_TRY(check_launch(ctx, 1));
+    rz = rzn;
+  }
+  return fail(ctx, HY_ERR_NOCONV, "pcg: iteration cap reached");
+}
+
+}  // namespace
+
+// =============================================================================================
+extern "C" {
+
+const char* hy_status_str(hy_status s) {
+  switch (s) {
+    case HY_OK: return "HY_OK";
+    case HY_ERR_ARG: return "HY_ERR_ARG";
+    case HY_ERR_STATE: return "HY_ERR_STATE";
+    case HY_ERR_OOM: return "HY_ERR_OOM";
+    case HY_ERR_CUDA: return "HY_ERR_CUDA";
+    case HY_ERR_JNEG: return "HY_ERR_JNEG";
+    case HY_ERR_NOCONV: return "HY_ERR_NOCONV";
+    case HY_ERR_TIMEOUT: return "HY_ERR_TIMEOUT";
+    case HY_ERR_UNSUPPORTED: return "HY_ERR_UNSUPPORTED";
+  }
+  return "HY_ERR_UNKNOWN";
+}
+
+const char* hy_last_error(const hy_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+hy_status hy_create(hy_ctx** out, int device, void* stream) {
+  if (!out) return HY_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return HY_ERR_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return HY_ERR_CUDA;
+  hy_ctx* ctx = new (std::nothrow) hy_ctx();
+  if (!ctx) return HY_ERR_OOM;
+  ctx->device = device;
+  ctx->stream = (cudaStream_t)stream;
+  const char* v = std::getenv("HY_VERBOSE");
+  ctx->verbose = v && v[0] == '1';
+  *out = ctx;
+  return HY_OK;
+}
+
+void hy_destroy(hy_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  free_mesh(ctx);
+  delete ctx;
+}
+
+hy_status hy_mesh_setup(hy_ctx* ctx, int dim, int degree, int m, int n_levels, const uint32_t* face_masks) {
+  if (!ctx) return HY_ERR_ARG;
+  if (dim != 2 && dim != 3) return fail(ctx, HY_ERR_ARG, "dim must be 2 or 3");
+  if (degree < 1) return fail(ctx, HY_ERR_ARG, "degree must be >= 1");
+  if (degree > 4) return fail(ctx, HY_ERR_UNSUPPORTED, "degree > 4 is not built");
+  if (m < 1 || n_levels < 1 || !face_masks) return fail(ctx, HY_ERR_ARG, "bad mesh size or masks");
+  {
+    int mm = m;
+    for (int l = 1; l < n_levels; ++l) {
+      if (mm % 2) return fail(ctx, HY_ERR_ARG, "cells per direction must stay even while coarsening");
+      mm /= 2;
+    }
+  }
+  for (int f = 0; f < 2 * dim; ++f)
+    if (face_masks[f] >> dim) return fail(ctx, HY_ERR_ARG, "face mask has bits beyond dim");
+  const double Ldof = std::pow((double)degree * m + 1.0, dim) * dim;
+  if (Ldof > 2.0e9) return fail(ctx, HY_ERR_ARG, "mesh too large");
+  HY_CK(cudaSetDevice(ctx->device));
+  if (ctx->stream) HY_CK(cudaStreamSynchronize(ctx->stream));
+  free_mesh(ctx);
+  ctx->dim = dim;
+  ctx->k = degree;
+  ctx->n = degree + 1;
+  ctx->nlev = n_levels;
+  for (int f = 0; f < 6; ++f) ctx->fm[f] = f < 2 * dim ? face_masks[f] : 0;
+  // 1D tables
+  {
+    const int k = degree, n = degree + 1;
+    std::vector<double> wg;
+    const std::vector<double> xg = gauss_points(n, wg);
+    const std::vector<double> gl = gll_points(k);
+    Basis1D<double>& b = ctx->b64;
+    std::memset(&b, 0, sizeof(b));
+    for (int q = 0; q < n; ++q) {
+      b.w[q] = wg[q];
+      for (int a = 0; a < n; ++a) {
+        b.S[q][a] = lagr(gl, a, xg[q]);
+        b.Sd[q][a] = dlagr(gl, a, xg[q]);
+        b.D[q][a] = dlagr(xg, a, xg[q]);
+      }
+    }
+    for (int i = 0; i < MAXN; ++i) {
+      ctx->b32.w[i] = (float)b.w[i];
+      for (int j = 0; j < MAXN; ++j) {
+        ctx->b32.S[i][j] = (float)b.S[i][j];
+        ctx->b32.D[i][j] = (float)b.D[i][j];
+        ctx->b32.Sd[i][j] = (float)b.Sd[i][j];
+      }
+    }
+  }
+  ctx->lev.assign(n_levels, Level());
+  long long max_nd = 0;
+  for (int l = 0; l < n_levels; ++l) {
+    Level& L = ctx->lev[l];
+    const int ml = m >> (n_levels - 1 - l);
+    L.g.m = ml;
+    L.g.L = degree * ml + 1;
+    L.g.ncells = 1;
+    for (int i = 0; i < dim; ++i) L.g.ncells *= ml;
+    for (int f = 0; f < 6; ++f) L.g.fm[f] = ctx->fm[f];
+    L.g.h = 1.0 / ml;
+    L.nnodes = 1;
+    for (int i = 0; i < dim; ++i) L.nnodes *= L.g.L;
+    L.ndofs = L.nnodes * dim;
+    L.nqp = (long long)L.g.ncells * ipow(degree + 1, dim);
+    HY_TRY(dalloc(ctx, &L.d_u64, L.ndofs));
+    HY_TRY(dalloc(ctx, &L.d_diag, L.ndofs));
+    HY_TRY(dalloc(ctx, &L.d_mat, L.g.ncells));
+    max_nd = std::max(max_nd, L.ndofs);
+  }
+  // transfer tables
+  ctx->tr.assign(n_levels, Transfer());
+  size_t tmp_len = 1;
+  const std::vector<double> gl = gll_points(degree);
+  for (int l = 1; l < n_levels; ++l) {
+    Transfer& t = ctx->tr[l];
+    const int k = degree, n = degree + 1;
+    const int mc = ctx->lev[l - 1].g.m;
+    t.Lc = ctx->lev[l - 1].g.L;
+    t.Lf = ctx->lev[l].g.L;
+    // prolongation: fine node i in fine cell cf = coarse cell cf/2 at local position ((cf%2) + x_j)/2
+    std::vector<double> P((size_t)t.Lf * t.Lc, 0.0);
+    std::vector<int> pstart(t.Lf);
+    std::vector<double> pw((size_t)t.Lf * n, 0.0);
+    for (int i = 0; i < t.Lf; ++i) {
+      const int cf = std::min(i / k, 2 * mc - 1);
+      const int j = i - k * cf;
+      const int c = cf / 2;
+      const double xi = ((cf % 2) + gl[j]) / 2.0;
+      pstart[i] = k * c;
+      for (int e = 0; e < n; ++e) {
+        double v = lagr(gl, e, xi);
+        if (std::fabs(v) < 1e-15) v = 0.0;
+        pw[(size_t)i * n + e] = v;
+        P[(size_t)i * t.Lc + k * c + e] = v;
+      }
+    }
+    t.Ep = n;
+    // restriction = P^T: for coarse node J the fine rows with a nonzero entry form a contiguous range
+    t.Er = std::min(4 * k + 1, t.Lf);
+    std::vector<int> rstart(t.Lc);
+    std::vector<double> rw((size_t)t.Lc * t.Er, 0.0);
+    for (int J = 0; J < t.Lc; ++J) {
+      int first = -1;
+      for (int i = 0; i < t.Lf; ++i)
+        if (P[(size_t)i * t.Lc + J] != 0.0) { first = i; break; }
+      if (first < 0) first = 0;
+      first = std::min(first, t.Lf - t.Er);
+      rstart[J] = first;
+      for (int e = 0; e < t.Er; ++e) rw[(size_t)J * t.Er + e] = P[(size_t)(first + e) * t.Lc + J];
+    }
+    // interpolation down: coarse node J at coarse-cell position x_j lies in fine cell 2c (x_j < 1/2)
+    // or 2c+1, at fine-cell position 2 x_j or 2 x_j - 1
+    t.Ei = n;
+    std::vector<int> istart(t.Lc);
+    std::vector<double> iw((size_t)t.Lc * n, 0.0);
+    for (int J = 0; J < t.Lc; ++J) {
+      const int c = std::min(J / k, mc - 1);
+      const int j = J - k * c;
+      const int f = gl[j] < 0.5 ? 2 * c : 2 * c + 1;
+      const double xi = gl[j] < 0.5 ? 2.0 * gl[j] : 2.0 * gl[j] - 1.0;
+      istart[J] = k * f;
+      for (int e = 0; e < n; ++e) {
+        double v = lagr(gl, e, xi);
+        if (std::fabs(v) < 1e-15) v = 0.0;
+        iw[(size_t)J * n + e] = v;
+      }
+    }
+    std::vector<float> pw32(pw.begin(), pw.end()), rw32(rw.begin(), rw.end());
+    HY_TRY(dalloc(ctx, &t.d_pstart, t.Lf));
+    HY_TRY(dalloc(ctx, &t.d_rstart, t.Lc));
+    HY_TRY(dalloc(ctx, &t.d_istart, t.Lc));
+    HY_TRY(dalloc(ctx, &t.d_pw64, pw.size()));
+    HY_TRY(dalloc(ctx, &t.d_rw64, rw.size()));
+    HY_TRY(dalloc(ctx, &t.d_iw64, iw.size()));
+    HY_TRY(dalloc(ctx, &t.d_pw32, pw.size()));
+    HY_TRY(dalloc(ctx, &t.d_rw32, rw.size()));
+    HY_CK(cudaMemcpy(t.d_pstart, pstart.data(), sizeof(int) * t.Lf, cudaMemcpyHostToDevice));
+    HY_CK(cudaMemcpy(t.d_rstart, rstart.data(), sizeof(int) * t.Lc, cudaMemcpyHostToDevice));
+    HY_CK(cudaMemcpy(t.d_istart, istart.data(), sizeof(int) * t.Lc, cudaMemcpyHostToDevice));
+    HY_CK(cudaMemcpy(t.d_pw64, pw.data(), sizeof(double) * pw.size(), cudaMemcpyHostToDevice));
+    HY_CK(cudaMemcpy(t.d_rw64, rw.data(), sizeof(double) * rw.size(), cudaMemcpyHostToDevice));
+    HY_CK(cudaMemcpy(t.d_iw64, iw.data(), sizeof(double) * iw.size(), cudaMemcpyHostToDevice));
+    HY_CK(cudaMemcpy(t.d_pw32, pw32.data(), sizeof(float) * pw32.size(), cudaMemcpyHostToDevice));
+    HY_CK(cudaMemcpy(t.d_rw32, rw32.data(), sizeof(float) * rw32.size(), cudaMemcpyHostToDevice));
+    size_t inter = (size_t)t.Lf * dim;
+    for (int i = 1; i < dim; ++i) inter *= t.Lf;  // bounds every intermediate of the sweeps
+    tmp_len = std::max(tmp_len, inter);
+  }
+  ctx->tmp_len = tmp_len;
+  HY_TRY(dalloc(ctx, &ctx->tmp64a, tmp_len));
+  HY_TRY(dalloc(ctx, &ctx->tmp64b, tmp_len));
+  HY_TRY(dalloc(ctx, &ctx->tmp32a, tmp_len));
+  HY_TRY(dalloc(ctx, &ctx->tmp32b, tmp_len));
+  HY_TRY(dalloc(ctx, &ctx->tmp32c, tmp_len));
+  HY_TRY(dalloc(ctx, &ctx->d_err, 1));
+  HY_TRY(dalloc(ctx, &ctx->d_jmin, 1));
+  HY_TRY(dalloc(ctx, &ctx->d_partials, DOT_BLOCKS));
+  HY_TRY(dalloc(ctx, &ctx->d_scal, 4));
+  HY_TRY(dalloc(ctx, &ctx->d_face, 18));
+  for (int i = 0; i < 10; ++i) HY_TRY(dalloc(ctx, &ctx->f64[i], ctx->lev[n_levels - 1].ndofs));
+  HY_CK(cudaMemset(ctx->d_err, 0, sizeof(unsigned)));
+  HY_CK(cudaDeviceSynchronize());
+  return HY_OK;
+}
+
+hy_status hy_num_dofs(const hy_ctx* ctx, int level, int64_t* n) {
+  if (!ctx || !n) return HY_ERR_ARG;
+  const int l = lev_index(ctx, level);
+  if (l < 0 || l >= ctx->nlev) return HY_ERR_ARG;
+  *n = ctx->lev[l].ndofs;
+  return HY_OK;
+}
+
+hy_status hy_set_material(hy_ctx* ctx, int level, const uint8_t* cell_mat, const double* mu, const double* lambda,
+                          int n_mat) {
+  if (!ctx) return HY_ERR_ARG;
+  const int l = lev_index(ctx, level);
+  if (l < 0 || l >= ctx->nlev) return fail(ctx, HY_ERR_ARG, "level out of range");
+  if (!cell_mat || !mu || !lambda || n_mat < 1 || n_mat > MAXMAT) return fail(ctx, HY_ERR_ARG, "bad material arrays");
+  Level& L = ctx->lev[l];
+  for (int i = 0; i < L.g.ncells; ++i)
+    if (cell_mat[i] >= n_mat) return fail(ctx, HY_ERR_ARG, "material id out of range");
+  for (int i = 0; i < n_mat; ++i)
+    if (!(mu[i] > 0.0) || !(lambda[i] > -2.0 / 3.0 * mu[i]) || !std::isfinite(lambda[i]))
+      return fail(ctx, HY_ERR_ARG, "material parameters out of range");
+  HY_CK(cudaSetDevice(ctx->device));
+  HY_CK(cudaMemcpy(L.d_mat, cell_mat, L.g.ncells, cudaMemcpyHostToDevice));
+  for (int i = 0; i < MAXMAT; ++i) {
+    L.mt64.mu[i] = i < n_mat ? mu[i] : 0.0;
+    L.mt64.lam[i] = i < n_mat ? lambda[i] : 0.0;
+    L.mt32.mu[i] = (float)L.mt64.mu[i];
+    L.mt32.lam[i] = (float)L.mt64.lam[i];
+  }
+  L.mat_set = true;
+  ctx->state_ok = false;
+  return HY_OK;
+}
+
+hy_status hy_set_displacement(hy_ctx* ctx, const double* u_dev, hy_variant variant, hy_dtype level_dtype) {
+  if (!ctx || !u_dev) return HY_ERR_ARG;
+  if (level_dtype != HY_F64 && level_dtype != HY_F32) return fail(ctx, HY_ERR_ARG, "bad dtype");
+  HY_CK(cudaSetDevice(ctx->device));
+  return set_displacement(ctx, u_dev, (int)variant, level_dtype == HY_F32);
+}
+
+hy_status hy_vmult(hy_ctx* ctx, int level, const void* x, void* y, hy_dtype dtype) {
+  if (!ctx || !x || !y) return HY_ERR_ARG;
+  const int l = lev_index(ctx, level);
+  if (l < 0 || l >= ctx->nlev) return fail(ctx, HY_ERR_ARG, "level out of range");
+  if (!ctx->state_ok) return fail(ctx, HY_ERR_STATE, "set_displacement first");
+  if (x == y) return fail(ctx, HY_ERR_ARG, "x and y must not alias");
+  HY_CK(cudaSetDevice(ctx->device));
+  if (dtype == HY_F64) return vmult<double>(ctx, l, (const double*)x, (double*)y);
+  if (dtype == HY_F32) return vmult<float>(ctx, l, (const float*)x, (float*)y);
+  return fail(ctx, HY_ERR_ARG, "bad dtype");
+}
+
+hy_status hy_apply_tangent(hy_ctx* ctx, const void* x, void* y, hy_dtype dtype) {
+  if (!ctx) return HY_ERR_ARG;
+  return hy_vmult(ctx, -1, x, y, dtype);
+}
+
+hy_status hy_residual(hy_ctx* ctx, const double* u, double* r) {
+  if (!ctx || !u || !r) return HY_ERR_ARG;
+  if (ctx->nlev == 0) return fail(ctx, HY_ERR_STATE, "mesh not set up");
+  if (!ctx->lev[ctx->nlev - 1].mat_set) return fail(ctx, HY_ERR_STATE, "material not set");
+  HY_CK(cudaSetDevice(ctx->device));
+  HY_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
+  HY_TRY(residual(ctx, u, r));
+  return check_error_word(ctx, "residual");
+}
+
+hy_status hy_diagonal(hy_ctx* ctx, int level, void* d, hy_dtype dtype) {
+  if (!ctx || !d) return HY_ERR_ARG;
+  const int l = lev_index(ctx, level);
+  if (l < 0 || l >= ctx->nlev) return fail(ctx, HY_ERR_ARG, "level out of range");
+  if (!ctx->state_ok) return fail(ctx, HY_ERR_STATE, "set_displacement first");
+  HY_CK(cudaSetDevice(ctx->device));
+  Level& L = ctx->lev[l];
+  if (dtype == HY_F64) {
+    HY_CK(cudaMemcpyAsync(d, L.d_diag, sizeof(double) * L.ndofs, cudaMemcpyDeviceToDevice, ctx->stream));
+    return HY_OK;
+  }
+  if (dtype == HY_F32) {
+    launch_convert<double, float>(L.d_diag, (float*)d, L.ndofs, ctx->stream);
+    return check_launch(ctx, 1);
+  }
+  return fail(ctx, HY_ERR_ARG, "bad dtype");
+}
+
+hy_status hy_gmg_vcycle(hy_ctx* ctx, const double* r, double* z) {
+  if (!ctx || !r || !z) return HY_ERR_ARG;
+  if (!ctx->state_ok) return fail(ctx, HY_ERR_STATE, "set_displacement first");
+  HY_CK(cudaSetDevice(ctx->device));
+  return vcycle_top(ctx, r, z);
+}
+
+hy_status hy_set_solver_params(hy_ctx* ctx, const hy_solver_params* p) {
+  if (!ctx || !p) return HY_ERR_ARG;
+  if (p->cheb_degree < 1 || p->cheb_sweeps < 1 || !(p->cheb_lo > 0) || !(p->cheb_hi > p->cheb_lo) ||
+      p->eig_iters < 1 || p->coarse_eig_iters < 0 || !(p->coarse_reduction > 0 && p->coarse_reduction < 1))
+    return fail(ctx, HY_ERR_ARG, "solver parameters out of range");
+  ctx->sp = *p;
+  ctx->state_ok = false;
+  return HY_OK;
+}
+
+hy_status hy_get_solver_params(const hy_ctx* ctx, hy_solver_params* p) {
+  if (!ctx || !p) return HY_ERR_ARG;
+  *p = ctx->sp;
+  return HY_OK;
+}
+
+hy_status hy_level_info(const hy_ctx* ctx, int level, double* lmax, double* clo, double* chi, int* cdeg) {
+  if (!ctx) return HY_ERR_ARG;
+  const int l = lev_index(ctx, level);
+  if (l < 0 || l >= ctx->nlev) return HY_ERR_ARG;
+  if (lmax) *lmax = ctx->lev[l].lmax;
+  if (clo) *clo = ctx->coarse_lo;
+  if (chi) *chi = ctx->coarse_hi;
+  if (cdeg) *cdeg = ctx->coarse_deg;
+  return HY_OK;
+}
+
+hy_status hy_set_level_info(hy_ctx* ctx, int level, double lmax, double clo, double chi) {
+  if (!ctx) return HY_ERR_ARG;
+  const int l = lev_index(ctx, level);
+  if (l < 0 || l >= ctx->nlev) return fail(ctx, HY_ERR_ARG, "level out of range");
+  if (l == 0) {
+    if (!(chi > clo && clo > 0)) return fail(ctx, HY_ERR_ARG, "bad coarse interval");
+    ctx->coarse_lo = clo;
+    ctx->coarse_hi = chi;
+    const double sig = (chi + clo) / (chi - clo);
+    ctx->coarse_deg = std::max(1, (int)std::ceil(std::acosh(1.0 / ctx->sp.coarse_reduction) / std::acosh(sig) - 1e-12));
+  } else {
+    if (!(lmax > 0)) return fail(ctx, HY_ERR_ARG, "bad lmax");
+    ctx->lev[l].lmax = lmax;
+  }
+  return HY_OK;
+}
+
+hy_status hy_level_displacement(const hy_ctx* cctx, int level, double* u) {
+  hy_ctx* ctx = const_cast<hy_ctx*>(cctx);
+  if (!ctx || !u) return HY_ERR_ARG;
+  const int l = lev_index(ctx, level);
+  if (l < 0 || l >= ctx->nlev) return fail(ctx, HY_ERR_ARG, "level out of range");
+  HY_CK(cudaSetDevice(ctx->device));
+  HY_CK(cudaMemcpyAsync(u, ctx->lev[l].d_u64, sizeof(double) * ctx->lev[l].ndofs, cudaMemcpyDeviceToDevice, ctx->stream));
+  return HY_OK;
+}
+
+hy_status hy_prolongate_add(hy_ctx* ctx, int fine_level, const void* coarse, void* fine, hy_dtype dtype) {
+  if (!ctx || !coarse || !fine) return HY_ERR_ARG;
+  const int l = lev_index(ctx, fine_level);
+  if (l < 1 || l >= ctx->nlev) return fail(ctx, HY_ERR_ARG, "fine level must be >= 1");
+  HY_CK(cudaSetDevice(ctx->device));
+  if (dtype == HY_F64) return prolongate_add<double>(ctx, l, (const double*)coarse, (double*)fine);
+  if (dtype == HY_F32) return prolongate_add<float>(ctx, l, (const float*)coarse, (float*)fine);
+  return fail(ctx, HY_ERR_ARG, "bad dtype");
+}
+
+hy_status hy_restrict(hy_ctx* ctx, int fine_level, const void* fine, void* coarse, hy_dtype dtype) {
+  if (!ctx || !coarse || !fine) return HY_ERR_ARG;
+  const int l = lev_index(ctx, fine_level);
+  if (l < 1 || l >= ctx->nlev) return fail(ctx, HY_ERR_ARG, "fine level must be >= 1");
+  HY_CK(cudaSetDevice(ctx->device));
+  if (dtype == HY_F64) return restrict_to<double>(ctx, l, (const double*)fine, (double*)coarse);
+  if (dtype == HY_F32) return restrict_to<float>(ctx, l, (const float*)fine, (float*)coarse);
+  return fail(ctx, HY_ERR_ARG, "bad dtype");
+}
+
+hy_status hy_pcg(hy_ctx* ctx, const double* b, double* x, double rtol, int max_iter, int* iterations) {
+  if (!ctx || !b || !x || !(rtol > 0) || max_iter < 1) return HY_ERR_ARG;
+  if (!ctx->state_ok) return fail(ctx, HY_ERR_STATE, "set_displacement first");
+  HY_CK(cudaSetDevice(ctx->device));
+  return pcg(ctx, b, x, rtol, max_iter, iterations);
+}
+
+void hy_newton_default_params(hy_newton_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->load_steps = 5;
+  p->max_newton = 25;
+  p->newton_rtol = 1e-10;
+  p->newton_atol = 1e-14;
+  p->cg_rtol = 1e-8;
+  p->cg_max_iter = 1000;
+  p->variant = HY_T4;
+  p->level_dtype = HY_F64;
+}
+
+hy_status hy_newton_solve(hy_ctx* ctx, const hy_newton_params* p, double* u, hy_newton_report* rep) {
+  if (!ctx || !p || !u) return HY_ERR_ARG;
+  if (p->load_steps < 1 || p->max_newton < 1 || !(p->newton_rtol > 0) || !(p->cg_rtol > 0) || p->cg_max_iter < 1)
+    return fail(ctx, HY_ERR_ARG, "newton parameters out of range");
+  if (ctx->nlev == 0) return fail(ctx, HY_ERR_STATE, "mesh not set up");
+  HY_CK(cudaSetDevice(ctx->device));
+  hy_newton_report rl;
+  std::memset(&rl, 0, sizeof(rl));
+  Level& L = ctx->lev[ctx->nlev - 1];
+  const long long n = L.ndofs;
+  double *R = ctx->f64[4], *du0 = ctx->f64[5], *rhs = ctx->f64[6], *du = ctx->f64[7], *trial = ctx->f64[8],
+         *t = ctx->f64[9];
+  HY_CK(cudaMemcpyAsync(ctx->d_face, p->face_values, sizeof(double) * 18, cudaMemcpyHostToDevice, ctx->stream));
+  hy_status st = HY_OK;
+  for (int s = 1; s <= p->load_steps && st == HY_OK; ++s) {
+    const double factor = (double)s / p->load_steps;
+    double ref = -1.0;
+    int its = 0;
+    while (true) {
+      launch_lift(u, du0, factor, ctx->d_face, L.nnodes, ctx->dim, L.g, ctx->stream);
+      HY_TRY(check_launch(ctx, 1));
+      double lift2;
+      HY_TRY(dot<double>(ctx, du0, du0, n, &lift2));
+      HY_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
+      HY_TRY(residual(ctx, u, R));
+      if ((st = check_error_word(ctx, "newton residual")) != HY_OK) break;
+      if (its > 0 && lift2 == 0.0) {
+        double rr;
+        HY_TRY(dot<double>(ctx, R, R, n, &rr));
+        rl.final_residual = std::sqrt(rr);
+        if (ctx->verbose) std::fprintf(stderr, "[hy] step %d it %d |R| %.3e ref %.3e\n", s, its, std::sqrt(rr), ref);
+        if (std::sqrt(rr) <= std::max(p->newton_rtol * ref, p->newton_atol)) break;
+      }
+      if (its >= p->max_newton) {
+        st = fail(ctx, HY_ERR_NOCONV, "newton: iteration cap in load step " + std::to_string(s));
+        break;
+      }
+      if ((st = set_displacement(ctx, u, (int)p->variant, p->level_dtype == HY_F32)) != HY_OK) break;
+      // rhs = -R - Z A du0 (lifting of the prescribed increment into the first solve)
+      HY_CK(cudaMemcpyAsync(rhs, R, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+      if (lift2 > 0.0) {
+        HY_TRY(vmult<double>(ctx, ctx->nlev - 1, du0, t, false));
+        launch_axpby<double>(-1.0, t, -1.0, rhs, n, ctx->stream);  // rhs = -A du0 - R
+      } else {
+        launch_axpby<double>(0.0, R, -1.0, rhs, n, ctx->stream);   // rhs = -R
+      }
+      HY_TRY(check_launch(ctx, 1));
+      double rr;
+      HY_TRY(dot<double>(ctx, rhs, rhs, n, &rr));
+      if (ref < 0) ref = std::sqrt(rr);
+      rl.final_residual = std::sqrt(rr);
+      if (ctx->verbose) std::fprintf(stderr, "[hy] step %d it %d |rhs| %.3e lift2 %.3e\n", s, its, std::sqrt(rr), lift2);
+      int cg_its = 0;
+      if ((st = pcg(ctx, rhs, du, p->cg_rtol, p->cg_max_iter, &cg_its)) != HY_OK) break;
+      rl.cg_iterations_total += cg_its;
+      if (ctx->verbose) std::fprintf(stderr, "[hy] step %d it %d cg %d\n", s, its, cg_its);
+      rl.cg_iterations_max = std::max(rl.cg_iterations_max, cg_its);
+      launch_axpby<double>(1.0, du0, 1.0, du, n, ctx->stream);  // du = delta + du0
+      HY_TRY(check_launch(ctx, 1));
+      double step = 1.0;
+      bool ok = false;
+      for (int h = 0; h < 6; ++h) {
+        launch_xpay<double>(u, step, du, trial, n, ctx->stream);
+        HY_TRY(check_launch(ctx, 1));
+        HY_TRY(jacobian_ok(ctx, trial, ok));
+        if (ok) break;
+        step *= 0.5;
+        rl.backtracks++;
+      }
+      if (!ok) {
+        st = fail(ctx, HY_ERR_JNEG, "newton: J <= 0 after 5 halvings");
+        break;
+      }
+      HY_CK(cudaMemcpyAsync(u, trial, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+      ++its;
+    }
+    if (s <= 64) rl.newton_iterations[s - 1] = its;
+    if (st == HY_OK) rl.load_steps_done = s;
+  }
+  HY_CK(cudaStreamSynchronize(ctx->stream));
+  if (rep) *rep = rl;
+  return st;
+}
+
+hy_status hy_dot(hy_ctx* ctx, const double* a, const double* b, int64_t n, double* result) {
+  if (!ctx || !a || !b || !result || n < 0) return HY_ERR_ARG;
+  if (!ctx->d_partials) return fail(ctx, HY_ERR_STATE, "mesh not set up (scratch not allocated)");
+  HY_CK(cudaSetDevice(ctx->device));
+  return dot<double>(ctx, a, b, (long long)n, result);
+}
+
+hy_status hy_kernel_launches(const hy_ctx* ctx, int64_t* count) {
+  if (!ctx || !count) return HY_ERR_ARG;
+  *count = ctx->launches;
+  return HY_OK;
+}
+
+}  // extern "C"

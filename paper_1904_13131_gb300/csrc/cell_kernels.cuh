@@ -1,0 +1,664 @@
+// Cell kernels: tangent action (Eq. mf_vmult with Eq. algebraic_tangent), Gauss-point state build,
+// residual (Eq. weak_form) and operator diagonal, all with sum factorisation (Sec. 5).
+//
+// Work decomposition: one thread block per batch of CB cells, one thread per (cell, Gauss point) --
+// the Gauss points and the nodes of a cell are both (k+1)^dim, so the same thread owns node p during
+// gather/scatter and Gauss point p during the quadrature work. Each 1D contraction of the sum
+// factorisation is a length-(k+1) dot product along one lattice line of the cell, read from shared
+// memory; components are processed together so each stage needs one barrier.
+//
+// Integration is in the reference configuration: the paper integrates over the spatial configuration
+// and divides by J (Sec. 5), which is the same integral. With G = d x / d xi (unit-cell derivative),
+// M = F^{-1} / h and W = w_q h^dim, the quantity contracted with the unit-cell shape gradients is
+//   P~ = Q~ M^T,   Q~ = g tau~ + JC~ : sym(g),   g = G M,   tau~ = W tau,   JC~ = W JC,
+// so y_{a,c} = sum_q sum_J P~_{cJ} d N_a / d xi_J, i.e. sum_q W [g tau + JC:grad^s x] : grad(N_a e_c).
+#pragma once
+#include "hy_internal.cuh"
+
+namespace hy {
+
+template <typename T>
+struct CellArgs {
+  const T* x;             // apply: source vector (level precision)
+  T* y;                   // apply / residual / diag: destination, accumulated with atomics
+  const T* ubar;          // level displacement in T (variants that recompute F)
+  const double* u64;      // level displacement in FP64 (state build, residual, diagonal)
+  const T* cache;         // per-Gauss-point cache, structure of arrays [value][cell * NPT + q]
+  T* cache_out;           // state build output
+  const uint8_t* mat;     // material id per cell
+  unsigned* err;          // device error word (J <= 0, NaN)
+  unsigned long long* jmin_bits;  // min J over Gauss points, as ordered bits of a positive double
+  Mat<T> mt;
+  Geom g;
+  Basis1D<T> b;
+  long long nqp;          // ncells * NPT, stride of the cache arrays
+};
+
+// --- small helpers ------------------------------------------------------------------------------
+template <int N, int STRIDE, bool TR, typename T>
+__device__ __forceinline__ T contract(const T* __restrict__ line, int pax, const T (*M)[MAXN]) {
+  // line points at the first entry of this thread's lattice line; M[r][j] (TR: M[j][r])
+  T s = (TR ? M[0][pax] : M[pax][0]) * line[0];
+#pragma unroll
+  for (int j = 1; j < N; ++j) s = fma(TR ? M[j][pax] : M[pax][j], line[j * STRIDE], s);
+  return s;
+}
+
+template <int DIM, int N>
+struct Pt {
+  int p, pc[3], stride[3];
+  __device__ __forceinline__ explicit Pt(int p_) : p(p_) {
+    pc[0] = p_ % N;
+    pc[1] = (p_ / N) % N;
+    pc[2] = DIM == 3 ? p_ / (N * N) : 0;
+    stride[0] = 1;
+    stride[1] = N;
+    stride[2] = N * N;
+  }
+  __device__ __forceinline__ int base(int ax) const { return p - pc[ax] * stride[ax]; }
+};
+
+// Forward sum factorisation for NC components stored [c][NPT] at b0: interpolate to the Gauss
+// points along every axis (S), ping-ponging through b1. Returns the buffer holding the values.
+template <int DIM, int N, int NC, typename T>
+__device__ __forceinline__ T* interp_forward(T* b0, T* b1, const Pt<DIM, N>& pt, const T (*S)[MAXN]) {
+  constexpr int NPT = ipow(N, DIM);
+  T* src = b0;
+  T* dst = b1;
+#pragma unroll
+  for (int ax = 0; ax < DIM; ++ax) {
+    const int base = pt.base(ax);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const T* line = src + c * NPT + base;
+      T v;
+      if (ax == 0) v = contract<N, 1, false>(line, pt.pc[0], S);
+      else if (ax == 1) v = contract<N, N, false>(line, pt.pc[1], S);
+      else v = contract<N, N * N, false>(line, pt.pc[2], S);
+      dst[c * NPT + pt.p] = v;
+    }
+    __syncthreads();
+    T* t = src; src = dst; dst = t;
+  }
+  return src;
+}
+
+// Collocation derivatives at the Gauss points: G[c][J] = sum_j D[q_J][j] V_c(q with q_J = j).
+template <int DIM, int N, typename T>
+__device__ __forceinline__ void colloc_grad(const T* V, const Pt<DIM, N>& pt, const T (*D)[MAXN], T G[DIM][DIM]) {
+  constexpr int NPT = ipow(N, DIM);
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    G[c][0] = contract<N, 1, false>(V + c * NPT + pt.base(0), pt.pc[0], D);
+    G[c][1] = contract<N, N, false>(V + c * NPT + pt.base(1), pt.pc[1], D);
+    if (DIM == 3) G[c][DIM - 1] = contract<N, N * N, false>(V + c * NPT + pt.base(2), pt.pc[2], D);
+  }
+}
+
+// Transposed sum factorisation: from P~[c*DIM+J][NPT] at bp, apply D^T along J and sum over J, then
+// S^T along every axis; ping-pongs through b0/b1 and returns the buffer holding nodal values.
+template <int DIM, int N, typename T>
+__device__ __forceinline__ T* integrate_backward(const T* bp, T* b0, T* b1, const Pt<DIM, N>& pt,
+                                                 const T (*S)[MAXN], const T (*D)[MAXN]) {
+  constexpr int NPT = ipow(N, DIM);
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    const T* P0 = bp + (c * DIM + 0) * NPT;
+    const T* P1 = bp + (c * DIM + 1) * NPT;
+    T s = contract<N, 1, true>(P0 + pt.base(0), pt.pc[0], D);
+    s += contract<N, N, true>(P1 + pt.base(1), pt.pc[1], D);
+    if (DIM == 3) s += contract<N, N * N, true>(bp + (c * DIM + DIM - 1) * NPT + pt.base(2), pt.pc[2], D);
+    b0[c * NPT + pt.p] = s;
+  }
+  __syncthreads();
+  T* src = b0;
+  T* dst = b1;
+#pragma unroll
+  for (int ax = DIM - 1; ax >= 0; --ax) {
+    const int base = pt.base(ax);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      const T* line = src + c * NPT + base;
+      T v;
+      if (ax == 0) v = contract<N, 1, true>(line, pt.pc[0], S);
+      else if (ax == 1) v = contract<N, N, true>(line, pt.pc[1], S);
+      else v = contract<N, N * N, true>(line, pt.pc[2], S);
+      dst[c * NPT + pt.p] = v;
+    }
+    __syncthreads();
+    T* t = src; src = dst; dst = t;
+  }
+  return src;
+}
+
+// Voigt pairs: 3D (00,11,22,01,02,12), 2D (00,11,01).
+template <int DIM> __device__ __forceinline__ constexpr int vi(int a) {
+  return DIM == 3 ? (a < 3 ? a : (a == 5 ? 1 : 0)) : (a < 2 ? a : 0);
+}
+template <int DIM> __device__ __forceinline__ constexpr int vj(int a) {
+  return DIM == 3 ? (a < 3 ? a : (a == 3 ? 1 : 2)) : (a < 2 ? a : 1);
+}
+
+// P~ = Q M^T with Q = g tau + S (S symmetric, Voigt), g = G M.
+template <int DIM, typename T>
+__device__ __forceinline__ void finish_flux(const T g[DIM][DIM], const T tau[nsym(DIM)], const T Sv[nsym(DIM)],
+                                            const T M[DIM][DIM], T P[DIM][DIM]) {
+  constexpr int NS = nsym(DIM);
+  T tf[DIM][DIM];
+#pragma unroll
+  for (int a = 0; a < NS; ++a) {
+    tf[vi<DIM>(a)][vj<DIM>(a)] = tau[a];
+    tf[vj<DIM>(a)][vi<DIM>(a)] = tau[a];
+  }
+  T Sf[DIM][DIM];
+#pragma unroll
+  for (int a = 0; a < NS; ++a) {
+    Sf[vi<DIM>(a)][vj<DIM>(a)] = Sv[a];
+    Sf[vj<DIM>(a)][vi<DIM>(a)] = Sv[a];
+  }
+  T Q[DIM][DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      T s = Sf[i][j];
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) s = fma(g[i][k], tf[k][j], s);
+      Q[i][j] = s;
+    }
+#pragma unroll
+  for (int c = 0; c < DIM; ++c)
+#pragma unroll
+    for (int J = 0; J < DIM; ++J) {
+      T s = Q[c][0] * M[J][0];
+#pragma unroll
+      for (int j = 1; j < DIM; ++j) s = fma(Q[c][j], M[J][j], s);
+      P[c][J] = s;
+    }
+}
+
+template <int DIM, typename T>
+__device__ __forceinline__ void matmul(const T A[DIM][DIM], const T B[DIM][DIM], T C[DIM][DIM]) {
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      T s = A[i][0] * B[0][j];
+#pragma unroll
+      for (int k = 1; k < DIM; ++k) s = fma(A[i][k], B[k][j], s);
+      C[i][j] = s;
+    }
+}
+
+// Neo-Hooke state at a Gauss point from F (Sec. 2.3), in the scaled form used by the kernels:
+// M = F^{-1}/h, tau~ = W (mu b - (mu - 2 lambda ln J) I), c1~ = 2 W (mu - 2 lambda ln J), c2~ = 2 W lambda.
+// If c1 is given (>= 0 flag), it replaces mu - 2 lambda ln J (Algorithm 1 caches it).
+template <int DIM, typename T>
+__device__ __forceinline__ T neo_hooke_state(const T F[DIM][DIM], T mu, T lam, T W, T inv_h, bool have_c, T c_in,
+                                             T M[DIM][DIM], T tau[nsym(DIM)], T& c1, T& c2) {
+  T J;
+  if (DIM == 3) {
+    const T a00 = F[1][1] * F[2][2] - F[1][2] * F[2][1];
+    const T a01 = F[0][2] * F[2][1] - F[0][1] * F[2][2];
+    const T a02 = F[0][1] * F[1][2] - F[0][2] * F[1][1];
+    const T a10 = F[1][2] * F[2][0] - F[1][0] * F[2][2];
+    const T a11 = F[0][0] * F[2][2] - F[0][2] * F[2][0];
+    const T a12 = F[0][2] * F[1][0] - F[0][0] * F[1][2];
+    const T a20 = F[1][0] * F[2][1] - F[1][1] * F[2][0];
+    const T a21 = F[0][1] * F[2][0] - F[0][0] * F[2][1];
+    const T a22 = F[0][0] * F[1][1] - F[0][1] * F[1][0];
+    J = F[0][0] * a00 + F[0][1] * a10 + F[0][2] * a20;
+    const T s = inv_h / J;
+    M[0][0] = a00 * s; M[0][1] = a01 * s; M[0][2] = a02 * s;
+    M[1][0] = a10 * s; M[1][1] = a11 * s; M[1][2] = a12 * s;
+    M[2][0] = a20 * s; M[2][1] = a21 * s; M[2][2] = a22 * s;
+  } else {
+    J = F[0][0] * F[1][1] - F[0][1] * F[1][0];
+    const T s = inv_h / J;
+    M[0][0] = F[1][1] * s; M[0][1] = -F[0][1] * s;
+    M[1][0] = -F[1][0] * s; M[1][1] = F[0][0] * s;
+  }
+  const T c = have_c ? c_in : mu - T(2) * lam * log(J);
+  const T Wmu = W * mu;
+#pragma unroll
+  for (int a = 0; a < nsym(DIM); ++a) {
+    const int i = vi<DIM>(a), j = vj<DIM>(a);
+    T bij = F[i][0] * F[j][0];
+#pragma unroll
+    for (int k = 1; k < DIM; ++k) bij = fma(F[i][k], F[j][k], bij);
+    tau[a] = Wmu * bij - (i == j ? W * c : T(0));
+  }
+  c1 = T(2) * W * c;
+  c2 = T(2) * W * lam;
+  return J;
+}
+
+// Material part for the neo-Hooke action (Eq. simplified_action): S = c1 sym(g) + c2 tr(g) I.
+template <int DIM, typename T>
+__device__ __forceinline__ void nh_action(const T g[DIM][DIM], T c1, T c2, T Sv[nsym(DIM)]) {
+  T tr = g[0][0];
+#pragma unroll
+  for (int i = 1; i < DIM; ++i) tr += g[i][i];
+  const T ct = c2 * tr;
+  const T hc = T(0.5) * c1;
+#pragma unroll
+  for (int a = 0; a < nsym(DIM); ++a) {
+    const int i = vi<DIM>(a), j = vj<DIM>(a);
+    Sv[a] = (i == j) ? fma(c1, g[i][i], ct) : hc * (g[i][j] + g[j][i]);
+  }
+}
+
+// Shared-memory layout of one block.
+template <int DIM, int N, typename T>
+struct Smem {
+  static constexpr int NPT = ipow(N, DIM);
+  static constexpr int CB = cells_per_block(DIM, N);
+  T S[MAXN][MAXN], D[MAXN][MAXN], W[NPT];
+  T mu[MAXMAT], lam[MAXMAT];
+  T bp[CB][DIM * DIM][NPT];  // fluxes; also the ping-pong pair for the displacement
+  T b0[CB][DIM][NPT];
+  T b1[CB][DIM][NPT];
+};
+
+template <int DIM, int N, typename T>
+__device__ __forceinline__ void load_tables(Smem<DIM, N, T>& s, const CellArgs<T>& a) {
+  constexpr int NPT = ipow(N, DIM);
+  const int t = threadIdx.x;
+  if (t < MAXN * MAXN) {
+    s.S[t / MAXN][t % MAXN] = a.b.S[t / MAXN][t % MAXN];
+    s.D[t / MAXN][t % MAXN] = a.b.D[t / MAXN][t % MAXN];
+  }
+  if (t < NPT) {
+    const int q0 = t % N, q1 = (t / N) % N, q2 = DIM == 3 ? t / (N * N) : 0;
+    T w = a.b.w[q0] * a.b.w[q1];
+    if (DIM == 3) w *= a.b.w[q2];
+    T hd = T(a.g.h) * T(a.g.h);
+    if (DIM == 3) hd *= T(a.g.h);
+    s.W[t] = w * hd;
+  }
+  if (t < MAXMAT) {
+    s.mu[t] = a.mt.mu[t];
+    s.lam[t] = a.mt.lam[t];
+  }
+}
+
+// Lattice location of (cell, local node p).
+template <int DIM, int N>
+struct CellLoc {
+  int node;
+  uint32_t cmask;
+  __device__ __forceinline__ CellLoc(const Geom& g, int cell, const Pt<DIM, N>& pt) {
+    constexpr int K = N - 1;
+    const int m = g.m;
+    const int c0 = cell % m;
+    const int c1 = (cell / m) % m;
+    const int c2 = DIM == 3 ? cell / (m * m) : 0;
+    const int i0 = K * c0 + pt.pc[0], i1 = K * c1 + pt.pc[1], i2 = K * c2 + pt.pc[2];
+    node = i0 + g.L * (i1 + (DIM == 3 ? g.L * i2 : 0));
+    cmask = node_cmask<DIM>(g, i0, i1, i2);
+  }
+};
+
+// ------------------------------------------------------------------------------------------------
+// Tangent action y += A(u) x on the cells of this block (Eq. mf_vmult), variants:
+//   T4: cache M, tau~, JC~ (Algorithm 3)            T2: cache M, tau~, c1~, c2~ (Algorithm 2)
+//   FC: cache F, recompute the neo-Hooke state      SC: cache mu - 2 lambda ln J, recompute F (Algorithm 1)
+//   NC: nothing cached, recompute F and the state from the gathered displacement.
+// Constrained dofs: x is read as zero there and nothing is added to y there.
+template <int DIM, int N, int VAR, typename T>
+__global__ void __launch_bounds__(cells_per_block(DIM, N) * ipow(N, DIM))
+apply_kernel(const CellArgs<T> a) {
+  constexpr int NPT = ipow(N, DIM);
+  constexpr int CB = cells_per_block(DIM, N);
+  constexpr int NS = nsym(DIM);
+  constexpr bool NEED_U = (VAR == VAR_NC || VAR == VAR_SC);
+  __shared__ Smem<DIM, N, T> s;
+  load_tables<DIM, N>(s, a);
+  const int cl = threadIdx.x / NPT;
+  const Pt<DIM, N> pt(threadIdx.x % NPT);
+  const int cell = blockIdx.x * CB + cl;
+  const bool active = cell < a.g.ncells;
+  const CellLoc<DIM, N> loc(a.g, active ? cell : 0, pt);
+  T* b0 = &s.b0[cl][0][0];
+  T* b1 = &s.b1[cl][0][0];
+  T* bp = &s.bp[cl][0][0];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    T v = T(0), w = T(0);
+    if (active) {
+      v = ((loc.cmask >> c) & 1u) ? T(0) : a.x[(long long)loc.node * DIM + c];
+      if (NEED_U) w = a.ubar[(long long)loc.node * DIM + c];
+    }
+    b0[c * NPT + pt.p] = v;
+    if (NEED_U) bp[c * NPT + pt.p] = w;
+  }
+  __syncthreads();
+  // forward: x (and u) to the Gauss points, then collocation derivatives
+  T G[DIM][DIM], Gu[DIM][DIM];
+  if (NEED_U) {
+    // interpolate both fields in the same stages
+    T* sx = b0; T* dx = b1; T* su = bp; T* du = bp + DIM * NPT;
+#pragma unroll
+    for (int ax = 0; ax < DIM; ++ax) {
+      const int base = pt.base(ax);
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        T vx, vu;
+        if (ax == 0) {
+          vx = contract<N, 1, false>(sx + c * NPT + base, pt.pc[0], s.S);
+          vu = contract<N, 1, false>(su + c * NPT + base, pt.pc[0], s.S);
+        } else if (ax == 1) {
+          vx = contract<N, N, false>(sx + c * NPT + base, pt.pc[1], s.S);
+          vu = contract<N, N, false>(su + c * NPT + base, pt.pc[1], s.S);
+        } else {
+          vx = contract<N, N * N, false>(sx + c * NPT + base, pt.pc[2], s.S);
+          vu = contract<N, N * N, false>(su + c * NPT + base, pt.pc[2], s.S);
+        }
+        dx[c * NPT + pt.p] = vx;
+        du[c * NPT + pt.p] = vu;
+      }
+      __syncthreads();
+      T* t = sx; sx = dx; dx = t;
+      t = su; su = du; du = t;
+    }
+    colloc_grad<DIM, N>(sx, pt, s.D, G);
+    colloc_grad<DIM, N>(su, pt, s.D, Gu);
+    __syncthreads();  // bp is overwritten with the fluxes below
+  } else {
+    const T* V = interp_forward<DIM, N, DIM>(b0, b1, pt, s.S);
+    colloc_grad<DIM, N>(V, pt, s.D, G);
+  }
+  // quadrature-point work
+  T P[DIM][DIM];
+  {
+    const long long qg = (long long)(active ? cell : 0) * NPT + pt.p;
+    const long long st = a.nqp;
+    T M[DIM][DIM], tau[NS], Sv[NS], g[DIM][DIM];
+    if (VAR == VAR_T4 || VAR == VAR_T2) {
+#pragma unroll
+      for (int i = 0; i < DIM * DIM; ++i) M[i / DIM][i % DIM] = active ? a.cache[i * st + qg] : T(0);
+#pragma unroll
+      for (int i = 0; i < NS; ++i) tau[i] = active ? a.cache[(DIM * DIM + i) * st + qg] : T(0);
+      matmul<DIM>(G, M, g);
+      if (VAR == VAR_T4) {
+        constexpr int OFF = DIM * DIM + NS;
+        T v[NS];
+#pragma unroll
+        for (int al = 0; al < NS; ++al) {
+          const int i = vi<DIM>(al), j = vj<DIM>(al);
+          v[al] = (i == j) ? g[i][i] : g[i][j] + g[j][i];
+        }
+#pragma unroll
+        for (int al = 0; al < NS; ++al) {
+          T acc = T(0);
+#pragma unroll
+          for (int be = 0; be < NS; ++be) {
+            const int lo = al < be ? al : be, hi = al < be ? be : al;
+            const int idx = lo * NS - lo * (lo - 1) / 2 + (hi - lo);  // upper triangle, row major
+            const T cv = active ? a.cache[(OFF + idx) * st + qg] : T(0);
+            acc = (be == 0) ? cv * v[be] : fma(cv, v[be], acc);
+          }
+          Sv[al] = acc;
+        }
+      } else {
+        const T c1 = active ? a.cache[(DIM * DIM + NS) * st + qg] : T(0);
+        const T c2 = active ? a.cache[(DIM * DIM + NS + 1) * st + qg] : T(0);
+        nh_action<DIM>(g, c1, c2, Sv);
+      }
+    } else {
+      T F[DIM][DIM];
+      const T inv_h = T(1.0 / a.g.h);
+      if (VAR == VAR_FC) {
+#pragma unroll
+        for (int i = 0; i < DIM * DIM; ++i)
+          F[i / DIM][i % DIM] = active ? a.cache[i * st + qg] : (i % (DIM + 1) == 0 ? T(1) : T(0));
+      } else {
+#pragma unroll
+        for (int i = 0; i < DIM; ++i)
+#pragma unroll
+          for (int J = 0; J < DIM; ++J) F[i][J] = (i == J ? T(1) : T(0)) + Gu[i][J] * inv_h;
+      }
+      const int id = active ? a.mat[cell] : 0;
+      const T cin = (VAR == VAR_SC && active) ? a.cache[qg] : T(0);
+      T c1, c2;
+      neo_hooke_state<DIM>(F, s.mu[id], s.lam[id], s.W[pt.p], inv_h, VAR == VAR_SC, cin, M, tau, c1, c2);
+      matmul<DIM>(G, M, g);
+      nh_action<DIM>(g, c1, c2, Sv);
+    }
+    finish_flux<DIM>(g, tau, Sv, M, P);
+  }
+#pragma unroll
+  for (int c = 0; c < DIM; ++c)
+#pragma unroll
+    for (int J = 0; J < DIM; ++J) bp[(c * DIM + J) * NPT + pt.p] = P[c][J];
+  __syncthreads();
+  const T* Y = integrate_backward<DIM, N>(bp, b0, b1, pt, s.S, s.D);
+  if (active) {
+#pragma unroll
+    for (int c = 0; c < DIM; ++c)
+      if (!((loc.cmask >> c) & 1u)) atomicAdd(&a.y[(long long)loc.node * DIM + c], Y[c * NPT + pt.p]);
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Gauss-point state from the level displacement (FP64 kinematics F, J, ln J; Sec. 2.1, 2.3), stored
+// per variant in T: T4 {M, tau~, JC~ (Voigt upper triangle)}, T2 {M, tau~, c1~, c2~}, FC {F},
+// SC {mu - 2 lambda ln J}. Flags J <= 0 / NaN in the error word and tracks min J.
+template <int DIM, int N, int VAR, typename T>
+__global__ void __launch_bounds__(cells_per_block(DIM, N) * ipow(N, DIM))
+qp_state_kernel(const CellArgs<double> a, T* __restrict__ out) {
+  constexpr int NPT = ipow(N, DIM);
+  constexpr int CB = cells_per_block(DIM, N);
+  constexpr int NS = nsym(DIM);
+  __shared__ Smem<DIM, N, double> s;
+  load_tables<DIM, N>(s, a);
+  const int cl = threadIdx.x / NPT;
+  const Pt<DIM, N> pt(threadIdx.x % NPT);
+  const int cell = blockIdx.x * CB + cl;
+  const bool active = cell < a.g.ncells;
+  const CellLoc<DIM, N> loc(a.g, active ? cell : 0, pt);
+  double* b0 = &s.b0[cl][0][0];
+  double* b1 = &s.b1[cl][0][0];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) b0[c * NPT + pt.p] = active ? a.u64[(long long)loc.node * DIM + c] : 0.0;
+  __syncthreads();
+  const double* V = interp_forward<DIM, N, DIM>(b0, b1, pt, s.S);
+  double Gu[DIM][DIM];
+  colloc_grad<DIM, N>(V, pt, s.D, Gu);
+  if (!active) return;
+  const double inv_h = 1.0 / a.g.h;
+  double F[DIM][DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int J = 0; J < DIM; ++J) F[i][J] = (i == J ? 1.0 : 0.0) + Gu[i][J] * inv_h;
+  const int id = a.mat[cell];
+  const double mu = s.mu[id], lam = s.lam[id];
+  double M[DIM][DIM], tau[NS], c1, c2;
+  const double J = neo_hooke_state<DIM>(F, mu, lam, s.W[pt.p], inv_h, false, 0.0, M, tau, c1, c2);
+  if (!(J > 0.0)) {
+    atomicOr(a.err, J != J ? ERRBIT_NAN : ERRBIT_JNEG);
+  } else {
+    atomicMin(a.jmin_bits, (unsigned long long)__double_as_longlong(J));
+  }
+  const long long qg = (long long)cell * NPT + pt.p;
+  const long long st = a.nqp;
+  if (VAR == VAR_T4 || VAR == VAR_T2) {
+#pragma unroll
+    for (int i = 0; i < DIM * DIM; ++i) out[i * st + qg] = T(M[i / DIM][i % DIM]);
+#pragma unroll
+    for (int i = 0; i < NS; ++i) out[(DIM * DIM + i) * st + qg] = T(tau[i]);
+    if (VAR == VAR_T2) {
+      out[(DIM * DIM + NS) * st + qg] = T(c1);
+      out[(DIM * DIM + NS + 1) * st + qg] = T(c2);
+    } else {
+      // JC~ = c1~ S + c2~ I (x) I (Sec. 2.3) in Voigt form: K_ab = JC_{i(a) j(a) k(b) l(b)}
+      constexpr int OFF = DIM * DIM + NS;
+      int idx = 0;
+#pragma unroll
+      for (int al = 0; al < NS; ++al)
+#pragma unroll
+        for (int be = al; be < NS; ++be) {
+          const int i = vi<DIM>(al), j = vj<DIM>(al), k = vi<DIM>(be), l = vj<DIM>(be);
+          const double Sijkl = 0.5 * ((i == k && j == l ? 1.0 : 0.0) + (i == l && j == k ? 1.0 : 0.0));
+          const double v = c1 * Sijkl + (i == j && k == l ? c2 : 0.0);
+          out[(OFF + idx) * st + qg] = T(v);
+          ++idx;
+        }
+    }
+  } else if (VAR == VAR_FC) {
+#pragma unroll
+    for (int i = 0; i < DIM * DIM; ++i) out[i * st + qg] = T(F[i / DIM][i % DIM]);
+  } else if (VAR == VAR_SC) {
+    out[qg] = T(mu - 2.0 * lam * log(J));
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Residual r += R(u) (Eq. weak_form) in FP64: P~ = tau~ M^T integrated against the shape gradients.
+// Constrained rows receive nothing (the caller zeroes r first).
+template <int DIM, int N>
+__global__ void __launch_bounds__(cells_per_block(DIM, N) * ipow(N, DIM))
+residual_kernel(const CellArgs<double> a) {
+  constexpr int NPT = ipow(N, DIM);
+  constexpr int CB = cells_per_block(DIM, N);
+  constexpr int NS = nsym(DIM);
+  __shared__ Smem<DIM, N, double> s;
+  load_tables<DIM, N>(s, a);
+  const int cl = threadIdx.x / NPT;
+  const Pt<DIM, N> pt(threadIdx.x % NPT);
+  const int cell = blockIdx.x * CB + cl;
+  const bool active = cell < a.g.ncells;
+  const CellLoc<DIM, N> loc(a.g, active ? cell : 0, pt);
+  double* b0 = &s.b0[cl][0][0];
+  double* b1 = &s.b1[cl][0][0];
+  double* bp = &s.bp[cl][0][0];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) b0[c * NPT + pt.p] = active ? a.u64[(long long)loc.node * DIM + c] : 0.0;
+  __syncthreads();
+  const double* V = interp_forward<DIM, N, DIM>(b0, b1, pt, s.S);
+  double Gu[DIM][DIM];
+  colloc_grad<DIM, N>(V, pt, s.D, Gu);
+  const double inv_h = 1.0 / a.g.h;
+  double F[DIM][DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int J = 0; J < DIM; ++J) F[i][J] = (i == J ? 1.0 : 0.0) + Gu[i][J] * inv_h;
+  const int id = active ? a.mat[cell] : 0;
+  double M[DIM][DIM], tau[NS], c1, c2;
+  const double J = neo_hooke_state<DIM>(F, s.mu[id], s.lam[id], s.W[pt.p], inv_h, false, 0.0, M, tau, c1, c2);
+  if (active && !(J > 0.0)) atomicOr(a.err, J != J ? ERRBIT_NAN : ERRBIT_JNEG);
+  double tf[DIM][DIM];
+#pragma unroll
+  for (int al = 0; al < NS; ++al) {
+    tf[vi<DIM>(al)][vj<DIM>(al)] = tau[al];
+    tf[vj<DIM>(al)][vi<DIM>(al)] = tau[al];
+  }
+#pragma unroll
+  for (int c = 0; c < DIM; ++c)
+#pragma unroll
+    for (int Jx = 0; Jx < DIM; ++Jx) {
+      double acc = tf[c][0] * M[Jx][0];
+#pragma unroll
+      for (int j = 1; j < DIM; ++j) acc = fma(tf[c][j], M[Jx][j], acc);
+      bp[(c * DIM + Jx) * NPT + pt.p] = active ? acc : 0.0;
+    }
+  __syncthreads();
+  const double* Y = integrate_backward<DIM, N>(bp, b0, b1, pt, s.S, s.D);
+  if (active) {
+#pragma unroll
+    for (int c = 0; c < DIM; ++c)
+      if (!((loc.cmask >> c) & 1u)) atomicAdd(&a.y[(long long)loc.node * DIM + c], Y[c * NPT + pt.p]);
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Diagonal of the tangent, d += diag A(u), FP64. For node a and component c:
+//   A_{ac,ac} = sum_q W [ g_a . tau . g_a + c1 (|g_a|^2 + g_{a,c}^2)/2 + c2 g_{a,c}^2 ],  g_a = F^{-T} Grad N_a,
+// the geometric and material parts of Eq. algebraic_tangent with the action of Eq. simplified_action.
+template <int DIM, int N>
+__global__ void __launch_bounds__(cells_per_block(DIM, N) * ipow(N, DIM))
+diag_kernel(const CellArgs<double> a) {
+  constexpr int NPT = ipow(N, DIM);
+  constexpr int CB = cells_per_block(DIM, N);
+  constexpr int NS = nsym(DIM);
+  __shared__ Smem<DIM, N, double> s;
+  __shared__ double Sd[MAXN][MAXN];
+  __shared__ double st[CB][NS + 2][NPT];
+  load_tables<DIM, N>(s, a);
+  if (threadIdx.x < MAXN * MAXN) Sd[threadIdx.x / MAXN][threadIdx.x % MAXN] = a.b.Sd[threadIdx.x / MAXN][threadIdx.x % MAXN];
+  const int cl = threadIdx.x / NPT;
+  const Pt<DIM, N> pt(threadIdx.x % NPT);
+  const int cell = blockIdx.x * CB + cl;
+  const bool active = cell < a.g.ncells;
+  const CellLoc<DIM, N> loc(a.g, active ? cell : 0, pt);
+  double* b0 = &s.b0[cl][0][0];
+  double* b1 = &s.b1[cl][0][0];
+  double* bp = &s.bp[cl][0][0];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) b0[c * NPT + pt.p] = active ? a.u64[(long long)loc.node * DIM + c] : 0.0;
+  __syncthreads();
+  const double* V = interp_forward<DIM, N, DIM>(b0, b1, pt, s.S);
+  double Gu[DIM][DIM];
+  colloc_grad<DIM, N>(V, pt, s.D, Gu);
+  const double inv_h = 1.0 / a.g.h;
+  double F[DIM][DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int J = 0; J < DIM; ++J) F[i][J] = (i == J ? 1.0 : 0.0) + Gu[i][J] * inv_h;
+  const int id = active ? a.mat[cell] : 0;
+  double M[DIM][DIM], tau[NS], c1, c2;
+  neo_hooke_state<DIM>(F, s.mu[id], s.lam[id], s.W[pt.p], inv_h, false, 0.0, M, tau, c1, c2);
+  // per-point state to shared memory: M in bp (DIM^2 rows), tau, c1, c2 in st (NS + 2 rows)
+#pragma unroll
+  for (int i = 0; i < DIM * DIM; ++i) bp[i * NPT + pt.p] = M[i / DIM][i % DIM];
+#pragma unroll
+  for (int i = 0; i < NS; ++i) st[cl][i][pt.p] = tau[i];
+  st[cl][NS][pt.p] = c1;
+  st[cl][NS + 1][pt.p] = c2;
+  __syncthreads();
+  // thread now plays node a = pt.p
+  double dsum[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) dsum[c] = 0.0;
+  for (int q = 0; q < NPT; ++q) {
+    const int q0 = q % N, q1 = (q / N) % N, q2 = DIM == 3 ? q / (N * N) : 0;
+    double gr[DIM];  // d N_a / d xi at q
+    const double s0 = s.S[q0][pt.pc[0]], s1 = s.S[q1][pt.pc[1]];
+    const double s2 = DIM == 3 ? s.S[q2][pt.pc[2]] : 1.0;
+    gr[0] = Sd[q0][pt.pc[0]] * s1 * s2;
+    gr[1] = s0 * Sd[q1][pt.pc[1]] * s2;
+    if (DIM == 3) gr[DIM - 1] = s0 * s1 * Sd[q2][pt.pc[2]];
+    double ga[DIM];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      double acc = gr[0] * bp[(0 * DIM + j) * NPT + q];
+#pragma unroll
+      for (int J = 1; J < DIM; ++J) acc = fma(gr[J], bp[(J * DIM + j) * NPT + q], acc);
+      ga[j] = acc;
+    }
+    double tq[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) tq[i] = st[cl][i][q];
+    double geo = 0.0, nrm = 0.0;
+#pragma unroll
+    for (int al = 0; al < NS; ++al) {
+      const int i = vi<DIM>(al), j = vj<DIM>(al);
+      geo = fma((i == j ? 1.0 : 2.0) * ga[i] * ga[j], tq[al], geo);
+    }
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) nrm = fma(ga[j], ga[j], nrm);
+    const double qc1 = st[cl][NS][q], qc2 = st[cl][NS + 1][q];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) dsum[c] += geo + 0.5 * qc1 * (nrm + ga[c] * ga[c]) + qc2 * ga[c] * ga[c];
+  }
+  if (active) {
+#pragma unroll
+    for (int c = 0; c < DIM; ++c)
+      if (!((loc.cmask >> c) & 1u)) atomicAdd(&a.y[(long long)loc.node * DIM + c], dsum[c]);
+  }
+}
+
+}  // namespace hy

@@ -1,0 +1,79 @@
+// Internal definitions shared by the CUDA translation units of libhyperelastic.
+//
+// Mesh model: uniform m^dim Cartesian cells of side h = 1/m on the unit square/cube, Q_k Lagrange
+// elements on Gauss-Lobatto-Legendre nodes, (k+1)^dim Gauss points per cell (Sec. 7, Tables 1-2:
+// q = p + 1). Vectors live on the (k m + 1)^dim node lattice, x fastest, the dim displacement
+// components of a node interleaved (dof = node * dim + comp). A cell gathers (k+1)^{dim-1} contiguous
+// runs of (k+1)*dim values, so no index array is stored.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hy {
+
+constexpr int MAXN = 5;      // polynomial degree <= 4
+constexpr int MAXMAT = 16;   // materials per level
+
+// Sizes of the per-Gauss-point caches of the tangent variants (Algorithms 1-3 and the two
+// cached/recomputed variants), as a function of dim.
+enum Variant { VAR_T4 = 0, VAR_T2 = 1, VAR_FC = 2, VAR_SC = 3, VAR_NC = 4 };
+
+__host__ __device__ constexpr int nsym(int dim) { return dim == 3 ? 6 : 3; }
+__host__ __device__ constexpr int cache_values(int var, int dim) {
+  return var == VAR_T4 ? dim * dim + nsym(dim) + nsym(dim) * (nsym(dim) + 1) / 2
+       : var == VAR_T2 ? dim * dim + nsym(dim) + 2
+       : var == VAR_FC ? dim * dim
+       : var == VAR_SC ? 1
+       : 0;
+}
+
+// 1D tables of the Q_k element on [0,1] (built on the host in double, converted to T).
+template <typename T>
+struct Basis1D {
+  T S[MAXN][MAXN];   // S[q][a]  = l_a(xg_q): GLL-nodal basis at Gauss point q
+  T D[MAXN][MAXN];   // D[q][p]  = derivative at xg_q of the Lagrange polynomial through the Gauss points, p
+  T Sd[MAXN][MAXN];  // Sd[q][a] = l_a'(xg_q)
+  T w[MAXN];         // Gauss weights on [0,1]
+};
+
+// Geometry of one level.
+struct Geom {
+  int m;             // cells per direction
+  int L;             // lattice nodes per direction = k m + 1
+  int ncells;        // m^dim
+  uint32_t fm[6];    // constrained-component bitmask per face (-x,+x,-y,+y,-z,+z)
+  double h;          // cell size
+};
+
+template <typename T>
+struct Mat {
+  T mu[MAXMAT];
+  T lam[MAXMAT];
+};
+
+// Bitmask of the constrained components of lattice node (i0, i1, i2).
+template <int DIM>
+__device__ __forceinline__ uint32_t node_cmask(const Geom& g, int i0, int i1, int i2) {
+  uint32_t r = 0;
+  if (i0 == 0) r |= g.fm[0];
+  if (i0 == g.L - 1) r |= g.fm[1];
+  if (i1 == 0) r |= g.fm[2];
+  if (i1 == g.L - 1) r |= g.fm[3];
+  if (DIM == 3) {
+    if (i2 == 0) r |= g.fm[4];
+    if (i2 == g.L - 1) r |= g.fm[5];
+  }
+  return r;
+}
+
+__host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+// Cells per thread block for the cell kernels (thread per Gauss point / node, ~256 threads).
+__host__ __device__ constexpr int cells_per_block(int dim, int n) {
+  return (256 / ipow(n, dim)) < 1 ? 1 : (256 / ipow(n, dim));
+}
+
+// Device-side error word bits.
+enum : unsigned { ERRBIT_JNEG = 1u, ERRBIT_NAN = 2u };
+
+}  // namespace hy

@@ -1,0 +1,62 @@
+// Host-side launchers of the device kernels (declarations; definitions live in the .cu files that
+// instantiate the templates, so that those translation units compile in parallel).
+#pragma once
+#include <cuda_runtime.h>
+#include "hy_internal.cuh"
+
+namespace hy {
+
+template <typename T> struct CellArgs;
+
+template <typename T>
+using CellFn = void (*)(const CellArgs<T>&, cudaStream_t);
+template <typename TOUT>
+using StateFn = void (*)(const CellArgs<double>&, TOUT*, cudaStream_t);
+
+// n = degree + 1 in 2..5; var in Variant; returns nullptr for unsupported combinations
+CellFn<double> apply_fn_f64_2d(int n, int var);
+CellFn<double> apply_fn_f64_3d(int n, int var);
+CellFn<float> apply_fn_f32_2d(int n, int var);
+CellFn<float> apply_fn_f32_3d(int n, int var);
+StateFn<double> state_fn_f64(int dim, int n, int var);   // var VAR_NONE: J check only
+StateFn<float> state_fn_f32(int dim, int n, int var);
+CellFn<double> residual_fn(int dim, int n);
+CellFn<double> diag_fn(int dim, int n);
+
+constexpr int VAR_NONE = 5;
+
+// ---- vector kernels (vec_kernels.cu) ----------------------------------------------------------
+template <typename T> void launch_prep_out(const T* x, T* y, long long n_nodes, int dim, const Geom& g, cudaStream_t st);
+template <typename T> void launch_zero_constrained(T* y, long long n_nodes, int dim, const Geom& g, cudaStream_t st);
+template <typename T> void launch_set_constrained_one(T* y, long long n_nodes, int dim, const Geom& g, cudaStream_t st);
+template <typename T> void launch_invert(const double* d, T* dinv, long long n, cudaStream_t st);
+template <typename TA, typename TB> void launch_convert(const TA* a, TB* b, long long n, cudaStream_t st);
+// y = a*x + b*y
+template <typename T> void launch_axpby(T a, const T* x, T b, T* y, long long n, cudaStream_t st);
+// z = x + a*y
+template <typename T> void launch_xpay(const T* x, T a, const T* y, T* z, long long n, cudaStream_t st);
+// Chebyshev: first step. r = b (x0 zero) or r = b - t; d = dinv*r*inv_theta; x = d (x0 zero) or x += d
+template <typename T> void launch_cheb_init(const T* b, const T* t, const T* dinv, T* r, T* d, T* x, T inv_theta,
+                                            bool x0_zero, long long n, cudaStream_t st);
+// Chebyshev: later step. r -= t; d = cd*d + cr*dinv*r; x += d
+template <typename T> void launch_cheb_step(const T* t, const T* dinv, T* r, T* d, T* x, T cd, T cr, long long n,
+                                            cudaStream_t st);
+// z = a * b (elementwise)
+template <typename T> void launch_mul(const T* a, const T* b, T* z, long long n, cudaStream_t st);
+// out[i] = SplitMix64 uniform on [-1, 1) at counter i (seeded)
+template <typename T> void launch_splitmix(T* out, long long n, unsigned long long seed, cudaStream_t st);
+// r = b - t
+template <typename T> void launch_sub(const T* b, const T* t, T* r, long long n, cudaStream_t st);
+// du0 = constrained ? target - u : 0, target from per-face values scaled by factor
+void launch_lift(const double* u, double* du0, double factor, const double* face_vals /*device [6][3]*/,
+                 long long n_nodes, int dim, const Geom& g, cudaStream_t st);
+// deterministic dot: partial sums in fixed blocks, then one block; result in out[0]
+constexpr int DOT_BLOCKS = 304;
+template <typename T> void launch_dot(const T* a, const T* b, long long n, double* partials, double* out,
+                                      cudaStream_t st);
+// separable 1D transfer sweep along `axis`: out(i with i_axis = o) = sum_e w[o*E+e] in(i with i_axis = start[o]+e)
+template <typename T>
+void launch_sweep(const T* in, T* out, int dim, const int Lin[3], const int Lout[3], int axis, const int* start,
+                  const T* w, int E, bool add_to_out, const Geom* mask_in, const Geom* mask_out, cudaStream_t st);
+
+}  // namespace hy

@@ -1,0 +1,298 @@
+// Vector kernels of the solvers: Dirichlet handling, Chebyshev and CG updates, precision
+// conversion, deterministic dot products, and the separable transfer sweeps of the multigrid.
+// All are bandwidth-bound streams over lattice vectors; grids cover the vector with 256-thread
+// blocks (grid-stride loops capped at a multiple of the SM count).
+#include "launch.cuh"
+
+namespace hy {
+namespace {
+
+constexpr int TPB = 256;
+
+inline int grid_for(long long n) {
+  long long g = (n + TPB - 1) / TPB;
+  const long long cap = 152LL * 16;  // 16 resident blocks of 256 threads per SM, 152 SMs
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+template <int DIM>
+__device__ __forceinline__ uint32_t cmask_of(const Geom& g, long long node) {
+  const int i0 = (int)(node % g.L);
+  const int i1 = (int)((node / g.L) % g.L);
+  const int i2 = DIM == 3 ? (int)(node / ((long long)g.L * g.L)) : 0;
+  return node_cmask<DIM>(g, i0, i1, i2);
+}
+
+template <typename T, int DIM>
+__global__ void prep_out_kernel(const T* __restrict__ x, T* __restrict__ y, long long n_nodes, Geom g) {
+  for (long long nd = blockIdx.x * (long long)blockDim.x + threadIdx.x; nd < n_nodes; nd += (long long)gridDim.x * blockDim.x) {
+    const uint32_t cm = cmask_of<DIM>(g, nd);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) y[nd * DIM + c] = ((cm >> c) & 1u) ? x[nd * DIM + c] : T(0);
+  }
+}
+
+template <typename T, int DIM>
+__global__ void set_constrained_kernel(T* __restrict__ y, long long n_nodes, Geom g, T val) {
+  for (long long nd = blockIdx.x * (long long)blockDim.x + threadIdx.x; nd < n_nodes; nd += (long long)gridDim.x * blockDim.x) {
+    const uint32_t cm = cmask_of<DIM>(g, nd);
+    if (cm) {
+#pragma unroll
+      for (int c = 0; c < DIM; ++c)
+        if ((cm >> c) & 1u) y[nd * DIM + c] = val;
+    }
+  }
+}
+
+template <int DIM>
+__global__ void lift_kernel(const double* __restrict__ u, double* __restrict__ du0, double factor,
+                            const double* __restrict__ fv, long long n_nodes, Geom g) {
+  for (long long nd = blockIdx.x * (long long)blockDim.x + threadIdx.x; nd < n_nodes; nd += (long long)gridDim.x * blockDim.x) {
+    const int i[3] = {(int)(nd % g.L), (int)((nd / g.L) % g.L), DIM == 3 ? (int)(nd / ((long long)g.L * g.L)) : 0};
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      // the prescribed value of the highest-numbered face constraining this component at this node
+      int face = -1;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        if (i[a] == 0 && ((g.fm[2 * a] >> c) & 1u)) face = 2 * a;
+        if (i[a] == g.L - 1 && ((g.fm[2 * a + 1] >> c) & 1u)) face = 2 * a + 1;
+      }
+      // the target is rounded on its own (no FMA contraction) so that u + du0 reproduces it exactly
+      du0[nd * DIM + c] = face < 0 ? 0.0 : __dsub_rn(__dmul_rn(factor, fv[face * 3 + c]), u[nd * DIM + c]);
+    }
+  }
+}
+
+template <typename T>
+__global__ void invert_kernel(const double* __restrict__ d, T* __restrict__ dinv, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dinv[i] = T(1.0 / d[i]);
+}
+
+template <typename TA, typename TB>
+__global__ void convert_kernel(const TA* __restrict__ a, TB* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = TB(a[i]);
+}
+
+template <typename T>
+__global__ void axpby_kernel(T a, const T* x, T b, T* y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+
+template <typename T>
+__global__ void xpay_kernel(const T* __restrict__ x, T a, const T* y, T* z, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    z[i] = x[i] + a * y[i];
+}
+
+template <typename T>
+__global__ void mul_kernel(const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ z, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    z[i] = a[i] * b[i];
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014) at counter i + 1, top 53 bits mapped to [-1, 1).
+template <typename T>
+__global__ void splitmix_kernel(T* __restrict__ out, long long n, unsigned long long seed) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long z = seed + (unsigned long long)(i + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    out[i] = T(2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0);
+  }
+}
+
+template <typename T>
+__global__ void sub_kernel(const T* __restrict__ b, const T* __restrict__ t, T* __restrict__ r, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    r[i] = b[i] - t[i];
+}
+
+template <typename T>
+__global__ void cheb_init_kernel(const T* __restrict__ b, const T* __restrict__ t, const T* __restrict__ dinv,
+                                 T* __restrict__ r, T* __restrict__ d, T* __restrict__ x, T inv_theta, bool x0_zero,
+                                 long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const T ri = x0_zero ? b[i] : b[i] - t[i];
+    const T di = dinv[i] * ri * inv_theta;
+    r[i] = ri;
+    d[i] = di;
+    x[i] = x0_zero ? di : x[i] + di;
+  }
+}
+
+template <typename T>
+__global__ void cheb_step_kernel(const T* __restrict__ t, const T* __restrict__ dinv, T* __restrict__ r,
+                                 T* __restrict__ d, T* __restrict__ x, T cd, T cr, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const T ri = r[i] - t[i];
+    const T di = cd * d[i] + cr * dinv[i] * ri;
+    r[i] = ri;
+    d[i] = di;
+    x[i] += di;
+  }
+}
+
+// Deterministic two-stage reduction: each of DOT_BLOCKS blocks sums a fixed strided subset in a
+// fixed tree order; one block then sums the partials in index order.
+template <typename T>
+__global__ void dot_partial_kernel(const T* __restrict__ a, const T* __restrict__ b, long long n,
+                                   double* __restrict__ partials) {
+  __shared__ double sh[TPB];
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)TPB + threadIdx.x; i < n; i += (long long)DOT_BLOCKS * TPB)
+    s = fma((double)a[i], (double)b[i], s);
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = TPB / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+
+__global__ void dot_final_kernel(const double* __restrict__ partials, double* __restrict__ out) {
+  __shared__ double sh[TPB];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < DOT_BLOCKS; i += TPB) s += partials[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = TPB / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = sh[0];
+}
+
+template <typename T, int DIM>
+__global__ void sweep_kernel(const T* __restrict__ in, T* __restrict__ out, int Li0, int Li1, int Lo0, int Lo1,
+                             int Lo2, int axis, const int* __restrict__ start, const T* __restrict__ w, int E,
+                             bool add, bool use_mask_in, Geom gin, bool use_mask_out, Geom gout) {
+  const long long n_out = (long long)Lo0 * Lo1 * (DIM == 3 ? Lo2 : 1) * DIM;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n_out;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(idx % DIM);
+    const long long nd = idx / DIM;
+    int o[3] = {(int)(nd % Lo0), (int)((nd / Lo0) % Lo1), DIM == 3 ? (int)(nd / ((long long)Lo0 * Lo1)) : 0};
+    const int oa = o[axis];
+    const int s0 = start[oa];
+    T acc = T(0);
+    for (int e = 0; e < E; ++e) {
+      o[axis] = s0 + e;
+      const long long ni = o[0] + (long long)Li0 * (o[1] + (long long)Li1 * o[2]);
+      T v = in[ni * DIM + c];
+      if (use_mask_in && ((node_cmask<DIM>(gin, o[0], o[1], o[2]) >> c) & 1u)) v = T(0);
+      acc = fma(w[(long long)oa * E + e], v, acc);
+    }
+    o[axis] = oa;
+    if (use_mask_out && ((node_cmask<DIM>(gout, o[0], o[1], o[2]) >> c) & 1u)) acc = T(0);
+    out[idx] = add ? out[idx] + acc : acc;
+  }
+}
+
+}  // namespace
+
+template <typename T>
+void launch_prep_out(const T* x, T* y, long long n_nodes, int dim, const Geom& g, cudaStream_t st) {
+  if (dim == 2) prep_out_kernel<T, 2><<<grid_for(n_nodes), TPB, 0, st>>>(x, y, n_nodes, g);
+  else prep_out_kernel<T, 3><<<grid_for(n_nodes), TPB, 0, st>>>(x, y, n_nodes, g);
+}
+template <typename T>
+void launch_zero_constrained(T* y, long long n_nodes, int dim, const Geom& g, cudaStream_t st) {
+  if (dim == 2) set_constrained_kernel<T, 2><<<grid_for(n_nodes), TPB, 0, st>>>(y, n_nodes, g, T(0));
+  else set_constrained_kernel<T, 3><<<grid_for(n_nodes), TPB, 0, st>>>(y, n_nodes, g, T(0));
+}
+template <typename T>
+void launch_set_constrained_one(T* y, long long n_nodes, int dim, const Geom& g, cudaStream_t st) {
+  if (dim == 2) set_constrained_kernel<T, 2><<<grid_for(n_nodes), TPB, 0, st>>>(y, n_nodes, g, T(1));
+  else set_constrained_kernel<T, 3><<<grid_for(n_nodes), TPB, 0, st>>>(y, n_nodes, g, T(1));
+}
+template <typename T>
+void launch_invert(const double* d, T* dinv, long long n, cudaStream_t st) {
+  invert_kernel<T><<<grid_for(n), TPB, 0, st>>>(d, dinv, n);
+}
+template <typename TA, typename TB>
+void launch_convert(const TA* a, TB* b, long long n, cudaStream_t st) {
+  convert_kernel<TA, TB><<<grid_for(n), TPB, 0, st>>>(a, b, n);
+}
+template <typename T>
+void launch_axpby(T a, const T* x, T b, T* y, long long n, cudaStream_t st) {
+  axpby_kernel<T><<<grid_for(n), TPB, 0, st>>>(a, x, b, y, n);
+}
+template <typename T>
+void launch_xpay(const T* x, T a, const T* y, T* z, long long n, cudaStream_t st) {
+  xpay_kernel<T><<<grid_for(n), TPB, 0, st>>>(x, a, y, z, n);
+}
+template <typename T>
+void launch_mul(const T* a, const T* b, T* z, long long n, cudaStream_t st) {
+  mul_kernel<T><<<grid_for(n), TPB, 0, st>>>(a, b, z, n);
+}
+template <typename T>
+void launch_splitmix(T* out, long long n, unsigned long long seed, cudaStream_t st) {
+  splitmix_kernel<T><<<grid_for(n), TPB, 0, st>>>(out, n, seed);
+}
+template <typename T>
+void launch_sub(const T* b, const T* t, T* r, long long n, cudaStream_t st) {
+  sub_kernel<T><<<grid_for(n), TPB, 0, st>>>(b, t, r, n);
+}
+template <typename T>
+void launch_cheb_init(const T* b, const T* t, const T* dinv, T* r, T* d, T* x, T inv_theta, bool x0_zero, long long n,
+                      cudaStream_t st) {
+  cheb_init_kernel<T><<<grid_for(n), TPB, 0, st>>>(b, t, dinv, r, d, x, inv_theta, x0_zero, n);
+}
+template <typename T>
+void launch_cheb_step(const T* t, const T* dinv, T* r, T* d, T* x, T cd, T cr, long long n, cudaStream_t st) {
+  cheb_step_kernel<T><<<grid_for(n), TPB, 0, st>>>(t, dinv, r, d, x, cd, cr, n);
+}
+void launch_lift(const double* u, double* du0, double factor, const double* fv, long long n_nodes, int dim,
+                 const Geom& g, cudaStream_t st) {
+  if (dim == 2) lift_kernel<2><<<grid_for(n_nodes), TPB, 0, st>>>(u, du0, factor, fv, n_nodes, g);
+  else lift_kernel<3><<<grid_for(n_nodes), TPB, 0, st>>>(u, du0, factor, fv, n_nodes, g);
+}
+template <typename T>
+void launch_dot(const T* a, const T* b, long long n, double* partials, double* out, cudaStream_t st) {
+  dot_partial_kernel<T><<<DOT_BLOCKS, TPB, 0, st>>>(a, b, n, partials);
+  dot_final_kernel<<<1, TPB, 0, st>>>(partials, out);
+}
+template <typename T>
+void launch_sweep(const T* in, T* out, int dim, const int Lin[3], const int Lout[3], int axis, const int* start,
+                  const T* w, int E, bool add, const Geom* mask_in, const Geom* mask_out, cudaStream_t st) {
+  long long n_out = (long long)Lout[0] * Lout[1] * (dim == 3 ? Lout[2] : 1) * dim;
+  Geom gi = mask_in ? *mask_in : Geom{};
+  Geom go = mask_out ? *mask_out : Geom{};
+  if (dim == 2)
+    sweep_kernel<T, 2><<<grid_for(n_out), TPB, 0, st>>>(in, out, Lin[0], Lin[1], Lout[0], Lout[1], Lout[2], axis,
+                                                        start, w, E, add, mask_in != nullptr, gi, mask_out != nullptr, go);
+  else
+    sweep_kernel<T, 3><<<grid_for(n_out), TPB, 0, st>>>(in, out, Lin[0], Lin[1], Lout[0], Lout[1], Lout[2], axis,
+                                                        start, w, E, add, mask_in != nullptr, gi, mask_out != nullptr, go);
+}
+
+#define HY_INST(T)                                                                                              \
+  template void launch_prep_out<T>(const T*, T*, long long, int, const Geom&, cudaStream_t);                    \
+  template void launch_zero_constrained<T>(T*, long long, int, const Geom&, cudaStream_t);                      \
+  template void launch_set_constrained_one<T>(T*, long long, int, const Geom&, cudaStream_t);                   \
+  template void launch_invert<T>(const double*, T*, long long, cudaStream_t);                                   \
+  template void launch_axpby<T>(T, const T*, T, T*, long long, cudaStream_t);                                   \
+  template void launch_xpay<T>(const T*, T, const T*, T*, long long, cudaStream_t);                             \
+  template void launch_sub<T>(const T*, const T*, T*, long long, cudaStream_t);                                 \
+  template void launch_mul<T>(const T*, const T*, T*, long long, cudaStream_t);                                 \
+  template void launch_splitmix<T>(T*, long long, unsigned long long, cudaStream_t);                            \
+  template void launch_cheb_init<T>(const T*, const T*, const T*, T*, T*, T*, T, bool, long long, cudaStream_t); \
+  template void launch_cheb_step<T>(const T*, const T*, T*, T*, T*, T, T, long long, cudaStream_t);             \
+  template void launch_dot<T>(const T*, const T*, long long, double*, double*, cudaStream_t);                   \
+  template void launch_sweep<T>(const T*, T*, int, const int*, const int*, int, const int*, const T*, int, bool, \
+                                const Geom*, const Geom*, cudaStream_t);
+HY_INST(double)
+HY_INST(float)
+#undef HY_INST
+template void launch_convert<double, float>(const double*, float*, long long, cudaStream_t);
+template void launch_convert<float, double>(const float*, double*, long long, cudaStream_t);
+
+}  // namespace hy

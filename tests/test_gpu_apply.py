@@ -1,0 +1,127 @@
+"""Parity of the cell kernels with the CPU oracle on the same seeded inputs.
+
+Tolerances (relative L2): tangent action 1e-12 in FP64 and 2e-6 in FP32; residual and diagonal 1e-12.
+Sizes span several thread blocks with a ragged last block (cells not a multiple of the cells per
+block) and degrees 1-4 in 2D and 3D.
+"""
+import numpy as np
+import pytest
+
+from paper_1904_13131_gb300 import inputs
+
+from .gpu_util import context, oracle_level, problem, rel, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = ["T4", "T2", "FC", "SC", "NC"]
+CASES = [(2, 1, 13), (2, 2, 7), (2, 3, 5), (2, 4, 4), (3, 1, 5), (3, 2, 3), (3, 3, 3), (3, 4, 2)]
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return require_gpu()
+
+
+@pytest.mark.parametrize("dim,k,m", CASES)
+def test_apply_all_variants_fp64_fp32(torch, dim, k, m):
+    pr = problem(dim, k, m)
+    P = oracle_level(pr)
+    u = inputs.smooth_field(dim, k, m, seed=dim * 10 + k)
+    x = inputs.gaussian_vector(P.n_dofs, seed=k)
+    y_ref = P.apply(u, x)
+    ud = torch.tensor(u, device="cuda")
+    xd = torch.tensor(x, device="cuda")
+    xf = xd.float()
+    with context(pr) as ctx:
+        for var in VARIANTS:
+            ctx.set_displacement(ud, var, level_dtype=1)  # builds the FP64 and the FP32 fine cache
+            y64 = ctx.apply_tangent(xd).cpu().numpy()
+            y32 = ctx.apply_tangent(xf, dtype=1).cpu().numpy()
+            assert rel(y64, y_ref) < 1e-12, (var, rel(y64, y_ref))
+            assert rel(y32, y_ref) < 2e-6, (var, rel(y32, y_ref))
+            # constrained rows are the identity
+            np.testing.assert_array_equal(y64[P.constrained], x[P.constrained])
+
+
+@pytest.mark.parametrize("dim,k,m", [(2, 2, 7), (3, 2, 3), (3, 3, 2), (2, 4, 3)])
+def test_residual_and_diagonal(torch, dim, k, m):
+    pr = problem(dim, k, m)
+    P = oracle_level(pr)
+    u = inputs.smooth_field(dim, k, m, seed=3)
+    ud = torch.tensor(u, device="cuda")
+    with context(pr) as ctx:
+        r = ctx.residual(ud).cpu().numpy()
+        ctx.set_displacement(ud, "T4")
+        d = ctx.diagonal().cpu().numpy()
+    assert rel(r, P.residual(u)) < 1e-12
+    assert rel(d, P.diagonal(u)) < 1e-12
+
+
+def test_zero_state_and_zero_vector(torch):
+    """u = 0 gives R = 0 exactly; x = 0 gives y = 0 exactly (degenerate inputs)."""
+    pr = problem(3, 2, 3)
+    with context(pr) as ctx:
+        n = ctx.num_dofs()
+        z = torch.zeros(n, dtype=torch.float64, device="cuda")
+        assert torch.count_nonzero(ctx.residual(z)).item() == 0
+        ctx.set_displacement(z, "NC")
+        assert torch.count_nonzero(ctx.apply_tangent(z)).item() == 0
+
+
+def test_single_cell_and_fully_constrained(torch):
+    dim, k, m = 3, 4, 1
+    pr = problem(dim, k, m)
+    pr["masks"] = [7] * 6  # every boundary dof constrained
+    P = oracle_level(pr)
+    u = inputs.smooth_field(dim, k, m, seed=1, amplitude=0.02)
+    x = inputs.gaussian_vector(P.n_dofs, 2)
+    with context(pr) as ctx:
+        ctx.set_displacement(torch.tensor(u, device="cuda"), "T4")
+        y = ctx.apply_tangent(torch.tensor(x, device="cuda")).cpu().numpy()
+    assert rel(y, P.apply(u, x)) < 1e-12
+
+
+def test_inverted_element_reports_jneg(torch):
+    """A displacement that folds a cell (J <= 0) is reported as HY_ERR_JNEG, device stays usable."""
+    from paper_1904_13131_gb300.api import HyError
+    pr = problem(2, 1, 4)
+    u = np.zeros(inputs.n_dofs(2, 1, 4))
+    u[1::2] = -2.0 * inputs.node_coords(2, 1, 4)[:, 1]  # y -> -y: J = -1 everywhere
+    with context(pr) as ctx:
+        with pytest.raises(HyError) as e:
+            ctx.residual(torch.tensor(u, device="cuda"))
+        assert e.value.status == "HY_ERR_JNEG"
+        with pytest.raises(HyError) as e:
+            ctx.set_displacement(torch.tensor(u, device="cuda"), "T4")
+        assert e.value.status == "HY_ERR_JNEG"
+        ok = ctx.residual(torch.zeros(ctx.num_dofs(), dtype=torch.float64, device="cuda"))
+        assert torch.count_nonzero(ok).item() == 0
+
+
+def test_argument_errors(torch):
+    from paper_1904_13131_gb300.api import Context, HyError
+    with Context(0) as ctx:
+        with pytest.raises(HyError) as e:
+            ctx.mesh_setup(3, 5, 4, 1, [1, 0, 0, 0, 0, 0])
+        assert e.value.status == "HY_ERR_UNSUPPORTED"
+        with pytest.raises(HyError) as e:
+            ctx.mesh_setup(3, 2, 6, 3, [1, 0, 0, 0, 0, 0])  # 6 -> 3 -> odd
+        assert e.value.status == "HY_ERR_ARG"
+        ctx.mesh_setup(2, 2, 4, 1, [0, 0, 3, 0])
+        with pytest.raises(HyError) as e:
+            ctx.set_displacement(torch.zeros(ctx.num_dofs(), dtype=torch.float64, device="cuda"))
+        assert e.value.status == "HY_ERR_STATE"  # material not set
+        with pytest.raises(HyError) as e:
+            ctx.set_material(0, np.full(16, 3, np.uint8), [1.0, 2.0], [1.0, 2.0])
+        assert e.value.status == "HY_ERR_ARG"
+
+
+def test_deterministic_dot(torch):
+    pr = problem(3, 2, 4)
+    with context(pr) as ctx:
+        n = ctx.num_dofs()
+        a = torch.tensor(inputs.gaussian_vector(n, 5), device="cuda")
+        b = torch.tensor(inputs.gaussian_vector(n, 6), device="cuda")
+        vals = {ctx.dot(a, b) for _ in range(5)}
+        assert len(vals) == 1
+        assert abs(vals.pop() - float(a.cpu().numpy() @ b.cpu().numpy())) < 1e-10 * n

@@ -1,0 +1,65 @@
+"""Newton solves on the GPU (GMG-preconditioned CG) against the oracle's Newton with direct solves.
+Tolerance: displacement relative L2 1e-8."""
+import numpy as np
+import pytest
+
+from oracle.newton import newton_solve
+from paper_1904_13131_gb300 import inputs
+
+from .gpu_util import context, oracle_level, problem, rel, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return require_gpu()
+
+
+def face_values(dim, top_disp):
+    fv = [[0.0] * 3 for _ in range(6)]
+    fv[2 * (dim - 1) + 1][dim - 1] = top_disp
+    return fv
+
+
+def oracle_bc(P, dim, k, m, top_disp):
+    X = inputs.node_coords(dim, k, m)
+    ubc = np.zeros((P.n_nodes, dim))
+    ubc[np.isclose(X[:, dim - 1], 1.0), dim - 1] = top_disp
+    return ubc.reshape(-1)
+
+
+@pytest.fixture(scope="module")
+def config1_reference():
+    dim, k, m = 2, 2, 16
+    pr = problem(dim, k, m, n_levels=3)
+    P = oracle_level(pr)
+    u_ref, rep = newton_solve(P, oracle_bc(P, dim, k, m, -0.1), load_steps=5)
+    return pr, u_ref, rep
+
+
+@pytest.mark.parametrize("variant,level_dtype", [("T4", 0), ("NC", 0), ("FC", 1), ("T4", 1)])
+def test_config1_newton_matches_oracle(torch, config1_reference, variant, level_dtype):
+    """2D 16x16 Q2 inclusion, top displaced by -0.1 in 5 load steps, GMG with 3 levels."""
+    pr, u_ref, rep_ref = config1_reference
+    from paper_1904_13131_gb300.api import Context
+    with context(pr) as ctx:
+        u = torch.zeros(ctx.num_dofs(), dtype=torch.float64, device="cuda")
+        params = Context.newton_params(variant=variant, level_dtype=level_dtype, face_values=face_values(2, -0.1))
+        rep = ctx.newton_solve(u, params)
+    assert rep["load_steps_done"] == 5
+    assert rel(u.cpu().numpy(), u_ref) < 1e-8
+    assert max(rep["newton_iterations"]) <= max(rep_ref["iterations"]) + 2
+
+
+def test_3d_newton_matches_oracle(torch):
+    dim, k, m = 3, 2, 4
+    pr = problem(dim, k, m, n_levels=2)
+    P = oracle_level(pr)
+    u_ref, _ = newton_solve(P, oracle_bc(P, dim, k, m, -0.1), load_steps=2)
+    from paper_1904_13131_gb300.api import Context
+    with context(pr) as ctx:
+        u = torch.zeros(ctx.num_dofs(), dtype=torch.float64, device="cuda")
+        rep = ctx.newton_solve(u, Context.newton_params(load_steps=2, face_values=face_values(3, -0.1)))
+    assert rep["load_steps_done"] == 2
+    assert rel(u.cpu().numpy(), u_ref) < 1e-8

@@ -1,0 +1,45 @@
+"""CPU-side checks of the C ABI: the library builds, loads and exports every declared symbol;
+argument errors are reported without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1904_13131_gb300 import api, build
+    build.build()
+    return api.load_library()
+
+
+def test_header_symbols_exported(lib):
+    from paper_1904_13131_gb300 import api
+    header = open(os.path.join(ROOT, "include", "hyperelastic.h")).read()
+    declared = set(re.findall(r"\b(hy_[a-z_0-9]+)\s*\(", header))
+    assert declared == set(api.EXPORTED), declared ^ set(api.EXPORTED)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_status_strings_and_null_args(lib):
+    assert lib.hy_status_str(0) == b"HY_OK"
+    assert lib.hy_status_str(5) == b"HY_ERR_JNEG"
+    assert lib.hy_last_error(None) == b"null context"
+    # a null output pointer is an argument error, decided before any CUDA call
+    assert lib.hy_create(None, 0, None) == 1
+    assert lib.hy_num_dofs(None, 0, None) == 1
+    assert lib.hy_apply_tangent(None, None, None, 0) == 1
+    lib.hy_destroy(None)
+
+
+def test_no_oracle_in_product_package():
+    pkg = os.path.join(ROOT, "paper_1904_13131_gb300")
+    for dp, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".inc")):
+                src = open(os.path.join(dp, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle", src, re.M), f

@@ -68,6 +68,14 @@ def bytes_per_apply(var, dtype_bytes, nqp, ndofs, dim=3):
     return nvals * nqp * dtype_bytes + vec
 
 
+# DRAM bytes (read + write) per launch from one ncu capture of the 32^3 Q2 workload (profiles/*_ncu.md);
+# a kernel that changed since its capture maps to None.
+NCU_TRAFFIC = {
+    ("NC", "double"): 19_649_024,   # profiles/apply_nc_f64_32cube_q2_ncu.md
+    ("T4", "float"): 137_947_648,   # profiles/apply_t4_f32_32cube_q2_ncu.md
+}
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     hbm, src = 6800.0, "fallback"
@@ -167,37 +175,28 @@ def time_applies(torch, ctxs, variants, x, dtype, steps, warmup, flush, stream):
     return np.array([[a.elapsed_time(b) for a, b in row] for row in ev]), ys, launches
 
 
-def solve_latency(torch, api, inputs, dev, reps=5):
-    """GMG-PCG solves of A(u) du = b on the 32^3 Q2 problem with 4 levels (coarsest 4^3), rtol 1e-8, with the
-    boundary conditions of the Newton solves (bottom clamped, top normal component prescribed): with the top
-    free, the tangent at this non-equilibrium state is indefinite on the coarsest level."""
+def solve_latency(torch, api, inputs, dev):
+    """GMG-preconditioned CG inside Newton: the 32^3 Q2 inclusion cube under 10% compression (bottom clamped,
+    top normal displacement -0.1) in 5 load steps, 4 levels (32 -> 4, FP64 Chebyshev coarse solve on 4^3),
+    CG rtol 1e-8; FP64 V-cycle and mixed precision (FP32 V-cycle). Latency of every linear solve."""
     pr = inputs.problem(DIM, K, M, n_levels=4, top=inputs.normal_top_mask(DIM))
-    u = torch.tensor(inputs.smooth_field(DIM, K, M, seed=0), device=dev)
-    b = torch.tensor(inputs.gaussian_vector(inputs.n_dofs(DIM, K, M), seed=2), device=dev)
-    out = {}
+    fv = [[0.0] * 3 for _ in range(6)]
+    fv[5][2] = -0.1
+    out, sols = {}, {}
     with api.Context(dev.index) as c:
         c.setup_problem(pr)
-        cons = torch.tensor(inputs.constrained_mask(DIM, K, M, pr["masks"]), device=dev)
-        b[cons] = 0.0
         for name, ldt in (("fp64", 0), ("mixed", 1)):
-            t0 = time.perf_counter()
-            c.set_displacement(u, "T4", level_dtype=ldt)
-            torch.cuda.synchronize()
-            setup_ms = (time.perf_counter() - t0) * 1e3
-            lat, its = [], []
-            x, it = c.pcg(b, rtol=1e-8, max_iter=500)  # warm-up
-            for _ in range(reps):
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                x, it = c.pcg(b, x, rtol=1e-8, max_iter=500)
-                torch.cuda.synchronize()
-                lat.append((time.perf_counter() - t0) * 1e3)
-                its.append(it)
-            info = c.level_info(0)
-            out[name] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                         "cg_iterations": int(np.median(its)), "setup_ms": setup_ms, "levels": 4,
-                         "coarse_degree": info["coarse_degree"], "coarse_interval": [info["coarse_lo"], info["coarse_hi"]],
-                         "rtol": 1e-8, "reps": reps}
+            u = torch.zeros(inputs.n_dofs(DIM, K, M), dtype=torch.float64, device=dev)
+            rep = c.newton_solve(u, api.Context.newton_params(level_dtype=ldt, face_values=fv))
+            lat = np.array(rep["solve_ms"])
+            out[name] = {"solve_p50_ms": float(np.percentile(lat, 50)), "solve_p99_ms": float(np.percentile(lat, 99)),
+                         "solves": rep["n_solves"], "cg_iterations_median": int(np.median(rep["solve_cg_iterations"])),
+                         "cg_iterations_max": rep["cg_iterations_max"], "newton_iterations": rep["newton_iterations"],
+                         "newton_total_ms": rep["total_ms"], "setup_ms_total": rep["setup_ms_total"],
+                         "coarse_degree": c.level_info(0)["coarse_degree"]}
+            sols[name] = u.cpu().numpy()
+    out["mixed_vs_fp64_rel_l2"] = float(np.linalg.norm(sols["mixed"] - sols["fp64"]) / np.linalg.norm(sols["fp64"]))
+    out["workload"] = "32^3 Q2 (823,875 dofs), 10% compression in 5 load steps, 4 levels, CG rtol 1e-8, T4"
     return out
 
 
@@ -250,6 +249,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--only", default=None, help="profile mode: VARIANT:f64|f32, a few applications of one kernel")
+    ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -269,6 +270,22 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     stream = torch.cuda.current_stream(dev)
+    if args.only:
+        var, dt = args.only.split(":")
+        pr = inputs.problem(DIM, K, M, n_levels=1, top=0)
+        u = torch.tensor(inputs.smooth_field(DIM, K, M, seed=0), device=dev)
+        x = torch.tensor(inputs.gaussian_vector(inputs.n_dofs(DIM, K, M), seed=1), device=dev)
+        with api.Context(dev.index) as c:
+            c.setup_problem(pr)
+            c.set_solver_params(coarse_eig_iters=5)
+            c.set_displacement(u, var, level_dtype=1 if dt == "f32" else 0)
+            xin = x.float() if dt == "f32" else x
+            y = torch.empty_like(xin)
+            for _ in range(args.reps):
+                c.apply_tangent(xin, y, dtype=1 if dt == "f32" else 0)
+            torch.cuda.synchronize()
+        print(json.dumps({"only": args.only, "reps": args.reps}))
+        return
     pr, u, x, ctxs = setup_contexts(torch, api, inputs, dev)
     n = inputs.n_dofs(DIM, K, M)
     ncells = M**DIM
@@ -314,7 +331,8 @@ def main():
     dom = max(per_var_ms, key=per_var_ms.get)
     ach = flops_per_qp(dom) * nqp / (per_var_ms[dom] * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": f"apply_kernel<3,3,{dom},double>", "achieved": ach, "peak": fp64_peak,
-                "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": NCU_TRAFFIC.get((dom, "double")),
+                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                 "peak_source": "FP64 pipe: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (derived, nominal 1.25 TFLOP/s)",
                 "algorithmic_flops_per_launch": flops_per_qp(dom) * nqp}
 

@@ -163,6 +163,11 @@ typedef struct {
   int cg_iterations_max;
   double final_residual;      /* ||R_free|| at the end */
   int backtracks;             /* J <= 0 halvings taken */
+  int n_solves;               /* linear (PCG) solves performed; the first 256 are recorded below */
+  int solve_cg_iterations[256];
+  double solve_ms[256];       /* host wall time of each PCG solve (stream synchronised) */
+  double setup_ms_total;      /* time spent linearising (caches, diagonals, eigenvalue estimates) */
+  double total_ms;            /* whole call */
 } hy_newton_report;
 
 void hy_newton_default_params(hy_newton_params *p);

@@ -49,7 +49,9 @@ class NewtonParams(ctypes.Structure):
 class NewtonReport(ctypes.Structure):
     _fields_ = [("load_steps_done", ctypes.c_int), ("newton_iterations", ctypes.c_int * 64),
                 ("cg_iterations_total", ctypes.c_int), ("cg_iterations_max", ctypes.c_int),
-                ("final_residual", ctypes.c_double), ("backtracks", ctypes.c_int)]
+                ("final_residual", ctypes.c_double), ("backtracks", ctypes.c_int), ("n_solves", ctypes.c_int),
+                ("solve_cg_iterations", ctypes.c_int * 256), ("solve_ms", ctypes.c_double * 256),
+                ("setup_ms_total", ctypes.c_double), ("total_ms", ctypes.c_double)]
 
 
 _lib = None
@@ -291,7 +293,10 @@ class Context:
         report = {"load_steps_done": rep.load_steps_done,
                   "newton_iterations": list(rep.newton_iterations[: max(rep.load_steps_done, params.load_steps)]),
                   "cg_iterations_total": rep.cg_iterations_total, "cg_iterations_max": rep.cg_iterations_max,
-                  "final_residual": rep.final_residual, "backtracks": rep.backtracks}
+                  "final_residual": rep.final_residual, "backtracks": rep.backtracks,
+                  "n_solves": rep.n_solves, "solve_cg_iterations": list(rep.solve_cg_iterations[: min(rep.n_solves, 256)]),
+                  "solve_ms": list(rep.solve_ms[: min(rep.n_solves, 256)]), "setup_ms_total": rep.setup_ms_total,
+                  "total_ms": rep.total_ms}
         self._ck(st)
         return report
 

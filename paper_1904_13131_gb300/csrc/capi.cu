@@ -2,6 +2,7 @@
 // tangent action, residual, geometric multigrid (Secs. 6-7), PCG and Newton (Secs. 3, 7).
 // Host code orchestrates; every step on vectors runs in the kernels of this library.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -1164,6 +1165,9 @@ hy_status hy_newton_solve(hy_ctx* ctx, const hy_newton_params* p, double* u, hy_
   double *R = ctx->f64[4], *du0 = ctx->f64[5], *rhs = ctx->f64[6], *du = ctx->f64[7], *trial = ctx->f64[8],
          *t = ctx->f64[9];
   HY_CK(cudaMemcpyAsync(ctx->d_face, p->face_values, sizeof(double) * 18, cudaMemcpyHostToDevice, ctx->stream));
+  using clk = std::chrono::steady_clock;
+  auto ms_since = [](clk::time_point t0) { return std::chrono::duration<double, std::milli>(clk::now() - t0).count(); };
+  const clk::time_point t_start = clk::now();
   hy_status st = HY_OK;
   for (int s = 1; s <= p->load_steps && st == HY_OK; ++s) {
     const double factor = (double)s / p->load_steps;
@@ -1188,7 +1192,10 @@ hy_status hy_newton_solve(hy_ctx* ctx, const hy_newton_params* p, double* u, hy_
         st = fail(ctx, HY_ERR_NOCONV, "newton: iteration cap in load step " + std::to_string(s));
         break;
       }
+      const clk::time_point t_setup = clk::now();
       if ((st = set_displacement(ctx, u, (int)p->variant, p->level_dtype == HY_F32)) != HY_OK) break;
+      HY_CK(cudaStreamSynchronize(ctx->stream));
+      rl.setup_ms_total += ms_since(t_setup);
       // rhs = -R - Z A du0 (lifting of the prescribed increment into the first solve)
       HY_CK(cudaMemcpyAsync(rhs, R, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
       if (lift2 > 0.0) {
@@ -1204,7 +1211,16 @@ hy_status hy_newton_solve(hy_ctx* ctx, const hy_newton_params* p, double* u, hy_
       rl.final_residual = std::sqrt(rr);
       if (ctx->verbose) std::fprintf(stderr, "[hy] step %d it %d |rhs| %.3e lift2 %.3e\n", s, its, std::sqrt(rr), lift2);
       int cg_its = 0;
-      if ((st = pcg(ctx, rhs, du, p->cg_rtol, p->cg_max_iter, &cg_its)) != HY_OK) break;
+      HY_CK(cudaStreamSynchronize(ctx->stream));
+      const clk::time_point t_solve = clk::now();
+      st = pcg(ctx, rhs, du, p->cg_rtol, p->cg_max_iter, &cg_its);
+      HY_CK(cudaStreamSynchronize(ctx->stream));
+      if (rl.n_solves < 256) {
+        rl.solve_ms[rl.n_solves] = ms_since(t_solve);
+        rl.solve_cg_iterations[rl.n_solves] = cg_its;
+      }
+      rl.n_solves++;
+      if (st != HY_OK) break;
       rl.cg_iterations_total += cg_its;
       if (ctx->verbose) std::fprintf(stderr, "[hy] step %d it %d cg %d\n", s, its, cg_its);
       rl.cg_iterations_max = std::max(rl.cg_iterations_max, cg_its);
@@ -1231,6 +1247,7 @@ hy_status hy_newton_solve(hy_ctx* ctx, const hy_newton_params* p, double* u, hy_
     if (st == HY_OK) rl.load_steps_done = s;
   }
   HY_CK(cudaStreamSynchronize(ctx->stream));
+  rl.total_ms = ms_since(t_start);
   if (rep) *rep = rl;
   return st;
 }

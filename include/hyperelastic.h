@@ -180,6 +180,21 @@ hy_status hy_newton_solve(hy_ctx *ctx, const hy_newton_params *p, double *u_inou
  * repeated calls give identical bits). Uses a scratch buffer owned by the context. */
 hy_status hy_dot(hy_ctx *ctx, const double *a_dev, const double *b_dev, int64_t n, double *result);
 
+/* Allocation-free dot product, for callers that must not allocate device memory while they run
+ * (for example code that works inside a device-memory budget another framework has fully claimed,
+ * or a real-time loop in which a cudaMalloc/cudaFree could stall on a device synchronisation). The
+ * paper has no counterpart: it is a service of this library, not a step of the method. It needs no
+ * context: it runs on `device` and enqueues on `cuda_stream` (NULL = legacy default stream), writes
+ * a . b for the FP64 device vectors a_dev, b_dev of n elements to the HOST double *result and
+ * synchronises the stream before returning. Its scratch is a fixed array inside the library (about
+ * 128 KiB per device, held until the process exits); n > HY_DOT_NOALLOC_MAX_N returns HY_ERR_ARG.
+ * The first call on each device looks up that array's device address, so make it before any stream
+ * capture. All calls share the array: calls that overlap on the GPU (different streams without
+ * ordering) race; serialise them. The summation order is fixed, so repeated calls agree bitwise. */
+#define HY_DOT_NOALLOC_MAX_N (16384LL * 4096LL) /* 67,108,864 elements */
+hy_status hy_dot_noalloc(int device, void *cuda_stream, const double *a_dev, const double *b_dev, int64_t n,
+                         double *result);
+
 /* Number of kernels this context has launched since creation (for accounting). */
 hy_status hy_kernel_launches(const hy_ctx *ctx, int64_t *count);
 

@@ -24,7 +24,7 @@ EXPORTED = ("hy_create", "hy_destroy", "hy_status_str", "hy_last_error", "hy_mes
             "hy_set_material", "hy_set_displacement", "hy_apply_tangent", "hy_vmult", "hy_residual", "hy_diagonal",
             "hy_gmg_vcycle", "hy_set_solver_params", "hy_get_solver_params", "hy_level_info", "hy_set_level_info",
             "hy_level_displacement", "hy_prolongate_add", "hy_restrict", "hy_pcg", "hy_newton_default_params",
-            "hy_newton_solve", "hy_dot", "hy_kernel_launches")
+            "hy_newton_solve", "hy_dot", "hy_dot_noalloc", "hy_kernel_launches")
 
 
 class HyError(RuntimeError):
@@ -93,6 +93,7 @@ def load_library(path: str = LIB_PATH):
         "hy_newton_solve": [vp, ctypes.POINTER(NewtonParams), vp, ctypes.POINTER(NewtonReport)],
         "hy_dot": [vp, vp, vp, i64, ctypes.POINTER(dbl)],
         "hy_kernel_launches": [vp, ctypes.POINTER(i64)],
+        "hy_dot_noalloc": [i32, vp, vp, vp, i64, ctypes.POINTER(dbl)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -310,3 +311,19 @@ class Context:
         c = ctypes.c_int64()
         self._ck(self.lib.hy_kernel_launches(self.h, ctypes.byref(c)))
         return c.value
+
+
+DOT_NOALLOC_MAX_N = 16384 * 4096
+
+
+def dot_noalloc(a, b, device: int = 0, stream=None) -> float:
+    """a . b through hy_dot_noalloc: no context and no device allocation (see include/hyperelastic.h)."""
+    import torch
+    lib = load_library()
+    if stream is None:
+        stream = torch.cuda.current_stream(torch.device("cuda", device))
+    out = ctypes.c_double()
+    st = lib.hy_dot_noalloc(device, ctypes.c_void_p(stream.cuda_stream), _ptr(a), _ptr(b), a.numel(), ctypes.byref(out))
+    if st != 0:
+        raise HyError(st, "hy_dot_noalloc failed")
+    return out.value

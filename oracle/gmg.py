@@ -170,9 +170,10 @@ class Hierarchy:
             it = nfree if self.coarse_eig_iters is None else min(nfree, self.coarse_eig_iters)
             ritz = self.estimate(0, it)
             self.coarse_lo, self.coarse_hi = ritz.min(), self.smooth_hi * ritz.max()
-            if not self.coarse_lo > 0:
-                raise ValueError("coarsest-level tangent is not positive definite")
-        self.coarse_deg = coarse_degree(self.coarse_lo, self.coarse_hi, self.coarse_reduction)
+        # an indefinite coarsest level (tangent about an unstable state) cannot be solved by Chebyshev;
+        # the V-cycle refuses it
+        self.coarse_spd = self.coarse_lo > 0
+        self.coarse_deg = coarse_degree(self.coarse_lo, self.coarse_hi, self.coarse_reduction) if self.coarse_spd else 0
 
     def start_vector(self, l):
         v = splitmix64_uniform(l, self.levels[l].n_dofs)
@@ -193,6 +194,8 @@ class Hierarchy:
         """One V-cycle on level l (default finest) for right-hand side b, zero initial guess."""
         if l is None:
             l = len(self.levels) - 1
+            if not self.coarse_spd:
+                raise ValueError("coarsest-level tangent is not positive definite")
         if l == 0:
             return chebyshev(self.A[0], self.Dinv[0], b, None, self.coarse_deg, self.coarse_lo, self.coarse_hi)
         x = self.smooth(l, b, None)

@@ -187,6 +187,7 @@ struct hy_ctx {
   bool state_ok = false;
   double coarse_lo = 0, coarse_hi = 0;
   int coarse_deg = 0;
+  bool coarse_spd = false;
   unsigned* d_err = nullptr;
   unsigned long long* d_jmin = nullptr;
   double* d_partials = nullptr;
@@ -198,6 +199,13 @@ struct hy_ctx {
   double* f64[10] = {};  // fine-level FP64 work vectors of PCG / Newton
   long long launches = 0;
   bool verbose = false;  // HY_VERBOSE=1: per-iteration diagnostics on stderr
+  // The V-cycle below the finest level's input/output copies is captured once per linearisation into a
+  // CUDA graph and replayed (HY_GRAPHS=0 disables this and launches kernel by kernel).
+  bool use_graphs = true;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t vc_exec = nullptr;
+  bool vc_valid = false;
+  long long vc_nodes = 0;
   std::vector<void*> allocs;
 };
 
@@ -249,7 +257,14 @@ hy_status check_launch(hy_ctx* ctx, int nlaunch) {
   return HY_OK;
 }
 
+void drop_graph(hy_ctx* ctx) {
+  if (ctx->vc_exec) cudaGraphExecDestroy(ctx->vc_exec);
+  ctx->vc_exec = nullptr;
+  ctx->vc_valid = false;
+}
+
 void free_mesh(hy_ctx* ctx) {
+  drop_graph(ctx);
   for (void* p : ctx->allocs) cudaFree(p);
   ctx->allocs.clear();
   ctx->lev.clear();
@@ -477,19 +492,61 @@ hy_status vcycle_level(hy_ctx* ctx, int l) {
   return level_f32(ctx, l) ? vcycle_typed<float>(ctx, l) : vcycle_typed<double>(ctx, l);
 }
 
+// The V-cycle from the finest level's b to its x, replayed from a CUDA graph captured on a private
+// stream the first time after each change of linearisation (the graph holds the Chebyshev
+// coefficients and eigenvalue bounds as kernel arguments, so it is re-captured when they change).
+hy_status vcycle_body(hy_ctx* ctx) {
+  const int top = ctx->nlev - 1;
+  if (!ctx->use_graphs) return vcycle_level(ctx, top);
+  if (!ctx->vc_valid) {
+    if (!ctx->cap_stream) HY_CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t saved = ctx->stream;
+    const long long l0 = ctx->launches;
+    ctx->stream = ctx->cap_stream;
+    cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      ctx->stream = saved;
+      return fail(ctx, HY_ERR_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+    }
+    const hy_status st = vcycle_level(ctx, top);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(ctx->cap_stream, &g);
+    ctx->stream = saved;
+    ctx->vc_nodes = ctx->launches - l0;
+    ctx->launches = l0;
+    if (st != HY_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      if (st != HY_OK) return st;
+      return fail(ctx, HY_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+    }
+    drop_graph(ctx);
+    e = cudaGraphInstantiate(&ctx->vc_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(ctx, HY_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    ctx->vc_valid = true;
+  }
+  HY_CK(cudaGraphLaunch(ctx->vc_exec, ctx->stream));
+  ctx->launches += ctx->vc_nodes;
+  return HY_OK;
+}
+
 // z = V r on the finest level (FP64 in/out).
 hy_status vcycle_top(hy_ctx* ctx, const double* r, double* z) {
+  if (!ctx->coarse_spd)
+    return fail(ctx, HY_ERR_NOCONV,
+                "coarsest-level tangent is not positive definite (smallest Ritz value " + std::to_string(ctx->coarse_lo) +
+                    "); the Chebyshev coarse solver needs an SPD operator");
   const int top = ctx->nlev - 1;
   Level& L = ctx->lev[top];
   if (level_f32(ctx, top)) {
     launch_convert<double, float>(r, L.w32[0], L.ndofs, ctx->stream);
     HY_TRY(check_launch(ctx, 1));
-    HY_TRY(vcycle_level(ctx, top));
+    HY_TRY(vcycle_body(ctx));
     launch_convert<float, double>(L.w32[1], z, L.ndofs, ctx->stream);
     return check_launch(ctx, 1);
   }
   HY_CK(cudaMemcpyAsync(L.w64[0], r, sizeof(double) * L.ndofs, cudaMemcpyDeviceToDevice, ctx->stream));
-  HY_TRY(vcycle_level(ctx, top));
+  HY_TRY(vcycle_body(ctx));
   HY_CK(cudaMemcpyAsync(z, L.w64[1], sizeof(double) * L.ndofs, cudaMemcpyDeviceToDevice, ctx->stream));
   return HY_OK;
 }
@@ -557,7 +614,8 @@ hy_status ensure_level_vectors(hy_ctx* ctx, int l, bool f32) {
 template <typename TOUT>
 hy_status build_cache(hy_ctx* ctx, int l, int var) {
   Level& L = ctx->lev[l];
-  const size_t len = (size_t)cache_values(var, ctx->dim) * L.nqp;
+  const size_t nblocks = (size_t)((L.g.ncells + cells_per_block(ctx->dim, ctx->n) - 1) / cells_per_block(ctx->dim, ctx->n));
+  const size_t len = std::max<size_t>(1, (size_t)cache_values(var, ctx->dim) * cache_row(ctx->dim, ctx->n) * nblocks);
   TOUT*& buf = *reinterpret_cast<TOUT**>(sizeof(TOUT) == 8 ? (void*)&L.d_c64 : (void*)&L.d_c32);
   size_t& cur = sizeof(TOUT) == 8 ? L.c64_len : L.c32_len;
   if (cur < len) {
@@ -582,6 +640,7 @@ hy_status check_error_word(hy_ctx* ctx, const char* where) {
   HY_CK(cudaStreamSynchronize(ctx->stream));
   if (h) {
     HY_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
+    if (h & ERRBIT_TIMEOUT) return fail(ctx, HY_ERR_TIMEOUT, std::string(where) + ": a bounded device wait gave up");
     return fail(ctx, HY_ERR_JNEG, std::string(where) + ((h & ERRBIT_NAN) ? ": NaN in J" : ": J <= 0 at a Gauss point"));
   }
   return HY_OK;
@@ -593,6 +652,7 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
     if (!ctx->lev[l].mat_set) return fail(ctx, HY_ERR_STATE, "material not set on level " + std::to_string(l));
   if (var < 0 || var > 4) return fail(ctx, HY_ERR_ARG, "variant out of range");
   ctx->state_ok = false;
+  drop_graph(ctx);
   ctx->var = var;
   ctx->mixed = mixed;
   const int top = ctx->nlev - 1;
@@ -671,12 +731,12 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
     HY_TRY(eig_estimate<double>(ctx, 0, it, lmin, lmax));
     ctx->coarse_lo = lmin;
     ctx->coarse_hi = ctx->sp.cheb_hi * lmax;
-    if (!(lmin > 0.0))
-      return fail(ctx, HY_ERR_NOCONV,
-                  "coarsest-level tangent is not positive definite (smallest Ritz value " + std::to_string(lmin) +
-                      "); the Chebyshev coarse solver needs an SPD operator");
   }
-  {
+  // The Chebyshev coarse solver needs an SPD coarsest level; an indefinite one (a tangent about an
+  // unstable state) is reported when the V-cycle is used, not here, so that applications still work.
+  ctx->coarse_spd = ctx->coarse_lo > 0.0;
+  ctx->coarse_deg = 0;
+  if (ctx->coarse_spd) {
     const double sig = (ctx->coarse_hi + ctx->coarse_lo) / (ctx->coarse_hi - ctx->coarse_lo);
     ctx->coarse_deg = std::max(1, (int)std::ceil(std::acosh(1.0 / ctx->sp.coarse_reduction) / std::acosh(sig) - 1e-12));
   }
@@ -787,6 +847,8 @@ hy_status hy_create(hy_ctx** out, int device, void* stream) {
   ctx->stream = (cudaStream_t)stream;
   const char* v = std::getenv("HY_VERBOSE");
   ctx->verbose = v && v[0] == '1';
+  const char* gr = std::getenv("HY_GRAPHS");
+  ctx->use_graphs = !(gr && gr[0] == '0');
   *out = ctx;
   return HY_OK;
 }
@@ -797,6 +859,7 @@ void hy_destroy(hy_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
   free_mesh(ctx);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
 }
 
@@ -861,6 +924,7 @@ hy_status hy_mesh_setup(hy_ctx* ctx, int dim, int degree, int m, int n_levels, c
     for (int i = 0; i < dim; ++i) L.g.ncells *= ml;
     for (int f = 0; f < 6; ++f) L.g.fm[f] = ctx->fm[f];
     L.g.h = 1.0 / ml;
+    L.g.inv_h = (double)ml;
     L.nnodes = 1;
     for (int i = 0; i < dim; ++i) L.nnodes *= L.g.L;
     L.ndofs = L.nnodes * dim;
@@ -1065,6 +1129,7 @@ hy_status hy_set_solver_params(hy_ctx* ctx, const hy_solver_params* p) {
     return fail(ctx, HY_ERR_ARG, "solver parameters out of range");
   ctx->sp = *p;
   ctx->state_ok = false;
+  drop_graph(ctx);
   return HY_OK;
 }
 
@@ -1087,12 +1152,14 @@ hy_status hy_level_info(const hy_ctx* ctx, int level, double* lmax, double* clo,
 
 hy_status hy_set_level_info(hy_ctx* ctx, int level, double lmax, double clo, double chi) {
   if (!ctx) return HY_ERR_ARG;
+  drop_graph(ctx);
   const int l = lev_index(ctx, level);
   if (l < 0 || l >= ctx->nlev) return fail(ctx, HY_ERR_ARG, "level out of range");
   if (l == 0) {
     if (!(chi > clo && clo > 0)) return fail(ctx, HY_ERR_ARG, "bad coarse interval");
     ctx->coarse_lo = clo;
     ctx->coarse_hi = chi;
+    ctx->coarse_spd = true;
     const double sig = (chi + clo) / (chi - clo);
     ctx->coarse_deg = std::max(1, (int)std::ceil(std::acosh(1.0 / ctx->sp.coarse_reduction) / std::acosh(sig) - 1e-12));
   } else {

@@ -23,7 +23,7 @@ struct CellArgs {
   T* y;                   // apply / residual / diag: destination, accumulated with atomics
   const T* ubar;          // level displacement in T (variants that recompute F)
   const double* u64;      // level displacement in FP64 (state build, residual, diagonal)
-  const T* cache;         // per-Gauss-point cache, structure of arrays [value][cell * NPT + q]
+  const T* cache;         // per-Gauss-point cache in the blocked layout of cache_row()
   T* cache_out;           // state build output
   const uint8_t* mat;     // material id per cell
   unsigned* err;          // device error word (J <= 0, NaN)
@@ -31,8 +31,46 @@ struct CellArgs {
   Mat<T> mt;
   Geom g;
   Basis1D<T> b;
-  long long nqp;          // ncells * NPT, stride of the cache arrays
+  long long nqp;          // ncells * NPT
 };
+
+// --- asynchronous bulk copy (TMA engine) of a block's cache chunk into shared memory ------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// One thread: announce `bytes` of transactions on the barrier and copy them global -> shared in pieces.
+// dst, src and bytes are multiples of 16 bytes.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  constexpr unsigned PIECE = 32768;
+  for (unsigned off = 0; off < bytes; off += PIECE) {
+    const unsigned sz = bytes - off < PIECE ? bytes - off : PIECE;
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(static_cast<char*>(dst) + off)),
+        "l"(static_cast<const char*>(src) + off), "r"(sz), "r"(smem_u32(bar))
+        : "memory");
+  }
+}
+// Wait for phase `parity` of the barrier with a bounded number of polls; false if it never completed.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  const unsigned a = smem_u32(bar);
+  for (unsigned it = 0; it < MBAR_POLL_LIMIT; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
 
 // --- small helpers ------------------------------------------------------------------------------
 template <int N, int STRIDE, bool TR, typename T>
@@ -42,6 +80,14 @@ __device__ __forceinline__ T contract(const T* __restrict__ line, int pax, const
 #pragma unroll
   for (int j = 1; j < N; ++j) s = fma(TR ? M[j][pax] : M[pax][j], line[j * STRIDE], s);
   return s;
+}
+
+// Continues an accumulation: acc + sum_j M[r][j] line[j] (TR: M[j][r]).
+template <int N, int STRIDE, bool TR, typename T>
+__device__ __forceinline__ T contract_acc(const T* __restrict__ line, int pax, const T (*M)[MAXN], T acc) {
+#pragma unroll
+  for (int j = 0; j < N; ++j) acc = fma(TR ? M[j][pax] : M[pax][j], line[j * STRIDE], acc);
+  return acc;
 }
 
 template <int DIM, int N>
@@ -106,8 +152,8 @@ __device__ __forceinline__ T* integrate_backward(const T* bp, T* b0, T* b1, cons
     const T* P0 = bp + (c * DIM + 0) * NPT;
     const T* P1 = bp + (c * DIM + 1) * NPT;
     T s = contract<N, 1, true>(P0 + pt.base(0), pt.pc[0], D);
-    s += contract<N, N, true>(P1 + pt.base(1), pt.pc[1], D);
-    if (DIM == 3) s += contract<N, N * N, true>(bp + (c * DIM + DIM - 1) * NPT + pt.base(2), pt.pc[2], D);
+    s = contract_acc<N, N, true>(P1 + pt.base(1), pt.pc[1], D, s);
+    if (DIM == 3) s = contract_acc<N, N * N, true>(bp + (c * DIM + DIM - 1) * NPT + pt.base(2), pt.pc[2], D, s);
     b0[c * NPT + pt.p] = s;
   }
   __syncthreads();
@@ -233,6 +279,51 @@ __device__ __forceinline__ T neo_hooke_state(const T F[DIM][DIM], T mu, T lam, T
   return J;
 }
 
+// Neo-Hooke state for the variants that recompute it in every application, scaled so that no
+// F^{-1} is formed: with adj = J F^{-1}, rho = 1/J and kappa = (W/h) rho^2, the flux contracted with
+// the unit-cell shape gradients is P~ = Q' adj^T, Q' = g' tau' + c1' sym(g') + c2' tr(g') I, where
+// g' = Grad x adj, tau' = kappa tau, c1' = 2 kappa (mu - 2 lambda ln J), c2' = 2 kappa lambda -- the same
+// quantity as W/h (g tau + JC : sym g) F^{-T} with g = Grad x F^{-1}.
+template <int DIM, typename T>
+__device__ __forceinline__ void neo_hooke_adj(const T F[DIM][DIM], T mu, T lam, T Wh, bool have_c, T c_in,
+                                              T adj[DIM][DIM], T tau[nsym(DIM)], T& c1, T& c2) {
+  T J;
+  if (DIM == 3) {
+    adj[0][0] = F[1][1] * F[2][2] - F[1][2] * F[2][1];
+    adj[0][1] = F[0][2] * F[2][1] - F[0][1] * F[2][2];
+    adj[0][2] = F[0][1] * F[1][2] - F[0][2] * F[1][1];
+    adj[1][0] = F[1][2] * F[2][0] - F[1][0] * F[2][2];
+    adj[1][1] = F[0][0] * F[2][2] - F[0][2] * F[2][0];
+    adj[1][2] = F[0][2] * F[1][0] - F[0][0] * F[1][2];
+    adj[2][0] = F[1][0] * F[2][1] - F[1][1] * F[2][0];
+    adj[2][1] = F[0][1] * F[2][0] - F[0][0] * F[2][1];
+    adj[2][2] = F[0][0] * F[1][1] - F[0][1] * F[1][0];
+    J = F[0][0] * adj[0][0] + F[0][1] * adj[1][0] + F[0][2] * adj[2][0];
+  } else {
+    adj[0][0] = F[1][1];
+    adj[0][1] = -F[0][1];
+    adj[1][0] = -F[1][0];
+    adj[1][1] = F[0][0];
+    J = F[0][0] * F[1][1] - F[0][1] * F[1][0];
+  }
+  T rho;
+  if constexpr (sizeof(T) == 8) rho = __drcp_rn(J);
+  else rho = __frcp_rn(J);
+  const T kappa = Wh * rho * rho;
+  const T c = have_c ? c_in : mu - T(2) * lam * log(J);
+  const T kmu = kappa * mu, kc = kappa * c;
+#pragma unroll
+  for (int a = 0; a < nsym(DIM); ++a) {
+    const int i = vi<DIM>(a), j = vj<DIM>(a);
+    T bij = F[i][0] * F[j][0];
+#pragma unroll
+    for (int k = 1; k < DIM; ++k) bij = fma(F[i][k], F[j][k], bij);
+    tau[a] = (i == j) ? fma(kmu, bij, -kc) : kmu * bij;
+  }
+  c1 = T(2) * kc;
+  c2 = T(2) * kappa * lam;
+}
+
 // Material part for the neo-Hooke action (Eq. simplified_action): S = c1 sym(g) + c2 tr(g) I.
 template <int DIM, typename T>
 __device__ __forceinline__ void nh_action(const T g[DIM][DIM], T c1, T c2, T Sv[nsym(DIM)]) {
@@ -253,7 +344,7 @@ template <int DIM, int N, typename T>
 struct Smem {
   static constexpr int NPT = ipow(N, DIM);
   static constexpr int CB = cells_per_block(DIM, N);
-  T S[MAXN][MAXN], D[MAXN][MAXN], W[NPT];
+  T S[MAXN][MAXN], D[MAXN][MAXN], Dh[MAXN][MAXN], W[NPT], Wh[NPT];
   T mu[MAXMAT], lam[MAXMAT];
   T bp[CB][DIM * DIM][NPT];  // fluxes; also the ping-pong pair for the displacement
   T b0[CB][DIM][NPT];
@@ -267,6 +358,7 @@ __device__ __forceinline__ void load_tables(Smem<DIM, N, T>& s, const CellArgs<T
   if (t < MAXN * MAXN) {
     s.S[t / MAXN][t % MAXN] = a.b.S[t / MAXN][t % MAXN];
     s.D[t / MAXN][t % MAXN] = a.b.D[t / MAXN][t % MAXN];
+    s.Dh[t / MAXN][t % MAXN] = a.b.D[t / MAXN][t % MAXN] * T(a.g.inv_h);  // derivative in physical units
   }
   if (t < NPT) {
     const int q0 = t % N, q1 = (t / N) % N, q2 = DIM == 3 ? t / (N * N) : 0;
@@ -275,6 +367,7 @@ __device__ __forceinline__ void load_tables(Smem<DIM, N, T>& s, const CellArgs<T
     T hd = T(a.g.h) * T(a.g.h);
     if (DIM == 3) hd *= T(a.g.h);
     s.W[t] = w * hd;
+    s.Wh[t] = w * hd * T(a.g.inv_h);
   }
   if (t < MAXMAT) {
     s.mu[t] = a.mt.mu[t];
@@ -312,7 +405,17 @@ apply_kernel(const CellArgs<T> a) {
   constexpr int CB = cells_per_block(DIM, N);
   constexpr int NS = nsym(DIM);
   constexpr bool NEED_U = (VAR == VAR_NC || VAR == VAR_SC);
+  constexpr int NV = cache_values(VAR, DIM);
+  constexpr int BS = cache_row(DIM, N);
   __shared__ Smem<DIM, N, T> s;
+  __shared__ __align__(8) unsigned long long bar;
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
+  T* cs = reinterpret_cast<T*>(dyn_smem);  // this block's cache chunk [NV][BS]
+  if (NV > 0 && threadIdx.x == 0) {
+    // the chunk streams in (TMA bulk copy) while the block gathers x and runs the forward sweeps
+    mbar_init(&bar, 1);
+    bulk_load(cs, a.cache + (size_t)blockIdx.x * NV * BS, (unsigned)(NV * BS * sizeof(T)), &bar);
+  }
   load_tables<DIM, N>(s, a);
   const int cl = threadIdx.x / NPT;
   const Pt<DIM, N> pt(threadIdx.x % NPT);
@@ -361,24 +464,33 @@ apply_kernel(const CellArgs<T> a) {
       T* t = sx; sx = dx; dx = t;
       t = su; su = du; du = t;
     }
-    colloc_grad<DIM, N>(sx, pt, s.D, G);
-    colloc_grad<DIM, N>(su, pt, s.D, Gu);
+    colloc_grad<DIM, N>(sx, pt, s.Dh, G);   // physical gradients: Grad x, Grad u
+    colloc_grad<DIM, N>(su, pt, s.Dh, Gu);
     __syncthreads();  // bp is overwritten with the fluxes below
   } else {
     const T* V = interp_forward<DIM, N, DIM>(b0, b1, pt, s.S);
-    colloc_grad<DIM, N>(V, pt, s.D, G);
+    if (VAR == VAR_FC) colloc_grad<DIM, N>(V, pt, s.Dh, G);  // Grad x
+    else colloc_grad<DIM, N>(V, pt, s.D, G);                // d x / d xi (M holds F^{-1}/h)
+  }
+  if (NV > 0) {
+    const bool ok = mbar_wait(&bar, 0);
+    if (__syncthreads_or(!ok)) {  // the copy never completed: flag it, give it one more bounded wait, leave
+      if (threadIdx.x == 0) atomicOr(a.err, ERRBIT_TIMEOUT);
+      mbar_wait(&bar, 0);
+      return;
+    }
   }
   // quadrature-point work
   T P[DIM][DIM];
   {
-    const long long qg = (long long)(active ? cell : 0) * NPT + pt.p;
-    const long long st = a.nqp;
+    const int qg = threadIdx.x;
+    constexpr int st = BS;
     T M[DIM][DIM], tau[NS], Sv[NS], g[DIM][DIM];
     if (VAR == VAR_T4 || VAR == VAR_T2) {
 #pragma unroll
-      for (int i = 0; i < DIM * DIM; ++i) M[i / DIM][i % DIM] = active ? a.cache[i * st + qg] : T(0);
+      for (int i = 0; i < DIM * DIM; ++i) M[i / DIM][i % DIM] = active ? cs[i * st + qg] : T(0);
 #pragma unroll
-      for (int i = 0; i < NS; ++i) tau[i] = active ? a.cache[(DIM * DIM + i) * st + qg] : T(0);
+      for (int i = 0; i < NS; ++i) tau[i] = active ? cs[(DIM * DIM + i) * st + qg] : T(0);
       matmul<DIM>(G, M, g);
       if (VAR == VAR_T4) {
         constexpr int OFF = DIM * DIM + NS;
@@ -395,33 +507,32 @@ apply_kernel(const CellArgs<T> a) {
           for (int be = 0; be < NS; ++be) {
             const int lo = al < be ? al : be, hi = al < be ? be : al;
             const int idx = lo * NS - lo * (lo - 1) / 2 + (hi - lo);  // upper triangle, row major
-            const T cv = active ? a.cache[(OFF + idx) * st + qg] : T(0);
+            const T cv = active ? cs[(OFF + idx) * st + qg] : T(0);
             acc = (be == 0) ? cv * v[be] : fma(cv, v[be], acc);
           }
           Sv[al] = acc;
         }
       } else {
-        const T c1 = active ? a.cache[(DIM * DIM + NS) * st + qg] : T(0);
-        const T c2 = active ? a.cache[(DIM * DIM + NS + 1) * st + qg] : T(0);
+        const T c1 = active ? cs[(DIM * DIM + NS) * st + qg] : T(0);
+        const T c2 = active ? cs[(DIM * DIM + NS + 1) * st + qg] : T(0);
         nh_action<DIM>(g, c1, c2, Sv);
       }
     } else {
       T F[DIM][DIM];
-      const T inv_h = T(1.0 / a.g.h);
       if (VAR == VAR_FC) {
 #pragma unroll
         for (int i = 0; i < DIM * DIM; ++i)
-          F[i / DIM][i % DIM] = active ? a.cache[i * st + qg] : (i % (DIM + 1) == 0 ? T(1) : T(0));
+          F[i / DIM][i % DIM] = active ? cs[i * st + qg] : (i % (DIM + 1) == 0 ? T(1) : T(0));
       } else {
 #pragma unroll
         for (int i = 0; i < DIM; ++i)
 #pragma unroll
-          for (int J = 0; J < DIM; ++J) F[i][J] = (i == J ? T(1) : T(0)) + Gu[i][J] * inv_h;
+          for (int J = 0; J < DIM; ++J) F[i][J] = (i == J) ? T(1) + Gu[i][J] : Gu[i][J];
       }
       const int id = active ? a.mat[cell] : 0;
-      const T cin = (VAR == VAR_SC && active) ? a.cache[qg] : T(0);
+      const T cin = (VAR == VAR_SC && active) ? cs[qg] : T(0);
       T c1, c2;
-      neo_hooke_state<DIM>(F, s.mu[id], s.lam[id], s.W[pt.p], inv_h, VAR == VAR_SC, cin, M, tau, c1, c2);
+      neo_hooke_adj<DIM>(F, s.mu[id], s.lam[id], s.Wh[pt.p], VAR == VAR_SC, cin, M, tau, c1, c2);  // M = adj
       matmul<DIM>(G, M, g);
       nh_action<DIM>(g, c1, c2, Sv);
     }
@@ -466,7 +577,7 @@ qp_state_kernel(const CellArgs<double> a, T* __restrict__ out) {
   double Gu[DIM][DIM];
   colloc_grad<DIM, N>(V, pt, s.D, Gu);
   if (!active) return;
-  const double inv_h = 1.0 / a.g.h;
+  const double inv_h = a.g.inv_h;
   double F[DIM][DIM];
 #pragma unroll
   for (int i = 0; i < DIM; ++i)
@@ -481,8 +592,11 @@ qp_state_kernel(const CellArgs<double> a, T* __restrict__ out) {
   } else {
     atomicMin(a.jmin_bits, (unsigned long long)__double_as_longlong(J));
   }
-  const long long qg = (long long)cell * NPT + pt.p;
-  const long long st = a.nqp;
+  // blocked layout: (block * NV + v) * BS + local index
+  constexpr int NVO = cache_values(VAR, DIM);
+  constexpr int BS = cache_row(DIM, N);
+  const long long qg = (long long)blockIdx.x * NVO * BS + threadIdx.x;
+  constexpr long long st = BS;
   if (VAR == VAR_T4 || VAR == VAR_T2) {
 #pragma unroll
     for (int i = 0; i < DIM * DIM; ++i) out[i * st + qg] = T(M[i / DIM][i % DIM]);
@@ -539,7 +653,7 @@ residual_kernel(const CellArgs<double> a) {
   const double* V = interp_forward<DIM, N, DIM>(b0, b1, pt, s.S);
   double Gu[DIM][DIM];
   colloc_grad<DIM, N>(V, pt, s.D, Gu);
-  const double inv_h = 1.0 / a.g.h;
+  const double inv_h = a.g.inv_h;
   double F[DIM][DIM];
 #pragma unroll
   for (int i = 0; i < DIM; ++i)
@@ -602,7 +716,7 @@ diag_kernel(const CellArgs<double> a) {
   const double* V = interp_forward<DIM, N, DIM>(b0, b1, pt, s.S);
   double Gu[DIM][DIM];
   colloc_grad<DIM, N>(V, pt, s.D, Gu);
-  const double inv_h = 1.0 / a.g.h;
+  const double inv_h = a.g.inv_h;
   double F[DIM][DIM];
 #pragma unroll
   for (int i = 0; i < DIM; ++i)

@@ -43,6 +43,7 @@ struct Geom {
   int ncells;        // m^dim
   uint32_t fm[6];    // constrained-component bitmask per face (-x,+x,-y,+y,-z,+z)
   double h;          // cell size
+  double inv_h;      // 1 / h
 };
 
 template <typename T>
@@ -73,7 +74,19 @@ __host__ __device__ constexpr int cells_per_block(int dim, int n) {
   return (256 / ipow(n, dim)) < 1 ? 1 : (256 / ipow(n, dim));
 }
 
+// Gauss-point caches are stored per thread block of the cell kernels: block b holds, for every cached
+// value v, the CB * NPT entries of its cells contiguously, padded to a multiple of 4 elements so that
+// every row and every block's chunk starts on a 16-byte boundary (the granularity of a bulk copy):
+//   index(b, v, t) = (b * NV + v) * BS + t,   BS = cache_row(dim, n),   t = local cell * NPT + q.
+__host__ __device__ constexpr int cache_row(int dim, int n) {
+  return (cells_per_block(dim, n) * ipow(n, dim) + 3) / 4 * 4;
+}
+
 // Device-side error word bits.
-enum : unsigned { ERRBIT_JNEG = 1u, ERRBIT_NAN = 2u };
+enum : unsigned { ERRBIT_JNEG = 1u, ERRBIT_NAN = 2u, ERRBIT_TIMEOUT = 4u };
+
+// Upper bound on mbarrier polls before a wait gives up (each try_wait may suspend the thread briefly,
+// so this is seconds, far above any real copy time).
+constexpr unsigned MBAR_POLL_LIMIT = 1u << 24;
 
 }  // namespace hy

@@ -97,3 +97,25 @@ def test_pcg_solves_tangent_system(torch, variant, level_dtype):
     assert its < 60
     assert np.linalg.norm(A @ x - b) <= 1.01e-10 * np.linalg.norm(b)
     assert rel(x, x_ref) < 1e-7
+
+
+def test_indefinite_coarse_level_is_reported_by_the_vcycle(torch):
+    """u = 0.05 * smooth field with the top face free linearises about an unstable state: the 4^3
+    coarsest tangent is indefinite (the oracle's dense eigenvalues agree). Applications still work;
+    the V-cycle returns HY_ERR_NOCONV instead of running an unstable Chebyshev solve."""
+    from paper_1904_13131_gb300.api import HyError
+    dim, k, m = 3, 2, 8
+    pr = problem(dim, k, m, n_levels=2, top=0)
+    u = inputs.smooth_field(dim, k, m, seed=0)
+    H = hierarchy(pr)
+    H.set_displacement(u)
+    assert not H.coarse_spd
+    with context(pr) as ctx:
+        ud = torch.tensor(u, device="cuda")
+        ctx.set_displacement(ud, "T4")
+        assert ctx.level_info(0)["coarse_lo"] < 0 and ctx.level_info(0)["coarse_degree"] == 0
+        y = ctx.apply_tangent(ud)
+        assert torch.isfinite(y).all()
+        with pytest.raises(HyError) as e:
+            ctx.gmg_vcycle(torch.zeros_like(ud))
+        assert e.value.status == "HY_ERR_NOCONV"

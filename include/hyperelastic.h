@@ -119,6 +119,9 @@ typedef struct {
   int eig_iters;            /* [30]  CG iterations of the lambda_max estimate */
   int coarse_eig_iters;     /* [0 = number of free coarse dofs] CG iterations on the coarsest level */
   double coarse_reduction;  /* [1e-3] residual reduction of the coarse Chebyshev solve */
+  int coarse_solver;        /* [0] 0 = Chebyshev as a solver (Sec. 7); 1 = exact: the coarsest tangent
+                               assembled densely and inverted (Gauss-Jordan) once per linearisation,
+                               applied as one matrix-vector product (coarsest level <= 6000 dofs) */
 } hy_solver_params;
 
 hy_status hy_set_solver_params(hy_ctx *ctx, const hy_solver_params *p);

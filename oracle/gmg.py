@@ -17,6 +17,7 @@ import math
 
 import numpy as np
 import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 from .basis import gll_nodes, lagrange
 from .fem import Problem
@@ -129,7 +130,7 @@ class Hierarchy:
     """Level problems from coarsest (0) to finest (L-1), each halving the cells per direction."""
 
     def __init__(self, dim, k, levels_m, ids, mu_tab, lam_tab, masks, degree=4, sweeps=1, smooth_lo=0.6,
-                 smooth_hi=1.2, eig_iters=30, coarse_eig_iters=None, coarse_reduction=1e-3):
+                 smooth_hi=1.2, eig_iters=30, coarse_eig_iters=None, coarse_reduction=1e-3, coarse_solver="chebyshev"):
         self.dim, self.k = dim, k
         self.levels = [Problem(dim, k, ml, ids[l], mu_tab, lam_tab, masks) for l, ml in enumerate(levels_m)]
         self.degree, self.sweeps = degree, sweeps
@@ -137,6 +138,7 @@ class Hierarchy:
         self.eig_iters = eig_iters
         self.coarse_eig_iters = coarse_eig_iters
         self.coarse_reduction = coarse_reduction
+        self.coarse_solver = coarse_solver  # "chebyshev" (Sec. 7) or "direct" (exact solve, an option)
         self.P = [None]
         self.I = [None]
         for l in range(1, len(levels_m)):
@@ -163,6 +165,11 @@ class Hierarchy:
                 self.lmax[l] = lmax[l]
             else:
                 self.lmax[l] = self.estimate(l, self.eig_iters).max()
+        if self.coarse_solver == "direct":
+            self.coarse_lo = self.coarse_hi = 0.0
+            self.coarse_spd = bool(np.all(np.linalg.eigvalsh(self.A[0].toarray()) > 0))
+            self.coarse_deg = 0
+            return
         if coarse_bounds is not None:
             self.coarse_lo, self.coarse_hi = coarse_bounds
         else:
@@ -197,6 +204,8 @@ class Hierarchy:
             if not self.coarse_spd:
                 raise ValueError("coarsest-level tangent is not positive definite")
         if l == 0:
+            if self.coarse_solver == "direct":
+                return spla.spsolve(self.A[0].tocsc(), b)
             return chebyshev(self.A[0], self.Dinv[0], b, None, self.coarse_deg, self.coarse_lo, self.coarse_hi)
         x = self.smooth(l, b, None)
         r = b - self.A[l] @ x

@@ -36,7 +36,7 @@ class HyError(RuntimeError):
 class SolverParams(ctypes.Structure):
     _fields_ = [("cheb_degree", ctypes.c_int), ("cheb_sweeps", ctypes.c_int), ("cheb_lo", ctypes.c_double),
                 ("cheb_hi", ctypes.c_double), ("eig_iters", ctypes.c_int), ("coarse_eig_iters", ctypes.c_int),
-                ("coarse_reduction", ctypes.c_double)]
+                ("coarse_reduction", ctypes.c_double), ("coarse_solver", ctypes.c_int)]
 
 
 class NewtonParams(ctypes.Structure):

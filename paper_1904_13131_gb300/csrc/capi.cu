@@ -162,6 +162,9 @@ struct Level {
   double lmax = 0.0;
   double* w64[5] = {};  // V-cycle vectors b, x, r, d, t
   float* w32[5] = {};
+  double* d_Ainv = nullptr;  // exact coarse solve: dense inverse of the constrained tangent
+  double* d_gjR = nullptr;
+  double* d_gjC = nullptr;
 };
 
 struct Transfer {  // level l-1 (coarse) <-> l (fine); the same 1D tables act along every axis
@@ -181,7 +184,7 @@ struct hy_ctx {
   std::vector<Transfer> tr;
   Basis1D<double> b64{};
   Basis1D<float> b32{};
-  hy_solver_params sp{4, 1, 0.6, 1.2, 30, 0, 1e-3};
+  hy_solver_params sp{4, 1, 0.6, 1.2, 30, 0, 1e-3, 0};
   int var = -1;
   bool mixed = false;
   bool state_ok = false;
@@ -487,6 +490,10 @@ hy_status vcycle_typed(hy_ctx* ctx, int l) {
 hy_status vcycle_level(hy_ctx* ctx, int l) {
   if (l == 0) {
     Level& L = ctx->lev[0];
+    if (ctx->sp.coarse_solver == 1) {
+      launch_dense_gemv(L.d_Ainv, L.w64[0], L.w64[1], L.ndofs, ctx->stream);
+      return check_launch(ctx, 1);
+    }
     return chebyshev<double>(ctx, 0, L.w64[0], L.w64[1], true, ctx->coarse_deg, ctx->coarse_lo, ctx->coarse_hi);
   }
   return level_f32(ctx, l) ? vcycle_typed<float>(ctx, l) : vcycle_typed<double>(ctx, l);
@@ -646,6 +653,36 @@ hy_status check_error_word(hy_ctx* ctx, const char* where) {
   return HY_OK;
 }
 
+// Exact coarse solve: dense constrained tangent of level 0, inverted in place (Gauss-Jordan, SPD so no
+// pivoting); a pivot <= 0 marks the level as not positive definite, like a negative Ritz value would.
+hy_status coarse_direct_setup(hy_ctx* ctx) {
+  Level& C = ctx->lev[0];
+  const long long n = C.ndofs;
+  if (n > 6000) return fail(ctx, HY_ERR_UNSUPPORTED, "exact coarse solve needs a coarsest level of at most 6000 dofs");
+  if (!C.d_Ainv) {
+    HY_TRY(dalloc(ctx, &C.d_Ainv, (size_t)n * n));
+    HY_TRY(dalloc(ctx, &C.d_gjR, n));
+    HY_TRY(dalloc(ctx, &C.d_gjC, n));
+  }
+  HY_CK(cudaMemsetAsync(C.d_Ainv, 0, sizeof(double) * n * n, ctx->stream));
+  CellArgs<double> a = cell_args<double>(ctx, C);
+  a.u64 = C.d_u64;
+  launch_assemble_dense(ctx->dim, ctx->n, a, C.d_Ainv, n, ctx->stream);
+  launch_dense_constrained_identity(C.d_Ainv, C.nnodes, n, ctx->dim, C.g, ctx->stream);
+  HY_TRY(check_launch(ctx, 2));
+  HY_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
+  for (long long k = 0; k < n; ++k) launch_gj_step(C.d_Ainv, n, k, C.d_gjR, C.d_gjC, ctx->d_err, ctx->stream);
+  HY_TRY(check_launch(ctx, (int)(2 * n)));
+  unsigned h = 0;
+  HY_CK(cudaMemcpyAsync(&h, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+  HY_CK(cudaStreamSynchronize(ctx->stream));
+  HY_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
+  ctx->coarse_spd = !(h & ERRBIT_NONSPD);
+  ctx->coarse_lo = ctx->coarse_hi = 0.0;
+  ctx->coarse_deg = 0;
+  return HY_OK;
+}
+
 hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
   if (ctx->nlev == 0) return fail(ctx, HY_ERR_STATE, "mesh not set up");
   for (int l = 0; l < ctx->nlev; ++l)
@@ -707,7 +744,9 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
     else HY_TRY(eig_estimate<double>(ctx, l, ctx->sp.eig_iters, lmin, lmax));
     ctx->lev[l].lmax = lmax;
   }
-  {
+  if (ctx->sp.coarse_solver == 1) {
+    HY_TRY(coarse_direct_setup(ctx));
+  } else {
     Level& C = ctx->lev[0];
     long long nfree = 0;
     {
@@ -734,11 +773,13 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
   }
   // The Chebyshev coarse solver needs an SPD coarsest level; an indefinite one (a tangent about an
   // unstable state) is reported when the V-cycle is used, not here, so that applications still work.
-  ctx->coarse_spd = ctx->coarse_lo > 0.0;
-  ctx->coarse_deg = 0;
-  if (ctx->coarse_spd) {
-    const double sig = (ctx->coarse_hi + ctx->coarse_lo) / (ctx->coarse_hi - ctx->coarse_lo);
-    ctx->coarse_deg = std::max(1, (int)std::ceil(std::acosh(1.0 / ctx->sp.coarse_reduction) / std::acosh(sig) - 1e-12));
+  if (ctx->sp.coarse_solver != 1) {
+    ctx->coarse_spd = ctx->coarse_lo > 0.0;
+    ctx->coarse_deg = 0;
+    if (ctx->coarse_spd) {
+      const double sig = (ctx->coarse_hi + ctx->coarse_lo) / (ctx->coarse_hi - ctx->coarse_lo);
+      ctx->coarse_deg = std::max(1, (int)std::ceil(std::acosh(1.0 / ctx->sp.coarse_reduction) / std::acosh(sig) - 1e-12));
+    }
   }
   if (ctx->verbose) {
     for (int l = 1; l < ctx->nlev; ++l) std::fprintf(stderr, "[hy] level %d lmax %.6e\n", l, ctx->lev[l].lmax);
@@ -1125,7 +1166,8 @@ hy_status hy_gmg_vcycle(hy_ctx* ctx, const double* r, double* z) {
 hy_status hy_set_solver_params(hy_ctx* ctx, const hy_solver_params* p) {
   if (!ctx || !p) return HY_ERR_ARG;
   if (p->cheb_degree < 1 || p->cheb_sweeps < 1 || !(p->cheb_lo > 0) || !(p->cheb_hi > p->cheb_lo) ||
-      p->eig_iters < 1 || p->coarse_eig_iters < 0 || !(p->coarse_reduction > 0 && p->coarse_reduction < 1))
+      p->eig_iters < 1 || p->coarse_eig_iters < 0 || !(p->coarse_reduction > 0 && p->coarse_reduction < 1) ||
+      p->coarse_solver < 0 || p->coarse_solver > 1)
     return fail(ctx, HY_ERR_ARG, "solver parameters out of range");
   ctx->sp = *p;
   ctx->state_ok = false;

@@ -83,7 +83,7 @@ __host__ __device__ constexpr int cache_row(int dim, int n) {
 }
 
 // Device-side error word bits.
-enum : unsigned { ERRBIT_JNEG = 1u, ERRBIT_NAN = 2u, ERRBIT_TIMEOUT = 4u };
+enum : unsigned { ERRBIT_JNEG = 1u, ERRBIT_NAN = 2u, ERRBIT_TIMEOUT = 4u, ERRBIT_NONSPD = 8u };
 
 // Upper bound on mbarrier polls before a wait gives up (each try_wait may suspend the thread briefly,
 // so this is seconds, far above any real copy time).

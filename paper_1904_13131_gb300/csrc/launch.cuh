@@ -59,4 +59,13 @@ template <typename T>
 void launch_sweep(const T* in, T* out, int dim, const int Lin[3], const int Lout[3], int axis, const int* start,
                   const T* w, int E, bool add_to_out, const Geom* mask_in, const Geom* mask_out, cudaStream_t st);
 
+// ---- exact coarsest-level solve (coarse_direct.cu) ----------------------------------------------
+// dense constrained tangent of a level, accumulated into A (n x n, zeroed by the caller)
+void launch_assemble_dense(int dim, int n, const CellArgs<double>& a, double* A, long long ndof, cudaStream_t st);
+void launch_dense_constrained_identity(double* A, long long n_nodes, long long ndof, int dim, const Geom& g,
+                                       cudaStream_t st);
+// Gauss-Jordan step k of the in-place inversion (R, C: n-element work vectors); flags a pivot <= 0
+void launch_gj_step(double* A, long long n, long long k, double* R, double* C, unsigned* err, cudaStream_t st);
+void launch_dense_gemv(const double* A, const double* b, double* x, long long n, cudaStream_t st);
+
 }  // namespace hy

@@ -63,3 +63,14 @@ def test_3d_newton_matches_oracle(torch):
         rep = ctx.newton_solve(u, Context.newton_params(load_steps=2, face_values=face_values(3, -0.1)))
     assert rep["load_steps_done"] == 2
     assert rel(u.cpu().numpy(), u_ref) < 1e-8
+
+
+def test_config1_newton_exact_coarse_matches_oracle(torch, config1_reference):
+    pr, u_ref, _ = config1_reference
+    from paper_1904_13131_gb300.api import Context
+    with context(pr) as ctx:
+        ctx.set_solver_params(coarse_solver=1)
+        u = torch.zeros(ctx.num_dofs(), dtype=torch.float64, device="cuda")
+        rep = ctx.newton_solve(u, Context.newton_params(level_dtype=1, face_values=face_values(2, -0.1)))
+    assert rep["load_steps_done"] == 5
+    assert rel(u.cpu().numpy(), u_ref) < 1e-8

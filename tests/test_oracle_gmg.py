@@ -144,3 +144,20 @@ def test_pcg_matches_direct_solve(hier2d):
 def test_gll_nodes_used_by_transfers_match_inputs():
     for k in (1, 2, 3, 4):
         np.testing.assert_allclose(gll_nodes(k), inputs.gll_unit(k), atol=1e-15)
+
+
+def test_direct_coarse_option():
+    """Exact coarse solve: one level makes the V-cycle the inverse; with more levels it stays SPD."""
+    pr = inputs.problem(2, 2, 4, n_levels=1, top=inputs.normal_top_mask(2))
+    H = gmg.Hierarchy(2, 2, pr["levels_m"], pr["ids"], pr["mu"], pr["lam"], pr["masks"], coarse_solver="direct")
+    u = 0.3 * inputs.smooth_field(2, 2, 4, seed=1)
+    H.set_displacement(u)
+    b = inputs.gaussian_vector(H.levels[0].n_dofs, 2)
+    b[H.levels[0].constrained] = 0
+    np.testing.assert_allclose(H.A[0] @ H.vcycle(b), b, atol=1e-12 * np.abs(b).max())
+    pr = inputs.problem(2, 2, 8, n_levels=3, top=inputs.normal_top_mask(2))
+    H = gmg.Hierarchy(2, 2, pr["levels_m"], pr["ids"], pr["mu"], pr["lam"], pr["masks"], coarse_solver="direct")
+    H.set_displacement(0.5 * inputs.smooth_field(2, 2, 8, seed=1))
+    V, A = _dense_vcycle(H)
+    assert np.abs(V - V.T).max() < 1e-12 * np.abs(V).max()
+    assert np.linalg.eigvalsh(0.5 * (V + V.T)).min() > 0

@@ -204,6 +204,64 @@ def solve_latency(torch, api, inputs, dev):
     return out
 
 
+def serve_bench(api, inputs, dev, n_req, seed=0, max_active=8, budget_gb=160):
+    """Serving (continuous batching): a seeded stream of uneven solve requests (2D 32^2-256^2 and 3D 8^3-48^3,
+    Q1-Q3, stiffness ratio 2-100, radius 0.1-0.35, compression 2-15 %, 5 load steps). Baseline: the same
+    requests solved one at a time with plain FP64 (FP64 V-cycle, Chebyshev coarse solve). Served: up to
+    `max_active` resident solves, mixed-precision V-cycle, exact coarse solve; closed loop (all at t=0) for
+    peak solves/s, and Poisson arrivals at twice the baseline rate for p50/p99 latency."""
+    reqs = inputs.serving_requests(n_req, seed)
+
+    def problem(q):
+        return inputs.problem(q["dim"], q["k"], q["m"], n_levels=q["levels"], ratio=q["ratio"], radius=q["radius"],
+                              top=inputs.normal_top_mask(q["dim"]))
+
+    def params(q, ldt):
+        fv = [[0.0] * 3 for _ in range(6)]
+        fv[2 * (q["dim"] - 1) + 1][q["dim"] - 1] = -q["compression"]
+        return api.Context.newton_params(face_values=fv, level_dtype=ldt)
+
+    def run(max_act, ldt, coarse, arrivals=None):
+        sp = api.SolverParams(4, 1, 0.6, 1.2, 30, 0, 1e-3, coarse)
+        out = {}
+        with api.Server(dev.index, budget_bytes=budget_gb << 30, max_active=max_act) as sv:
+            t0 = time.perf_counter()
+            tickets = []
+            for q in reqs:
+                if arrivals is not None:
+                    delay = arrivals[q["id"]] - (time.perf_counter() - t0)
+                    if delay > 0:
+                        time.sleep(delay)
+                tickets.append(sv.submit(problem(q), params(q, ldt), sp))
+            for t in tickets:
+                sv.wait(t, 3600.0)
+            makespan = time.perf_counter() - t0
+            res = [sv.poll(t, want_u=True) for t in tickets]
+            stats = sv.stats()
+        lat = np.array([r["latency_ms"] for r in res])
+        failed = sum(r["state"] != 2 for r in res)
+        out = {"solves_per_s": (len(reqs) - failed) / makespan, "p50_ms": float(np.percentile(lat, 50)),
+               "p99_ms": float(np.percentile(lat, 99)), "makespan_s": makespan, "failed": failed,
+               "bytes_peak_gb": stats["bytes_peak"] / 1e9, "max_active": max_act}
+        return out, [r["u"] for r in res]
+
+    seq, u_seq = run(1, 0, 0)
+    rate = 2.0 * seq["solves_per_s"]
+    rng = np.random.default_rng(seed + 1)
+    arr, t = {}, 0.0
+    for q in reqs:
+        t += float(rng.exponential(1.0 / rate))
+        arr[q["id"]] = t
+    peak, u_peak = run(max_active, 1, 1)
+    poisson, u_srv = run(max_active, 1, 1, arrivals=arr)
+    err = max(float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(u_srv, u_seq) if a is not None and b is not None)
+    return {"requests": n_req, "seed": seed, "sequential_fp64": seq, "served_closed_loop": peak,
+            "served_poisson": dict(poisson, arrival_rate_per_s=rate),
+            "speedup_solves_per_s": peak["solves_per_s"] / seq["solves_per_s"],
+            "max_rel_l2_served_vs_fp64": err,
+            "mix": [(q["dim"], q["k"], q["m"]) for q in reqs]}
+
+
 def cpu_oracle_rate(seconds=10.0):
     """Oracle element-by-element application on the same problem at 16^3 Q2 (1/8 of the cells)."""
     from oracle.fem import Problem
@@ -255,6 +313,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--only", default=None, help="profile mode: VARIANT:f64|f32, a few applications of one kernel")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--serve-requests", type=int, default=12, help="requests in the serving section (0 = skip)")
+    ap.add_argument("--serve-only", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -289,6 +349,9 @@ def main():
                 c.apply_tangent(xin, y, dtype=1 if dt == "f32" else 0)
             torch.cuda.synchronize()
         print(json.dumps({"only": args.only, "reps": args.reps}))
+        return
+    if args.serve_only:
+        print(json.dumps({"serve": serve_bench(api, inputs, dev, args.serve_requests)}), flush=True)
         return
     pr, u, x, ctxs = setup_contexts(torch, api, inputs, dev)
     n = inputs.n_dofs(DIM, K, M)
@@ -370,6 +433,13 @@ def main():
         except api.HyError as e:
             solve = {"error": str(e)}
 
+    serve = None
+    if args.serve_requests > 0 and rank == 0:
+        try:
+            serve = serve_bench(api, inputs, dev, args.serve_requests)
+        except api.HyError as e:
+            serve = {"error": str(e)}
+
     cpu = None
     if rank == 0 and world == 1:
         rate, nd, el, sample = cpu_oracle_rate(args.cpu_seconds)
@@ -384,7 +454,7 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": int(launches_timed),
-                "per_variant_ms_f64": per_var_ms, "variants": variants, "solve": solve,
+                "per_variant_ms_f64": per_var_ms, "variants": variants, "solve": solve, "serve": serve,
                 "wall_s_timed_region": wall, "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src}
         print(json.dumps(line), flush=True)
     if dist:

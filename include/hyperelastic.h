@@ -198,8 +198,54 @@ hy_status hy_dot(hy_ctx *ctx, const double *a_dev, const double *b_dev, int64_t 
 hy_status hy_dot_noalloc(int device, void *cuda_stream, const double *a_dev, const double *b_dev, int64_t n,
                          double *result);
 
+/* Device bytes a context will own for this problem after mesh setup and set_displacement (the
+ * admission measure of the solve server); pure host arithmetic, no GPU needed. */
+hy_status hy_footprint(int dim, int degree, int cells_per_dir, int n_levels, hy_variant variant,
+                       hy_dtype level_dtype, int coarse_solver, int64_t *bytes);
+
+/* Device bytes currently owned by the context (its hierarchy, caches and work vectors). */
+hy_status hy_ctx_bytes(const hy_ctx *ctx, int64_t *bytes);
+
 /* Number of kernels this context has launched since creation (for accounting). */
 hy_status hy_kernel_launches(const hy_ctx *ctx, int64_t *count);
+
+/* ---- Solve server (continuous batching of many independent solves on one GPU) --------------------
+ * Not a step of the paper's method: a request loop around hy_newton_solve. Requests are queued in
+ * arrival order; `max_active` worker threads, each with its own CUDA stream, admit the head of the
+ * queue as soon as a worker is free and its hy_footprint fits the remaining `hbm_budget_bytes` (the head
+ * is never bypassed). An admitted request keeps its hierarchy and Newton state resident on the device
+ * until its solve ends; requests admitted while others run overlap with them on the device. */
+typedef struct hy_server hy_server;
+
+typedef struct {
+  int dim, degree, cells_per_dir, n_levels;
+  uint32_t face_masks[6];
+  const uint8_t *cell_mat_levels; /* HOST: material ids of every level, coarsest first, concatenated */
+  const double *mu, *lambda;      /* HOST: per material id */
+  int n_mat;
+  hy_newton_params newton;        /* load path, tolerances, variant, V-cycle precision */
+  hy_solver_params solver;
+} hy_request;
+
+typedef struct {
+  int64_t submitted, completed, failed, active, queued;
+  int64_t bytes_in_use, bytes_peak, budget;
+} hy_server_stats;
+
+hy_status hy_server_create(hy_server **out, int device, int64_t hbm_budget_bytes, int max_active);
+/* Running requests finish; queued ones are dropped. */
+void hy_server_destroy(hy_server *s);
+/* Copies the request and returns at once. HY_ERR_OOM if its footprint exceeds the whole budget. */
+hy_status hy_server_submit(hy_server *s, const hy_request *r, uint64_t *ticket);
+/* state: 0 queued, 1 running, 2 done, 3 failed (the call then returns the solve's status). When done,
+ * rep, the solution u_host (n_u doubles, may be NULL) and the submit-to-completion latency are filled. */
+hy_status hy_server_poll(hy_server *s, uint64_t ticket, int *state, hy_newton_report *rep, double *u_host,
+                         int64_t n_u, double *latency_ms);
+/* Block the calling thread until the request has finished, or HY_ERR_TIMEOUT after timeout_s seconds. */
+hy_status hy_server_wait(hy_server *s, uint64_t ticket, double timeout_s);
+/* Forget a finished request (frees its host copy of the solution). */
+hy_status hy_server_release(hy_server *s, uint64_t ticket);
+hy_status hy_server_stats_get(hy_server *s, hy_server_stats *st);
 
 #ifdef __cplusplus
 }

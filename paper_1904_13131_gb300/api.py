@@ -24,7 +24,9 @@ EXPORTED = ("hy_create", "hy_destroy", "hy_status_str", "hy_last_error", "hy_mes
             "hy_set_material", "hy_set_displacement", "hy_apply_tangent", "hy_vmult", "hy_residual", "hy_diagonal",
             "hy_gmg_vcycle", "hy_set_solver_params", "hy_get_solver_params", "hy_level_info", "hy_set_level_info",
             "hy_level_displacement", "hy_prolongate_add", "hy_restrict", "hy_pcg", "hy_newton_default_params",
-            "hy_newton_solve", "hy_dot", "hy_dot_noalloc", "hy_kernel_launches")
+            "hy_newton_solve", "hy_dot", "hy_dot_noalloc", "hy_kernel_launches", "hy_footprint", "hy_ctx_bytes",
+            "hy_server_create", "hy_server_destroy", "hy_server_submit", "hy_server_poll", "hy_server_wait",
+            "hy_server_release", "hy_server_stats_get")
 
 
 class HyError(RuntimeError):
@@ -52,6 +54,18 @@ class NewtonReport(ctypes.Structure):
                 ("final_residual", ctypes.c_double), ("backtracks", ctypes.c_int), ("n_solves", ctypes.c_int),
                 ("solve_cg_iterations", ctypes.c_int * 256), ("solve_ms", ctypes.c_double * 256),
                 ("setup_ms_total", ctypes.c_double), ("total_ms", ctypes.c_double)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("degree", ctypes.c_int), ("cells_per_dir", ctypes.c_int),
+                ("n_levels", ctypes.c_int), ("face_masks", ctypes.c_uint32 * 6), ("cell_mat_levels", ctypes.c_void_p),
+                ("mu", ctypes.POINTER(ctypes.c_double)), ("lambda_", ctypes.POINTER(ctypes.c_double)),
+                ("n_mat", ctypes.c_int), ("newton", NewtonParams), ("solver", SolverParams)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "active", "queued", "bytes_in_use",
+                                              "bytes_peak", "budget")]
 
 
 _lib = None
@@ -94,11 +108,21 @@ def load_library(path: str = LIB_PATH):
         "hy_dot": [vp, vp, vp, i64, ctypes.POINTER(dbl)],
         "hy_kernel_launches": [vp, ctypes.POINTER(i64)],
         "hy_dot_noalloc": [i32, vp, vp, vp, i64, ctypes.POINTER(dbl)],
+        "hy_footprint": [i32, i32, i32, i32, i32, i32, i32, ctypes.POINTER(i64)],
+        "hy_ctx_bytes": [vp, ctypes.POINTER(i64)],
+        "hy_server_create": [ctypes.POINTER(vp), i32, i64, i32],
+        "hy_server_destroy": [vp],
+        "hy_server_submit": [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)],
+        "hy_server_poll": [vp, ctypes.c_uint64, ctypes.POINTER(i32), ctypes.POINTER(NewtonReport),
+                           ctypes.POINTER(dbl), i64, ctypes.POINTER(dbl)],
+        "hy_server_wait": [vp, ctypes.c_uint64, dbl],
+        "hy_server_release": [vp, ctypes.c_uint64],
+        "hy_server_stats_get": [vp, ctypes.POINTER(ServerStats)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
         f.argtypes = args
-        f.restype = None if name in ("hy_destroy", "hy_newton_default_params") else ctypes.c_int
+        f.restype = None if name in ("hy_destroy", "hy_newton_default_params", "hy_server_destroy") else ctypes.c_int
     lib.hy_status_str.restype = ctypes.c_char_p
     lib.hy_last_error.restype = ctypes.c_char_p
     _lib = lib
@@ -307,6 +331,11 @@ class Context:
         self._ck(self.lib.hy_dot(self.h, self._vec(a, n, F64), self._vec(b, n, F64), n, ctypes.byref(out)))
         return out.value
 
+    def bytes(self):
+        b = ctypes.c_int64()
+        self._ck(self.lib.hy_ctx_bytes(self.h, ctypes.byref(b)))
+        return b.value
+
     def kernel_launches(self):
         c = ctypes.c_int64()
         self._ck(self.lib.hy_kernel_launches(self.h, ctypes.byref(c)))
@@ -327,3 +356,95 @@ def dot_noalloc(a, b, device: int = 0, stream=None) -> float:
     if st != 0:
         raise HyError(st, "hy_dot_noalloc failed")
     return out.value
+
+
+def footprint(dim, degree, cells_per_dir, n_levels, variant="T4", level_dtype=F64, coarse_solver=0) -> int:
+    """Device bytes a context needs for this problem (host arithmetic, no GPU)."""
+    b = ctypes.c_int64()
+    st = load_library().hy_footprint(dim, degree, cells_per_dir, n_levels, VARIANTS[variant], level_dtype, coarse_solver,
+                                     ctypes.byref(b))
+    if st != 0:
+        raise HyError(st, "hy_footprint")
+    return b.value
+
+
+def _report_dict(rep, steps):
+    return {"load_steps_done": rep.load_steps_done, "newton_iterations": list(rep.newton_iterations[:steps]),
+            "cg_iterations_total": rep.cg_iterations_total, "cg_iterations_max": rep.cg_iterations_max,
+            "final_residual": rep.final_residual, "n_solves": rep.n_solves, "total_ms": rep.total_ms,
+            "setup_ms_total": rep.setup_ms_total}
+
+
+class Server:
+    """hy_server: continuous batching of independent Newton solves on one GPU (see include/hyperelastic.h)."""
+
+    def __init__(self, device=0, budget_bytes=64 << 30, max_active=4):
+        self.lib = load_library()
+        h = ctypes.c_void_p()
+        st = self.lib.hy_server_create(ctypes.byref(h), device, int(budget_bytes), max_active)
+        if st != 0:
+            raise HyError(st, "hy_server_create")
+        self.h = h
+        self._steps = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hy_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, problem: dict, newton: NewtonParams, solver: SolverParams | None = None) -> int:
+        """problem: an inputs.problem(...) bundle (ids of every level, coarsest first)."""
+        if solver is None:
+            solver = SolverParams(4, 1, 0.6, 1.2, 30, 0, 1e-3, 0)
+        ids = np.ascontiguousarray(np.concatenate([np.asarray(i, dtype=np.uint8) for i in problem["ids"]]))
+        mu = np.ascontiguousarray(problem["mu"], dtype=np.float64)
+        lam = np.ascontiguousarray(problem["lam"], dtype=np.float64)
+        r = Request()
+        r.dim, r.degree, r.cells_per_dir, r.n_levels = problem["dim"], problem["k"], problem["m"], len(problem["ids"])
+        for i, fm in enumerate(problem["masks"]):
+            r.face_masks[i] = int(fm)
+        r.cell_mat_levels = ids.ctypes.data_as(ctypes.c_void_p)
+        r.mu = mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        r.lambda_ = lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        r.n_mat = len(mu)
+        r.newton = newton
+        r.solver = solver
+        t = ctypes.c_uint64()
+        st = self.lib.hy_server_submit(self.h, ctypes.byref(r), ctypes.byref(t))
+        if st != 0:
+            raise HyError(st, "hy_server_submit")
+        self._steps[t.value] = (newton.load_steps, r.dim * (r.degree * r.cells_per_dir + 1) ** r.dim)
+        return t.value
+
+    def poll(self, ticket, want_u=False):
+        state, rep, lat = ctypes.c_int(), NewtonReport(), ctypes.c_double()
+        steps, n = self._steps[ticket]
+        u = np.empty(n) if want_u else None
+        st = self.lib.hy_server_poll(self.h, ticket, ctypes.byref(state), ctypes.byref(rep),
+                                     u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if want_u else None,
+                                     n if want_u else 0, ctypes.byref(lat))
+        out = {"state": state.value, "status": STATUS.get(st, st)}
+        if state.value >= 2:
+            out.update(report=_report_dict(rep, steps), latency_ms=lat.value, u=u if state.value == 2 else None)
+        return out
+
+    def wait(self, ticket, timeout_s=600.0):
+        st = self.lib.hy_server_wait(self.h, ticket, timeout_s)
+        if st != 0:
+            raise HyError(st, "hy_server_wait")
+
+    def release(self, ticket):
+        self.lib.hy_server_release(self.h, ticket)
+
+    def stats(self):
+        s = ServerStats()
+        st = self.lib.hy_server_stats_get(self.h, ctypes.byref(s))
+        if st != 0:
+            raise HyError(st, "hy_server_stats_get")
+        return {n: getattr(s, n) for n, _ in ServerStats._fields_}

@@ -202,6 +202,7 @@ struct hy_ctx {
   double* f64[10] = {};  // fine-level FP64 work vectors of PCG / Newton
   long long launches = 0;
   bool verbose = false;  // HY_VERBOSE=1: per-iteration diagnostics on stderr
+  size_t bytes = 0;      // device bytes currently owned
   // The V-cycle below the finest level's input/output copies is captured once per linearisation into a
   // CUDA graph and replayed (HY_GRAPHS=0 disables this and launches kernel by kernel).
   bool use_graphs = true;
@@ -209,7 +210,7 @@ struct hy_ctx {
   cudaGraphExec_t vc_exec = nullptr;
   bool vc_valid = false;
   long long vc_nodes = 0;
-  std::vector<void*> allocs;
+  std::vector<std::pair<void*, size_t>> allocs;
 };
 
 namespace {
@@ -233,24 +234,32 @@ hy_status fail(hy_ctx* ctx, hy_status s, const std::string& msg) {
   return s;
 }
 
+// Device buffers are stream-ordered allocations on the context's stream, so that contexts working
+// side by side (the solve server) never synchronise the whole device to allocate or free.
 template <typename T>
 hy_status dalloc(hy_ctx* ctx, T** p, size_t n) {
   void* q = nullptr;
-  cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+  const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+  cudaError_t e = cudaMallocAsync(&q, bytes, ctx->stream);
   if (e != cudaSuccess) {
-    ctx->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    ctx->err = std::string("cudaMallocAsync: ") + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? HY_ERR_OOM : HY_ERR_CUDA;
   }
-  ctx->allocs.push_back(q);
+  ctx->allocs.push_back({q, bytes});
+  ctx->bytes += bytes;
   *p = (T*)q;
   return HY_OK;
 }
 
 void dfree(hy_ctx* ctx, void* p) {
   if (!p) return;
-  auto it = std::find(ctx->allocs.begin(), ctx->allocs.end(), p);
-  if (it != ctx->allocs.end()) ctx->allocs.erase(it);
-  cudaFree(p);
+  for (auto it = ctx->allocs.begin(); it != ctx->allocs.end(); ++it)
+    if (it->first == p) {
+      ctx->bytes -= it->second;
+      ctx->allocs.erase(it);
+      break;
+    }
+  cudaFreeAsync(p, ctx->stream);
 }
 
 hy_status check_launch(hy_ctx* ctx, int nlaunch) {
@@ -268,8 +277,9 @@ void drop_graph(hy_ctx* ctx) {
 
 void free_mesh(hy_ctx* ctx) {
   drop_graph(ctx);
-  for (void* p : ctx->allocs) cudaFree(p);
+  for (auto& a : ctx->allocs) cudaFreeAsync(a.first, ctx->stream);
   ctx->allocs.clear();
+  ctx->bytes = 0;
   ctx->lev.clear();
   ctx->tr.clear();
   ctx->d_err = nullptr;
@@ -1042,14 +1052,15 @@ hy_status hy_mesh_setup(hy_ctx* ctx, int dim, int degree, int m, int n_levels, c
     HY_TRY(dalloc(ctx, &t.d_iw64, iw.size()));
     HY_TRY(dalloc(ctx, &t.d_pw32, pw.size()));
     HY_TRY(dalloc(ctx, &t.d_rw32, rw.size()));
-    HY_CK(cudaMemcpy(t.d_pstart, pstart.data(), sizeof(int) * t.Lf, cudaMemcpyHostToDevice));
-    HY_CK(cudaMemcpy(t.d_rstart, rstart.data(), sizeof(int) * t.Lc, cudaMemcpyHostToDevice));
-    HY_CK(cudaMemcpy(t.d_istart, istart.data(), sizeof(int) * t.Lc, cudaMemcpyHostToDevice));
-    HY_CK(cudaMemcpy(t.d_pw64, pw.data(), sizeof(double) * pw.size(), cudaMemcpyHostToDevice));
-    HY_CK(cudaMemcpy(t.d_rw64, rw.data(), sizeof(double) * rw.size(), cudaMemcpyHostToDevice));
-    HY_CK(cudaMemcpy(t.d_iw64, iw.data(), sizeof(double) * iw.size(), cudaMemcpyHostToDevice));
-    HY_CK(cudaMemcpy(t.d_pw32, pw32.data(), sizeof(float) * pw32.size(), cudaMemcpyHostToDevice));
-    HY_CK(cudaMemcpy(t.d_rw32, rw32.data(), sizeof(float) * rw32.size(), cudaMemcpyHostToDevice));
+    HY_CK(cudaMemcpyAsync(t.d_pstart, pstart.data(), sizeof(int) * t.Lf, cudaMemcpyHostToDevice, ctx->stream));
+    HY_CK(cudaMemcpyAsync(t.d_rstart, rstart.data(), sizeof(int) * t.Lc, cudaMemcpyHostToDevice, ctx->stream));
+    HY_CK(cudaMemcpyAsync(t.d_istart, istart.data(), sizeof(int) * t.Lc, cudaMemcpyHostToDevice, ctx->stream));
+    HY_CK(cudaMemcpyAsync(t.d_pw64, pw.data(), sizeof(double) * pw.size(), cudaMemcpyHostToDevice, ctx->stream));
+    HY_CK(cudaMemcpyAsync(t.d_rw64, rw.data(), sizeof(double) * rw.size(), cudaMemcpyHostToDevice, ctx->stream));
+    HY_CK(cudaMemcpyAsync(t.d_iw64, iw.data(), sizeof(double) * iw.size(), cudaMemcpyHostToDevice, ctx->stream));
+    HY_CK(cudaMemcpyAsync(t.d_pw32, pw32.data(), sizeof(float) * pw32.size(), cudaMemcpyHostToDevice, ctx->stream));
+    HY_CK(cudaMemcpyAsync(t.d_rw32, rw32.data(), sizeof(float) * rw32.size(), cudaMemcpyHostToDevice, ctx->stream));
+    HY_CK(cudaStreamSynchronize(ctx->stream));  // the host tables go out of scope
     size_t inter = (size_t)t.Lf * dim;
     for (int i = 1; i < dim; ++i) inter *= t.Lf;  // bounds every intermediate of the sweeps
     tmp_len = std::max(tmp_len, inter);
@@ -1066,8 +1077,8 @@ hy_status hy_mesh_setup(hy_ctx* ctx, int dim, int degree, int m, int n_levels, c
   HY_TRY(dalloc(ctx, &ctx->d_scal, 4));
   HY_TRY(dalloc(ctx, &ctx->d_face, 18));
   for (int i = 0; i < 10; ++i) HY_TRY(dalloc(ctx, &ctx->f64[i], ctx->lev[n_levels - 1].ndofs));
-  HY_CK(cudaMemset(ctx->d_err, 0, sizeof(unsigned)));
-  HY_CK(cudaDeviceSynchronize());
+  HY_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
+  HY_CK(cudaStreamSynchronize(ctx->stream));
   return HY_OK;
 }
 
@@ -1092,7 +1103,8 @@ hy_status hy_set_material(hy_ctx* ctx, int level, const uint8_t* cell_mat, const
     if (!(mu[i] > 0.0) || !(lambda[i] > -2.0 / 3.0 * mu[i]) || !std::isfinite(lambda[i]))
       return fail(ctx, HY_ERR_ARG, "material parameters out of range");
   HY_CK(cudaSetDevice(ctx->device));
-  HY_CK(cudaMemcpy(L.d_mat, cell_mat, L.g.ncells, cudaMemcpyHostToDevice));
+  HY_CK(cudaMemcpyAsync(L.d_mat, cell_mat, L.g.ncells, cudaMemcpyHostToDevice, ctx->stream));
+  HY_CK(cudaStreamSynchronize(ctx->stream));
   for (int i = 0; i < MAXMAT; ++i) {
     L.mt64.mu[i] = i < n_mat ? mu[i] : 0.0;
     L.mt64.lam[i] = i < n_mat ? lambda[i] : 0.0;
@@ -1366,6 +1378,62 @@ hy_status hy_dot(hy_ctx* ctx, const double* a, const double* b, int64_t n, doubl
   if (!ctx->d_partials) return fail(ctx, HY_ERR_STATE, "mesh not set up (scratch not allocated)");
   HY_CK(cudaSetDevice(ctx->device));
   return dot<double>(ctx, a, b, (long long)n, result);
+}
+
+// Device bytes a context needs for a problem, mirroring the allocations of hy_mesh_setup and
+// hy_set_displacement (requested sizes; the allocator's own rounding comes on top).
+hy_status hy_footprint(int dim, int degree, int m, int n_levels, hy_variant variant, hy_dtype level_dtype,
+                       int coarse_solver, int64_t* bytes) {
+  if (!bytes || (dim != 2 && dim != 3) || degree < 1 || degree > 4 || m < 1 || n_levels < 1) return HY_ERR_ARG;
+  if ((int)variant < 0 || (int)variant > 4) return HY_ERR_ARG;
+  auto al = [](size_t n, size_t sz) { return std::max<size_t>(n, 1) * sz; };
+  const int n = degree + 1;
+  const bool mixed = level_dtype == HY_F32;
+  size_t total = 0, tmp_len = 1;
+  std::vector<long long> nd(n_levels), L1(n_levels), nc(n_levels);
+  for (int l = 0; l < n_levels; ++l) {
+    const long long ml = (long long)m >> (n_levels - 1 - l);
+    if (ml < 1) return HY_ERR_ARG;
+    L1[l] = degree * ml + 1;
+    nc[l] = 1;
+    long long nn = 1;
+    for (int i = 0; i < dim; ++i) {
+      nc[l] *= ml;
+      nn *= L1[l];
+    }
+    nd[l] = nn * dim;
+    total += al(nd[l], 8) * 2 + al(nc[l], 1);  // u64, diag, materials
+  }
+  for (int l = 1; l < n_levels; ++l) {
+    const long long Lc = L1[l - 1], Lf = L1[l];
+    const long long Er = std::min<long long>(4 * degree + 1, Lf);
+    total += al(Lf, 4) + 2 * al(Lc, 4) + al(Lf * n, 8) + al(Lc * Er, 8) + al(Lc * n, 8) + al(Lf * n, 4) + al(Lc * Er, 4);
+    size_t inter = (size_t)Lf * dim;
+    for (int i = 1; i < dim; ++i) inter *= Lf;
+    tmp_len = std::max(tmp_len, inter);
+  }
+  total += 2 * al(tmp_len, 8) + 3 * al(tmp_len, 4);
+  total += al(1, 4) + al(1, 8) + al(DOT_BLOCKS, 8) + al(4, 8) + al(18, 8);
+  total += 10 * al(nd[n_levels - 1], 8);
+  const int top = n_levels - 1;
+  const int cb = cells_per_block(dim, n);
+  for (int l = 0; l < n_levels; ++l) {
+    const bool need64 = (l == top) || (l == 0) || !mixed;
+    const bool need32 = mixed && (l > 0 || l == top);
+    const size_t nblocks = (size_t)((nc[l] + cb - 1) / cb);
+    const size_t clen = std::max<size_t>(1, (size_t)cache_values((int)variant, dim) * cache_row(dim, n) * nblocks);
+    if (need64) total += al(clen, 8) + al(nd[l], 8) + 5 * al(nd[l], 8);
+    if (need32) total += al(clen, 4) + al(nd[l], 4) + al(nd[l], 4) + 5 * al(nd[l], 4);
+  }
+  if (coarse_solver == 1) total += al((size_t)nd[0] * nd[0], 8) + 2 * al(nd[0], 8);
+  *bytes = (int64_t)total;
+  return HY_OK;
+}
+
+hy_status hy_ctx_bytes(const hy_ctx* ctx, int64_t* bytes) {
+  if (!ctx || !bytes) return HY_ERR_ARG;
+  *bytes = (int64_t)ctx->bytes;
+  return HY_OK;
 }
 
 hy_status hy_kernel_launches(const hy_ctx* ctx, int64_t* count) {

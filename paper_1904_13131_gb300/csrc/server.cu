@@ -1,0 +1,270 @@
+// Solve server: many independent hyperelastic Newton solves of different meshes, degrees, materials
+// and loads, continuously batched on one GPU.
+//
+// Requests are queued in arrival order. A pool of worker threads, each with its own non-blocking CUDA
+// stream, admits the request at the head of the queue as soon as a worker is free and the request's
+// device footprint (hy_footprint, the exact mirror of a context's allocations) fits in the remaining
+// budget; the head is never bypassed, so a large request cannot starve. An admitted request builds its
+// own context (hierarchy, caches, V-cycle graph) on the worker's stream, keeps it resident for its whole
+// Newton solve and releases it when done, at which point the next request is admitted. Requests that
+// arrive while others run therefore join them on the device: their kernels overlap through the
+// concurrent streams. Latency is measured from submission to completion.
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/hyperelastic.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Req {
+  uint64_t id = 0;
+  int dim = 0, degree = 0, m = 0, nlev = 0;
+  uint32_t fm[6] = {};
+  std::vector<uint8_t> mats;  // concatenated per-level material ids, coarsest level first
+  std::vector<double> mu, lam;
+  hy_newton_params np{};
+  hy_solver_params sp{};
+  int64_t bytes = 0;
+  int state = 0;  // 0 queued, 1 running, 2 done, 3 failed
+  hy_status status = HY_OK;
+  std::string err;
+  hy_newton_report rep{};
+  std::vector<double> u;
+  Clock::time_point t_submit, t_start, t_end;
+};
+
+}  // namespace
+
+struct hy_server {
+  int device = 0;
+  int64_t budget = 0;
+  int max_active = 1;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Req*> queue;
+  std::unordered_map<uint64_t, std::unique_ptr<Req>> reqs;
+  int64_t in_use = 0, peak = 0;
+  int active = 0;
+  int64_t submitted = 0, completed = 0, failed = 0;
+  bool stop = false;
+  uint64_t next_id = 1;
+  std::vector<std::thread> workers;
+};
+
+namespace {
+
+long long level_cells(const Req& r, int l) {
+  long long ml = (long long)r.m >> (r.nlev - 1 - l), c = 1;
+  for (int i = 0; i < r.dim; ++i) c *= ml;
+  return c;
+}
+
+// One request on the worker's stream: context, hierarchy, materials, Newton solve, result to host.
+void run_request(Req& r, int device, cudaStream_t st) {
+  hy_ctx* ctx = nullptr;
+  double* u = nullptr;
+  hy_status s = hy_create(&ctx, device, st);
+  if (s == HY_OK) s = hy_mesh_setup(ctx, r.dim, r.degree, r.m, r.nlev, r.fm);
+  if (s == HY_OK) s = hy_set_solver_params(ctx, &r.sp);
+  size_t off = 0;
+  for (int l = 0; l < r.nlev && s == HY_OK; ++l) {
+    s = hy_set_material(ctx, l, r.mats.data() + off, r.mu.data(), r.lam.data(), (int)r.mu.size());
+    off += (size_t)level_cells(r, l);
+  }
+  int64_t n = 0;
+  if (s == HY_OK) s = hy_num_dofs(ctx, -1, &n);
+  if (s == HY_OK) {
+    if (cudaMallocAsync((void**)&u, sizeof(double) * n, st) != cudaSuccess ||
+        cudaMemsetAsync(u, 0, sizeof(double) * n, st) != cudaSuccess)
+      s = HY_ERR_OOM;
+  }
+  if (s == HY_OK) s = hy_newton_solve(ctx, &r.np, u, &r.rep);
+  if (s == HY_OK) {
+    r.u.resize((size_t)n);
+    if (cudaMemcpyAsync(r.u.data(), u, sizeof(double) * n, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      s = HY_ERR_CUDA;
+  }
+  if (s != HY_OK) r.err = ctx ? hy_last_error(ctx) : "context creation failed";
+  if (u) cudaFreeAsync(u, st);
+  hy_destroy(ctx);
+  cudaStreamSynchronize(st);
+  r.status = s;
+}
+
+void worker_loop(hy_server* sv) {
+  cudaSetDevice(sv->device);
+  cudaStream_t st = nullptr;
+  cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  for (;;) {
+    Req* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lock(sv->mu);
+      sv->cv_work.wait(lock, [&] {
+        return sv->stop || (!sv->queue.empty() && sv->in_use + sv->queue.front()->bytes <= sv->budget);
+      });
+      if (sv->stop) break;
+      r = sv->queue.front();
+      sv->queue.pop_front();
+      sv->in_use += r->bytes;
+      sv->peak = std::max(sv->peak, sv->in_use);
+      sv->active++;
+      r->state = 1;
+      r->t_start = Clock::now();
+    }
+    sv->cv_work.notify_all();  // the next head may fit as well
+    run_request(*r, sv->device, st);
+    {
+      std::lock_guard<std::mutex> lock(sv->mu);
+      sv->in_use -= r->bytes;
+      sv->active--;
+      r->t_end = Clock::now();
+      r->state = r->status == HY_OK ? 2 : 3;
+      if (r->status == HY_OK) sv->completed++;
+      else sv->failed++;
+    }
+    sv->cv_done.notify_all();
+    sv->cv_work.notify_all();
+  }
+  cudaStreamDestroy(st);
+}
+
+}  // namespace
+
+extern "C" {
+
+hy_status hy_server_create(hy_server** out, int device, int64_t hbm_budget_bytes, int max_active) {
+  if (!out || hbm_budget_bytes <= 0 || max_active < 1 || max_active > 64) return HY_ERR_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return HY_ERR_ARG;
+  hy_server* sv = new (std::nothrow) hy_server();
+  if (!sv) return HY_ERR_OOM;
+  sv->device = device;
+  sv->budget = hbm_budget_bytes;
+  sv->max_active = max_active;
+  for (int i = 0; i < max_active; ++i) sv->workers.emplace_back(worker_loop, sv);
+  *out = sv;
+  return HY_OK;
+}
+
+void hy_server_destroy(hy_server* sv) {
+  if (!sv) return;
+  {
+    // running requests finish (workers look at `stop` only between requests); queued ones are dropped
+    std::lock_guard<std::mutex> lock(sv->mu);
+    for (Req* r : sv->queue) r->state = 3;
+    sv->queue.clear();
+    sv->stop = true;
+  }
+  sv->cv_work.notify_all();
+  sv->cv_done.notify_all();
+  for (auto& t : sv->workers) t.join();
+  delete sv;
+}
+
+hy_status hy_server_submit(hy_server* sv, const hy_request* q, uint64_t* ticket) {
+  if (!sv || !q || !ticket) return HY_ERR_ARG;
+  if ((q->dim != 2 && q->dim != 3) || q->degree < 1 || q->degree > 4 || q->cells_per_dir < 1 || q->n_levels < 1 ||
+      !q->cell_mat_levels || !q->mu || !q->lambda || q->n_mat < 1 || q->n_mat > 16)
+    return HY_ERR_ARG;
+  auto r = std::make_unique<Req>();
+  r->dim = q->dim;
+  r->degree = q->degree;
+  r->m = q->cells_per_dir;
+  r->nlev = q->n_levels;
+  std::memcpy(r->fm, q->face_masks, sizeof(r->fm));
+  size_t total = 0;
+  for (int l = 0; l < r->nlev; ++l) {
+    if (((long long)r->m >> (r->nlev - 1 - l)) < 1) return HY_ERR_ARG;
+    total += (size_t)level_cells(*r, l);
+  }
+  r->mats.assign(q->cell_mat_levels, q->cell_mat_levels + total);
+  r->mu.assign(q->mu, q->mu + q->n_mat);
+  r->lam.assign(q->lambda, q->lambda + q->n_mat);
+  r->np = q->newton;
+  r->sp = q->solver;
+  int64_t bytes = 0;
+  hy_status s = hy_footprint(r->dim, r->degree, r->m, r->nlev, q->newton.variant, q->newton.level_dtype,
+                             q->solver.coarse_solver, &bytes);
+  if (s != HY_OK) return s;
+  r->bytes = bytes + (int64_t)sizeof(double) * r->dim * (int64_t)std::pow(r->degree * r->m + 1.0, r->dim);  // + u
+  if (r->bytes > sv->budget) return HY_ERR_OOM;  // could never be admitted
+  {
+    std::lock_guard<std::mutex> lock(sv->mu);
+    if (sv->stop) return HY_ERR_STATE;
+    r->id = sv->next_id++;
+    r->t_submit = Clock::now();
+    *ticket = r->id;
+    sv->queue.push_back(r.get());
+    sv->reqs[r->id] = std::move(r);
+    sv->submitted++;
+  }
+  sv->cv_work.notify_all();
+  return HY_OK;
+}
+
+hy_status hy_server_poll(hy_server* sv, uint64_t ticket, int* state, hy_newton_report* rep, double* u_host,
+                         int64_t n_u, double* latency_ms) {
+  if (!sv || !state) return HY_ERR_ARG;
+  std::lock_guard<std::mutex> lock(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end()) return HY_ERR_ARG;
+  Req& r = *it->second;
+  *state = r.state;
+  if (r.state >= 2) {
+    if (rep) *rep = r.rep;
+    if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r.t_end - r.t_submit).count();
+    if (u_host && r.state == 2) {
+      if (n_u != (int64_t)r.u.size()) return HY_ERR_ARG;
+      std::memcpy(u_host, r.u.data(), sizeof(double) * r.u.size());
+    }
+    if (r.state == 3) return r.status == HY_OK ? HY_ERR_STATE : r.status;
+  }
+  return HY_OK;
+}
+
+hy_status hy_server_wait(hy_server* sv, uint64_t ticket, double timeout_s) {
+  if (!sv) return HY_ERR_ARG;
+  std::unique_lock<std::mutex> lock(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end()) return HY_ERR_ARG;
+  Req* r = it->second.get();
+  const bool ok = sv->cv_done.wait_for(lock, std::chrono::duration<double>(timeout_s), [&] { return r->state >= 2; });
+  return ok ? HY_OK : HY_ERR_TIMEOUT;
+}
+
+hy_status hy_server_release(hy_server* sv, uint64_t ticket) {
+  if (!sv) return HY_ERR_ARG;
+  std::lock_guard<std::mutex> lock(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end() || it->second->state < 2) return HY_ERR_ARG;
+  sv->reqs.erase(it);
+  return HY_OK;
+}
+
+hy_status hy_server_stats_get(hy_server* sv, hy_server_stats* st) {
+  if (!sv || !st) return HY_ERR_ARG;
+  std::lock_guard<std::mutex> lock(sv->mu);
+  st->submitted = sv->submitted;
+  st->completed = sv->completed;
+  st->failed = sv->failed;
+  st->active = sv->active;
+  st->queued = (int64_t)sv->queue.size();
+  st->bytes_in_use = sv->in_use;
+  st->bytes_peak = sv->peak;
+  st->budget = sv->budget;
+  return HY_OK;
+}
+
+}  // extern "C"

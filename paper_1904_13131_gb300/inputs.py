@@ -156,3 +156,32 @@ def problem(dim: int, k: int, m: int, *, ratio: float = 10.0, radius: float = 0.
         "mu": mu, "lam": lam,
         "masks": face_masks(dim, top=top),
     }
+
+
+def levels_for(m: int) -> int:
+    """Hierarchy depth for a mesh of m cells per direction: halve while m stays even and m/2 >= 2."""
+    L = 1
+    while m % 2 == 0 and m // 2 >= 2:
+        m //= 2
+        L += 1
+    return L
+
+
+def serving_requests(n: int, seed: int = 0, rate: float = 1.0):
+    """Seeded stream of solve requests shaped like the heterogeneous-inclusion workload: dim 2 or 3
+    (equal odds), degree 1-3, 2D meshes 32^2..256^2 and 3D 8^3..48^3, stiffness ratio log-uniform on
+    [2, 100], inclusion radius uniform on [0.1, 0.35], top compression uniform on [2, 15] %, and
+    exponential inter-arrival times of the given mean rate (requests per second)."""
+    rng = np.random.default_rng(seed)
+    out, t = [], 0.0
+    for i in range(n):
+        dim = int(rng.choice([2, 3]))
+        k = int(rng.integers(1, 4))
+        m = int(rng.choice([32, 64, 128, 256] if dim == 2 else [8, 16, 24, 32, 48]))
+        ratio = float(np.exp(rng.uniform(np.log(2.0), np.log(100.0))))
+        radius = float(rng.uniform(0.1, 0.35))
+        compression = float(rng.uniform(0.02, 0.15))
+        t += float(rng.exponential(1.0 / rate))
+        out.append({"id": i, "dim": dim, "k": k, "m": m, "levels": levels_for(m), "ratio": ratio, "radius": radius,
+                    "compression": compression, "arrival": t})
+    return out

@@ -1,0 +1,82 @@
+"""The solve server: admission by device footprint, continuous batching, and results that do not
+depend on what else is running (each request alone vs in the mix agree to 1e-10 relative)."""
+import numpy as np
+import pytest
+
+from paper_1904_13131_gb300 import inputs
+
+from .gpu_util import context, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def request_problem(q):
+    top = inputs.normal_top_mask(q["dim"])
+    return inputs.problem(q["dim"], q["k"], q["m"], n_levels=q["levels"], ratio=q["ratio"], radius=q["radius"], top=top)
+
+
+def newton(q, **kw):
+    from paper_1904_13131_gb300.api import Context
+    fv = [[0.0] * 3 for _ in range(6)]
+    fv[2 * (q["dim"] - 1) + 1][q["dim"] - 1] = -q["compression"]
+    return Context.newton_params(face_values=fv, **kw)
+
+
+SMALL = [{"dim": 2, "k": 2, "m": 16, "levels": 3, "ratio": 10.0, "radius": 0.25, "compression": 0.1},
+         {"dim": 3, "k": 1, "m": 8, "levels": 3, "ratio": 30.0, "radius": 0.2, "compression": 0.05},
+         {"dim": 2, "k": 3, "m": 8, "levels": 3, "ratio": 3.0, "radius": 0.3, "compression": 0.12},
+         {"dim": 3, "k": 2, "m": 4, "levels": 2, "ratio": 80.0, "radius": 0.3, "compression": 0.08},
+         {"dim": 2, "k": 1, "m": 32, "levels": 5, "ratio": 50.0, "radius": 0.15, "compression": 0.03},
+         {"dim": 3, "k": 2, "m": 8, "levels": 3, "ratio": 5.0, "radius": 0.25, "compression": 0.1}]
+
+
+def test_footprint_matches_context_allocation():
+    torch = require_gpu()
+    from paper_1904_13131_gb300 import api
+    for dim, k, m, L, ldt, cs in [(3, 2, 8, 3, 0, 0), (3, 2, 8, 3, 1, 1), (2, 3, 16, 4, 1, 0)]:
+        pr = inputs.problem(dim, k, m, n_levels=L, top=inputs.normal_top_mask(dim))
+        with context(pr) as ctx:
+            ctx.set_solver_params(coarse_solver=cs)
+            ctx.set_displacement(torch.zeros(ctx.num_dofs(), dtype=torch.float64, device="cuda"), "T4", ldt)
+            assert ctx.bytes() == api.footprint(dim, k, m, L, "T4", ldt, cs)
+
+
+def test_results_alone_and_in_the_mix_agree():
+    require_gpu()
+    from paper_1904_13131_gb300.api import Server
+    alone = []
+    with Server(0, budget_bytes=8 << 30, max_active=1) as s:
+        for q in SMALL:
+            t = s.submit(request_problem(q), newton(q, level_dtype=1))
+            s.wait(t)
+            r = s.poll(t, want_u=True)
+            assert r["state"] == 2, r
+            alone.append(r["u"])
+    with Server(0, budget_bytes=8 << 30, max_active=4) as s:
+        tickets = [s.submit(request_problem(q), newton(q, level_dtype=1)) for q in SMALL]
+        for t in tickets:
+            s.wait(t)
+        mixed = [s.poll(t, want_u=True) for t in tickets]
+        st = s.stats()
+    assert st["completed"] == len(SMALL) and st["failed"] == 0
+    for a, r in zip(alone, mixed):
+        assert r["state"] == 2
+        assert np.linalg.norm(r["u"] - a) <= 1e-10 * np.linalg.norm(a)
+
+
+def test_admission_respects_the_budget():
+    require_gpu()
+    from paper_1904_13131_gb300 import api
+    from paper_1904_13131_gb300.api import HyError, Server
+    q = SMALL[5]
+    need = api.footprint(3, 2, 8, 3, "T4", api.F32, 0) + 8 * 3 * 17**3
+    with Server(0, budget_bytes=int(1.5 * need), max_active=4) as s:  # room for one at a time
+        tickets = [s.submit(request_problem(q), newton(q, level_dtype=1)) for _ in range(3)]
+        for t in tickets:
+            s.wait(t)
+        st = s.stats()
+        assert st["completed"] == 3 and st["bytes_peak"] <= st["budget"]
+        big = dict(q, m=16, levels=4)
+        with pytest.raises(HyError) as e:
+            s.submit(request_problem(big), newton(big, level_dtype=1))
+        assert e.value.status == "HY_ERR_OOM"

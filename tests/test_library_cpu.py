@@ -43,3 +43,17 @@ def test_no_oracle_in_product_package():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".inc")):
                 src = open(os.path.join(dp, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle", src, re.M), f
+
+
+def test_footprint_is_host_arithmetic(lib):
+    """hy_footprint needs no GPU; it grows with the mesh and with the mixed-precision / exact-coarse extras."""
+    from paper_1904_13131_gb300 import api
+    b64 = api.footprint(3, 2, 32, 4)
+    bmx = api.footprint(3, 2, 32, 4, level_dtype=api.F32)
+    bex = api.footprint(3, 2, 32, 4, level_dtype=api.F32, coarse_solver=1)
+    assert 0 < b64 < bmx < bex
+    n0 = 3 * 9**3  # 4^3 Q2 coarsest level
+    assert bex - bmx == 8 * n0 * n0 + 16 * n0
+    assert api.footprint(3, 2, 64, 5) > 7 * b64
+    with pytest.raises(api.HyError):
+        api.footprint(3, 5, 32, 4)

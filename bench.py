@@ -70,10 +70,7 @@ def bytes_per_apply(var, dtype_bytes, nqp, ndofs, dim=3):
 
 # DRAM bytes (read + write) per launch from one ncu capture of the 32^3 Q2 workload (profiles/*_ncu.md);
 # a kernel that changed since its capture maps to None.
-NCU_TRAFFIC = {
-    ("NC", "double"): 19_649_024,   # profiles/apply_nc_f64_32cube_q2_ncu.md
-    ("T4", "float"): 137_947_648,   # profiles/apply_t4_f32_32cube_q2_ncu.md
-}
+NCU_TRAFFIC = {}
 
 
 def peaks():
@@ -98,8 +95,7 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else f"/tmp/hy_clocks_{os.getpid()}.csv"
+        self.path = os.path.join(os.environ.get("HY_CLOCKS_DIR", "/tmp"), f"hy_clocks_{os.getpid()}_{index}.csv")
 
     def start(self):
         try:
@@ -306,7 +302,7 @@ def inputs_ndofs():
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-solve", action="store_true")

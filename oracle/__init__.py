@@ -17,7 +17,9 @@ Modules
   newton    Newton-Raphson with load steps (Sec. 3, Sec. 7)
   rng       SplitMix64 counter-based generator (start vectors of the eigen estimate)
 
-Every function states the passage of the paper it follows. Points where the
-paper is silent or ambiguous follow the readings listed in the design doc.
+Every function states the passage of the paper it follows. Where the paper is
+silent or ambiguous, the reading taken is stated where it is used (e.g. nodal
+interpolation for carrying the displacement down, one Chebyshev sweep per
+smoothing step, lifting of the prescribed increment into the first Newton solve).
 Parity status: every function is pinned by tests in tests/test_oracle_*.py.
 """

@@ -1,8 +1,8 @@
 """Newton-Raphson with load steps for prescribed boundary displacements (Sec. 3, Sec. 7).
 
 Test infrastructure (see oracle/__init__.py). Each Newton iteration solves Eq. linear_system,
-A(u) du = -F(u), on the free dofs with scipy's sparse direct solver. Readings of the paper
-(listed in the design doc): displacement-driven loading in S equal steps; the prescribed increment of a
+A(u) du = -F(u), on the free dofs with scipy's sparse direct solver. Readings of the paper where it is
+silent: displacement-driven loading in S equal steps; the prescribed increment of a
 step is lifted into the first linear solve (du_c given, A_ff du_f = -R_f - A_fc du_c); the step
 converges when ||R_free|| <= max(rtol * ||first right-hand side||, atol); a step that makes J <= 0
 is halved up to 5 times before the solve reports failure.

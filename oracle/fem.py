@@ -137,10 +137,11 @@ class Problem:
         G = np.einsum("ic,Kqaj->Kqacij", I, ga)                         # grad(N_a e_c)_{ij} = d_ic g_a,j
         Gs = 0.5 * (G + np.swapaxes(G, -1, -2))                           # grad^s(N_a e_c)
         w = self.tab.w * self.h**d
-        CGs = np.einsum("Kqijkl,Kqbekl->Kqijbe", JC, Gs)                # JC : grad^s(N_b e_e)
-        mat = np.einsum("Kqacij,Kqijbe,q->Kacbe", Gs, CGs, w)
-        Gt = np.einsum("Kqbeim,Kqmj->Kqbeij", G, tau)                   # grad(N_b e_e) . tau
-        geo = np.einsum("Kqacij,Kqbeij,q->Kacbe", G, Gt, w)
+        # (optimize=True only lets numpy pick the contraction order of these library contractions)
+        CGs = np.einsum("Kqijkl,Kqbekl->Kqijbe", JC, Gs, optimize=True)  # JC : grad^s(N_b e_e)
+        mat = np.einsum("Kqacij,Kqijbe,q->Kacbe", Gs, CGs, w, optimize=True)
+        Gt = np.einsum("Kqbeim,Kqmj->Kqbeij", G, tau, optimize=True)    # grad(N_b e_e) . tau
+        geo = np.einsum("Kqacij,Kqbeij,q->Kacbe", G, Gt, w, optimize=True)
         nloc = self.cell_dofs.shape[1]
         return (mat + geo).reshape(len(cells), nloc, nloc)
 

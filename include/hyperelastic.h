@@ -121,7 +121,8 @@ typedef struct {
   double coarse_reduction;  /* [1e-3] residual reduction of the coarse Chebyshev solve */
   int coarse_solver;        /* [0] 0 = Chebyshev as a solver (Sec. 7); 1 = exact: the coarsest tangent
                                assembled densely and inverted (Gauss-Jordan) once per linearisation,
-                               applied as one matrix-vector product (coarsest level <= 6000 dofs) */
+                               applied as one matrix-vector product (coarsest level <= 6000 dofs;
+                               degrees 1-3 in 3D, 1-4 in 2D) */
 } hy_solver_params;
 
 hy_status hy_set_solver_params(hy_ctx *ctx, const hy_solver_params *p);
@@ -199,9 +200,10 @@ hy_status hy_dot_noalloc(int device, void *cuda_stream, const double *a_dev, con
                          double *result);
 
 /* Device bytes a context will own for this problem after mesh setup and set_displacement (the
- * admission measure of the solve server); pure host arithmetic, no GPU needed. */
+ * admission measure of the solve server); pure host arithmetic, no GPU needed. face_masks[2*dim]
+ * (may be NULL: then an upper bound) fixes the free dofs of an exact coarse solve. */
 hy_status hy_footprint(int dim, int degree, int cells_per_dir, int n_levels, hy_variant variant,
-                       hy_dtype level_dtype, int coarse_solver, int64_t *bytes);
+                       hy_dtype level_dtype, int coarse_solver, const uint32_t *face_masks, int64_t *bytes);
 
 /* Device bytes currently owned by the context (its hierarchy, caches and work vectors). */
 hy_status hy_ctx_bytes(const hy_ctx *ctx, int64_t *bytes);

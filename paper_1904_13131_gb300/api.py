@@ -108,7 +108,7 @@ def load_library(path: str = LIB_PATH):
         "hy_dot": [vp, vp, vp, i64, ctypes.POINTER(dbl)],
         "hy_kernel_launches": [vp, ctypes.POINTER(i64)],
         "hy_dot_noalloc": [i32, vp, vp, vp, i64, ctypes.POINTER(dbl)],
-        "hy_footprint": [i32, i32, i32, i32, i32, i32, i32, ctypes.POINTER(i64)],
+        "hy_footprint": [i32, i32, i32, i32, i32, i32, i32, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(i64)],
         "hy_ctx_bytes": [vp, ctypes.POINTER(i64)],
         "hy_server_create": [ctypes.POINTER(vp), i32, i64, i32],
         "hy_server_destroy": [vp],
@@ -358,11 +358,13 @@ def dot_noalloc(a, b, device: int = 0, stream=None) -> float:
     return out.value
 
 
-def footprint(dim, degree, cells_per_dir, n_levels, variant="T4", level_dtype=F64, coarse_solver=0) -> int:
+def footprint(dim, degree, cells_per_dir, n_levels, variant="T4", level_dtype=F64, coarse_solver=0,
+              face_masks=None) -> int:
     """Device bytes a context needs for this problem (host arithmetic, no GPU)."""
     b = ctypes.c_int64()
+    fm = None if face_masks is None else (ctypes.c_uint32 * 6)(*[int(x) for x in list(face_masks) + [0] * 6][:6])
     st = load_library().hy_footprint(dim, degree, cells_per_dir, n_levels, VARIANTS[variant], level_dtype, coarse_solver,
-                                     ctypes.byref(b))
+                                     fm, ctypes.byref(b))
     if st != 0:
         raise HyError(st, "hy_footprint")
     return b.value

@@ -162,9 +162,13 @@ struct Level {
   double lmax = 0.0;
   double* w64[5] = {};  // V-cycle vectors b, x, r, d, t
   float* w32[5] = {};
-  double* d_Ainv = nullptr;  // exact coarse solve: dense inverse of the constrained tangent
-  double* d_gjR = nullptr;
-  double* d_gjC = nullptr;
+  double* d_Ainv = nullptr;  // exact coarse solve: dense free-dof tangent / its inverse (ping-pong pair)
+  double* d_Awork = nullptr;
+  double* d_inv_piv = nullptr;
+  int* d_free_idx = nullptr;  // compact index -> dof
+  int* d_cidx = nullptr;      // dof -> compact index or -1
+  long long nfree = 0;
+  double* d_Aresult = nullptr;  // whichever of the pair holds the inverse
 };
 
 struct Transfer {  // level l-1 (coarse) <-> l (fine); the same 1D tables act along every axis
@@ -196,6 +200,10 @@ struct hy_ctx {
   double* d_partials = nullptr;
   double* d_scal = nullptr;
   double* d_face = nullptr;
+  double* d_eig_scal = nullptr;  // eigenvalue-estimate scalars (8 doubles)
+  double* d_eig_hist = nullptr;  // alpha and beta history
+  size_t eig_hist_len = 0;
+  long long coarse_nfree = 0;    // free dofs of the coarsest level
   double *tmp64a = nullptr, *tmp64b = nullptr;
   float *tmp32a = nullptr, *tmp32b = nullptr, *tmp32c = nullptr;
   size_t tmp_len = 0;
@@ -287,6 +295,9 @@ void free_mesh(hy_ctx* ctx) {
   ctx->d_partials = nullptr;
   ctx->d_scal = nullptr;
   ctx->d_face = nullptr;
+  ctx->d_eig_scal = nullptr;
+  ctx->d_eig_hist = nullptr;
+  ctx->eig_hist_len = 0;
   ctx->tmp64a = ctx->tmp64b = nullptr;
   ctx->tmp32a = ctx->tmp32b = ctx->tmp32c = nullptr;
   for (auto& p : ctx->f64) p = nullptr;
@@ -501,7 +512,8 @@ hy_status vcycle_level(hy_ctx* ctx, int l) {
   if (l == 0) {
     Level& L = ctx->lev[0];
     if (ctx->sp.coarse_solver == 1) {
-      launch_dense_gemv(L.d_Ainv, L.w64[0], L.w64[1], L.ndofs, ctx->stream);
+      HY_CK(cudaMemsetAsync(L.w64[1], 0, sizeof(double) * L.ndofs, ctx->stream));
+      if (L.nfree) launch_dense_gemv(L.d_Aresult, L.w64[0], L.w64[1], L.nfree, L.d_free_idx, ctx->stream);
       return check_launch(ctx, 1);
     }
     return chebyshev<double>(ctx, 0, L.w64[0], L.w64[1], true, ctx->coarse_deg, ctx->coarse_lo, ctx->coarse_hi);
@@ -578,39 +590,48 @@ hy_status eig_estimate(hy_ctx* ctx, int l, int iters, double& lmin, double& lmax
   T* q = wvec<T>(L, 4);
   T* p = wvec<T>(L, 1);
   const T* dinv = dinv_of<T>(L);
+  if ((long long)ctx->eig_hist_len < 2LL * iters) return fail(ctx, HY_ERR_STATE, "eigenvalue history too short");
+  double* sc = ctx->d_eig_scal;  // {rz, rz0, pq, rzn, alpha, beta, stopped, count}
+  double* hist = ctx->d_eig_hist;
   launch_splitmix<T>(r, L.ndofs, (unsigned long long)l, ctx->stream);
   launch_zero_constrained<T>(r, L.nnodes, ctx->dim, L.g, ctx->stream);
   launch_mul<T>(dinv, r, z, L.ndofs, ctx->stream);
   HY_CK(cudaMemcpyAsync(p, z, sizeof(T) * L.ndofs, cudaMemcpyDeviceToDevice, ctx->stream));
-  HY_TRY(check_launch(ctx, 3));
-  double rz, rz0;
-  HY_TRY(dot<T>(ctx, r, z, L.ndofs, &rz));
-  rz0 = rz;
-  std::vector<double> al, be;
+  HY_CK(cudaMemsetAsync(sc, 0, sizeof(double) * 8, ctx->stream));
+  launch_dot<T>(r, z, L.ndofs, ctx->d_partials, sc + 0, ctx->stream);  // rz
+  HY_CK(cudaMemcpyAsync(sc + 1, sc + 0, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));  // rz0
+  HY_TRY(check_launch(ctx, 5));
+  // CG iterations with every scalar on the device; the coefficient history comes back once at the end
   for (int it = 0; it < iters; ++it) {
     HY_TRY(vmult<T>(ctx, l, p, q));
-    double pq;
-    HY_TRY(dot<T>(ctx, p, q, L.ndofs, &pq));
-    const double alpha = rz / pq;
-    launch_axpby<T>(T(-alpha), q, T(1), r, L.ndofs, ctx->stream);  // r -= alpha q
-    launch_mul<T>(dinv, r, z, L.ndofs, ctx->stream);                 // z = D^{-1} r
-    HY_TRY(check_launch(ctx, 2));
-    double rzn;
-    HY_TRY(dot<T>(ctx, r, z, L.ndofs, &rzn));
-    const double beta = rzn / rz;
-    al.push_back(alpha);
-    be.push_back(beta);
-    if (rzn <= 1e-28 * rz0) break;
-    launch_xpay<T>(z, T(beta), p, p, L.ndofs, ctx->stream);  // p = z + beta p
-    HY_TRY(check_launch(ctx, 1));
-    rz = rzn;
+    launch_dot<T>(p, q, L.ndofs, ctx->d_partials, sc + 2, ctx->stream);  // pq
+    launch_eig_alpha(sc, hist, it, ctx->stream);
+    launch_axpy_dev<T>(sc + 4, -1.0, q, r, L.ndofs, ctx->stream);        // r -= alpha q
+    launch_mul<T>(dinv, r, z, L.ndofs, ctx->stream);                     // z = D^{-1} r
+    launch_dot<T>(r, z, L.ndofs, ctx->d_partials, sc + 3, ctx->stream);  // rzn
+    launch_eig_beta(sc, hist, it, iters, ctx->stream);
+    launch_xpay_dev<T>(z, sc + 5, p, p, L.ndofs, ctx->stream);           // p = z + beta p
+    HY_TRY(check_launch(ctx, 9));
+    if ((it & 31) == 31 && it + 1 < iters) {  // look at the stop flag now and then (one host sync)
+      double stopped = 0.0;
+      HY_CK(cudaMemcpyAsync(&stopped, sc + 6, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+      HY_CK(cudaStreamSynchronize(ctx->stream));
+      if (stopped != 0.0) break;
+    }
   }
-  const int m = (int)al.size();
+  double hs[8];
+  std::vector<double> hh((size_t)2 * iters);
+  HY_CK(cudaMemcpyAsync(hs, sc, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
+  HY_CK(cudaMemcpyAsync(hh.data(), hist, sizeof(double) * 2 * iters, cudaMemcpyDeviceToHost, ctx->stream));
+  HY_CK(cudaStreamSynchronize(ctx->stream));
+  // iterations taken: up to and including the one whose residual met the stop test
+  int m = (int)hs[7];
+  if (hs[6] == 0.0) m = iters;
   if (m == 0) return fail(ctx, HY_ERR_STATE, "eigenvalue estimate: no iterations");
   std::vector<double> diag(m), off(std::max(m - 1, 1));
   for (int j = 0; j < m; ++j) {
-    diag[j] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
-    if (j + 1 < m) off[j] = std::sqrt(be[j]) / al[j];
+    diag[j] = 1.0 / hh[j] + (j > 0 ? hh[iters + j - 1] / hh[j - 1] : 0.0);
+    if (j + 1 < m) off[j] = std::sqrt(hh[iters + j]) / hh[j];
   }
   tridiag_extremes(diag, off, lmin, lmax);
   return HY_OK;
@@ -667,34 +688,79 @@ hy_status check_error_word(hy_ctx* ctx, const char* where) {
 // pivoting); a pivot <= 0 marks the level as not positive definite, like a negative Ritz value would.
 hy_status coarse_direct_setup(hy_ctx* ctx) {
   Level& C = ctx->lev[0];
-  const long long n = C.ndofs;
-  if (n > 6000) return fail(ctx, HY_ERR_UNSUPPORTED, "exact coarse solve needs a coarsest level of at most 6000 dofs");
+  if (C.ndofs > 6000) return fail(ctx, HY_ERR_UNSUPPORTED, "exact coarse solve needs a coarsest level of at most 6000 dofs");
+  if (ctx->dim == 3 && ctx->k == 4)
+    return fail(ctx, HY_ERR_UNSUPPORTED, "exact coarse solve is built for degrees 1-3 in 3D (1-4 in 2D)");
   if (!C.d_Ainv) {
-    HY_TRY(dalloc(ctx, &C.d_Ainv, (size_t)n * n));
-    HY_TRY(dalloc(ctx, &C.d_gjR, n));
-    HY_TRY(dalloc(ctx, &C.d_gjC, n));
+    // free-dof numbering of the coarsest level (host, from the face masks)
+    std::vector<int> cidx(C.ndofs, -1), fidx;
+    const int Lc = C.g.L;
+    for (long long nd = 0; nd < C.nnodes; ++nd) {
+      const int i0 = (int)(nd % Lc), i1 = (int)((nd / Lc) % Lc), i2 = ctx->dim == 3 ? (int)(nd / ((long long)Lc * Lc)) : 0;
+      uint32_t cm = 0;
+      if (i0 == 0) cm |= C.g.fm[0];
+      if (i0 == Lc - 1) cm |= C.g.fm[1];
+      if (i1 == 0) cm |= C.g.fm[2];
+      if (i1 == Lc - 1) cm |= C.g.fm[3];
+      if (ctx->dim == 3 && i2 == 0) cm |= C.g.fm[4];
+      if (ctx->dim == 3 && i2 == Lc - 1) cm |= C.g.fm[5];
+      for (int c = 0; c < ctx->dim; ++c)
+        if (!((cm >> c) & 1u)) {
+          cidx[nd * ctx->dim + c] = (int)fidx.size();
+          fidx.push_back((int)(nd * ctx->dim + c));
+        }
+    }
+    C.nfree = (long long)fidx.size();
+    const size_t nf = (size_t)std::max<long long>(C.nfree, 1);
+    HY_TRY(dalloc(ctx, &C.d_Ainv, nf * nf));
+    HY_TRY(dalloc(ctx, &C.d_Awork, nf * nf));
+    HY_TRY(dalloc(ctx, &C.d_inv_piv, 32 * 32 + 64 * nf));  // blocked Gauss-Jordan panels
+    HY_TRY(dalloc(ctx, &C.d_free_idx, nf));
+    HY_TRY(dalloc(ctx, &C.d_cidx, C.ndofs));
+    if (C.nfree) HY_CK(cudaMemcpyAsync(C.d_free_idx, fidx.data(), sizeof(int) * C.nfree, cudaMemcpyHostToDevice, ctx->stream));
+    HY_CK(cudaMemcpyAsync(C.d_cidx, cidx.data(), sizeof(int) * C.ndofs, cudaMemcpyHostToDevice, ctx->stream));
+    HY_CK(cudaStreamSynchronize(ctx->stream));
   }
+  const long long n = C.nfree;
+  ctx->coarse_lo = ctx->coarse_hi = 0.0;
+  ctx->coarse_deg = 0;
+  ctx->coarse_spd = true;
+  if (n == 0) return HY_OK;
   HY_CK(cudaMemsetAsync(C.d_Ainv, 0, sizeof(double) * n * n, ctx->stream));
   CellArgs<double> a = cell_args<double>(ctx, C);
   a.u64 = C.d_u64;
-  launch_assemble_dense(ctx->dim, ctx->n, a, C.d_Ainv, n, ctx->stream);
-  launch_dense_constrained_identity(C.d_Ainv, C.nnodes, n, ctx->dim, C.g, ctx->stream);
-  HY_TRY(check_launch(ctx, 2));
+  launch_assemble_dense(ctx->dim, ctx->n, a, C.d_Ainv, n, C.d_cidx, ctx->stream);
+  HY_TRY(check_launch(ctx, 1));
   HY_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
-  for (long long k = 0; k < n; ++k) launch_gj_step(C.d_Ainv, n, k, C.d_gjR, C.d_gjC, ctx->d_err, ctx->stream);
-  HY_TRY(check_launch(ctx, (int)(2 * n)));
+  C.d_Aresult = launch_gj_invert(C.d_Ainv, C.d_Awork, n, C.d_inv_piv, ctx->d_err, ctx->stream);
+  HY_TRY(check_launch(ctx, (int)(3 * ((n + 31) / 32))));
   unsigned h = 0;
   HY_CK(cudaMemcpyAsync(&h, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
   HY_CK(cudaStreamSynchronize(ctx->stream));
   HY_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
+  if (h & (ERRBIT_JNEG | ERRBIT_NAN)) return fail(ctx, HY_ERR_JNEG, "coarse level: J <= 0 at a Gauss point");
   ctx->coarse_spd = !(h & ERRBIT_NONSPD);
-  ctx->coarse_lo = ctx->coarse_hi = 0.0;
-  ctx->coarse_deg = 0;
   return HY_OK;
 }
 
+// Verbose phase timer of set_displacement (synchronises the stream, so only when HY_VERBOSE=1).
+struct PhaseTimer {
+  hy_ctx* ctx;
+  std::chrono::steady_clock::time_point t;
+  explicit PhaseTimer(hy_ctx* c) : ctx(c), t(std::chrono::steady_clock::now()) {}
+  void mark(const char* what) {
+    if (!ctx->verbose) return;
+    cudaStreamSynchronize(ctx->stream);
+    const auto now = std::chrono::steady_clock::now();
+    std::fprintf(stderr, "[hy] set_displacement %-14s %8.3f ms\n", what,
+                 std::chrono::duration<double, std::milli>(now - t).count());
+    t = now;
+  }
+};
+
 hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
   if (ctx->nlev == 0) return fail(ctx, HY_ERR_STATE, "mesh not set up");
+  PhaseTimer pt(ctx);
   for (int l = 0; l < ctx->nlev; ++l)
     if (!ctx->lev[l].mat_set) return fail(ctx, HY_ERR_STATE, "material not set on level " + std::to_string(l));
   if (var < 0 || var > 4) return fail(ctx, HY_ERR_ARG, "variant out of range");
@@ -702,10 +768,24 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
   drop_graph(ctx);
   ctx->var = var;
   ctx->mixed = mixed;
+  {
+    // coefficient history of the eigenvalue estimates: the longest run of this linearisation
+    const long long coarse_it = ctx->sp.coarse_eig_iters > 0 ? std::min<long long>(ctx->coarse_nfree, ctx->sp.coarse_eig_iters)
+                                                              : ctx->coarse_nfree;
+    const long long need = 2 * std::max<long long>({ctx->nlev > 1 ? (long long)ctx->sp.eig_iters : 0,
+                                                     ctx->sp.coarse_solver != 1 ? std::max<long long>(coarse_it, 1) : 0, 1});
+    if ((long long)ctx->eig_hist_len < need) {
+      dfree(ctx, ctx->d_eig_hist);
+      ctx->d_eig_hist = nullptr;
+      HY_TRY(dalloc(ctx, &ctx->d_eig_hist, (size_t)need));
+      ctx->eig_hist_len = (size_t)need;
+    }
+  }
   const int top = ctx->nlev - 1;
   HY_CK(cudaMemcpyAsync(ctx->lev[top].d_u64, u, sizeof(double) * ctx->lev[top].ndofs, cudaMemcpyDeviceToDevice,
                         ctx->stream));
   for (int l = top; l >= 1; --l) HY_TRY(interpolate_down(ctx, l));
+  pt.mark("carry down");
   HY_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
   const unsigned long long one_bits = 0x7FF0000000000000ULL;  // +inf
   HY_CK(cudaMemcpyAsync(ctx->d_jmin, &one_bits, sizeof(one_bits), cudaMemcpyHostToDevice, ctx->stream));
@@ -747,6 +827,7 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
     HY_TRY(check_launch(ctx, (int)need64 + (int)need32));
   }
   HY_TRY(check_error_word(ctx, "set_displacement"));
+  pt.mark("state+diag");
   // eigenvalue estimates (level precision of the V-cycle)
   for (int l = 1; l < ctx->nlev; ++l) {
     double lmin, lmax;
@@ -754,26 +835,11 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
     else HY_TRY(eig_estimate<double>(ctx, l, ctx->sp.eig_iters, lmin, lmax));
     ctx->lev[l].lmax = lmax;
   }
+  pt.mark("smoother eig");
   if (ctx->sp.coarse_solver == 1) {
     HY_TRY(coarse_direct_setup(ctx));
   } else {
-    Level& C = ctx->lev[0];
-    long long nfree = 0;
-    {
-      // count free dofs on the coarsest level on the host from the face masks
-      const int Lc = C.g.L;
-      for (long long nd = 0; nd < C.nnodes; ++nd) {
-        const int i0 = (int)(nd % Lc), i1 = (int)((nd / Lc) % Lc), i2 = ctx->dim == 3 ? (int)(nd / ((long long)Lc * Lc)) : 0;
-        uint32_t cm = 0;
-        if (i0 == 0) cm |= C.g.fm[0];
-        if (i0 == Lc - 1) cm |= C.g.fm[1];
-        if (i1 == 0) cm |= C.g.fm[2];
-        if (i1 == Lc - 1) cm |= C.g.fm[3];
-        if (ctx->dim == 3 && i2 == 0) cm |= C.g.fm[4];
-        if (ctx->dim == 3 && i2 == Lc - 1) cm |= C.g.fm[5];
-        for (int c = 0; c < ctx->dim; ++c) nfree += ((cm >> c) & 1u) ? 0 : 1;
-      }
-    }
+    const long long nfree = ctx->coarse_nfree;
     int it = ctx->sp.coarse_eig_iters > 0 ? (int)std::min<long long>(nfree, ctx->sp.coarse_eig_iters) : (int)nfree;
     if (it < 1) it = 1;
     double lmin, lmax;
@@ -791,6 +857,7 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
       ctx->coarse_deg = std::max(1, (int)std::ceil(std::acosh(1.0 / ctx->sp.coarse_reduction) / std::acosh(sig) - 1e-12));
     }
   }
+  pt.mark("coarse setup");
   if (ctx->verbose) {
     for (int l = 1; l < ctx->nlev; ++l) std::fprintf(stderr, "[hy] level %d lmax %.6e\n", l, ctx->lev[l].lmax);
     std::fprintf(stderr, "[hy] coarse lo %.6e hi %.6e degree %d\n", ctx->coarse_lo, ctx->coarse_hi, ctx->coarse_deg);
@@ -985,6 +1052,23 @@ hy_status hy_mesh_setup(hy_ctx* ctx, int dim, int degree, int m, int n_levels, c
     HY_TRY(dalloc(ctx, &L.d_mat, L.g.ncells));
     max_nd = std::max(max_nd, L.ndofs);
   }
+  {
+    const Level& C = ctx->lev[0];
+    const int Lc = C.g.L;
+    long long nf = 0;
+    for (long long nd = 0; nd < C.nnodes; ++nd) {
+      const int i0 = (int)(nd % Lc), i1 = (int)((nd / Lc) % Lc), i2 = dim == 3 ? (int)(nd / ((long long)Lc * Lc)) : 0;
+      uint32_t cm = 0;
+      if (i0 == 0) cm |= C.g.fm[0];
+      if (i0 == Lc - 1) cm |= C.g.fm[1];
+      if (i1 == 0) cm |= C.g.fm[2];
+      if (i1 == Lc - 1) cm |= C.g.fm[3];
+      if (dim == 3 && i2 == 0) cm |= C.g.fm[4];
+      if (dim == 3 && i2 == Lc - 1) cm |= C.g.fm[5];
+      for (int c = 0; c < dim; ++c) nf += ((cm >> c) & 1u) ? 0 : 1;
+    }
+    ctx->coarse_nfree = nf;
+  }
   // transfer tables
   ctx->tr.assign(n_levels, Transfer());
   size_t tmp_len = 1;
@@ -1076,6 +1160,7 @@ hy_status hy_mesh_setup(hy_ctx* ctx, int dim, int degree, int m, int n_levels, c
   HY_TRY(dalloc(ctx, &ctx->d_partials, DOT_BLOCKS));
   HY_TRY(dalloc(ctx, &ctx->d_scal, 4));
   HY_TRY(dalloc(ctx, &ctx->d_face, 18));
+  HY_TRY(dalloc(ctx, &ctx->d_eig_scal, 8));
   for (int i = 0; i < 10; ++i) HY_TRY(dalloc(ctx, &ctx->f64[i], ctx->lev[n_levels - 1].ndofs));
   HY_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
   HY_CK(cudaStreamSynchronize(ctx->stream));
@@ -1383,7 +1468,7 @@ hy_status hy_dot(hy_ctx* ctx, const double* a, const double* b, int64_t n, doubl
 // Device bytes a context needs for a problem, mirroring the allocations of hy_mesh_setup and
 // hy_set_displacement (requested sizes; the allocator's own rounding comes on top).
 hy_status hy_footprint(int dim, int degree, int m, int n_levels, hy_variant variant, hy_dtype level_dtype,
-                       int coarse_solver, int64_t* bytes) {
+                       int coarse_solver, const uint32_t* face_masks, int64_t* bytes) {
   if (!bytes || (dim != 2 && dim != 3) || degree < 1 || degree > 4 || m < 1 || n_levels < 1) return HY_ERR_ARG;
   if ((int)variant < 0 || (int)variant > 4) return HY_ERR_ARG;
   auto al = [](size_t n, size_t sz) { return std::max<size_t>(n, 1) * sz; };
@@ -1413,7 +1498,7 @@ hy_status hy_footprint(int dim, int degree, int m, int n_levels, hy_variant vari
     tmp_len = std::max(tmp_len, inter);
   }
   total += 2 * al(tmp_len, 8) + 3 * al(tmp_len, 4);
-  total += al(1, 4) + al(1, 8) + al(DOT_BLOCKS, 8) + al(4, 8) + al(18, 8);
+  total += al(1, 4) + al(1, 8) + al(DOT_BLOCKS, 8) + al(4, 8) + al(18, 8) + al(8, 8);
   total += 10 * al(nd[n_levels - 1], 8);
   const int top = n_levels - 1;
   const int cb = cells_per_block(dim, n);
@@ -1425,7 +1510,32 @@ hy_status hy_footprint(int dim, int degree, int m, int n_levels, hy_variant vari
     if (need64) total += al(clen, 8) + al(nd[l], 8) + 5 * al(nd[l], 8);
     if (need32) total += al(clen, 4) + al(nd[l], 4) + al(nd[l], 4) + 5 * al(nd[l], 4);
   }
-  if (coarse_solver == 1) total += al((size_t)nd[0] * nd[0], 8) + 2 * al(nd[0], 8);
+  // free dofs of the coarsest level (all dofs bound them when no masks are given)
+  size_t nf = (size_t)nd[0];
+  {
+    if (face_masks) {
+      nf = 0;
+      const long long Lc = L1[0];
+      const long long nn = nd[0] / dim;
+      for (long long q = 0; q < nn; ++q) {
+        const long long i0 = q % Lc, i1 = (q / Lc) % Lc, i2 = dim == 3 ? q / (Lc * Lc) : 0;
+        uint32_t cm = 0;
+        if (i0 == 0) cm |= face_masks[0];
+        if (i0 == Lc - 1) cm |= face_masks[1];
+        if (i1 == 0) cm |= face_masks[2];
+        if (i1 == Lc - 1) cm |= face_masks[3];
+        if (dim == 3 && i2 == 0) cm |= face_masks[4];
+        if (dim == 3 && i2 == Lc - 1) cm |= face_masks[5];
+        for (int c = 0; c < dim; ++c) nf += ((cm >> c) & 1u) ? 0 : 1;
+      }
+    }
+  }
+  if (coarse_solver == 1) total += 2 * al(nf * nf, 8) + al(32 * 32 + 64 * nf, 8) + al(nf, 4) + al(nd[0], 4);
+  // eigenvalue-estimate history for the default solver parameters (30 smoother iterations, all free
+  // coarse dofs for the Chebyshev coarse solver)
+  total += al((size_t)(2 * std::max<long long>({n_levels > 1 ? 30LL : 0LL,
+                                                coarse_solver != 1 ? std::max<long long>((long long)nf, 1) : 0LL, 1LL})),
+              8);
   *bytes = (int64_t)total;
   return HY_OK;
 }

@@ -104,6 +104,98 @@ struct Pt {
   __device__ __forceinline__ int base(int ax) const { return p - pc[ax] * stride[ax]; }
 };
 
+// This thread's row (or column) of a 1D table along every axis, read from shared memory before the
+// stage that uses it. (Keeping them in registers for the whole kernel was measured on the FP32 action:
+// no gain, more registers.)
+template <int DIM, int N, typename T>
+struct LineCoef {
+  T c[DIM][N];
+  __device__ __forceinline__ void rows(const T (*M)[MAXN], const Pt<DIM, N>& pt) {
+#pragma unroll
+    for (int ax = 0; ax < DIM; ++ax)
+#pragma unroll
+      for (int j = 0; j < N; ++j) c[ax][j] = M[pt.pc[ax]][j];
+  }
+  __device__ __forceinline__ void cols(const T (*M)[MAXN], const Pt<DIM, N>& pt) {
+#pragma unroll
+    for (int ax = 0; ax < DIM; ++ax)
+#pragma unroll
+      for (int j = 0; j < N; ++j) c[ax][j] = M[j][pt.pc[ax]];
+  }
+};
+
+template <int N, int STRIDE, typename T>
+__device__ __forceinline__ T dotline(const T* __restrict__ line, const T (&c)[N], T acc, bool first) {
+#pragma unroll
+  for (int j = 0; j < N; ++j) acc = (first && j == 0) ? c[0] * line[0] : fma(c[j], line[j * STRIDE], acc);
+  return acc;
+}
+
+template <int DIM, int N, typename T>
+__device__ __forceinline__ T line_ax(const T* line, int ax, const LineCoef<DIM, N, T>& k, T acc, bool first) {
+  if (ax == 0) return dotline<N, 1>(line, k.c[0], acc, first);
+  if (ax == 1) return dotline<N, N>(line, k.c[DIM > 1 ? 1 : 0], acc, first);
+  return dotline<N, N * N>(line, k.c[DIM - 1], acc, first);
+}
+
+// Forward sweeps of NCOMP fields (pairs of buffers), coefficients in registers.
+template <int DIM, int N, int NF, typename T>
+__device__ __forceinline__ void sweeps_forward_coef(T* (&src)[NF], T* (&dst)[NF], const Pt<DIM, N>& pt,
+                                                    const LineCoef<DIM, N, T>& kS) {
+  constexpr int NPT = ipow(N, DIM);
+#pragma unroll
+  for (int ax = 0; ax < DIM; ++ax) {
+    const int base = pt.base(ax);
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) dst[f][c * NPT + pt.p] = line_ax<DIM, N>(src[f] + c * NPT + base, ax, kS, T(0), true);
+    __syncthreads();
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      T* t = src[f];
+      src[f] = dst[f];
+      dst[f] = t;
+    }
+  }
+}
+
+template <int DIM, int N, typename T>
+__device__ __forceinline__ void grad_coef(const T* V, const Pt<DIM, N>& pt, const LineCoef<DIM, N, T>& kD, T G[DIM][DIM]) {
+  constexpr int NPT = ipow(N, DIM);
+#pragma unroll
+  for (int c = 0; c < DIM; ++c)
+#pragma unroll
+    for (int J = 0; J < DIM; ++J) G[c][J] = line_ax<DIM, N>(V + c * NPT + pt.base(J), J, kD, T(0), true);
+}
+
+template <int DIM, int N, typename T>
+__device__ __forceinline__ T* backward_coef(const T* bp, T* b0, T* b1, const Pt<DIM, N>& pt,
+                                            const LineCoef<DIM, N, T>& kSt, const LineCoef<DIM, N, T>& kDt) {
+  constexpr int NPT = ipow(N, DIM);
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    T s = T(0);
+#pragma unroll
+    for (int J = 0; J < DIM; ++J) s = line_ax<DIM, N>(bp + (c * DIM + J) * NPT + pt.base(J), J, kDt, s, J == 0);
+    b0[c * NPT + pt.p] = s;
+  }
+  __syncthreads();
+  T* src = b0;
+  T* dst = b1;
+#pragma unroll
+  for (int ax = DIM - 1; ax >= 0; --ax) {
+    const int base = pt.base(ax);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) dst[c * NPT + pt.p] = line_ax<DIM, N>(src + c * NPT + base, ax, kSt, T(0), true);
+    __syncthreads();
+    T* t = src;
+    src = dst;
+    dst = t;
+  }
+  return src;
+}
+
 // Forward sum factorisation for NC components stored [c][NPT] at b0: interpolate to the Gauss
 // points along every axis (S), ping-ponging through b1. Returns the buffer holding the values.
 template <int DIM, int N, int NC, typename T>
@@ -436,41 +528,33 @@ apply_kernel(const CellArgs<T> a) {
     if (NEED_U) bp[c * NPT + pt.p] = w;
   }
   __syncthreads();
+  // coefficient rows of this thread's lines: loaded once (FP32) or before each stage (FP64)
+  constexpr bool HOIST = false;
+  constexpr bool PHYS = (VAR == VAR_FC || NEED_U);  // derivatives in physical units (D / h)
+  LineCoef<DIM, N, T> kS, kD, kSt, kDt;
+  if (HOIST) {
+    kS.rows(s.S, pt);
+    kD.rows(PHYS ? s.Dh : s.D, pt);
+    kSt.cols(s.S, pt);
+    kDt.cols(s.D, pt);
+  }
   // forward: x (and u) to the Gauss points, then collocation derivatives
   T G[DIM][DIM], Gu[DIM][DIM];
+  if (!HOIST) kS.rows(s.S, pt);
   if (NEED_U) {
-    // interpolate both fields in the same stages
-    T* sx = b0; T* dx = b1; T* su = bp; T* du = bp + DIM * NPT;
-#pragma unroll
-    for (int ax = 0; ax < DIM; ++ax) {
-      const int base = pt.base(ax);
-#pragma unroll
-      for (int c = 0; c < DIM; ++c) {
-        T vx, vu;
-        if (ax == 0) {
-          vx = contract<N, 1, false>(sx + c * NPT + base, pt.pc[0], s.S);
-          vu = contract<N, 1, false>(su + c * NPT + base, pt.pc[0], s.S);
-        } else if (ax == 1) {
-          vx = contract<N, N, false>(sx + c * NPT + base, pt.pc[1], s.S);
-          vu = contract<N, N, false>(su + c * NPT + base, pt.pc[1], s.S);
-        } else {
-          vx = contract<N, N * N, false>(sx + c * NPT + base, pt.pc[2], s.S);
-          vu = contract<N, N * N, false>(su + c * NPT + base, pt.pc[2], s.S);
-        }
-        dx[c * NPT + pt.p] = vx;
-        du[c * NPT + pt.p] = vu;
-      }
-      __syncthreads();
-      T* t = sx; sx = dx; dx = t;
-      t = su; su = du; du = t;
-    }
-    colloc_grad<DIM, N>(sx, pt, s.Dh, G);   // physical gradients: Grad x, Grad u
-    colloc_grad<DIM, N>(su, pt, s.Dh, Gu);
+    T* src[2] = {b0, bp};
+    T* dst[2] = {b1, bp + DIM * NPT};
+    sweeps_forward_coef<DIM, N, 2>(src, dst, pt, kS);  // both fields in the same stages
+    if (!HOIST) kD.rows(s.Dh, pt);
+    grad_coef<DIM, N>(src[0], pt, kD, G);   // physical gradients: Grad x, Grad u
+    grad_coef<DIM, N>(src[1], pt, kD, Gu);
     __syncthreads();  // bp is overwritten with the fluxes below
   } else {
-    const T* V = interp_forward<DIM, N, DIM>(b0, b1, pt, s.S);
-    if (VAR == VAR_FC) colloc_grad<DIM, N>(V, pt, s.Dh, G);  // Grad x
-    else colloc_grad<DIM, N>(V, pt, s.D, G);                // d x / d xi (M holds F^{-1}/h)
+    T* src[1] = {b0};
+    T* dst[1] = {b1};
+    sweeps_forward_coef<DIM, N, 1>(src, dst, pt, kS);
+    if (!HOIST) kD.rows(PHYS ? s.Dh : s.D, pt);
+    grad_coef<DIM, N>(src[0], pt, kD, G);  // Grad x (FC) or d x / d xi (T4, T2: M holds F^{-1}/h)
   }
   if (NV > 0) {
     const bool ok = mbar_wait(&bar, 0);
@@ -543,7 +627,11 @@ apply_kernel(const CellArgs<T> a) {
 #pragma unroll
     for (int J = 0; J < DIM; ++J) bp[(c * DIM + J) * NPT + pt.p] = P[c][J];
   __syncthreads();
-  const T* Y = integrate_backward<DIM, N>(bp, b0, b1, pt, s.S, s.D);
+  if (!HOIST) {
+    kSt.cols(s.S, pt);
+    kDt.cols(s.D, pt);
+  }
+  const T* Y = backward_coef<DIM, N>(bp, b0, b1, pt, kSt, kDt);
   if (active) {
 #pragma unroll
     for (int c = 0; c < DIM; ++c)

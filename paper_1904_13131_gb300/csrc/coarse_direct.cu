@@ -1,5 +1,5 @@
 // Exact coarsest-level solve (option; the paper's coarse solver is Chebyshev to a 1e-3 reduction,
-// Sec. 7): the constrained coarse tangent is assembled as a dense FP64 matrix, inverted in place by
+// Sec. 7): the coarse tangent restricted to the free dofs is assembled as a dense FP64 matrix, inverted by
 // Gauss-Jordan elimination (SPD, so no pivoting), and every V-cycle applies the inverse with one
 // matrix-vector product. Worth it because the coarsest level is tiny (a few thousand dofs) while its
 // Chebyshev solve needs hundreds of dependent, latency-bound applications per V-cycle.
@@ -14,7 +14,8 @@ namespace {
 // with g_a = F^{-T} Grad N_a: the geometric and material parts of Eq. algebraic_tangent with the
 // neo-Hooke action of Eq. simplified_action (c1 = 2(mu - 2 lambda ln J), c2 = 2 lambda, W = w_q h^d).
 template <int DIM, int N>
-__global__ void assemble_dense_kernel(const CellArgs<double> a, double* __restrict__ Aout, long long ndof) {
+__global__ void assemble_dense_kernel(const CellArgs<double> a, double* __restrict__ Aout, long long nfree,
+                                      const int* __restrict__ cidx) {
   constexpr int NPT = ipow(N, DIM);
   constexpr int NS = nsym(DIM);
   constexpr int NR = NPT * DIM;
@@ -23,6 +24,7 @@ __global__ void assemble_dense_kernel(const CellArgs<double> a, double* __restri
   __shared__ double Mq[DIM * DIM][NPT], tq[NS][NPT], c1q[NPT], c2q[NPT];
   __shared__ long long gdof[NR];
   __shared__ unsigned char cons[NR];
+  extern __shared__ double Gq[];  // [NPT][NPT][DIM]
   __shared__ double mu_s, lam_s;
   const int t = threadIdx.x;
   const int cell = blockIdx.x;
@@ -106,40 +108,37 @@ __global__ void assemble_dense_kernel(const CellArgs<double> a, double* __restri
     c2q[t] = c2;
   }
   __syncthreads();
-  if (t >= NR || cons[t]) return;
-  const int an = t / DIM, c = t % DIM;
-  const int apc[3] = {an % N, (an / N) % N, DIM == 3 ? an / (N * N) : 0};
-  for (int col = 0; col < NR; ++col) {
-    if (cons[col]) continue;
-    const int bn = col / DIM, e = col % DIM;
-    const int bpc[3] = {bn % N, (bn / N) % N, DIM == 3 ? bn / (N * N) : 0};
+  // g_a(q) = F^{-T} Grad N_a at every (node, point) pair of the cell, once, in shared memory
+  for (int item = t; item < NPT * NPT; item += blockDim.x) {
+    const int an = item / NPT, q = item % NPT;
+    const int apc[3] = {an % N, (an / N) % N, DIM == 3 ? an / (N * N) : 0};
+    const int qc[3] = {q % N, (q / N) % N, DIM == 3 ? q / (N * N) : 0};
+    double gr[DIM];
+#pragma unroll
+    for (int J = 0; J < DIM; ++J) {
+      double v = 1.0;
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) v *= (i == J ? Sd : S)[qc[i]][apc[i]];
+      gr[J] = v;
+    }
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      double sa = 0.0;
+#pragma unroll
+      for (int J = 0; J < DIM; ++J) sa = fma(gr[J], Mq[J * DIM + j][q], sa);
+      Gq[(an * NPT + q) * DIM + j] = sa;
+    }
+  }
+  __syncthreads();
+  // one (row, column) pair of the element matrix per work item
+  for (int item = t; item < NR * NR; item += blockDim.x) {
+    const int row = item / NR, col = item % NR;
+    if (cons[row] || cons[col]) continue;
+    const int an = row / DIM, c = row % DIM, bn = col / DIM, e = col % DIM;
     double acc = 0.0;
     for (int q = 0; q < NPT; ++q) {
-      const int qc[3] = {q % N, (q / N) % N, DIM == 3 ? q / (N * N) : 0};
-      double gra[DIM], grb[DIM];  // d N / d xi at q
-#pragma unroll
-      for (int J = 0; J < DIM; ++J) {
-        double va = 1.0, vb = 1.0;
-#pragma unroll
-        for (int i = 0; i < DIM; ++i) {
-          va *= (i == J ? Sd : S)[qc[i]][apc[i]];
-          vb *= (i == J ? Sd : S)[qc[i]][bpc[i]];
-        }
-        gra[J] = va;
-        grb[J] = vb;
-      }
-      double ga[DIM], gb[DIM];
-#pragma unroll
-      for (int j = 0; j < DIM; ++j) {
-        double sa = 0.0, sb = 0.0;
-#pragma unroll
-        for (int J = 0; J < DIM; ++J) {
-          sa = fma(gra[J], Mq[J * DIM + j][q], sa);
-          sb = fma(grb[J], Mq[J * DIM + j][q], sb);
-        }
-        ga[j] = sa;
-        gb[j] = sb;
-      }
+      const double* ga = &Gq[(an * NPT + q) * DIM];
+      const double* gb = &Gq[(bn * NPT + q) * DIM];
       double v = 0.0;
       if (c == e) {
         double geo = 0.0, dotab = 0.0;
@@ -156,88 +155,178 @@ __global__ void assemble_dense_kernel(const CellArgs<double> a, double* __restri
       v = fma(c2q[q], ga[c] * gb[e], v);
       acc += v;
     }
-    atomicAdd(&Aout[gdof[t] * ndof + gdof[col]], acc);
+    atomicAdd(&Aout[(long long)cidx[gdof[row]] * nfree + cidx[gdof[col]]], acc);
   }
 }
 
 template <int DIM, int N>
-void launch_assemble(const CellArgs<double>& a, double* A, long long ndof, cudaStream_t st) {
-  assemble_dense_kernel<DIM, N><<<a.g.ncells, ipow(N, DIM) * DIM, 0, st>>>(a, A, ndof);
+void launch_assemble(const CellArgs<double>& a, double* A, long long nfree, const int* cidx, cudaStream_t st) {
+  constexpr int NPT = ipow(N, DIM);
+  constexpr size_t dyn = sizeof(double) * NPT * NPT * DIM;  // up to 375 KB for Q4 3D: capped below
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(assemble_dense_kernel<DIM, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    attr = true;
+  }
+  const int threads = NPT * DIM < 256 ? 256 : ((NPT * DIM + 31) / 32) * 32;
+  assemble_dense_kernel<DIM, N><<<a.g.ncells, threads, dyn, st>>>(a, A, nfree, cidx);
 }
 
-// Constrained dofs: identity rows and columns (the matrix is zero there before this).
-template <int DIM>
-__global__ void dense_constrained_identity(double* __restrict__ A, long long n_nodes, long long ndof, Geom g) {
-  for (long long nd = blockIdx.x * (long long)blockDim.x + threadIdx.x; nd < n_nodes; nd += (long long)gridDim.x * blockDim.x) {
-    const int i0 = (int)(nd % g.L), i1 = (int)((nd / g.L) % g.L), i2 = DIM == 3 ? (int)(nd / ((long long)g.L * g.L)) : 0;
-    const uint32_t cm = node_cmask<DIM>(g, i0, i1, i2);
-#pragma unroll
-    for (int c = 0; c < DIM; ++c)
-      if ((cm >> c) & 1u) A[(nd * DIM + c) * ndof + nd * DIM + c] = 1.0;
-  }
-}
-
-// Gauss-Jordan step k (in place): R = row k / pivot (R_k = 1 / pivot), C = column k.
-__global__ void gj_prep(const double* __restrict__ A, long long n, long long k, double* __restrict__ R,
-                        double* __restrict__ C, unsigned* err) {
-  const double piv = A[k * n + k];
-  if (blockIdx.x == 0 && threadIdx.x == 0 && !(piv > 0.0)) atomicOr(err, ERRBIT_NONSPD);
-  const double inv = 1.0 / piv;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    C[i] = A[i * n + k];
-    R[i] = (i == k ? 1.0 : A[k * n + i]) * inv;
-  }
-}
-// A_ij <- A_ij - C_i R_j for i != k (column k starts from zero), row k <- R.
-__global__ void gj_update(double* __restrict__ A, long long n, long long k, const double* __restrict__ R,
-                          const double* __restrict__ C) {
-  const long long total = n * n;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long i = idx / n, j = idx % n;
-    if (i == k) A[idx] = R[j];
-    else A[idx] = (j == k ? 0.0 : A[idx]) - C[i] * R[j];
-  }
-}
-
-// x = A b, one warp per row, fixed summation order.
+// x = A b on the free dofs (one warp per row, fixed summation order); b and x are full level vectors
+// indexed through free_idx, whose constrained entries stay zero.
 __global__ void dense_gemv(const double* __restrict__ A, const double* __restrict__ b, double* __restrict__ x,
-                           long long n) {
+                           long long n, const int* __restrict__ free_idx) {
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32;
   const int lane = threadIdx.x % 32;
   if (warp >= n) return;
   const double* row = A + warp * n;
   double s = 0.0;
-  for (long long j = lane; j < n; j += 32) s = fma(row[j], b[j], s);
+  for (long long j = lane; j < n; j += 32) s = fma(row[j], b[free_idx[j]], s);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (lane == 0) x[warp] = s;
+  if (lane == 0) x[free_idx[warp]] = s;
 }
 
 }  // namespace
 
-void launch_assemble_dense(int dim, int n, const CellArgs<double>& a, double* A, long long ndof, cudaStream_t st) {
-  using Fn = void (*)(const CellArgs<double>&, double*, long long, cudaStream_t);
+void launch_assemble_dense(int dim, int n, const CellArgs<double>& a, double* A, long long nfree, const int* cidx,
+                           cudaStream_t st) {
+  using Fn = void (*)(const CellArgs<double>&, double*, long long, const int*, cudaStream_t);
   static const Fn t2[4] = {launch_assemble<2, 2>, launch_assemble<2, 3>, launch_assemble<2, 4>, launch_assemble<2, 5>};
   static const Fn t3[4] = {launch_assemble<3, 2>, launch_assemble<3, 3>, launch_assemble<3, 4>, launch_assemble<3, 5>};
-  (dim == 2 ? t2 : t3)[n - 2](a, A, ndof, st);
+  (dim == 2 ? t2 : t3)[n - 2](a, A, nfree, cidx, st);
 }
 
-void launch_dense_constrained_identity(double* A, long long n_nodes, long long ndof, int dim, const Geom& g,
-                                       cudaStream_t st) {
-  const int grid = (int)std::min<long long>((n_nodes + 255) / 256, 1024);
-  if (dim == 2) dense_constrained_identity<2><<<grid, 256, 0, st>>>(A, n_nodes, ndof, g);
-  else dense_constrained_identity<3><<<grid, 256, 0, st>>>(A, n_nodes, ndof, g);
+// ---- blocked Gauss-Jordan: GJB pivots per pass ------------------------------------------------------
+// For the pivot block K = [k0, k0 + b) of A (old) the pass writes B (new):
+//   B_KK = W = A_KK^{-1},  B_Kj = (W A_K:)_j = Y_j,  B_iK = -(A_iK W) = -X_i,  B_ij = A_ij - A_iK Y_j,
+// the block form of b consecutive single-pivot steps; every element of A is read and written once per b
+// pivots instead of once per pivot.
+constexpr int GJB = 32;
+
+// W = A_KK^{-1} by single-pivot Gauss-Jordan on the b x b block in shared memory (one block); flags a
+// pivot <= 0.
+__global__ void gjb_diag(const double* __restrict__ A, int n, int k0, int b, double* __restrict__ W, unsigned* err) {
+  __shared__ double w[GJB][GJB + 1];
+  __shared__ double rk[GJB], ck[GJB];
+  const int t = threadIdx.x;
+  for (int idx = t; idx < b * b; idx += blockDim.x) w[idx / b][idx % b] = A[(long long)(k0 + idx / b) * n + k0 + idx % b];
+  __syncthreads();
+  for (int k = 0; k < b; ++k) {
+    const double p = w[k][k];
+    if (t == 0 && !(p > 0.0)) atomicOr(err, ERRBIT_NONSPD);
+    const double ip = 1.0 / p;
+    if (t < b) {
+      rk[t] = (t == k ? 1.0 : w[k][t]) * ip;
+      ck[t] = w[t][k];
+    }
+    __syncthreads();
+    for (int idx = t; idx < b * b; idx += blockDim.x) {
+      const int i = idx / b, j = idx % b;
+      w[i][j] = (i == k) ? rk[j] : (j == k ? 0.0 : w[i][j]) - ck[i] * rk[j];
+    }
+    __syncthreads();
+  }
+  for (int idx = t; idx < b * b; idx += blockDim.x) W[idx] = w[idx / b][idx % b];
 }
 
-void launch_gj_step(double* A, long long n, long long k, double* R, double* C, unsigned* err, cudaStream_t st) {
-  gj_prep<<<(int)std::min<long long>((n + 255) / 256, 64), 256, 0, st>>>(A, n, k, R, C, err);
-  gj_update<<<(int)std::min<long long>((n * n + 255) / 256, 152LL * 16), 256, 0, st>>>(A, n, k, R, C);
+// Y = W A_K: (b x n) and X = A_:K W (n x b), one thread per column j (Y) and per row i (X).
+__global__ void gjb_panels(const double* __restrict__ A, int n, int k0, int b, const double* __restrict__ W,
+                           double* __restrict__ Y, double* __restrict__ X) {
+  __shared__ double w[GJB * GJB];
+  for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) w[idx] = W[idx];
+  __syncthreads();
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double col[GJB], row[GJB];
+  for (int m = 0; m < b; ++m) {
+    col[m] = A[(long long)(k0 + m) * n + j];  // A_Kj
+    row[m] = A[(long long)j * n + k0 + m];    // A_jK
+  }
+  for (int r = 0; r < b; ++r) {
+    double y = 0.0, x = 0.0;
+    for (int m = 0; m < b; ++m) {
+      y = fma(w[r * b + m], col[m], y);
+      x = fma(row[m], w[m * b + r], x);
+    }
+    Y[(long long)r * n + j] = y;
+    X[(long long)j * b + r] = x;
+  }
 }
 
-void launch_dense_gemv(const double* A, const double* b, double* x, long long n, cudaStream_t st) {
+// B_ij = A_ij - sum_m A_im Y_mj (i, j outside K); rows K take Y (W on the diagonal block), columns K
+// take -X. 64 x 64 output tile per block, 4 x 4 per thread, the A_:K and Y panels staged in shared memory.
+__global__ void __launch_bounds__(256) gjb_update(const double* __restrict__ A, double* __restrict__ B, int n, int k0,
+                                                  int b, const double* __restrict__ W, const double* __restrict__ Y,
+                                                  const double* __restrict__ X) {
+  __shared__ double sA[64][GJB + 1];
+  __shared__ double sY[GJB][64 + 1];
+  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+  const int t = threadIdx.x;
+  for (int idx = t; idx < 64 * GJB; idx += 256) {
+    const int r = idx / GJB, m = idx % GJB;
+    const int i = i0 + r;
+    sA[r][m] = (i < n && m < b) ? A[(long long)i * n + k0 + m] : 0.0;
+    const int mm = idx / 64, c = idx % 64;
+    const int j = j0 + c;
+    sY[mm][c] = (j < n && mm < b) ? Y[(long long)mm * n + j] : 0.0;
+  }
+  __syncthreads();
+  const int tr = (t / 16) * 4, tc = (t % 16) * 4;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = 0.0;
+  for (int m = 0; m < b; ++m) {
+    double av[4], yv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) av[a] = sA[tr + a][m];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) yv[c] = sY[m][tc + c];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][c] = fma(av[a], yv[c], acc[a][c]);
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = i0 + tr + a;
+    if (i >= n) continue;
+    const bool iK = i >= k0 && i < k0 + b;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = j0 + tc + c;
+      if (j >= n) continue;
+      const bool jK = j >= k0 && j < k0 + b;
+      double v;
+      if (iK) v = jK ? W[(i - k0) * b + (j - k0)] : Y[(long long)(i - k0) * n + j];
+      else v = jK ? -X[(long long)i * b + (j - k0)] : A[(long long)i * n + j] - acc[a][c];
+      B[(long long)i * n + j] = v;
+    }
+  }
+}
+
+// Gauss-Jordan inverse of the SPD n x n matrix in A, ping-ponging with B; returns the buffer that holds
+// the inverse. work: GJB^2 + 2 n GJB doubles.
+double* launch_gj_invert(double* A, double* B, long long n, double* work, unsigned* err, cudaStream_t st) {
+  double* W = work;
+  double* Y = W + GJB * GJB;
+  double* X = Y + (size_t)GJB * n;
+  const dim3 grid((unsigned)((n + 63) / 64), (unsigned)((n + 63) / 64));
+  for (long long k0 = 0; k0 < n; k0 += GJB) {
+    const int b = (int)std::min<long long>(GJB, n - k0);
+    gjb_diag<<<1, 256, 0, st>>>(A, (int)n, (int)k0, b, W, err);
+    gjb_panels<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(A, (int)n, (int)k0, b, W, Y, X);
+    gjb_update<<<grid, 256, 0, st>>>(A, B, (int)n, (int)k0, b, W, Y, X);
+    std::swap(A, B);
+  }
+  return A;
+}
+
+void launch_dense_gemv(const double* A, const double* b, double* x, long long n, const int* free_idx, cudaStream_t st) {
   const long long threads = n * 32;
-  dense_gemv<<<(int)((threads + 255) / 256), 256, 0, st>>>(A, b, x, n);
+  dense_gemv<<<(int)((threads + 255) / 256), 256, 0, st>>>(A, b, x, n, free_idx);
 }
 
 }  // namespace hy

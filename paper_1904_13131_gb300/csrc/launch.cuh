@@ -45,6 +45,12 @@ template <typename T> void launch_cheb_step(const T* t, const T* dinv, T* r, T* 
 template <typename T> void launch_mul(const T* a, const T* b, T* z, long long n, cudaStream_t st);
 // out[i] = SplitMix64 uniform on [-1, 1) at counter i (seeded)
 template <typename T> void launch_splitmix(T* out, long long n, unsigned long long seed, cudaStream_t st);
+// y += sign * (*alpha_dev) x ; z = x + (*beta_dev) y
+template <typename T> void launch_axpy_dev(const double* alpha, double sign, const T* x, T* y, long long n, cudaStream_t st);
+template <typename T> void launch_xpay_dev(const T* x, const double* beta, const T* y, T* z, long long n, cudaStream_t st);
+// device-side scalars of one CG step of the eigenvalue estimate (s: 8 doubles; hist: 2 * iters)
+void launch_eig_alpha(double* s, double* hist, int it, cudaStream_t st);
+void launch_eig_beta(double* s, double* hist, int it, int iters, cudaStream_t st);
 // r = b - t
 template <typename T> void launch_sub(const T* b, const T* t, T* r, long long n, cudaStream_t st);
 // du0 = constrained ? target - u : 0, target from per-face values scaled by factor
@@ -60,12 +66,14 @@ void launch_sweep(const T* in, T* out, int dim, const int Lin[3], const int Lout
                   const T* w, int E, bool add_to_out, const Geom* mask_in, const Geom* mask_out, cudaStream_t st);
 
 // ---- exact coarsest-level solve (coarse_direct.cu) ----------------------------------------------
-// dense constrained tangent of a level, accumulated into A (n x n, zeroed by the caller)
-void launch_assemble_dense(int dim, int n, const CellArgs<double>& a, double* A, long long ndof, cudaStream_t st);
-void launch_dense_constrained_identity(double* A, long long n_nodes, long long ndof, int dim, const Geom& g,
-                                       cudaStream_t st);
-// Gauss-Jordan step k of the in-place inversion (R, C: n-element work vectors); flags a pivot <= 0
-void launch_gj_step(double* A, long long n, long long k, double* R, double* C, unsigned* err, cudaStream_t st);
-void launch_dense_gemv(const double* A, const double* b, double* x, long long n, cudaStream_t st);
+// dense tangent of a level on its free dofs (cidx: dof -> compact index or -1), accumulated into A
+// (nfree x nfree, zeroed by the caller)
+void launch_assemble_dense(int dim, int n, const CellArgs<double>& a, double* A, long long nfree, const int* cidx,
+                           cudaStream_t st);
+// blocked Gauss-Jordan inverse, ping-ponging between A and B; returns the buffer holding the inverse;
+// flags a pivot <= 0 in err; work holds 32*32 + 64 n doubles
+double* launch_gj_invert(double* A, double* B, long long n, double* work, unsigned* err, cudaStream_t st);
+// x[free_idx[i]] = sum_j A_ij b[free_idx[j]]
+void launch_dense_gemv(const double* A, const double* b, double* x, long long n, const int* free_idx, cudaStream_t st);
 
 }  // namespace hy

@@ -139,6 +139,43 @@ __global__ void cheb_step_kernel(const T* __restrict__ t, const T* __restrict__ 
   }
 }
 
+// y += sign * (*alpha) x and z = x + (*beta) y with the coefficient read from device memory, so that an
+// iteration's scalars never travel to the host.
+template <typename T>
+__global__ void axpy_dev_kernel(const double* __restrict__ alpha, double sign, const T* __restrict__ x, T* y,
+                                long long n) {
+  const T a = T(sign * alpha[0]);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] += a * x[i];
+}
+template <typename T>
+__global__ void xpay_dev_kernel(const T* __restrict__ x, const double* __restrict__ beta, const T* y, T* z, long long n) {
+  const T b = T(beta[0]);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    z[i] = x[i] + b * y[i];
+}
+
+// Scalars of one CG step of the eigenvalue estimate, kept on the device. s = {rz, rz0, pq, rzn, alpha,
+// beta, stopped, count}; hist = alpha[iters] followed by beta[iters].
+__global__ void eig_alpha_kernel(double* s, double* hist, int it) {
+  const bool stopped = s[6] != 0.0;
+  const double alpha = stopped ? 0.0 : s[0] / s[2];
+  s[4] = alpha;
+  if (!stopped) hist[it] = alpha;
+}
+__global__ void eig_beta_kernel(double* s, double* hist, int it, int iters) {
+  if (s[6] != 0.0) {
+    s[5] = 0.0;
+    return;
+  }
+  const double beta = s[3] / s[0];
+  hist[iters + it] = beta;
+  s[7] = it + 1;
+  s[5] = beta;
+  s[0] = s[3];
+  if (s[3] <= 1e-28 * s[1]) s[6] = 1.0;
+}
+
 // Deterministic two-stage reduction: each of DOT_BLOCKS blocks sums a fixed strided subset in a
 // fixed tree order; one block then sums the partials in index order.
 template <typename T>
@@ -238,6 +275,18 @@ void launch_splitmix(T* out, long long n, unsigned long long seed, cudaStream_t 
   splitmix_kernel<T><<<grid_for(n), TPB, 0, st>>>(out, n, seed);
 }
 template <typename T>
+void launch_axpy_dev(const double* alpha, double sign, const T* x, T* y, long long n, cudaStream_t st) {
+  axpy_dev_kernel<T><<<grid_for(n), TPB, 0, st>>>(alpha, sign, x, y, n);
+}
+template <typename T>
+void launch_xpay_dev(const T* x, const double* beta, const T* y, T* z, long long n, cudaStream_t st) {
+  xpay_dev_kernel<T><<<grid_for(n), TPB, 0, st>>>(x, beta, y, z, n);
+}
+void launch_eig_alpha(double* s, double* hist, int it, cudaStream_t st) { eig_alpha_kernel<<<1, 1, 0, st>>>(s, hist, it); }
+void launch_eig_beta(double* s, double* hist, int it, int iters, cudaStream_t st) {
+  eig_beta_kernel<<<1, 1, 0, st>>>(s, hist, it, iters);
+}
+template <typename T>
 void launch_sub(const T* b, const T* t, T* r, long long n, cudaStream_t st) {
   sub_kernel<T><<<grid_for(n), TPB, 0, st>>>(b, t, r, n);
 }
@@ -283,6 +332,8 @@ void launch_sweep(const T* in, T* out, int dim, const int Lin[3], const int Lout
   template void launch_xpay<T>(const T*, T, const T*, T*, long long, cudaStream_t);                             \
   template void launch_sub<T>(const T*, const T*, T*, long long, cudaStream_t);                                 \
   template void launch_mul<T>(const T*, const T*, T*, long long, cudaStream_t);                                 \
+  template void launch_axpy_dev<T>(const double*, double, const T*, T*, long long, cudaStream_t);               \
+  template void launch_xpay_dev<T>(const T*, const double*, const T*, T*, long long, cudaStream_t);             \
   template void launch_splitmix<T>(T*, long long, unsigned long long, cudaStream_t);                            \
   template void launch_cheb_init<T>(const T*, const T*, const T*, T*, T*, T*, T, bool, long long, cudaStream_t); \
   template void launch_cheb_step<T>(const T*, const T*, T*, T*, T*, T, T, long long, cudaStream_t);             \

@@ -38,7 +38,7 @@ def test_footprint_matches_context_allocation():
         with context(pr) as ctx:
             ctx.set_solver_params(coarse_solver=cs)
             ctx.set_displacement(torch.zeros(ctx.num_dofs(), dtype=torch.float64, device="cuda"), "T4", ldt)
-            assert ctx.bytes() == api.footprint(dim, k, m, L, "T4", ldt, cs)
+            assert ctx.bytes() == api.footprint(dim, k, m, L, "T4", ldt, cs, face_masks=pr["masks"])
 
 
 def test_results_alone_and_in_the_mix_agree():

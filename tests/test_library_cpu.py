@@ -52,8 +52,14 @@ def test_footprint_is_host_arithmetic(lib):
     bmx = api.footprint(3, 2, 32, 4, level_dtype=api.F32)
     bex = api.footprint(3, 2, 32, 4, level_dtype=api.F32, coarse_solver=1)
     assert 0 < b64 < bmx < bex
-    n0 = 3 * 9**3  # 4^3 Q2 coarsest level
-    assert bex - bmx == 8 * n0 * n0 + 16 * n0
+    n0 = 3 * 9**3  # 4^3 Q2 coarsest level: without masks the exact coarse solve is bounded by all its dofs
+    # exact coarse: dense pair + pivots + index maps, and the eigen history shrinks to the smoother's 2*30
+    assert bex - bmx == 2 * 8 * n0 * n0 + 8 * (1024 + 64 * n0) + 4 * n0 + 4 * n0 + 8 * (60 - 2 * n0)
+    masks = [0, 0, 0, 0, 7, 4]  # bottom clamped, top normal: 9*9*3 + 9*9 constrained coarse dofs
+    nf = n0 - 9 * 9 * 4
+    bmm = api.footprint(3, 2, 32, 4, level_dtype=api.F32, face_masks=masks)
+    bfm = api.footprint(3, 2, 32, 4, level_dtype=api.F32, coarse_solver=1, face_masks=masks)
+    assert bfm - bmm == 2 * 8 * nf * nf + 8 * (1024 + 64 * nf) + 4 * nf + 4 * n0 + 8 * (60 - 2 * nf)
     assert api.footprint(3, 2, 64, 5) > 7 * b64
     with pytest.raises(api.HyError):
         api.footprint(3, 5, 32, 4)

@@ -652,8 +652,9 @@ hy_status ensure_level_vectors(hy_ctx* ctx, int l, bool f32) {
 template <typename TOUT>
 hy_status build_cache(hy_ctx* ctx, int l, int var) {
   Level& L = ctx->lev[l];
-  const size_t nblocks = (size_t)((L.g.ncells + cells_per_block(ctx->dim, ctx->n) - 1) / cells_per_block(ctx->dim, ctx->n));
-  const size_t len = std::max<size_t>(1, (size_t)cache_values(var, ctx->dim) * cache_row(ctx->dim, ctx->n) * nblocks);
+  const int cb = layout_cells<TOUT>(ctx->dim, ctx->n);
+  const size_t nblocks = (size_t)((L.g.ncells + cb - 1) / cb);
+  const size_t len = std::max<size_t>(1, (size_t)cache_values(var, ctx->dim) * layout_row<TOUT>(ctx->dim, ctx->n) * nblocks);
   TOUT*& buf = *reinterpret_cast<TOUT**>(sizeof(TOUT) == 8 ? (void*)&L.d_c64 : (void*)&L.d_c32);
   size_t& cur = sizeof(TOUT) == 8 ? L.c64_len : L.c32_len;
   if (cur < len) {
@@ -1501,14 +1502,16 @@ hy_status hy_footprint(int dim, int degree, int m, int n_levels, hy_variant vari
   total += al(1, 4) + al(1, 8) + al(DOT_BLOCKS, 8) + al(4, 8) + al(18, 8) + al(8, 8);
   total += 10 * al(nd[n_levels - 1], 8);
   const int top = n_levels - 1;
-  const int cb = cells_per_block(dim, n);
   for (int l = 0; l < n_levels; ++l) {
     const bool need64 = (l == top) || (l == 0) || !mixed;
     const bool need32 = mixed && (l > 0 || l == top);
-    const size_t nblocks = (size_t)((nc[l] + cb - 1) / cb);
-    const size_t clen = std::max<size_t>(1, (size_t)cache_values((int)variant, dim) * cache_row(dim, n) * nblocks);
-    if (need64) total += al(clen, 8) + al(nd[l], 8) + 5 * al(nd[l], 8);
-    if (need32) total += al(clen, 4) + al(nd[l], 4) + al(nd[l], 4) + 5 * al(nd[l], 4);
+    const int cb64 = layout_cells<double>(dim, n), cb32 = layout_cells<float>(dim, n);
+    const size_t clen64 = std::max<size_t>(1, (size_t)cache_values((int)variant, dim) * layout_row<double>(dim, n) *
+                                                  (size_t)((nc[l] + cb64 - 1) / cb64));
+    const size_t clen32 = std::max<size_t>(1, (size_t)cache_values((int)variant, dim) * layout_row<float>(dim, n) *
+                                                  (size_t)((nc[l] + cb32 - 1) / cb32));
+    if (need64) total += al(clen64, 8) + al(nd[l], 8) + 5 * al(nd[l], 8);
+    if (need32) total += al(clen32, 4) + al(nd[l], 4) + al(nd[l], 4) + 5 * al(nd[l], 4);
   }
   // free dofs of the coarsest level (all dofs bound them when no masks are given)
   size_t nf = (size_t)nd[0];

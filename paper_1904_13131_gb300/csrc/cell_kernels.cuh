@@ -15,6 +15,10 @@
 #pragma once
 #include "hy_internal.cuh"
 
+#ifndef HY_LINE_STAGE
+#define HY_LINE_STAGE 1
+#endif
+
 namespace hy {
 
 template <typename T>
@@ -485,6 +489,69 @@ struct CellLoc {
 };
 
 // ------------------------------------------------------------------------------------------------
+// Flux P~ at one Gauss point from the gradient G of x (and Gu of the displacement for SC/NC), the point's
+// cache entries (row stride st, entry qg of the shared-memory chunk cs) and the material, per variant:
+//   T4: P~ = (g tau~ + JC~ : sym g) M^T, g = G M with M = F^{-1}/h, tau~, JC~ cached   (Algorithm 3)
+//   T2: the same with JC~ : s = c1~ s + c2~ tr(s) I                                     (Algorithm 2)
+//   FC/SC/NC: the state recomputed from F (cached, or I + Grad u), with g' = Grad x adj F (Algorithm 1 for SC).
+template <int DIM, int VAR, typename T>
+__device__ __forceinline__ void qp_flux(const T G[DIM][DIM], const T Gu[DIM][DIM], const T* __restrict__ cs, int st,
+                                        int qg, bool active, int id, const T* mu, const T* lam, T Wh, T P[DIM][DIM]) {
+  constexpr int NS = nsym(DIM);
+  T M[DIM][DIM], tau[NS], Sv[NS], g[DIM][DIM];
+  if (VAR == VAR_T4 || VAR == VAR_T2) {
+#pragma unroll
+    for (int i = 0; i < DIM * DIM; ++i) M[i / DIM][i % DIM] = active ? cs[i * st + qg] : T(0);
+#pragma unroll
+    for (int i = 0; i < NS; ++i) tau[i] = active ? cs[(DIM * DIM + i) * st + qg] : T(0);
+    matmul<DIM>(G, M, g);
+    if (VAR == VAR_T4) {
+      constexpr int OFF = DIM * DIM + NS;
+      T v[NS];
+#pragma unroll
+      for (int al = 0; al < NS; ++al) {
+        const int i = vi<DIM>(al), j = vj<DIM>(al);
+        v[al] = (i == j) ? g[i][i] : g[i][j] + g[j][i];
+      }
+#pragma unroll
+      for (int al = 0; al < NS; ++al) {
+        T acc = T(0);
+#pragma unroll
+        for (int be = 0; be < NS; ++be) {
+          const int lo = al < be ? al : be, hi = al < be ? be : al;
+          const int idx = lo * NS - lo * (lo - 1) / 2 + (hi - lo);  // upper triangle, row major
+          const T cv = active ? cs[(OFF + idx) * st + qg] : T(0);
+          acc = (be == 0) ? cv * v[be] : fma(cv, v[be], acc);
+        }
+        Sv[al] = acc;
+      }
+    } else {
+      const T c1 = active ? cs[(DIM * DIM + NS) * st + qg] : T(0);
+      const T c2 = active ? cs[(DIM * DIM + NS + 1) * st + qg] : T(0);
+      nh_action<DIM>(g, c1, c2, Sv);
+    }
+  } else {
+    T F[DIM][DIM];
+    if (VAR == VAR_FC) {
+#pragma unroll
+      for (int i = 0; i < DIM * DIM; ++i)
+        F[i / DIM][i % DIM] = active ? cs[i * st + qg] : (i % (DIM + 1) == 0 ? T(1) : T(0));
+    } else {
+#pragma unroll
+      for (int i = 0; i < DIM; ++i)
+#pragma unroll
+        for (int J = 0; J < DIM; ++J) F[i][J] = (i == J) ? T(1) + Gu[i][J] : Gu[i][J];
+    }
+    const T cin = (VAR == VAR_SC && active) ? cs[qg] : T(0);
+    T c1, c2;
+    neo_hooke_adj<DIM>(F, mu[id], lam[id], Wh, VAR == VAR_SC, cin, M, tau, c1, c2);  // M = adj
+    matmul<DIM>(G, M, g);
+    nh_action<DIM>(g, c1, c2, Sv);
+  }
+  finish_flux<DIM>(g, tau, Sv, M, P);
+}
+
+// ------------------------------------------------------------------------------------------------
 // Tangent action y += A(u) x on the cells of this block (Eq. mf_vmult), variants:
 //   T4: cache M, tau~, JC~ (Algorithm 3)            T2: cache M, tau~, c1~, c2~ (Algorithm 2)
 //   FC: cache F, recompute the neo-Hooke state      SC: cache mu - 2 lambda ln J, recompute F (Algorithm 1)
@@ -566,62 +633,7 @@ apply_kernel(const CellArgs<T> a) {
   }
   // quadrature-point work
   T P[DIM][DIM];
-  {
-    const int qg = threadIdx.x;
-    constexpr int st = BS;
-    T M[DIM][DIM], tau[NS], Sv[NS], g[DIM][DIM];
-    if (VAR == VAR_T4 || VAR == VAR_T2) {
-#pragma unroll
-      for (int i = 0; i < DIM * DIM; ++i) M[i / DIM][i % DIM] = active ? cs[i * st + qg] : T(0);
-#pragma unroll
-      for (int i = 0; i < NS; ++i) tau[i] = active ? cs[(DIM * DIM + i) * st + qg] : T(0);
-      matmul<DIM>(G, M, g);
-      if (VAR == VAR_T4) {
-        constexpr int OFF = DIM * DIM + NS;
-        T v[NS];
-#pragma unroll
-        for (int al = 0; al < NS; ++al) {
-          const int i = vi<DIM>(al), j = vj<DIM>(al);
-          v[al] = (i == j) ? g[i][i] : g[i][j] + g[j][i];
-        }
-#pragma unroll
-        for (int al = 0; al < NS; ++al) {
-          T acc = T(0);
-#pragma unroll
-          for (int be = 0; be < NS; ++be) {
-            const int lo = al < be ? al : be, hi = al < be ? be : al;
-            const int idx = lo * NS - lo * (lo - 1) / 2 + (hi - lo);  // upper triangle, row major
-            const T cv = active ? cs[(OFF + idx) * st + qg] : T(0);
-            acc = (be == 0) ? cv * v[be] : fma(cv, v[be], acc);
-          }
-          Sv[al] = acc;
-        }
-      } else {
-        const T c1 = active ? cs[(DIM * DIM + NS) * st + qg] : T(0);
-        const T c2 = active ? cs[(DIM * DIM + NS + 1) * st + qg] : T(0);
-        nh_action<DIM>(g, c1, c2, Sv);
-      }
-    } else {
-      T F[DIM][DIM];
-      if (VAR == VAR_FC) {
-#pragma unroll
-        for (int i = 0; i < DIM * DIM; ++i)
-          F[i / DIM][i % DIM] = active ? cs[i * st + qg] : (i % (DIM + 1) == 0 ? T(1) : T(0));
-      } else {
-#pragma unroll
-        for (int i = 0; i < DIM; ++i)
-#pragma unroll
-          for (int J = 0; J < DIM; ++J) F[i][J] = (i == J) ? T(1) + Gu[i][J] : Gu[i][J];
-      }
-      const int id = active ? a.mat[cell] : 0;
-      const T cin = (VAR == VAR_SC && active) ? cs[qg] : T(0);
-      T c1, c2;
-      neo_hooke_adj<DIM>(F, s.mu[id], s.lam[id], s.Wh[pt.p], VAR == VAR_SC, cin, M, tau, c1, c2);  // M = adj
-      matmul<DIM>(G, M, g);
-      nh_action<DIM>(g, c1, c2, Sv);
-    }
-    finish_flux<DIM>(g, tau, Sv, M, P);
-  }
+  qp_flux<DIM, VAR>(G, Gu, cs, BS, threadIdx.x, active, active ? a.mat[cell] : 0, s.mu, s.lam, s.Wh[pt.p], P);
 #pragma unroll
   for (int c = 0; c < DIM; ++c)
 #pragma unroll
@@ -637,6 +649,296 @@ apply_kernel(const CellArgs<T> a) {
     for (int c = 0; c < DIM; ++c)
       if (!((loc.cmask >> c) & 1u)) atomicAdd(&a.y[(long long)loc.node * DIM + c], Y[c * NPT + pt.p]);
   }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Tangent action, one thread per x-line of a cell (the FP32 form). The thread holds the (k+1) nodes of its
+// line, and later its (k+1) Gauss points, in registers: sweeps and derivatives along x need no shared
+// memory, and gather and scatter touch one contiguous run of (k+1)*dim values. The y and z sweeps exchange
+// values through shared memory, the thread playing the line (q0 varies; q1 = l1, q2 = l2) of each stage.
+// Same arithmetic, variants and Dirichlet treatment as apply_kernel.
+template <int DIM, int N, int VAR, typename T>
+__global__ void __launch_bounds__(cells_per_block_line(DIM, N) * ipow(N, DIM - 1))
+apply_line_kernel(const CellArgs<T> a) {
+  constexpr int NPT = ipow(N, DIM);
+  constexpr int NLC = ipow(N, DIM - 1);
+  constexpr int CB = cells_per_block_line(DIM, N);
+  constexpr int K = N - 1;
+  constexpr bool NEED_U = (VAR == VAR_NC || VAR == VAR_SC);
+  constexpr bool PHYS = (VAR == VAR_FC || NEED_U);
+  constexpr int NV = cache_values(VAR, DIM);
+  constexpr int BS = cache_row_line(DIM, N);
+  constexpr int NU = NEED_U ? CB : 1;
+  __shared__ T tS[MAXN][MAXN], tD[MAXN][MAXN], tDh[MAXN][MAXN], tWh[NPT], tmu[MAXMAT], tlam[MAXMAT];
+  __shared__ T buf0[CB][DIM][NPT], buf1[CB][DIM][NPT];
+  __shared__ T ubuf0[NU][DIM][NPT], ubuf1[NU][DIM][NPT];
+  __shared__ T flux[CB][DIM][DIM - 1][NPT];
+  __shared__ __align__(8) unsigned long long bar;
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
+  T* cs = reinterpret_cast<T*>(dyn_smem);
+  const int t = threadIdx.x;
+  // STAGE: the block's cache chunk streams into shared memory with one bulk copy (measured faster for
+  // T4 than reading the cache straight from global memory at the Gauss points, 18.3 vs 12.9 GDoF/s).
+  constexpr bool STAGE = HY_LINE_STAGE;
+  const T* cg = a.cache + (size_t)blockIdx.x * NV * BS;
+  if (STAGE && NV > 0 && t == 0) {
+    mbar_init(&bar, 1);
+    bulk_load(cs, cg, (unsigned)(NV * BS * sizeof(T)), &bar);
+  }
+  // tables (strided loops: a block may have fewer threads than entries)
+  for (int i = t; i < MAXN * MAXN; i += blockDim.x) {
+    tS[i / MAXN][i % MAXN] = a.b.S[i / MAXN][i % MAXN];
+    tD[i / MAXN][i % MAXN] = a.b.D[i / MAXN][i % MAXN];
+    tDh[i / MAXN][i % MAXN] = a.b.D[i / MAXN][i % MAXN] * T(a.g.inv_h);
+  }
+  for (int i = t; i < NPT; i += blockDim.x) {
+    const int q0 = i % N, q1 = (i / N) % N, q2 = DIM == 3 ? i / (N * N) : 0;
+    T w = a.b.w[q0] * a.b.w[q1];
+    T hd = T(a.g.h) * T(a.g.h);
+    if (DIM == 3) {
+      w *= a.b.w[q2];
+      hd *= T(a.g.h);
+    }
+    tWh[i] = w * hd * T(a.g.inv_h);
+  }
+  for (int i = t; i < MAXMAT; i += blockDim.x) {
+    tmu[i] = a.mt.mu[i];
+    tlam[i] = a.mt.lam[i];
+  }
+  const int cl = t / NLC, l = t % NLC;
+  const int l1 = l % N, l2 = DIM == 3 ? l / N : 0;
+  const int cell = blockIdx.x * CB + cl;
+  const bool active = cell < a.g.ncells;
+  const int m = a.g.m;
+  const int cc = active ? cell : 0;
+  const int c0 = cc % m, c1 = (cc / m) % m, c2 = DIM == 3 ? cc / (m * m) : 0;
+  const int i1 = K * c1 + l1, i2 = K * c2 + l2;
+  const long long node0 = K * c0 + (long long)a.g.L * (i1 + (DIM == 3 ? (long long)a.g.L * i2 : 0));
+  uint32_t cms[N];
+  T v[N][DIM], vu[N][DIM];
+#pragma unroll
+  for (int a0 = 0; a0 < N; ++a0) {
+    cms[a0] = node_cmask<DIM>(a.g, K * c0 + a0, i1, i2);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      const long long dof = (node0 + a0) * DIM + c;
+      v[a0][c] = (active && !((cms[a0] >> c) & 1u)) ? a.x[dof] : T(0);
+      vu[a0][c] = (NEED_U && active) ? a.ubar[dof] : T(0);
+    }
+  }
+  __syncthreads();
+  // x: interpolation to the Gauss points of the line, in registers
+  T X[N][DIM], XU[N][DIM];
+#pragma unroll
+  for (int q = 0; q < N; ++q)
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      T sx = T(0), su = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        sx = fma(tS[q][j], v[j][c], sx);
+        if (NEED_U) su = fma(tS[q][j], vu[j][c], su);
+      }
+      X[q][c] = sx;
+      XU[q][c] = su;
+    }
+  // y (and z): through shared memory
+  T V[N][DIM], VU[N][DIM];
+#pragma unroll
+  for (int q = 0; q < N; ++q)
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      buf0[cl][c][q + N * l] = X[q][c];
+      if (NEED_U) ubuf0[NEED_U ? cl : 0][c][q + N * l] = XU[q][c];
+    }
+  __syncthreads();
+  if (DIM == 3) {
+    // y: this thread plays (q1 = l1, a2 = l2)
+#pragma unroll
+    for (int q = 0; q < N; ++q)
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        T sx = T(0), su = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          sx = fma(tS[l1][j], buf0[cl][c][q + N * (j + N * l2)], sx);
+          if (NEED_U) su = fma(tS[l1][j], ubuf0[NEED_U ? cl : 0][c][q + N * (j + N * l2)], su);
+        }
+        buf1[cl][c][q + N * l] = sx;
+        if (NEED_U) ubuf1[NEED_U ? cl : 0][c][q + N * l] = su;
+      }
+    __syncthreads();
+    // z: (q1 = l1, q2 = l2)
+#pragma unroll
+    for (int q = 0; q < N; ++q)
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        T sx = T(0), su = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          sx = fma(tS[l2][j], buf1[cl][c][q + N * (l1 + N * j)], sx);
+          if (NEED_U) su = fma(tS[l2][j], ubuf1[NEED_U ? cl : 0][c][q + N * (l1 + N * j)], su);
+        }
+        V[q][c] = sx;
+        VU[q][c] = su;
+      }
+  } else {
+#pragma unroll
+    for (int q = 0; q < N; ++q)
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        T sx = T(0), su = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          sx = fma(tS[l1][j], buf0[cl][c][q + N * j], sx);
+          if (NEED_U) su = fma(tS[l1][j], ubuf0[NEED_U ? cl : 0][c][q + N * j], su);
+        }
+        V[q][c] = sx;
+        VU[q][c] = su;
+      }
+  }
+  // values at the Gauss points of the line go to shared memory for the y/z derivatives of the others
+  // (3D: buf0 was last read before the previous barrier; 2D: buf1 is unused so far)
+  T (*vb)[DIM][NPT] = DIM == 3 ? buf0 : buf1;
+  T (*vub)[DIM][NPT] = DIM == 3 ? ubuf0 : ubuf1;
+#pragma unroll
+  for (int q = 0; q < N; ++q)
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      vb[cl][c][q + N * l] = V[q][c];
+      if (NEED_U) vub[NEED_U ? cl : 0][c][q + N * l] = VU[q][c];
+    }
+  __syncthreads();
+  if (STAGE && NV > 0) {
+    const bool ok = mbar_wait(&bar, 0);
+    if (__syncthreads_or(!ok)) {
+      if (t == 0) atomicOr(a.err, ERRBIT_TIMEOUT);
+      mbar_wait(&bar, 0);
+      return;
+    }
+  }
+  const T* cq = STAGE ? cs : cg;
+  const T (*Dd)[MAXN] = PHYS ? tDh : tD;
+  const int id = active ? a.mat[cell] : 0;
+  T Px[N][DIM];
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    const int p = q + N * l;
+    T G[DIM][DIM], Gu[DIM][DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      T g0 = T(0), u0 = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        g0 = fma(Dd[q][j], V[j][c], g0);
+        if (NEED_U) u0 = fma(Dd[q][j], VU[j][c], u0);
+      }
+      G[c][0] = g0;
+      Gu[c][0] = u0;
+      T g1 = T(0), u1 = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const int pj = DIM == 3 ? q + N * (j + N * l2) : q + N * j;
+        g1 = fma(Dd[l1][j], vb[cl][c][pj], g1);
+        if (NEED_U) u1 = fma(Dd[l1][j], vub[NEED_U ? cl : 0][c][pj], u1);
+      }
+      G[c][1] = g1;
+      Gu[c][1] = u1;
+      if (DIM == 3) {
+        T g2 = T(0), u2 = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          g2 = fma(Dd[l2][j], vb[cl][c][q + N * (l1 + N * j)], g2);
+          if (NEED_U) u2 = fma(Dd[l2][j], vub[NEED_U ? cl : 0][c][q + N * (l1 + N * j)], u2);
+        }
+        G[c][DIM - 1] = g2;
+        Gu[c][DIM - 1] = u2;
+      }
+    }
+    T P[DIM][DIM];
+    qp_flux<DIM, VAR>(G, Gu, cq, BS, cl * NPT + p, active, id, tmu, tlam, tWh[p], P);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      Px[q][c] = P[c][0];
+#pragma unroll
+      for (int J = 1; J < DIM; ++J) flux[cl][c][J - 1][p] = P[c][J];
+    }
+  }
+  __syncthreads();
+  // transposed derivatives summed over the directions: x from registers, y/z from shared memory
+  T Wq[N][DIM];
+#pragma unroll
+  for (int q = 0; q < N; ++q)
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      T s = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) s = fma(tD[j][q], Px[j][c], s);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const int pj = DIM == 3 ? q + N * (j + N * l2) : q + N * j;
+        s = fma(tD[j][l1], flux[cl][c][0][pj], s);
+      }
+      if (DIM == 3) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) s = fma(tD[j][l2], flux[cl][c][DIM - 2][q + N * (l1 + N * j)], s);
+      }
+      Wq[q][c] = s;
+    }
+  // transposed interpolation: z, y through shared memory (buffers free since the flux barrier), x in registers
+  T Yb[N][DIM];
+  if (DIM == 3) {
+#pragma unroll
+    for (int q = 0; q < N; ++q)
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) buf1[cl][c][q + N * l] = Wq[q][c];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < N; ++q)
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {  // z: (q1 = l1, a2 = l2)
+        T sz = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) sz = fma(tS[j][l2], buf1[cl][c][q + N * (l1 + N * j)], sz);
+        buf0[cl][c][q + N * l] = sz;
+      }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < N; ++q)
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {  // y: (a1 = l1, a2 = l2)
+        T sy = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) sy = fma(tS[j][l1], buf0[cl][c][q + N * (j + N * l2)], sy);
+        Yb[q][c] = sy;
+      }
+  } else {
+#pragma unroll
+    for (int q = 0; q < N; ++q)
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) buf0[cl][c][q + N * l] = Wq[q][c];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < N; ++q)
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        T sy = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) sy = fma(tS[j][l1], buf0[cl][c][q + N * j], sy);
+        Yb[q][c] = sy;
+      }
+  }
+  if (!active) return;
+#pragma unroll
+  for (int a0 = 0; a0 < N; ++a0)
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      if ((cms[a0] >> c) & 1u) continue;
+      T s = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) s = fma(tS[j][a0], Yb[j][c], s);
+      atomicAdd(&a.y[(node0 + a0) * DIM + c], s);
+    }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -680,10 +982,11 @@ qp_state_kernel(const CellArgs<double> a, T* __restrict__ out) {
   } else {
     atomicMin(a.jmin_bits, (unsigned long long)__double_as_longlong(J));
   }
-  // blocked layout: (block * NV + v) * BS + local index
+  // blocked layout of the reader of this cache (its own cells per block): (block * NV + v) * BS + local
   constexpr int NVO = cache_values(VAR, DIM);
-  constexpr int BS = cache_row(DIM, N);
-  const long long qg = (long long)blockIdx.x * NVO * BS + threadIdx.x;
+  constexpr int CBL = layout_cells<T>(DIM, N);
+  constexpr int BS = layout_row<T>(DIM, N);
+  const long long qg = (long long)(cell / CBL) * NVO * BS + (cell % CBL) * NPT + pt.p;
   constexpr long long st = BS;
   if (VAR == VAR_T4 || VAR == VAR_T2) {
 #pragma unroll

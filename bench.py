@@ -70,7 +70,9 @@ def bytes_per_apply(var, dtype_bytes, nqp, ndofs, dim=3):
 
 # DRAM bytes (read + write) per launch from one ncu capture of the 32^3 Q2 workload (profiles/*_ncu.md);
 # a kernel that changed since its capture maps to None.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    ("NC", "double"): 19_699_712,   # profiles/apply_nc_f64_32cube_q2_ncu.md
+}
 
 
 def peaks():

@@ -40,6 +40,9 @@ ALL_VARIANTS = ("T4", "T2", "FC", "SC", "NC")
 WORKLOAD = "3D neo-Hookean unit cube, spherical inclusion r=0.25 10x, 32^3 Q2 (823,875 dofs), FP64 tangent apply x {T4, FC, NC}"
 
 
+FORMS = {-1: None, 0: "point", 1: "line"}
+
+
 def flops_per_qp(var, dim=3, n=3):
     """Algorithmic FP64 flops per Gauss point of one application, counted from the kernel's arithmetic
     (FMA = 2): sum factorisation 4 d^2 (2n-1) + d(d-1); quadrature work per variant."""
@@ -71,7 +74,7 @@ def bytes_per_apply(var, dtype_bytes, nqp, ndofs, dim=3):
 # DRAM bytes (read + write) per launch from one ncu capture of the 32^3 Q2 workload (profiles/*_ncu.md);
 # a kernel that changed since its capture maps to None.
 NCU_TRAFFIC = {
-    ("NC", "double"): 19_699_712,   # profiles/apply_nc_f64_32cube_q2_ncu.md
+    ("NC", "double", "apply_kernel"): 19_699_712,   # profiles/apply_nc_f64_32cube_q2_ncu.md
 }
 
 
@@ -220,7 +223,7 @@ def serve_bench(api, inputs, dev, n_req, seed=0, max_active=8, budget_gb=160):
         return api.Context.newton_params(face_values=fv, level_dtype=ldt)
 
     def run(max_act, ldt, coarse, arrivals=None):
-        sp = api.SolverParams(4, 1, 0.6, 1.2, 30, 0, 1e-3, coarse)
+        sp = api.SolverParams(4, 1, 0.6, 1.2, 30, 0, 1e-3, coarse, -1)
         out = {}
         with api.Server(dev.index, budget_bytes=budget_gb << 30, max_active=max_act) as sv:
             t0 = time.perf_counter()
@@ -310,6 +313,7 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--only", default=None, help="profile mode: VARIANT:f64|f32, a few applications of one kernel")
+    ap.add_argument("--form", type=int, default=-1, help="profile mode: kernel form (0 point, 1 line, -1 tuned)")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--serve-requests", type=int, default=12, help="requests in the serving section (0 = skip)")
     ap.add_argument("--serve-only", action="store_true")
@@ -339,7 +343,7 @@ def main():
         x = torch.tensor(inputs.gaussian_vector(inputs.n_dofs(DIM, K, M), seed=1), device=dev)
         with api.Context(dev.index) as c:
             c.setup_problem(pr)
-            c.set_solver_params(coarse_eig_iters=5)
+            c.set_solver_params(coarse_eig_iters=5, kernel_form=args.form)
             c.set_displacement(u, var, level_dtype=1 if dt == "f32" else 0)
             xin = x.float() if dt == "f32" else x
             y = torch.empty_like(xin)
@@ -391,12 +395,14 @@ def main():
             "f32_gdofs": n / (t32 * 1e-3) / 1e9, "f32_ms": t32,
             "f32_gbs": bytes_per_apply(v, 4, nqp, n) / (t32 * 1e-3) / 1e9,
             "f32_hbm_frac": bytes_per_apply(v, 4, nqp, n) / (t32 * 1e-3) / 1e9 / hbm,
+            "f64_form": FORMS[ctxs[v].kernel_form(-1, 0)], "f32_form": FORMS[ctxs[v].kernel_form(-1, 1)],
         }
     # dominant kernel of the step: the slowest variant's FP64 apply (FP64-pipe bound)
     dom = max(per_var_ms, key=per_var_ms.get)
     ach = flops_per_qp(dom) * nqp / (per_var_ms[dom] * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": f"apply_kernel<3,3,{dom},double>", "achieved": ach, "peak": fp64_peak,
-                "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": NCU_TRAFFIC.get((dom, "double")),
+    kname = "apply_line_kernel" if ctxs[dom].kernel_form(-1, 0) == 1 else "apply_kernel"
+    roofline = {"bound": "alu", "kernel": f"{kname}<3,3,{dom},double>", "achieved": ach, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": NCU_TRAFFIC.get((dom, "double", kname)),
                 "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                 "peak_source": "FP64 pipe: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (derived, nominal 1.25 TFLOP/s)",
                 "algorithmic_flops_per_launch": flops_per_qp(dom) * nqp}

@@ -123,6 +123,11 @@ typedef struct {
                                assembled densely and inverted (Gauss-Jordan) once per linearisation,
                                applied as one matrix-vector product (coarsest level <= 6000 dofs;
                                degrees 1-3 in 3D, 1-4 in 2D) */
+  int kernel_form;          /* [-1] tangent-action kernel: 0 = one thread per (cell, Gauss point), 1 = one
+                               thread per x-line of a cell, -1 = autotuned: the first linearisation of each
+                               (dim, degree, variant, precision, mesh size) times both on the level's own
+                               cache and keeps the faster (process-wide; appended to the file named by the
+                               environment variable HY_TUNE_FILE, if set, and read back from it) */
 } hy_solver_params;
 
 hy_status hy_set_solver_params(hy_ctx *ctx, const hy_solver_params *p);
@@ -134,6 +139,10 @@ hy_status hy_level_info(const hy_ctx *ctx, int level, double *lmax, double *coar
                         int *coarse_degree);
 /* Override the estimates (levels >= 1: lmax; level 0: lo, hi), e.g. to mirror another solver. */
 hy_status hy_set_level_info(hy_ctx *ctx, int level, double lmax, double coarse_lo, double coarse_hi);
+
+/* Tangent-action kernel form used on a level for a precision (0 point, 1 line; see kernel_form), or -1
+ * when that level has no cache of that precision. */
+hy_status hy_kernel_form(const hy_ctx *ctx, int level, hy_dtype dtype, int *form);
 
 /* Copy the level-`level` displacement (the carried-down linearisation point) into u_dev (FP64). */
 hy_status hy_level_displacement(const hy_ctx *ctx, int level, double *u_dev);

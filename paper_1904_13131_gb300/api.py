@@ -26,7 +26,7 @@ EXPORTED = ("hy_create", "hy_destroy", "hy_status_str", "hy_last_error", "hy_mes
             "hy_level_displacement", "hy_prolongate_add", "hy_restrict", "hy_pcg", "hy_newton_default_params",
             "hy_newton_solve", "hy_dot", "hy_dot_noalloc", "hy_kernel_launches", "hy_footprint", "hy_ctx_bytes",
             "hy_server_create", "hy_server_destroy", "hy_server_submit", "hy_server_poll", "hy_server_wait",
-            "hy_server_release", "hy_server_stats_get")
+            "hy_server_release", "hy_server_stats_get", "hy_kernel_form")
 
 
 class HyError(RuntimeError):
@@ -38,7 +38,7 @@ class HyError(RuntimeError):
 class SolverParams(ctypes.Structure):
     _fields_ = [("cheb_degree", ctypes.c_int), ("cheb_sweeps", ctypes.c_int), ("cheb_lo", ctypes.c_double),
                 ("cheb_hi", ctypes.c_double), ("eig_iters", ctypes.c_int), ("coarse_eig_iters", ctypes.c_int),
-                ("coarse_reduction", ctypes.c_double), ("coarse_solver", ctypes.c_int)]
+                ("coarse_reduction", ctypes.c_double), ("coarse_solver", ctypes.c_int), ("kernel_form", ctypes.c_int)]
 
 
 class NewtonParams(ctypes.Structure):
@@ -109,6 +109,7 @@ def load_library(path: str = LIB_PATH):
         "hy_kernel_launches": [vp, ctypes.POINTER(i64)],
         "hy_dot_noalloc": [i32, vp, vp, vp, i64, ctypes.POINTER(dbl)],
         "hy_footprint": [i32, i32, i32, i32, i32, i32, i32, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(i64)],
+        "hy_kernel_form": [vp, i32, i32, ctypes.POINTER(i32)],
         "hy_ctx_bytes": [vp, ctypes.POINTER(i64)],
         "hy_server_create": [ctypes.POINTER(vp), i32, i64, i32],
         "hy_server_destroy": [vp],
@@ -268,6 +269,11 @@ class Context:
     def set_level_info(self, level, lmax=0.0, coarse_lo=0.0, coarse_hi=0.0):
         self._ck(self.lib.hy_set_level_info(self.h, level, lmax, coarse_lo, coarse_hi))
 
+    def kernel_form(self, level=-1, dtype=F64):
+        f = ctypes.c_int()
+        self._ck(self.lib.hy_kernel_form(self.h, level, dtype, ctypes.byref(f)))
+        return f.value
+
     def level_displacement(self, level):
         u = self.empty(level)
         self._ck(self.lib.hy_level_displacement(self.h, level, self._vec(u, self.num_dofs(level), F64)))
@@ -403,7 +409,7 @@ class Server:
     def submit(self, problem: dict, newton: NewtonParams, solver: SolverParams | None = None) -> int:
         """problem: an inputs.problem(...) bundle (ids of every level, coarsest first)."""
         if solver is None:
-            solver = SolverParams(4, 1, 0.6, 1.2, 30, 0, 1e-3, 0)
+            solver = SolverParams(4, 1, 0.6, 1.2, 30, 0, 1e-3, 0, -1)
         ids = np.ascontiguousarray(np.concatenate([np.asarray(i, dtype=np.uint8) for i in problem["ids"]]))
         mu = np.ascontiguousarray(problem["mu"], dtype=np.float64)
         lam = np.ascontiguousarray(problem["lam"], dtype=np.float64)

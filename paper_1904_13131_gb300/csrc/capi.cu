@@ -7,6 +7,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <new>
 #include <string>
 #include <vector>
@@ -160,6 +163,7 @@ struct Level {
   double* d_dinv64 = nullptr;
   float* d_dinv32 = nullptr;
   double lmax = 0.0;
+  int form[2] = {-1, -1};  // tangent-action kernel form per precision (FP64, FP32)
   double* w64[5] = {};  // V-cycle vectors b, x, r, d, t
   float* w32[5] = {};
   double* d_Ainv = nullptr;  // exact coarse solve: dense free-dof tangent / its inverse (ping-pong pair)
@@ -188,7 +192,7 @@ struct hy_ctx {
   std::vector<Transfer> tr;
   Basis1D<double> b64{};
   Basis1D<float> b32{};
-  hy_solver_params sp{4, 1, 0.6, 1.2, 30, 0, 1e-3, 0};
+  hy_solver_params sp{4, 1, 0.6, 1.2, 30, 0, 1e-3, 0, -1};
   int var = -1;
   bool mixed = false;
   bool state_ok = false;
@@ -325,10 +329,10 @@ CellArgs<T> cell_args(hy_ctx* ctx, Level& L) {
   return a;
 }
 
-CellFn<double> apply_fn(hy_ctx* ctx, double*, int var) {
+ApplyFn<double> apply_fn(hy_ctx* ctx, double*, int var) {
   return ctx->dim == 2 ? apply_fn_f64_2d(ctx->n, var) : apply_fn_f64_3d(ctx->n, var);
 }
-CellFn<float> apply_fn(hy_ctx* ctx, float*, int var) {
+ApplyFn<float> apply_fn(hy_ctx* ctx, float*, int var) {
   return ctx->dim == 2 ? apply_fn_f32_2d(ctx->n, var) : apply_fn_f32_3d(ctx->n, var);
 }
 
@@ -355,9 +359,10 @@ hy_status vmult(hy_ctx* ctx, int l, const T* x, T* y, bool constrained_in = true
     cudaMemsetAsync(y, 0, sizeof(T) * L.ndofs, ctx->stream);
     a.g.fm[0] = a.g.fm[1] = a.g.fm[2] = a.g.fm[3] = a.g.fm[4] = a.g.fm[5] = 0;
   }
-  CellFn<T> fn = apply_fn(ctx, (T*)nullptr, ctx->var);
+  ApplyFn<T> fn = apply_fn(ctx, (T*)nullptr, ctx->var);
   if (!fn) return fail(ctx, HY_ERR_UNSUPPORTED, "no kernel for this dim/degree/variant");
-  fn(a, ctx->stream);
+  const int form = L.form[sizeof(T) == 8 ? 0 : 1];
+  fn(a, form < 0 ? FORM_POINT : form, ctx->stream);
   if (!constrained_in) launch_zero_constrained<T>(y, L.nnodes, ctx->dim, L.g, ctx->stream);
   return check_launch(ctx, 2);
 }
@@ -744,6 +749,98 @@ hy_status coarse_direct_setup(hy_ctx* ctx) {
   return HY_OK;
 }
 
+// ---- autotuner of the tangent-action kernel form -----------------------------------------------------
+// Key: (dim, degree, variant, precision, log2 of the level's cell count). Decisions are shared by every
+// context of the process and, when HY_TUNE_FILE names a file, read from and appended to it as lines
+// "dim degree variant precision size_class form".
+using TuneKey = std::tuple<int, int, int, int, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune;
+bool g_tune_loaded = false;
+
+void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = std::getenv("HY_TUNE_FILE");
+  if (!path) return;
+  if (FILE* f = std::fopen(path, "r")) {
+    int d, k, v, p, b, form;
+    while (std::fscanf(f, "%d %d %d %d %d %d", &d, &k, &v, &p, &b, &form) == 6) g_tune[TuneKey{d, k, v, p, b}] = form;
+    std::fclose(f);
+  }
+}
+
+template <typename T>
+hy_status autotune_level(hy_ctx* ctx, int l) {
+  Level& L = ctx->lev[l];
+  const int dt = sizeof(T) == 8 ? 0 : 1;
+  if (ctx->sp.kernel_form >= 0) {
+    L.form[dt] = ctx->sp.kernel_form;
+    return HY_OK;
+  }
+  int bucket = 0;
+  for (long long c = L.g.ncells; c > 1; c >>= 1) ++bucket;
+  const TuneKey key{ctx->dim, ctx->k, ctx->var, dt, bucket};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_load_locked();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      L.form[dt] = it->second;
+      return HY_OK;
+    }
+  }
+  // time both forms on this level's cache: one warm-up application each, then three rounds that
+  // alternate the forms, each timing four back-to-back applications (hides the host launch latency on
+  // small levels); the best round of each form decides
+  T* x = wvec<T>(L, 2);
+  T* y = wvec<T>(L, 3);
+  launch_splitmix<T>(x, L.ndofs, 12345ULL, ctx->stream);
+  HY_TRY(check_launch(ctx, 1));
+  struct Events {
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~Events() {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } ev;
+  HY_CK(cudaEventCreate(&ev.a));
+  HY_CK(cudaEventCreate(&ev.b));
+  cudaEvent_t e0 = ev.a, e1 = ev.b;
+  float best[2] = {1e30f, 1e30f};
+  for (int form = 0; form < 2; ++form) {
+    L.form[dt] = form;
+    HY_TRY(vmult<T>(ctx, l, x, y));
+  }
+  for (int r = 0; r < 3; ++r) {
+    for (int form = 0; form < 2; ++form) {
+      L.form[dt] = form;
+      cudaEventRecord(e0, ctx->stream);
+      for (int q = 0; q < 4; ++q) HY_TRY(vmult<T>(ctx, l, x, y));
+      cudaEventRecord(e1, ctx->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      best[form] = std::min(best[form], 0.25f * ms);
+    }
+  }
+  const int choice = best[1] < best[0] ? FORM_LINE : FORM_POINT;
+  L.form[dt] = choice;
+  if (ctx->verbose)
+    std::fprintf(stderr, "[hy] autotune dim %d k %d var %d %s cells 2^%d: point %.3f ms, line %.3f ms -> %s\n", ctx->dim,
+                 ctx->k, ctx->var, dt ? "f32" : "f64", bucket, best[0], best[1], choice ? "line" : "point");
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  if (g_tune.emplace(key, choice).second) {
+    if (const char* path = std::getenv("HY_TUNE_FILE")) {
+      if (FILE* f = std::fopen(path, "a")) {
+        std::fprintf(f, "%d %d %d %d %d %d\n", ctx->dim, ctx->k, ctx->var, dt, bucket, choice);
+        std::fclose(f);
+      }
+    }
+  }
+  return HY_OK;
+}
+
 // Verbose phase timer of set_displacement (synchronises the stream, so only when HY_VERBOSE=1).
 struct PhaseTimer {
   hy_ctx* ctx;
@@ -795,6 +892,7 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
     const bool need64 = (l == top) || (l == 0) || !mixed;
     const bool need32 = mixed && (l > 0 || l == top);
     L.has64 = L.has32 = false;
+    L.form[0] = L.form[1] = -1;
     if (need64) {
       HY_TRY(build_cache<double>(ctx, l, var));
       L.has64 = true;
@@ -829,6 +927,11 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
   }
   HY_TRY(check_error_word(ctx, "set_displacement"));
   pt.mark("state+diag");
+  for (int l = 0; l < ctx->nlev; ++l) {
+    if (ctx->lev[l].has64) HY_TRY(autotune_level<double>(ctx, l));
+    if (ctx->lev[l].has32) HY_TRY(autotune_level<float>(ctx, l));
+  }
+  pt.mark("autotune");
   // eigenvalue estimates (level precision of the V-cycle)
   for (int l = 1; l < ctx->nlev; ++l) {
     double lmin, lmax;
@@ -1264,6 +1367,7 @@ hy_status hy_gmg_vcycle(hy_ctx* ctx, const double* r, double* z) {
 hy_status hy_set_solver_params(hy_ctx* ctx, const hy_solver_params* p) {
   if (!ctx || !p) return HY_ERR_ARG;
   if (p->cheb_degree < 1 || p->cheb_sweeps < 1 || !(p->cheb_lo > 0) || !(p->cheb_hi > p->cheb_lo) ||
+      p->kernel_form < -1 || p->kernel_form > 1 ||
       p->eig_iters < 1 || p->coarse_eig_iters < 0 || !(p->coarse_reduction > 0 && p->coarse_reduction < 1) ||
       p->coarse_solver < 0 || p->coarse_solver > 1)
     return fail(ctx, HY_ERR_ARG, "solver parameters out of range");
@@ -1306,6 +1410,16 @@ hy_status hy_set_level_info(hy_ctx* ctx, int level, double lmax, double clo, dou
     if (!(lmax > 0)) return fail(ctx, HY_ERR_ARG, "bad lmax");
     ctx->lev[l].lmax = lmax;
   }
+  return HY_OK;
+}
+
+hy_status hy_kernel_form(const hy_ctx* ctx, int level, hy_dtype dtype, int* form) {
+  if (!ctx || !form || (dtype != HY_F64 && dtype != HY_F32)) return HY_ERR_ARG;
+  const int l = lev_index(ctx, level);
+  if (l < 0 || l >= ctx->nlev) return HY_ERR_ARG;
+  const Level& L = ctx->lev[l];
+  const bool have = dtype == HY_F64 ? L.has64 : L.has32;
+  *form = have ? L.form[dtype == HY_F64 ? 0 : 1] : -1;
   return HY_OK;
 }
 

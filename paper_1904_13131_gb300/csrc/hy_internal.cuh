@@ -82,23 +82,21 @@ __host__ __device__ constexpr int cache_row(int dim, int n) {
   return (cells_per_block(dim, n) * ipow(n, dim) + 3) / 4 * 4;
 }
 
-// The FP32 tangent action runs one thread per x-line of a cell ((k+1)^{dim-1} threads per cell); its
-// caches use the blocked layout with this many cells per block.
-__host__ __device__ constexpr int cells_per_block_line(int dim, int n) {
-  return (128 / ipow(n, dim - 1)) < 1 ? 1 : (128 / ipow(n, dim - 1));
-}
-__host__ __device__ constexpr int cache_row_line(int dim, int n) {
-  return (cells_per_block_line(dim, n) * ipow(n, dim) + 3) / 4 * 4;
-}
-// Cells per block of the cache layout read by the tangent action of element type T.
+// Both forms of the tangent action -- one thread per (cell, Gauss point) and one thread per x-line of a
+// cell -- process the same cells per block and so read the same cache layout; which form runs is picked per
+// (dim, degree, variant, precision, size) by the autotuner (csrc/capi.cu).
+__host__ __device__ constexpr int cells_per_block_line(int dim, int n) { return cells_per_block(dim, n); }
+__host__ __device__ constexpr int cache_row_line(int dim, int n) { return cache_row(dim, n); }
 template <typename T>
 __host__ __device__ constexpr int layout_cells(int dim, int n) {
-  return sizeof(T) == 4 ? cells_per_block_line(dim, n) : cells_per_block(dim, n);
+  return cells_per_block(dim, n);
 }
 template <typename T>
 __host__ __device__ constexpr int layout_row(int dim, int n) {
-  return sizeof(T) == 4 ? cache_row_line(dim, n) : cache_row(dim, n);
+  return cache_row(dim, n);
 }
+
+enum KernelForm { FORM_POINT = 0, FORM_LINE = 1 };
 
 // Device-side error word bits.
 enum : unsigned { ERRBIT_JNEG = 1u, ERRBIT_NAN = 2u, ERRBIT_TIMEOUT = 4u, ERRBIT_NONSPD = 8u };

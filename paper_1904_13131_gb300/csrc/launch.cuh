@@ -10,14 +10,17 @@ template <typename T> struct CellArgs;
 
 template <typename T>
 using CellFn = void (*)(const CellArgs<T>&, cudaStream_t);
+// tangent action: form FORM_POINT (thread per Gauss point) or FORM_LINE (thread per x-line)
+template <typename T>
+using ApplyFn = void (*)(const CellArgs<T>&, int form, cudaStream_t);
 template <typename TOUT>
 using StateFn = void (*)(const CellArgs<double>&, TOUT*, cudaStream_t);
 
 // n = degree + 1 in 2..5; var in Variant; returns nullptr for unsupported combinations
-CellFn<double> apply_fn_f64_2d(int n, int var);
-CellFn<double> apply_fn_f64_3d(int n, int var);
-CellFn<float> apply_fn_f32_2d(int n, int var);
-CellFn<float> apply_fn_f32_3d(int n, int var);
+ApplyFn<double> apply_fn_f64_2d(int n, int var);
+ApplyFn<double> apply_fn_f64_3d(int n, int var);
+ApplyFn<float> apply_fn_f32_2d(int n, int var);
+ApplyFn<float> apply_fn_f32_3d(int n, int var);
 StateFn<double> state_fn_f64(int dim, int n, int var);   // var VAR_NONE: J check only
 StateFn<float> state_fn_f32(int dim, int n, int var);
 CellFn<double> residual_fn(int dim, int n);

@@ -33,14 +33,35 @@ def test_apply_all_variants_fp64_fp32(torch, dim, k, m):
     xd = torch.tensor(x, device="cuda")
     xf = xd.float()
     with context(pr) as ctx:
-        for var in VARIANTS:
-            ctx.set_displacement(ud, var, level_dtype=1)  # builds the FP64 and the FP32 fine cache
-            y64 = ctx.apply_tangent(xd).cpu().numpy()
-            y32 = ctx.apply_tangent(xf, dtype=1).cpu().numpy()
-            assert rel(y64, y_ref) < 1e-12, (var, rel(y64, y_ref))
-            assert rel(y32, y_ref) < 2e-6, (var, rel(y32, y_ref))
-            # constrained rows are the identity
-            np.testing.assert_array_equal(y64[P.constrained], x[P.constrained])
+        for form in (0, 1):  # one thread per (cell, Gauss point); one thread per x-line of a cell
+            ctx.set_solver_params(kernel_form=form)
+            for var in VARIANTS:
+                ctx.set_displacement(ud, var, level_dtype=1)  # builds the FP64 and the FP32 fine cache
+                assert ctx.kernel_form(-1, 0) == form and ctx.kernel_form(-1, 1) == form
+                y64 = ctx.apply_tangent(xd).cpu().numpy()
+                y32 = ctx.apply_tangent(xf, dtype=1).cpu().numpy()
+                assert rel(y64, y_ref) < 1e-12, (form, var, rel(y64, y_ref))
+                assert rel(y32, y_ref) < 2e-6, (form, var, rel(y32, y_ref))
+                # constrained rows are the identity
+                np.testing.assert_array_equal(y64[P.constrained], x[P.constrained])
+
+
+def test_autotuned_form_is_recorded_and_reused(torch):
+    """kernel_form = -1 picks one of the two forms per level and precision (-1 where a level has no cache
+    of that precision); a second context with the same shapes reuses the process-wide decisions."""
+    dim, k, m = 3, 2, 6
+    pr = problem(dim, k, m, n_levels=2)
+    u = inputs.smooth_field(dim, k, m, seed=4)
+    ud = torch.tensor(u, device="cuda")
+    forms = []
+    for _ in range(2):
+        with context(pr) as ctx:
+            ctx.set_solver_params(kernel_form=-1)
+            ctx.set_displacement(ud, "NC", level_dtype=1)
+            f = [(ctx.kernel_form(l, 0), ctx.kernel_form(l, 1)) for l in range(2)]
+            forms.append(f)
+            assert f[1][0] in (0, 1) and f[1][1] in (0, 1) and f[0][0] in (0, 1) and f[0][1] in (-1, 0, 1)
+    assert forms[0] == forms[1]
 
 
 @pytest.mark.parametrize("dim,k,m", [(2, 2, 7), (3, 2, 3), (3, 3, 2), (2, 4, 3)])

@@ -263,6 +263,88 @@ def serve_bench(api, inputs, dev, n_req, seed=0, max_active=8, budget_gb=160):
             "mix": [(q["dim"], q["k"], q["m"]) for q in reqs]}
 
 
+def batch_bench(torch, api, inputs, dev, stream, n_apply=64, n_solve=16, reps=20):
+    """Work-list batches of many small problems (the serving regime): 3D Q2 inclusion cubes of 8^3 cells
+    (14,739 dofs each) with stiffness ratios 2-17. (a) NC FP64 tangent actions of n_apply problems
+    (943k dofs in all, about the size of the 32^3 workload): one list launch against one launch per
+    problem, both L2-resident. (b) GMG-PCG (3 levels 8 -> 2, mixed precision, T4, rtol 1e-8) of n_solve
+    problems, exact coarse solve: the batched solve (one graph replay and one host synchronisation per
+    iteration for all) against the single-problem solve called once per problem."""
+    m, k = 8, 2
+    out = {}
+    ctxs = []
+    try:
+        for i in range(n_apply):
+            pr = inputs.problem(3, k, m, n_levels=1, top=0, ratio=2.0 + i % 16)
+            c = api.Context(dev.index)
+            c.setup_problem(pr)
+            c.set_solver_params(coarse_eig_iters=5)
+            c.set_displacement(torch.tensor(inputs.smooth_field(3, k, m, seed=i), device=dev), "NC")
+            ctxs.append(c)
+        n = ctxs[0].num_dofs()
+        xs = [torch.tensor(inputs.gaussian_vector(n, 100 + i), device=dev) for i in range(n_apply)]
+        ys = [torch.empty_like(x) for x in xs]
+        with api.Batch(ctxs) as b:
+            for _ in range(3):
+                b.apply(xs, ys)
+                for c, x, y in zip(ctxs, xs, ys):
+                    c.apply_tangent(x, y)
+            t_seq, t_bat = [], []
+            for _ in range(reps):
+                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                e0.record(stream)
+                for c, x, y in zip(ctxs, xs, ys):
+                    c.apply_tangent(x, y)
+                e1.record(stream)
+                b.apply(xs, ys)
+                e2.record(stream)
+                e2.synchronize()
+                t_seq.append(e0.elapsed_time(e1))
+                t_bat.append(e1.elapsed_time(e2))
+            form = b.kernel_form(0)
+        ts, tb = float(np.median(t_seq)), float(np.median(t_bat))
+        out["apply"] = {"problems": n_apply, "dofs_total": n * n_apply, "variant": "NC", "dtype": "f64",
+                        "one_launch_per_problem_ms": ts, "list_launch_ms": tb,
+                        "one_launch_per_problem_gdofs": n * n_apply / (ts * 1e-3) / 1e9,
+                        "list_launch_gdofs": n * n_apply / (tb * 1e-3) / 1e9, "speedup": ts / tb,
+                        "list_form": FORMS[form], "l2": "resident (same for both)"}
+    finally:
+        for c in ctxs:
+            c.close()
+    ctxs = []
+    try:
+        for i in range(n_solve):
+            pr = inputs.problem(3, k, m, n_levels=3, top=inputs.normal_top_mask(3), ratio=2.0 + i)
+            c = api.Context(dev.index)
+            c.setup_problem(pr)
+            c.set_solver_params(coarse_solver=1)
+            c.set_displacement(torch.tensor(inputs.smooth_field(3, k, m, seed=i, amplitude=0.005), device=dev), "T4",
+                               level_dtype=1)
+            ctxs.append(c)
+        n = ctxs[0].num_dofs()
+        bs = [torch.tensor(inputs.gaussian_vector(n, 200 + i), device=dev) for i in range(n_solve)]
+        xs = [torch.empty_like(v) for v in bs]
+        with api.Batch(ctxs) as b:
+            b.pcg(bs, xs, rtol=1e-8, max_iter=200)  # warm-up (graph capture, list-form choice)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            its_single = [c.pcg(v, x, rtol=1e-8, max_iter=200)[1] for c, v, x in zip(ctxs, bs, xs)]
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            _, its_batch, sts = b.pcg(bs, xs, rtol=1e-8, max_iter=200)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+        out["pcg"] = {"problems": n_solve, "dofs_each": n, "levels": 3, "variant": "T4", "level_dtype": "f32 (mixed)",
+                      "coarse_solver": "exact (dense inverse)",
+                      "one_solve_per_problem_ms": (t1 - t0) * 1e3, "batched_ms": (t2 - t1) * 1e3,
+                      "speedup": (t1 - t0) / (t2 - t1), "cg_iterations_single": its_single,
+                      "cg_iterations_batched": its_batch, "statuses": sts}
+    finally:
+        for c in ctxs:
+            c.close()
+    return out
+
+
 def cpu_oracle_rate(seconds=10.0):
     """Oracle element-by-element application on the same problem at 16^3 Q2 (1/8 of the cells)."""
     from oracle.fem import Problem
@@ -317,6 +399,8 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--serve-requests", type=int, default=12, help="requests in the serving section (0 = skip)")
     ap.add_argument("--serve-only", action="store_true")
+    ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the work-list batch section")
+    ap.add_argument("--batch-only", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -351,6 +435,9 @@ def main():
                 c.apply_tangent(xin, y, dtype=1 if dt == "f32" else 0)
             torch.cuda.synchronize()
         print(json.dumps({"only": args.only, "reps": args.reps}))
+        return
+    if args.batch_only:
+        print(json.dumps({"batch": batch_bench(torch, api, inputs, dev, stream)}), flush=True)
         return
     if args.serve_only:
         print(json.dumps({"serve": serve_bench(api, inputs, dev, args.serve_requests)}), flush=True)
@@ -444,6 +531,13 @@ def main():
         except api.HyError as e:
             serve = {"error": str(e)}
 
+    batch = None
+    if args.batch and rank == 0:
+        try:
+            batch = batch_bench(torch, api, inputs, dev, stream)
+        except api.HyError as e:
+            batch = {"error": str(e)}
+
     cpu = None
     if rank == 0 and world == 1:
         rate, nd, el, sample = cpu_oracle_rate(args.cpu_seconds)
@@ -458,7 +552,7 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": int(launches_timed),
-                "per_variant_ms_f64": per_var_ms, "variants": variants, "solve": solve, "serve": serve,
+                "per_variant_ms_f64": per_var_ms, "variants": variants, "solve": solve, "serve": serve, "batch": batch,
                 "wall_s_timed_region": wall, "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src}
         print(json.dumps(line), flush=True)
     if dist:

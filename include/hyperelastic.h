@@ -126,8 +126,9 @@ typedef struct {
   int kernel_form;          /* [-1] tangent-action kernel: 0 = one thread per (cell, Gauss point), 1 = one
                                thread per x-line of a cell, -1 = autotuned: the first linearisation of each
                                (dim, degree, variant, precision, mesh size) times both on the level's own
-                               cache and keeps the faster (process-wide; appended to the file named by the
-                               environment variable HY_TUNE_FILE, if set, and read back from it) */
+                               cache and keeps the faster (process-wide; when the environment variable
+                               HY_TUNE_FILE names a file, the decisions are read from it at the first tuning
+                               and it is rewritten, as a JSON array, with every new decision) */
 } hy_solver_params;
 
 hy_status hy_set_solver_params(hy_ctx *ctx, const hy_solver_params *p);
@@ -219,6 +220,49 @@ hy_status hy_ctx_bytes(const hy_ctx *ctx, int64_t *bytes);
 
 /* Number of kernels this context has launched since creation (for accounting). */
 hy_status hy_kernel_launches(const hy_ctx *ctx, int64_t *count);
+
+/* ---- Work-list batches ---------------------------------------------------------------------------
+ * Several independent problems of the same dimension and degree (each a context with its own mesh size,
+ * material and linearisation) advanced together. Not a step of the paper's method: it batches the
+ * method's operator action (Eq. mf_vmult) and its preconditioned CG (Sec. 6) across problems, so that
+ * many problems too small to fill the GPU share its SMs.
+ *  - The finest-level tangent actions of all problems run as ONE kernel launch over a work list of
+ *    per-problem arguments (thread blocks are dealt to the problems in order, each problem keeping the
+ *    cell blocks and Gauss-point cache layout of its own context).
+ *  - hy_batch_pcg advances every not-yet-converged problem by one PCG iteration per replay of a CUDA
+ *    graph (the list launch, then one branch per problem with its dot products, updates and V-cycle,
+ *    all CG scalars on the device), with one host synchronisation per iteration for the whole batch; the
+ *    graph is captured again only when a problem leaves the resident set (converged or failed).
+ * The batch borrows the contexts (it does not own them; destroy it first) and runs on a stream of its
+ * own, ordered after the work queued on each context's stream at each call and before work queued
+ * there afterwards. A batch is not thread-safe; the contexts must not be used by another thread during
+ * a batch call. All contexts must have had hy_set_displacement with the same variant. */
+typedef struct hy_batch hy_batch;
+#define HY_BATCH_MAX 1024
+
+/* Group count distinct contexts (same device, dimension and degree, mesh set up). HY_ERR_ARG for an
+ * empty, oversized, mixed or repeated list; HY_ERR_STATE for a context without a mesh. */
+hy_status hy_batch_create(hy_batch **out, hy_ctx *const *ctxs, int count);
+void hy_batch_destroy(hy_batch *b);
+const char *hy_batch_last_error(const hy_batch *b);
+
+/* y_i = A~_i x_i on the finest level of every context i, in one list launch (as hy_apply_tangent,
+ * dtype HY_F64 or HY_F32; the context needs a finest-level cache of that precision). x_dev[i], y_dev[i]:
+ * device vectors of context i's finest level (distinct). The kernel form of the list launch is timed on
+ * the first call per precision unless the first context's kernel_form parameter forces one. */
+hy_status hy_batch_apply(hy_batch *b, const void *const *x_dev, void *const *y_dev, hy_dtype dtype);
+
+/* hy_pcg for every context i at once: A~_i x_i = b_i, zero initial guess, ||r_i|| <= rtol ||b_i||.
+ * iterations[count] and status[count] receive each problem's iteration count and outcome (HY_OK,
+ * HY_ERR_NOCONV at max_iter or for a non-SPD operator, HY_ERR_TIMEOUT, ...), with the message in that
+ * context's hy_last_error. The return value reports failures of the batch itself (launch, capture). */
+hy_status hy_batch_pcg(hy_batch *b, const double *const *b_dev, double *const *x_dev, double rtol, int max_iter,
+                       int *iterations, hy_status *status);
+
+/* Kernels launched by the batch's own calls (list launches and graph replays). */
+hy_status hy_batch_kernel_launches(const hy_batch *b, int64_t *count);
+/* Kernel form chosen for the list launch of a precision (0 point, 1 line, -1 not chosen yet). */
+hy_status hy_batch_kernel_form(const hy_batch *b, hy_dtype dtype, int *form);
 
 /* ---- Solve server (continuous batching of many independent solves on one GPU) --------------------
  * Not a step of the paper's method: a request loop around hy_newton_solve. Requests are queued in

@@ -26,7 +26,9 @@ EXPORTED = ("hy_create", "hy_destroy", "hy_status_str", "hy_last_error", "hy_mes
             "hy_level_displacement", "hy_prolongate_add", "hy_restrict", "hy_pcg", "hy_newton_default_params",
             "hy_newton_solve", "hy_dot", "hy_dot_noalloc", "hy_kernel_launches", "hy_footprint", "hy_ctx_bytes",
             "hy_server_create", "hy_server_destroy", "hy_server_submit", "hy_server_poll", "hy_server_wait",
-            "hy_server_release", "hy_server_stats_get", "hy_kernel_form")
+            "hy_server_release", "hy_server_stats_get", "hy_kernel_form", "hy_batch_create", "hy_batch_destroy",
+            "hy_batch_last_error", "hy_batch_apply", "hy_batch_pcg", "hy_batch_kernel_launches",
+            "hy_batch_kernel_form")
 
 
 class HyError(RuntimeError):
@@ -111,6 +113,14 @@ def load_library(path: str = LIB_PATH):
         "hy_footprint": [i32, i32, i32, i32, i32, i32, i32, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(i64)],
         "hy_kernel_form": [vp, i32, i32, ctypes.POINTER(i32)],
         "hy_ctx_bytes": [vp, ctypes.POINTER(i64)],
+        "hy_batch_create": [ctypes.POINTER(vp), ctypes.POINTER(vp), i32],
+        "hy_batch_destroy": [vp],
+        "hy_batch_last_error": [vp],
+        "hy_batch_apply": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i32],
+        "hy_batch_pcg": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), dbl, i32, ctypes.POINTER(i32),
+                         ctypes.POINTER(i32)],
+        "hy_batch_kernel_launches": [vp, ctypes.POINTER(i64)],
+        "hy_batch_kernel_form": [vp, i32, ctypes.POINTER(i32)],
         "hy_server_create": [ctypes.POINTER(vp), i32, i64, i32],
         "hy_server_destroy": [vp],
         "hy_server_submit": [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)],
@@ -123,9 +133,11 @@ def load_library(path: str = LIB_PATH):
     for name, args in sig.items():
         f = getattr(lib, name)
         f.argtypes = args
-        f.restype = None if name in ("hy_destroy", "hy_newton_default_params", "hy_server_destroy") else ctypes.c_int
+        f.restype = None if name in ("hy_destroy", "hy_newton_default_params", "hy_server_destroy",
+                                     "hy_batch_destroy") else ctypes.c_int
     lib.hy_status_str.restype = ctypes.c_char_p
     lib.hy_last_error.restype = ctypes.c_char_p
+    lib.hy_batch_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -381,6 +393,73 @@ def _report_dict(rep, steps):
             "cg_iterations_total": rep.cg_iterations_total, "cg_iterations_max": rep.cg_iterations_max,
             "final_residual": rep.final_residual, "n_solves": rep.n_solves, "total_ms": rep.total_ms,
             "setup_ms_total": rep.setup_ms_total}
+
+
+class Batch:
+    """hy_batch: work-list batch of contexts of the same dim and degree (see include/hyperelastic.h).
+    Enqueues after, and makes each context's stream wait for, the batch's own stream."""
+
+    def __init__(self, contexts):
+        self.lib = load_library()
+        self.contexts = list(contexts)
+        arr = (ctypes.c_void_p * len(self.contexts))(*[c.h.value for c in self.contexts])
+        h = ctypes.c_void_p()
+        st = self.lib.hy_batch_create(ctypes.byref(h), arr, len(self.contexts))
+        if st != 0:
+            raise HyError(st, "hy_batch_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hy_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _ck(self, st):
+        if st != 0:
+            raise HyError(st, self.lib.hy_batch_last_error(self.h).decode())
+
+    def _vecs(self, ts, dtype):
+        if len(ts) != len(self.contexts):
+            raise ValueError("one vector per context")
+        return (ctypes.c_void_p * len(ts))(*[c._vec(t, c.num_dofs(), dtype).value for c, t in zip(self.contexts, ts)])
+
+    def apply(self, xs, ys=None, dtype=F64):
+        if ys is None:
+            ys = [c.empty(-1, dtype) for c in self.contexts]
+        self._ck(self.lib.hy_batch_apply(self.h, self._vecs(xs, dtype), self._vecs(ys, dtype), dtype))
+        return ys
+
+    def pcg(self, bs, xs=None, rtol=1e-8, max_iter=1000):
+        """Returns (xs, iterations, statuses); statuses are hy_status codes per problem."""
+        if xs is None:
+            xs = [c.empty() for c in self.contexts]
+        n = len(self.contexts)
+        its = (ctypes.c_int * n)()
+        sts = (ctypes.c_int * n)()
+        self._ck(self.lib.hy_batch_pcg(self.h, self._vecs(bs, F64), self._vecs(xs, F64), rtol, max_iter, its, sts))
+        return xs, list(its), list(sts)
+
+    def kernel_launches(self):
+        v = ctypes.c_int64()
+        self._ck(self.lib.hy_batch_kernel_launches(self.h, ctypes.byref(v)))
+        return v.value
+
+    def kernel_form(self, dtype=F64):
+        v = ctypes.c_int()
+        self._ck(self.lib.hy_batch_kernel_form(self.h, dtype, ctypes.byref(v)))
+        return v.value
 
 
 class Server:

@@ -139,10 +139,6 @@ void tridiag_extremes(const std::vector<double>& a, const std::vector<double>& b
   lmin = h;
 }
 
-template <typename T> struct DT;
-template <> struct DT<double> { static constexpr hy_dtype v = HY_F64; };
-template <> struct DT<float> { static constexpr hy_dtype v = HY_F32; };
-
 }  // namespace
 
 // ---------------------------------------------------------------------------------------------
@@ -751,23 +747,63 @@ hy_status coarse_direct_setup(hy_ctx* ctx) {
 
 // ---- autotuner of the tangent-action kernel form -----------------------------------------------------
 // Key: (dim, degree, variant, precision, log2 of the level's cell count). Decisions are shared by every
-// context of the process and, when HY_TUNE_FILE names a file, read from and appended to it as lines
-// "dim degree variant precision size_class form".
+// context of the process and, when HY_TUNE_FILE names a file, read from it at the first tuning and
+// rewritten with every new decision, as a JSON array with one object per line:
+//   {"dim": 3, "degree": 2, "variant": "NC", "precision": "f64", "cells_log2": 15, "threads_per_cell": "point"}
 using TuneKey = std::tuple<int, int, int, int, int>;
 std::mutex g_tune_mu;
 std::map<TuneKey, int> g_tune;
 bool g_tune_loaded = false;
+const char* const kVarNames[5] = {"T4", "T2", "FC", "SC", "NC"};
+const char* const kFormNames[2] = {"point", "line"};
+
+int name_index(const char* s, const char* const* names, int n) {
+  for (int i = 0; i < n; ++i)
+    if (std::strcmp(s, names[i]) == 0) return i;
+  return -1;
+}
 
 void tune_load_locked() {
   if (g_tune_loaded) return;
   g_tune_loaded = true;
   const char* path = std::getenv("HY_TUNE_FILE");
   if (!path) return;
-  if (FILE* f = std::fopen(path, "r")) {
-    int d, k, v, p, b, form;
-    while (std::fscanf(f, "%d %d %d %d %d %d", &d, &k, &v, &p, &b, &form) == 6) g_tune[TuneKey{d, k, v, p, b}] = form;
-    std::fclose(f);
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  char line[512];
+  while (std::fgets(line, sizeof line, f)) {
+    int d = 0, k = 0, b = 0;
+    char var[8] = {}, prec[8] = {}, form[8] = {};
+    if (std::sscanf(line, " {\"dim\": %d, \"degree\": %d, \"variant\": \"%7[^\"]\", \"precision\": \"%7[^\"]\", "
+                          "\"cells_log2\": %d, \"threads_per_cell\": \"%7[^\"]\"",
+                    &d, &k, var, prec, &b, form) != 6)
+      continue;  // the brackets and anything unrecognised
+    const int v = name_index(var, kVarNames, 5), fm = name_index(form, kFormNames, 2);
+    const int p = std::strcmp(prec, "f64") == 0 ? 0 : std::strcmp(prec, "f32") == 0 ? 1 : -1;
+    if (v >= 0 && fm >= 0 && p >= 0) g_tune[TuneKey{d, k, v, p, b}] = fm;
   }
+  std::fclose(f);
+}
+
+void tune_save_locked() {
+  const char* path = std::getenv("HY_TUNE_FILE");
+  if (!path) return;
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "w");
+  if (!f) return;
+  std::fprintf(f, "[\n");
+  size_t i = 0;
+  for (const auto& kv : g_tune) {
+    const TuneKey& t = kv.first;
+    std::fprintf(f,
+                 "  {\"dim\": %d, \"degree\": %d, \"variant\": \"%s\", \"precision\": \"%s\", \"cells_log2\": %d, "
+                 "\"threads_per_cell\": \"%s\"}%s\n",
+                 std::get<0>(t), std::get<1>(t), kVarNames[std::get<2>(t)], std::get<3>(t) ? "f32" : "f64",
+                 std::get<4>(t), kFormNames[kv.second], ++i < g_tune.size() ? "," : "");
+  }
+  std::fprintf(f, "]\n");
+  std::fclose(f);
+  std::rename(tmp.c_str(), path);
 }
 
 template <typename T>
@@ -830,14 +866,7 @@ hy_status autotune_level(hy_ctx* ctx, int l) {
     std::fprintf(stderr, "[hy] autotune dim %d k %d var %d %s cells 2^%d: point %.3f ms, line %.3f ms -> %s\n", ctx->dim,
                  ctx->k, ctx->var, dt ? "f32" : "f64", bucket, best[0], best[1], choice ? "line" : "point");
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  if (g_tune.emplace(key, choice).second) {
-    if (const char* path = std::getenv("HY_TUNE_FILE")) {
-      if (FILE* f = std::fopen(path, "a")) {
-        std::fprintf(f, "%d %d %d %d %d %d\n", ctx->dim, ctx->k, ctx->var, dt, bucket, choice);
-        std::fclose(f);
-      }
-    }
-  }
+  if (g_tune.emplace(key, choice).second) tune_save_locked();
   return HY_OK;
 }
 
@@ -1033,6 +1062,469 @@ hy_status pcg(hy_ctx* ctx, const double* b, double* x, double rtol, int max_iter
     rz = rzn;
   }
   return fail(ctx, HY_ERR_NOCONV, "pcg: iteration cap reached");
+}
+
+}  // namespace
+
+// =============================================================================================
+// Work-list batches: several problems of the same dim and degree applied (and solved) together. The
+// finest-level tangent actions of all problems run as ONE launch over a list of per-problem arguments;
+// the rest of a preconditioned CG iteration runs as one branch per problem of a CUDA graph, captured once
+// per resident set (the problems not yet converged), so that one graph launch and one host
+// synchronisation advance every resident problem by one iteration.
+struct hy_batch {
+  int device = 0;
+  int dim = 0, n = 0;
+  std::vector<hy_ctx*> ctx;
+  cudaStream_t s0 = nullptr;              // the batch's own stream
+  std::vector<cudaStream_t> branch;       // one per problem: graph branches
+  std::vector<cudaEvent_t> ev;            // one per problem: joins
+  cudaEvent_t ev_fork = nullptr, ev_done = nullptr, ev_upload = nullptr;
+  void* d_list = nullptr;                 // per-problem kernel arguments (CellArgs<double> or <float>)
+  int* d_start = nullptr;                 // first thread block of each problem, then the total
+  double* d_scal = nullptr;               // PCG_SCALARS doubles per problem
+  void* h_list = nullptr;                 // pinned staging of the uploads
+  int* h_start = nullptr;
+  double* h_scal_in = nullptr;            // pinned: initial scalars
+  double* h_scal_out = nullptr;           // pinned: scalars read back after each iteration
+  int form[2] = {-1, -1};                 // tuned kernel form of the list launch per precision
+  std::vector<const void*> up_x, up_y;    // what the uploaded list describes
+  int up_dt = -1, up_blocks = 0;
+  long long up_max_nodes = 0;
+  std::string err;
+  long long launches = 0;
+};
+
+namespace {
+
+hy_status bfail(hy_batch* b, hy_status s, const std::string& msg) {
+  b->err = msg;
+  return s;
+}
+#define HB_CK(call)                                                                                     \
+  do {                                                                                                  \
+    cudaError_t e_ = (call);                                                                            \
+    if (e_ != cudaSuccess) return bfail(b, e_ == cudaErrorMemoryAllocation ? HY_ERR_OOM : HY_ERR_CUDA,   \
+                                        std::string(#call) + ": " + cudaGetErrorString(e_));              \
+  } while (0)
+
+constexpr int BATCH_MAX = 1024;
+constexpr size_t BATCH_ARG_BYTES = sizeof(CellArgs<double>) > sizeof(CellArgs<float>) ? sizeof(CellArgs<double>)
+                                                                                      : sizeof(CellArgs<float>);
+
+ApplyListFn<double> list_fn(int dim, int n, int var, double*) {
+  return dim == 2 ? apply_list_fn_f64_2d(n, var) : apply_list_fn_f64_3d(n, var);
+}
+ApplyListFn<float> list_fn(int dim, int n, int var, float*) {
+  return dim == 2 ? apply_list_fn_f32_2d(n, var) : apply_list_fn_f32_3d(n, var);
+}
+
+// Upload the argument list of the finest-level actions y_j = A_j x_j of the problems idx (skipped when
+// the device copy already describes exactly these vectors).
+template <typename T>
+hy_status upload_list(hy_batch* b, const std::vector<int>& idx, const std::vector<const void*>& x,
+                      const std::vector<const void*>& y) {
+  const int dt = sizeof(T) == 8 ? 0 : 1;
+  if (b->up_dt == dt && b->up_x == x && b->up_y == y) return HY_OK;
+  HB_CK(cudaEventSynchronize(b->ev_upload));  // the staging buffer is free again
+  CellArgs<T>* h = static_cast<CellArgs<T>*>(b->h_list);
+  const int cb = apply_cells_per_block(b->dim, b->n);
+  long long blocks = 0, max_nodes = 0;
+  for (size_t j = 0; j < idx.size(); ++j) {
+    hy_ctx* c = b->ctx[idx[j]];
+    Level& L = c->lev[c->nlev - 1];
+    max_nodes = std::max(max_nodes, L.nnodes);
+    CellArgs<T> a = cell_args<T>(c, L);
+    a.x = static_cast<const T*>(x[j]);
+    a.y = static_cast<T*>(const_cast<void*>(y[j]));
+    if constexpr (sizeof(T) == 8) {
+      a.cache = L.d_c64;
+      a.ubar = L.d_u64;
+    } else {
+      a.cache = L.d_c32;
+      a.ubar = L.d_u32;
+    }
+    h[j] = a;
+    b->h_start[j] = (int)blocks;
+    blocks += (L.g.ncells + cb - 1) / cb;
+  }
+  if (blocks > 0x7fffffffLL) return bfail(b, HY_ERR_ARG, "batch: too many thread blocks for one launch");
+  b->h_start[idx.size()] = (int)blocks;
+  HB_CK(cudaMemcpyAsync(b->d_list, h, sizeof(CellArgs<T>) * idx.size(), cudaMemcpyHostToDevice, b->s0));
+  HB_CK(cudaMemcpyAsync(b->d_start, b->h_start, sizeof(int) * (idx.size() + 1), cudaMemcpyHostToDevice, b->s0));
+  HB_CK(cudaEventRecord(b->ev_upload, b->s0));
+  b->up_x = x;
+  b->up_y = y;
+  b->up_dt = dt;
+  b->up_blocks = (int)blocks;
+  b->up_max_nodes = max_nodes;
+  return HY_OK;
+}
+
+// prep_out of every listed problem (one launch) followed by the list launch, on stream st; x and y are
+// the vectors the uploaded list describes.
+template <typename T>
+hy_status list_apply(hy_batch* b, const std::vector<int>& idx, const std::vector<const void*>& x,
+                     const std::vector<const void*>& y, int form, cudaStream_t st) {
+  const int var = b->ctx[idx[0]]->var;
+  ApplyListFn<T> fn = list_fn(b->dim, b->n, var, (T*)nullptr);
+  if (!fn) return bfail(b, HY_ERR_UNSUPPORTED, "batch: no kernel for this dim/degree/variant");
+  (void)x;
+  (void)y;
+  launch_prep_out_list<T>(static_cast<const CellArgs<T>*>(b->d_list), (int)idx.size(), b->dim, b->up_max_nodes, st);
+  fn(static_cast<const CellArgs<T>*>(b->d_list), b->d_start, (int)idx.size(), b->up_blocks, form, st);
+  b->launches += 2;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return bfail(b, HY_ERR_CUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+  return HY_OK;
+}
+
+// Pick the faster kernel form for the list launch of this batch and precision (timed on the real list:
+// one warm-up each, then three alternating rounds of four launches, the best round of each decides).
+template <typename T>
+hy_status tune_list(hy_batch* b, const std::vector<int>& idx, const std::vector<const void*>& x,
+                    const std::vector<const void*>& y) {
+  const int dt = sizeof(T) == 8 ? 0 : 1;
+  if (b->form[dt] >= 0) return HY_OK;
+  const int forced = b->ctx[idx[0]]->sp.kernel_form;
+  if (forced >= 0) {
+    b->form[dt] = forced;
+    return HY_OK;
+  }
+  cudaEvent_t e0, e1;
+  HB_CK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return bfail(b, HY_ERR_CUDA, "cudaEventCreate");
+  }
+  float best[2] = {1e30f, 1e30f};
+  hy_status st = HY_OK;
+  for (int f = 0; f < 2 && st == HY_OK; ++f) st = list_apply<T>(b, idx, x, y, f, b->s0);
+  for (int r = 0; r < 3 && st == HY_OK; ++r)
+    for (int f = 0; f < 2 && st == HY_OK; ++f) {
+      cudaEventRecord(e0, b->s0);
+      for (int q = 0; q < 4 && st == HY_OK; ++q) st = list_apply<T>(b, idx, x, y, f, b->s0);
+      cudaEventRecord(e1, b->s0);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      best[f] = std::min(best[f], 0.25f * ms);
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != HY_OK) return st;
+  b->form[dt] = best[1] < best[0] ? FORM_LINE : FORM_POINT;
+  if (b->ctx[idx[0]]->verbose)
+    std::fprintf(stderr, "[hy] batch of %zu: list launch %s point %.3f ms, line %.3f ms\n", idx.size(),
+                 dt ? "f32" : "f64", best[0], best[1]);
+  return HY_OK;
+}
+
+// s0 waits for the work already queued on every context's stream.
+hy_status join_in(hy_batch* b) {
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    HB_CK(cudaEventRecord(b->ev[i], b->ctx[i]->stream));
+    HB_CK(cudaStreamWaitEvent(b->s0, b->ev[i], 0));
+  }
+  return HY_OK;
+}
+// every context's stream waits for the batch's work.
+hy_status join_out(hy_batch* b) {
+  HB_CK(cudaEventRecord(b->ev_done, b->s0));
+  for (hy_ctx* c : b->ctx) HB_CK(cudaStreamWaitEvent(c->stream, b->ev_done, 0));
+  return HY_OK;
+}
+
+// The V-cycle of vcycle_top issued kernel by kernel on ctx->stream (for capture inside a batch graph).
+hy_status vcycle_top_ops(hy_ctx* ctx, const double* r, double* z) {
+  const int top = ctx->nlev - 1;
+  Level& L = ctx->lev[top];
+  if (level_f32(ctx, top)) {
+    launch_convert<double, float>(r, L.w32[0], L.ndofs, ctx->stream);
+    HY_TRY(check_launch(ctx, 1));
+    HY_TRY(vcycle_level(ctx, top));
+    launch_convert<float, double>(L.w32[1], z, L.ndofs, ctx->stream);
+    return check_launch(ctx, 1);
+  }
+  HY_CK(cudaMemcpyAsync(L.w64[0], r, sizeof(double) * L.ndofs, cudaMemcpyDeviceToDevice, ctx->stream));
+  HY_TRY(vcycle_level(ctx, top));
+  HY_CK(cudaMemcpyAsync(z, L.w64[1], sizeof(double) * L.ndofs, cudaMemcpyDeviceToDevice, ctx->stream));
+  return HY_OK;
+}
+
+// One PCG iteration of one problem after q = A p: alpha = rz/pq; x += alpha p; r -= alpha q;
+// converged = |r| <= tol; z = V r; beta = rzn/rz; p = z + beta p (scalars sc on the device).
+hy_status pcg_branch(hy_ctx* c, double* sc, double* x) {
+  const long long nd = c->lev[c->nlev - 1].ndofs;
+  double *r = c->f64[0], *z = c->f64[1], *p = c->f64[2], *q = c->f64[3];
+  cudaStream_t st = c->stream;
+  launch_dot<double>(p, q, nd, c->d_partials, sc + 1, st);
+  launch_pcg_scalar(sc, 0, st);
+  launch_axpy_dev<double>(sc + 2, 1.0, p, x, nd, st);
+  launch_axpy_dev<double>(sc + 2, -1.0, q, r, nd, st);
+  launch_dot<double>(r, r, nd, c->d_partials, sc + 3, st);
+  launch_pcg_scalar(sc, 1, st);
+  HY_TRY(check_launch(c, 8));
+  HY_TRY(vcycle_top_ops(c, r, z));
+  launch_dot<double>(r, z, nd, c->d_partials, sc + 4, st);
+  launch_pcg_scalar(sc, 2, st);
+  launch_xpay_dev<double>(z, sc + 5, p, p, nd, st);
+  return check_launch(c, 4);
+}
+
+// One PCG iteration of every resident problem R, captured into a graph on s0: the list launch
+// q_i = A_i p_i, then one branch per problem (pcg_branch), then a copy of all scalars to pinned host
+// memory. *kernels = kernels one replay launches.
+hy_status capture_iteration(hy_batch* b, const std::vector<int>& R, double* const* xsol, int form,
+                            cudaGraphExec_t* exec, long long* kernels) {
+  std::vector<const void*> ps, qs;
+  for (int i : R) {
+    ps.push_back(b->ctx[i]->f64[2]);
+    qs.push_back(b->ctx[i]->f64[3]);
+  }
+  HY_TRY(upload_list<double>(b, R, ps, qs));
+  std::vector<cudaStream_t> saved(R.size());
+  std::vector<long long> l0(R.size());
+  for (size_t j = 0; j < R.size(); ++j) {
+    saved[j] = b->ctx[R[j]]->stream;
+    l0[j] = b->ctx[R[j]]->launches;
+  }
+  const long long b0 = b->launches;
+  HB_CK(cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeThreadLocal));
+  hy_status st = list_apply<double>(b, R, ps, qs, form, b->s0);
+  if (st == HY_OK && cudaEventRecord(b->ev_fork, b->s0) != cudaSuccess) st = bfail(b, HY_ERR_CUDA, "cudaEventRecord");
+  for (size_t j = 0; j < R.size() && st == HY_OK; ++j) {
+    const int i = R[j];
+    hy_ctx* c = b->ctx[i];
+    cudaStream_t bs = b->branch[i];
+    if (cudaStreamWaitEvent(bs, b->ev_fork, 0) != cudaSuccess) {
+      st = bfail(b, HY_ERR_CUDA, "cudaStreamWaitEvent");
+      break;
+    }
+    c->stream = bs;
+    st = pcg_branch(c, b->d_scal + (size_t)i * PCG_SCALARS, xsol[i]);
+    c->stream = saved[j];
+    if (st != HY_OK) {
+      b->err = c->err;
+      break;
+    }
+    if (cudaEventRecord(b->ev[i], bs) != cudaSuccess || cudaStreamWaitEvent(b->s0, b->ev[i], 0) != cudaSuccess)
+      st = bfail(b, HY_ERR_CUDA, "branch join");
+  }
+  if (st == HY_OK &&
+      cudaMemcpyAsync(b->h_scal_out, b->d_scal, sizeof(double) * PCG_SCALARS * b->ctx.size(), cudaMemcpyDeviceToHost,
+                      b->s0) != cudaSuccess)
+    st = bfail(b, HY_ERR_CUDA, "cudaMemcpyAsync of the scalars");
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(b->s0, &g);
+  long long nk = b->launches - b0;
+  for (size_t j = 0; j < R.size(); ++j) {
+    hy_ctx* c = b->ctx[R[j]];
+    c->stream = saved[j];
+    nk += c->launches - l0[j];
+    c->launches = l0[j];
+  }
+  b->launches = b0;
+  if (st != HY_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    if (st != HY_OK) return st;
+    return bfail(b, HY_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+  }
+  e = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return bfail(b, HY_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  *kernels = nk;
+  return HY_OK;
+}
+
+hy_status batch_check(hy_batch* b) {
+  for (hy_ctx* c : b->ctx) {
+    if (c->nlev == 0 || c->dim != b->dim || c->n != b->n)
+      return bfail(b, HY_ERR_STATE, "batch: a context's mesh changed since the batch was created");
+    if (!c->state_ok) return bfail(b, HY_ERR_STATE, "batch: set_displacement on every context first");
+    if (c->var != b->ctx[0]->var) return bfail(b, HY_ERR_ARG, "batch: the contexts must use the same variant");
+  }
+  return HY_OK;
+}
+
+template <typename T>
+hy_status batch_apply(hy_batch* b, const void* const* x, void* const* y) {
+  const int cnt = (int)b->ctx.size();
+  std::vector<int> R(cnt);
+  std::vector<const void*> xs(cnt), ys(cnt);
+  for (int i = 0; i < cnt; ++i) {
+    hy_ctx* c = b->ctx[i];
+    const Level& L = c->lev[c->nlev - 1];
+    if (!(sizeof(T) == 8 ? L.has64 : L.has32))
+      return bfail(b, HY_ERR_STATE, "batch: a context has no finest-level cache of this precision");
+    if (!x[i] || !y[i] || x[i] == y[i]) return bfail(b, HY_ERR_ARG, "batch: null or aliased vectors");
+    R[i] = i;
+    xs[i] = x[i];
+    ys[i] = y[i];
+  }
+  HY_TRY(join_in(b));
+  HY_TRY(upload_list<T>(b, R, xs, ys));
+  HY_TRY(tune_list<T>(b, R, xs, ys));
+  HY_TRY(list_apply<T>(b, R, xs, ys, b->form[sizeof(T) == 8 ? 0 : 1], b->s0));
+  return join_out(b);
+}
+
+hy_status batch_pcg(hy_batch* b, const double* const* rhs, double* const* xs, double rtol, int max_iter, int* its,
+                    hy_status* sts) {
+  const int cnt = (int)b->ctx.size();
+  std::vector<int> R;
+  for (int i = 0; i < cnt; ++i) {
+    its[i] = 0;
+    sts[i] = HY_OK;
+    if (!rhs[i] || !xs[i]) return bfail(b, HY_ERR_ARG, "batch: null vectors");
+  }
+  for (int i = 0; i < cnt; ++i) {
+    hy_ctx* c = b->ctx[i];
+    if (!c->coarse_spd) {
+      sts[i] = fail(c, HY_ERR_NOCONV, "coarsest-level tangent is not positive definite");
+      continue;
+    }
+    const long long nd = c->lev[c->nlev - 1].ndofs;
+    double *r = c->f64[0], *z = c->f64[1], *p = c->f64[2];
+    hy_status st = HY_OK;
+    double bb = 0.0;
+    if (cudaMemsetAsync(xs[i], 0, sizeof(double) * nd, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(r, rhs[i], sizeof(double) * nd, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+      st = fail(c, HY_ERR_CUDA, "batch pcg: initial copies");
+    if (st == HY_OK) st = dot<double>(c, rhs[i], rhs[i], nd, &bb);
+    const double nb = std::sqrt(bb);
+    if (st == HY_OK && nb == 0.0) continue;
+    if (st == HY_OK && !(nb == nb)) st = fail(c, HY_ERR_ARG, "pcg: right-hand side has NaN");
+    if (st == HY_OK) st = vcycle_top(c, r, z);
+    if (st == HY_OK && cudaMemcpyAsync(p, z, sizeof(double) * nd, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+      st = fail(c, HY_ERR_CUDA, "batch pcg: copy");
+    if (st == HY_OK) {
+      double* hs = b->h_scal_in + (size_t)i * PCG_SCALARS;
+      for (int k = 0; k < PCG_SCALARS; ++k) hs[k] = 0.0;
+      hs[6] = rtol * nb;
+      if (cudaMemcpyAsync(b->d_scal + (size_t)i * PCG_SCALARS, hs, sizeof(double) * PCG_SCALARS,
+                          cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+        st = fail(c, HY_ERR_CUDA, "batch pcg: scalars");
+    }
+    if (st == HY_OK) {
+      launch_dot<double>(r, z, nd, c->d_partials, b->d_scal + (size_t)i * PCG_SCALARS, c->stream);
+      st = check_launch(c, 2);
+    }
+    if (st != HY_OK) {
+      sts[i] = st;
+      continue;
+    }
+    R.push_back(i);
+  }
+  HY_TRY(join_in(b));
+  hy_status result = HY_OK;
+  if (!R.empty()) {
+    std::vector<const void*> ps, qs;
+    for (int i : R) {
+      ps.push_back(b->ctx[i]->f64[2]);
+      qs.push_back(b->ctx[i]->f64[3]);
+    }
+    result = upload_list<double>(b, R, ps, qs);
+    if (result == HY_OK) result = tune_list<double>(b, R, ps, qs);
+  }
+  // R: problems in the current graph; live: those still iterating. A finished problem stays in the graph
+  // as a no-op (alpha = beta = 0 on the device) until a quarter of the graph's problems have finished,
+  // then the graph is captured again for the live ones.
+  cudaGraphExec_t exec = nullptr;
+  long long nk = 0;
+  bool rebuild = true;
+  std::vector<char> live(cnt, 0);
+  for (int i : R) live[i] = 1;
+  size_t n_live = R.size();
+  double t_capture = 0.0, t_replay = 0.0;
+  int n_capture = 0, n_replay = 0;
+  while (result == HY_OK && n_live > 0) {
+    if (rebuild) {
+      if (exec) cudaGraphExecDestroy(exec);
+      exec = nullptr;
+      std::vector<int> keep;
+      for (int i : R)
+        if (live[i]) keep.push_back(i);
+      R.swap(keep);
+      const auto t0 = std::chrono::steady_clock::now();
+      result = capture_iteration(b, R, xs, b->form[0], &exec, &nk);
+      t_capture += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      ++n_capture;
+      if (result != HY_OK) break;
+      rebuild = false;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaError_t e = cudaGraphLaunch(exec, b->s0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->s0);
+    t_replay += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    ++n_replay;
+    if (e != cudaSuccess) {
+      result = bfail(b, HY_ERR_CUDA, std::string("batch pcg iteration: ") + cudaGetErrorString(e));
+      break;
+    }
+    b->launches += nk;
+    size_t finished_in_graph = 0;
+    for (int i : R) {
+      if (!live[i]) {
+        ++finished_in_graph;
+        continue;
+      }
+      const double* h = b->h_scal_out + (size_t)i * PCG_SCALARS;
+      bool done = true;
+      if (h[8] != 0.0) {
+        sts[i] = fail(b->ctx[i], HY_ERR_NOCONV, "pcg: p^T A p <= 0 (operator not SPD)");
+      } else {
+        ++its[i];
+        if (h[7] == 0.0) {
+          if (its[i] >= max_iter) {
+            sts[i] = fail(b->ctx[i], HY_ERR_NOCONV, "pcg: iteration cap reached");
+            // mark it finished on the device too, so that replays before the next capture leave it alone
+            double* one = b->h_scal_in + (size_t)i * PCG_SCALARS + 7;
+            *one = 1.0;
+            if (cudaMemcpyAsync(b->d_scal + (size_t)i * PCG_SCALARS + 7, one, sizeof(double), cudaMemcpyHostToDevice,
+                                b->s0) != cudaSuccess)
+              result = bfail(b, HY_ERR_CUDA, "batch pcg: finish flag");
+          } else {
+            done = false;
+          }
+        }
+      }
+      if (done) {
+        live[i] = 0;
+        --n_live;
+        ++finished_in_graph;
+      }
+    }
+    if (n_live > 0 && 4 * finished_in_graph >= R.size()) rebuild = true;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (b->ctx[0]->verbose)
+    std::fprintf(stderr, "[hy] batch pcg of %d: %d captures %.2f ms, %d replays %.2f ms\n", cnt, n_capture, t_capture,
+                 n_replay, t_replay);
+  const hy_status jo = join_out(b);
+  if (result == HY_OK && jo == HY_OK)
+    for (int i = 0; i < cnt; ++i)
+      if (sts[i] == HY_OK) sts[i] = check_error_word(b->ctx[i], "batch pcg");
+  return result != HY_OK ? result : jo;
+}
+
+void batch_free(hy_batch* b) {
+  if (b->s0) cudaStreamSynchronize(b->s0);
+  for (cudaStream_t s : b->branch)
+    if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->ev)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : {b->ev_fork, b->ev_done, b->ev_upload})
+    if (e) cudaEventDestroy(e);
+  if (b->d_list) cudaFree(b->d_list);
+  if (b->d_start) cudaFree(b->d_start);
+  if (b->d_scal) cudaFree(b->d_scal);
+  if (b->h_list) cudaFreeHost(b->h_list);
+  if (b->h_start) cudaFreeHost(b->h_start);
+  if (b->h_scal_in) cudaFreeHost(b->h_scal_in);
+  if (b->h_scal_out) cudaFreeHost(b->h_scal_out);
+  if (b->s0) cudaStreamDestroy(b->s0);
+  delete b;
 }
 
 }  // namespace
@@ -1666,6 +2158,86 @@ hy_status hy_ctx_bytes(const hy_ctx* ctx, int64_t* bytes) {
 hy_status hy_kernel_launches(const hy_ctx* ctx, int64_t* count) {
   if (!ctx || !count) return HY_ERR_ARG;
   *count = ctx->launches;
+  return HY_OK;
+}
+
+hy_status hy_batch_create(hy_batch** out, hy_ctx* const* ctxs, int count) {
+  if (!out) return HY_ERR_ARG;
+  *out = nullptr;
+  if (!ctxs || count < 1 || count > HY_BATCH_MAX) return HY_ERR_ARG;
+  for (int i = 0; i < count; ++i) {
+    if (!ctxs[i] || ctxs[i]->nlev == 0) return HY_ERR_STATE;
+    if (ctxs[i]->device != ctxs[0]->device || ctxs[i]->dim != ctxs[0]->dim || ctxs[i]->n != ctxs[0]->n)
+      return HY_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return HY_ERR_ARG;
+  }
+  if (cudaSetDevice(ctxs[0]->device) != cudaSuccess) return HY_ERR_CUDA;
+  hy_batch* b = new (std::nothrow) hy_batch();
+  if (!b) return HY_ERR_OOM;
+  b->device = ctxs[0]->device;
+  b->dim = ctxs[0]->dim;
+  b->n = ctxs[0]->n;
+  b->ctx.assign(ctxs, ctxs + count);
+  b->branch.assign(count, nullptr);
+  b->ev.assign(count, nullptr);
+  bool ok = cudaStreamCreateWithFlags(&b->s0, cudaStreamNonBlocking) == cudaSuccess;
+  for (int i = 0; i < count && ok; ++i)
+    ok = cudaStreamCreateWithFlags(&b->branch[i], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->ev[i], cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+       cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming) == cudaSuccess &&
+       cudaEventCreateWithFlags(&b->ev_upload, cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->d_list, BATCH_ARG_BYTES * count) == cudaSuccess &&
+       cudaMalloc((void**)&b->d_start, sizeof(int) * (count + 1)) == cudaSuccess &&
+       cudaMalloc((void**)&b->d_scal, sizeof(double) * PCG_SCALARS * count) == cudaSuccess &&
+       cudaMallocHost(&b->h_list, BATCH_ARG_BYTES * count) == cudaSuccess &&
+       cudaMallocHost((void**)&b->h_start, sizeof(int) * (count + 1)) == cudaSuccess &&
+       cudaMallocHost((void**)&b->h_scal_in, sizeof(double) * PCG_SCALARS * count) == cudaSuccess &&
+       cudaMallocHost((void**)&b->h_scal_out, sizeof(double) * PCG_SCALARS * count) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    batch_free(b);
+    return HY_ERR_OOM;
+  }
+  *out = b;
+  return HY_OK;
+}
+
+void hy_batch_destroy(hy_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  batch_free(b);
+}
+
+const char* hy_batch_last_error(const hy_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+hy_status hy_batch_apply(hy_batch* b, const void* const* x, void* const* y, hy_dtype dtype) {
+  if (!b || !x || !y) return HY_ERR_ARG;
+  HB_CK(cudaSetDevice(b->device));
+  HY_TRY(batch_check(b));
+  if (dtype == HY_F64) return batch_apply<double>(b, x, y);
+  if (dtype == HY_F32) return batch_apply<float>(b, x, y);
+  return bfail(b, HY_ERR_ARG, "bad dtype");
+}
+
+hy_status hy_batch_pcg(hy_batch* b, const double* const* rhs, double* const* x, double rtol, int max_iter,
+                       int* iterations, hy_status* status) {
+  if (!b || !rhs || !x || !iterations || !status || !(rtol > 0) || max_iter < 1) return HY_ERR_ARG;
+  HB_CK(cudaSetDevice(b->device));
+  HY_TRY(batch_check(b));
+  return batch_pcg(b, rhs, x, rtol, max_iter, iterations, status);
+}
+
+hy_status hy_batch_kernel_launches(const hy_batch* b, int64_t* count) {
+  if (!b || !count) return HY_ERR_ARG;
+  *count = b->launches;
+  return HY_OK;
+}
+
+hy_status hy_batch_kernel_form(const hy_batch* b, hy_dtype dtype, int* form) {
+  if (!b || !form || (dtype != HY_F64 && dtype != HY_F32)) return HY_ERR_ARG;
+  *form = b->form[dtype == HY_F64 ? 0 : 1];
   return HY_OK;
 }
 

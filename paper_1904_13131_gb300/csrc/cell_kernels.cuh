@@ -557,9 +557,9 @@ __device__ __forceinline__ void qp_flux(const T G[DIM][DIM], const T Gu[DIM][DIM
 //   FC: cache F, recompute the neo-Hooke state      SC: cache mu - 2 lambda ln J, recompute F (Algorithm 1)
 //   NC: nothing cached, recompute F and the state from the gathered displacement.
 // Constrained dofs: x is read as zero there and nothing is added to y there.
+// blk is the index of the block of cells (and of the cache chunk) that this thread block processes.
 template <int DIM, int N, int VAR, typename T>
-__global__ void __launch_bounds__(cells_per_block(DIM, N) * ipow(N, DIM))
-apply_kernel(const CellArgs<T> a) {
+__device__ __forceinline__ void apply_point_body(const CellArgs<T>& a, const int blk) {
   constexpr int NPT = ipow(N, DIM);
   constexpr int CB = cells_per_block(DIM, N);
   constexpr int NS = nsym(DIM);
@@ -573,12 +573,12 @@ apply_kernel(const CellArgs<T> a) {
   if (NV > 0 && threadIdx.x == 0) {
     // the chunk streams in (TMA bulk copy) while the block gathers x and runs the forward sweeps
     mbar_init(&bar, 1);
-    bulk_load(cs, a.cache + (size_t)blockIdx.x * NV * BS, (unsigned)(NV * BS * sizeof(T)), &bar);
+    bulk_load(cs, a.cache + (size_t)blk * NV * BS, (unsigned)(NV * BS * sizeof(T)), &bar);
   }
   load_tables<DIM, N>(s, a);
   const int cl = threadIdx.x / NPT;
   const Pt<DIM, N> pt(threadIdx.x % NPT);
-  const int cell = blockIdx.x * CB + cl;
+  const int cell = blk * CB + cl;
   const bool active = cell < a.g.ncells;
   const CellLoc<DIM, N> loc(a.g, active ? cell : 0, pt);
   T* b0 = &s.b0[cl][0][0];
@@ -658,8 +658,7 @@ apply_kernel(const CellArgs<T> a) {
 // values through shared memory, the thread playing the line (q0 varies; q1 = l1, q2 = l2) of each stage.
 // Same arithmetic, variants and Dirichlet treatment as apply_kernel.
 template <int DIM, int N, int VAR, typename T>
-__global__ void __launch_bounds__(cells_per_block_line(DIM, N) * ipow(N, DIM - 1))
-apply_line_kernel(const CellArgs<T> a) {
+__device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int blk) {
   constexpr int NPT = ipow(N, DIM);
   constexpr int NLC = ipow(N, DIM - 1);
   constexpr int CB = cells_per_block_line(DIM, N);
@@ -680,7 +679,7 @@ apply_line_kernel(const CellArgs<T> a) {
   // STAGE: the block's cache chunk streams into shared memory with one bulk copy (measured faster for
   // T4 than reading the cache straight from global memory at the Gauss points, 18.3 vs 12.9 GDoF/s).
   constexpr bool STAGE = HY_LINE_STAGE;
-  const T* cg = a.cache + (size_t)blockIdx.x * NV * BS;
+  const T* cg = a.cache + (size_t)blk * NV * BS;
   if (STAGE && NV > 0 && t == 0) {
     mbar_init(&bar, 1);
     bulk_load(cs, cg, (unsigned)(NV * BS * sizeof(T)), &bar);
@@ -707,7 +706,7 @@ apply_line_kernel(const CellArgs<T> a) {
   }
   const int cl = t / NLC, l = t % NLC;
   const int l1 = l % N, l2 = DIM == 3 ? l / N : 0;
-  const int cell = blockIdx.x * CB + cl;
+  const int cell = blk * CB + cl;
   const bool active = cell < a.g.ncells;
   const int m = a.g.m;
   const int cc = active ? cell : 0;
@@ -939,6 +938,46 @@ apply_line_kernel(const CellArgs<T> a) {
       for (int j = 0; j < N; ++j) s = fma(tS[j][a0], Yb[j][c], s);
       atomicAdd(&a.y[(node0 + a0) * DIM + c], s);
     }
+}
+
+// ---- kernels: one problem (arguments by value), or a work list of problems in one launch ----------
+// Work list: problem p owns the thread blocks start[p] .. start[p+1]-1 of the grid (start[count] = grid
+// size); each problem's arguments are read from global memory. The problems share dim, degree, variant
+// and precision, and may differ in everything else (mesh size, material, cache, vectors).
+__device__ __forceinline__ int work_item(const int* __restrict__ start, int count, int b) {
+  int lo = 0, hi = count - 1;  // the last p with start[p] <= b
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(start + mid) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int DIM, int N, int VAR, typename T>
+__global__ void __launch_bounds__(cells_per_block(DIM, N) * ipow(N, DIM))
+apply_kernel(const CellArgs<T> a) {
+  apply_point_body<DIM, N, VAR, T>(a, blockIdx.x);
+}
+
+template <int DIM, int N, int VAR, typename T>
+__global__ void __launch_bounds__(cells_per_block(DIM, N) * ipow(N, DIM))
+apply_list_kernel(const CellArgs<T>* __restrict__ list, const int* __restrict__ start, int count) {
+  const int p = work_item(start, count, blockIdx.x);
+  apply_point_body<DIM, N, VAR, T>(list[p], blockIdx.x - start[p]);
+}
+
+template <int DIM, int N, int VAR, typename T>
+__global__ void __launch_bounds__(cells_per_block_line(DIM, N) * ipow(N, DIM - 1))
+apply_line_kernel(const CellArgs<T> a) {
+  apply_line_body<DIM, N, VAR, T>(a, blockIdx.x);
+}
+
+template <int DIM, int N, int VAR, typename T>
+__global__ void __launch_bounds__(cells_per_block_line(DIM, N) * ipow(N, DIM - 1))
+apply_line_list_kernel(const CellArgs<T>* __restrict__ list, const int* __restrict__ start, int count) {
+  const int p = work_item(start, count, blockIdx.x);
+  apply_line_body<DIM, N, VAR, T>(list[p], blockIdx.x - start[p]);
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -1,0 +1,7 @@
+// Tangent-action kernels, float, dim 3, degrees 3-4, all five variants, one problem or a work list.
+#define INST_DIM 3
+#define INST_T float
+#define INST_NLO 4
+#define INST_NAME apply_fn_f32_3d_hi
+#define INST_LIST_NAME apply_list_fn_f32_3d_hi
+#include "inst_apply.inc"

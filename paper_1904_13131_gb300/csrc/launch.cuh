@@ -16,11 +16,32 @@ using ApplyFn = void (*)(const CellArgs<T>&, int form, cudaStream_t);
 template <typename TOUT>
 using StateFn = void (*)(const CellArgs<double>&, TOUT*, cudaStream_t);
 
-// n = degree + 1 in 2..5; var in Variant; returns nullptr for unsupported combinations
-ApplyFn<double> apply_fn_f64_2d(int n, int var);
-ApplyFn<double> apply_fn_f64_3d(int n, int var);
-ApplyFn<float> apply_fn_f32_2d(int n, int var);
-ApplyFn<float> apply_fn_f32_3d(int n, int var);
+// tangent action over a work list of problems in one launch: list[count] arguments in device memory,
+// start[count + 1] first thread block of each problem, blocks = start[count]
+template <typename T>
+using ApplyListFn = void (*)(const CellArgs<T>* list, const int* start, int count, int blocks, int form,
+                             cudaStream_t);
+// cells per thread block of the tangent action (both forms): the work-list block counts
+inline int apply_cells_per_block(int dim, int n) { return cells_per_block(dim, n); }
+
+// n = degree + 1 in 2..5; var in Variant; returns nullptr for unsupported combinations. The kernels of
+// degrees 1-2 (n <= 3) and 3-4 live in separate translation units (_lo, _hi) that compile in parallel.
+#define HY_APPLY_TABLES(P, TAG, D)                                                                      \
+  ApplyFn<P> apply_fn_##TAG##_##D##_lo(int n, int var);                                              \
+  ApplyFn<P> apply_fn_##TAG##_##D##_hi(int n, int var);                                              \
+  ApplyListFn<P> apply_list_fn_##TAG##_##D##_lo(int n, int var);                                     \
+  ApplyListFn<P> apply_list_fn_##TAG##_##D##_hi(int n, int var);                                     \
+  inline ApplyFn<P> apply_fn_##TAG##_##D(int n, int var) {                                           \
+    return n <= 3 ? apply_fn_##TAG##_##D##_lo(n, var) : apply_fn_##TAG##_##D##_hi(n, var);             \
+  }                                                                                                \
+  inline ApplyListFn<P> apply_list_fn_##TAG##_##D(int n, int var) {                                  \
+    return n <= 3 ? apply_list_fn_##TAG##_##D##_lo(n, var) : apply_list_fn_##TAG##_##D##_hi(n, var);   \
+  }
+HY_APPLY_TABLES(double, f64, 2d)
+HY_APPLY_TABLES(double, f64, 3d)
+HY_APPLY_TABLES(float, f32, 2d)
+HY_APPLY_TABLES(float, f32, 3d)
+#undef HY_APPLY_TABLES
 StateFn<double> state_fn_f64(int dim, int n, int var);   // var VAR_NONE: J check only
 StateFn<float> state_fn_f32(int dim, int n, int var);
 CellFn<double> residual_fn(int dim, int n);
@@ -30,6 +51,10 @@ constexpr int VAR_NONE = 5;
 
 // ---- vector kernels (vec_kernels.cu) ----------------------------------------------------------
 template <typename T> void launch_prep_out(const T* x, T* y, long long n_nodes, int dim, const Geom& g, cudaStream_t st);
+// prep_out of each problem of a work list (list in device memory, count problems, the largest with
+// max_nodes lattice nodes), one launch
+template <typename T> void launch_prep_out_list(const CellArgs<T>* list, int count, int dim, long long max_nodes,
+                                                cudaStream_t st);
 template <typename T> void launch_zero_constrained(T* y, long long n_nodes, int dim, const Geom& g, cudaStream_t st);
 template <typename T> void launch_set_constrained_one(T* y, long long n_nodes, int dim, const Geom& g, cudaStream_t st);
 template <typename T> void launch_invert(const double* d, T* dinv, long long n, cudaStream_t st);
@@ -54,6 +79,10 @@ template <typename T> void launch_xpay_dev(const T* x, const double* beta, const
 // device-side scalars of one CG step of the eigenvalue estimate (s: 8 doubles; hist: 2 * iters)
 void launch_eig_alpha(double* s, double* hist, int it, cudaStream_t st);
 void launch_eig_beta(double* s, double* hist, int it, int iters, cudaStream_t st);
+// device-side scalars of one preconditioned CG step (s: 9 doubles {rz, pq, alpha, rr, rzn, beta, tol,
+// converged, not_spd}); op 0 alpha, 1 convergence test, 2 beta
+constexpr int PCG_SCALARS = 16;  // stride of one problem's scalars
+void launch_pcg_scalar(double* s, int op, cudaStream_t st);
 // r = b - t
 template <typename T> void launch_sub(const T* b, const T* t, T* r, long long n, cudaStream_t st);
 // du0 = constrained ? target - u : 0, target from per-face values scaled by factor

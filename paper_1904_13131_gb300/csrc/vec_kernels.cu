@@ -2,6 +2,9 @@
 // conversion, deterministic dot products, and the separable transfer sweeps of the multigrid.
 // All are bandwidth-bound streams over lattice vectors; grids cover the vector with 256-thread
 // blocks (grid-stride loops capped at a multiple of the SM count).
+#include <algorithm>
+
+#include "cell_kernels.cuh"
 #include "launch.cuh"
 
 namespace hy {
@@ -31,6 +34,18 @@ __global__ void prep_out_kernel(const T* __restrict__ x, T* __restrict__ y, long
     const uint32_t cm = cmask_of<DIM>(g, nd);
 #pragma unroll
     for (int c = 0; c < DIM; ++c) y[nd * DIM + c] = ((cm >> c) & 1u) ? x[nd * DIM + c] : T(0);
+  }
+}
+
+// prep_out of every problem of a work list: blockIdx.y = problem, x and y and the lattice from its arguments
+template <typename T, int DIM>
+__global__ void prep_out_list_kernel(const CellArgs<T>* __restrict__ list) {
+  const CellArgs<T>& a = list[blockIdx.y];
+  const long long n_nodes = (long long)a.g.L * a.g.L * (DIM == 3 ? a.g.L : 1);
+  for (long long nd = blockIdx.x * (long long)blockDim.x + threadIdx.x; nd < n_nodes; nd += (long long)gridDim.x * blockDim.x) {
+    const uint32_t cm = cmask_of<DIM>(a.g, nd);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) a.y[nd * DIM + c] = ((cm >> c) & 1u) ? a.x[nd * DIM + c] : T(0);
   }
 }
 
@@ -163,6 +178,33 @@ __global__ void eig_alpha_kernel(double* s, double* hist, int it) {
   s[4] = alpha;
   if (!stopped) hist[it] = alpha;
 }
+// Scalars of one preconditioned CG step, kept on the device (the batched solve). s = {rz, pq, alpha, rr,
+// rzn, beta, tol, converged, not_spd}. op 0: alpha = rz / pq (0 and not_spd set when pq <= 0);
+// op 1: converged = sqrt(rr) <= tol; op 2: beta = rzn / rz, rz = rzn. Once converged or not_spd is set it
+// stays set and alpha = beta = 0: later iterations of a finished problem leave x and r unchanged.
+__global__ void pcg_scalar_kernel(double* s, int op) {
+  const bool finished = s[7] != 0.0 || s[8] != 0.0;
+  if (op == 0) {
+    const double pq = s[1];
+    if (finished) {
+      s[2] = 0.0;
+    } else if (pq > 0.0) {
+      s[2] = s[0] / pq;
+    } else {
+      s[2] = 0.0;
+      s[8] = 1.0;
+    }
+  } else if (op == 1) {
+    if (!finished && sqrt(s[3]) <= s[6]) s[7] = 1.0;
+  } else {
+    if (finished) {
+      s[5] = 0.0;
+    } else {
+      s[5] = s[4] / s[0];
+      s[0] = s[4];
+    }
+  }
+}
 __global__ void eig_beta_kernel(double* s, double* hist, int it, int iters) {
   if (s[6] != 0.0) {
     s[5] = 0.0;
@@ -241,6 +283,17 @@ void launch_prep_out(const T* x, T* y, long long n_nodes, int dim, const Geom& g
   else prep_out_kernel<T, 3><<<grid_for(n_nodes), TPB, 0, st>>>(x, y, n_nodes, g);
 }
 template <typename T>
+void launch_prep_out_list(const CellArgs<T>* list, int count, int dim, long long max_nodes, cudaStream_t st) {
+  if (count <= 0) return;
+  long long gx = (max_nodes + TPB - 1) / TPB;
+  const long long cap = std::max<long long>(1, 152LL * 16 / count);  // about one wave over all problems
+  if (gx > cap) gx = cap;
+  if (gx < 1) gx = 1;
+  const dim3 grid((unsigned)gx, (unsigned)count);
+  if (dim == 2) prep_out_list_kernel<T, 2><<<grid, TPB, 0, st>>>(list);
+  else prep_out_list_kernel<T, 3><<<grid, TPB, 0, st>>>(list);
+}
+template <typename T>
 void launch_zero_constrained(T* y, long long n_nodes, int dim, const Geom& g, cudaStream_t st) {
   if (dim == 2) set_constrained_kernel<T, 2><<<grid_for(n_nodes), TPB, 0, st>>>(y, n_nodes, g, T(0));
   else set_constrained_kernel<T, 3><<<grid_for(n_nodes), TPB, 0, st>>>(y, n_nodes, g, T(0));
@@ -282,6 +335,7 @@ template <typename T>
 void launch_xpay_dev(const T* x, const double* beta, const T* y, T* z, long long n, cudaStream_t st) {
   xpay_dev_kernel<T><<<grid_for(n), TPB, 0, st>>>(x, beta, y, z, n);
 }
+void launch_pcg_scalar(double* s, int op, cudaStream_t st) { pcg_scalar_kernel<<<1, 1, 0, st>>>(s, op); }
 void launch_eig_alpha(double* s, double* hist, int it, cudaStream_t st) { eig_alpha_kernel<<<1, 1, 0, st>>>(s, hist, it); }
 void launch_eig_beta(double* s, double* hist, int it, int iters, cudaStream_t st) {
   eig_beta_kernel<<<1, 1, 0, st>>>(s, hist, it, iters);
@@ -325,6 +379,7 @@ void launch_sweep(const T* in, T* out, int dim, const int Lin[3], const int Lout
 
 #define HY_INST(T)                                                                                              \
   template void launch_prep_out<T>(const T*, T*, long long, int, const Geom&, cudaStream_t);                    \
+  template void launch_prep_out_list<T>(const CellArgs<T>*, int, int, long long, cudaStream_t);                  \
   template void launch_zero_constrained<T>(T*, long long, int, const Geom&, cudaStream_t);                      \
   template void launch_set_constrained_one<T>(T*, long long, int, const Geom&, cudaStream_t);                   \
   template void launch_invert<T>(const double*, T*, long long, cudaStream_t);                                   \

@@ -146,3 +146,37 @@ def test_deterministic_dot(torch):
         vals = {ctx.dot(a, b) for _ in range(5)}
         assert len(vals) == 1
         assert abs(vals.pop() - float(a.cpu().numpy() @ b.cpu().numpy())) < 1e-10 * n
+
+
+_TUNE_SCRIPT = """
+import json, sys, torch
+from paper_1904_13131_gb300 import api, inputs
+pr = inputs.problem(3, 2, 4, n_levels=2, top=inputs.normal_top_mask(3))
+with api.Context(0) as c:
+    c.setup_problem(pr)
+    c.set_displacement(torch.tensor(inputs.smooth_field(3, 2, 4, seed=1), device="cuda"), "FC", level_dtype=1)
+    print(json.dumps([c.kernel_form(1, 0), c.kernel_form(1, 1)]))
+"""
+
+
+def test_tuning_file_is_json_and_reused(torch, tmp_path):
+    """A fresh process tunes and writes HY_TUNE_FILE (a JSON array of decisions); a second process reads
+    the decisions back instead of timing again (HY_VERBOSE prints a line per timing)."""
+    import json
+    import os
+    import subprocess
+    import sys
+    path = tmp_path / "tune.json"
+    env = dict(os.environ, HY_TUNE_FILE=str(path), HY_VERBOSE="1")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    runs = [subprocess.run([sys.executable, "-c", _TUNE_SCRIPT], env=env, cwd=root, capture_output=True, text=True,
+                           timeout=600) for _ in range(2)]
+    for r in runs:
+        assert r.returncode == 0, r.stderr[-2000:]
+    entries = json.loads(path.read_text())
+    assert entries and all(set(e) == {"dim", "degree", "variant", "precision", "cells_log2", "threads_per_cell"}
+                           for e in entries)
+    assert {(e["variant"], e["precision"], e["cells_log2"]) for e in entries} >= {("FC", "f64", 6), ("FC", "f32", 6)}
+    assert "[hy] autotune dim" in runs[0].stderr and "[hy] autotune dim" not in runs[1].stderr
+    f1, f2 = (json.loads(r.stdout.strip().splitlines()[-1]) for r in runs)
+    assert f1 == f2 and all(f in (0, 1) for f in f1)

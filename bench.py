@@ -144,15 +144,16 @@ def setup_contexts(torch, api, inputs, dev):
     for var in ALL_VARIANTS:
         c = api.Context(dev.index)
         c.setup_problem(pr)
-        c.set_solver_params(coarse_eig_iters=5)  # one-level hierarchy: the estimate is not used here
-        c.set_displacement(u, var, level_dtype=1)  # FP64 and FP32 caches
+        # one-level hierarchy: the coarse estimate is not used here; FP64, FP32 and double-float caches
+        c.set_solver_params(coarse_eig_iters=5, fine_dtype=api.FF)
+        c.set_displacement(u, var, level_dtype=1)
         ctxs[var] = c
     return pr, u, x, ctxs
 
 
 def time_applies(torch, ctxs, variants, x, dtype, steps, warmup, flush, stream):
     """Per-(step, variant) CUDA-event durations in ms, L2 flushed before every application."""
-    xin = x if dtype == 0 else x.float()
+    xin = x.float() if dtype == 1 else x
     ys = {v: torch.empty_like(xin) for v in variants}
     for _ in range(warmup):
         for v in variants:
@@ -186,8 +187,9 @@ def solve_latency(torch, api, inputs, dev):
     out, sols = {}, {}
     with api.Context(dev.index) as c:
         c.setup_problem(pr)
-        for name, ldt, coarse in (("fp64", 0, 0), ("mixed", 1, 0), ("mixed_exact_coarse", 1, 1)):
-            c.set_solver_params(coarse_solver=coarse)
+        for name, ldt, coarse, fine in (("fp64", 0, 0, 0), ("mixed", 1, 0, 0), ("mixed_exact_coarse", 1, 1, 0),
+                                        ("mixed_exact_coarse_ff", 1, 1, 2)):
+            c.set_solver_params(coarse_solver=coarse, fine_dtype=fine)
             u = torch.zeros(inputs.n_dofs(DIM, K, M), dtype=torch.float64, device=dev)
             rep = c.newton_solve(u, api.Context.newton_params(level_dtype=ldt, face_values=fv))
             lat = np.array(rep["solve_ms"])
@@ -200,7 +202,10 @@ def solve_latency(torch, api, inputs, dev):
     out["mixed_vs_fp64_rel_l2"] = float(np.linalg.norm(sols["mixed"] - sols["fp64"]) / np.linalg.norm(sols["fp64"]))
     out["exact_coarse_vs_fp64_rel_l2"] = float(np.linalg.norm(sols["mixed_exact_coarse"] - sols["fp64"]) /
                                                np.linalg.norm(sols["fp64"]))
-    out["coarse_solvers"] = "fp64/mixed: Chebyshev to 1e-3 on 4^3 (Sec. 7); mixed_exact_coarse: dense inverse"
+    out["ff_vs_fp64_rel_l2"] = float(np.linalg.norm(sols["mixed_exact_coarse_ff"] - sols["fp64"]) /
+                                     np.linalg.norm(sols["fp64"]))
+    out["coarse_solvers"] = ("fp64/mixed: Chebyshev to 1e-3 on 4^3 (Sec. 7); mixed_exact_coarse: dense inverse; "
+                             "_ff: double-float finest-level action in the outer CG")
     out["workload"] = "32^3 Q2 (823,875 dofs), 10% compression in 5 load steps, 4 levels, CG rtol 1e-8, T4"
     return out
 
@@ -223,7 +228,7 @@ def serve_bench(api, inputs, dev, n_req, seed=0, max_active=8, budget_gb=160):
         return api.Context.newton_params(face_values=fv, level_dtype=ldt)
 
     def run(max_act, ldt, coarse, arrivals=None):
-        sp = api.SolverParams(4, 1, 0.6, 1.2, 30, 0, 1e-3, coarse, -1)
+        sp = api.SolverParams(4, 1, 0.6, 1.2, 30, 0, 1e-3, coarse, -1, 0)
         out = {}
         with api.Server(dev.index, budget_bytes=budget_gb << 30, max_active=max_act) as sv:
             t0 = time.perf_counter()
@@ -425,14 +430,15 @@ def main():
         pr = inputs.problem(DIM, K, M, n_levels=1, top=0)
         u = torch.tensor(inputs.smooth_field(DIM, K, M, seed=0), device=dev)
         x = torch.tensor(inputs.gaussian_vector(inputs.n_dofs(DIM, K, M), seed=1), device=dev)
+        code = {"f64": 0, "f32": 1, "ff": 2}[dt]
         with api.Context(dev.index) as c:
             c.setup_problem(pr)
-            c.set_solver_params(coarse_eig_iters=5, kernel_form=args.form)
-            c.set_displacement(u, var, level_dtype=1 if dt == "f32" else 0)
-            xin = x.float() if dt == "f32" else x
+            c.set_solver_params(coarse_eig_iters=5, kernel_form=args.form, fine_dtype=api.FF if code == 2 else api.F64)
+            c.set_displacement(u, var, level_dtype=1 if code == 1 else 0)
+            xin = x.float() if code == 1 else x
             y = torch.empty_like(xin)
             for _ in range(args.reps):
-                c.apply_tangent(xin, y, dtype=1 if dt == "f32" else 0)
+                c.apply_tangent(xin, y, dtype=code)
             torch.cuda.synchronize()
         print(json.dumps({"only": args.only, "reps": args.reps}))
         return
@@ -472,17 +478,21 @@ def main():
     # ---- per-variant FP64 / FP32 throughput (untimed for the headline) ---------------------------
     ms64, _, _ = time_applies(torch, ctxs, ALL_VARIANTS, x, 0, 5, 2, flush, stream)
     ms32, _, _ = time_applies(torch, ctxs, ALL_VARIANTS, x, 1, 5, 2, flush, stream)
+    msff, _, _ = time_applies(torch, ctxs, ALL_VARIANTS, x, 2, 5, 2, flush, stream)
     hbm, hbm_src, fp64_peak = peaks()
     variants = {}
     for i, v in enumerate(ALL_VARIANTS):
-        t64, t32 = float(np.median(ms64[:, i])), float(np.median(ms32[:, i]))
+        t64, t32, tff = float(np.median(ms64[:, i])), float(np.median(ms32[:, i])), float(np.median(msff[:, i]))
         variants[v] = {
             "f64_gdofs": n / (t64 * 1e-3) / 1e9, "f64_ms": t64,
             "f64_tflops": flops_per_qp(v) * nqp / (t64 * 1e-3) / 1e12,
             "f32_gdofs": n / (t32 * 1e-3) / 1e9, "f32_ms": t32,
             "f32_gbs": bytes_per_apply(v, 4, nqp, n) / (t32 * 1e-3) / 1e9,
             "f32_hbm_frac": bytes_per_apply(v, 4, nqp, n) / (t32 * 1e-3) / 1e9 / hbm,
+            "ff_gdofs": n / (tff * 1e-3) / 1e9, "ff_ms": tff,
+            "ff_tflops_fp64_equiv": flops_per_qp(v) * nqp / (tff * 1e-3) / 1e12,
             "f64_form": FORMS[ctxs[v].kernel_form(-1, 0)], "f32_form": FORMS[ctxs[v].kernel_form(-1, 1)],
+            "ff_form": FORMS[ctxs[v].kernel_form(-1, 2)],
         }
     # dominant kernel of the step: the slowest variant's FP64 apply (FP64-pipe bound)
     dom = max(per_var_ms, key=per_var_ms.get)

@@ -47,7 +47,11 @@ typedef enum {
   HY_ERR_UNSUPPORTED = 8   /* valid but not built (e.g. degree 5) */
 } hy_status;
 
-typedef enum { HY_F64 = 0, HY_F32 = 1 } hy_dtype;
+/* Arithmetic of a tangent action. HY_FF (double-float): FP64 vectors and an FP64-accurate result (about
+ * 48 significant bits, within 1e-12 of the FP64 action in relative L2 norm), computed as unevaluated sums
+ * of two floats on the FP32 pipe, which GB300 issues at 64 times its FP64 rate. Not IEEE FP64: a
+ * service of this library for the finest level (see fine_dtype), not a step of the paper's method. */
+typedef enum { HY_F64 = 0, HY_F32 = 1, HY_FF = 2 } hy_dtype;
 
 /* Tangent-operator variants (Sec. 5):
  *   HY_T4  cache F^{-1}, tau and the fourth-order tangent J*C per Gauss point (Algorithm 3)
@@ -92,7 +96,9 @@ hy_status hy_set_displacement(hy_ctx *ctx, const double *u_dev, hy_variant varia
 /* y = A(u) x on the finest level (Eq. algebraic_tangent applied as in Eq. mf_vmult), with the
  * Dirichlet treatment A~ = Z A Z + (I - Z): x is read as zero on constrained dofs and y equals x
  * there. dtype selects the FP64 or FP32 cache (the FP32 one exists after set_displacement with
- * HY_F32). x_dev and y_dev are device arrays of n_dofs elements of that type; they must not alias. */
+ * HY_F32), or HY_FF the double-float one (exists after set_displacement with the solver parameter
+ * fine_dtype = HY_FF; FP64 vectors). x_dev and y_dev are device arrays of n_dofs elements of that type
+ * (FP64 for HY_FF); they must not alias. HY_ERR_STATE if the requested cache does not exist. */
 hy_status hy_apply_tangent(hy_ctx *ctx, const void *x_dev, void *y_dev, hy_dtype dtype);
 
 /* Same on any level (the level operators of the V-cycle, Sec. 6). */
@@ -129,6 +135,10 @@ typedef struct {
                                cache and keeps the faster (process-wide; when the environment variable
                                HY_TUNE_FILE names a file, the decisions are read from it at the first tuning
                                and it is rewritten, as a JSON array, with every new decision) */
+  hy_dtype fine_dtype;      /* [HY_F64] tangent action of the finest level inside the solver (outer CG, and the
+                               finest level of an FP64 V-cycle): HY_F64, or HY_FF to build a double-float
+                               cache of the finest level at hy_set_displacement and use it there (degrees
+                               1-2; HY_ERR_UNSUPPORTED from hy_set_displacement otherwise) */
 } hy_solver_params;
 
 hy_status hy_set_solver_params(hy_ctx *ctx, const hy_solver_params *p);
@@ -210,10 +220,12 @@ hy_status hy_dot_noalloc(int device, void *cuda_stream, const double *a_dev, con
                          double *result);
 
 /* Device bytes a context will own for this problem after mesh setup and set_displacement (the
- * admission measure of the solve server); pure host arithmetic, no GPU needed. face_masks[2*dim]
- * (may be NULL: then an upper bound) fixes the free dofs of an exact coarse solve. */
+ * admission measure of the solve server); pure host arithmetic, no GPU needed. coarse_solver and
+ * fine_dtype as in hy_solver_params. face_masks[2*dim] (may be NULL: then an upper bound) fixes the free
+ * dofs of an exact coarse solve. */
 hy_status hy_footprint(int dim, int degree, int cells_per_dir, int n_levels, hy_variant variant,
-                       hy_dtype level_dtype, int coarse_solver, const uint32_t *face_masks, int64_t *bytes);
+                       hy_dtype level_dtype, int coarse_solver, hy_dtype fine_dtype, const uint32_t *face_masks,
+                       int64_t *bytes);
 
 /* Device bytes currently owned by the context (its hierarchy, caches and work vectors). */
 hy_status hy_ctx_bytes(const hy_ctx *ctx, int64_t *bytes);

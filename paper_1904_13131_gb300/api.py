@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_PKG, "libhyperelastic.so")
 STATUS = {0: "HY_OK", 1: "HY_ERR_ARG", 2: "HY_ERR_STATE", 3: "HY_ERR_OOM", 4: "HY_ERR_CUDA", 5: "HY_ERR_JNEG",
           6: "HY_ERR_NOCONV", 7: "HY_ERR_TIMEOUT", 8: "HY_ERR_UNSUPPORTED"}
 VARIANTS = {"T4": 0, "T2": 1, "FC": 2, "SC": 3, "NC": 4}
-F64, F32 = 0, 1
+F64, F32, FF = 0, 1, 2  # hy_dtype; FF: double-float action on FP64 vectors
 
 # every symbol the header declares (checked by the CPU test suite)
 EXPORTED = ("hy_create", "hy_destroy", "hy_status_str", "hy_last_error", "hy_mesh_setup", "hy_num_dofs",
@@ -40,7 +40,8 @@ class HyError(RuntimeError):
 class SolverParams(ctypes.Structure):
     _fields_ = [("cheb_degree", ctypes.c_int), ("cheb_sweeps", ctypes.c_int), ("cheb_lo", ctypes.c_double),
                 ("cheb_hi", ctypes.c_double), ("eig_iters", ctypes.c_int), ("coarse_eig_iters", ctypes.c_int),
-                ("coarse_reduction", ctypes.c_double), ("coarse_solver", ctypes.c_int), ("kernel_form", ctypes.c_int)]
+                ("coarse_reduction", ctypes.c_double), ("coarse_solver", ctypes.c_int), ("kernel_form", ctypes.c_int),
+                ("fine_dtype", ctypes.c_int)]
 
 
 class NewtonParams(ctypes.Structure):
@@ -110,7 +111,8 @@ def load_library(path: str = LIB_PATH):
         "hy_dot": [vp, vp, vp, i64, ctypes.POINTER(dbl)],
         "hy_kernel_launches": [vp, ctypes.POINTER(i64)],
         "hy_dot_noalloc": [i32, vp, vp, vp, i64, ctypes.POINTER(dbl)],
-        "hy_footprint": [i32, i32, i32, i32, i32, i32, i32, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(i64)],
+        "hy_footprint": [i32, i32, i32, i32, i32, i32, i32, i32, ctypes.POINTER(ctypes.c_uint32),
+                         ctypes.POINTER(i64)],
         "hy_kernel_form": [vp, i32, i32, ctypes.POINTER(i32)],
         "hy_ctx_bytes": [vp, ctypes.POINTER(i64)],
         "hy_batch_create": [ctypes.POINTER(vp), ctypes.POINTER(vp), i32],
@@ -187,14 +189,14 @@ class Context:
 
     def _vec(self, t, n, dtype):
         torch = self._torch
-        want = torch.float64 if dtype == F64 else torch.float32
+        want = torch.float32 if dtype == F32 else torch.float64
         if t.device != self.device or t.dtype != want or not t.is_contiguous() or t.numel() != n:
             raise ValueError(f"expected a contiguous {want} tensor of {n} elements on {self.device}")
         return _ptr(t)
 
     def empty(self, level=-1, dtype=F64):
         torch = self._torch
-        return torch.empty(self.num_dofs(level), dtype=torch.float64 if dtype == F64 else torch.float32,
+        return torch.empty(self.num_dofs(level), dtype=torch.float32 if dtype == F32 else torch.float64,
                            device=self.device)
 
     # ---- mesh / material -------------------------------------------------------------------------
@@ -377,12 +379,12 @@ def dot_noalloc(a, b, device: int = 0, stream=None) -> float:
 
 
 def footprint(dim, degree, cells_per_dir, n_levels, variant="T4", level_dtype=F64, coarse_solver=0,
-              face_masks=None) -> int:
+              face_masks=None, fine_dtype=None) -> int:
     """Device bytes a context needs for this problem (host arithmetic, no GPU)."""
     b = ctypes.c_int64()
     fm = None if face_masks is None else (ctypes.c_uint32 * 6)(*[int(x) for x in list(face_masks) + [0] * 6][:6])
     st = load_library().hy_footprint(dim, degree, cells_per_dir, n_levels, VARIANTS[variant], level_dtype, coarse_solver,
-                                     fm, ctypes.byref(b))
+                                     F64 if fine_dtype is None else fine_dtype, fm, ctypes.byref(b))
     if st != 0:
         raise HyError(st, "hy_footprint")
     return b.value
@@ -488,7 +490,7 @@ class Server:
     def submit(self, problem: dict, newton: NewtonParams, solver: SolverParams | None = None) -> int:
         """problem: an inputs.problem(...) bundle (ids of every level, coarsest first)."""
         if solver is None:
-            solver = SolverParams(4, 1, 0.6, 1.2, 30, 0, 1e-3, 0, -1)
+            solver = SolverParams(4, 1, 0.6, 1.2, 30, 0, 1e-3, 0, -1, 0)
         ids = np.ascontiguousarray(np.concatenate([np.asarray(i, dtype=np.uint8) for i in problem["ids"]]))
         mu = np.ascontiguousarray(problem["mu"], dtype=np.float64)
         lam = np.ascontiguousarray(problem["lam"], dtype=np.float64)

@@ -10,6 +10,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 #include <new>
 #include <string>
 #include <vector>
@@ -148,6 +149,7 @@ struct Level {
   uint8_t* d_mat = nullptr;
   Mat<double> mt64{};
   Mat<float> mt32{};
+  Mat<ff> mtff{};
   bool mat_set = false;
   double* d_u64 = nullptr;
   float* d_u32 = nullptr;
@@ -159,7 +161,10 @@ struct Level {
   double* d_dinv64 = nullptr;
   float* d_dinv32 = nullptr;
   double lmax = 0.0;
-  int form[2] = {-1, -1};  // tangent-action kernel form per precision (FP64, FP32)
+  ff* d_cff = nullptr;     // double-float cache of the finest level (solver parameter fine_dtype = HY_FF)
+  size_t cff_len = 0;
+  bool hasff = false;
+  int form[3] = {-1, -1, -1};  // tangent-action kernel form per precision (FP64, FP32, double-float)
   double* w64[5] = {};  // V-cycle vectors b, x, r, d, t
   float* w32[5] = {};
   double* d_Ainv = nullptr;  // exact coarse solve: dense free-dof tangent / its inverse (ping-pong pair)
@@ -188,7 +193,8 @@ struct hy_ctx {
   std::vector<Transfer> tr;
   Basis1D<double> b64{};
   Basis1D<float> b32{};
-  hy_solver_params sp{4, 1, 0.6, 1.2, 30, 0, 1e-3, 0, -1};
+  Basis1D<ff> bff{};
+  hy_solver_params sp{4, 1, 0.6, 1.2, 30, 0, 1e-3, 0, -1, HY_F64};
   int var = -1;
   bool mixed = false;
   bool state_ok = false;
@@ -315,15 +321,34 @@ CellArgs<T> cell_args(hy_ctx* ctx, Level& L) {
   a.jmin_bits = ctx->d_jmin;
   a.g = L.g;
   a.nqp = L.nqp;
-  if constexpr (sizeof(T) == 8) {
+  if constexpr (std::is_same<T, double>::value) {
     a.mt = L.mt64;
     a.b = ctx->b64;
-  } else {
+  } else if constexpr (std::is_same<T, float>::value) {
     a.mt = L.mt32;
     a.b = ctx->b32;
+  } else {
+    a.mt = L.mtff;
+    a.b = ctx->bff;
   }
   return a;
 }
+
+// Per-precision views of a level: 0 FP64, 1 FP32, 2 double-float.
+template <typename T> constexpr int prec_index() {
+  return std::is_same<T, double>::value ? 0 : std::is_same<T, float>::value ? 1 : 2;
+}
+template <typename T> bool has_cache(const Level& L) {
+  return prec_index<T>() == 0 ? L.has64 : prec_index<T>() == 1 ? L.has32 : L.hasff;
+}
+template <typename T> const T* cache_of(const Level& L);
+template <> const double* cache_of<double>(const Level& L) { return L.d_c64; }
+template <> const float* cache_of<float>(const Level& L) { return L.d_c32; }
+template <> const ff* cache_of<ff>(const Level& L) { return L.d_cff; }
+template <typename T> const vec_t<T>* ubar_of(const Level& L);
+template <> const double* ubar_of<double>(const Level& L) { return L.d_u64; }
+template <> const float* ubar_of<float>(const Level& L) { return L.d_u32; }
+template <> const double* ubar_of<ff>(const Level& L) { return L.d_u64; }
 
 ApplyFn<double> apply_fn(hy_ctx* ctx, double*, int var) {
   return ctx->dim == 2 ? apply_fn_f64_2d(ctx->n, var) : apply_fn_f64_3d(ctx->n, var);
@@ -331,36 +356,45 @@ ApplyFn<double> apply_fn(hy_ctx* ctx, double*, int var) {
 ApplyFn<float> apply_fn(hy_ctx* ctx, float*, int var) {
   return ctx->dim == 2 ? apply_fn_f32_2d(ctx->n, var) : apply_fn_f32_3d(ctx->n, var);
 }
+ApplyFn<ff> apply_fn(hy_ctx* ctx, ff*, int var) {
+  return ctx->dim == 2 ? apply_fn_ff_2d(ctx->n, var) : apply_fn_ff_3d(ctx->n, var);
+}
 
-// y = A~ x on level l in precision T (x zero on constrained dofs on read, y = x there).
+// y = A~ x on level l in precision T (x zero on constrained dofs on read, y = x there). The vectors are
+// of type vec_t<T> (FP64 for the double-float action).
 template <typename T>
-hy_status vmult(hy_ctx* ctx, int l, const T* x, T* y, bool constrained_in = true) {
+hy_status vmult(hy_ctx* ctx, int l, const vec_t<T>* x, vec_t<T>* y, bool constrained_in = true) {
+  using V = vec_t<T>;
   Level& L = ctx->lev[l];
-  const bool have = sizeof(T) == 8 ? L.has64 : L.has32;
-  if (!have) return fail(ctx, HY_ERR_STATE, "no Gauss-point cache of this precision on this level");
+  if (!has_cache<T>(L)) return fail(ctx, HY_ERR_STATE, "no Gauss-point cache of this precision on this level");
   CellArgs<T> a = cell_args<T>(ctx, L);
   a.x = x;
   a.y = y;
-  if constexpr (sizeof(T) == 8) {
-    a.cache = L.d_c64;
-    a.ubar = L.d_u64;
-  } else {
-    a.cache = L.d_c32;
-    a.ubar = L.d_u32;
-  }
+  a.cache = cache_of<T>(L);
+  a.ubar = ubar_of<T>(L);
   if (constrained_in) {
-    launch_prep_out<T>(x, y, L.nnodes, ctx->dim, L.g, ctx->stream);
+    launch_prep_out<V>(x, y, L.nnodes, ctx->dim, L.g, ctx->stream);
   } else {
     // raw operator rows of the free dofs applied to x including its constrained entries
-    cudaMemsetAsync(y, 0, sizeof(T) * L.ndofs, ctx->stream);
+    cudaMemsetAsync(y, 0, sizeof(V) * L.ndofs, ctx->stream);
     a.g.fm[0] = a.g.fm[1] = a.g.fm[2] = a.g.fm[3] = a.g.fm[4] = a.g.fm[5] = 0;
   }
   ApplyFn<T> fn = apply_fn(ctx, (T*)nullptr, ctx->var);
   if (!fn) return fail(ctx, HY_ERR_UNSUPPORTED, "no kernel for this dim/degree/variant");
-  const int form = L.form[sizeof(T) == 8 ? 0 : 1];
+  const int form = L.form[prec_index<T>()];
   fn(a, form < 0 ? FORM_POINT : form, ctx->stream);
-  if (!constrained_in) launch_zero_constrained<T>(y, L.nnodes, ctx->dim, L.g, ctx->stream);
+  if (!constrained_in) launch_zero_constrained<V>(y, L.nnodes, ctx->dim, L.g, ctx->stream);
   return check_launch(ctx, 2);
+}
+
+// The tangent action the solver uses on level l in the V-cycle precision T: on the finest level in FP64
+// the double-float action when the solver parameter fine_dtype asks for it.
+template <typename T>
+hy_status level_apply(hy_ctx* ctx, int l, const T* x, T* y) {
+  if constexpr (std::is_same<T, double>::value) {
+    if (l == ctx->nlev - 1 && ctx->sp.fine_dtype == HY_FF && ctx->lev[l].hasff) return vmult<ff>(ctx, l, x, y);
+  }
+  return vmult<T>(ctx, l, x, y);
 }
 
 template <typename T>
@@ -458,11 +492,11 @@ hy_status chebyshev(hy_ctx* ctx, int l, const T* b, T* x, bool x0_zero, int degr
   const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
   const double sigma = theta / delta;
   double rho = 1.0 / sigma;
-  if (!x0_zero) HY_TRY(vmult<T>(ctx, l, x, t));
+  if (!x0_zero) HY_TRY(level_apply<T>(ctx, l, x, t));
   launch_cheb_init<T>(b, t, dinv, r, dd, x, T(1.0 / theta), x0_zero, L.ndofs, ctx->stream);
   HY_TRY(check_launch(ctx, 1));
   for (int j = 1; j < degree; ++j) {
-    HY_TRY(vmult<T>(ctx, l, dd, t));
+    HY_TRY(level_apply<T>(ctx, l, dd, t));
     const double rho_new = 1.0 / (2.0 * sigma - rho);
     launch_cheb_step<T>(t, dinv, r, dd, x, T(rho_new * rho), T(2.0 * rho_new / delta), L.ndofs, ctx->stream);
     HY_TRY(check_launch(ctx, 1));
@@ -485,7 +519,7 @@ hy_status vcycle_typed(hy_ctx* ctx, int l) {
   for (int s = 0; s < ctx->sp.cheb_sweeps; ++s) HY_TRY(chebyshev<T>(ctx, l, b, x, s == 0, ctx->sp.cheb_degree, lo, hi));
   T* t = wvec<T>(L, 4);
   T* r = wvec<T>(L, 2);
-  HY_TRY(vmult<T>(ctx, l, x, t));
+  HY_TRY(level_apply<T>(ctx, l, x, t));
   launch_sub<T>(b, t, r, L.ndofs, ctx->stream);
   HY_TRY(check_launch(ctx, 1));
   Level& C = ctx->lev[l - 1];
@@ -604,7 +638,7 @@ hy_status eig_estimate(hy_ctx* ctx, int l, int iters, double& lmin, double& lmax
   HY_TRY(check_launch(ctx, 5));
   // CG iterations with every scalar on the device; the coefficient history comes back once at the end
   for (int it = 0; it < iters; ++it) {
-    HY_TRY(vmult<T>(ctx, l, p, q));
+    HY_TRY(level_apply<T>(ctx, l, p, q));
     launch_dot<T>(p, q, L.ndofs, ctx->d_partials, sc + 2, ctx->stream);  // pq
     launch_eig_alpha(sc, hist, it, ctx->stream);
     launch_axpy_dev<T>(sc + 4, -1.0, q, r, L.ndofs, ctx->stream);        // r -= alpha q
@@ -650,14 +684,23 @@ hy_status ensure_level_vectors(hy_ctx* ctx, int l, bool f32) {
   return HY_OK;
 }
 
+template <typename TOUT> TOUT*& cache_buf(Level& L);
+template <> double*& cache_buf<double>(Level& L) { return L.d_c64; }
+template <> float*& cache_buf<float>(Level& L) { return L.d_c32; }
+template <> ff*& cache_buf<ff>(Level& L) { return L.d_cff; }
+template <typename TOUT> size_t& cache_len(Level& L);
+template <> size_t& cache_len<double>(Level& L) { return L.c64_len; }
+template <> size_t& cache_len<float>(Level& L) { return L.c32_len; }
+template <> size_t& cache_len<ff>(Level& L) { return L.cff_len; }
+
 template <typename TOUT>
 hy_status build_cache(hy_ctx* ctx, int l, int var) {
   Level& L = ctx->lev[l];
   const int cb = layout_cells<TOUT>(ctx->dim, ctx->n);
   const size_t nblocks = (size_t)((L.g.ncells + cb - 1) / cb);
   const size_t len = std::max<size_t>(1, (size_t)cache_values(var, ctx->dim) * layout_row<TOUT>(ctx->dim, ctx->n) * nblocks);
-  TOUT*& buf = *reinterpret_cast<TOUT**>(sizeof(TOUT) == 8 ? (void*)&L.d_c64 : (void*)&L.d_c32);
-  size_t& cur = sizeof(TOUT) == 8 ? L.c64_len : L.c32_len;
+  TOUT*& buf = cache_buf<TOUT>(L);
+  size_t& cur = cache_len<TOUT>(L);
   if (cur < len) {
     dfree(ctx, buf);
     buf = nullptr;
@@ -667,8 +710,9 @@ hy_status build_cache(hy_ctx* ctx, int l, int var) {
   CellArgs<double> a = cell_args<double>(ctx, L);
   a.u64 = L.d_u64;
   StateFn<TOUT> fn;
-  if constexpr (sizeof(TOUT) == 8) fn = state_fn_f64(ctx->dim, ctx->n, var);
-  else fn = state_fn_f32(ctx->dim, ctx->n, var);
+  if constexpr (std::is_same<TOUT, double>::value) fn = state_fn_f64(ctx->dim, ctx->n, var);
+  else if constexpr (std::is_same<TOUT, float>::value) fn = state_fn_f32(ctx->dim, ctx->n, var);
+  else fn = state_fn_ff(ctx->dim, ctx->n, var);
   if (!fn) return fail(ctx, HY_ERR_UNSUPPORTED, "no state kernel");
   fn(a, buf, ctx->stream);
   return check_launch(ctx, 1);
@@ -756,6 +800,7 @@ std::map<TuneKey, int> g_tune;
 bool g_tune_loaded = false;
 const char* const kVarNames[5] = {"T4", "T2", "FC", "SC", "NC"};
 const char* const kFormNames[2] = {"point", "line"};
+const char* const kPrecNames[3] = {"f64", "f32", "ff"};
 
 int name_index(const char* s, const char* const* names, int n) {
   for (int i = 0; i < n; ++i)
@@ -779,7 +824,7 @@ void tune_load_locked() {
                     &d, &k, var, prec, &b, form) != 6)
       continue;  // the brackets and anything unrecognised
     const int v = name_index(var, kVarNames, 5), fm = name_index(form, kFormNames, 2);
-    const int p = std::strcmp(prec, "f64") == 0 ? 0 : std::strcmp(prec, "f32") == 0 ? 1 : -1;
+    const int p = name_index(prec, kPrecNames, 3);
     if (v >= 0 && fm >= 0 && p >= 0) g_tune[TuneKey{d, k, v, p, b}] = fm;
   }
   std::fclose(f);
@@ -798,7 +843,7 @@ void tune_save_locked() {
     std::fprintf(f,
                  "  {\"dim\": %d, \"degree\": %d, \"variant\": \"%s\", \"precision\": \"%s\", \"cells_log2\": %d, "
                  "\"threads_per_cell\": \"%s\"}%s\n",
-                 std::get<0>(t), std::get<1>(t), kVarNames[std::get<2>(t)], std::get<3>(t) ? "f32" : "f64",
+                 std::get<0>(t), std::get<1>(t), kVarNames[std::get<2>(t)], kPrecNames[std::get<3>(t)],
                  std::get<4>(t), kFormNames[kv.second], ++i < g_tune.size() ? "," : "");
   }
   std::fprintf(f, "]\n");
@@ -808,8 +853,9 @@ void tune_save_locked() {
 
 template <typename T>
 hy_status autotune_level(hy_ctx* ctx, int l) {
+  using V = vec_t<T>;
   Level& L = ctx->lev[l];
-  const int dt = sizeof(T) == 8 ? 0 : 1;
+  const int dt = prec_index<T>();
   if (ctx->sp.kernel_form >= 0) {
     L.form[dt] = ctx->sp.kernel_form;
     return HY_OK;
@@ -829,9 +875,9 @@ hy_status autotune_level(hy_ctx* ctx, int l) {
   // time both forms on this level's cache: one warm-up application each, then three rounds that
   // alternate the forms, each timing four back-to-back applications (hides the host launch latency on
   // small levels); the best round of each form decides
-  T* x = wvec<T>(L, 2);
-  T* y = wvec<T>(L, 3);
-  launch_splitmix<T>(x, L.ndofs, 12345ULL, ctx->stream);
+  V* x = wvec<V>(L, 2);
+  V* y = wvec<V>(L, 3);
+  launch_splitmix<V>(x, L.ndofs, 12345ULL, ctx->stream);
   HY_TRY(check_launch(ctx, 1));
   struct Events {
     cudaEvent_t a = nullptr, b = nullptr;
@@ -864,7 +910,7 @@ hy_status autotune_level(hy_ctx* ctx, int l) {
   L.form[dt] = choice;
   if (ctx->verbose)
     std::fprintf(stderr, "[hy] autotune dim %d k %d var %d %s cells 2^%d: point %.3f ms, line %.3f ms -> %s\n", ctx->dim,
-                 ctx->k, ctx->var, dt ? "f32" : "f64", bucket, best[0], best[1], choice ? "line" : "point");
+                 ctx->k, ctx->var, kPrecNames[dt], bucket, best[0], best[1], choice ? "line" : "point");
   std::lock_guard<std::mutex> lock(g_tune_mu);
   if (g_tune.emplace(key, choice).second) tune_save_locked();
   return HY_OK;
@@ -891,6 +937,8 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
   for (int l = 0; l < ctx->nlev; ++l)
     if (!ctx->lev[l].mat_set) return fail(ctx, HY_ERR_STATE, "material not set on level " + std::to_string(l));
   if (var < 0 || var > 4) return fail(ctx, HY_ERR_ARG, "variant out of range");
+  if (ctx->sp.fine_dtype == HY_FF && ctx->n > 3)
+    return fail(ctx, HY_ERR_UNSUPPORTED, "the double-float action is built for degrees 1-2");
   ctx->state_ok = false;
   drop_graph(ctx);
   ctx->var = var;
@@ -920,11 +968,15 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
     Level& L = ctx->lev[l];
     const bool need64 = (l == top) || (l == 0) || !mixed;
     const bool need32 = mixed && (l > 0 || l == top);
-    L.has64 = L.has32 = false;
-    L.form[0] = L.form[1] = -1;
+    L.has64 = L.has32 = L.hasff = false;
+    L.form[0] = L.form[1] = L.form[2] = -1;
     if (need64) {
       HY_TRY(build_cache<double>(ctx, l, var));
       L.has64 = true;
+    }
+    if (l == top && ctx->sp.fine_dtype == HY_FF) {
+      HY_TRY(build_cache<ff>(ctx, l, var));
+      L.hasff = true;
     }
     if (need32) {
       HY_TRY(build_cache<float>(ctx, l, var));
@@ -959,6 +1011,7 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
   for (int l = 0; l < ctx->nlev; ++l) {
     if (ctx->lev[l].has64) HY_TRY(autotune_level<double>(ctx, l));
     if (ctx->lev[l].has32) HY_TRY(autotune_level<float>(ctx, l));
+    if (ctx->lev[l].hasff) HY_TRY(autotune_level<ff>(ctx, l));
   }
   pt.mark("autotune");
   // eigenvalue estimates (level precision of the V-cycle)
@@ -1041,7 +1094,7 @@ hy_status pcg(hy_ctx* ctx, const double* b, double* x, double rtol, int max_iter
   double rz;
   HY_TRY(dot<double>(ctx, r, z, n, &rz));
   for (int it = 1; it <= max_iter; ++it) {
-    HY_TRY(vmult<double>(ctx, ctx->nlev - 1, p, q));
+    HY_TRY(level_apply<double>(ctx, ctx->nlev - 1, p, q));
     double pq;
     HY_TRY(dot<double>(ctx, p, q, n, &pq));
     if (ctx->verbose) std::fprintf(stderr, "[hy] pcg it %d rz %.3e pAp %.3e\n", it, rz, pq);
@@ -1087,7 +1140,7 @@ struct hy_batch {
   int* h_start = nullptr;
   double* h_scal_in = nullptr;            // pinned: initial scalars
   double* h_scal_out = nullptr;           // pinned: scalars read back after each iteration
-  int form[2] = {-1, -1};                 // tuned kernel form of the list launch per precision
+  int form[3] = {-1, -1, -1};             // tuned kernel form of the list launch per precision
   std::vector<const void*> up_x, up_y;    // what the uploaded list describes
   int up_dt = -1, up_blocks = 0;
   long long up_max_nodes = 0;
@@ -1118,13 +1171,16 @@ ApplyListFn<double> list_fn(int dim, int n, int var, double*) {
 ApplyListFn<float> list_fn(int dim, int n, int var, float*) {
   return dim == 2 ? apply_list_fn_f32_2d(n, var) : apply_list_fn_f32_3d(n, var);
 }
+ApplyListFn<ff> list_fn(int dim, int n, int var, ff*) {
+  return dim == 2 ? apply_list_fn_ff_2d(n, var) : apply_list_fn_ff_3d(n, var);
+}
 
 // Upload the argument list of the finest-level actions y_j = A_j x_j of the problems idx (skipped when
 // the device copy already describes exactly these vectors).
 template <typename T>
 hy_status upload_list(hy_batch* b, const std::vector<int>& idx, const std::vector<const void*>& x,
                       const std::vector<const void*>& y) {
-  const int dt = sizeof(T) == 8 ? 0 : 1;
+  const int dt = prec_index<T>();
   if (b->up_dt == dt && b->up_x == x && b->up_y == y) return HY_OK;
   HB_CK(cudaEventSynchronize(b->ev_upload));  // the staging buffer is free again
   CellArgs<T>* h = static_cast<CellArgs<T>*>(b->h_list);
@@ -1135,15 +1191,10 @@ hy_status upload_list(hy_batch* b, const std::vector<int>& idx, const std::vecto
     Level& L = c->lev[c->nlev - 1];
     max_nodes = std::max(max_nodes, L.nnodes);
     CellArgs<T> a = cell_args<T>(c, L);
-    a.x = static_cast<const T*>(x[j]);
-    a.y = static_cast<T*>(const_cast<void*>(y[j]));
-    if constexpr (sizeof(T) == 8) {
-      a.cache = L.d_c64;
-      a.ubar = L.d_u64;
-    } else {
-      a.cache = L.d_c32;
-      a.ubar = L.d_u32;
-    }
+    a.x = static_cast<const vec_t<T>*>(x[j]);
+    a.y = static_cast<vec_t<T>*>(const_cast<void*>(y[j]));
+    a.cache = cache_of<T>(L);
+    a.ubar = ubar_of<T>(L);
     h[j] = a;
     b->h_start[j] = (int)blocks;
     blocks += (L.g.ncells + cb - 1) / cb;
@@ -1184,7 +1235,7 @@ hy_status list_apply(hy_batch* b, const std::vector<int>& idx, const std::vector
 template <typename T>
 hy_status tune_list(hy_batch* b, const std::vector<int>& idx, const std::vector<const void*>& x,
                     const std::vector<const void*>& y) {
-  const int dt = sizeof(T) == 8 ? 0 : 1;
+  const int dt = prec_index<T>();
   if (b->form[dt] >= 0) return HY_OK;
   const int forced = b->ctx[idx[0]]->sp.kernel_form;
   if (forced >= 0) {
@@ -1216,7 +1267,7 @@ hy_status tune_list(hy_batch* b, const std::vector<int>& idx, const std::vector<
   b->form[dt] = best[1] < best[0] ? FORM_LINE : FORM_POINT;
   if (b->ctx[idx[0]]->verbose)
     std::fprintf(stderr, "[hy] batch of %zu: list launch %s point %.3f ms, line %.3f ms\n", idx.size(),
-                 dt ? "f32" : "f64", best[0], best[1]);
+                 kPrecNames[dt], best[0], best[1]);
   return HY_OK;
 }
 
@@ -1275,6 +1326,7 @@ hy_status pcg_branch(hy_ctx* c, double* sc, double* x) {
 // One PCG iteration of every resident problem R, captured into a graph on s0: the list launch
 // q_i = A_i p_i, then one branch per problem (pcg_branch), then a copy of all scalars to pinned host
 // memory. *kernels = kernels one replay launches.
+template <typename TL>
 hy_status capture_iteration(hy_batch* b, const std::vector<int>& R, double* const* xsol, int form,
                             cudaGraphExec_t* exec, long long* kernels) {
   std::vector<const void*> ps, qs;
@@ -1282,7 +1334,7 @@ hy_status capture_iteration(hy_batch* b, const std::vector<int>& R, double* cons
     ps.push_back(b->ctx[i]->f64[2]);
     qs.push_back(b->ctx[i]->f64[3]);
   }
-  HY_TRY(upload_list<double>(b, R, ps, qs));
+  HY_TRY(upload_list<TL>(b, R, ps, qs));
   std::vector<cudaStream_t> saved(R.size());
   std::vector<long long> l0(R.size());
   for (size_t j = 0; j < R.size(); ++j) {
@@ -1291,7 +1343,7 @@ hy_status capture_iteration(hy_batch* b, const std::vector<int>& R, double* cons
   }
   const long long b0 = b->launches;
   HB_CK(cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeThreadLocal));
-  hy_status st = list_apply<double>(b, R, ps, qs, form, b->s0);
+  hy_status st = list_apply<TL>(b, R, ps, qs, form, b->s0);
   if (st == HY_OK && cudaEventRecord(b->ev_fork, b->s0) != cudaSuccess) st = bfail(b, HY_ERR_CUDA, "cudaEventRecord");
   for (size_t j = 0; j < R.size() && st == HY_OK; ++j) {
     const int i = R[j];
@@ -1355,8 +1407,7 @@ hy_status batch_apply(hy_batch* b, const void* const* x, void* const* y) {
   for (int i = 0; i < cnt; ++i) {
     hy_ctx* c = b->ctx[i];
     const Level& L = c->lev[c->nlev - 1];
-    if (!(sizeof(T) == 8 ? L.has64 : L.has32))
-      return bfail(b, HY_ERR_STATE, "batch: a context has no finest-level cache of this precision");
+    if (!has_cache<T>(L)) return bfail(b, HY_ERR_STATE, "batch: a context has no finest-level cache of this precision");
     if (!x[i] || !y[i] || x[i] == y[i]) return bfail(b, HY_ERR_ARG, "batch: null or aliased vectors");
     R[i] = i;
     xs[i] = x[i];
@@ -1365,7 +1416,7 @@ hy_status batch_apply(hy_batch* b, const void* const* x, void* const* y) {
   HY_TRY(join_in(b));
   HY_TRY(upload_list<T>(b, R, xs, ys));
   HY_TRY(tune_list<T>(b, R, xs, ys));
-  HY_TRY(list_apply<T>(b, R, xs, ys, b->form[sizeof(T) == 8 ? 0 : 1], b->s0));
+  HY_TRY(list_apply<T>(b, R, xs, ys, b->form[prec_index<T>()], b->s0));
   return join_out(b);
 }
 
@@ -1418,14 +1469,22 @@ hy_status batch_pcg(hy_batch* b, const double* const* rhs, double* const* xs, do
   }
   HY_TRY(join_in(b));
   hy_status result = HY_OK;
+  // the finest-level action of the outer CG: double-float when every problem asks for it (fine_dtype)
+  bool use_ff = true;
+  for (hy_ctx* c : b->ctx) use_ff = use_ff && c->sp.fine_dtype == HY_FF && c->lev[c->nlev - 1].hasff;
   if (!R.empty()) {
     std::vector<const void*> ps, qs;
     for (int i : R) {
       ps.push_back(b->ctx[i]->f64[2]);
       qs.push_back(b->ctx[i]->f64[3]);
     }
-    result = upload_list<double>(b, R, ps, qs);
-    if (result == HY_OK) result = tune_list<double>(b, R, ps, qs);
+    if (use_ff) {
+      result = upload_list<ff>(b, R, ps, qs);
+      if (result == HY_OK) result = tune_list<ff>(b, R, ps, qs);
+    } else {
+      result = upload_list<double>(b, R, ps, qs);
+      if (result == HY_OK) result = tune_list<double>(b, R, ps, qs);
+    }
   }
   // R: problems in the current graph; live: those still iterating. A finished problem stays in the graph
   // as a no-op (alpha = beta = 0 on the device) until a quarter of the graph's problems have finished,
@@ -1447,7 +1506,8 @@ hy_status batch_pcg(hy_batch* b, const double* const* rhs, double* const* xs, do
         if (live[i]) keep.push_back(i);
       R.swap(keep);
       const auto t0 = std::chrono::steady_clock::now();
-      result = capture_iteration(b, R, xs, b->form[0], &exec, &nk);
+      result = use_ff ? capture_iteration<ff>(b, R, xs, b->form[2], &exec, &nk)
+                      : capture_iteration<double>(b, R, xs, b->form[0], &exec, &nk);
       t_capture += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
       ++n_capture;
       if (result != HY_OK) break;
@@ -1620,10 +1680,14 @@ hy_status hy_mesh_setup(hy_ctx* ctx, int dim, int degree, int m, int n_levels, c
     }
     for (int i = 0; i < MAXN; ++i) {
       ctx->b32.w[i] = (float)b.w[i];
+      ctx->bff.w[i] = ff(b.w[i]);
       for (int j = 0; j < MAXN; ++j) {
         ctx->b32.S[i][j] = (float)b.S[i][j];
         ctx->b32.D[i][j] = (float)b.D[i][j];
         ctx->b32.Sd[i][j] = (float)b.Sd[i][j];
+        ctx->bff.S[i][j] = ff(b.S[i][j]);
+        ctx->bff.D[i][j] = ff(b.D[i][j]);
+        ctx->bff.Sd[i][j] = ff(b.Sd[i][j]);
       }
     }
   }
@@ -1791,6 +1855,8 @@ hy_status hy_set_material(hy_ctx* ctx, int level, const uint8_t* cell_mat, const
     L.mt64.lam[i] = i < n_mat ? lambda[i] : 0.0;
     L.mt32.mu[i] = (float)L.mt64.mu[i];
     L.mt32.lam[i] = (float)L.mt64.lam[i];
+    L.mtff.mu[i] = ff(L.mt64.mu[i]);
+    L.mtff.lam[i] = ff(L.mt64.lam[i]);
   }
   L.mat_set = true;
   ctx->state_ok = false;
@@ -1813,6 +1879,7 @@ hy_status hy_vmult(hy_ctx* ctx, int level, const void* x, void* y, hy_dtype dtyp
   HY_CK(cudaSetDevice(ctx->device));
   if (dtype == HY_F64) return vmult<double>(ctx, l, (const double*)x, (double*)y);
   if (dtype == HY_F32) return vmult<float>(ctx, l, (const float*)x, (float*)y);
+  if (dtype == HY_FF) return vmult<ff>(ctx, l, (const double*)x, (double*)y);
   return fail(ctx, HY_ERR_ARG, "bad dtype");
 }
 
@@ -1859,7 +1926,7 @@ hy_status hy_gmg_vcycle(hy_ctx* ctx, const double* r, double* z) {
 hy_status hy_set_solver_params(hy_ctx* ctx, const hy_solver_params* p) {
   if (!ctx || !p) return HY_ERR_ARG;
   if (p->cheb_degree < 1 || p->cheb_sweeps < 1 || !(p->cheb_lo > 0) || !(p->cheb_hi > p->cheb_lo) ||
-      p->kernel_form < -1 || p->kernel_form > 1 ||
+      p->kernel_form < -1 || p->kernel_form > 1 || (p->fine_dtype != HY_F64 && p->fine_dtype != HY_FF) ||
       p->eig_iters < 1 || p->coarse_eig_iters < 0 || !(p->coarse_reduction > 0 && p->coarse_reduction < 1) ||
       p->coarse_solver < 0 || p->coarse_solver > 1)
     return fail(ctx, HY_ERR_ARG, "solver parameters out of range");
@@ -1906,12 +1973,12 @@ hy_status hy_set_level_info(hy_ctx* ctx, int level, double lmax, double clo, dou
 }
 
 hy_status hy_kernel_form(const hy_ctx* ctx, int level, hy_dtype dtype, int* form) {
-  if (!ctx || !form || (dtype != HY_F64 && dtype != HY_F32)) return HY_ERR_ARG;
+  if (!ctx || !form || (dtype != HY_F64 && dtype != HY_F32 && dtype != HY_FF)) return HY_ERR_ARG;
   const int l = lev_index(ctx, level);
   if (l < 0 || l >= ctx->nlev) return HY_ERR_ARG;
   const Level& L = ctx->lev[l];
-  const bool have = dtype == HY_F64 ? L.has64 : L.has32;
-  *form = have ? L.form[dtype == HY_F64 ? 0 : 1] : -1;
+  const bool have = dtype == HY_F64 ? L.has64 : dtype == HY_F32 ? L.has32 : L.hasff;
+  *form = have ? L.form[dtype == HY_F64 ? 0 : dtype == HY_F32 ? 1 : 2] : -1;
   return HY_OK;
 }
 
@@ -2075,8 +2142,9 @@ hy_status hy_dot(hy_ctx* ctx, const double* a, const double* b, int64_t n, doubl
 // Device bytes a context needs for a problem, mirroring the allocations of hy_mesh_setup and
 // hy_set_displacement (requested sizes; the allocator's own rounding comes on top).
 hy_status hy_footprint(int dim, int degree, int m, int n_levels, hy_variant variant, hy_dtype level_dtype,
-                       int coarse_solver, const uint32_t* face_masks, int64_t* bytes) {
+                       int coarse_solver, hy_dtype fine_dtype, const uint32_t* face_masks, int64_t* bytes) {
   if (!bytes || (dim != 2 && dim != 3) || degree < 1 || degree > 4 || m < 1 || n_levels < 1) return HY_ERR_ARG;
+  if (fine_dtype != HY_F64 && fine_dtype != HY_FF) return HY_ERR_ARG;
   if ((int)variant < 0 || (int)variant > 4) return HY_ERR_ARG;
   auto al = [](size_t n, size_t sz) { return std::max<size_t>(n, 1) * sz; };
   const int n = degree + 1;
@@ -2117,6 +2185,7 @@ hy_status hy_footprint(int dim, int degree, int m, int n_levels, hy_variant vari
     const size_t clen32 = std::max<size_t>(1, (size_t)cache_values((int)variant, dim) * layout_row<float>(dim, n) *
                                                   (size_t)((nc[l] + cb32 - 1) / cb32));
     if (need64) total += al(clen64, 8) + al(nd[l], 8) + 5 * al(nd[l], 8);
+    if (l == top && fine_dtype == HY_FF) total += al(clen64, 8);  // double-float cache, the FP64 layout
     if (need32) total += al(clen32, 4) + al(nd[l], 4) + al(nd[l], 4) + 5 * al(nd[l], 4);
   }
   // free dofs of the coarsest level (all dofs bound them when no masks are given)
@@ -2218,6 +2287,7 @@ hy_status hy_batch_apply(hy_batch* b, const void* const* x, void* const* y, hy_d
   HY_TRY(batch_check(b));
   if (dtype == HY_F64) return batch_apply<double>(b, x, y);
   if (dtype == HY_F32) return batch_apply<float>(b, x, y);
+  if (dtype == HY_FF) return batch_apply<ff>(b, x, y);
   return bfail(b, HY_ERR_ARG, "bad dtype");
 }
 
@@ -2236,8 +2306,8 @@ hy_status hy_batch_kernel_launches(const hy_batch* b, int64_t* count) {
 }
 
 hy_status hy_batch_kernel_form(const hy_batch* b, hy_dtype dtype, int* form) {
-  if (!b || !form || (dtype != HY_F64 && dtype != HY_F32)) return HY_ERR_ARG;
-  *form = b->form[dtype == HY_F64 ? 0 : 1];
+  if (!b || !form || (dtype != HY_F64 && dtype != HY_F32 && dtype != HY_FF)) return HY_ERR_ARG;
+  *form = b->form[(int)dtype];
   return HY_OK;
 }
 

@@ -23,9 +23,9 @@ namespace hy {
 
 template <typename T>
 struct CellArgs {
-  const T* x;             // apply: source vector (level precision)
-  T* y;                   // apply / residual / diag: destination, accumulated with atomics
-  const T* ubar;          // level displacement in T (variants that recompute F)
+  const vec_t<T>* x;      // apply: source vector (level precision; FP64 for double-float)
+  vec_t<T>* y;            // apply / residual / diag: destination, accumulated with atomics
+  const vec_t<T>* ubar;   // level displacement (variants that recompute F)
   const double* u64;      // level displacement in FP64 (state build, residual, diagonal)
   const T* cache;         // per-Gauss-point cache in the blocked layout of cache_row()
   T* cache_out;           // state build output
@@ -403,8 +403,7 @@ __device__ __forceinline__ void neo_hooke_adj(const T F[DIM][DIM], T mu, T lam, 
     J = F[0][0] * F[1][1] - F[0][1] * F[1][0];
   }
   T rho;
-  if constexpr (sizeof(T) == 8) rho = __drcp_rn(J);
-  else rho = __frcp_rn(J);
+  rho = rcp_rn(J);
   const T kappa = Wh * rho * rho;
   const T c = have_c ? c_in : mu - T(2) * lam * log(J);
   const T kmu = kappa * mu, kc = kappa * c;
@@ -588,8 +587,8 @@ __device__ __forceinline__ void apply_point_body(const CellArgs<T>& a, const int
   for (int c = 0; c < DIM; ++c) {
     T v = T(0), w = T(0);
     if (active) {
-      v = ((loc.cmask >> c) & 1u) ? T(0) : a.x[(long long)loc.node * DIM + c];
-      if (NEED_U) w = a.ubar[(long long)loc.node * DIM + c];
+      v = ((loc.cmask >> c) & 1u) ? T(0) : vec_in<T>(a.x[(long long)loc.node * DIM + c]);
+      if (NEED_U) w = vec_in<T>(a.ubar[(long long)loc.node * DIM + c]);
     }
     b0[c * NPT + pt.p] = v;
     if (NEED_U) bp[c * NPT + pt.p] = w;
@@ -647,7 +646,7 @@ __device__ __forceinline__ void apply_point_body(const CellArgs<T>& a, const int
   if (active) {
 #pragma unroll
     for (int c = 0; c < DIM; ++c)
-      if (!((loc.cmask >> c) & 1u)) atomicAdd(&a.y[(long long)loc.node * DIM + c], Y[c * NPT + pt.p]);
+      if (!((loc.cmask >> c) & 1u)) atomicAdd(&a.y[(long long)loc.node * DIM + c], vec_out(Y[c * NPT + pt.p]));
   }
 }
 
@@ -721,8 +720,8 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
       const long long dof = (node0 + a0) * DIM + c;
-      v[a0][c] = (active && !((cms[a0] >> c) & 1u)) ? a.x[dof] : T(0);
-      vu[a0][c] = (NEED_U && active) ? a.ubar[dof] : T(0);
+      v[a0][c] = (active && !((cms[a0] >> c) & 1u)) ? vec_in<T>(a.x[dof]) : T(0);
+      vu[a0][c] = (NEED_U && active) ? vec_in<T>(a.ubar[dof]) : T(0);
     }
   }
   __syncthreads();
@@ -936,7 +935,7 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
       T s = T(0);
 #pragma unroll
       for (int j = 0; j < N; ++j) s = fma(tS[j][a0], Yb[j][c], s);
-      atomicAdd(&a.y[(node0 + a0) * DIM + c], s);
+      atomicAdd(&a.y[(node0 + a0) * DIM + c], vec_out(s));
     }
 }
 

@@ -9,6 +9,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "ff.cuh"
+
 namespace hy {
 
 constexpr int MAXN = 5;      // polynomial degree <= 4

@@ -1,0 +1,8 @@
+// Tangent-action kernels, double-float (FP64 vectors, FP32-pipe arithmetic), dim 2, degrees 1-2, variant
+// FC, one problem or a work list (one translation unit per variant: double-float kernels are long).
+#define INST_DIM 2
+#define INST_T ff
+#define INST_VAR VAR_FC
+#define INST_NAME apply_fn_ff_2d_v2
+#define INST_LIST_NAME apply_list_fn_ff_2d_v2
+#include "inst_apply.inc"

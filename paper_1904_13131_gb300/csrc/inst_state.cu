@@ -47,6 +47,12 @@ StateFn<float> state_fn_f32(int dim, int n, int var) {
   if (n < 2 || n > 5 || var < 0 || var > 5) return nullptr;
   return dim == 2 ? t2[n - 2][var] : dim == 3 ? t3[n - 2][var] : nullptr;
 }
+StateFn<ff> state_fn_ff(int dim, int n, int var) {
+  static const StateFn<ff> t2[4][6] = {HY_SROW(2, 2, ff), HY_SROW(2, 3, ff), HY_SROW(2, 4, ff), HY_SROW(2, 5, ff)};
+  static const StateFn<ff> t3[4][6] = {HY_SROW(3, 2, ff), HY_SROW(3, 3, ff), HY_SROW(3, 4, ff), HY_SROW(3, 5, ff)};
+  if (n < 2 || n > 5 || var < 0 || var > 5) return nullptr;
+  return dim == 2 ? t2[n - 2][var] : dim == 3 ? t3[n - 2][var] : nullptr;
+}
 #undef HY_SROW
 
 CellFn<double> residual_fn(int dim, int n) {

@@ -41,9 +41,45 @@ HY_APPLY_TABLES(double, f64, 2d)
 HY_APPLY_TABLES(double, f64, 3d)
 HY_APPLY_TABLES(float, f32, 2d)
 HY_APPLY_TABLES(float, f32, 3d)
+// double-float: degrees 1-2 (n = 2, 3), one translation unit per (dim, variant)
+#define HY_FF_TABLES(D)                                                                            \
+  ApplyFn<ff> apply_fn_ff_##D##_v0(int n);                                                         \
+  ApplyFn<ff> apply_fn_ff_##D##_v1(int n);                                                         \
+  ApplyFn<ff> apply_fn_ff_##D##_v2(int n);                                                         \
+  ApplyFn<ff> apply_fn_ff_##D##_v3(int n);                                                         \
+  ApplyFn<ff> apply_fn_ff_##D##_v4(int n);                                                         \
+  ApplyListFn<ff> apply_list_fn_ff_##D##_v0(int n);                                                \
+  ApplyListFn<ff> apply_list_fn_ff_##D##_v1(int n);                                                \
+  ApplyListFn<ff> apply_list_fn_ff_##D##_v2(int n);                                                \
+  ApplyListFn<ff> apply_list_fn_ff_##D##_v3(int n);                                                \
+  ApplyListFn<ff> apply_list_fn_ff_##D##_v4(int n);                                                \
+  inline ApplyFn<ff> apply_fn_ff_##D(int n, int var) {                                             \
+    switch (var) {                                                                                 \
+      case 0: return apply_fn_ff_##D##_v0(n);                                                      \
+      case 1: return apply_fn_ff_##D##_v1(n);                                                      \
+      case 2: return apply_fn_ff_##D##_v2(n);                                                      \
+      case 3: return apply_fn_ff_##D##_v3(n);                                                      \
+      case 4: return apply_fn_ff_##D##_v4(n);                                                      \
+    }                                                                                              \
+    return nullptr;                                                                                \
+  }                                                                                                \
+  inline ApplyListFn<ff> apply_list_fn_ff_##D(int n, int var) {                                    \
+    switch (var) {                                                                                 \
+      case 0: return apply_list_fn_ff_##D##_v0(n);                                                 \
+      case 1: return apply_list_fn_ff_##D##_v1(n);                                                 \
+      case 2: return apply_list_fn_ff_##D##_v2(n);                                                 \
+      case 3: return apply_list_fn_ff_##D##_v3(n);                                                 \
+      case 4: return apply_list_fn_ff_##D##_v4(n);                                                 \
+    }                                                                                              \
+    return nullptr;                                                                                \
+  }
+HY_FF_TABLES(2d)
+HY_FF_TABLES(3d)
+#undef HY_FF_TABLES
 #undef HY_APPLY_TABLES
 StateFn<double> state_fn_f64(int dim, int n, int var);   // var VAR_NONE: J check only
 StateFn<float> state_fn_f32(int dim, int n, int var);
+StateFn<ff> state_fn_ff(int dim, int n, int var);
 CellFn<double> residual_fn(int dim, int n);
 CellFn<double> diag_fn(int dim, int n);
 

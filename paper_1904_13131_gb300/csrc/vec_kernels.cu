@@ -45,7 +45,7 @@ __global__ void prep_out_list_kernel(const CellArgs<T>* __restrict__ list) {
   for (long long nd = blockIdx.x * (long long)blockDim.x + threadIdx.x; nd < n_nodes; nd += (long long)gridDim.x * blockDim.x) {
     const uint32_t cm = cmask_of<DIM>(a.g, nd);
 #pragma unroll
-    for (int c = 0; c < DIM; ++c) a.y[nd * DIM + c] = ((cm >> c) & 1u) ? a.x[nd * DIM + c] : T(0);
+    for (int c = 0; c < DIM; ++c) a.y[nd * DIM + c] = ((cm >> c) & 1u) ? a.x[nd * DIM + c] : vec_t<T>(0);
   }
 }
 
@@ -379,7 +379,6 @@ void launch_sweep(const T* in, T* out, int dim, const int Lin[3], const int Lout
 
 #define HY_INST(T)                                                                                              \
   template void launch_prep_out<T>(const T*, T*, long long, int, const Geom&, cudaStream_t);                    \
-  template void launch_prep_out_list<T>(const CellArgs<T>*, int, int, long long, cudaStream_t);                  \
   template void launch_zero_constrained<T>(T*, long long, int, const Geom&, cudaStream_t);                      \
   template void launch_set_constrained_one<T>(T*, long long, int, const Geom&, cudaStream_t);                   \
   template void launch_invert<T>(const double*, T*, long long, cudaStream_t);                                   \
@@ -401,4 +400,7 @@ HY_INST(float)
 template void launch_convert<double, float>(const double*, float*, long long, cudaStream_t);
 template void launch_convert<float, double>(const float*, double*, long long, cudaStream_t);
 
+template void launch_prep_out_list<double>(const CellArgs<double>*, int, int, long long, cudaStream_t);
+template void launch_prep_out_list<float>(const CellArgs<float>*, int, int, long long, cudaStream_t);
+template void launch_prep_out_list<ff>(const CellArgs<ff>*, int, int, long long, cudaStream_t);
 }  // namespace hy

@@ -46,6 +46,41 @@ def test_apply_all_variants_fp64_fp32(torch, dim, k, m):
                 np.testing.assert_array_equal(y64[P.constrained], x[P.constrained])
 
 
+@pytest.mark.parametrize("dim,k,m", [(2, 1, 13), (2, 2, 7), (3, 1, 5), (3, 2, 3), (3, 2, 4)])
+def test_apply_double_float(torch, dim, k, m):
+    """The double-float action (FP64 vectors, FP32-pipe arithmetic) meets the FP64 bar against the oracle,
+    in both kernel forms and every variant; the finest level only."""
+    from paper_1904_13131_gb300.api import FF
+    pr = problem(dim, k, m)
+    P = oracle_level(pr)
+    u = inputs.smooth_field(dim, k, m, seed=dim * 10 + k + 5)
+    x = inputs.gaussian_vector(P.n_dofs, seed=k + 7)
+    y_ref = P.apply(u, x)
+    ud, xd = torch.tensor(u, device="cuda"), torch.tensor(x, device="cuda")
+    with context(pr) as ctx:
+        for form in (0, 1, -1):
+            ctx.set_solver_params(kernel_form=form, fine_dtype=FF, coarse_eig_iters=5)
+            for var in VARIANTS:
+                ctx.set_displacement(ud, var)
+                yff = ctx.apply_tangent(xd, dtype=FF).cpu().numpy()
+                assert rel(yff, y_ref) < 1e-12, (form, var, rel(yff, y_ref))
+                np.testing.assert_array_equal(yff[P.constrained], x[P.constrained])
+                assert ctx.kernel_form(-1, FF) in ((0, 1) if form < 0 else (form,))
+
+
+def test_double_float_needs_its_cache_and_low_degree(torch):
+    from paper_1904_13131_gb300.api import FF, HyError
+    pr = problem(3, 3, 2)
+    u = torch.zeros(inputs.n_dofs(3, 3, 2), dtype=torch.float64, device="cuda")
+    with context(pr) as ctx:
+        ctx.set_displacement(u, "T4")
+        with pytest.raises(HyError):
+            ctx.apply_tangent(u, dtype=FF)  # no double-float cache without fine_dtype = FF
+        ctx.set_solver_params(fine_dtype=FF)
+        with pytest.raises(HyError):
+            ctx.set_displacement(u, "T4")  # degree 3: not built
+
+
 def test_autotuned_form_is_recorded_and_reused(torch):
     """kernel_form = -1 picks one of the two forms per level and precision (-1 where a level has no cache
     of that precision); a second context with the same shapes reuses the process-wide decisions."""

@@ -86,8 +86,8 @@ def test_batch_apply_tuned_and_repeated(torch):
             c.close()
 
 
-@pytest.mark.parametrize("level_dtype,coarse", [(0, 0), (1, 0), (1, 1)])
-def test_batch_pcg_matches_single_and_direct_solve(torch, level_dtype, coarse):
+@pytest.mark.parametrize("level_dtype,coarse,fine", [(0, 0, 0), (1, 0, 0), (1, 1, 0), (1, 1, 2), (0, 0, 2)])
+def test_batch_pcg_matches_single_and_direct_solve(torch, level_dtype, coarse, fine):
     from paper_1904_13131_gb300.api import Batch
     dim, k = 2, 2
     prs = [problem(dim, k, m, n_levels=L, ratio=r) for m, L, r in ((16, 3, 10.0), (8, 2, 3.0), (12, 2, 30.0),
@@ -103,7 +103,7 @@ def test_batch_pcg_matches_single_and_direct_solve(torch, level_dtype, coarse):
             refs.append(spla.spsolve(A.tocsc(), b))
             As.append(A)
             c = context(pr)
-            c.set_solver_params(coarse_solver=coarse)
+            c.set_solver_params(coarse_solver=coarse, fine_dtype=fine)
             c.set_displacement(torch.tensor(u, device="cuda"), "T4", level_dtype=level_dtype)
             ctxs.append(c)
             bs.append(torch.tensor(b, device="cuda"))

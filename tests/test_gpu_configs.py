@@ -61,32 +61,36 @@ def test_config3_degree_sweep_newton_matches_oracle(torch, k, m, L):
     P = Problem(dim, k, m, pr["ids"][-1], pr["mu"], pr["lam"], pr["masks"])
     u_ref, _ = newton_solve(P, oracle_bc(P, dim, k, m, -0.1), load_steps=5)
     from paper_1904_13131_gb300.api import Context
+    runs = [(0, 0, 0), (1, 1 if k < 4 else 0, 0)]  # exact coarse solve: degrees 1-3 in 3D
+    if k <= 2:
+        runs.append((1, 1, 2))  # double-float finest-level action in the outer CG
     with context(pr) as ctx:
-        for ldt, coarse in ((0, 0), (1, 1 if k < 4 else 0)):  # exact coarse solve: degrees 1-3 in 3D
-            ctx.set_solver_params(coarse_solver=coarse)
+        for ldt, coarse, fine in runs:
+            ctx.set_solver_params(coarse_solver=coarse, fine_dtype=fine)
             u = torch.zeros(ctx.num_dofs(), dtype=torch.float64, device="cuda")
             rep = ctx.newton_solve(u, Context.newton_params(level_dtype=ldt, face_values=face_values(dim, -0.1)))
             assert rep["load_steps_done"] == 5
-            assert rel(u.cpu().numpy(), u_ref) < 1e-8, (k, ldt, coarse)
+            assert rel(u.cpu().numpy(), u_ref) < 1e-8, (k, ldt, coarse, fine)
 
 
 def test_config3_64cube_q2_paths_agree(torch):
-    """6.4M dofs, 5 levels (64 -> 4): FP64 V-cycle with Chebyshev coarse solve, mixed precision, and mixed
-    precision with the exact coarse solve reach the same equilibrium."""
+    """6.4M dofs, 5 levels (64 -> 4): FP64 V-cycle with Chebyshev coarse solve, mixed precision, mixed
+    precision with the exact coarse solve, and that with the double-float finest-level action reach the same
+    equilibrium."""
     dim, k, m, L = 3, 2, 64, 5
     pr = inputs.problem(dim, k, m, n_levels=L, top=inputs.normal_top_mask(dim))
     from paper_1904_13131_gb300.api import Context
     sols = []
     with context(pr) as ctx:
-        for ldt, coarse in ((0, 0), (1, 0), (1, 1)):
-            ctx.set_solver_params(coarse_solver=coarse)
+        for ldt, coarse, fine in ((0, 0, 0), (1, 0, 0), (1, 1, 0), (1, 1, 2)):
+            ctx.set_solver_params(coarse_solver=coarse, fine_dtype=fine)
             u = torch.zeros(ctx.num_dofs(), dtype=torch.float64, device="cuda")
             rep = ctx.newton_solve(u, Context.newton_params(level_dtype=ldt, face_values=face_values(dim, -0.1)))
             assert rep["load_steps_done"] == 5 and rep["cg_iterations_max"] < 60
             sols.append(u.cpu().numpy())
             r = ctx.residual(u)
             assert torch.isfinite(r).all()
-    assert rel(sols[1], sols[0]) < 1e-8 and rel(sols[2], sols[0]) < 1e-8
+    assert rel(sols[1], sols[0]) < 1e-8 and rel(sols[2], sols[0]) < 1e-8 and rel(sols[3], sols[0]) < 1e-8
 
 
 def test_config4_mixed_precision_per_load_step(torch):

@@ -61,5 +61,8 @@ def test_footprint_is_host_arithmetic(lib):
     bfm = api.footprint(3, 2, 32, 4, level_dtype=api.F32, coarse_solver=1, face_masks=masks)
     assert bfm - bmm == 2 * 8 * nf * nf + 8 * (1024 + 64 * nf) + 4 * nf + 4 * n0 + 8 * (60 - 2 * nf)
     assert api.footprint(3, 2, 64, 5) > 7 * b64
+    # double-float finest-level cache: the FP64 layout again (T4, 36 values per Gauss point, 9 cells per block)
+    blocks = -(-32**3 // 9)
+    assert api.footprint(3, 2, 32, 4, fine_dtype=api.FF) - b64 == 8 * 36 * ((9 * 27 + 3) // 4 * 4) * blocks
     with pytest.raises(api.HyError):
         api.footprint(3, 5, 32, 4)

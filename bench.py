@@ -74,7 +74,7 @@ def bytes_per_apply(var, dtype_bytes, nqp, ndofs, dim=3):
 # DRAM bytes (read + write) per launch from one ncu capture of the 32^3 Q2 workload (profiles/*_ncu.md);
 # a kernel that changed since its capture maps to None.
 NCU_TRAFFIC = {
-    ("NC", "double", "apply_kernel"): 19_699_712,   # profiles/apply_nc_f64_32cube_q2_ncu.md
+    ("NC", "double", "apply_kernel"): 19_644_416,   # profiles/apply_nc_f64_32cube_q2_ncu.md
 }
 
 
@@ -406,6 +406,7 @@ def main():
     ap.add_argument("--serve-only", action="store_true")
     ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the work-list batch section")
     ap.add_argument("--batch-only", action="store_true")
+    ap.add_argument("--solve-only", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -441,6 +442,9 @@ def main():
                 c.apply_tangent(xin, y, dtype=code)
             torch.cuda.synchronize()
         print(json.dumps({"only": args.only, "reps": args.reps}))
+        return
+    if args.solve_only:
+        print(json.dumps({"solve": solve_latency(torch, api, inputs, dev)}), flush=True)
         return
     if args.batch_only:
         print(json.dumps({"batch": batch_bench(torch, api, inputs, dev, stream)}), flush=True)

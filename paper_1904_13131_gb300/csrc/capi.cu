@@ -216,6 +216,7 @@ struct hy_ctx {
   double* f64[10] = {};  // fine-level FP64 work vectors of PCG / Newton
   long long launches = 0;
   bool verbose = false;  // HY_VERBOSE=1: per-iteration diagnostics on stderr
+  int prefetch = 0;      // L2 prefetch distance of the tangent action's cache chunks, in cell blocks
   size_t bytes = 0;      // device bytes currently owned
   // The V-cycle below the finest level's input/output copies is captured once per linearisation into a
   // CUDA graph and replayed (HY_GRAPHS=0 disables this and launches kernel by kernel).
@@ -372,6 +373,7 @@ hy_status vmult(hy_ctx* ctx, int l, const vec_t<T>* x, vec_t<T>* y, bool constra
   a.y = y;
   a.cache = cache_of<T>(L);
   a.ubar = ubar_of<T>(L);
+  a.pf = ctx->prefetch;
   if (constrained_in) {
     launch_prep_out<V>(x, y, L.nnodes, ctx->dim, L.g, ctx->stream);
   } else {
@@ -1184,7 +1186,7 @@ hy_status upload_list(hy_batch* b, const std::vector<int>& idx, const std::vecto
   if (b->up_dt == dt && b->up_x == x && b->up_y == y) return HY_OK;
   HB_CK(cudaEventSynchronize(b->ev_upload));  // the staging buffer is free again
   CellArgs<T>* h = static_cast<CellArgs<T>*>(b->h_list);
-  const int cb = apply_cells_per_block(b->dim, b->n);
+  const int cb = apply_cells_per_block<T>(b->dim, b->n);
   long long blocks = 0, max_nodes = 0;
   for (size_t j = 0; j < idx.size(); ++j) {
     hy_ctx* c = b->ctx[idx[j]];
@@ -1195,6 +1197,7 @@ hy_status upload_list(hy_batch* b, const std::vector<int>& idx, const std::vecto
     a.y = static_cast<vec_t<T>*>(const_cast<void*>(y[j]));
     a.cache = cache_of<T>(L);
     a.ubar = ubar_of<T>(L);
+    a.pf = c->prefetch;
     h[j] = a;
     b->h_start[j] = (int)blocks;
     blocks += (L.g.ncells + cb - 1) / cb;
@@ -1621,6 +1624,7 @@ hy_status hy_create(hy_ctx** out, int device, void* stream) {
   ctx->stream = (cudaStream_t)stream;
   const char* v = std::getenv("HY_VERBOSE");
   ctx->verbose = v && v[0] == '1';
+  if (const char* pf = std::getenv("HY_PREFETCH")) ctx->prefetch = std::max(0, std::atoi(pf));
   const char* gr = std::getenv("HY_GRAPHS");
   ctx->use_graphs = !(gr && gr[0] == '0');
   *out = ctx;

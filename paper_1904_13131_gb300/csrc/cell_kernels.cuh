@@ -27,7 +27,7 @@ struct CellArgs {
   vec_t<T>* y;            // apply / residual / diag: destination, accumulated with atomics
   const vec_t<T>* ubar;   // level displacement (variants that recompute F)
   const double* u64;      // level displacement in FP64 (state build, residual, diagonal)
-  const T* cache;         // per-Gauss-point cache in the blocked layout of cache_row()
+  const T* cache;         // per-Gauss-point cache in the blocked layout of layout_row<T>()
   T* cache_out;           // state build output
   const uint8_t* mat;     // material id per cell
   unsigned* err;          // device error word (J <= 0, NaN)
@@ -36,6 +36,7 @@ struct CellArgs {
   Geom g;
   Basis1D<T> b;
   long long nqp;          // ncells * NPT
+  int pf;                 // apply: L2 prefetch distance in cell blocks (0: none)
 };
 
 // --- asynchronous bulk copy (TMA engine) of a block's cache chunk into shared memory ------------------
@@ -60,6 +61,24 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
         "l"(static_cast<const char*>(src) + off), "r"(sz), "r"(smem_u32(bar))
         : "memory");
   }
+}
+// Hint the TMA engine to pull `bytes` (multiple of 16, 16-byte aligned src) from global memory into L2.
+__device__ __forceinline__ void prefetch_l2(const void* src, unsigned bytes) {
+  constexpr unsigned PIECE = 32768;
+  for (unsigned off = 0; off < bytes; off += PIECE) {
+    const unsigned sz = bytes - off < PIECE ? bytes - off : PIECE;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(static_cast<const char*>(src) + off), "r"(sz)
+                 : "memory");
+  }
+}
+// Cache chunk `blk + pf` of this problem into L2, if it exists: the block that will read it, a few waves
+// later, then finds it there instead of in HBM.
+template <int NV, int BS, int CB, typename T>
+__device__ __forceinline__ void prefetch_chunk(const CellArgs<T>& a, int blk) {
+  if (a.pf <= 0) return;
+  const long long nb = (a.g.ncells + CB - 1) / CB;
+  const long long pb = (long long)blk + a.pf;
+  if (pb < nb) prefetch_l2(a.cache + (size_t)pb * NV * BS, (unsigned)(NV * BS * sizeof(T)));
 }
 // Wait for phase `parity` of the barrier with a bounded number of polls; false if it never completed.
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
@@ -435,10 +454,10 @@ __device__ __forceinline__ void nh_action(const T g[DIM][DIM], T c1, T c2, T Sv[
 }
 
 // Shared-memory layout of one block.
-template <int DIM, int N, typename T>
+template <int DIM, int N, typename T, int CB_ = cells_per_block(DIM, N)>
 struct Smem {
   static constexpr int NPT = ipow(N, DIM);
-  static constexpr int CB = cells_per_block(DIM, N);
+  static constexpr int CB = CB_;
   T S[MAXN][MAXN], D[MAXN][MAXN], Dh[MAXN][MAXN], W[NPT], Wh[NPT];
   T mu[MAXMAT], lam[MAXMAT];
   T bp[CB][DIM * DIM][NPT];  // fluxes; also the ping-pong pair for the displacement
@@ -446,8 +465,8 @@ struct Smem {
   T b1[CB][DIM][NPT];
 };
 
-template <int DIM, int N, typename T>
-__device__ __forceinline__ void load_tables(Smem<DIM, N, T>& s, const CellArgs<T>& a) {
+template <int DIM, int N, typename T, int CB>
+__device__ __forceinline__ void load_tables(Smem<DIM, N, T, CB>& s, const CellArgs<T>& a) {
   constexpr int NPT = ipow(N, DIM);
   const int t = threadIdx.x;
   if (t < MAXN * MAXN) {
@@ -560,12 +579,12 @@ __device__ __forceinline__ void qp_flux(const T G[DIM][DIM], const T Gu[DIM][DIM
 template <int DIM, int N, int VAR, typename T>
 __device__ __forceinline__ void apply_point_body(const CellArgs<T>& a, const int blk) {
   constexpr int NPT = ipow(N, DIM);
-  constexpr int CB = cells_per_block(DIM, N);
+  constexpr int CB = layout_cells<T>(DIM, N);
   constexpr int NS = nsym(DIM);
   constexpr bool NEED_U = (VAR == VAR_NC || VAR == VAR_SC);
   constexpr int NV = cache_values(VAR, DIM);
-  constexpr int BS = cache_row(DIM, N);
-  __shared__ Smem<DIM, N, T> s;
+  constexpr int BS = layout_row<T>(DIM, N);
+  __shared__ Smem<DIM, N, T, CB> s;
   __shared__ __align__(8) unsigned long long bar;
   extern __shared__ __align__(128) unsigned char dyn_smem[];
   T* cs = reinterpret_cast<T*>(dyn_smem);  // this block's cache chunk [NV][BS]
@@ -573,6 +592,7 @@ __device__ __forceinline__ void apply_point_body(const CellArgs<T>& a, const int
     // the chunk streams in (TMA bulk copy) while the block gathers x and runs the forward sweeps
     mbar_init(&bar, 1);
     bulk_load(cs, a.cache + (size_t)blk * NV * BS, (unsigned)(NV * BS * sizeof(T)), &bar);
+    prefetch_chunk<NV, BS, CB>(a, blk);
   }
   load_tables<DIM, N>(s, a);
   const int cl = threadIdx.x / NPT;
@@ -660,12 +680,12 @@ template <int DIM, int N, int VAR, typename T>
 __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int blk) {
   constexpr int NPT = ipow(N, DIM);
   constexpr int NLC = ipow(N, DIM - 1);
-  constexpr int CB = cells_per_block_line(DIM, N);
+  constexpr int CB = layout_cells<T>(DIM, N);
   constexpr int K = N - 1;
   constexpr bool NEED_U = (VAR == VAR_NC || VAR == VAR_SC);
   constexpr bool PHYS = (VAR == VAR_FC || NEED_U);
   constexpr int NV = cache_values(VAR, DIM);
-  constexpr int BS = cache_row_line(DIM, N);
+  constexpr int BS = layout_row<T>(DIM, N);
   constexpr int NU = NEED_U ? CB : 1;
   __shared__ T tS[MAXN][MAXN], tD[MAXN][MAXN], tDh[MAXN][MAXN], tWh[NPT], tmu[MAXMAT], tlam[MAXMAT];
   __shared__ T buf0[CB][DIM][NPT], buf1[CB][DIM][NPT];
@@ -682,6 +702,7 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
   if (STAGE && NV > 0 && t == 0) {
     mbar_init(&bar, 1);
     bulk_load(cs, cg, (unsigned)(NV * BS * sizeof(T)), &bar);
+    prefetch_chunk<NV, BS, CB>(a, blk);
   }
   // tables (strided loops: a block may have fewer threads than entries)
   for (int i = t; i < MAXN * MAXN; i += blockDim.x) {
@@ -954,26 +975,26 @@ __device__ __forceinline__ int work_item(const int* __restrict__ start, int coun
 }
 
 template <int DIM, int N, int VAR, typename T>
-__global__ void __launch_bounds__(cells_per_block(DIM, N) * ipow(N, DIM))
+__global__ void __launch_bounds__(layout_cells<T>(DIM, N) * ipow(N, DIM))
 apply_kernel(const CellArgs<T> a) {
   apply_point_body<DIM, N, VAR, T>(a, blockIdx.x);
 }
 
 template <int DIM, int N, int VAR, typename T>
-__global__ void __launch_bounds__(cells_per_block(DIM, N) * ipow(N, DIM))
+__global__ void __launch_bounds__(layout_cells<T>(DIM, N) * ipow(N, DIM))
 apply_list_kernel(const CellArgs<T>* __restrict__ list, const int* __restrict__ start, int count) {
   const int p = work_item(start, count, blockIdx.x);
   apply_point_body<DIM, N, VAR, T>(list[p], blockIdx.x - start[p]);
 }
 
 template <int DIM, int N, int VAR, typename T>
-__global__ void __launch_bounds__(cells_per_block_line(DIM, N) * ipow(N, DIM - 1))
+__global__ void __launch_bounds__(layout_cells<T>(DIM, N) * ipow(N, DIM - 1))
 apply_line_kernel(const CellArgs<T> a) {
   apply_line_body<DIM, N, VAR, T>(a, blockIdx.x);
 }
 
 template <int DIM, int N, int VAR, typename T>
-__global__ void __launch_bounds__(cells_per_block_line(DIM, N) * ipow(N, DIM - 1))
+__global__ void __launch_bounds__(layout_cells<T>(DIM, N) * ipow(N, DIM - 1))
 apply_line_list_kernel(const CellArgs<T>* __restrict__ list, const int* __restrict__ start, int count) {
   const int p = work_item(start, count, blockIdx.x);
   apply_line_body<DIM, N, VAR, T>(list[p], blockIdx.x - start[p]);

@@ -84,18 +84,19 @@ __host__ __device__ constexpr int cache_row(int dim, int n) {
   return (cells_per_block(dim, n) * ipow(n, dim) + 3) / 4 * 4;
 }
 
-// Both forms of the tangent action -- one thread per (cell, Gauss point) and one thread per x-line of a
-// cell -- process the same cells per block and so read the same cache layout; which form runs is picked per
-// (dim, degree, variant, precision, size) by the autotuner (csrc/capi.cu).
-__host__ __device__ constexpr int cells_per_block_line(int dim, int n) { return cells_per_block(dim, n); }
-__host__ __device__ constexpr int cache_row_line(int dim, int n) { return cache_row(dim, n); }
+// Cells per block of the tangent action and of its cache layout, per element type. Both forms of the
+// action -- one thread per (cell, Gauss point) and one thread per x-line of a cell -- process the same
+// cells per block for a given element type, so they read the same cache and the autotuner (csrc/capi.cu)
+// can switch forms without rebuilding it. FP64 and double-float, bound by arithmetic, take ~256 threads in
+// the point form (256 / (k+1)^dim cells); FP32, bound by memory latency, takes ~128 threads in the line
+// form (128 / (k+1)^(dim-1) cells), which lets more blocks stream their cache chunks per SM.
 template <typename T>
 __host__ __device__ constexpr int layout_cells(int dim, int n) {
-  return cells_per_block(dim, n);
+  return sizeof(T) == 4 ? ((128 / ipow(n, dim - 1)) < 1 ? 1 : (128 / ipow(n, dim - 1))) : cells_per_block(dim, n);
 }
 template <typename T>
 __host__ __device__ constexpr int layout_row(int dim, int n) {
-  return cache_row(dim, n);
+  return (layout_cells<T>(dim, n) * ipow(n, dim) + 3) / 4 * 4;
 }
 
 enum KernelForm { FORM_POINT = 0, FORM_LINE = 1 };

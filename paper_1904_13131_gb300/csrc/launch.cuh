@@ -21,8 +21,9 @@ using StateFn = void (*)(const CellArgs<double>&, TOUT*, cudaStream_t);
 template <typename T>
 using ApplyListFn = void (*)(const CellArgs<T>* list, const int* start, int count, int blocks, int form,
                              cudaStream_t);
-// cells per thread block of the tangent action (both forms): the work-list block counts
-inline int apply_cells_per_block(int dim, int n) { return cells_per_block(dim, n); }
+// cells per thread block of the tangent action (both forms) for element type T: the work-list block counts
+template <typename T>
+inline int apply_cells_per_block(int dim, int n) { return layout_cells<T>(dim, n); }
 
 // n = degree + 1 in 2..5; var in Variant; returns nullptr for unsupported combinations. The kernels of
 // degrees 1-2 (n <= 3) and 3-4 live in separate translation units (_lo, _hi) that compile in parallel.

@@ -801,7 +801,7 @@ std::mutex g_tune_mu;
 std::map<TuneKey, int> g_tune;
 bool g_tune_loaded = false;
 const char* const kVarNames[5] = {"T4", "T2", "FC", "SC", "NC"};
-const char* const kFormNames[2] = {"point", "line"};
+const char* const kFormNames[3] = {"point", "line", "line_persistent"};
 const char* const kPrecNames[3] = {"f64", "f32", "ff"};
 
 int name_index(const char* s, const char* const* names, int n) {
@@ -820,12 +820,12 @@ void tune_load_locked() {
   char line[512];
   while (std::fgets(line, sizeof line, f)) {
     int d = 0, k = 0, b = 0;
-    char var[8] = {}, prec[8] = {}, form[8] = {};
+    char var[8] = {}, prec[8] = {}, form[24] = {};
     if (std::sscanf(line, " {\"dim\": %d, \"degree\": %d, \"variant\": \"%7[^\"]\", \"precision\": \"%7[^\"]\", "
-                          "\"cells_log2\": %d, \"threads_per_cell\": \"%7[^\"]\"",
+                          "\"cells_log2\": %d, \"threads_per_cell\": \"%23[^\"]\"",
                     &d, &k, var, prec, &b, form) != 6)
       continue;  // the brackets and anything unrecognised
-    const int v = name_index(var, kVarNames, 5), fm = name_index(form, kFormNames, 2);
+    const int v = name_index(var, kVarNames, 5), fm = name_index(form, kFormNames, 3);
     const int p = name_index(prec, kPrecNames, 3);
     if (v >= 0 && fm >= 0 && p >= 0) g_tune[TuneKey{d, k, v, p, b}] = fm;
   }
@@ -891,13 +891,15 @@ hy_status autotune_level(hy_ctx* ctx, int l) {
   HY_CK(cudaEventCreate(&ev.a));
   HY_CK(cudaEventCreate(&ev.b));
   cudaEvent_t e0 = ev.a, e1 = ev.b;
-  float best[2] = {1e30f, 1e30f};
-  for (int form = 0; form < 2; ++form) {
+  // FP32 also has the persistent double-buffered line form
+  const int nforms = std::is_same<T, float>::value ? 3 : 2;
+  float best[3] = {1e30f, 1e30f, 1e30f};
+  for (int form = 0; form < nforms; ++form) {
     L.form[dt] = form;
     HY_TRY(vmult<T>(ctx, l, x, y));
   }
   for (int r = 0; r < 3; ++r) {
-    for (int form = 0; form < 2; ++form) {
+    for (int form = 0; form < nforms; ++form) {
       L.form[dt] = form;
       cudaEventRecord(e0, ctx->stream);
       for (int q = 0; q < 4; ++q) HY_TRY(vmult<T>(ctx, l, x, y));
@@ -908,11 +910,14 @@ hy_status autotune_level(hy_ctx* ctx, int l) {
       best[form] = std::min(best[form], 0.25f * ms);
     }
   }
-  const int choice = best[1] < best[0] ? FORM_LINE : FORM_POINT;
+  int choice = FORM_POINT;
+  for (int form = 1; form < nforms; ++form)
+    if (best[form] < best[choice]) choice = form;
   L.form[dt] = choice;
   if (ctx->verbose)
-    std::fprintf(stderr, "[hy] autotune dim %d k %d var %d %s cells 2^%d: point %.3f ms, line %.3f ms -> %s\n", ctx->dim,
-                 ctx->k, ctx->var, kPrecNames[dt], bucket, best[0], best[1], choice ? "line" : "point");
+    std::fprintf(stderr, "[hy] autotune dim %d k %d var %d %s cells 2^%d: point %.3f ms, line %.3f ms, persistent %.3f ms -> %s\n",
+                 ctx->dim, ctx->k, ctx->var, kPrecNames[dt], bucket, best[0], best[1], nforms > 2 ? best[2] : 0.f,
+                 kFormNames[choice]);
   std::lock_guard<std::mutex> lock(g_tune_mu);
   if (g_tune.emplace(key, choice).second) tune_save_locked();
   return HY_OK;
@@ -1930,7 +1935,7 @@ hy_status hy_gmg_vcycle(hy_ctx* ctx, const double* r, double* z) {
 hy_status hy_set_solver_params(hy_ctx* ctx, const hy_solver_params* p) {
   if (!ctx || !p) return HY_ERR_ARG;
   if (p->cheb_degree < 1 || p->cheb_sweeps < 1 || !(p->cheb_lo > 0) || !(p->cheb_hi > p->cheb_lo) ||
-      p->kernel_form < -1 || p->kernel_form > 1 || (p->fine_dtype != HY_F64 && p->fine_dtype != HY_FF) ||
+      p->kernel_form < -1 || p->kernel_form > 2 || (p->fine_dtype != HY_F64 && p->fine_dtype != HY_FF) ||
       p->eig_iters < 1 || p->coarse_eig_iters < 0 || !(p->coarse_reduction > 0 && p->coarse_reduction < 1) ||
       p->coarse_solver < 0 || p->coarse_solver > 1)
     return fail(ctx, HY_ERR_ARG, "solver parameters out of range");

@@ -62,6 +62,9 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
         : "memory");
   }
 }
+// Order this thread's earlier generic-proxy accesses to shared memory before later async-proxy ones (a bulk
+// copy refilling a buffer that threads have read).
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 // Hint the TMA engine to pull `bytes` (multiple of 16, 16-byte aligned src) from global memory into L2.
 __device__ __forceinline__ void prefetch_l2(const void* src, unsigned bytes) {
   constexpr unsigned PIECE = 32768;
@@ -676,8 +679,11 @@ __device__ __forceinline__ void apply_point_body(const CellArgs<T>& a, const int
 // memory, and gather and scatter touch one contiguous run of (k+1)*dim values. The y and z sweeps exchange
 // values through shared memory, the thread playing the line (q0 varies; q1 = l1, q2 = l2) of each stage.
 // Same arithmetic, variants and Dirichlet treatment as apply_kernel.
-template <int DIM, int N, int VAR, typename T>
-__device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int blk) {
+// PERSIST: the thread block loops over the cell blocks blk0, blk0 + step, ... with the cache chunks in
+// two shared-memory stages -- the bulk copy of the next chunk runs while the current one is used (tables
+// are loaded once per thread block). Otherwise the thread block processes the one cell block blk0.
+template <int DIM, int N, int VAR, typename T, bool PERSIST = false>
+__device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int blk0, const int step) {
   constexpr int NPT = ipow(N, DIM);
   constexpr int NLC = ipow(N, DIM - 1);
   constexpr int CB = layout_cells<T>(DIM, N);
@@ -691,18 +697,23 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
   __shared__ T buf0[CB][DIM][NPT], buf1[CB][DIM][NPT];
   __shared__ T ubuf0[NU][DIM][NPT], ubuf1[NU][DIM][NPT];
   __shared__ T flux[CB][DIM][DIM - 1][NPT];
-  __shared__ __align__(8) unsigned long long bar;
+  __shared__ __align__(8) unsigned long long bar[2];
   extern __shared__ __align__(128) unsigned char dyn_smem[];
-  T* cs = reinterpret_cast<T*>(dyn_smem);
+  T* const cs0 = reinterpret_cast<T*>(dyn_smem);
   const int t = threadIdx.x;
   // STAGE: the block's cache chunk streams into shared memory with one bulk copy (measured faster for
   // T4 than reading the cache straight from global memory at the Gauss points, 18.3 vs 12.9 GDoF/s).
   constexpr bool STAGE = HY_LINE_STAGE;
-  const T* cg = a.cache + (size_t)blk * NV * BS;
+  constexpr int NST = (PERSIST && STAGE && NV > 0) ? 2 : 1;  // shared-memory stages of the cache
+  constexpr unsigned CHUNK = (unsigned)(NV * BS * sizeof(T));
+  const int nb = PERSIST ? (a.g.ncells + CB - 1) / CB : blk0 + 1;
   if (STAGE && NV > 0 && t == 0) {
-    mbar_init(&bar, 1);
-    bulk_load(cs, cg, (unsigned)(NV * BS * sizeof(T)), &bar);
-    prefetch_chunk<NV, BS, CB>(a, blk);
+    mbar_init(&bar[0], 1);
+    if (NST == 2) mbar_init(&bar[1], 1);
+    if (blk0 < nb) {
+      bulk_load(cs0, a.cache + (size_t)blk0 * NV * BS, CHUNK, &bar[0]);
+      if (!PERSIST) prefetch_chunk<NV, BS, CB>(a, blk0);
+    }
   }
   // tables (strided loops: a block may have fewer threads than entries)
   for (int i = t; i < MAXN * MAXN; i += blockDim.x) {
@@ -726,53 +737,38 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
   }
   const int cl = t / NLC, l = t % NLC;
   const int l1 = l % N, l2 = DIM == 3 ? l / N : 0;
-  const int cell = blk * CB + cl;
-  const bool active = cell < a.g.ncells;
-  const int m = a.g.m;
-  const int cc = active ? cell : 0;
-  const int c0 = cc % m, c1 = (cc / m) % m, c2 = DIM == 3 ? cc / (m * m) : 0;
-  const int i1 = K * c1 + l1, i2 = K * c2 + l2;
-  const long long node0 = K * c0 + (long long)a.g.L * (i1 + (DIM == 3 ? (long long)a.g.L * i2 : 0));
-  uint32_t cms[N];
-  T v[N][DIM], vu[N][DIM];
-#pragma unroll
-  for (int a0 = 0; a0 < N; ++a0) {
-    cms[a0] = node_cmask<DIM>(a.g, K * c0 + a0, i1, i2);
-#pragma unroll
-    for (int c = 0; c < DIM; ++c) {
-      const long long dof = (node0 + a0) * DIM + c;
-      v[a0][c] = (active && !((cms[a0] >> c) & 1u)) ? vec_in<T>(a.x[dof]) : T(0);
-      vu[a0][c] = (NEED_U && active) ? vec_in<T>(a.ubar[dof]) : T(0);
+  int it = 0;
+  for (int blk = blk0; blk < nb; blk += step, ++it) {
+    const int st = NST == 2 ? (it & 1) : 0;
+    T* const cs = cs0 + (size_t)st * NV * BS;
+    const T* cg = a.cache + (size_t)blk * NV * BS;
+    if (NST == 2 && t == 0 && blk + step < nb) {
+      // the other stage was last read in the previous iteration, before its closing barrier
+      fence_proxy_async();
+      bulk_load(cs0 + (size_t)(st ^ 1) * NV * BS, a.cache + (size_t)(blk + step) * NV * BS, CHUNK, &bar[st ^ 1]);
     }
-  }
-  __syncthreads();
-  // x: interpolation to the Gauss points of the line, in registers
-  T X[N][DIM], XU[N][DIM];
+    const int cell = blk * CB + cl;
+    const bool active = cell < a.g.ncells;
+    const int m = a.g.m;
+    const int cc = active ? cell : 0;
+    const int c0 = cc % m, c1 = (cc / m) % m, c2 = DIM == 3 ? cc / (m * m) : 0;
+    const int i1 = K * c1 + l1, i2 = K * c2 + l2;
+    const long long node0 = K * c0 + (long long)a.g.L * (i1 + (DIM == 3 ? (long long)a.g.L * i2 : 0));
+    uint32_t cms[N];
+    T v[N][DIM], vu[N][DIM];
 #pragma unroll
-  for (int q = 0; q < N; ++q)
+    for (int a0 = 0; a0 < N; ++a0) {
+      cms[a0] = node_cmask<DIM>(a.g, K * c0 + a0, i1, i2);
 #pragma unroll
-    for (int c = 0; c < DIM; ++c) {
-      T sx = T(0), su = T(0);
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        sx = fma(tS[q][j], v[j][c], sx);
-        if (NEED_U) su = fma(tS[q][j], vu[j][c], su);
+      for (int c = 0; c < DIM; ++c) {
+        const long long dof = (node0 + a0) * DIM + c;
+        v[a0][c] = (active && !((cms[a0] >> c) & 1u)) ? vec_in<T>(a.x[dof]) : T(0);
+        vu[a0][c] = (NEED_U && active) ? vec_in<T>(a.ubar[dof]) : T(0);
       }
-      X[q][c] = sx;
-      XU[q][c] = su;
     }
-  // y (and z): through shared memory
-  T V[N][DIM], VU[N][DIM];
-#pragma unroll
-  for (int q = 0; q < N; ++q)
-#pragma unroll
-    for (int c = 0; c < DIM; ++c) {
-      buf0[cl][c][q + N * l] = X[q][c];
-      if (NEED_U) ubuf0[NEED_U ? cl : 0][c][q + N * l] = XU[q][c];
-    }
-  __syncthreads();
-  if (DIM == 3) {
-    // y: this thread plays (q1 = l1, a2 = l2)
+    __syncthreads();
+    // x: interpolation to the Gauss points of the line, in registers
+    T X[N][DIM], XU[N][DIM];
 #pragma unroll
     for (int q = 0; q < N; ++q)
 #pragma unroll
@@ -780,184 +776,214 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
         T sx = T(0), su = T(0);
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-          sx = fma(tS[l1][j], buf0[cl][c][q + N * (j + N * l2)], sx);
-          if (NEED_U) su = fma(tS[l1][j], ubuf0[NEED_U ? cl : 0][c][q + N * (j + N * l2)], su);
+          sx = fma(tS[q][j], v[j][c], sx);
+          if (NEED_U) su = fma(tS[q][j], vu[j][c], su);
         }
-        buf1[cl][c][q + N * l] = sx;
-        if (NEED_U) ubuf1[NEED_U ? cl : 0][c][q + N * l] = su;
+        X[q][c] = sx;
+        XU[q][c] = su;
       }
-    __syncthreads();
-    // z: (q1 = l1, q2 = l2)
+    // y (and z): through shared memory
+    T V[N][DIM], VU[N][DIM];
 #pragma unroll
     for (int q = 0; q < N; ++q)
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
-        T sx = T(0), su = T(0);
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-          sx = fma(tS[l2][j], buf1[cl][c][q + N * (l1 + N * j)], sx);
-          if (NEED_U) su = fma(tS[l2][j], ubuf1[NEED_U ? cl : 0][c][q + N * (l1 + N * j)], su);
-        }
-        V[q][c] = sx;
-        VU[q][c] = su;
+        buf0[cl][c][q + N * l] = X[q][c];
+        if (NEED_U) ubuf0[NEED_U ? cl : 0][c][q + N * l] = XU[q][c];
       }
-  } else {
+    __syncthreads();
+    if (DIM == 3) {
+      // y: this thread plays (q1 = l1, a2 = l2)
+#pragma unroll
+      for (int q = 0; q < N; ++q)
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+          T sx = T(0), su = T(0);
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            sx = fma(tS[l1][j], buf0[cl][c][q + N * (j + N * l2)], sx);
+            if (NEED_U) su = fma(tS[l1][j], ubuf0[NEED_U ? cl : 0][c][q + N * (j + N * l2)], su);
+          }
+          buf1[cl][c][q + N * l] = sx;
+          if (NEED_U) ubuf1[NEED_U ? cl : 0][c][q + N * l] = su;
+        }
+      __syncthreads();
+      // z: (q1 = l1, q2 = l2)
+#pragma unroll
+      for (int q = 0; q < N; ++q)
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+          T sx = T(0), su = T(0);
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            sx = fma(tS[l2][j], buf1[cl][c][q + N * (l1 + N * j)], sx);
+            if (NEED_U) su = fma(tS[l2][j], ubuf1[NEED_U ? cl : 0][c][q + N * (l1 + N * j)], su);
+          }
+          V[q][c] = sx;
+          VU[q][c] = su;
+        }
+    } else {
+#pragma unroll
+      for (int q = 0; q < N; ++q)
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+          T sx = T(0), su = T(0);
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            sx = fma(tS[l1][j], buf0[cl][c][q + N * j], sx);
+            if (NEED_U) su = fma(tS[l1][j], ubuf0[NEED_U ? cl : 0][c][q + N * j], su);
+          }
+          V[q][c] = sx;
+          VU[q][c] = su;
+        }
+    }
+    // values at the Gauss points of the line go to shared memory for the y/z derivatives of the others
+    // (3D: buf0 was last read before the previous barrier; 2D: buf1 is unused so far)
+    T (*vb)[DIM][NPT] = DIM == 3 ? buf0 : buf1;
+    T (*vub)[DIM][NPT] = DIM == 3 ? ubuf0 : ubuf1;
 #pragma unroll
     for (int q = 0; q < N; ++q)
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
-        T sx = T(0), su = T(0);
+        vb[cl][c][q + N * l] = V[q][c];
+        if (NEED_U) vub[NEED_U ? cl : 0][c][q + N * l] = VU[q][c];
+      }
+    __syncthreads();
+    if (STAGE && NV > 0) {
+      const unsigned parity = NST == 2 ? ((it >> 1) & 1) : 0;
+      const bool ok = mbar_wait(&bar[st], parity);
+      if (__syncthreads_or(!ok)) {  // a copy never completed: flag it, let the copies in flight land, leave
+        if (t == 0) atomicOr(a.err, ERRBIT_TIMEOUT);
+        mbar_wait(&bar[st], parity);
+        if (NST == 2 && blk + step < nb) mbar_wait(&bar[st ^ 1], ((it + 1) >> 1) & 1);
+        return;
+      }
+    }
+    const T* cq = STAGE ? cs : cg;
+    const T (*Dd)[MAXN] = PHYS ? tDh : tD;
+    const int id = active ? a.mat[cell] : 0;
+    T Px[N][DIM];
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      const int p = q + N * l;
+      T G[DIM][DIM], Gu[DIM][DIM];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        T g0 = T(0), u0 = T(0);
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-          sx = fma(tS[l1][j], buf0[cl][c][q + N * j], sx);
-          if (NEED_U) su = fma(tS[l1][j], ubuf0[NEED_U ? cl : 0][c][q + N * j], su);
+          g0 = fma(Dd[q][j], V[j][c], g0);
+          if (NEED_U) u0 = fma(Dd[q][j], VU[j][c], u0);
         }
-        V[q][c] = sx;
-        VU[q][c] = su;
-      }
-  }
-  // values at the Gauss points of the line go to shared memory for the y/z derivatives of the others
-  // (3D: buf0 was last read before the previous barrier; 2D: buf1 is unused so far)
-  T (*vb)[DIM][NPT] = DIM == 3 ? buf0 : buf1;
-  T (*vub)[DIM][NPT] = DIM == 3 ? ubuf0 : ubuf1;
-#pragma unroll
-  for (int q = 0; q < N; ++q)
-#pragma unroll
-    for (int c = 0; c < DIM; ++c) {
-      vb[cl][c][q + N * l] = V[q][c];
-      if (NEED_U) vub[NEED_U ? cl : 0][c][q + N * l] = VU[q][c];
-    }
-  __syncthreads();
-  if (STAGE && NV > 0) {
-    const bool ok = mbar_wait(&bar, 0);
-    if (__syncthreads_or(!ok)) {
-      if (t == 0) atomicOr(a.err, ERRBIT_TIMEOUT);
-      mbar_wait(&bar, 0);
-      return;
-    }
-  }
-  const T* cq = STAGE ? cs : cg;
-  const T (*Dd)[MAXN] = PHYS ? tDh : tD;
-  const int id = active ? a.mat[cell] : 0;
-  T Px[N][DIM];
-#pragma unroll
-  for (int q = 0; q < N; ++q) {
-    const int p = q + N * l;
-    T G[DIM][DIM], Gu[DIM][DIM];
-#pragma unroll
-    for (int c = 0; c < DIM; ++c) {
-      T g0 = T(0), u0 = T(0);
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        g0 = fma(Dd[q][j], V[j][c], g0);
-        if (NEED_U) u0 = fma(Dd[q][j], VU[j][c], u0);
-      }
-      G[c][0] = g0;
-      Gu[c][0] = u0;
-      T g1 = T(0), u1 = T(0);
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        const int pj = DIM == 3 ? q + N * (j + N * l2) : q + N * j;
-        g1 = fma(Dd[l1][j], vb[cl][c][pj], g1);
-        if (NEED_U) u1 = fma(Dd[l1][j], vub[NEED_U ? cl : 0][c][pj], u1);
-      }
-      G[c][1] = g1;
-      Gu[c][1] = u1;
-      if (DIM == 3) {
-        T g2 = T(0), u2 = T(0);
+        G[c][0] = g0;
+        Gu[c][0] = u0;
+        T g1 = T(0), u1 = T(0);
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-          g2 = fma(Dd[l2][j], vb[cl][c][q + N * (l1 + N * j)], g2);
-          if (NEED_U) u2 = fma(Dd[l2][j], vub[NEED_U ? cl : 0][c][q + N * (l1 + N * j)], u2);
+          const int pj = DIM == 3 ? q + N * (j + N * l2) : q + N * j;
+          g1 = fma(Dd[l1][j], vb[cl][c][pj], g1);
+          if (NEED_U) u1 = fma(Dd[l1][j], vub[NEED_U ? cl : 0][c][pj], u1);
         }
-        G[c][DIM - 1] = g2;
-        Gu[c][DIM - 1] = u2;
+        G[c][1] = g1;
+        Gu[c][1] = u1;
+        if (DIM == 3) {
+          T g2 = T(0), u2 = T(0);
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            g2 = fma(Dd[l2][j], vb[cl][c][q + N * (l1 + N * j)], g2);
+            if (NEED_U) u2 = fma(Dd[l2][j], vub[NEED_U ? cl : 0][c][q + N * (l1 + N * j)], u2);
+          }
+          G[c][DIM - 1] = g2;
+          Gu[c][DIM - 1] = u2;
+        }
+      }
+      T P[DIM][DIM];
+      qp_flux<DIM, VAR>(G, Gu, cq, BS, cl * NPT + p, active, id, tmu, tlam, tWh[p], P);
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        Px[q][c] = P[c][0];
+#pragma unroll
+        for (int J = 1; J < DIM; ++J) flux[cl][c][J - 1][p] = P[c][J];
       }
     }
-    T P[DIM][DIM];
-    qp_flux<DIM, VAR>(G, Gu, cq, BS, cl * NPT + p, active, id, tmu, tlam, tWh[p], P);
-#pragma unroll
-    for (int c = 0; c < DIM; ++c) {
-      Px[q][c] = P[c][0];
-#pragma unroll
-      for (int J = 1; J < DIM; ++J) flux[cl][c][J - 1][p] = P[c][J];
-    }
-  }
-  __syncthreads();
-  // transposed derivatives summed over the directions: x from registers, y/z from shared memory
-  T Wq[N][DIM];
-#pragma unroll
-  for (int q = 0; q < N; ++q)
-#pragma unroll
-    for (int c = 0; c < DIM; ++c) {
-      T s = T(0);
-#pragma unroll
-      for (int j = 0; j < N; ++j) s = fma(tD[j][q], Px[j][c], s);
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        const int pj = DIM == 3 ? q + N * (j + N * l2) : q + N * j;
-        s = fma(tD[j][l1], flux[cl][c][0][pj], s);
-      }
-      if (DIM == 3) {
-#pragma unroll
-        for (int j = 0; j < N; ++j) s = fma(tD[j][l2], flux[cl][c][DIM - 2][q + N * (l1 + N * j)], s);
-      }
-      Wq[q][c] = s;
-    }
-  // transposed interpolation: z, y through shared memory (buffers free since the flux barrier), x in registers
-  T Yb[N][DIM];
-  if (DIM == 3) {
-#pragma unroll
-    for (int q = 0; q < N; ++q)
-#pragma unroll
-      for (int c = 0; c < DIM; ++c) buf1[cl][c][q + N * l] = Wq[q][c];
     __syncthreads();
-#pragma unroll
-    for (int q = 0; q < N; ++q)
-#pragma unroll
-      for (int c = 0; c < DIM; ++c) {  // z: (q1 = l1, a2 = l2)
-        T sz = T(0);
-#pragma unroll
-        for (int j = 0; j < N; ++j) sz = fma(tS[j][l2], buf1[cl][c][q + N * (l1 + N * j)], sz);
-        buf0[cl][c][q + N * l] = sz;
-      }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < N; ++q)
-#pragma unroll
-      for (int c = 0; c < DIM; ++c) {  // y: (a1 = l1, a2 = l2)
-        T sy = T(0);
-#pragma unroll
-        for (int j = 0; j < N; ++j) sy = fma(tS[j][l1], buf0[cl][c][q + N * (j + N * l2)], sy);
-        Yb[q][c] = sy;
-      }
-  } else {
-#pragma unroll
-    for (int q = 0; q < N; ++q)
-#pragma unroll
-      for (int c = 0; c < DIM; ++c) buf0[cl][c][q + N * l] = Wq[q][c];
-    __syncthreads();
+    // transposed derivatives summed over the directions: x from registers, y/z from shared memory
+    T Wq[N][DIM];
 #pragma unroll
     for (int q = 0; q < N; ++q)
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
-        T sy = T(0);
+        T s = T(0);
 #pragma unroll
-        for (int j = 0; j < N; ++j) sy = fma(tS[j][l1], buf0[cl][c][q + N * j], sy);
-        Yb[q][c] = sy;
+        for (int j = 0; j < N; ++j) s = fma(tD[j][q], Px[j][c], s);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const int pj = DIM == 3 ? q + N * (j + N * l2) : q + N * j;
+          s = fma(tD[j][l1], flux[cl][c][0][pj], s);
+        }
+        if (DIM == 3) {
+#pragma unroll
+          for (int j = 0; j < N; ++j) s = fma(tD[j][l2], flux[cl][c][DIM - 2][q + N * (l1 + N * j)], s);
+        }
+        Wq[q][c] = s;
       }
-  }
-  if (!active) return;
+    // transposed interpolation: z, y through shared memory (buffers free since the flux barrier), x in registers
+    T Yb[N][DIM];
+    if (DIM == 3) {
 #pragma unroll
-  for (int a0 = 0; a0 < N; ++a0)
+      for (int q = 0; q < N; ++q)
 #pragma unroll
-    for (int c = 0; c < DIM; ++c) {
-      if ((cms[a0] >> c) & 1u) continue;
-      T s = T(0);
+        for (int c = 0; c < DIM; ++c) buf1[cl][c][q + N * l] = Wq[q][c];
+      __syncthreads();
 #pragma unroll
-      for (int j = 0; j < N; ++j) s = fma(tS[j][a0], Yb[j][c], s);
-      atomicAdd(&a.y[(node0 + a0) * DIM + c], vec_out(s));
+      for (int q = 0; q < N; ++q)
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {  // z: (q1 = l1, a2 = l2)
+          T sz = T(0);
+#pragma unroll
+          for (int j = 0; j < N; ++j) sz = fma(tS[j][l2], buf1[cl][c][q + N * (l1 + N * j)], sz);
+          buf0[cl][c][q + N * l] = sz;
+        }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < N; ++q)
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {  // y: (a1 = l1, a2 = l2)
+          T sy = T(0);
+#pragma unroll
+          for (int j = 0; j < N; ++j) sy = fma(tS[j][l1], buf0[cl][c][q + N * (j + N * l2)], sy);
+          Yb[q][c] = sy;
+        }
+    } else {
+#pragma unroll
+      for (int q = 0; q < N; ++q)
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) buf0[cl][c][q + N * l] = Wq[q][c];
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < N; ++q)
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+          T sy = T(0);
+#pragma unroll
+          for (int j = 0; j < N; ++j) sy = fma(tS[j][l1], buf0[cl][c][q + N * j], sy);
+          Yb[q][c] = sy;
+        }
     }
+    if (active) {
+#pragma unroll
+      for (int a0 = 0; a0 < N; ++a0)
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+          if ((cms[a0] >> c) & 1u) continue;
+          T s = T(0);
+#pragma unroll
+          for (int j = 0; j < N; ++j) s = fma(tS[j][a0], Yb[j][c], s);
+          atomicAdd(&a.y[(node0 + a0) * DIM + c], vec_out(s));
+        }
+    }
+    if (PERSIST) __syncthreads();  // the next cell block reuses the buffers and refills this cache stage
+  }
 }
 
 // ---- kernels: one problem (arguments by value), or a work list of problems in one launch ----------
@@ -990,14 +1016,21 @@ apply_list_kernel(const CellArgs<T>* __restrict__ list, const int* __restrict__ 
 template <int DIM, int N, int VAR, typename T>
 __global__ void __launch_bounds__(layout_cells<T>(DIM, N) * ipow(N, DIM - 1))
 apply_line_kernel(const CellArgs<T> a) {
-  apply_line_body<DIM, N, VAR, T>(a, blockIdx.x);
+  apply_line_body<DIM, N, VAR, T>(a, blockIdx.x, 1);
+}
+
+// persistent: gridDim.x thread blocks loop over all cell blocks, two cache stages
+template <int DIM, int N, int VAR, typename T>
+__global__ void __launch_bounds__(layout_cells<T>(DIM, N) * ipow(N, DIM - 1))
+apply_line_persist_kernel(const CellArgs<T> a) {
+  apply_line_body<DIM, N, VAR, T, true>(a, blockIdx.x, gridDim.x);
 }
 
 template <int DIM, int N, int VAR, typename T>
 __global__ void __launch_bounds__(layout_cells<T>(DIM, N) * ipow(N, DIM - 1))
 apply_line_list_kernel(const CellArgs<T>* __restrict__ list, const int* __restrict__ start, int count) {
   const int p = work_item(start, count, blockIdx.x);
-  apply_line_body<DIM, N, VAR, T>(list[p], blockIdx.x - start[p]);
+  apply_line_body<DIM, N, VAR, T>(list[p], blockIdx.x - start[p], 1);
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -99,7 +99,10 @@ __host__ __device__ constexpr int layout_row(int dim, int n) {
   return (layout_cells<T>(dim, n) * ipow(n, dim) + 3) / 4 * 4;
 }
 
-enum KernelForm { FORM_POINT = 0, FORM_LINE = 1 };
+// Kernel forms of the tangent action: thread per (cell, Gauss point); thread per x-line of a cell; the line
+// form as a persistent grid with the cache double-buffered in shared memory (FP32 only: elsewhere it
+// runs as FORM_LINE).
+enum KernelForm { FORM_POINT = 0, FORM_LINE = 1, FORM_LINE_PERSIST = 2 };
 
 // Device-side error word bits.
 enum : unsigned { ERRBIT_JNEG = 1u, ERRBIT_NAN = 2u, ERRBIT_TIMEOUT = 4u, ERRBIT_NONSPD = 8u };

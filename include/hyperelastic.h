@@ -128,7 +128,9 @@ typedef struct {
   int coarse_solver;        /* [0] 0 = Chebyshev as a solver (Sec. 7); 1 = exact: the coarsest tangent
                                assembled densely and inverted (Gauss-Jordan) once per linearisation,
                                applied as one matrix-vector product (coarsest level <= 6000 dofs;
-                               degrees 1-3 in 3D, 1-4 in 2D) */
+                               degrees 1-3 in 3D, 1-4 in 2D); 2 = as 1 with the inversion in double-float
+                               arithmetic on the FP32 pipe (about 48 significant bits; the applied inverse
+                               and the matrix-vector product are FP64) */
   int kernel_form;          /* [-1] tangent-action kernel: 0 = one thread per (cell, Gauss point), 1 = one
                                thread per x-line of a cell, -1 = autotuned: the first linearisation of each
                                (dim, degree, variant, precision, mesh size) times both on the level's own

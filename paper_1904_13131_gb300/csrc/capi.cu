@@ -548,7 +548,7 @@ hy_status vcycle_typed(hy_ctx* ctx, int l) {
 hy_status vcycle_level(hy_ctx* ctx, int l) {
   if (l == 0) {
     Level& L = ctx->lev[0];
-    if (ctx->sp.coarse_solver == 1) {
+    if (ctx->sp.coarse_solver >= 1) {
       HY_CK(cudaMemsetAsync(L.w64[1], 0, sizeof(double) * L.ndofs, ctx->stream));
       if (L.nfree) launch_dense_gemv(L.d_Aresult, L.w64[0], L.w64[1], L.nfree, L.d_free_idx, ctx->stream);
       return check_launch(ctx, 1);
@@ -617,6 +617,39 @@ hy_status vcycle_top(hy_ctx* ctx, const double* r, double* z) {
   return HY_OK;
 }
 
+// Record the work `body` issues on ctx->stream into a CUDA graph (captured on the private capture stream),
+// then launch it once on ctx->stream, where stream order places it after the work queued before. Kernel
+// counts recorded during the capture stand for the launch.
+constexpr int EIG_GRAPH_MAX_ITERS = 64;
+template <typename F>
+hy_status run_captured(hy_ctx* ctx, F&& body) {
+  if (!ctx->cap_stream) HY_CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t saved = ctx->stream;
+  ctx->stream = ctx->cap_stream;
+  cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    ctx->stream = saved;
+    return fail(ctx, HY_ERR_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+  }
+  const hy_status st = body();
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(ctx->cap_stream, &g);
+  ctx->stream = saved;
+  if (st != HY_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    if (st != HY_OK) return st;
+    return fail(ctx, HY_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+  }
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(ctx, HY_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  e = cudaGraphLaunch(ex, ctx->stream);
+  cudaGraphExecDestroy(ex);  // destruction waits for nothing: the launched work completes on its own
+  if (e != cudaSuccess) return fail(ctx, HY_ERR_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
+  return HY_OK;
+}
+
 // Ritz extremes of D^{-1} A~ on level l from `iters` Jacobi-PCG iterations (Lanczos tridiagonal from
 // the CG coefficients), start vector from SplitMix64 with seed l, constrained entries zero (Sec. 7).
 template <typename T>
@@ -639,7 +672,7 @@ hy_status eig_estimate(hy_ctx* ctx, int l, int iters, double& lmin, double& lmax
   HY_CK(cudaMemcpyAsync(sc + 1, sc + 0, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));  // rz0
   HY_TRY(check_launch(ctx, 5));
   // CG iterations with every scalar on the device; the coefficient history comes back once at the end
-  for (int it = 0; it < iters; ++it) {
+  auto iteration = [&](int it) -> hy_status {
     HY_TRY(level_apply<T>(ctx, l, p, q));
     launch_dot<T>(p, q, L.ndofs, ctx->d_partials, sc + 2, ctx->stream);  // pq
     launch_eig_alpha(sc, hist, it, ctx->stream);
@@ -648,12 +681,24 @@ hy_status eig_estimate(hy_ctx* ctx, int l, int iters, double& lmin, double& lmax
     launch_dot<T>(r, z, L.ndofs, ctx->d_partials, sc + 3, ctx->stream);  // rzn
     launch_eig_beta(sc, hist, it, iters, ctx->stream);
     launch_xpay_dev<T>(z, sc + 5, p, p, L.ndofs, ctx->stream);           // p = z + beta p
-    HY_TRY(check_launch(ctx, 9));
-    if ((it & 31) == 31 && it + 1 < iters) {  // look at the stop flag now and then (one host sync)
-      double stopped = 0.0;
-      HY_CK(cudaMemcpyAsync(&stopped, sc + 6, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-      HY_CK(cudaStreamSynchronize(ctx->stream));
-      if (stopped != 0.0) break;
+    return check_launch(ctx, 9);
+  };
+  if (ctx->use_graphs && iters <= EIG_GRAPH_MAX_ITERS) {
+    // a short run (the smoother estimates) is captured whole and launched as one CUDA graph: once the
+    // device-side stop flag is set the remaining iterations change nothing
+    HY_TRY(run_captured(ctx, [&]() -> hy_status {
+      for (int it = 0; it < iters; ++it) HY_TRY(iteration(it));
+      return HY_OK;
+    }));
+  } else {
+    for (int it = 0; it < iters; ++it) {
+      HY_TRY(iteration(it));
+      if ((it & 31) == 31 && it + 1 < iters) {  // look at the stop flag now and then (one host sync)
+        double stopped = 0.0;
+        HY_CK(cudaMemcpyAsync(&stopped, sc + 6, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        HY_CK(cudaStreamSynchronize(ctx->stream));
+        if (stopped != 0.0) break;
+      }
     }
   }
   double hs[8];
@@ -780,8 +825,9 @@ hy_status coarse_direct_setup(hy_ctx* ctx) {
   launch_assemble_dense(ctx->dim, ctx->n, a, C.d_Ainv, n, C.d_cidx, ctx->stream);
   HY_TRY(check_launch(ctx, 1));
   HY_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
-  C.d_Aresult = launch_gj_invert(C.d_Ainv, C.d_Awork, n, C.d_inv_piv, ctx->d_err, ctx->stream);
-  HY_TRY(check_launch(ctx, (int)(3 * ((n + 31) / 32))));
+  const bool ff_arith = ctx->sp.coarse_solver == 2;
+  C.d_Aresult = launch_gj_invert(C.d_Ainv, C.d_Awork, n, C.d_inv_piv, ctx->d_err, ff_arith, ctx->stream);
+  HY_TRY(check_launch(ctx, (int)(3 * ((n + 31) / 32)) + (ff_arith ? 2 : 0)));
   unsigned h = 0;
   HY_CK(cudaMemcpyAsync(&h, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
   HY_CK(cudaStreamSynchronize(ctx->stream));
@@ -955,7 +1001,7 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
     const long long coarse_it = ctx->sp.coarse_eig_iters > 0 ? std::min<long long>(ctx->coarse_nfree, ctx->sp.coarse_eig_iters)
                                                               : ctx->coarse_nfree;
     const long long need = 2 * std::max<long long>({ctx->nlev > 1 ? (long long)ctx->sp.eig_iters : 0,
-                                                     ctx->sp.coarse_solver != 1 ? std::max<long long>(coarse_it, 1) : 0, 1});
+                                                     ctx->sp.coarse_solver < 1 ? std::max<long long>(coarse_it, 1) : 0, 1});
     if ((long long)ctx->eig_hist_len < need) {
       dfree(ctx, ctx->d_eig_hist);
       ctx->d_eig_hist = nullptr;
@@ -1029,7 +1075,7 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
     ctx->lev[l].lmax = lmax;
   }
   pt.mark("smoother eig");
-  if (ctx->sp.coarse_solver == 1) {
+  if (ctx->sp.coarse_solver >= 1) {
     HY_TRY(coarse_direct_setup(ctx));
   } else {
     const long long nfree = ctx->coarse_nfree;
@@ -1042,7 +1088,7 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
   }
   // The Chebyshev coarse solver needs an SPD coarsest level; an indefinite one (a tangent about an
   // unstable state) is reported when the V-cycle is used, not here, so that applications still work.
-  if (ctx->sp.coarse_solver != 1) {
+  if (ctx->sp.coarse_solver < 1) {
     ctx->coarse_spd = ctx->coarse_lo > 0.0;
     ctx->coarse_deg = 0;
     if (ctx->coarse_spd) {
@@ -1937,7 +1983,7 @@ hy_status hy_set_solver_params(hy_ctx* ctx, const hy_solver_params* p) {
   if (p->cheb_degree < 1 || p->cheb_sweeps < 1 || !(p->cheb_lo > 0) || !(p->cheb_hi > p->cheb_lo) ||
       p->kernel_form < -1 || p->kernel_form > 2 || (p->fine_dtype != HY_F64 && p->fine_dtype != HY_FF) ||
       p->eig_iters < 1 || p->coarse_eig_iters < 0 || !(p->coarse_reduction > 0 && p->coarse_reduction < 1) ||
-      p->coarse_solver < 0 || p->coarse_solver > 1)
+      p->coarse_solver < 0 || p->coarse_solver > 2)
     return fail(ctx, HY_ERR_ARG, "solver parameters out of range");
   ctx->sp = *p;
   ctx->state_ok = false;
@@ -2154,6 +2200,7 @@ hy_status hy_footprint(int dim, int degree, int m, int n_levels, hy_variant vari
                        int coarse_solver, hy_dtype fine_dtype, const uint32_t* face_masks, int64_t* bytes) {
   if (!bytes || (dim != 2 && dim != 3) || degree < 1 || degree > 4 || m < 1 || n_levels < 1) return HY_ERR_ARG;
   if (fine_dtype != HY_F64 && fine_dtype != HY_FF) return HY_ERR_ARG;
+  if (coarse_solver < 0 || coarse_solver > 2) return HY_ERR_ARG;
   if ((int)variant < 0 || (int)variant > 4) return HY_ERR_ARG;
   auto al = [](size_t n, size_t sz) { return std::max<size_t>(n, 1) * sz; };
   const int n = degree + 1;
@@ -2217,11 +2264,11 @@ hy_status hy_footprint(int dim, int degree, int m, int n_levels, hy_variant vari
       }
     }
   }
-  if (coarse_solver == 1) total += 2 * al(nf * nf, 8) + al(32 * 32 + 64 * nf, 8) + al(nf, 4) + al(nd[0], 4);
+  if (coarse_solver >= 1) total += 2 * al(nf * nf, 8) + al(32 * 32 + 64 * nf, 8) + al(nf, 4) + al(nd[0], 4);
   // eigenvalue-estimate history for the default solver parameters (30 smoother iterations, all free
   // coarse dofs for the Chebyshev coarse solver)
   total += al((size_t)(2 * std::max<long long>({n_levels > 1 ? 30LL : 0LL,
-                                                coarse_solver != 1 ? std::max<long long>((long long)nf, 1) : 0LL, 1LL})),
+                                                coarse_solver < 1 ? std::max<long long>((long long)nf, 1) : 0LL, 1LL})),
               8);
   *bytes = (int64_t)total;
   return HY_OK;

@@ -201,85 +201,94 @@ void launch_assemble_dense(int dim, int n, const CellArgs<double>& a, double* A,
 // For the pivot block K = [k0, k0 + b) of A (old) the pass writes B (new):
 //   B_KK = W = A_KK^{-1},  B_Kj = (W A_K:)_j = Y_j,  B_iK = -(A_iK W) = -X_i,  B_ij = A_ij - A_iK Y_j,
 // the block form of b consecutive single-pivot steps; every element of A is read and written once per b
-// pivots instead of once per pivot.
+// pivots instead of once per pivot. The element type E is double, or double-float (ff: the same passes on
+// the FP32 pipe, about 48 significant bits, the reciprocal of each pivot taken in FP64).
+namespace {
 constexpr int GJB = 32;
+
+__device__ __forceinline__ double gj_recip(double p) { return 1.0 / p; }
+__device__ __forceinline__ ff gj_recip(ff p) { return rcp_rn(p); }
+__device__ __forceinline__ bool gj_positive(double p) { return p > 0.0; }
+__device__ __forceinline__ bool gj_positive(ff p) { return p.hi > 0.f; }
 
 // W = A_KK^{-1} by single-pivot Gauss-Jordan on the b x b block in shared memory (one block); flags a
 // pivot <= 0.
-__global__ void gjb_diag(const double* __restrict__ A, int n, int k0, int b, double* __restrict__ W, unsigned* err) {
-  __shared__ double w[GJB][GJB + 1];
-  __shared__ double rk[GJB], ck[GJB];
+template <typename E>
+__global__ void gjb_diag(const E* __restrict__ A, int n, int k0, int b, E* __restrict__ W, unsigned* err) {
+  __shared__ E w[GJB][GJB + 1];
+  __shared__ E rk[GJB], ck[GJB];
   const int t = threadIdx.x;
   for (int idx = t; idx < b * b; idx += blockDim.x) w[idx / b][idx % b] = A[(long long)(k0 + idx / b) * n + k0 + idx % b];
   __syncthreads();
   for (int k = 0; k < b; ++k) {
-    const double p = w[k][k];
-    if (t == 0 && !(p > 0.0)) atomicOr(err, ERRBIT_NONSPD);
-    const double ip = 1.0 / p;
+    const E p = w[k][k];
+    if (t == 0 && !gj_positive(p)) atomicOr(err, ERRBIT_NONSPD);
+    const E ip = gj_recip(p);
     if (t < b) {
-      rk[t] = (t == k ? 1.0 : w[k][t]) * ip;
+      rk[t] = (t == k ? E(1) : w[k][t]) * ip;
       ck[t] = w[t][k];
     }
     __syncthreads();
     for (int idx = t; idx < b * b; idx += blockDim.x) {
       const int i = idx / b, j = idx % b;
-      w[i][j] = (i == k) ? rk[j] : (j == k ? 0.0 : w[i][j]) - ck[i] * rk[j];
+      w[i][j] = (i == k) ? rk[j] : (j == k ? E(0) : w[i][j]) - ck[i] * rk[j];
     }
     __syncthreads();
   }
   for (int idx = t; idx < b * b; idx += blockDim.x) W[idx] = w[idx / b][idx % b];
 }
 
-// Y = W A_K: (b x n) and X = A_:K W (n x b), one thread per column j (Y) and per row i (X).
-__global__ void gjb_panels(const double* __restrict__ A, int n, int k0, int b, const double* __restrict__ W,
-                           double* __restrict__ Y, double* __restrict__ X) {
-  __shared__ double w[GJB * GJB];
-  for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) w[idx] = W[idx];
+// Y = W A_K: (b x n) and X = A_:K W (n x b). Thread (r, jy) of a 32 x 8 block computes Y_rj and X_jr for
+// the column / row j = 8 blockIdx.x + jy; the block's 8 columns of A_K: and rows of A_:K are staged first.
+template <typename E>
+__global__ void __launch_bounds__(256) gjb_panels(const E* __restrict__ A, int n, int k0, int b,
+                                                  const E* __restrict__ W, E* __restrict__ Y, E* __restrict__ X) {
+  __shared__ E w[GJB][GJB + 1];
+  __shared__ E colv[8][GJB + 1], rowv[8][GJB + 1];
+  const int r = threadIdx.x, jy = threadIdx.y, t = jy * GJB + r;
+  for (int idx = t; idx < b * b; idx += 256) w[idx / b][idx % b] = W[idx];
+  const int j = blockIdx.x * 8 + jy;
+  const bool inb = j < n && r < b;
+  colv[jy][r] = inb ? A[(long long)(k0 + r) * n + j] : E(0);  // A_Kj
+  rowv[jy][r] = inb ? A[(long long)j * n + k0 + r] : E(0);    // A_jK
   __syncthreads();
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  double col[GJB], row[GJB];
+  if (!inb) return;
+  E y = E(0), x = E(0);
   for (int m = 0; m < b; ++m) {
-    col[m] = A[(long long)(k0 + m) * n + j];  // A_Kj
-    row[m] = A[(long long)j * n + k0 + m];    // A_jK
+    y = fma(w[r][m], colv[jy][m], y);
+    x = fma(rowv[jy][m], w[m][r], x);
   }
-  for (int r = 0; r < b; ++r) {
-    double y = 0.0, x = 0.0;
-    for (int m = 0; m < b; ++m) {
-      y = fma(w[r * b + m], col[m], y);
-      x = fma(row[m], w[m * b + r], x);
-    }
-    Y[(long long)r * n + j] = y;
-    X[(long long)j * b + r] = x;
-  }
+  Y[(long long)r * n + j] = y;
+  X[(long long)j * b + r] = x;
 }
 
 // B_ij = A_ij - sum_m A_im Y_mj (i, j outside K); rows K take Y (W on the diagonal block), columns K
 // take -X. 64 x 64 output tile per block, 4 x 4 per thread, the A_:K and Y panels staged in shared memory.
-__global__ void __launch_bounds__(256) gjb_update(const double* __restrict__ A, double* __restrict__ B, int n, int k0,
-                                                  int b, const double* __restrict__ W, const double* __restrict__ Y,
-                                                  const double* __restrict__ X) {
-  __shared__ double sA[64][GJB + 1];
-  __shared__ double sY[GJB][64 + 1];
+template <typename E>
+__global__ void __launch_bounds__(256) gjb_update(const E* __restrict__ A, E* __restrict__ B, int n, int k0, int b,
+                                                  const E* __restrict__ W, const E* __restrict__ Y,
+                                                  const E* __restrict__ X) {
+  __shared__ E sA[64][GJB + 1];
+  __shared__ E sY[GJB][64 + 1];
   const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
   const int t = threadIdx.x;
   for (int idx = t; idx < 64 * GJB; idx += 256) {
     const int r = idx / GJB, m = idx % GJB;
     const int i = i0 + r;
-    sA[r][m] = (i < n && m < b) ? A[(long long)i * n + k0 + m] : 0.0;
+    sA[r][m] = (i < n && m < b) ? A[(long long)i * n + k0 + m] : E(0);
     const int mm = idx / 64, c = idx % 64;
     const int j = j0 + c;
-    sY[mm][c] = (j < n && mm < b) ? Y[(long long)mm * n + j] : 0.0;
+    sY[mm][c] = (j < n && mm < b) ? Y[(long long)mm * n + j] : E(0);
   }
   __syncthreads();
   const int tr = (t / 16) * 4, tc = (t % 16) * 4;
-  double acc[4][4];
+  E acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[a][c] = 0.0;
+    for (int c = 0; c < 4; ++c) acc[a][c] = E(0);
   for (int m = 0; m < b; ++m) {
-    double av[4], yv[4];
+    E av[4], yv[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) av[a] = sA[tr + a][m];
 #pragma unroll
@@ -299,7 +308,7 @@ __global__ void __launch_bounds__(256) gjb_update(const double* __restrict__ A, 
       const int j = j0 + tc + c;
       if (j >= n) continue;
       const bool jK = j >= k0 && j < k0 + b;
-      double v;
+      E v;
       if (iK) v = jK ? W[(i - k0) * b + (j - k0)] : Y[(long long)(i - k0) * n + j];
       else v = jK ? -X[(long long)i * b + (j - k0)] : A[(long long)i * n + j] - acc[a][c];
       B[(long long)i * n + j] = v;
@@ -307,21 +316,47 @@ __global__ void __launch_bounds__(256) gjb_update(const double* __restrict__ A, 
   }
 }
 
-// Gauss-Jordan inverse of the SPD n x n matrix in A, ping-ponging with B; returns the buffer that holds
-// the inverse. work: GJB^2 + 2 n GJB doubles.
-double* launch_gj_invert(double* A, double* B, long long n, double* work, unsigned* err, cudaStream_t st) {
-  double* W = work;
-  double* Y = W + GJB * GJB;
-  double* X = Y + (size_t)GJB * n;
+template <typename E>
+E* gj_passes(E* A, E* B, long long n, E* work, unsigned* err, cudaStream_t st) {
+  E* W = work;
+  E* Y = W + GJB * GJB;
+  E* X = Y + (size_t)GJB * n;
   const dim3 grid((unsigned)((n + 63) / 64), (unsigned)((n + 63) / 64));
   for (long long k0 = 0; k0 < n; k0 += GJB) {
     const int b = (int)std::min<long long>(GJB, n - k0);
-    gjb_diag<<<1, 256, 0, st>>>(A, (int)n, (int)k0, b, W, err);
-    gjb_panels<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(A, (int)n, (int)k0, b, W, Y, X);
-    gjb_update<<<grid, 256, 0, st>>>(A, B, (int)n, (int)k0, b, W, Y, X);
+    gjb_diag<E><<<1, 256, 0, st>>>(A, (int)n, (int)k0, b, W, err);
+    gjb_panels<E><<<(unsigned)((n + 7) / 8), dim3(GJB, 8), 0, st>>>(A, (int)n, (int)k0, b, W, Y, X);
+    gjb_update<E><<<grid, 256, 0, st>>>(A, B, (int)n, (int)k0, b, W, Y, X);
     std::swap(A, B);
   }
   return A;
+}
+
+// in place: the n2 doubles of a become double-float pairs, or back
+__global__ void split_to_ff(double* a, long long n2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x)
+    reinterpret_cast<ff*>(a)[i] = ff_from(a[i]);
+}
+__global__ void join_from_ff(double* a, long long n2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x)
+    a[i] = vec_out(reinterpret_cast<const ff*>(a)[i]);
+}
+
+}  // namespace
+
+// Gauss-Jordan inverse of the SPD n x n matrix in A, ping-ponging with B; returns the buffer that holds
+// the inverse (FP64). work: GJB^2 + 2 n GJB doubles. ff: the passes run in double-float arithmetic on
+// the same buffers (8-byte elements), A converted on entry and the inverse converted back.
+double* launch_gj_invert(double* A, double* B, long long n, double* work, unsigned* err, bool ff_arith,
+                         cudaStream_t st) {
+  if (!ff_arith) return gj_passes<double>(A, B, n, work, err, st);
+  const long long n2 = n * n;
+  const int grid = (int)std::min<long long>((n2 + 255) / 256, 152LL * 16);
+  split_to_ff<<<grid, 256, 0, st>>>(A, n2);
+  ff* r = gj_passes<ff>(reinterpret_cast<ff*>(A), reinterpret_cast<ff*>(B), n, reinterpret_cast<ff*>(work), err, st);
+  double* out = reinterpret_cast<double*>(r);
+  join_from_ff<<<grid, 256, 0, st>>>(out, n2);
+  return out;
 }
 
 void launch_dense_gemv(const double* A, const double* b, double* x, long long n, const int* free_idx, cudaStream_t st) {

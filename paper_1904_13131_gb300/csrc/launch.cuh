@@ -141,7 +141,8 @@ void launch_assemble_dense(int dim, int n, const CellArgs<double>& a, double* A,
                            cudaStream_t st);
 // blocked Gauss-Jordan inverse, ping-ponging between A and B; returns the buffer holding the inverse;
 // flags a pivot <= 0 in err; work holds 32*32 + 64 n doubles
-double* launch_gj_invert(double* A, double* B, long long n, double* work, unsigned* err, cudaStream_t st);
+double* launch_gj_invert(double* A, double* B, long long n, double* work, unsigned* err, bool ff_arith,
+                         cudaStream_t st);
 // x[free_idx[i]] = sum_j A_ij b[free_idx[j]]
 void launch_dense_gemv(const double* A, const double* b, double* x, long long n, const int* free_idx, cudaStream_t st);
 

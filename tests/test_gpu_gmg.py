@@ -121,16 +121,18 @@ def test_indefinite_coarse_level_is_reported_by_the_vcycle(torch):
         assert e.value.status == "HY_ERR_NOCONV"
 
 
+@pytest.mark.parametrize("coarse", [1, 2])
 @pytest.mark.parametrize("dim,k,m,L", [(2, 2, 8, 3), (3, 2, 4, 2), (3, 1, 8, 3)])
-def test_exact_coarse_vcycle(torch, dim, k, m, L):
-    """Option: the coarsest level solved exactly (dense inverse) instead of by Chebyshev."""
+def test_exact_coarse_vcycle(torch, dim, k, m, L, coarse):
+    """Option: the coarsest level solved exactly (dense inverse; coarse = 2 inverts in double-float)
+    instead of by Chebyshev."""
     pr = problem(dim, k, m, n_levels=L)
     H = Hierarchy(pr["dim"], pr["k"], pr["levels_m"], pr["ids"], pr["mu"], pr["lam"], pr["masks"],
                   coarse_solver="direct")
     u = inputs.smooth_field(dim, k, m, seed=5, amplitude=0.02)
     b = inputs.gaussian_vector(inputs.n_dofs(dim, k, m), 8)
     with context(pr) as ctx:
-        ctx.set_solver_params(coarse_solver=1)
+        ctx.set_solver_params(coarse_solver=coarse)
         ctx.set_displacement(torch.tensor(u, device="cuda"), "T4")
         info = [ctx.level_info(l) for l in range(L)]
         H.set_displacement(u, lmax=[i["lmax"] for i in info])
@@ -140,7 +142,10 @@ def test_exact_coarse_vcycle(torch, dim, k, m, L):
     assert rel(z, H.vcycle(bb)) < 1e-10
 
 
-def test_exact_coarse_single_level_is_the_inverse(torch):
+@pytest.mark.parametrize("coarse,tol", [(1, 1e-11), (2, 1e-9)])
+def test_exact_coarse_single_level_is_the_inverse(torch, coarse, tol):
+    """The inverse applied on a one-level hierarchy is the sparse direct solve; the double-float inverse
+    carries about 48 significant bits times the condition number of the coarse tangent."""
     dim, k, m = 3, 2, 3
     pr = problem(dim, k, m, n_levels=1)
     H = hierarchy(pr)
@@ -150,9 +155,9 @@ def test_exact_coarse_single_level_is_the_inverse(torch):
     b = inputs.gaussian_vector(A.shape[0], 3)
     b[H.levels[0].constrained] = 0.0
     with context(pr) as ctx:
-        ctx.set_solver_params(coarse_solver=1)
+        ctx.set_solver_params(coarse_solver=coarse)
         ctx.set_displacement(torch.tensor(u, device="cuda"), "T4")
         z = ctx.gmg_vcycle(torch.tensor(b, device="cuda")).cpu().numpy()
         x, its = ctx.pcg(torch.tensor(b, device="cuda"), rtol=1e-12)
-    assert rel(z, spla.spsolve(A.tocsc(), b)) < 1e-11
-    assert its <= 2
+    assert rel(z, spla.spsolve(A.tocsc(), b)) < tol
+    assert its <= 2 if coarse == 1 else its <= 4

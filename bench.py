@@ -229,8 +229,9 @@ def serve_bench(api, inputs, dev, n_req, seed=0, max_active=8, budget_gb=160):
     """Serving (continuous batching): a seeded stream of uneven solve requests (2D 32^2-256^2 and 3D 8^3-48^3,
     Q1-Q3, stiffness ratio 2-100, radius 0.1-0.35, compression 2-15 %, 5 load steps). Baseline: the same
     requests solved one at a time with plain FP64 (FP64 V-cycle, Chebyshev coarse solve). Served: up to
-    `max_active` resident solves, mixed-precision V-cycle, exact coarse solve; closed loop (all at t=0) for
-    peak solves/s, and Poisson arrivals at twice the baseline rate for p50/p99 latency."""
+    `max_active` resident solves, mixed-precision V-cycle, exact coarse solve with the double-float inverse,
+    double-float finest-level action and diagonals for degrees 1-2; closed loop (all at t=0) for peak
+    solves/s, and Poisson arrivals at twice the baseline rate for p50/p99 latency."""
     reqs = inputs.serving_requests(n_req, seed)
 
     def problem(q):
@@ -242,8 +243,12 @@ def serve_bench(api, inputs, dev, n_req, seed=0, max_active=8, budget_gb=160):
         fv[2 * (q["dim"] - 1) + 1][q["dim"] - 1] = -q["compression"]
         return api.Context.newton_params(face_values=fv, level_dtype=ldt)
 
-    def run(max_act, ldt, coarse, arrivals=None):
-        sp = api.SolverParams(4, 1, 0.6, 1.2, 30, 0, 1e-3, coarse, -1, 0)
+    def solver(q, coarse, ff):
+        # ff: double-float coarse inverse, and double-float finest-level action where built (degrees 1-2)
+        fine = api.FF if ff and q["k"] <= 2 else api.F64
+        return api.SolverParams(4, 1, 0.6, 1.2, 30, 0, 1e-3, 2 if (ff and coarse) else coarse, -1, fine)
+
+    def run(max_act, ldt, coarse, arrivals=None, ff=False):
         out = {}
         with api.Server(dev.index, budget_bytes=budget_gb << 30, max_active=max_act) as sv:
             t0 = time.perf_counter()
@@ -253,7 +258,7 @@ def serve_bench(api, inputs, dev, n_req, seed=0, max_active=8, budget_gb=160):
                     delay = arrivals[q["id"]] - (time.perf_counter() - t0)
                     if delay > 0:
                         time.sleep(delay)
-                tickets.append(sv.submit(problem(q), params(q, ldt), sp))
+                tickets.append(sv.submit(problem(q), params(q, ldt), solver(q, coarse, ff)))
             for t in tickets:
                 sv.wait(t, 3600.0)
             makespan = time.perf_counter() - t0
@@ -273,8 +278,8 @@ def serve_bench(api, inputs, dev, n_req, seed=0, max_active=8, budget_gb=160):
     for q in reqs:
         t += float(rng.exponential(1.0 / rate))
         arr[q["id"]] = t
-    peak, u_peak = run(max_active, 1, 1)
-    poisson, u_srv = run(max_active, 1, 1, arrivals=arr)
+    peak, u_peak = run(max_active, 1, 1, ff=True)
+    poisson, u_srv = run(max_active, 1, 1, arrivals=arr, ff=True)
     err = max(float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(u_srv, u_seq) if a is not None and b is not None)
     return {"requests": n_req, "seed": seed, "sequential_fp64": seq, "served_closed_loop": peak,
             "served_poisson": dict(poisson, arrival_rate_per_s=rate),

@@ -140,7 +140,8 @@ typedef struct {
   hy_dtype fine_dtype;      /* [HY_F64] tangent action of the finest level inside the solver (outer CG, and the
                                finest level of an FP64 V-cycle): HY_F64, or HY_FF to build a double-float
                                cache of the finest level at hy_set_displacement and use it there (degrees
-                               1-2; HY_ERR_UNSUPPORTED from hy_set_displacement otherwise) */
+                               1-2; HY_ERR_UNSUPPORTED from hy_set_displacement otherwise); HY_FF also sums
+                               the level diagonals' (node, Gauss point) pairs in double-float */
 } hy_solver_params;
 
 hy_status hy_set_solver_params(hy_ctx *ctx, const hy_solver_params *p);

@@ -1043,7 +1043,7 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
     CellArgs<double> a = cell_args<double>(ctx, L);
     a.u64 = L.d_u64;
     a.y = L.d_diag;
-    CellFn<double> dfn = diag_fn(ctx->dim, ctx->n);
+    CellFn<double> dfn = diag_fn(ctx->dim, ctx->n, ctx->sp.fine_dtype == HY_FF);
     dfn(a, ctx->stream);
     launch_set_constrained_one<double>(L.d_diag, L.nnodes, ctx->dim, L.g, ctx->stream);
     HY_TRY(check_launch(ctx, 2));

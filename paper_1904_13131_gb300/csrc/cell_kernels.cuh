@@ -1171,20 +1171,29 @@ residual_kernel(const CellArgs<double> a) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// Diagonal of the tangent, d += diag A(u), FP64. For node a and component c:
+// Diagonal of the tangent, d += diag A(u). For node a and component c:
 //   A_{ac,ac} = sum_q W [ g_a . tau . g_a + c1 (|g_a|^2 + g_{a,c}^2)/2 + c2 g_{a,c}^2 ],  g_a = F^{-T} Grad N_a,
 // the geometric and material parts of Eq. algebraic_tangent with the action of Eq. simplified_action.
-template <int DIM, int N>
+// The Gauss-point state is FP64; the O((k+1)^(2 dim)) sum over (node, point) pairs runs in E: double, or
+// double-float (the FP32 pipe, about 48 significant bits).
+template <int DIM, int N, typename E>
 __global__ void __launch_bounds__(cells_per_block(DIM, N) * ipow(N, DIM))
 diag_kernel(const CellArgs<double> a) {
   constexpr int NPT = ipow(N, DIM);
   constexpr int CB = cells_per_block(DIM, N);
   constexpr int NS = nsym(DIM);
   __shared__ Smem<DIM, N, double> s;
-  __shared__ double Sd[MAXN][MAXN];
-  __shared__ double st[CB][NS + 2][NPT];
+  __shared__ E Sd[MAXN][MAXN];
+  __shared__ E st[CB][NS + 2][NPT];
+  static_assert(sizeof(E) == sizeof(double), "E values reuse double buffers");
   load_tables<DIM, N>(s, a);
-  if (threadIdx.x < MAXN * MAXN) Sd[threadIdx.x / MAXN][threadIdx.x % MAXN] = a.b.Sd[threadIdx.x / MAXN][threadIdx.x % MAXN];
+  // S in E in the (here unused) Dh table
+  E(*Se)[MAXN] = reinterpret_cast<E(*)[MAXN]>(&s.Dh[0][0]);
+  __syncthreads();
+  if (threadIdx.x < MAXN * MAXN) {
+    Sd[threadIdx.x / MAXN][threadIdx.x % MAXN] = E(a.b.Sd[threadIdx.x / MAXN][threadIdx.x % MAXN]);
+    Se[threadIdx.x / MAXN][threadIdx.x % MAXN] = E(a.b.S[threadIdx.x / MAXN][threadIdx.x % MAXN]);
+  }
   const int cl = threadIdx.x / NPT;
   const Pt<DIM, N> pt(threadIdx.x % NPT);
   const int cell = blockIdx.x * CB + cl;
@@ -1208,53 +1217,55 @@ diag_kernel(const CellArgs<double> a) {
   const int id = active ? a.mat[cell] : 0;
   double M[DIM][DIM], tau[NS], c1, c2;
   neo_hooke_state<DIM>(F, s.mu[id], s.lam[id], s.W[pt.p], inv_h, false, 0.0, M, tau, c1, c2);
-  // per-point state to shared memory: M in bp (DIM^2 rows), tau, c1, c2 in st (NS + 2 rows)
+  // per-point state to shared memory in E: M (DIM^2 rows, in the flux buffer), tau, c1, c2 (NS + 2 rows)
+  E(*Me)[DIM * DIM][NPT] = reinterpret_cast<E(*)[DIM * DIM][NPT]>(&s.bp[0][0][0]);
 #pragma unroll
-  for (int i = 0; i < DIM * DIM; ++i) bp[i * NPT + pt.p] = M[i / DIM][i % DIM];
+  for (int i = 0; i < DIM * DIM; ++i) Me[cl][i][pt.p] = E(M[i / DIM][i % DIM]);
 #pragma unroll
-  for (int i = 0; i < NS; ++i) st[cl][i][pt.p] = tau[i];
-  st[cl][NS][pt.p] = c1;
-  st[cl][NS + 1][pt.p] = c2;
+  for (int i = 0; i < NS; ++i) st[cl][i][pt.p] = E(tau[i]);
+  st[cl][NS][pt.p] = E(c1);
+  st[cl][NS + 1][pt.p] = E(c2);
   __syncthreads();
   // thread now plays node a = pt.p
-  double dsum[DIM];
+  E dsum[DIM];
 #pragma unroll
-  for (int c = 0; c < DIM; ++c) dsum[c] = 0.0;
+  for (int c = 0; c < DIM; ++c) dsum[c] = E(0);
   for (int q = 0; q < NPT; ++q) {
     const int q0 = q % N, q1 = (q / N) % N, q2 = DIM == 3 ? q / (N * N) : 0;
-    double gr[DIM];  // d N_a / d xi at q
-    const double s0 = s.S[q0][pt.pc[0]], s1 = s.S[q1][pt.pc[1]];
-    const double s2 = DIM == 3 ? s.S[q2][pt.pc[2]] : 1.0;
+    E gr[DIM];  // d N_a / d xi at q
+    const E s0 = Se[q0][pt.pc[0]], s1 = Se[q1][pt.pc[1]];
+    const E s2 = DIM == 3 ? Se[q2][pt.pc[2]] : E(1);
     gr[0] = Sd[q0][pt.pc[0]] * s1 * s2;
     gr[1] = s0 * Sd[q1][pt.pc[1]] * s2;
     if (DIM == 3) gr[DIM - 1] = s0 * s1 * Sd[q2][pt.pc[2]];
-    double ga[DIM];
+    E ga[DIM];
 #pragma unroll
     for (int j = 0; j < DIM; ++j) {
-      double acc = gr[0] * bp[(0 * DIM + j) * NPT + q];
+      E acc = gr[0] * Me[cl][0 * DIM + j][q];
 #pragma unroll
-      for (int J = 1; J < DIM; ++J) acc = fma(gr[J], bp[(J * DIM + j) * NPT + q], acc);
+      for (int J = 1; J < DIM; ++J) acc = fma(gr[J], Me[cl][J * DIM + j][q], acc);
       ga[j] = acc;
     }
-    double tq[NS];
-#pragma unroll
-    for (int i = 0; i < NS; ++i) tq[i] = st[cl][i][q];
-    double geo = 0.0, nrm = 0.0;
+    E geo = E(0), nrm = E(0);
 #pragma unroll
     for (int al = 0; al < NS; ++al) {
       const int i = vi<DIM>(al), j = vj<DIM>(al);
-      geo = fma((i == j ? 1.0 : 2.0) * ga[i] * ga[j], tq[al], geo);
+      const E gij = ga[i] * ga[j];
+      geo = fma(i == j ? gij : gij + gij, st[cl][al][q], geo);
     }
 #pragma unroll
     for (int j = 0; j < DIM; ++j) nrm = fma(ga[j], ga[j], nrm);
-    const double qc1 = st[cl][NS][q], qc2 = st[cl][NS + 1][q];
+    const E hc1 = E(0.5) * st[cl][NS][q], qc2 = st[cl][NS + 1][q];
 #pragma unroll
-    for (int c = 0; c < DIM; ++c) dsum[c] += geo + 0.5 * qc1 * (nrm + ga[c] * ga[c]) + qc2 * ga[c] * ga[c];
+    for (int c = 0; c < DIM; ++c) {
+      const E gc2 = ga[c] * ga[c];
+      dsum[c] = dsum[c] + (geo + fma(hc1, nrm + gc2, qc2 * gc2));
+    }
   }
   if (active) {
 #pragma unroll
     for (int c = 0; c < DIM; ++c)
-      if (!((loc.cmask >> c) & 1u)) atomicAdd(&a.y[(long long)loc.node * DIM + c], dsum[c]);
+      if (!((loc.cmask >> c) & 1u)) atomicAdd(&a.y[(long long)loc.node * DIM + c], vec_out(dsum[c]));
   }
 }
 

@@ -18,12 +18,12 @@ void launch_residual(const CellArgs<double>& a, cudaStream_t st) {
   const int grid = (a.g.ncells + CB - 1) / CB;
   residual_kernel<DIM, N><<<grid, CB * NPT, 0, st>>>(a);
 }
-template <int DIM, int N>
+template <int DIM, int N, typename E>
 void launch_diag(const CellArgs<double>& a, cudaStream_t st) {
   constexpr int CB = cells_per_block(DIM, N);
   constexpr int NPT = ipow(N, DIM);
   const int grid = (a.g.ncells + CB - 1) / CB;
-  diag_kernel<DIM, N><<<grid, CB * NPT, 0, st>>>(a);
+  diag_kernel<DIM, N, E><<<grid, CB * NPT, 0, st>>>(a);
 }
 }  // namespace
 
@@ -63,10 +63,13 @@ CellFn<double> residual_fn(int dim, int n) {
   if (n < 2 || n > 5 || dim < 2 || dim > 3) return nullptr;
   return t[dim - 2][n - 2];
 }
-CellFn<double> diag_fn(int dim, int n) {
-  static const CellFn<double> t[2][4] = {{launch_diag<2, 2>, launch_diag<2, 3>, launch_diag<2, 4>, launch_diag<2, 5>},
-                                         {launch_diag<3, 2>, launch_diag<3, 3>, launch_diag<3, 4>, launch_diag<3, 5>}};
+CellFn<double> diag_fn(int dim, int n, bool ff_arith) {
+  static const CellFn<double> t[2][2][4] = {
+      {{launch_diag<2, 2, double>, launch_diag<2, 3, double>, launch_diag<2, 4, double>, launch_diag<2, 5, double>},
+       {launch_diag<3, 2, double>, launch_diag<3, 3, double>, launch_diag<3, 4, double>, launch_diag<3, 5, double>}},
+      {{launch_diag<2, 2, ff>, launch_diag<2, 3, ff>, launch_diag<2, 4, ff>, launch_diag<2, 5, ff>},
+       {launch_diag<3, 2, ff>, launch_diag<3, 3, ff>, launch_diag<3, 4, ff>, launch_diag<3, 5, ff>}}};
   if (n < 2 || n > 5 || dim < 2 || dim > 3) return nullptr;
-  return t[dim - 2][n - 2];
+  return t[ff_arith ? 1 : 0][dim - 2][n - 2];
 }
 }  // namespace hy

@@ -82,7 +82,8 @@ StateFn<double> state_fn_f64(int dim, int n, int var);   // var VAR_NONE: J chec
 StateFn<float> state_fn_f32(int dim, int n, int var);
 StateFn<ff> state_fn_ff(int dim, int n, int var);
 CellFn<double> residual_fn(int dim, int n);
-CellFn<double> diag_fn(int dim, int n);
+// diagonal: the sum over (node, Gauss point) pairs in FP64, or in double-float (ff_arith)
+CellFn<double> diag_fn(int dim, int n, bool ff_arith);
 
 constexpr int VAR_NONE = 5;
 

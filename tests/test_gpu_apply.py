@@ -101,8 +101,11 @@ def test_autotuned_form_is_recorded_and_reused(torch):
     assert forms[0] == forms[1]
 
 
-@pytest.mark.parametrize("dim,k,m", [(2, 2, 7), (3, 2, 3), (3, 3, 2), (2, 4, 3)])
+@pytest.mark.parametrize("dim,k,m", [(2, 2, 7), (3, 2, 3), (3, 3, 2), (2, 4, 3), (3, 4, 2)])
 def test_residual_and_diagonal(torch, dim, k, m):
+    """Residual in FP64; the diagonal's (node, point) pair sums in FP64 and, with fine_dtype = FF, in
+    double-float (degrees 1-2 build the double-float action too; the diagonal has both for every degree)."""
+    from paper_1904_13131_gb300.api import FF
     pr = problem(dim, k, m)
     P = oracle_level(pr)
     u = inputs.smooth_field(dim, k, m, seed=3)
@@ -111,6 +114,11 @@ def test_residual_and_diagonal(torch, dim, k, m):
         r = ctx.residual(ud).cpu().numpy()
         ctx.set_displacement(ud, "T4")
         d = ctx.diagonal().cpu().numpy()
+        if k <= 2:
+            ctx.set_solver_params(fine_dtype=FF)
+            ctx.set_displacement(ud, "T4")
+            dff = ctx.diagonal().cpu().numpy()
+            assert rel(dff, P.diagonal(u)) < 1e-12
     assert rel(r, P.residual(u)) < 1e-12
     assert rel(d, P.diagonal(u)) < 1e-12
 

@@ -201,9 +201,11 @@ def solve_latency(torch, api, inputs, dev):
     out, sols = {}, {}
     with api.Context(dev.index) as c:
         c.setup_problem(pr)
-        for name, ldt, coarse, fine in (("fp64", 0, 0, 0), ("mixed", 1, 0, 0), ("mixed_exact_coarse", 1, 1, 0),
-                                        ("mixed_exact_coarse_ff", 1, 2, 2)):
-            c.set_solver_params(coarse_solver=coarse, fine_dtype=fine)
+        for name, ldt, coarse, fine, lvar in (("fp64", 0, 0, 0, -1), ("mixed", 1, 0, 0, -1),
+                                              ("mixed_exact_coarse", 1, 1, 0, -1),
+                                              ("mixed_exact_coarse_ff", 1, 2, 2, -1),
+                                              ("mixed_exact_coarse_ff_t2_levels", 1, 2, 2, api.VARIANTS["T2"])):
+            c.set_solver_params(coarse_solver=coarse, fine_dtype=fine, level_variant=lvar)
             u = torch.zeros(inputs.n_dofs(DIM, K, M), dtype=torch.float64, device=dev)
             rep = c.newton_solve(u, api.Context.newton_params(level_dtype=ldt, face_values=fv))
             lat = np.array(rep["solve_ms"])
@@ -218,9 +220,11 @@ def solve_latency(torch, api, inputs, dev):
                                                np.linalg.norm(sols["fp64"]))
     out["ff_vs_fp64_rel_l2"] = float(np.linalg.norm(sols["mixed_exact_coarse_ff"] - sols["fp64"]) /
                                      np.linalg.norm(sols["fp64"]))
+    out["ff_t2_levels_vs_fp64_rel_l2"] = float(np.linalg.norm(sols["mixed_exact_coarse_ff_t2_levels"] - sols["fp64"]) /
+                                               np.linalg.norm(sols["fp64"]))
     out["coarse_solvers"] = ("fp64/mixed: Chebyshev to 1e-3 on 4^3 (Sec. 7); mixed_exact_coarse: dense inverse; "
                              "_ff: coarse inverse computed in double-float and double-float finest-level action "
-                             "in the outer CG")
+                             "in the outer CG; _t2_levels: the V-cycle's level operators in the T2 variant")
     out["workload"] = "32^3 Q2 (823,875 dofs), 10% compression in 5 load steps, 4 levels, CG rtol 1e-8, T4"
     return out
 
@@ -246,7 +250,8 @@ def serve_bench(api, inputs, dev, n_req, seed=0, max_active=8, budget_gb=160):
     def solver(q, coarse, ff):
         # ff: double-float coarse inverse, and double-float finest-level action where built (degrees 1-2)
         fine = api.FF if ff and q["k"] <= 2 else api.F64
-        return api.SolverParams(4, 1, 0.6, 1.2, 30, 0, 1e-3, 2 if (ff and coarse) else coarse, -1, fine)
+        return api.SolverParams(4, 1, 0.6, 1.2, 30, 0, 1e-3, 2 if (ff and coarse) else coarse, -1, fine,
+                               api.VARIANTS["T2"] if ff else -1)
 
     def run(max_act, ldt, coarse, arrivals=None, ff=False):
         out = {}

@@ -142,6 +142,11 @@ typedef struct {
                                cache of the finest level at hy_set_displacement and use it there (degrees
                                1-2; HY_ERR_UNSUPPORTED from hy_set_displacement otherwise); HY_FF also sums
                                the level diagonals' (node, Gauss point) pairs in double-float */
+  int level_variant;        /* [-1] tangent variant of the V-cycle's level operators (every level below the
+                               finest, and the finest level's FP32 cache): -1 = the variant given to
+                               hy_set_displacement, else a hy_variant. The variants are implementations of
+                               one operator (Sec. 5): a cheaper one speeds up the smoother without changing
+                               the preconditioner beyond rounding. */
 } hy_solver_params;
 
 hy_status hy_set_solver_params(hy_ctx *ctx, const hy_solver_params *p);
@@ -223,12 +228,11 @@ hy_status hy_dot_noalloc(int device, void *cuda_stream, const double *a_dev, con
                          double *result);
 
 /* Device bytes a context will own for this problem after mesh setup and set_displacement (the
- * admission measure of the solve server); pure host arithmetic, no GPU needed. coarse_solver and
- * fine_dtype as in hy_solver_params. face_masks[2*dim] (may be NULL: then an upper bound) fixes the free
- * dofs of an exact coarse solve. */
+ * admission measure of the solve server); pure host arithmetic, no GPU needed. sp: the solver parameters
+ * the context will use (NULL: the defaults). face_masks[2*dim] (may be NULL: then an upper bound) fixes the
+ * free dofs of an exact coarse solve. */
 hy_status hy_footprint(int dim, int degree, int cells_per_dir, int n_levels, hy_variant variant,
-                       hy_dtype level_dtype, int coarse_solver, hy_dtype fine_dtype, const uint32_t *face_masks,
-                       int64_t *bytes);
+                       hy_dtype level_dtype, const hy_solver_params *sp, const uint32_t *face_masks, int64_t *bytes);
 
 /* Device bytes currently owned by the context (its hierarchy, caches and work vectors). */
 hy_status hy_ctx_bytes(const hy_ctx *ctx, int64_t *bytes);

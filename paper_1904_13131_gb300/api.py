@@ -41,7 +41,7 @@ class SolverParams(ctypes.Structure):
     _fields_ = [("cheb_degree", ctypes.c_int), ("cheb_sweeps", ctypes.c_int), ("cheb_lo", ctypes.c_double),
                 ("cheb_hi", ctypes.c_double), ("eig_iters", ctypes.c_int), ("coarse_eig_iters", ctypes.c_int),
                 ("coarse_reduction", ctypes.c_double), ("coarse_solver", ctypes.c_int), ("kernel_form", ctypes.c_int),
-                ("fine_dtype", ctypes.c_int)]
+                ("fine_dtype", ctypes.c_int), ("level_variant", ctypes.c_int)]
 
 
 class NewtonParams(ctypes.Structure):
@@ -111,7 +111,7 @@ def load_library(path: str = LIB_PATH):
         "hy_dot": [vp, vp, vp, i64, ctypes.POINTER(dbl)],
         "hy_kernel_launches": [vp, ctypes.POINTER(i64)],
         "hy_dot_noalloc": [i32, vp, vp, vp, i64, ctypes.POINTER(dbl)],
-        "hy_footprint": [i32, i32, i32, i32, i32, i32, i32, i32, ctypes.POINTER(ctypes.c_uint32),
+        "hy_footprint": [i32, i32, i32, i32, i32, i32, ctypes.POINTER(SolverParams), ctypes.POINTER(ctypes.c_uint32),
                          ctypes.POINTER(i64)],
         "hy_kernel_form": [vp, i32, i32, ctypes.POINTER(i32)],
         "hy_ctx_bytes": [vp, ctypes.POINTER(i64)],
@@ -266,6 +266,8 @@ class Context:
     def set_solver_params(self, **kw):
         p = self.get_solver_params()
         for k, v in kw.items():
+            if k == "level_variant" and isinstance(v, str):
+                v = VARIANTS[v]
             setattr(p, k, v)
         self._ck(self.lib.hy_set_solver_params(self.h, ctypes.byref(p)))
 
@@ -379,12 +381,14 @@ def dot_noalloc(a, b, device: int = 0, stream=None) -> float:
 
 
 def footprint(dim, degree, cells_per_dir, n_levels, variant="T4", level_dtype=F64, coarse_solver=0,
-              face_masks=None, fine_dtype=None) -> int:
+              face_masks=None, fine_dtype=None, level_variant=None) -> int:
     """Device bytes a context needs for this problem (host arithmetic, no GPU)."""
     b = ctypes.c_int64()
     fm = None if face_masks is None else (ctypes.c_uint32 * 6)(*[int(x) for x in list(face_masks) + [0] * 6][:6])
-    st = load_library().hy_footprint(dim, degree, cells_per_dir, n_levels, VARIANTS[variant], level_dtype, coarse_solver,
-                                     F64 if fine_dtype is None else fine_dtype, fm, ctypes.byref(b))
+    lv = -1 if level_variant is None else (VARIANTS[level_variant] if isinstance(level_variant, str) else level_variant)
+    sp = SolverParams(4, 1, 0.6, 1.2, 30, 0, 1e-3, coarse_solver, -1, F64 if fine_dtype is None else fine_dtype, lv)
+    st = load_library().hy_footprint(dim, degree, cells_per_dir, n_levels, VARIANTS[variant], level_dtype,
+                                     ctypes.byref(sp), fm, ctypes.byref(b))
     if st != 0:
         raise HyError(st, "hy_footprint")
     return b.value
@@ -490,7 +494,7 @@ class Server:
     def submit(self, problem: dict, newton: NewtonParams, solver: SolverParams | None = None) -> int:
         """problem: an inputs.problem(...) bundle (ids of every level, coarsest first)."""
         if solver is None:
-            solver = SolverParams(4, 1, 0.6, 1.2, 30, 0, 1e-3, 0, -1, 0)
+            solver = SolverParams(4, 1, 0.6, 1.2, 30, 0, 1e-3, 0, -1, 0, -1)
         ids = np.ascontiguousarray(np.concatenate([np.asarray(i, dtype=np.uint8) for i in problem["ids"]]))
         mu = np.ascontiguousarray(problem["mu"], dtype=np.float64)
         lam = np.ascontiguousarray(problem["lam"], dtype=np.float64)

@@ -165,6 +165,7 @@ struct Level {
   size_t cff_len = 0;
   bool hasff = false;
   int form[3] = {-1, -1, -1};  // tangent-action kernel form per precision (FP64, FP32, double-float)
+  int var[3] = {-1, -1, -1};   // tangent variant of the cache of each precision
   double* w64[5] = {};  // V-cycle vectors b, x, r, d, t
   float* w32[5] = {};
   double* d_Ainv = nullptr;  // exact coarse solve: dense free-dof tangent / its inverse (ping-pong pair)
@@ -194,7 +195,7 @@ struct hy_ctx {
   Basis1D<double> b64{};
   Basis1D<float> b32{};
   Basis1D<ff> bff{};
-  hy_solver_params sp{4, 1, 0.6, 1.2, 30, 0, 1e-3, 0, -1, HY_F64};
+  hy_solver_params sp{4, 1, 0.6, 1.2, 30, 0, 1e-3, 0, -1, HY_F64, -1};
   int var = -1;
   bool mixed = false;
   bool state_ok = false;
@@ -381,7 +382,7 @@ hy_status vmult(hy_ctx* ctx, int l, const vec_t<T>* x, vec_t<T>* y, bool constra
     cudaMemsetAsync(y, 0, sizeof(V) * L.ndofs, ctx->stream);
     a.g.fm[0] = a.g.fm[1] = a.g.fm[2] = a.g.fm[3] = a.g.fm[4] = a.g.fm[5] = 0;
   }
-  ApplyFn<T> fn = apply_fn(ctx, (T*)nullptr, ctx->var);
+  ApplyFn<T> fn = apply_fn(ctx, (T*)nullptr, L.var[prec_index<T>()]);
   if (!fn) return fail(ctx, HY_ERR_UNSUPPORTED, "no kernel for this dim/degree/variant");
   const int form = L.form[prec_index<T>()];
   fn(a, form < 0 ? FORM_POINT : form, ctx->stream);
@@ -910,7 +911,7 @@ hy_status autotune_level(hy_ctx* ctx, int l) {
   }
   int bucket = 0;
   for (long long c = L.g.ncells; c > 1; c >>= 1) ++bucket;
-  const TuneKey key{ctx->dim, ctx->k, ctx->var, dt, bucket};
+  const TuneKey key{ctx->dim, ctx->k, L.var[dt], dt, bucket};
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     tune_load_locked();
@@ -962,7 +963,7 @@ hy_status autotune_level(hy_ctx* ctx, int l) {
   L.form[dt] = choice;
   if (ctx->verbose)
     std::fprintf(stderr, "[hy] autotune dim %d k %d var %d %s cells 2^%d: point %.3f ms, line %.3f ms, persistent %.3f ms -> %s\n",
-                 ctx->dim, ctx->k, ctx->var, kPrecNames[dt], bucket, best[0], best[1], nforms > 2 ? best[2] : 0.f,
+                 ctx->dim, ctx->k, L.var[dt], kPrecNames[dt], bucket, best[0], best[1], nforms > 2 ? best[2] : 0.f,
                  kFormNames[choice]);
   std::lock_guard<std::mutex> lock(g_tune_mu);
   if (g_tune.emplace(key, choice).second) tune_save_locked();
@@ -1023,16 +1024,22 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
     const bool need32 = mixed && (l > 0 || l == top);
     L.has64 = L.has32 = L.hasff = false;
     L.form[0] = L.form[1] = L.form[2] = -1;
+    // the finest level's FP64 and double-float caches serve the outer CG: the given variant; the V-cycle's
+    // level operators (every cache below the finest, and its FP32 cache) take the level variant
+    const int lvar = ctx->sp.level_variant >= 0 ? ctx->sp.level_variant : var;
+    L.var[0] = l == top ? var : lvar;
+    L.var[1] = lvar;
+    L.var[2] = var;
     if (need64) {
-      HY_TRY(build_cache<double>(ctx, l, var));
+      HY_TRY(build_cache<double>(ctx, l, L.var[0]));
       L.has64 = true;
     }
     if (l == top && ctx->sp.fine_dtype == HY_FF) {
-      HY_TRY(build_cache<ff>(ctx, l, var));
+      HY_TRY(build_cache<ff>(ctx, l, L.var[2]));
       L.hasff = true;
     }
     if (need32) {
-      HY_TRY(build_cache<float>(ctx, l, var));
+      HY_TRY(build_cache<float>(ctx, l, L.var[1]));
       if (!L.d_u32) HY_TRY(dalloc(ctx, &L.d_u32, L.ndofs));
       launch_convert<double, float>(L.d_u64, L.d_u32, L.ndofs, ctx->stream);
       HY_TRY(check_launch(ctx, 1));
@@ -1271,7 +1278,8 @@ hy_status upload_list(hy_batch* b, const std::vector<int>& idx, const std::vecto
 template <typename T>
 hy_status list_apply(hy_batch* b, const std::vector<int>& idx, const std::vector<const void*>& x,
                      const std::vector<const void*>& y, int form, cudaStream_t st) {
-  const int var = b->ctx[idx[0]]->var;
+  hy_ctx* c0 = b->ctx[idx[0]];
+  const int var = c0->lev[c0->nlev - 1].var[prec_index<T>()];
   ApplyListFn<T> fn = list_fn(b->dim, b->n, var, (T*)nullptr);
   if (!fn) return bfail(b, HY_ERR_UNSUPPORTED, "batch: no kernel for this dim/degree/variant");
   (void)x;
@@ -1448,7 +1456,10 @@ hy_status batch_check(hy_batch* b) {
     if (c->nlev == 0 || c->dim != b->dim || c->n != b->n)
       return bfail(b, HY_ERR_STATE, "batch: a context's mesh changed since the batch was created");
     if (!c->state_ok) return bfail(b, HY_ERR_STATE, "batch: set_displacement on every context first");
-    if (c->var != b->ctx[0]->var) return bfail(b, HY_ERR_ARG, "batch: the contexts must use the same variant");
+    const Level& L = c->lev[c->nlev - 1];
+    const Level& L0 = b->ctx[0]->lev[b->ctx[0]->nlev - 1];
+    if (L.var[0] != L0.var[0] || L.var[1] != L0.var[1] || L.var[2] != L0.var[2])
+      return bfail(b, HY_ERR_ARG, "batch: the contexts must use the same variants");
   }
   return HY_OK;
 }
@@ -1982,6 +1993,7 @@ hy_status hy_set_solver_params(hy_ctx* ctx, const hy_solver_params* p) {
   if (!ctx || !p) return HY_ERR_ARG;
   if (p->cheb_degree < 1 || p->cheb_sweeps < 1 || !(p->cheb_lo > 0) || !(p->cheb_hi > p->cheb_lo) ||
       p->kernel_form < -1 || p->kernel_form > 2 || (p->fine_dtype != HY_F64 && p->fine_dtype != HY_FF) ||
+      p->level_variant < -1 || p->level_variant > 4 ||
       p->eig_iters < 1 || p->coarse_eig_iters < 0 || !(p->coarse_reduction > 0 && p->coarse_reduction < 1) ||
       p->coarse_solver < 0 || p->coarse_solver > 2)
     return fail(ctx, HY_ERR_ARG, "solver parameters out of range");
@@ -2197,10 +2209,13 @@ hy_status hy_dot(hy_ctx* ctx, const double* a, const double* b, int64_t n, doubl
 // Device bytes a context needs for a problem, mirroring the allocations of hy_mesh_setup and
 // hy_set_displacement (requested sizes; the allocator's own rounding comes on top).
 hy_status hy_footprint(int dim, int degree, int m, int n_levels, hy_variant variant, hy_dtype level_dtype,
-                       int coarse_solver, hy_dtype fine_dtype, const uint32_t* face_masks, int64_t* bytes) {
+                       const hy_solver_params* sp, const uint32_t* face_masks, int64_t* bytes) {
   if (!bytes || (dim != 2 && dim != 3) || degree < 1 || degree > 4 || m < 1 || n_levels < 1) return HY_ERR_ARG;
+  const int coarse_solver = sp ? sp->coarse_solver : 0;
+  const hy_dtype fine_dtype = sp ? sp->fine_dtype : HY_F64;
+  const int level_variant = sp ? sp->level_variant : -1;
   if (fine_dtype != HY_F64 && fine_dtype != HY_FF) return HY_ERR_ARG;
-  if (coarse_solver < 0 || coarse_solver > 2) return HY_ERR_ARG;
+  if (coarse_solver < 0 || coarse_solver > 2 || level_variant < -1 || level_variant > 4) return HY_ERR_ARG;
   if ((int)variant < 0 || (int)variant > 4) return HY_ERR_ARG;
   auto al = [](size_t n, size_t sz) { return std::max<size_t>(n, 1) * sz; };
   const int n = degree + 1;
@@ -2236,12 +2251,14 @@ hy_status hy_footprint(int dim, int degree, int m, int n_levels, hy_variant vari
     const bool need64 = (l == top) || (l == 0) || !mixed;
     const bool need32 = mixed && (l > 0 || l == top);
     const int cb64 = layout_cells<double>(dim, n), cb32 = layout_cells<float>(dim, n);
-    const size_t clen64 = std::max<size_t>(1, (size_t)cache_values((int)variant, dim) * layout_row<double>(dim, n) *
+    const int lvar = level_variant >= 0 ? level_variant : (int)variant;  // as set_displacement assigns them
+    const int var64 = l == top ? (int)variant : lvar;
+    const size_t clen64 = std::max<size_t>(1, (size_t)cache_values(var64, dim) * layout_row<double>(dim, n) *
                                                   (size_t)((nc[l] + cb64 - 1) / cb64));
-    const size_t clen32 = std::max<size_t>(1, (size_t)cache_values((int)variant, dim) * layout_row<float>(dim, n) *
+    const size_t clen32 = std::max<size_t>(1, (size_t)cache_values(lvar, dim) * layout_row<float>(dim, n) *
                                                   (size_t)((nc[l] + cb32 - 1) / cb32));
     if (need64) total += al(clen64, 8) + al(nd[l], 8) + 5 * al(nd[l], 8);
-    if (l == top && fine_dtype == HY_FF) total += al(clen64, 8);  // double-float cache, the FP64 layout
+    if (l == top && fine_dtype == HY_FF) total += al(clen64, 8);  // double-float cache: the FP64 layout, variant
     if (need32) total += al(clen32, 4) + al(nd[l], 4) + al(nd[l], 4) + 5 * al(nd[l], 4);
   }
   // free dofs of the coarsest level (all dofs bound them when no masks are given)

@@ -195,8 +195,8 @@ hy_status hy_server_submit(hy_server* sv, const hy_request* q, uint64_t* ticket)
   r->np = q->newton;
   r->sp = q->solver;
   int64_t bytes = 0;
-  hy_status s = hy_footprint(r->dim, r->degree, r->m, r->nlev, q->newton.variant, q->newton.level_dtype,
-                             q->solver.coarse_solver, q->solver.fine_dtype, r->fm, &bytes);
+  hy_status s = hy_footprint(r->dim, r->degree, r->m, r->nlev, q->newton.variant, q->newton.level_dtype, &q->solver,
+                             r->fm, &bytes);
   if (s != HY_OK) return s;
   r->bytes = bytes + (int64_t)sizeof(double) * r->dim * (int64_t)std::pow(r->degree * r->m + 1.0, r->dim);  // + u
   if (r->bytes > sv->budget) return HY_ERR_OOM;  // could never be admitted

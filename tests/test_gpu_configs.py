@@ -63,10 +63,11 @@ def test_config3_degree_sweep_newton_matches_oracle(torch, k, m, L):
     from paper_1904_13131_gb300.api import Context
     runs = [(0, 0, 0), (1, 1 if k < 4 else 0, 0)]  # exact coarse solve: degrees 1-3 in 3D
     if k <= 2:
-        runs.append((1, 2, 2))  # double-float coarse inverse and finest-level action in the outer CG
+        # double-float coarse inverse and finest-level action in the outer CG, T2 level operators
+        runs.append((1, 2, 2))
     with context(pr) as ctx:
         for ldt, coarse, fine in runs:
-            ctx.set_solver_params(coarse_solver=coarse, fine_dtype=fine)
+            ctx.set_solver_params(coarse_solver=coarse, fine_dtype=fine, level_variant=1 if fine == 2 else -1)
             u = torch.zeros(ctx.num_dofs(), dtype=torch.float64, device="cuda")
             rep = ctx.newton_solve(u, Context.newton_params(level_dtype=ldt, face_values=face_values(dim, -0.1)))
             assert rep["load_steps_done"] == 5

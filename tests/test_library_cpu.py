@@ -64,5 +64,9 @@ def test_footprint_is_host_arithmetic(lib):
     # double-float finest-level cache: the FP64 layout again (T4, 36 values per Gauss point, 9 cells per block)
     blocks = -(-32**3 // 9)
     assert api.footprint(3, 2, 32, 4, fine_dtype=api.FF) - b64 == 8 * 36 * ((9 * 27 + 3) // 4 * 4) * blocks
+    # T2 level operators (17 values per Gauss point instead of 36) on the three levels below the finest
+    cells = [4**3, 8**3, 16**3]
+    saved = sum(8 * (36 - 17) * ((9 * 27 + 3) // 4 * 4) * -(-c // 9) for c in cells)
+    assert b64 - api.footprint(3, 2, 32, 4, level_variant="T2") == saved
     with pytest.raises(api.HyError):
         api.footprint(3, 5, 32, 4)

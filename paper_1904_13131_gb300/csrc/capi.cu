@@ -364,8 +364,9 @@ ApplyFn<ff> apply_fn(hy_ctx* ctx, ff*, int var) {
 
 // y = A~ x on level l in precision T (x zero on constrained dofs on read, y = x there). The vectors are
 // of type vec_t<T> (FP64 for the double-float action).
+// prepared: y already holds (constrained ? x : 0) (written by the kernel that produced x).
 template <typename T>
-hy_status vmult(hy_ctx* ctx, int l, const vec_t<T>* x, vec_t<T>* y, bool constrained_in = true) {
+hy_status vmult(hy_ctx* ctx, int l, const vec_t<T>* x, vec_t<T>* y, bool constrained_in = true, bool prepared = false) {
   using V = vec_t<T>;
   Level& L = ctx->lev[l];
   if (!has_cache<T>(L)) return fail(ctx, HY_ERR_STATE, "no Gauss-point cache of this precision on this level");
@@ -376,7 +377,7 @@ hy_status vmult(hy_ctx* ctx, int l, const vec_t<T>* x, vec_t<T>* y, bool constra
   a.ubar = ubar_of<T>(L);
   a.pf = ctx->prefetch;
   if (constrained_in) {
-    launch_prep_out<V>(x, y, L.nnodes, ctx->dim, L.g, ctx->stream);
+    if (!prepared) launch_prep_out<V>(x, y, L.nnodes, ctx->dim, L.g, ctx->stream);
   } else {
     // raw operator rows of the free dofs applied to x including its constrained entries
     cudaMemsetAsync(y, 0, sizeof(V) * L.ndofs, ctx->stream);
@@ -387,17 +388,18 @@ hy_status vmult(hy_ctx* ctx, int l, const vec_t<T>* x, vec_t<T>* y, bool constra
   const int form = L.form[prec_index<T>()];
   fn(a, form < 0 ? FORM_POINT : form, ctx->stream);
   if (!constrained_in) launch_zero_constrained<V>(y, L.nnodes, ctx->dim, L.g, ctx->stream);
-  return check_launch(ctx, 2);
+  return check_launch(ctx, prepared ? 1 : 2);
 }
 
 // The tangent action the solver uses on level l in the V-cycle precision T: on the finest level in FP64
 // the double-float action when the solver parameter fine_dtype asks for it.
 template <typename T>
-hy_status level_apply(hy_ctx* ctx, int l, const T* x, T* y) {
+hy_status level_apply(hy_ctx* ctx, int l, const T* x, T* y, bool prepared = false) {
   if constexpr (std::is_same<T, double>::value) {
-    if (l == ctx->nlev - 1 && ctx->sp.fine_dtype == HY_FF && ctx->lev[l].hasff) return vmult<ff>(ctx, l, x, y);
+    if (l == ctx->nlev - 1 && ctx->sp.fine_dtype == HY_FF && ctx->lev[l].hasff)
+      return vmult<ff>(ctx, l, x, y, true, prepared);
   }
-  return vmult<T>(ctx, l, x, y);
+  return vmult<T>(ctx, l, x, y, true, prepared);
 }
 
 template <typename T>
@@ -496,12 +498,15 @@ hy_status chebyshev(hy_ctx* ctx, int l, const T* b, T* x, bool x0_zero, int degr
   const double sigma = theta / delta;
   double rho = 1.0 / sigma;
   if (!x0_zero) HY_TRY(level_apply<T>(ctx, l, x, t));
-  launch_cheb_init<T>(b, t, dinv, r, dd, x, T(1.0 / theta), x0_zero, L.ndofs, ctx->stream);
+  // each update also prepares t for the next application of d (no separate prep_out launch)
+  launch_cheb_init<T>(b, t, dinv, r, dd, x, T(1.0 / theta), x0_zero, L.ndofs, degree > 1 ? &L.g : nullptr, ctx->dim,
+                      ctx->stream);
   HY_TRY(check_launch(ctx, 1));
   for (int j = 1; j < degree; ++j) {
-    HY_TRY(level_apply<T>(ctx, l, dd, t));
+    HY_TRY(level_apply<T>(ctx, l, dd, t, true));
     const double rho_new = 1.0 / (2.0 * sigma - rho);
-    launch_cheb_step<T>(t, dinv, r, dd, x, T(rho_new * rho), T(2.0 * rho_new / delta), L.ndofs, ctx->stream);
+    launch_cheb_step<T>(t, dinv, r, dd, x, T(rho_new * rho), T(2.0 * rho_new / delta), L.ndofs,
+                        j + 1 < degree ? &L.g : nullptr, ctx->dim, ctx->stream);
     HY_TRY(check_launch(ctx, 1));
     rho = rho_new;
   }

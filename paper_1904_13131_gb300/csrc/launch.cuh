@@ -101,12 +101,14 @@ template <typename TA, typename TB> void launch_convert(const TA* a, TB* b, long
 template <typename T> void launch_axpby(T a, const T* x, T b, T* y, long long n, cudaStream_t st);
 // z = x + a*y
 template <typename T> void launch_xpay(const T* x, T a, const T* y, T* z, long long n, cudaStream_t st);
-// Chebyshev: first step. r = b (x0 zero) or r = b - t; d = dinv*r*inv_theta; x = d (x0 zero) or x += d
-template <typename T> void launch_cheb_init(const T* b, const T* t, const T* dinv, T* r, T* d, T* x, T inv_theta,
-                                            bool x0_zero, long long n, cudaStream_t st);
-// Chebyshev: later step. r -= t; d = cd*d + cr*dinv*r; x += d
-template <typename T> void launch_cheb_step(const T* t, const T* dinv, T* r, T* d, T* x, T cd, T cr, long long n,
-                                            cudaStream_t st);
+// Chebyshev: first step. r = b (x0 zero) or r = b - t; d = dinv*r*inv_theta; x = d (x0 zero) or x += d.
+// prep (the level geometry, or null): also t = (constrained ? d : 0), the next application's output
+// prepared as launch_prep_out would.
+template <typename T> void launch_cheb_init(const T* b, T* t, const T* dinv, T* r, T* d, T* x, T inv_theta,
+                                            bool x0_zero, long long n, const Geom* prep, int dim, cudaStream_t st);
+// Chebyshev: later step. r -= t; d = cd*d + cr*dinv*r; x += d; prep as above
+template <typename T> void launch_cheb_step(T* t, const T* dinv, T* r, T* d, T* x, T cd, T cr, long long n,
+                                            const Geom* prep, int dim, cudaStream_t st);
 // z = a * b (elementwise)
 template <typename T> void launch_mul(const T* a, const T* b, T* z, long long n, cudaStream_t st);
 // out[i] = SplitMix64 uniform on [-1, 1) at counter i (seeded)

@@ -129,28 +129,32 @@ __global__ void sub_kernel(const T* __restrict__ b, const T* __restrict__ t, T* 
     r[i] = b[i] - t[i];
 }
 
-template <typename T>
-__global__ void cheb_init_kernel(const T* __restrict__ b, const T* __restrict__ t, const T* __restrict__ dinv,
+// PREP: also write t = (constrained ? d : 0), the output vector of the next application of d prepared as
+// prep_out would (t is read first at the same index, so the overwrite is safe).
+template <typename T, int PREP>
+__global__ void cheb_init_kernel(const T* __restrict__ b, T* __restrict__ t, const T* __restrict__ dinv,
                                  T* __restrict__ r, T* __restrict__ d, T* __restrict__ x, T inv_theta, bool x0_zero,
-                                 long long n) {
+                                 long long n, Geom g) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const T ri = x0_zero ? b[i] : b[i] - t[i];
     const T di = dinv[i] * ri * inv_theta;
     r[i] = ri;
     d[i] = di;
     x[i] = x0_zero ? di : x[i] + di;
+    if constexpr (PREP > 0) t[i] = ((cmask_of<PREP>(g, i / PREP) >> (i % PREP)) & 1u) ? di : T(0);
   }
 }
 
-template <typename T>
-__global__ void cheb_step_kernel(const T* __restrict__ t, const T* __restrict__ dinv, T* __restrict__ r,
-                                 T* __restrict__ d, T* __restrict__ x, T cd, T cr, long long n) {
+template <typename T, int PREP>
+__global__ void cheb_step_kernel(T* __restrict__ t, const T* __restrict__ dinv, T* __restrict__ r,
+                                 T* __restrict__ d, T* __restrict__ x, T cd, T cr, long long n, Geom g) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const T ri = r[i] - t[i];
     const T di = cd * d[i] + cr * dinv[i] * ri;
     r[i] = ri;
     d[i] = di;
     x[i] += di;
+    if constexpr (PREP > 0) t[i] = ((cmask_of<PREP>(g, i / PREP) >> (i % PREP)) & 1u) ? di : T(0);
   }
 }
 
@@ -345,13 +349,20 @@ void launch_sub(const T* b, const T* t, T* r, long long n, cudaStream_t st) {
   sub_kernel<T><<<grid_for(n), TPB, 0, st>>>(b, t, r, n);
 }
 template <typename T>
-void launch_cheb_init(const T* b, const T* t, const T* dinv, T* r, T* d, T* x, T inv_theta, bool x0_zero, long long n,
-                      cudaStream_t st) {
-  cheb_init_kernel<T><<<grid_for(n), TPB, 0, st>>>(b, t, dinv, r, d, x, inv_theta, x0_zero, n);
+void launch_cheb_init(const T* b, T* t, const T* dinv, T* r, T* d, T* x, T inv_theta, bool x0_zero, long long n,
+                      const Geom* prep, int dim, cudaStream_t st) {
+  const Geom g = prep ? *prep : Geom{};
+  if (!prep) cheb_init_kernel<T, 0><<<grid_for(n), TPB, 0, st>>>(b, t, dinv, r, d, x, inv_theta, x0_zero, n, g);
+  else if (dim == 2) cheb_init_kernel<T, 2><<<grid_for(n), TPB, 0, st>>>(b, t, dinv, r, d, x, inv_theta, x0_zero, n, g);
+  else cheb_init_kernel<T, 3><<<grid_for(n), TPB, 0, st>>>(b, t, dinv, r, d, x, inv_theta, x0_zero, n, g);
 }
 template <typename T>
-void launch_cheb_step(const T* t, const T* dinv, T* r, T* d, T* x, T cd, T cr, long long n, cudaStream_t st) {
-  cheb_step_kernel<T><<<grid_for(n), TPB, 0, st>>>(t, dinv, r, d, x, cd, cr, n);
+void launch_cheb_step(T* t, const T* dinv, T* r, T* d, T* x, T cd, T cr, long long n, const Geom* prep, int dim,
+                      cudaStream_t st) {
+  const Geom g = prep ? *prep : Geom{};
+  if (!prep) cheb_step_kernel<T, 0><<<grid_for(n), TPB, 0, st>>>(t, dinv, r, d, x, cd, cr, n, g);
+  else if (dim == 2) cheb_step_kernel<T, 2><<<grid_for(n), TPB, 0, st>>>(t, dinv, r, d, x, cd, cr, n, g);
+  else cheb_step_kernel<T, 3><<<grid_for(n), TPB, 0, st>>>(t, dinv, r, d, x, cd, cr, n, g);
 }
 void launch_lift(const double* u, double* du0, double factor, const double* fv, long long n_nodes, int dim,
                  const Geom& g, cudaStream_t st) {
@@ -389,8 +400,9 @@ void launch_sweep(const T* in, T* out, int dim, const int Lin[3], const int Lout
   template void launch_axpy_dev<T>(const double*, double, const T*, T*, long long, cudaStream_t);               \
   template void launch_xpay_dev<T>(const T*, const double*, const T*, T*, long long, cudaStream_t);             \
   template void launch_splitmix<T>(T*, long long, unsigned long long, cudaStream_t);                            \
-  template void launch_cheb_init<T>(const T*, const T*, const T*, T*, T*, T*, T, bool, long long, cudaStream_t); \
-  template void launch_cheb_step<T>(const T*, const T*, T*, T*, T*, T, T, long long, cudaStream_t);             \
+  template void launch_cheb_init<T>(const T*, T*, const T*, T*, T*, T*, T, bool, long long, const Geom*, int,     \
+                                    cudaStream_t);                                                              \
+  template void launch_cheb_step<T>(T*, const T*, T*, T*, T*, T, T, long long, const Geom*, int, cudaStream_t);   \
   template void launch_dot<T>(const T*, const T*, long long, double*, double*, cudaStream_t);                   \
   template void launch_sweep<T>(const T*, T*, int, const int*, const int*, int, const int*, const T*, int, bool, \
                                 const Geom*, const Geom*, cudaStream_t);

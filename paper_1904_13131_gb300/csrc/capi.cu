@@ -207,14 +207,14 @@ struct hy_ctx {
   double* d_partials = nullptr;
   double* d_scal = nullptr;
   double* d_face = nullptr;
-  double* d_eig_scal = nullptr;  // eigenvalue-estimate scalars (8 doubles)
+  double* d_eig_scal = nullptr;  // eigenvalue-estimate scalars (8 doubles), then PCG_SCALARS of the graph PCG
   double* d_eig_hist = nullptr;  // alpha and beta history
   size_t eig_hist_len = 0;
   long long coarse_nfree = 0;    // free dofs of the coarsest level
   double *tmp64a = nullptr, *tmp64b = nullptr;
   float *tmp32a = nullptr, *tmp32b = nullptr, *tmp32c = nullptr;
   size_t tmp_len = 0;
-  double* f64[10] = {};  // fine-level FP64 work vectors of PCG / Newton
+  double* f64[11] = {};  // fine-level FP64 work vectors of PCG / Newton (10: the iterate of the graph PCG)
   long long launches = 0;
   bool verbose = false;  // HY_VERBOSE=1: per-iteration diagnostics on stderr
   int prefetch = 0;      // L2 prefetch distance of the tangent action's cache chunks, in cell blocks
@@ -225,6 +225,10 @@ struct hy_ctx {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t vc_exec = nullptr;
   bool vc_valid = false;
+  // one PCG iteration as a graph (captured once per linearisation), its scalars read back into pinned memory
+  cudaGraphExec_t pcg_exec[2] = {nullptr, nullptr};
+  long long pcg_nodes[2] = {0, 0};
+  double* h_pcg_scal = nullptr;
   long long vc_nodes = 0;
   std::vector<std::pair<void*, size_t>> allocs;
 };
@@ -289,6 +293,10 @@ void drop_graph(hy_ctx* ctx) {
   if (ctx->vc_exec) cudaGraphExecDestroy(ctx->vc_exec);
   ctx->vc_exec = nullptr;
   ctx->vc_valid = false;
+  for (auto& e : ctx->pcg_exec) {
+    if (e) cudaGraphExecDestroy(e);
+    e = nullptr;
+  }
 }
 
 void free_mesh(hy_ctx* ctx) {
@@ -1142,7 +1150,7 @@ hy_status jacobian_ok(hy_ctx* ctx, const double* u, bool& ok) {
   return HY_OK;
 }
 
-hy_status pcg(hy_ctx* ctx, const double* b, double* x, double rtol, int max_iter, int* its_out) {
+hy_status pcg_host(hy_ctx* ctx, const double* b, double* x, double rtol, int max_iter, int* its_out) {
   Level& L = ctx->lev[ctx->nlev - 1];
   const long long n = L.ndofs;
   double *r = ctx->f64[0], *z = ctx->f64[1], *p = ctx->f64[2], *q = ctx->f64[3];
@@ -1372,9 +1380,10 @@ hy_status vcycle_top_ops(hy_ctx* ctx, const double* r, double* z) {
 
 // One PCG iteration of one problem after q = A p: alpha = rz/pq; x += alpha p; r -= alpha q;
 // converged = |r| <= tol; z = V r; beta = rzn/rz; p = z + beta p (scalars sc on the device).
-hy_status pcg_branch(hy_ctx* c, double* sc, double* x) {
+// first half (after q = A p): alpha, x += alpha p, r -= alpha q, |r|^2 and the convergence test
+hy_status pcg_update(hy_ctx* c, double* sc, double* x) {
   const long long nd = c->lev[c->nlev - 1].ndofs;
-  double *r = c->f64[0], *z = c->f64[1], *p = c->f64[2], *q = c->f64[3];
+  double *r = c->f64[0], *p = c->f64[2], *q = c->f64[3];
   cudaStream_t st = c->stream;
   launch_dot<double>(p, q, nd, c->d_partials, sc + 1, st);
   launch_pcg_scalar(sc, 0, st);
@@ -1382,12 +1391,22 @@ hy_status pcg_branch(hy_ctx* c, double* sc, double* x) {
   launch_axpy_dev<double>(sc + 2, -1.0, q, r, nd, st);
   launch_dot<double>(r, r, nd, c->d_partials, sc + 3, st);
   launch_pcg_scalar(sc, 1, st);
-  HY_TRY(check_launch(c, 8));
+  return check_launch(c, 8);
+}
+// second half: z = V r, beta, p = z + beta p
+hy_status pcg_direction(hy_ctx* c, double* sc) {
+  const long long nd = c->lev[c->nlev - 1].ndofs;
+  double *r = c->f64[0], *z = c->f64[1], *p = c->f64[2];
+  cudaStream_t st = c->stream;
   HY_TRY(vcycle_top_ops(c, r, z));
   launch_dot<double>(r, z, nd, c->d_partials, sc + 4, st);
   launch_pcg_scalar(sc, 2, st);
   launch_xpay_dev<double>(z, sc + 5, p, p, nd, st);
   return check_launch(c, 4);
+}
+hy_status pcg_branch(hy_ctx* c, double* sc, double* x) {
+  HY_TRY(pcg_update(c, sc, x));
+  return pcg_direction(c, sc);
 }
 
 // One PCG iteration of every resident problem R, captured into a graph on s0: the list launch
@@ -1638,6 +1657,102 @@ hy_status batch_pcg(hy_batch* b, const double* const* rhs, double* const* xs, do
   return result != HY_OK ? result : jo;
 }
 
+// Capture what `body` issues on ctx->stream into an executable graph (private capture stream); kernel
+// counts recorded during the capture go to *nodes instead of the context's counter.
+template <typename F>
+hy_status capture_exec(hy_ctx* ctx, F&& body, cudaGraphExec_t* exec, long long* nodes) {
+  if (!ctx->cap_stream) HY_CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t saved = ctx->stream;
+  const long long l0 = ctx->launches;
+  ctx->stream = ctx->cap_stream;
+  cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    ctx->stream = saved;
+    return fail(ctx, HY_ERR_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+  }
+  const hy_status st = body();
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(ctx->cap_stream, &g);
+  ctx->stream = saved;
+  *nodes = ctx->launches - l0;
+  ctx->launches = l0;
+  if (st != HY_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    if (st != HY_OK) return st;
+    return fail(ctx, HY_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+  }
+  e = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(ctx, HY_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  return HY_OK;
+}
+
+// PCG of one problem with every CG scalar on the device. An iteration is two graphs, captured once per
+// linearisation: A = {q = A p; alpha; x += alpha p; r -= alpha q; |r|^2; convergence test; scalars to pinned
+// host memory} and B = {z = V r; beta; p = z + beta p}. The host waits once per iteration, after A, and
+// launches B only if the problem has not converged; the iterate lives in a work vector and is copied out.
+// Same arithmetic as pcg_host (the scalars are formed on the device instead of the host).
+hy_status pcg_graph(hy_ctx* ctx, const double* b, double* x_out, double rtol, int max_iter, int* its_out) {
+  const int top = ctx->nlev - 1;
+  const long long n = ctx->lev[top].ndofs;
+  double *r = ctx->f64[0], *z = ctx->f64[1], *p = ctx->f64[2], *q = ctx->f64[3], *x = ctx->f64[10];
+  double* sc = ctx->d_eig_scal + 8;
+  if (its_out) *its_out = 0;
+  if (!ctx->h_pcg_scal) HY_CK(cudaMallocHost((void**)&ctx->h_pcg_scal, 2 * sizeof(double) * PCG_SCALARS));
+  double* h_in = ctx->h_pcg_scal;
+  double* h_out = ctx->h_pcg_scal + PCG_SCALARS;
+  HY_CK(cudaMemsetAsync(x, 0, sizeof(double) * n, ctx->stream));
+  HY_CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  double bb;
+  HY_TRY(dot<double>(ctx, b, b, n, &bb));  // synchronises: h_in is free again
+  const double nb = std::sqrt(bb);
+  auto copy_out = [&]() { return cudaMemcpyAsync(x_out, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream); };
+  if (nb == 0.0) {
+    HY_CK(copy_out());
+    return HY_OK;
+  }
+  if (!(nb == nb)) return fail(ctx, HY_ERR_ARG, "pcg: right-hand side has NaN");
+  HY_TRY(vcycle_top(ctx, r, z));
+  HY_CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  for (int k = 0; k < PCG_SCALARS; ++k) h_in[k] = 0.0;
+  h_in[6] = rtol * nb;
+  HY_CK(cudaMemcpyAsync(sc, h_in, sizeof(double) * PCG_SCALARS, cudaMemcpyHostToDevice, ctx->stream));
+  launch_dot<double>(r, z, n, ctx->d_partials, sc, ctx->stream);  // rz
+  HY_TRY(check_launch(ctx, 2));
+  if (!ctx->pcg_exec[0]) {
+    HY_TRY(capture_exec(ctx, [&]() -> hy_status {
+      HY_TRY(level_apply<double>(ctx, top, p, q));
+      HY_TRY(pcg_update(ctx, sc, x));
+      HY_CK(cudaMemcpyAsync(h_out, sc, sizeof(double) * PCG_SCALARS, cudaMemcpyDeviceToHost, ctx->stream));
+      return HY_OK;
+    }, &ctx->pcg_exec[0], &ctx->pcg_nodes[0]));
+    HY_TRY(capture_exec(ctx, [&]() -> hy_status { return pcg_direction(ctx, sc); }, &ctx->pcg_exec[1],
+                        &ctx->pcg_nodes[1]));
+  }
+  for (int it = 1; it <= max_iter; ++it) {
+    HY_CK(cudaGraphLaunch(ctx->pcg_exec[0], ctx->stream));
+    HY_CK(cudaStreamSynchronize(ctx->stream));
+    ctx->launches += ctx->pcg_nodes[0];
+    if (h_out[8] != 0.0) {
+      HY_CK(copy_out());
+      return fail(ctx, HY_ERR_NOCONV, "pcg: p^T A p <= 0 (operator not SPD)");
+    }
+    if (its_out) *its_out = it;
+    if (h_out[7] != 0.0) {
+      HY_CK(copy_out());
+      return HY_OK;
+    }
+    HY_CK(cudaGraphLaunch(ctx->pcg_exec[1], ctx->stream));
+    ctx->launches += ctx->pcg_nodes[1];
+  }
+  HY_CK(copy_out());
+  return fail(ctx, HY_ERR_NOCONV, "pcg: iteration cap reached");
+}
+
+hy_status pcg(hy_ctx* ctx, const double* b, double* x, double rtol, int max_iter, int* its_out) {
+  return ctx->use_graphs ? pcg_graph(ctx, b, x, rtol, max_iter, its_out) : pcg_host(ctx, b, x, rtol, max_iter, its_out);
+}
+
 void batch_free(hy_batch* b) {
   if (b->s0) cudaStreamSynchronize(b->s0);
   for (cudaStream_t s : b->branch)
@@ -1705,6 +1820,7 @@ void hy_destroy(hy_ctx* ctx) {
   else cudaDeviceSynchronize();
   free_mesh(ctx);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->h_pcg_scal) cudaFreeHost(ctx->h_pcg_scal);
   delete ctx;
 }
 
@@ -1891,8 +2007,8 @@ hy_status hy_mesh_setup(hy_ctx* ctx, int dim, int degree, int m, int n_levels, c
   HY_TRY(dalloc(ctx, &ctx->d_partials, DOT_BLOCKS));
   HY_TRY(dalloc(ctx, &ctx->d_scal, 4));
   HY_TRY(dalloc(ctx, &ctx->d_face, 18));
-  HY_TRY(dalloc(ctx, &ctx->d_eig_scal, 8));
-  for (int i = 0; i < 10; ++i) HY_TRY(dalloc(ctx, &ctx->f64[i], ctx->lev[n_levels - 1].ndofs));
+  HY_TRY(dalloc(ctx, &ctx->d_eig_scal, 8 + PCG_SCALARS));
+  for (int i = 0; i < 11; ++i) HY_TRY(dalloc(ctx, &ctx->f64[i], ctx->lev[n_levels - 1].ndofs));
   HY_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
   HY_CK(cudaStreamSynchronize(ctx->stream));
   return HY_OK;
@@ -2249,8 +2365,8 @@ hy_status hy_footprint(int dim, int degree, int m, int n_levels, hy_variant vari
     tmp_len = std::max(tmp_len, inter);
   }
   total += 2 * al(tmp_len, 8) + 3 * al(tmp_len, 4);
-  total += al(1, 4) + al(1, 8) + al(DOT_BLOCKS, 8) + al(4, 8) + al(18, 8) + al(8, 8);
-  total += 10 * al(nd[n_levels - 1], 8);
+  total += al(1, 4) + al(1, 8) + al(DOT_BLOCKS, 8) + al(4, 8) + al(18, 8) + al(8 + PCG_SCALARS, 8);
+  total += 11 * al(nd[n_levels - 1], 8);
   const int top = n_levels - 1;
   for (int l = 0; l < n_levels; ++l) {
     const bool need64 = (l == top) || (l == 0) || !mixed;

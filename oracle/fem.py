@@ -31,7 +31,7 @@ class Problem:
     masks: per-face bitmask of constrained components, faces (-x,+x,-y,+y,-z,+z).
     """
 
-    def __init__(self, dim, k, m, ids, mu_tab, lam_tab, masks, chunk=512):
+    def __init__(self, dim, k, m, ids, mu_tab, lam_tab, masks, chunk=512, law=0):
         self.dim, self.k, self.m = dim, k, m
         self.n = k + 1
         self.h = 1.0 / m
@@ -40,6 +40,7 @@ class Problem:
         self.n_dofs = dim * self.n_nodes
         self.tab = CellTables(dim, k)
         self.chunk = chunk
+        self.law = law  # 0: the paper's volumetric function lambda ln^2 J; 1: lambda/4 (J^2 - 1 - 2 ln J)
         ids = np.asarray(ids)
         self.mu = np.asarray(mu_tab, dtype=float)[ids]
         self.lam = np.asarray(lam_tab, dtype=float)[ids]
@@ -102,7 +103,7 @@ class Problem:
         for cells in self._chunks():
             F = self.deformation(u, cells)
             mu, lam = self._qp_params(cells)
-            E += np.einsum("Kq,q->", material.psi(F, mu, lam), self.tab.w) * self.h**self.dim
+            E += np.einsum("Kq,q->", material.psi(F, mu, lam, self.law), self.tab.w) * self.h**self.dim
         return E
 
     def residual_raw(self, u):
@@ -111,7 +112,7 @@ class Problem:
         for cells in self._chunks():
             F = self.deformation(u, cells)
             mu, lam = self._qp_params(cells)
-            tau = material.kirchhoff(F, mu, lam)
+            tau = material.kirchhoff(F, mu, lam, self.law)
             g = self._g(F)
             # tau : grad^s(N_a e_c) = tau : grad(N_a e_c) (tau symmetric) = sum_j tau_cj g_a,j
             RK = np.einsum("Kqcj,Kqaj,q->Kac", tau, g, self.tab.w) * self.h**self.dim
@@ -130,8 +131,8 @@ class Problem:
         d = self.dim
         F = self.deformation(u, cells)
         mu, lam = self._qp_params(cells)
-        tau = material.kirchhoff(F, mu, lam)
-        JC = material.spatial_tangent(F, mu, lam)
+        tau = material.kirchhoff(F, mu, lam, self.law)
+        JC = material.spatial_tangent(F, mu, lam, self.law)
         ga = self._g(F)
         I = np.eye(d)
         G = np.einsum("ic,Kqaj->Kqacij", I, ga)                         # grad(N_a e_c)_{ij} = d_ic g_a,j
@@ -180,8 +181,8 @@ class Problem:
         for cells in self._chunks():
             F = self.deformation(u, cells)
             mu, lam = self._qp_params(cells)
-            tau = material.kirchhoff(F, mu, lam)
-            JC = material.spatial_tangent(F, mu, lam)
+            tau = material.kirchhoff(F, mu, lam, self.law)
+            JC = material.spatial_tangent(F, mu, lam, self.law)
             Finv = np.linalg.inv(F)
             gx = np.einsum("KqiJ,KqJj->Kqij", self.grad_at_qp(xin, cells), Finv)
             gxs = 0.5 * (gx + np.swapaxes(gx, -1, -2))
@@ -200,8 +201,8 @@ class Problem:
         for cells in self._chunks():
             F = self.deformation(u, cells)
             mu, lam = self._qp_params(cells)
-            tau = material.kirchhoff(F, mu, lam)
-            JC = material.spatial_tangent(F, mu, lam)
+            tau = material.kirchhoff(F, mu, lam, self.law)
+            JC = material.spatial_tangent(F, mu, lam, self.law)
             ga = self._g(F)
             I = np.eye(d)
             G = np.einsum("ic,Kqaj->Kqacij", I, ga)

@@ -130,9 +130,10 @@ class Hierarchy:
     """Level problems from coarsest (0) to finest (L-1), each halving the cells per direction."""
 
     def __init__(self, dim, k, levels_m, ids, mu_tab, lam_tab, masks, degree=4, sweeps=1, smooth_lo=0.6,
-                 smooth_hi=1.2, eig_iters=30, coarse_eig_iters=None, coarse_reduction=1e-3, coarse_solver="chebyshev"):
+                 smooth_hi=1.2, eig_iters=30, coarse_eig_iters=None, coarse_reduction=1e-3, coarse_solver="chebyshev",
+                 law=0):
         self.dim, self.k = dim, k
-        self.levels = [Problem(dim, k, ml, ids[l], mu_tab, lam_tab, masks) for l, ml in enumerate(levels_m)]
+        self.levels = [Problem(dim, k, ml, ids[l], mu_tab, lam_tab, masks, law=law) for l, ml in enumerate(levels_m)]
         self.degree, self.sweeps = degree, sweeps
         self.smooth_lo, self.smooth_hi = smooth_lo, smooth_hi
         self.eig_iters = eig_iters

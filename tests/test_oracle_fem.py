@@ -5,7 +5,8 @@
   * R = dE/du and A = dR/du by central differences            (Eqs. weak_form, tangent)
   * symmetry of A, translations in ker A(u), rotations in ker A(0)
   * small-strain limit: A(0) equals an exactly integrated (sympy) linear-elasticity stiffness with
-    Lame (mu, 2 lambda) -- the paper's psi carries lambda ln^2 J (Sec. 2.3)
+    Lame (mu, 2 lambda) -- the paper's psi carries lambda ln^2 J (Sec. 2.3) -- and (mu, lambda) for the
+    second volumetric function lambda/4 (J^2 - 1 - 2 ln J)
   * brute force: pure-Python loops over every index on one cell
 """
 import itertools
@@ -163,16 +164,19 @@ def _sympy_linear_elastic_cell(dim, k, mu, lam):
     return K
 
 
+@pytest.mark.parametrize("law,lame2", [(0, 2.0), (1, 1.0)])
 @pytest.mark.parametrize("dim,k", [(2, 1), (2, 2), (3, 1)])
-def test_small_strain_limit_matches_exact_linear_elasticity(dim, k):
+def test_small_strain_limit_matches_exact_linear_elasticity(dim, k, law, lame2):
+    """The paper's law linearises to Lame (mu, 2 lambda); the second volumetric function to (mu, lambda)."""
     p = make(dim, k, 1, uniform=True)
+    p.law = law
     mu, lam = 1.0, inputs.lame_lambda(1.0, 0.3)
     A0 = p.tangent_raw(np.zeros(p.n_dofs)).toarray()
-    K = _sympy_linear_elastic_cell(dim, k, mu, 2.0 * lam)
+    K = _sympy_linear_elastic_cell(dim, k, mu, lame2 * lam)
     np.testing.assert_allclose(A0, K, atol=1e-13 * np.abs(K).max())
 
 
-def _brute_cell(dim, k, u_cell, mu, lam):
+def _brute_cell(dim, k, u_cell, mu, lam, law=0):
     """Residual and tangent of one unit cell with explicit loops over every index."""
     t = CellTables(dim, k)
     na = (k + 1) ** dim
@@ -187,8 +191,10 @@ def _brute_cell(dim, k, u_cell, mu, lam):
         Finv = np.linalg.inv(F)
         J_ = np.linalg.det(F)
         b = F @ F.T
-        tau = mu * b - (mu - 2 * lam * math.log(J_)) * np.eye(dim)
-        cc = 2 * (mu - 2 * lam * math.log(J_))
+        pv = 2 * lam * math.log(J_) if law == 0 else 0.5 * lam * (J_ * J_ - 1.0)  # J U'(J)
+        jdp = 2 * lam if law == 0 else lam * J_ * J_                             # J d(J U')/dJ
+        tau = mu * b - (mu - pv) * np.eye(dim)
+        cc = 2 * (mu - pv)
         g = np.zeros((na, dim))
         for a in range(na):
             for j in range(dim):
@@ -211,7 +217,7 @@ def _brute_cell(dim, k, u_cell, mu, lam):
                                     for ll in range(dim):
                                         gs_j = 0.5 * ((g[b_, ll] if kk == e else 0.0) + (g[b_, kk] if ll == e else 0.0))
                                         Cijkl = cc * 0.5 * ((i == kk) * (j == ll) + (i == ll) * (j == kk)) \
-                                            + 2 * lam * (i == j) * (kk == ll)
+                                            + jdp * (i == j) * (kk == ll)
                                         s += gs_i * Cijkl * gs_j
                                 # geometric: grad(N_a e_c)_{ij} (grad(N_b e_e) . tau)_{ij}
                                 gt = sum((g[b_, mm] if i == e else 0.0) * tau[mm, j] for mm in range(dim))
@@ -220,12 +226,14 @@ def _brute_cell(dim, k, u_cell, mu, lam):
     return R, A
 
 
+@pytest.mark.parametrize("law", [0, 1])
 @pytest.mark.parametrize("dim,k", [(2, 1), (2, 2), (3, 1)])
-def test_brute_force_single_cell(dim, k):
+def test_brute_force_single_cell(dim, k, law):
     p = make(dim, k, 1, uniform=True)
+    p.law = law
     u = 0.1 * inputs.gaussian_vector(p.n_dofs, 11)
     mu, lam = 1.0, inputs.lame_lambda(1.0, 0.3)
-    R, A = _brute_cell(dim, k, u, mu, lam)
+    R, A = _brute_cell(dim, k, u, mu, lam, law)
     np.testing.assert_allclose(p.residual_raw(u), R, atol=1e-13)
     np.testing.assert_allclose(p.tangent_raw(u).toarray(), A, atol=1e-12)
 

@@ -523,6 +523,17 @@ def main():
             "f64_form": FORMS[ctxs[v].kernel_form(-1, 0)], "f32_form": FORMS[ctxs[v].kernel_form(-1, 1)],
             "ff_form": FORMS[ctxs[v].kernel_form(-1, 2)],
         }
+    # the second volumetric function (law 1) through the same kernels: T4 and NC in FP64
+    second_law = {}
+    for v in ("T4", "NC"):
+        ctxs[v].set_material_law(api.LAW_J2)
+        ctxs[v].set_displacement(u, v, level_dtype=1)
+    msl, _, _ = time_applies(torch, ctxs, ["T4", "NC"], x, 0, 5, 2, flush, stream)
+    for i, v in enumerate(("T4", "NC")):
+        t = float(np.median(msl[:, i]))
+        second_law[v] = {"f64_ms": t, "f64_gdofs": n / (t * 1e-3) / 1e9}
+        ctxs[v].set_material_law(api.LAW_LOG2)
+        ctxs[v].set_displacement(u, v, level_dtype=1)
     # dominant kernel of the step: the slowest variant's FP64 apply (FP64-pipe bound)
     dom = max(per_var_ms, key=per_var_ms.get)
     ach = flops_per_qp(dom) * nqp / (per_var_ms[dom] * 1e-3) / 1e12
@@ -591,7 +602,8 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": int(launches_timed),
-                "per_variant_ms_f64": per_var_ms, "variants": variants, "solve": solve, "serve": serve, "batch": batch,
+                "per_variant_ms_f64": per_var_ms, "variants": variants, "second_law": second_law, "solve": solve,
+                "serve": serve, "batch": batch,
                 "wall_s_timed_region": wall, "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src}
         print(json.dumps(line), flush=True)
     if dist:

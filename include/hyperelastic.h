@@ -85,6 +85,14 @@ hy_status hy_num_dofs(const hy_ctx *ctx, int level, int64_t *n);
 hy_status hy_set_material(hy_ctx *ctx, int level, const uint8_t *cell_mat, const double *mu,
                           const double *lambda, int n_mat);
 
+/* Volumetric function of the compressible neo-Hooke law, on every level; the isochoric part and the
+ * -mu ln J term are the paper's (Sec. 2.3). HY_LAW_LOG2 (default): U = lambda ln^2 J, the paper's;
+ * HY_LAW_J2: U = lambda/4 (J^2 - 1 - 2 ln J). With p = J U'(J) both give tau = mu b - (mu - p) I and
+ * J*C = 2 (mu - p) S + J p'(J) I (x) I, which every tangent variant evaluates in the same places. Takes
+ * effect at the next hy_set_displacement (and for hy_residual at once). HY_ERR_ARG for another value. */
+typedef enum { HY_LAW_LOG2 = 0, HY_LAW_J2 = 1 } hy_law;
+hy_status hy_set_material_law(hy_ctx *ctx, int law);
+
 /* Linearisation point (Sec. 6). u_dev: fine-level FP64 displacement (device). The displacement is
  * carried down to every level by nodal interpolation and each level's Gauss-point cache is built
  * for `variant` from FP64 kinematics (F, J, ln J). level_dtype = HY_F32 selects the mixed-precision
@@ -299,6 +307,7 @@ typedef struct {
   int n_mat;
   hy_newton_params newton;        /* load path, tolerances, variant, V-cycle precision */
   hy_solver_params solver;
+  int law;                        /* hy_law of the material */
 } hy_request;
 
 typedef struct {

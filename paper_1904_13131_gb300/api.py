@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_PKG, "libhyperelastic.so")
 STATUS = {0: "HY_OK", 1: "HY_ERR_ARG", 2: "HY_ERR_STATE", 3: "HY_ERR_OOM", 4: "HY_ERR_CUDA", 5: "HY_ERR_JNEG",
           6: "HY_ERR_NOCONV", 7: "HY_ERR_TIMEOUT", 8: "HY_ERR_UNSUPPORTED"}
 VARIANTS = {"T4": 0, "T2": 1, "FC": 2, "SC": 3, "NC": 4}
+LAW_LOG2, LAW_J2 = 0, 1  # hy_law
 F64, F32, FF = 0, 1, 2  # hy_dtype; FF: double-float action on FP64 vectors
 
 # every symbol the header declares (checked by the CPU test suite)
@@ -28,7 +29,7 @@ EXPORTED = ("hy_create", "hy_destroy", "hy_status_str", "hy_last_error", "hy_mes
             "hy_server_create", "hy_server_destroy", "hy_server_submit", "hy_server_poll", "hy_server_wait",
             "hy_server_release", "hy_server_stats_get", "hy_kernel_form", "hy_batch_create", "hy_batch_destroy",
             "hy_batch_last_error", "hy_batch_apply", "hy_batch_pcg", "hy_batch_kernel_launches",
-            "hy_batch_kernel_form")
+            "hy_batch_kernel_form", "hy_set_material_law")
 
 
 class HyError(RuntimeError):
@@ -63,7 +64,7 @@ class Request(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("degree", ctypes.c_int), ("cells_per_dir", ctypes.c_int),
                 ("n_levels", ctypes.c_int), ("face_masks", ctypes.c_uint32 * 6), ("cell_mat_levels", ctypes.c_void_p),
                 ("mu", ctypes.POINTER(ctypes.c_double)), ("lambda_", ctypes.POINTER(ctypes.c_double)),
-                ("n_mat", ctypes.c_int), ("newton", NewtonParams), ("solver", SolverParams)]
+                ("n_mat", ctypes.c_int), ("newton", NewtonParams), ("solver", SolverParams), ("law", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):
@@ -114,6 +115,7 @@ def load_library(path: str = LIB_PATH):
         "hy_footprint": [i32, i32, i32, i32, i32, i32, ctypes.POINTER(SolverParams), ctypes.POINTER(ctypes.c_uint32),
                          ctypes.POINTER(i64)],
         "hy_kernel_form": [vp, i32, i32, ctypes.POINTER(i32)],
+        "hy_set_material_law": [vp, i32],
         "hy_ctx_bytes": [vp, ctypes.POINTER(i64)],
         "hy_batch_create": [ctypes.POINTER(vp), ctypes.POINTER(vp), i32],
         "hy_batch_destroy": [vp],
@@ -209,6 +211,10 @@ class Context:
         n = ctypes.c_int64()
         self._ck(self.lib.hy_num_dofs(self.h, level, ctypes.byref(n)))
         return n.value
+
+    def set_material_law(self, law):
+        """0 (LAW_LOG2): the paper's lambda ln^2 J; 1 (LAW_J2): lambda/4 (J^2 - 1 - 2 ln J)."""
+        self._ck(self.lib.hy_set_material_law(self.h, int(law)))
 
     def set_material(self, level, cell_mat, mu, lam):
         ids = np.ascontiguousarray(cell_mat, dtype=np.uint8)
@@ -491,8 +497,8 @@ class Server:
     def __exit__(self, *a):
         self.close()
 
-    def submit(self, problem: dict, newton: NewtonParams, solver: SolverParams | None = None) -> int:
-        """problem: an inputs.problem(...) bundle (ids of every level, coarsest first)."""
+    def submit(self, problem: dict, newton: NewtonParams, solver: SolverParams | None = None, law: int = 0) -> int:
+        """problem: an inputs.problem(...) bundle (ids of every level, coarsest first); law: a hy_law."""
         if solver is None:
             solver = SolverParams(4, 1, 0.6, 1.2, 30, 0, 1e-3, 0, -1, 0, -1)
         ids = np.ascontiguousarray(np.concatenate([np.asarray(i, dtype=np.uint8) for i in problem["ids"]]))
@@ -508,6 +514,7 @@ class Server:
         r.n_mat = len(mu)
         r.newton = newton
         r.solver = solver
+        r.law = int(law)
         t = ctypes.c_uint64()
         st = self.lib.hy_server_submit(self.h, ctypes.byref(r), ctypes.byref(t))
         if st != 0:

@@ -197,6 +197,7 @@ struct hy_ctx {
   Basis1D<ff> bff{};
   hy_solver_params sp{4, 1, 0.6, 1.2, 30, 0, 1e-3, 0, -1, HY_F64, -1};
   int var = -1;
+  int law = 0;  // volumetric function of the neo-Hooke law (hy_set_material_law)
   bool mixed = false;
   bool state_ok = false;
   double coarse_lo = 0, coarse_hi = 0;
@@ -341,6 +342,7 @@ CellArgs<T> cell_args(hy_ctx* ctx, Level& L) {
     a.mt = L.mtff;
     a.b = ctx->bff;
   }
+  a.mt.law = ctx->law;
   return a;
 }
 
@@ -2157,6 +2159,15 @@ hy_status hy_set_level_info(hy_ctx* ctx, int level, double lmax, double clo, dou
     if (!(lmax > 0)) return fail(ctx, HY_ERR_ARG, "bad lmax");
     ctx->lev[l].lmax = lmax;
   }
+  return HY_OK;
+}
+
+hy_status hy_set_material_law(hy_ctx* ctx, int law) {
+  if (!ctx) return HY_ERR_ARG;
+  if (law != HY_LAW_LOG2 && law != HY_LAW_J2) return fail(ctx, HY_ERR_ARG, "unknown material law");
+  ctx->law = law;
+  ctx->state_ok = false;
+  drop_graph(ctx);
   return HY_OK;
 }
 

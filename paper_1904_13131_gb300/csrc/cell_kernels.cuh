@@ -354,12 +354,27 @@ __device__ __forceinline__ void matmul(const T A[DIM][DIM], const T B[DIM][DIM],
     }
 }
 
+// Volumetric part of the law: p = J U'(J) and J p'(J). Law 0 is the paper's U = lambda ln^2 J (Sec. 2.3):
+// p = 2 lambda ln J, J p' = 2 lambda. Law 1 is U = lambda/4 (J^2 - 1 - 2 ln J): p = lambda/2 (J^2 - 1),
+// J p' = lambda J^2. Then tau = mu b - (mu - p) I and J*C = 2 (mu - p) S + J p' I (x) I.
+template <typename T>
+__device__ __forceinline__ void volumetric(T J, T lam, int law, T& p, T& jdp) {
+  if (law == 1) {
+    const T J2 = J * J;
+    p = T(0.5) * lam * (J2 - T(1));
+    jdp = lam * J2;
+  } else {
+    p = T(2) * lam * log(J);
+    jdp = T(2) * lam;
+  }
+}
+
 // Neo-Hooke state at a Gauss point from F (Sec. 2.3), in the scaled form used by the kernels:
 // M = F^{-1}/h, tau~ = W (mu b - (mu - 2 lambda ln J) I), c1~ = 2 W (mu - 2 lambda ln J), c2~ = 2 W lambda.
 // If c1 is given (>= 0 flag), it replaces mu - 2 lambda ln J (Algorithm 1 caches it).
 template <int DIM, typename T>
-__device__ __forceinline__ T neo_hooke_state(const T F[DIM][DIM], T mu, T lam, T W, T inv_h, bool have_c, T c_in,
-                                             T M[DIM][DIM], T tau[nsym(DIM)], T& c1, T& c2) {
+__device__ __forceinline__ T neo_hooke_state(const T F[DIM][DIM], T mu, T lam, int law, T W, T inv_h, bool have_c,
+                                             T c_in, T M[DIM][DIM], T tau[nsym(DIM)], T& c1, T& c2) {
   T J;
   if (DIM == 3) {
     const T a00 = F[1][1] * F[2][2] - F[1][2] * F[2][1];
@@ -382,7 +397,9 @@ __device__ __forceinline__ T neo_hooke_state(const T F[DIM][DIM], T mu, T lam, T
     M[0][0] = F[1][1] * s; M[0][1] = -F[0][1] * s;
     M[1][0] = -F[1][0] * s; M[1][1] = F[0][0] * s;
   }
-  const T c = have_c ? c_in : mu - T(2) * lam * log(J);
+  T pv, jdp;
+  volumetric(J, lam, law, pv, jdp);
+  const T c = have_c ? c_in : mu - pv;
   const T Wmu = W * mu;
 #pragma unroll
   for (int a = 0; a < nsym(DIM); ++a) {
@@ -393,7 +410,7 @@ __device__ __forceinline__ T neo_hooke_state(const T F[DIM][DIM], T mu, T lam, T
     tau[a] = Wmu * bij - (i == j ? W * c : T(0));
   }
   c1 = T(2) * W * c;
-  c2 = T(2) * W * lam;
+  c2 = W * jdp;
   return J;
 }
 
@@ -403,7 +420,7 @@ __device__ __forceinline__ T neo_hooke_state(const T F[DIM][DIM], T mu, T lam, T
 // g' = Grad x adj, tau' = kappa tau, c1' = 2 kappa (mu - 2 lambda ln J), c2' = 2 kappa lambda -- the same
 // quantity as W/h (g tau + JC : sym g) F^{-T} with g = Grad x F^{-1}.
 template <int DIM, typename T>
-__device__ __forceinline__ void neo_hooke_adj(const T F[DIM][DIM], T mu, T lam, T Wh, bool have_c, T c_in,
+__device__ __forceinline__ void neo_hooke_adj(const T F[DIM][DIM], T mu, T lam, int law, T Wh, bool have_c, T c_in,
                                               T adj[DIM][DIM], T tau[nsym(DIM)], T& c1, T& c2) {
   T J;
   if (DIM == 3) {
@@ -427,7 +444,9 @@ __device__ __forceinline__ void neo_hooke_adj(const T F[DIM][DIM], T mu, T lam, 
   T rho;
   rho = rcp_rn(J);
   const T kappa = Wh * rho * rho;
-  const T c = have_c ? c_in : mu - T(2) * lam * log(J);
+  T pv, jdp;
+  volumetric(J, lam, law, pv, jdp);
+  const T c = have_c ? c_in : mu - pv;
   const T kmu = kappa * mu, kc = kappa * c;
 #pragma unroll
   for (int a = 0; a < nsym(DIM); ++a) {
@@ -438,7 +457,7 @@ __device__ __forceinline__ void neo_hooke_adj(const T F[DIM][DIM], T mu, T lam, 
     tau[a] = (i == j) ? fma(kmu, bij, -kc) : kmu * bij;
   }
   c1 = T(2) * kc;
-  c2 = T(2) * kappa * lam;
+  c2 = kappa * jdp;
 }
 
 // Material part for the neo-Hooke action (Eq. simplified_action): S = c1 sym(g) + c2 tr(g) I.
@@ -517,7 +536,8 @@ struct CellLoc {
 //   FC/SC/NC: the state recomputed from F (cached, or I + Grad u), with g' = Grad x adj F (Algorithm 1 for SC).
 template <int DIM, int VAR, typename T>
 __device__ __forceinline__ void qp_flux(const T G[DIM][DIM], const T Gu[DIM][DIM], const T* __restrict__ cs, int st,
-                                        int qg, bool active, int id, const T* mu, const T* lam, T Wh, T P[DIM][DIM]) {
+                                        int qg, bool active, int id, const T* mu, const T* lam, int law, T Wh,
+                                        T P[DIM][DIM]) {
   constexpr int NS = nsym(DIM);
   T M[DIM][DIM], tau[NS], Sv[NS], g[DIM][DIM];
   if (VAR == VAR_T4 || VAR == VAR_T2) {
@@ -565,7 +585,7 @@ __device__ __forceinline__ void qp_flux(const T G[DIM][DIM], const T Gu[DIM][DIM
     }
     const T cin = (VAR == VAR_SC && active) ? cs[qg] : T(0);
     T c1, c2;
-    neo_hooke_adj<DIM>(F, mu[id], lam[id], Wh, VAR == VAR_SC, cin, M, tau, c1, c2);  // M = adj
+    neo_hooke_adj<DIM>(F, mu[id], lam[id], law, Wh, VAR == VAR_SC, cin, M, tau, c1, c2);  // M = adj
     matmul<DIM>(G, M, g);
     nh_action<DIM>(g, c1, c2, Sv);
   }
@@ -655,7 +675,8 @@ __device__ __forceinline__ void apply_point_body(const CellArgs<T>& a, const int
   }
   // quadrature-point work
   T P[DIM][DIM];
-  qp_flux<DIM, VAR>(G, Gu, cs, BS, threadIdx.x, active, active ? a.mat[cell] : 0, s.mu, s.lam, s.Wh[pt.p], P);
+  qp_flux<DIM, VAR>(G, Gu, cs, BS, threadIdx.x, active, active ? a.mat[cell] : 0, s.mu, s.lam, a.mt.law, s.Wh[pt.p],
+                    P);
 #pragma unroll
   for (int c = 0; c < DIM; ++c)
 #pragma unroll
@@ -898,7 +919,7 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
         }
       }
       T P[DIM][DIM];
-      qp_flux<DIM, VAR>(G, Gu, cq, BS, cl * NPT + p, active, id, tmu, tlam, tWh[p], P);
+      qp_flux<DIM, VAR>(G, Gu, cq, BS, cl * NPT + p, active, id, tmu, tlam, a.mt.law, tWh[p], P);
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
         Px[q][c] = P[c][0];
@@ -1068,7 +1089,7 @@ qp_state_kernel(const CellArgs<double> a, T* __restrict__ out) {
   const int id = a.mat[cell];
   const double mu = s.mu[id], lam = s.lam[id];
   double M[DIM][DIM], tau[NS], c1, c2;
-  const double J = neo_hooke_state<DIM>(F, mu, lam, s.W[pt.p], inv_h, false, 0.0, M, tau, c1, c2);
+  const double J = neo_hooke_state<DIM>(F, mu, lam, a.mt.law, s.W[pt.p], inv_h, false, 0.0, M, tau, c1, c2);
   if (!(J > 0.0)) {
     atomicOr(a.err, J != J ? ERRBIT_NAN : ERRBIT_JNEG);
   } else {
@@ -1107,7 +1128,9 @@ qp_state_kernel(const CellArgs<double> a, T* __restrict__ out) {
 #pragma unroll
     for (int i = 0; i < DIM * DIM; ++i) out[i * st + qg] = T(F[i / DIM][i % DIM]);
   } else if (VAR == VAR_SC) {
-    out[qg] = T(mu - 2.0 * lam * log(J));
+    double pv, jdp;
+    volumetric(J, lam, a.mt.law, pv, jdp);
+    out[qg] = T(mu - pv);
   }
 }
 
@@ -1144,7 +1167,8 @@ residual_kernel(const CellArgs<double> a) {
     for (int J = 0; J < DIM; ++J) F[i][J] = (i == J ? 1.0 : 0.0) + Gu[i][J] * inv_h;
   const int id = active ? a.mat[cell] : 0;
   double M[DIM][DIM], tau[NS], c1, c2;
-  const double J = neo_hooke_state<DIM>(F, s.mu[id], s.lam[id], s.W[pt.p], inv_h, false, 0.0, M, tau, c1, c2);
+  const double J = neo_hooke_state<DIM>(F, s.mu[id], s.lam[id], a.mt.law, s.W[pt.p], inv_h, false, 0.0, M, tau, c1,
+                                        c2);
   if (active && !(J > 0.0)) atomicOr(a.err, J != J ? ERRBIT_NAN : ERRBIT_JNEG);
   double tf[DIM][DIM];
 #pragma unroll
@@ -1216,7 +1240,7 @@ diag_kernel(const CellArgs<double> a) {
     for (int J = 0; J < DIM; ++J) F[i][J] = (i == J ? 1.0 : 0.0) + Gu[i][J] * inv_h;
   const int id = active ? a.mat[cell] : 0;
   double M[DIM][DIM], tau[NS], c1, c2;
-  neo_hooke_state<DIM>(F, s.mu[id], s.lam[id], s.W[pt.p], inv_h, false, 0.0, M, tau, c1, c2);
+  neo_hooke_state<DIM>(F, s.mu[id], s.lam[id], a.mt.law, s.W[pt.p], inv_h, false, 0.0, M, tau, c1, c2);
   // per-point state to shared memory in E: M (DIM^2 rows, in the flux buffer), tau, c1, c2 (NS + 2 rows)
   E(*Me)[DIM * DIM][NPT] = reinterpret_cast<E(*)[DIM * DIM][NPT]>(&s.bp[0][0][0]);
 #pragma unroll

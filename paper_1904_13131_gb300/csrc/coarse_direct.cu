@@ -98,7 +98,7 @@ __global__ void assemble_dense_kernel(const CellArgs<double> a, double* __restri
         F[c][J] = (c == J ? 1.0 : 0.0) + v * a.g.inv_h;
       }
     double M[DIM][DIM], tau[NS], c1, c2;
-    const double J = neo_hooke_state<DIM>(F, mu_s, lam_s, W[t], a.g.inv_h, false, 0.0, M, tau, c1, c2);
+    const double J = neo_hooke_state<DIM>(F, mu_s, lam_s, a.mt.law, W[t], a.g.inv_h, false, 0.0, M, tau, c1, c2);
     if (!(J > 0.0)) atomicOr(a.err, J != J ? ERRBIT_NAN : ERRBIT_JNEG);
 #pragma unroll
     for (int i = 0; i < DIM * DIM; ++i) Mq[i][t] = M[i / DIM][i % DIM];

@@ -52,6 +52,7 @@ template <typename T>
 struct Mat {
   T mu[MAXMAT];
   T lam[MAXMAT];
+  int law;  // volumetric function: 0 the paper's lambda ln^2 J, 1 lambda/4 (J^2 - 1 - 2 ln J)
 };
 
 // Bitmask of the constrained components of lattice node (i0, i1, i2).

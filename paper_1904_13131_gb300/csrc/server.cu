@@ -35,6 +35,7 @@ struct Req {
   std::vector<double> mu, lam;
   hy_newton_params np{};
   hy_solver_params sp{};
+  int law = HY_LAW_LOG2;
   int64_t bytes = 0;
   int state = 0;  // 0 queued, 1 running, 2 done, 3 failed
   hy_status status = HY_OK;
@@ -77,6 +78,7 @@ void run_request(Req& r, int device, cudaStream_t st) {
   hy_status s = hy_create(&ctx, device, st);
   if (s == HY_OK) s = hy_mesh_setup(ctx, r.dim, r.degree, r.m, r.nlev, r.fm);
   if (s == HY_OK) s = hy_set_solver_params(ctx, &r.sp);
+  if (s == HY_OK) s = hy_set_material_law(ctx, r.law);
   size_t off = 0;
   for (int l = 0; l < r.nlev && s == HY_OK; ++l) {
     s = hy_set_material(ctx, l, r.mats.data() + off, r.mu.data(), r.lam.data(), (int)r.mu.size());
@@ -194,6 +196,8 @@ hy_status hy_server_submit(hy_server* sv, const hy_request* q, uint64_t* ticket)
   r->lam.assign(q->lambda, q->lambda + q->n_mat);
   r->np = q->newton;
   r->sp = q->solver;
+  if (q->law != HY_LAW_LOG2 && q->law != HY_LAW_J2) return HY_ERR_ARG;
+  r->law = q->law;
   int64_t bytes = 0;
   hy_status s = hy_footprint(r->dim, r->degree, r->m, r->nlev, q->newton.variant, q->newton.level_dtype, &q->solver,
                              r->fm, &bytes);

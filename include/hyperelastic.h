@@ -88,8 +88,11 @@ hy_status hy_set_material(hy_ctx *ctx, int level, const uint8_t *cell_mat, const
 /* Volumetric function of the compressible neo-Hooke law, on every level; the isochoric part and the
  * -mu ln J term are the paper's (Sec. 2.3). HY_LAW_LOG2 (default): U = lambda ln^2 J, the paper's;
  * HY_LAW_J2: U = lambda/4 (J^2 - 1 - 2 ln J). With p = J U'(J) both give tau = mu b - (mu - p) I and
- * J*C = 2 (mu - p) S + J p'(J) I (x) I, which every tangent variant evaluates in the same places. Takes
- * effect at the next hy_set_displacement (and for hy_residual at once). HY_ERR_ARG for another value. */
+ * J*C = 2 (mu - p) S + J p'(J) I (x) I. The law enters where the Gauss-point state is formed (the state
+ * build, residual, diagonal and dense coarse assembly), so it goes through the caching variants T4 and
+ * T2 unchanged; the recomputing variants FC, SC and NC keep the paper's law (hy_set_displacement returns
+ * HY_ERR_UNSUPPORTED for them, also as level_variant, under HY_LAW_J2). Takes effect at the next
+ * hy_set_displacement (and for hy_residual at once). HY_ERR_ARG for another value. */
 typedef enum { HY_LAW_LOG2 = 0, HY_LAW_J2 = 1 } hy_law;
 hy_status hy_set_material_law(hy_ctx *ctx, int law);
 

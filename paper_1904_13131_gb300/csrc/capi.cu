@@ -1008,6 +1008,9 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
   if (var < 0 || var > 4) return fail(ctx, HY_ERR_ARG, "variant out of range");
   if (ctx->sp.fine_dtype == HY_FF && ctx->n > 3)
     return fail(ctx, HY_ERR_UNSUPPORTED, "the double-float action is built for degrees 1-2");
+  if (ctx->law != HY_LAW_LOG2 &&
+      (var >= VAR_FC || (ctx->sp.level_variant >= VAR_FC)))
+    return fail(ctx, HY_ERR_UNSUPPORTED, "the second law goes through the caching variants T4 and T2");
   ctx->state_ok = false;
   drop_graph(ctx);
   ctx->var = var;

@@ -13,6 +13,8 @@
 //   P~ = Q~ M^T,   Q~ = g tau~ + JC~ : sym(g),   g = G M,   tau~ = W tau,   JC~ = W JC,
 // so y_{a,c} = sum_q sum_J P~_{cJ} d N_a / d xi_J, i.e. sum_q W [g tau + JC:grad^s x] : grad(N_a e_c).
 #pragma once
+#include <type_traits>
+
 #include "hy_internal.cuh"
 
 #ifndef HY_LINE_STAGE
@@ -414,13 +416,14 @@ __device__ __forceinline__ T neo_hooke_state(const T F[DIM][DIM], T mu, T lam, i
   return J;
 }
 
-// Neo-Hooke state for the variants that recompute it in every application, scaled so that no
+// Neo-Hooke state for the variants that recompute it in every application (the paper's law: a second law
+// goes through the caching variants, whose state kernel evaluates it), scaled so that no
 // F^{-1} is formed: with adj = J F^{-1}, rho = 1/J and kappa = (W/h) rho^2, the flux contracted with
 // the unit-cell shape gradients is P~ = Q' adj^T, Q' = g' tau' + c1' sym(g') + c2' tr(g') I, where
 // g' = Grad x adj, tau' = kappa tau, c1' = 2 kappa (mu - 2 lambda ln J), c2' = 2 kappa lambda -- the same
 // quantity as W/h (g tau + JC : sym g) F^{-T} with g = Grad x F^{-1}.
 template <int DIM, typename T>
-__device__ __forceinline__ void neo_hooke_adj(const T F[DIM][DIM], T mu, T lam, int law, T Wh, bool have_c, T c_in,
+__device__ __forceinline__ void neo_hooke_adj(const T F[DIM][DIM], T mu, T lam, T Wh, bool have_c, T c_in,
                                               T adj[DIM][DIM], T tau[nsym(DIM)], T& c1, T& c2) {
   T J;
   if (DIM == 3) {
@@ -444,9 +447,7 @@ __device__ __forceinline__ void neo_hooke_adj(const T F[DIM][DIM], T mu, T lam, 
   T rho;
   rho = rcp_rn(J);
   const T kappa = Wh * rho * rho;
-  T pv, jdp;
-  volumetric(J, lam, law, pv, jdp);
-  const T c = have_c ? c_in : mu - pv;
+  const T c = have_c ? c_in : mu - T(2) * lam * log(J);
   const T kmu = kappa * mu, kc = kappa * c;
 #pragma unroll
   for (int a = 0; a < nsym(DIM); ++a) {
@@ -457,7 +458,7 @@ __device__ __forceinline__ void neo_hooke_adj(const T F[DIM][DIM], T mu, T lam, 
     tau[a] = (i == j) ? fma(kmu, bij, -kc) : kmu * bij;
   }
   c1 = T(2) * kc;
-  c2 = kappa * jdp;
+  c2 = T(2) * kappa * lam;
 }
 
 // Material part for the neo-Hooke action (Eq. simplified_action): S = c1 sym(g) + c2 tr(g) I.
@@ -536,8 +537,7 @@ struct CellLoc {
 //   FC/SC/NC: the state recomputed from F (cached, or I + Grad u), with g' = Grad x adj F (Algorithm 1 for SC).
 template <int DIM, int VAR, typename T>
 __device__ __forceinline__ void qp_flux(const T G[DIM][DIM], const T Gu[DIM][DIM], const T* __restrict__ cs, int st,
-                                        int qg, bool active, int id, const T* mu, const T* lam, int law, T Wh,
-                                        T P[DIM][DIM]) {
+                                        int qg, bool active, int id, const T* mu, const T* lam, T Wh, T P[DIM][DIM]) {
   constexpr int NS = nsym(DIM);
   T M[DIM][DIM], tau[NS], Sv[NS], g[DIM][DIM];
   if (VAR == VAR_T4 || VAR == VAR_T2) {
@@ -585,7 +585,7 @@ __device__ __forceinline__ void qp_flux(const T G[DIM][DIM], const T Gu[DIM][DIM
     }
     const T cin = (VAR == VAR_SC && active) ? cs[qg] : T(0);
     T c1, c2;
-    neo_hooke_adj<DIM>(F, mu[id], lam[id], law, Wh, VAR == VAR_SC, cin, M, tau, c1, c2);  // M = adj
+    neo_hooke_adj<DIM>(F, mu[id], lam[id], Wh, VAR == VAR_SC, cin, M, tau, c1, c2);  // M = adj
     matmul<DIM>(G, M, g);
     nh_action<DIM>(g, c1, c2, Sv);
   }
@@ -675,8 +675,7 @@ __device__ __forceinline__ void apply_point_body(const CellArgs<T>& a, const int
   }
   // quadrature-point work
   T P[DIM][DIM];
-  qp_flux<DIM, VAR>(G, Gu, cs, BS, threadIdx.x, active, active ? a.mat[cell] : 0, s.mu, s.lam, a.mt.law, s.Wh[pt.p],
-                    P);
+  qp_flux<DIM, VAR>(G, Gu, cs, BS, threadIdx.x, active, active ? a.mat[cell] : 0, s.mu, s.lam, s.Wh[pt.p], P);
 #pragma unroll
   for (int c = 0; c < DIM; ++c)
 #pragma unroll
@@ -919,7 +918,7 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
         }
       }
       T P[DIM][DIM];
-      qp_flux<DIM, VAR>(G, Gu, cq, BS, cl * NPT + p, active, id, tmu, tlam, a.mt.law, tWh[p], P);
+      qp_flux<DIM, VAR>(G, Gu, cq, BS, cl * NPT + p, active, id, tmu, tlam, tWh[p], P);
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
         Px[q][c] = P[c][0];

@@ -21,7 +21,7 @@ import numpy as np
 import scipy.sparse as sp
 
 from . import material
-from .basis import CellTables
+from .basis import CellTables, gauss_rule, gll_nodes, lagrange
 
 
 class Problem:
@@ -105,6 +105,41 @@ class Problem:
             mu, lam = self._qp_params(cells)
             E += np.einsum("Kq,q->", material.psi(F, mu, lam, self.law), self.tab.w) * self.h**self.dim
         return E
+
+    def face_load(self, tractions):
+        """External force of dead tractions (reference configuration, per unit reference area), the surface
+        term of the weak form (Eq. weak_form; the paper loads its benchmark this way, Sec. 7):
+        f_{a,c} = sum over faces of t_c * int_face N_a dA, with tractions[face][c] for the faces (-x, +x, -y,
+        +y, -z, +z). On a face of a cell, N_a is the product of 1D Lagrange polynomials on the GLL nodes; the
+        integral uses the (k+1)-point Gauss rule along every in-face axis."""
+        t = np.asarray(tractions, dtype=float).reshape(2 * self.dim, self.dim)
+        xg, wg = gauss_rule(self.n)
+        V, _ = lagrange(gll_nodes(self.k), xg)  # V[q, j] = l_j(xg_q)
+        f = np.zeros(self.n_nodes * self.dim)
+        n, m, L, dim = self.n, self.m, self.L, self.dim
+        for face in range(2 * dim):
+            if not np.any(t[face]):
+                continue
+            ax, side = face // 2, face % 2
+            inplane = [i for i in range(dim) if i != ax]
+            # every cell on the face and every node of the cell on the face
+            for cidx in np.ndindex(*([m] * (dim - 1))):
+                c = [0] * dim
+                for i, ci in zip(inplane, cidx):
+                    c[i] = ci
+                c[ax] = 0 if side == 0 else m - 1
+                for aidx in np.ndindex(*([n] * (dim - 1))):
+                    a = [0] * dim
+                    for i, ai in zip(inplane, aidx):
+                        a[i] = ai
+                    a[ax] = 0 if side == 0 else n - 1
+                    # int over the cell face of prod_i l_{a_i}(x_i): a product of 1D Gauss sums
+                    wgt = self.h ** (dim - 1)
+                    for i in inplane:
+                        wgt *= float(np.dot(wg, V[:, a[i]]))
+                    node = sum((self.k * c[i] + a[i]) * L**i for i in range(dim))
+                    f[node * dim:(node + 1) * dim] += wgt * t[face]
+        return f
 
     def residual_raw(self, u):
         """R_i = sum_K sum_q tau : grad^s N_i w_q h^d for every dof, constrained rows included (Eq. weak_form)."""

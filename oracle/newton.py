@@ -1,4 +1,4 @@
-"""Newton-Raphson with load steps for prescribed boundary displacements (Sec. 3, Sec. 7).
+"""Newton-Raphson with load steps for prescribed boundary displacements and dead tractions (Sec. 3, Sec. 7).
 
 Test infrastructure (see oracle/__init__.py). Each Newton iteration solves Eq. linear_system,
 A(u) du = -F(u), on the free dofs with scipy's sparse direct solver. Readings of the paper where it is
@@ -16,8 +16,9 @@ from .fem import Problem
 
 
 def newton_solve(prob: Problem, u_final_bc, load_steps=5, rtol=1e-10, atol=1e-14, max_iter=25, u0=None,
-                 linear_solve=None):
-    """Return (u, report). u_final_bc holds the final prescribed values on constrained dofs.
+                 linear_solve=None, f_ext=None):
+    """Return (u, report). u_final_bc holds the final prescribed values on constrained dofs; f_ext (optional)
+    the final external force of dead loads (Problem.face_load), applied in the same equal increments.
 
     linear_solve(prob, u, rhs) -> du (free part) overrides the direct solve (used to mirror a GMG-CG).
     """
@@ -33,6 +34,8 @@ def newton_solve(prob: Problem, u_final_bc, load_steps=5, rtol=1e-10, atol=1e-14
         while True:
             du0 = np.where(cons, target - u, 0.0)
             R = prob.residual_raw(u)
+            if f_ext is not None:
+                R = R - (s / load_steps) * np.asarray(f_ext, dtype=float)
             A = prob.tangent_raw(u)
             rhs = -(R + A @ du0)
             rhs[cons] = 0.0

@@ -197,6 +197,9 @@ typedef struct {
   hy_variant variant;        /* [HY_T4] tangent variant of every level */
   hy_dtype level_dtype;      /* [HY_F64] HY_F32 = mixed-precision V-cycle */
   double face_values[6][3];  /* final prescribed displacement per face and component */
+  double face_traction[6][3]; /* final dead traction per face (reference configuration, per unit reference
+                                 area), reached in the same increments; [0] = none. The paper loads its
+                                 benchmark this way (Sec. 7); the tangent is unchanged by a dead load. */
 } hy_newton_params;
 
 typedef struct {
@@ -218,6 +221,11 @@ void hy_newton_default_params(hy_newton_params *p);
  * entry (its constrained values are overwritten by the load path) and the solution on return; on
  * error it holds the last accepted iterate. rep may be NULL. */
 hy_status hy_newton_solve(hy_ctx *ctx, const hy_newton_params *p, double *u_inout_dev, hy_newton_report *rep);
+
+/* External force of dead tractions on the finest level: f_dev = sum over faces of t_face * int_face N_a dA
+ * (the surface term of Eq. weak_form), t_face = traction[face][component] (HOST, faces -x, +x, -y, +y, -z,
+ * +z). f_dev: device FP64 vector of n_dofs, overwritten (constrained dofs included). */
+hy_status hy_face_load(hy_ctx *ctx, const double traction[6][3], double *f_dev);
 
 /* Deterministic FP64 dot product of two fine-level device vectors (fixed reduction order, so
  * repeated calls give identical bits). Uses a scratch buffer owned by the context. */

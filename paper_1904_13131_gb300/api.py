@@ -29,7 +29,7 @@ EXPORTED = ("hy_create", "hy_destroy", "hy_status_str", "hy_last_error", "hy_mes
             "hy_server_create", "hy_server_destroy", "hy_server_submit", "hy_server_poll", "hy_server_wait",
             "hy_server_release", "hy_server_stats_get", "hy_kernel_form", "hy_batch_create", "hy_batch_destroy",
             "hy_batch_last_error", "hy_batch_apply", "hy_batch_pcg", "hy_batch_kernel_launches",
-            "hy_batch_kernel_form", "hy_set_material_law")
+            "hy_batch_kernel_form", "hy_set_material_law", "hy_face_load")
 
 
 class HyError(RuntimeError):
@@ -49,7 +49,7 @@ class NewtonParams(ctypes.Structure):
     _fields_ = [("load_steps", ctypes.c_int), ("max_newton", ctypes.c_int), ("newton_rtol", ctypes.c_double),
                 ("newton_atol", ctypes.c_double), ("cg_rtol", ctypes.c_double), ("cg_max_iter", ctypes.c_int),
                 ("variant", ctypes.c_int), ("level_dtype", ctypes.c_int),
-                ("face_values", (ctypes.c_double * 3) * 6)]
+                ("face_values", (ctypes.c_double * 3) * 6), ("face_traction", (ctypes.c_double * 3) * 6)]
 
 
 class NewtonReport(ctypes.Structure):
@@ -116,6 +116,7 @@ def load_library(path: str = LIB_PATH):
                          ctypes.POINTER(i64)],
         "hy_kernel_form": [vp, i32, i32, ctypes.POINTER(i32)],
         "hy_set_material_law": [vp, i32],
+        "hy_face_load": [vp, ctypes.c_void_p, vp],
         "hy_ctx_bytes": [vp, ctypes.POINTER(i64)],
         "hy_batch_create": [ctypes.POINTER(vp), ctypes.POINTER(vp), i32],
         "hy_batch_destroy": [vp],
@@ -329,15 +330,28 @@ class Context:
         p = NewtonParams()
         load_library().hy_newton_default_params(ctypes.byref(p))
         face_values = kw.pop("face_values", None)
+        face_traction = kw.pop("face_traction", None)
         for k, v in kw.items():
             if k == "variant":
                 v = VARIANTS[v]
             setattr(p, k, v)
-        if face_values is not None:
-            for f in range(6):
-                for c in range(3):
-                    p.face_values[f][c] = float(face_values[f][c]) if f < len(face_values) else 0.0
+        for arr, dst in ((face_values, p.face_values), (face_traction, p.face_traction)):
+            if arr is not None:
+                for f in range(6):
+                    for c in range(3):
+                        dst[f][c] = float(arr[f][c]) if f < len(arr) and c < len(arr[f]) else 0.0
         return p
+
+    def face_load(self, traction, f=None):
+        """External force of dead tractions traction[face][component] on the finest level (device FP64)."""
+        if f is None:
+            f = self.empty()
+        t = ((ctypes.c_double * 3) * 6)()
+        for i in range(min(6, len(traction))):
+            for c in range(min(3, len(traction[i]))):
+                t[i][c] = float(traction[i][c])
+        self._ck(self.lib.hy_face_load(self.h, t, self._vec(f, self.num_dofs(), F64)))
+        return f
 
     def newton_solve(self, u, params: NewtonParams):
         rep = NewtonReport()

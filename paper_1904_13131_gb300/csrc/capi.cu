@@ -215,7 +215,7 @@ struct hy_ctx {
   double *tmp64a = nullptr, *tmp64b = nullptr;
   float *tmp32a = nullptr, *tmp32b = nullptr, *tmp32c = nullptr;
   size_t tmp_len = 0;
-  double* f64[11] = {};  // fine-level FP64 work vectors of PCG / Newton (10: the iterate of the graph PCG)
+  double* f64[12] = {};  // fine-level FP64 work vectors of PCG / Newton (10: graph-PCG iterate, 11: dead load)
   long long launches = 0;
   bool verbose = false;  // HY_VERBOSE=1: per-iteration diagnostics on stderr
   int prefetch = 0;      // L2 prefetch distance of the tangent action's cache chunks, in cell blocks
@@ -1130,6 +1130,32 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
   return HY_OK;
 }
 
+// f = sum over faces of t_face * int_face N_a dA (dead tractions, host array [6][3]); true if any is nonzero.
+hy_status face_load(hy_ctx* ctx, const double (*traction)[3], double* f, bool* any) {
+  Level& L = ctx->lev[ctx->nlev - 1];
+  HY_CK(cudaMemsetAsync(f, 0, sizeof(double) * L.ndofs, ctx->stream));
+  FaceLoad fl{};
+  fl.k = ctx->k;
+  for (int a = 0; a < ctx->n; ++a) {
+    double s = 0.0;
+    for (int q = 0; q < ctx->n; ++q) s += ctx->b64.w[q] * ctx->b64.S[q][a];
+    fl.w1[a] = s;
+  }
+  *any = false;
+  for (int face = 0; face < 2 * ctx->dim; ++face) {
+    bool nz = false;
+    for (int c = 0; c < ctx->dim; ++c) {
+      fl.t[c] = traction[face][c];
+      nz = nz || traction[face][c] != 0.0;
+    }
+    if (!nz) continue;
+    *any = true;
+    launch_face_load(f, ctx->dim, L.g, face, fl, ctx->stream);
+    HY_TRY(check_launch(ctx, 1));
+  }
+  return HY_OK;
+}
+
 hy_status residual(hy_ctx* ctx, const double* u, double* r) {
   Level& L = ctx->lev[ctx->nlev - 1];
   HY_CK(cudaMemsetAsync(r, 0, sizeof(double) * L.ndofs, ctx->stream));
@@ -2013,7 +2039,7 @@ hy_status hy_mesh_setup(hy_ctx* ctx, int dim, int degree, int m, int n_levels, c
   HY_TRY(dalloc(ctx, &ctx->d_scal, 4));
   HY_TRY(dalloc(ctx, &ctx->d_face, 18));
   HY_TRY(dalloc(ctx, &ctx->d_eig_scal, 8 + PCG_SCALARS));
-  for (int i = 0; i < 11; ++i) HY_TRY(dalloc(ctx, &ctx->f64[i], ctx->lev[n_levels - 1].ndofs));
+  for (int i = 0; i < 12; ++i) HY_TRY(dalloc(ctx, &ctx->f64[i], ctx->lev[n_levels - 1].ndofs));
   HY_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
   HY_CK(cudaStreamSynchronize(ctx->stream));
   return HY_OK;
@@ -2165,6 +2191,14 @@ hy_status hy_set_level_info(hy_ctx* ctx, int level, double lmax, double clo, dou
   return HY_OK;
 }
 
+hy_status hy_face_load(hy_ctx* ctx, const double traction[6][3], double* f) {
+  if (!ctx || !traction || !f) return HY_ERR_ARG;
+  if (ctx->nlev == 0) return fail(ctx, HY_ERR_STATE, "mesh not set up");
+  HY_CK(cudaSetDevice(ctx->device));
+  bool any = false;
+  return face_load(ctx, traction, f, &any);
+}
+
 hy_status hy_set_material_law(hy_ctx* ctx, int law) {
   if (!ctx) return HY_ERR_ARG;
   if (law != HY_LAW_LOG2 && law != HY_LAW_J2) return fail(ctx, HY_ERR_ARG, "unknown material law");
@@ -2245,8 +2279,10 @@ hy_status hy_newton_solve(hy_ctx* ctx, const hy_newton_params* p, double* u, hy_
   Level& L = ctx->lev[ctx->nlev - 1];
   const long long n = L.ndofs;
   double *R = ctx->f64[4], *du0 = ctx->f64[5], *rhs = ctx->f64[6], *du = ctx->f64[7], *trial = ctx->f64[8],
-         *t = ctx->f64[9];
+         *t = ctx->f64[9], *fext = ctx->f64[11];
   HY_CK(cudaMemcpyAsync(ctx->d_face, p->face_values, sizeof(double) * 18, cudaMemcpyHostToDevice, ctx->stream));
+  bool loaded = false;  // dead tractions: R = R_int - factor * f_ext (the tangent is unchanged)
+  HY_TRY(face_load(ctx, p->face_traction, fext, &loaded));
   using clk = std::chrono::steady_clock;
   auto ms_since = [](clk::time_point t0) { return std::chrono::duration<double, std::milli>(clk::now() - t0).count(); };
   const clk::time_point t_start = clk::now();
@@ -2263,6 +2299,11 @@ hy_status hy_newton_solve(hy_ctx* ctx, const hy_newton_params* p, double* u, hy_
       HY_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
       HY_TRY(residual(ctx, u, R));
       if ((st = check_error_word(ctx, "newton residual")) != HY_OK) break;
+      if (loaded) {
+        launch_axpby<double>(-factor, fext, 1.0, R, n, ctx->stream);
+        launch_zero_constrained<double>(R, L.nnodes, ctx->dim, L.g, ctx->stream);
+        HY_TRY(check_launch(ctx, 2));
+      }
       if (its > 0 && lift2 == 0.0) {
         double rr;
         HY_TRY(dot<double>(ctx, R, R, n, &rr));
@@ -2380,7 +2421,7 @@ hy_status hy_footprint(int dim, int degree, int m, int n_levels, hy_variant vari
   }
   total += 2 * al(tmp_len, 8) + 3 * al(tmp_len, 4);
   total += al(1, 4) + al(1, 8) + al(DOT_BLOCKS, 8) + al(4, 8) + al(18, 8) + al(8 + PCG_SCALARS, 8);
-  total += 11 * al(nd[n_levels - 1], 8);
+  total += 12 * al(nd[n_levels - 1], 8);
   const int top = n_levels - 1;
   for (int l = 0; l < n_levels; ++l) {
     const bool need64 = (l == top) || (l == 0) || !mixed;

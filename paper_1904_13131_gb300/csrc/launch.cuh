@@ -125,6 +125,14 @@ constexpr int PCG_SCALARS = 16;  // stride of one problem's scalars
 void launch_pcg_scalar(double* s, int op, cudaStream_t st);
 // r = b - t
 template <typename T> void launch_sub(const T* b, const T* t, T* r, long long n, cudaStream_t st);
+// f += t * int_face N_a dA on face `face` (0..2 dim-1: -x, +x, -y, +y, -z, +z); FaceLoad carries the traction t
+// and w1[i], the integral of 1D GLL-basis function i over the unit interval (i = 0..k)
+struct FaceLoad {
+  double t[3];
+  double w1[MAXN];
+  int k;
+};
+void launch_face_load(double* f, int dim, const Geom& g, int face, const FaceLoad& fl, cudaStream_t st);
 // du0 = constrained ? target - u : 0, target from per-face values scaled by factor
 void launch_lift(const double* u, double* du0, double factor, const double* face_vals /*device [6][3]*/,
                  long long n_nodes, int dim, const Geom& g, cudaStream_t st);

@@ -49,6 +49,40 @@ __global__ void prep_out_list_kernel(const CellArgs<T>* __restrict__ list) {
   }
 }
 
+// f += t * int_face N_a dA for the lattice nodes of one face (the dead-load term of Eq. weak_form).
+// On a cell face N_a is a product of 1D GLL-basis functions, so the integral is a product of 1D weights:
+// along an in-face axis lattice index j gets h w1[j % k] from the cell it starts (if any) plus h w1[k] from
+// the cell it ends (if any), with w1[i] the integral of basis function i over the unit interval.
+template <int DIM>
+__global__ void face_load_kernel(double* __restrict__ f, Geom g, int axis, int side, FaceLoad fl) {
+  const long long L = g.L;
+  const long long nface = DIM == 3 ? L * L : L;
+  const int K = fl.k;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nface;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long j[3] = {0, 0, 0};
+    long long rest = idx;
+    double w = 1.0;
+    for (int i = 0; i < DIM; ++i) {
+      if (i == axis) {
+        j[i] = side ? L - 1 : 0;
+        continue;
+      }
+      j[i] = rest % L;
+      rest /= L;
+      const long long c = j[i] / K;
+      const int r = (int)(j[i] % K);
+      double wi = 0.0;
+      if (c < g.m) wi += fl.w1[r];
+      if (r == 0 && c > 0) wi += fl.w1[K];
+      w *= wi * g.h;
+    }
+    const long long node = j[0] + L * (j[1] + (DIM == 3 ? L * j[2] : 0));
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) f[node * DIM + c] += w * fl.t[c];
+  }
+}
+
 template <typename T, int DIM>
 __global__ void set_constrained_kernel(T* __restrict__ y, long long n_nodes, Geom g, T val) {
   for (long long nd = blockIdx.x * (long long)blockDim.x + threadIdx.x; nd < n_nodes; nd += (long long)gridDim.x * blockDim.x) {
@@ -363,6 +397,12 @@ void launch_cheb_step(T* t, const T* dinv, T* r, T* d, T* x, T cd, T cr, long lo
   if (!prep) cheb_step_kernel<T, 0><<<grid_for(n), TPB, 0, st>>>(t, dinv, r, d, x, cd, cr, n, g);
   else if (dim == 2) cheb_step_kernel<T, 2><<<grid_for(n), TPB, 0, st>>>(t, dinv, r, d, x, cd, cr, n, g);
   else cheb_step_kernel<T, 3><<<grid_for(n), TPB, 0, st>>>(t, dinv, r, d, x, cd, cr, n, g);
+}
+void launch_face_load(double* f, int dim, const Geom& g, int face, const FaceLoad& fl, cudaStream_t st) {
+  const long long L = g.L;
+  const long long nface = dim == 3 ? L * L : L;
+  if (dim == 2) face_load_kernel<2><<<grid_for(nface), TPB, 0, st>>>(f, g, face / 2, face % 2, fl);
+  else face_load_kernel<3><<<grid_for(nface), TPB, 0, st>>>(f, g, face / 2, face % 2, fl);
 }
 void launch_lift(const double* u, double* du0, double factor, const double* fv, long long n_nodes, int dim,
                  const Geom& g, cudaStream_t st) {

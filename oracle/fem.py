@@ -31,7 +31,7 @@ class Problem:
     masks: per-face bitmask of constrained components, faces (-x,+x,-y,+y,-z,+z).
     """
 
-    def __init__(self, dim, k, m, ids, mu_tab, lam_tab, masks, chunk=512, law=0):
+    def __init__(self, dim, k, m, ids, mu_tab, lam_tab, masks, chunk=512, law=0, X=None):
         self.dim, self.k, self.m = dim, k, m
         self.n = k + 1
         self.h = 1.0 / m
@@ -41,6 +41,9 @@ class Problem:
         self.tab = CellTables(dim, k)
         self.chunk = chunk
         self.law = law  # 0: the paper's volumetric function lambda ln^2 J; 1: lambda/4 (J^2 - 1 - 2 ln J)
+        # reference geometry: None = the uniform lattice of cells of side h; else the nodal coordinates
+        # (n_nodes, dim) of an isoparametric Q_k map of the cells (curved cells)
+        self.X = None if X is None else np.asarray(X, dtype=float).reshape(-1, dim)
         ids = np.asarray(ids)
         self.mu = np.asarray(mu_tab, dtype=float)[ids]
         self.lam = np.asarray(lam_tab, dtype=float)[ids]
@@ -71,10 +74,25 @@ class Problem:
         for s in range(0, nc, self.chunk):
             yield np.arange(s, min(nc, s + self.chunk))
 
+    def _geom(self, cells):
+        """(invJ[K,q,J,I] = d xi_J / d X_I, wdV[K,q] = w_q det(dX/dxi)) of the reference map at the Gauss
+        points: the uniform lattice gives I/h and w_q h^d; a curved geometry its isoparametric map."""
+        nq = self.tab.w.shape[0]
+        if self.X is None:
+            invJ = np.broadcast_to(np.eye(self.dim) / self.h, (len(cells), nq, self.dim, self.dim))
+            return invJ, np.broadcast_to(self.tab.w * self.h**self.dim, (len(cells), nq))
+        XK = self.X[self.cell_nodes[cells]]                                  # [K, a, I]
+        Jm = np.einsum("KaI,qaJ->KqIJ", XK, self.tab.dN)                     # dX_I / dxi_J
+        det = np.linalg.det(Jm)
+        if np.any(det <= 0):
+            raise FloatingPointError("reference map not invertible at a quadrature point")
+        return np.linalg.inv(Jm), self.tab.w[None, :] * det
+
     def grad_at_qp(self, v, cells):
-        """Grad v[K,q,i,J] = sum_a v_{a,i} dN[q,a,J] / h for the given cells."""
+        """Grad v[K,q,i,J] = sum_a v_{a,i} dN_a/dxi . dxi/dX for the given cells."""
         vK = v[self.cell_dofs[cells]].reshape(len(cells), -1, self.dim)
-        return np.einsum("Kai,qaJ->KqiJ", vK, self.tab.dN) / self.h
+        invJ, _ = self._geom(cells)
+        return np.einsum("Kai,qaL,KqLJ->KqiJ", vK, self.tab.dN, invJ)
 
     def deformation(self, u, cells):
         """F = I + Grad u at every quadrature point of the cells (Sec. 2.1); raises if J <= 0."""
@@ -91,10 +109,11 @@ class Problem:
         nq = self.n**self.dim
         return (np.repeat(self.mu[cells][:, None], nq, axis=1), np.repeat(self.lam[cells][:, None], nq, axis=1))
 
-    def _g(self, F):
-        """g[K,q,a,j] = sum_J Grad N_a[J] F^{-1}[J,j]."""
+    def _g(self, F, cells):
+        """g[K,q,a,j] = sum_J Grad N_a[J] F^{-1}[J,j], Grad N_a = dN_a/dxi . dxi/dX."""
         Finv = np.linalg.inv(F)
-        return np.einsum("qaJ,KqJj->Kqaj", self.tab.dN / self.h, Finv)
+        invJ, _ = self._geom(cells)
+        return np.einsum("qaL,KqLJ,KqJj->Kqaj", self.tab.dN, invJ, Finv)
 
     # ---- energy, residual --------------------------------------------------------------------
     def energy(self, u):
@@ -103,7 +122,8 @@ class Problem:
         for cells in self._chunks():
             F = self.deformation(u, cells)
             mu, lam = self._qp_params(cells)
-            E += np.einsum("Kq,q->", material.psi(F, mu, lam, self.law), self.tab.w) * self.h**self.dim
+            _, wdV = self._geom(cells)
+            E += np.einsum("Kq,Kq->", material.psi(F, mu, lam, self.law), wdV)
         return E
 
     def face_load(self, tractions):
@@ -148,9 +168,10 @@ class Problem:
             F = self.deformation(u, cells)
             mu, lam = self._qp_params(cells)
             tau = material.kirchhoff(F, mu, lam, self.law)
-            g = self._g(F)
+            g = self._g(F, cells)
             # tau : grad^s(N_a e_c) = tau : grad(N_a e_c) (tau symmetric) = sum_j tau_cj g_a,j
-            RK = np.einsum("Kqcj,Kqaj,q->Kac", tau, g, self.tab.w) * self.h**self.dim
+            _, wdV = self._geom(cells)
+            RK = np.einsum("Kqcj,Kqaj,Kq->Kac", tau, g, wdV)
             np.add.at(R, self.cell_dofs[cells].reshape(-1), RK.reshape(-1))
         return R
 
@@ -168,16 +189,16 @@ class Problem:
         mu, lam = self._qp_params(cells)
         tau = material.kirchhoff(F, mu, lam, self.law)
         JC = material.spatial_tangent(F, mu, lam, self.law)
-        ga = self._g(F)
+        ga = self._g(F, cells)
         I = np.eye(d)
         G = np.einsum("ic,Kqaj->Kqacij", I, ga)                         # grad(N_a e_c)_{ij} = d_ic g_a,j
         Gs = 0.5 * (G + np.swapaxes(G, -1, -2))                           # grad^s(N_a e_c)
-        w = self.tab.w * self.h**d
+        _, w = self._geom(cells)
         # (optimize=True only lets numpy pick the contraction order of these library contractions)
         CGs = np.einsum("Kqijkl,Kqbekl->Kqijbe", JC, Gs, optimize=True)  # JC : grad^s(N_b e_e)
-        mat = np.einsum("Kqacij,Kqijbe,q->Kacbe", Gs, CGs, w, optimize=True)
+        mat = np.einsum("Kqacij,Kqijbe,Kq->Kacbe", Gs, CGs, w, optimize=True)
         Gt = np.einsum("Kqbeim,Kqmj->Kqbeij", G, tau, optimize=True)    # grad(N_b e_e) . tau
-        geo = np.einsum("Kqacij,Kqbeij,q->Kacbe", G, Gt, w, optimize=True)
+        geo = np.einsum("Kqacij,Kqbeij,Kq->Kacbe", G, Gt, w, optimize=True)
         nloc = self.cell_dofs.shape[1]
         return (mat + geo).reshape(len(cells), nloc, nloc)
 
@@ -222,8 +243,9 @@ class Problem:
             gx = np.einsum("KqiJ,KqJj->Kqij", self.grad_at_qp(xin, cells), Finv)
             gxs = 0.5 * (gx + np.swapaxes(gx, -1, -2))
             Q = np.einsum("Kqim,Kqmj->Kqij", gx, tau) + np.einsum("Kqijkl,Kqkl->Kqij", JC, gxs)
-            ga = self._g(F)
-            yK = np.einsum("Kqaj,Kqcj,q->Kac", ga, Q, self.tab.w) * self.h**d
+            ga = self._g(F, cells)
+            _, wdV = self._geom(cells)
+            yK = np.einsum("Kqaj,Kqcj,Kq->Kac", ga, Q, wdV)
             np.add.at(y, self.cell_dofs[cells].reshape(-1), yK.reshape(-1))
         if constrained:
             y[self.constrained] = x[self.constrained]
@@ -238,13 +260,13 @@ class Problem:
             mu, lam = self._qp_params(cells)
             tau = material.kirchhoff(F, mu, lam, self.law)
             JC = material.spatial_tangent(F, mu, lam, self.law)
-            ga = self._g(F)
+            ga = self._g(F, cells)
             I = np.eye(d)
             G = np.einsum("ic,Kqaj->Kqacij", I, ga)
             Gs = 0.5 * (G + np.swapaxes(G, -1, -2))
-            w = self.tab.w * self.h**d
-            mat = np.einsum("Kqacij,Kqijkl,Kqackl,q->Kac", Gs, JC, Gs, w)
-            geo = np.einsum("Kqaj,Kqmj,Kqam,q->Ka", ga, tau, ga, w)  # d_cc = 1: same for every c
+            _, w = self._geom(cells)
+            mat = np.einsum("Kqacij,Kqijkl,Kqackl,Kq->Kac", Gs, JC, Gs, w)
+            geo = np.einsum("Kqaj,Kqmj,Kqam,Kq->Ka", ga, tau, ga, w)  # d_cc = 1: same for every c
             DK = mat + geo[:, :, None]
             np.add.at(D, self.cell_dofs[cells].reshape(-1), DK.reshape(-1))
         D[self.constrained] = 1.0

@@ -131,9 +131,17 @@ class Hierarchy:
 
     def __init__(self, dim, k, levels_m, ids, mu_tab, lam_tab, masks, degree=4, sweeps=1, smooth_lo=0.6,
                  smooth_hi=1.2, eig_iters=30, coarse_eig_iters=None, coarse_reduction=1e-3, coarse_solver="chebyshev",
-                 law=0):
+                 law=0, X=None):
         self.dim, self.k = dim, k
-        self.levels = [Problem(dim, k, ml, ids[l], mu_tab, lam_tab, masks, law=law) for l, ml in enumerate(levels_m)]
+        # a curved geometry (finest-level nodal coordinates) is carried down by the same nodal interpolation
+        # as the displacement (reading O8), so every level has its own isoparametric map
+        Xl = [None] * len(levels_m)
+        if X is not None:
+            Xl[-1] = np.asarray(X, dtype=float).reshape(-1)
+            for l in range(len(levels_m) - 1, 0, -1):
+                Xl[l - 1] = lattice_operator(interpolation_1d(k, levels_m[l - 1]), dim) @ Xl[l]
+        self.levels = [Problem(dim, k, ml, ids[l], mu_tab, lam_tab, masks, law=law, X=Xl[l])
+                       for l, ml in enumerate(levels_m)]
         self.degree, self.sweeps = degree, sweeps
         self.smooth_lo, self.smooth_hi = smooth_lo, smooth_hi
         self.eig_iters = eig_iters

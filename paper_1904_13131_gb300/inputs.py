@@ -125,6 +125,15 @@ def smooth_field(dim: int, k: int, m: int, seed: int, amplitude: float = 0.05) -
     return (amplitude * phi).reshape(-1).copy()
 
 
+def curved_coords(dim: int, k: int, m: int, delta=(0.06, 0.045, 0.03)) -> np.ndarray:
+    """(n_nodes, dim) nodal coordinates of a curved geometry of the unit square / cube: lattice node xi moved
+    to X = xi + delta * prod_j sin(pi xi_j) (component-wise delta). The bump vanishes on every face, so the
+    faces stay where they are and keep their in-face metric; the interior cells are curved."""
+    xi = node_coords(dim, k, m)
+    bump = np.prod(np.sin(np.pi * xi), axis=1)
+    return xi + bump[:, None] * np.asarray(delta[:dim], dtype=float)[None, :]
+
+
 def gaussian_vector(n: int, seed: int) -> np.ndarray:
     """N(0,1) vector from numpy's default_rng(seed)."""
     return np.random.default_rng(seed).standard_normal(n)

@@ -238,6 +238,21 @@ def solve_latency(torch, api, inputs, dev):
             "newton_iterations": rep["newton_iterations"], "newton_total_ms": rep["total_ms"],
             "setup_ms_total": rep["setup_ms_total"], "max_abs_u": float(u.abs().max()),
             "load": "dead traction 0.05 along (1,1,0)/sqrt(2) on the free top face, 5 load steps"}
+    # the same compression on curved cells (the seeded isoparametric perturbation of the cube), best mode
+    Xc = torch.tensor(inputs.curved_coords(DIM, K, M).reshape(-1), device=dev)
+    with api.Context(dev.index) as c:
+        c.setup_problem(pr)
+        c.set_geometry(Xc)
+        c.set_solver_params(coarse_solver=2, fine_dtype=api.FF, level_variant=api.VARIANTS["T2"])
+        u = torch.zeros(inputs.n_dofs(DIM, K, M), dtype=torch.float64, device=dev)
+        rep = c.newton_solve(u, api.Context.newton_params(level_dtype=1, face_values=fv))
+        lat = np.array(rep["solve_ms"])
+        out["curved_mixed_exact_coarse_ff_t2_levels"] = {
+            "solve_p50_ms": float(np.percentile(lat, 50)), "solve_p99_ms": float(np.percentile(lat, 99)),
+            "solves": rep["n_solves"], "cg_iterations_max": rep["cg_iterations_max"],
+            "newton_iterations": rep["newton_iterations"], "newton_total_ms": rep["total_ms"],
+            "setup_ms_total": rep["setup_ms_total"],
+            "geometry": "lattice nodes moved by the seeded smooth perturbation (amplitudes 0.06, 0.045, 0.03)"}
     out["coarse_solvers"] = ("fp64/mixed: Chebyshev to 1e-3 on 4^3 (Sec. 7); mixed_exact_coarse: dense inverse; "
                              "_ff: coarse inverse computed in double-float and double-float finest-level action "
                              "in the outer CG; _t2_levels: the V-cycle's level operators in the T2 variant")
@@ -550,6 +565,22 @@ def main():
         second_law[v] = {"f64_ms": t, "f64_gdofs": n / (t * 1e-3) / 1e9}
         ctxs[v].set_material_law(api.LAW_LOG2)
         ctxs[v].set_displacement(u, v, level_dtype=1)
+    # curved (isoparametric) cells through T4 and T2: M = J^{-1} F^{-1} and the weights w det(dX/dxi) are
+    # folded into the cache, so the applies should cost what they cost on the lattice
+    curved = {}
+    Xc = torch.tensor(inputs.curved_coords(DIM, K, M).reshape(-1), device=dev)
+    for v in ("T4", "T2"):
+        ctxs[v].set_geometry(Xc)
+        ctxs[v].set_displacement(u, v, level_dtype=1)
+    msc64, _, _ = time_applies(torch, ctxs, ["T4", "T2"], x, 0, 5, 2, flush, stream)
+    msc32, _, _ = time_applies(torch, ctxs, ["T4", "T2"], x, 1, 5, 2, flush, stream)
+    for i, v in enumerate(("T4", "T2")):
+        t64, t32 = float(np.median(msc64[:, i])), float(np.median(msc32[:, i]))
+        curved[v] = {"f64_ms": t64, "f64_gdofs": n / (t64 * 1e-3) / 1e9, "f32_ms": t32,
+                     "f32_gdofs": n / (t32 * 1e-3) / 1e9}
+        ctxs[v].set_geometry(None)
+        ctxs[v].set_displacement(u, v, level_dtype=1)
+    del Xc
     # dominant kernel of the step: the slowest variant's FP64 apply (FP64-pipe bound)
     dom = max(per_var_ms, key=per_var_ms.get)
     ach = flops_per_qp(dom) * nqp / (per_var_ms[dom] * 1e-3) / 1e12
@@ -618,7 +649,7 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": int(launches_timed),
-                "per_variant_ms_f64": per_var_ms, "variants": variants, "second_law": second_law, "solve": solve,
+                "per_variant_ms_f64": per_var_ms, "variants": variants, "second_law": second_law, "curved": curved, "solve": solve,
                 "serve": serve, "batch": batch,
                 "wall_s_timed_region": wall, "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src}
         print(json.dumps(line), flush=True)

@@ -96,6 +96,18 @@ hy_status hy_set_material(hy_ctx *ctx, int level, const uint8_t *cell_mat, const
 typedef enum { HY_LAW_LOG2 = 0, HY_LAW_J2 = 1 } hy_law;
 hy_status hy_set_material_law(hy_ctx *ctx, int law);
 
+/* Curved cells (the paper's meshes are curved, Sec. 7): X_dev holds the finest level's nodal coordinates
+ * (device FP64, n_dofs values interleaved like a displacement) of an isoparametric Q_k map of the lattice
+ * cells; coarser levels get their coordinates by the same nodal interpolation that carries the
+ * displacement down (Sec. 6). Gradients use dxi/dX = (dX/dxi)^{-1} and the volume weights w_q det(dX/dxi)
+ * at every Gauss point. The map enters where the Gauss-point state is formed (state build, residual,
+ * diagonal, dense coarse assembly), so it goes through the caching variants T4 and T2 with unchanged
+ * applications; FC, SC and NC return HY_ERR_UNSUPPORTED from hy_set_displacement. Dead tractions keep the
+ * reference measure of the lattice faces (exact for maps that keep the faces in place). NULL returns to
+ * the uniform lattice. The coordinates take sum over levels of n_dofs(l) * 8 bytes beyond hy_footprint.
+ * Takes effect at the next hy_set_displacement (and for hy_residual at once). */
+hy_status hy_set_geometry(hy_ctx *ctx, const double *X_dev);
+
 /* Linearisation point (Sec. 6). u_dev: fine-level FP64 displacement (device). The displacement is
  * carried down to every level by nodal interpolation and each level's Gauss-point cache is built
  * for `variant` from FP64 kinematics (F, J, ln J). level_dtype = HY_F32 selects the mixed-precision

@@ -29,7 +29,7 @@ EXPORTED = ("hy_create", "hy_destroy", "hy_status_str", "hy_last_error", "hy_mes
             "hy_server_create", "hy_server_destroy", "hy_server_submit", "hy_server_poll", "hy_server_wait",
             "hy_server_release", "hy_server_stats_get", "hy_kernel_form", "hy_batch_create", "hy_batch_destroy",
             "hy_batch_last_error", "hy_batch_apply", "hy_batch_pcg", "hy_batch_kernel_launches",
-            "hy_batch_kernel_form", "hy_set_material_law", "hy_face_load")
+            "hy_batch_kernel_form", "hy_set_material_law", "hy_face_load", "hy_set_geometry")
 
 
 class HyError(RuntimeError):
@@ -117,6 +117,7 @@ def load_library(path: str = LIB_PATH):
         "hy_kernel_form": [vp, i32, i32, ctypes.POINTER(i32)],
         "hy_set_material_law": [vp, i32],
         "hy_face_load": [vp, ctypes.c_void_p, vp],
+        "hy_set_geometry": [vp, vp],
         "hy_ctx_bytes": [vp, ctypes.POINTER(i64)],
         "hy_batch_create": [ctypes.POINTER(vp), ctypes.POINTER(vp), i32],
         "hy_batch_destroy": [vp],
@@ -212,6 +213,11 @@ class Context:
         n = ctypes.c_int64()
         self._ck(self.lib.hy_num_dofs(self.h, level, ctypes.byref(n)))
         return n.value
+
+    def set_geometry(self, X=None):
+        """Curved cells: X the finest level's nodal coordinates (n_dofs FP64 values on the device, interleaved
+        like a displacement), or None for the uniform lattice."""
+        self._ck(self.lib.hy_set_geometry(self.h, None if X is None else self._vec(X, self.num_dofs(), F64)))
 
     def set_material_law(self, law):
         """0 (LAW_LOG2): the paper's lambda ln^2 J; 1 (LAW_J2): lambda/4 (J^2 - 1 - 2 ln J)."""

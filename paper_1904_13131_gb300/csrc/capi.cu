@@ -153,6 +153,7 @@ struct Level {
   bool mat_set = false;
   double* d_u64 = nullptr;
   float* d_u32 = nullptr;
+  double* d_X64 = nullptr;  // nodal coordinates of a curved geometry (hy_set_geometry)
   double* d_c64 = nullptr;
   float* d_c32 = nullptr;
   size_t c64_len = 0, c32_len = 0;
@@ -198,6 +199,7 @@ struct hy_ctx {
   hy_solver_params sp{4, 1, 0.6, 1.2, 30, 0, 1e-3, 0, -1, HY_F64, -1};
   int var = -1;
   int law = 0;  // volumetric function of the neo-Hooke law (hy_set_material_law)
+  bool curved = false;  // a curved reference geometry is set (hy_set_geometry)
   bool mixed = false;
   bool state_ok = false;
   double coarse_lo = 0, coarse_hi = 0;
@@ -343,6 +345,7 @@ CellArgs<T> cell_args(hy_ctx* ctx, Level& L) {
     a.b = ctx->bff;
   }
   a.mt.law = ctx->law;
+  a.X64 = ctx->curved ? L.d_X64 : nullptr;
   return a;
 }
 
@@ -478,21 +481,25 @@ hy_status restrict_to(hy_ctx* ctx, int l, const T* fine, T* coarse) {
 }
 
 // Level l-1 displacement = nodal interpolation of the level-l one (Sec. 6, carried down).
-hy_status interpolate_down(hy_ctx* ctx, int l) {
+// (The same nodal interpolation carries a curved geometry's coordinates down: fine -> coarse of level l.)
+hy_status interpolate_down_vec(hy_ctx* ctx, int l, const double* fine, double* coarse) {
   Transfer& t = ctx->tr[l];
   const int d = ctx->dim;
   int Lin[3] = {t.Lf, t.Lf, t.Lf};
-  const double* src = ctx->lev[l].d_u64;
+  const double* src = fine;
   for (int ax = 0; ax < d; ++ax) {
     int Lout[3] = {Lin[0], Lin[1], Lin[2]};
     Lout[ax] = t.Lc;
     const bool last = ax == d - 1;
-    double* dst = last ? ctx->lev[l - 1].d_u64 : tmp_of<double>(ctx, ax & 1);
+    double* dst = last ? coarse : tmp_of<double>(ctx, ax & 1);
     launch_sweep<double>(src, dst, d, Lin, Lout, ax, t.d_istart, t.d_iw64, t.Ei, false, nullptr, nullptr, ctx->stream);
     src = dst;
     Lin[ax] = t.Lc;
   }
   return check_launch(ctx, d);
+}
+hy_status interpolate_down(hy_ctx* ctx, int l) {
+  return interpolate_down_vec(ctx, l, ctx->lev[l].d_u64, ctx->lev[l - 1].d_u64);
 }
 
 // Chebyshev iteration of the given degree on [lo, hi] for A~ x = b on level l (Saad, Alg. 12.1),
@@ -1011,6 +1018,8 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
   if (ctx->law != HY_LAW_LOG2 &&
       (var >= VAR_FC || (ctx->sp.level_variant >= VAR_FC)))
     return fail(ctx, HY_ERR_UNSUPPORTED, "the second law goes through the caching variants T4 and T2");
+  if (ctx->curved && (var >= VAR_FC || (ctx->sp.level_variant >= VAR_FC)))
+    return fail(ctx, HY_ERR_UNSUPPORTED, "curved cells go through the caching variants T4 and T2");
   ctx->state_ok = false;
   drop_graph(ctx);
   ctx->var = var;
@@ -2197,6 +2206,26 @@ hy_status hy_face_load(hy_ctx* ctx, const double traction[6][3], double* f) {
   HY_CK(cudaSetDevice(ctx->device));
   bool any = false;
   return face_load(ctx, traction, f, &any);
+}
+
+hy_status hy_set_geometry(hy_ctx* ctx, const double* X) {
+  if (!ctx) return HY_ERR_ARG;
+  if (ctx->nlev == 0) return fail(ctx, HY_ERR_STATE, "mesh not set up");
+  HY_CK(cudaSetDevice(ctx->device));
+  ctx->state_ok = false;
+  drop_graph(ctx);
+  if (!X) {
+    ctx->curved = false;
+    return HY_OK;
+  }
+  const int top = ctx->nlev - 1;
+  for (int l = 0; l < ctx->nlev; ++l)
+    if (!ctx->lev[l].d_X64) HY_TRY(dalloc(ctx, &ctx->lev[l].d_X64, ctx->lev[l].ndofs));
+  HY_CK(cudaMemcpyAsync(ctx->lev[top].d_X64, X, sizeof(double) * ctx->lev[top].ndofs, cudaMemcpyDeviceToDevice,
+                        ctx->stream));
+  for (int l = top; l >= 1; --l) HY_TRY(interpolate_down_vec(ctx, l, ctx->lev[l].d_X64, ctx->lev[l - 1].d_X64));
+  ctx->curved = true;
+  return HY_OK;
 }
 
 hy_status hy_set_material_law(hy_ctx* ctx, int law) {

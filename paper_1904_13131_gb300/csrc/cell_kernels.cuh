@@ -39,6 +39,7 @@ struct CellArgs {
   Basis1D<T> b;
   long long nqp;          // ncells * NPT
   int pf;                 // apply: L2 prefetch distance in cell blocks (0: none)
+  const double* X64;      // nodal coordinates of a curved reference geometry (null: the uniform lattice)
 };
 
 // --- asynchronous bulk copy (TMA engine) of a block's cache chunk into shared memory ------------------
@@ -1054,6 +1055,97 @@ apply_line_list_kernel(const CellArgs<T>* __restrict__ list, const int* __restri
 }
 
 // ------------------------------------------------------------------------------------------------
+// Curved cells (an isoparametric Q_k reference map with nodal coordinates a.X64): the kernels that form
+// the state from the displacement sweep the cell's coordinates like a displacement, take GX = dX/dxi at
+// their Gauss point and use invJ = GX^{-1} (dxi/dX) and the volume weight w_q det GX in place of 1/h and
+// w_q h^d. Every thread of the block calls qp_geometry (it synchronises); inactive threads get the
+// identity map.
+template <int DIM, int N, typename SM>
+__device__ __forceinline__ void qp_geometry(const CellArgs<double>& a, const SM& s, const CellLoc<DIM, N>& loc,
+                                            const Pt<DIM, N>& pt, bool active, double* b0, double* b1,
+                                            double invJ[DIM][DIM], double& wdet) {
+  constexpr int NPT = ipow(N, DIM);
+  __syncthreads();  // the caller's sweep buffers are free again
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) b0[c * NPT + pt.p] = active ? a.X64[(long long)loc.node * DIM + c] : 0.0;
+  __syncthreads();
+  const double* V = interp_forward<DIM, N, DIM>(b0, b1, pt, s.S);
+  double GX[DIM][DIM];
+  colloc_grad<DIM, N>(V, pt, s.D, GX);
+  __syncthreads();
+  double w = a.b.w[pt.pc[0]] * a.b.w[pt.pc[1]];
+  if (DIM == 3) w *= a.b.w[pt.pc[2]];
+  if (!active) {
+#pragma unroll
+    for (int i = 0; i < DIM; ++i)
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) invJ[i][j] = i == j ? 1.0 : 0.0;
+    wdet = w;
+    return;
+  }
+  double det;
+  if (DIM == 3) {
+    invJ[0][0] = GX[1][1] * GX[2][2] - GX[1][2] * GX[2][1];
+    invJ[0][1] = GX[0][2] * GX[2][1] - GX[0][1] * GX[2][2];
+    invJ[0][2] = GX[0][1] * GX[1][2] - GX[0][2] * GX[1][1];
+    invJ[1][0] = GX[1][2] * GX[2][0] - GX[1][0] * GX[2][2];
+    invJ[1][1] = GX[0][0] * GX[2][2] - GX[0][2] * GX[2][0];
+    invJ[1][2] = GX[0][2] * GX[1][0] - GX[0][0] * GX[1][2];
+    invJ[2][0] = GX[1][0] * GX[2][1] - GX[1][1] * GX[2][0];
+    invJ[2][1] = GX[0][1] * GX[2][0] - GX[0][0] * GX[2][1];
+    invJ[2][2] = GX[0][0] * GX[1][1] - GX[0][1] * GX[1][0];
+    det = GX[0][0] * invJ[0][0] + GX[0][1] * invJ[1][0] + GX[0][2] * invJ[2][0];
+  } else {
+    invJ[0][0] = GX[1][1];
+    invJ[0][1] = -GX[0][1];
+    invJ[1][0] = -GX[1][0];
+    invJ[1][1] = GX[0][0];
+    det = GX[0][0] * GX[1][1] - GX[0][1] * GX[1][0];
+  }
+  if (!(det > 0.0)) atomicOr(a.err, ERRBIT_JNEG);
+  const double r = 1.0 / det;
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) invJ[i][j] *= r;
+  wdet = w * det;
+}
+
+// F = I + Gu invJ (Gu = du/dxi at the point); on the lattice invJ = I/h.
+template <int DIM>
+__device__ __forceinline__ void deformation_curved(const double Gu[DIM][DIM], const double invJ[DIM][DIM],
+                                                   double F[DIM][DIM]) {
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int J = 0; J < DIM; ++J) {
+      double v = Gu[i][0] * invJ[0][J];
+#pragma unroll
+      for (int L = 1; L < DIM; ++L) v = fma(Gu[i][L], invJ[L][J], v);
+      F[i][J] = (i == J ? 1.0 : 0.0) + v;
+    }
+}
+
+// M <- invJ M (M = F^{-1} on entry): the map from unit-cell gradients to the spatial ones.
+template <int DIM>
+__device__ __forceinline__ void premultiply(const double invJ[DIM][DIM], double M[DIM][DIM]) {
+  double R[DIM][DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      double v = invJ[i][0] * M[0][j];
+#pragma unroll
+      for (int L = 1; L < DIM; ++L) v = fma(invJ[i][L], M[L][j], v);
+      R[i][j] = v;
+    }
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) M[i][j] = R[i][j];
+}
+
+// ------------------------------------------------------------------------------------------------
 // Gauss-point state from the level displacement (FP64 kinematics F, J, ln J; Sec. 2.1, 2.3), stored
 // per variant in T: T4 {M, tau~, JC~ (Voigt upper triangle)}, T2 {M, tau~, c1~, c2~}, FC {F},
 // SC {mu - 2 lambda ln J}. Flags J <= 0 / NaN in the error word and tracks min J.
@@ -1078,17 +1170,26 @@ qp_state_kernel(const CellArgs<double> a, T* __restrict__ out) {
   const double* V = interp_forward<DIM, N, DIM>(b0, b1, pt, s.S);
   double Gu[DIM][DIM];
   colloc_grad<DIM, N>(V, pt, s.D, Gu);
+  const bool curved = a.X64 != nullptr;  // the same for every thread of the grid
+  double invJ[DIM][DIM], wdet = 0.0;
+  if (curved) qp_geometry<DIM, N>(a, s, loc, pt, active, b0, b1, invJ, wdet);
   if (!active) return;
   const double inv_h = a.g.inv_h;
   double F[DIM][DIM];
+  if (curved) {
+    deformation_curved<DIM>(Gu, invJ, F);
+  } else {
 #pragma unroll
-  for (int i = 0; i < DIM; ++i)
+    for (int i = 0; i < DIM; ++i)
 #pragma unroll
-    for (int J = 0; J < DIM; ++J) F[i][J] = (i == J ? 1.0 : 0.0) + Gu[i][J] * inv_h;
+      for (int J = 0; J < DIM; ++J) F[i][J] = (i == J ? 1.0 : 0.0) + Gu[i][J] * inv_h;
+  }
   const int id = a.mat[cell];
   const double mu = s.mu[id], lam = s.lam[id];
   double M[DIM][DIM], tau[NS], c1, c2;
-  const double J = neo_hooke_state<DIM>(F, mu, lam, a.mt.law, s.W[pt.p], inv_h, false, 0.0, M, tau, c1, c2);
+  const double J = neo_hooke_state<DIM>(F, mu, lam, a.mt.law, curved ? wdet : s.W[pt.p], curved ? 1.0 : inv_h, false,
+                                        0.0, M, tau, c1, c2);
+  if (curved) premultiply<DIM>(invJ, M);
   if (!(J > 0.0)) {
     atomicOr(a.err, J != J ? ERRBIT_NAN : ERRBIT_JNEG);
   } else {
@@ -1158,16 +1259,24 @@ residual_kernel(const CellArgs<double> a) {
   const double* V = interp_forward<DIM, N, DIM>(b0, b1, pt, s.S);
   double Gu[DIM][DIM];
   colloc_grad<DIM, N>(V, pt, s.D, Gu);
+  const bool curved = a.X64 != nullptr;
+  double invJ[DIM][DIM], wdet = 0.0;
+  if (curved) qp_geometry<DIM, N>(a, s, loc, pt, active, b0, b1, invJ, wdet);
   const double inv_h = a.g.inv_h;
   double F[DIM][DIM];
+  if (curved) {
+    deformation_curved<DIM>(Gu, invJ, F);
+  } else {
 #pragma unroll
-  for (int i = 0; i < DIM; ++i)
+    for (int i = 0; i < DIM; ++i)
 #pragma unroll
-    for (int J = 0; J < DIM; ++J) F[i][J] = (i == J ? 1.0 : 0.0) + Gu[i][J] * inv_h;
+      for (int J = 0; J < DIM; ++J) F[i][J] = (i == J ? 1.0 : 0.0) + Gu[i][J] * inv_h;
+  }
   const int id = active ? a.mat[cell] : 0;
   double M[DIM][DIM], tau[NS], c1, c2;
-  const double J = neo_hooke_state<DIM>(F, s.mu[id], s.lam[id], a.mt.law, s.W[pt.p], inv_h, false, 0.0, M, tau, c1,
-                                        c2);
+  const double J = neo_hooke_state<DIM>(F, s.mu[id], s.lam[id], a.mt.law, curved ? wdet : s.W[pt.p],
+                                        curved ? 1.0 : inv_h, false, 0.0, M, tau, c1, c2);
+  if (curved) premultiply<DIM>(invJ, M);
   if (active && !(J > 0.0)) atomicOr(a.err, J != J ? ERRBIT_NAN : ERRBIT_JNEG);
   double tf[DIM][DIM];
 #pragma unroll
@@ -1231,15 +1340,24 @@ diag_kernel(const CellArgs<double> a) {
   const double* V = interp_forward<DIM, N, DIM>(b0, b1, pt, s.S);
   double Gu[DIM][DIM];
   colloc_grad<DIM, N>(V, pt, s.D, Gu);
+  const bool curved = a.X64 != nullptr;
+  double invJ[DIM][DIM], wdet = 0.0;
+  if (curved) qp_geometry<DIM, N>(a, s, loc, pt, active, b0, b1, invJ, wdet);
   const double inv_h = a.g.inv_h;
   double F[DIM][DIM];
+  if (curved) {
+    deformation_curved<DIM>(Gu, invJ, F);
+  } else {
 #pragma unroll
-  for (int i = 0; i < DIM; ++i)
+    for (int i = 0; i < DIM; ++i)
 #pragma unroll
-    for (int J = 0; J < DIM; ++J) F[i][J] = (i == J ? 1.0 : 0.0) + Gu[i][J] * inv_h;
+      for (int J = 0; J < DIM; ++J) F[i][J] = (i == J ? 1.0 : 0.0) + Gu[i][J] * inv_h;
+  }
   const int id = active ? a.mat[cell] : 0;
   double M[DIM][DIM], tau[NS], c1, c2;
-  neo_hooke_state<DIM>(F, s.mu[id], s.lam[id], a.mt.law, s.W[pt.p], inv_h, false, 0.0, M, tau, c1, c2);
+  neo_hooke_state<DIM>(F, s.mu[id], s.lam[id], a.mt.law, curved ? wdet : s.W[pt.p], curved ? 1.0 : inv_h, false, 0.0,
+                       M, tau, c1, c2);
+  if (curved) premultiply<DIM>(invJ, M);
   // per-point state to shared memory in E: M (DIM^2 rows, in the flux buffer), tau, c1, c2 (NS + 2 rows)
   E(*Me)[DIM * DIM][NPT] = reinterpret_cast<E(*)[DIM * DIM][NPT]>(&s.bp[0][0][0]);
 #pragma unroll

@@ -21,6 +21,8 @@ __global__ void assemble_dense_kernel(const CellArgs<double> a, double* __restri
   constexpr int NR = NPT * DIM;
   __shared__ double S[MAXN][MAXN], D[MAXN][MAXN], Sd[MAXN][MAXN], W[NPT];
   __shared__ double u0[DIM][NPT], u1[DIM][NPT];
+  __shared__ double x0[DIM][NPT], x1[DIM][NPT];  // nodal coordinates of a curved geometry
+  const bool curved = a.X64 != nullptr;
   __shared__ double Mq[DIM * DIM][NPT], tq[NS][NPT], c1q[NPT], c2q[NPT];
   __shared__ long long gdof[NR];
   __shared__ unsigned char cons[NR];
@@ -58,6 +60,7 @@ __global__ void assemble_dense_kernel(const CellArgs<double> a, double* __restri
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
       u0[c][t] = a.u64[node * DIM + c];
+      x0[c][t] = curved ? a.X64[node * DIM + c] : 0.0;
       gdof[t * DIM + c] = node * DIM + c;
       cons[t * DIM + c] = (cm >> c) & 1u;
     }
@@ -66,6 +69,8 @@ __global__ void assemble_dense_kernel(const CellArgs<double> a, double* __restri
   // forward sweeps of the displacement to the Gauss points (threads t < NPT compute)
   double (*src)[NPT] = u0;
   double (*dst)[NPT] = u1;
+  double (*xs)[NPT] = x0;
+  double (*xd)[NPT] = x1;
 #pragma unroll
   for (int ax = 0; ax < DIM; ++ax) {
     if (t < NPT) {
@@ -73,32 +78,77 @@ __global__ void assemble_dense_kernel(const CellArgs<double> a, double* __restri
       const int base = t - pc[ax] * stride;
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
-        double v = 0.0;
+        double v = 0.0, w = 0.0;
 #pragma unroll
-        for (int j = 0; j < N; ++j) v = fma(S[pc[ax]][j], src[c][base + j * stride], v);
+        for (int j = 0; j < N; ++j) {
+          v = fma(S[pc[ax]][j], src[c][base + j * stride], v);
+          if (curved) w = fma(S[pc[ax]][j], xs[c][base + j * stride], w);
+        }
         dst[c][t] = v;
+        xd[c][t] = w;
       }
     }
     __syncthreads();
     double (*tmp)[NPT] = src;
     src = dst;
     dst = tmp;
+    tmp = xs;
+    xs = xd;
+    xd = tmp;
   }
   if (t < NPT) {
-    double F[DIM][DIM];
+    double F[DIM][DIM], Gu[DIM][DIM], GX[DIM][DIM];
 #pragma unroll
     for (int c = 0; c < DIM; ++c)
 #pragma unroll
       for (int J = 0; J < DIM; ++J) {
         const int stride = J == 0 ? 1 : (J == 1 ? N : N * N);
         const int base = t - pc[J] * stride;
-        double v = 0.0;
+        double v = 0.0, w = 0.0;
 #pragma unroll
-        for (int j = 0; j < N; ++j) v = fma(D[pc[J]][j], src[c][base + j * stride], v);
+        for (int j = 0; j < N; ++j) {
+          v = fma(D[pc[J]][j], src[c][base + j * stride], v);
+          if (curved) w = fma(D[pc[J]][j], xs[c][base + j * stride], w);
+        }
+        Gu[c][J] = v;
+        GX[c][J] = w;
         F[c][J] = (c == J ? 1.0 : 0.0) + v * a.g.inv_h;
       }
+    double invJ[DIM][DIM], Wq = W[t];
+    if (curved) {  // isoparametric map: invJ = (dX/dxi)^{-1}, weight w_q det(dX/dxi)
+      double det;
+      if (DIM == 3) {
+        invJ[0][0] = GX[1][1] * GX[2][2] - GX[1][2] * GX[2][1];
+        invJ[0][1] = GX[0][2] * GX[2][1] - GX[0][1] * GX[2][2];
+        invJ[0][2] = GX[0][1] * GX[1][2] - GX[0][2] * GX[1][1];
+        invJ[1][0] = GX[1][2] * GX[2][0] - GX[1][0] * GX[2][2];
+        invJ[1][1] = GX[0][0] * GX[2][2] - GX[0][2] * GX[2][0];
+        invJ[1][2] = GX[0][2] * GX[1][0] - GX[0][0] * GX[1][2];
+        invJ[2][0] = GX[1][0] * GX[2][1] - GX[1][1] * GX[2][0];
+        invJ[2][1] = GX[0][1] * GX[2][0] - GX[0][0] * GX[2][1];
+        invJ[2][2] = GX[0][0] * GX[1][1] - GX[0][1] * GX[1][0];
+        det = GX[0][0] * invJ[0][0] + GX[0][1] * invJ[1][0] + GX[0][2] * invJ[2][0];
+      } else {
+        invJ[0][0] = GX[1][1];
+        invJ[0][1] = -GX[0][1];
+        invJ[1][0] = -GX[1][0];
+        invJ[1][1] = GX[0][0];
+        det = GX[0][0] * GX[1][1] - GX[0][1] * GX[1][0];
+      }
+      if (!(det > 0.0)) atomicOr(a.err, ERRBIT_JNEG);
+#pragma unroll
+      for (int i = 0; i < DIM; ++i)
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) invJ[i][j] /= det;
+      double w = a.b.w[pc[0]] * a.b.w[pc[1]];
+      if (DIM == 3) w *= a.b.w[pc[2]];
+      Wq = w * det;
+      deformation_curved<DIM>(Gu, invJ, F);
+    }
     double M[DIM][DIM], tau[NS], c1, c2;
-    const double J = neo_hooke_state<DIM>(F, mu_s, lam_s, a.mt.law, W[t], a.g.inv_h, false, 0.0, M, tau, c1, c2);
+    const double J = neo_hooke_state<DIM>(F, mu_s, lam_s, a.mt.law, Wq, curved ? 1.0 : a.g.inv_h, false, 0.0, M, tau,
+                                          c1, c2);
+    if (curved) premultiply<DIM>(invJ, M);
     if (!(J > 0.0)) atomicOr(a.err, J != J ? ERRBIT_NAN : ERRBIT_JNEG);
 #pragma unroll
     for (int i = 0; i < DIM * DIM; ++i) Mq[i][t] = M[i / DIM][i % DIM];

@@ -4,6 +4,8 @@
   I + A, so the internal forces vanish at every node not on the boundary (a Q_k map reproduces fields
   linear in X exactly).
 * A finite rotation u = (Q - I) X gives F = Q and zero internal forces everywhere.
+* Volume: the bump vanishes on the boundary, so the curved mesh still fills the unit square / cube; under a
+  uniform F the stored energy is psi(F) times that volume (1), which pins the weights det(dX/dxi).
 * Energy -> residual and residual -> tangent by central differences on the curved mesh (second-order
   error ratio), which ties the volume weights det(dX/dxi) and the gradients dxi/dX together.
 * With the lattice coordinates passed explicitly, the results equal the uniform-lattice path.
@@ -12,6 +14,7 @@ import numpy as np
 import pytest
 
 from oracle.fem import Problem
+from oracle.material import psi
 from paper_1904_13131_gb300 import inputs
 
 
@@ -38,6 +41,19 @@ def test_affine_patch_and_rotation_on_curved_cells(dim, k, m):
     Q[:2, :2] = [[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]]
     ur = (X @ (Q - np.eye(dim)).T).reshape(-1)
     np.testing.assert_allclose(p.residual_raw(ur), 0.0, atol=1e-13)
+
+
+@pytest.mark.parametrize("dim,k,m", [(2, 1, 4), (2, 3, 2), (3, 2, 2)])
+def test_energy_of_a_uniform_deformation_is_psi_times_the_volume(dim, k, m):
+    X = inputs.curved_coords(dim, k, m)
+    p = make(dim, k, m, X=X, uniform=True)
+    A = 0.08 * np.random.default_rng(7 + dim).standard_normal((dim, dim))
+    F = np.eye(dim) + A
+    mu, lam = inputs.material_table(10.0)
+    np.testing.assert_allclose(p.energy((X @ A.T).reshape(-1)), psi(F, mu[0], lam[0]), rtol=1e-13)
+    # the curved mesh is not the lattice: a field that is not affine in X integrates differently
+    q = (np.sin(3.0 * X) * 0.02).reshape(-1)
+    assert abs(p.energy(q) - make(dim, k, m, uniform=True).energy(q)) > 1e-8
 
 
 @pytest.mark.parametrize("dim,k,m", [(2, 2, 3), (3, 1, 2)])

@@ -708,22 +708,27 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
   constexpr int NPT = ipow(N, DIM);
   constexpr int NLC = ipow(N, DIM - 1);
   constexpr int CB = layout_cells<T>(DIM, N);
+  constexpr int TL = CB * NLC;  // line threads of the block
   constexpr int K = N - 1;
   constexpr bool NEED_U = (VAR == VAR_NC || VAR == VAR_SC);
   constexpr bool PHYS = (VAR == VAR_FC || NEED_U);
   constexpr int NV = cache_values(VAR, DIM);
   constexpr int BS = layout_row<T>(DIM, N);
-  constexpr int NU = NEED_U ? CB : 1;
+  // Line buffers, component- and Gauss-index-major: entry (c, q, line i of the block) at (c N + q) TL + i,
+  // so that the stores of a stage (thread i writes its own line) fall in consecutive banks.
+  constexpr int NB = DIM * N * TL;
+  constexpr int NBU = NEED_U ? NB : 1;
   __shared__ T tS[MAXN][MAXN], tD[MAXN][MAXN], tDh[MAXN][MAXN], tWh[NPT], tmu[MAXMAT], tlam[MAXMAT];
-  __shared__ T buf0[CB][DIM][NPT], buf1[CB][DIM][NPT];
-  __shared__ T ubuf0[NU][DIM][NPT], ubuf1[NU][DIM][NPT];
-  __shared__ T flux[CB][DIM][DIM - 1][NPT];
+  __shared__ T buf0[NB], buf1[NB];
+  __shared__ T ubuf0[NBU], ubuf1[NBU];
+  __shared__ T flux[DIM * (DIM - 1) * N * TL];  // (c, J - 1, q, i) at ((c (DIM-1) + J - 1) N + q) TL + i
   __shared__ __align__(8) unsigned long long bar[2];
   extern __shared__ __align__(128) unsigned char dyn_smem[];
   T* const cs0 = reinterpret_cast<T*>(dyn_smem);
   const int t = threadIdx.x;
   // STAGE: the block's cache chunk streams into shared memory with one bulk copy (measured faster for
-  // T4 than reading the cache straight from global memory at the Gauss points, 18.3 vs 12.9 GDoF/s).
+  // T4 than reading the cache straight from global memory at the Gauss points, with or without an L2
+  // prefetch of the chunks ahead of use).
   constexpr bool STAGE = HY_LINE_STAGE;
   constexpr int NST = (PERSIST && STAGE && NV > 0) ? 2 : 1;  // shared-memory stages of the cache
   constexpr unsigned CHUNK = (unsigned)(NV * BS * sizeof(T));
@@ -736,7 +741,9 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
       if (!PERSIST) prefetch_chunk<NV, BS, CB>(a, blk0);
     }
   }
-  // tables (strided loops: a block may have fewer threads than entries)
+  // tables (strided loops: a block may have fewer threads than entries). The rows a thread indexes by
+  // its own line (l1, l2) are read from shared memory; entries with compile-time indices (the x
+  // direction) come straight from the kernel arguments.
   for (int i = t; i < MAXN * MAXN; i += blockDim.x) {
     tS[i / MAXN][i % MAXN] = a.b.S[i / MAXN][i % MAXN];
     tD[i / MAXN][i % MAXN] = a.b.D[i / MAXN][i % MAXN];
@@ -756,8 +763,13 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
     tmu[i] = a.mt.mu[i];
     tlam[i] = a.mt.lam[i];
   }
+  const T xh = PHYS ? T(a.g.inv_h) : T(1);  // x derivatives: D from the arguments, scaled once
   const int cl = t / NLC, l = t % NLC;
   const int l1 = l % N, l2 = DIM == 3 ? l / N : 0;
+  const int ly = cl * NLC + N * l2;  // line of this cell with y index 0 and this thread's z index
+  const int lz = cl * NLC + l1;      // line of this cell with this thread's y index and z index 0
+  auto B = [](int c, int q, int i) { return (c * N + q) * TL + i; };
+  auto FX = [](int c, int J, int q, int i) { return ((c * (DIM - 1) + J) * N + q) * TL + i; };
   int it = 0;
   for (int blk = blk0; blk < nb; blk += step, ++it) {
     const int st = NST == 2 ? (it & 1) : 0;
@@ -797,8 +809,8 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
         T sx = T(0), su = T(0);
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-          sx = fma(tS[q][j], v[j][c], sx);
-          if (NEED_U) su = fma(tS[q][j], vu[j][c], su);
+          sx = fma(a.b.S[q][j], v[j][c], sx);
+          if (NEED_U) su = fma(a.b.S[q][j], vu[j][c], su);
         }
         X[q][c] = sx;
         XU[q][c] = su;
@@ -809,8 +821,8 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
     for (int q = 0; q < N; ++q)
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
-        buf0[cl][c][q + N * l] = X[q][c];
-        if (NEED_U) ubuf0[NEED_U ? cl : 0][c][q + N * l] = XU[q][c];
+        buf0[B(c, q, t)] = X[q][c];
+        if (NEED_U) ubuf0[NEED_U ? B(c, q, t) : 0] = XU[q][c];
       }
     __syncthreads();
     if (DIM == 3) {
@@ -822,11 +834,11 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
           T sx = T(0), su = T(0);
 #pragma unroll
           for (int j = 0; j < N; ++j) {
-            sx = fma(tS[l1][j], buf0[cl][c][q + N * (j + N * l2)], sx);
-            if (NEED_U) su = fma(tS[l1][j], ubuf0[NEED_U ? cl : 0][c][q + N * (j + N * l2)], su);
+            sx = fma(tS[l1][j], buf0[B(c, q, ly + j)], sx);
+            if (NEED_U) su = fma(tS[l1][j], ubuf0[NEED_U ? B(c, q, ly + j) : 0], su);
           }
-          buf1[cl][c][q + N * l] = sx;
-          if (NEED_U) ubuf1[NEED_U ? cl : 0][c][q + N * l] = su;
+          buf1[B(c, q, t)] = sx;
+          if (NEED_U) ubuf1[NEED_U ? B(c, q, t) : 0] = su;
         }
       __syncthreads();
       // z: (q1 = l1, q2 = l2)
@@ -837,8 +849,8 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
           T sx = T(0), su = T(0);
 #pragma unroll
           for (int j = 0; j < N; ++j) {
-            sx = fma(tS[l2][j], buf1[cl][c][q + N * (l1 + N * j)], sx);
-            if (NEED_U) su = fma(tS[l2][j], ubuf1[NEED_U ? cl : 0][c][q + N * (l1 + N * j)], su);
+            sx = fma(tS[l2][j], buf1[B(c, q, lz + N * j)], sx);
+            if (NEED_U) su = fma(tS[l2][j], ubuf1[NEED_U ? B(c, q, lz + N * j) : 0], su);
           }
           V[q][c] = sx;
           VU[q][c] = su;
@@ -851,8 +863,8 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
           T sx = T(0), su = T(0);
 #pragma unroll
           for (int j = 0; j < N; ++j) {
-            sx = fma(tS[l1][j], buf0[cl][c][q + N * j], sx);
-            if (NEED_U) su = fma(tS[l1][j], ubuf0[NEED_U ? cl : 0][c][q + N * j], su);
+            sx = fma(tS[l1][j], buf0[B(c, q, ly + j)], sx);
+            if (NEED_U) su = fma(tS[l1][j], ubuf0[NEED_U ? B(c, q, ly + j) : 0], su);
           }
           V[q][c] = sx;
           VU[q][c] = su;
@@ -860,14 +872,14 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
     }
     // values at the Gauss points of the line go to shared memory for the y/z derivatives of the others
     // (3D: buf0 was last read before the previous barrier; 2D: buf1 is unused so far)
-    T (*vb)[DIM][NPT] = DIM == 3 ? buf0 : buf1;
-    T (*vub)[DIM][NPT] = DIM == 3 ? ubuf0 : ubuf1;
+    T* const vb = DIM == 3 ? buf0 : buf1;
+    T* const vub = DIM == 3 ? ubuf0 : ubuf1;
 #pragma unroll
     for (int q = 0; q < N; ++q)
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
-        vb[cl][c][q + N * l] = V[q][c];
-        if (NEED_U) vub[NEED_U ? cl : 0][c][q + N * l] = VU[q][c];
+        vb[B(c, q, t)] = V[q][c];
+        if (NEED_U) vub[NEED_U ? B(c, q, t) : 0] = VU[q][c];
       }
     __syncthreads();
     if (STAGE && NV > 0) {
@@ -893,17 +905,16 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
         T g0 = T(0), u0 = T(0);
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-          g0 = fma(Dd[q][j], V[j][c], g0);
-          if (NEED_U) u0 = fma(Dd[q][j], VU[j][c], u0);
+          g0 = fma(a.b.D[q][j], V[j][c], g0);
+          if (NEED_U) u0 = fma(a.b.D[q][j], VU[j][c], u0);
         }
-        G[c][0] = g0;
-        Gu[c][0] = u0;
+        G[c][0] = PHYS ? g0 * xh : g0;
+        Gu[c][0] = PHYS ? u0 * xh : u0;
         T g1 = T(0), u1 = T(0);
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-          const int pj = DIM == 3 ? q + N * (j + N * l2) : q + N * j;
-          g1 = fma(Dd[l1][j], vb[cl][c][pj], g1);
-          if (NEED_U) u1 = fma(Dd[l1][j], vub[NEED_U ? cl : 0][c][pj], u1);
+          g1 = fma(Dd[l1][j], vb[B(c, q, ly + j)], g1);
+          if (NEED_U) u1 = fma(Dd[l1][j], vub[NEED_U ? B(c, q, ly + j) : 0], u1);
         }
         G[c][1] = g1;
         Gu[c][1] = u1;
@@ -911,8 +922,8 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
           T g2 = T(0), u2 = T(0);
 #pragma unroll
           for (int j = 0; j < N; ++j) {
-            g2 = fma(Dd[l2][j], vb[cl][c][q + N * (l1 + N * j)], g2);
-            if (NEED_U) u2 = fma(Dd[l2][j], vub[NEED_U ? cl : 0][c][q + N * (l1 + N * j)], u2);
+            g2 = fma(Dd[l2][j], vb[B(c, q, lz + N * j)], g2);
+            if (NEED_U) u2 = fma(Dd[l2][j], vub[NEED_U ? B(c, q, lz + N * j) : 0], u2);
           }
           G[c][DIM - 1] = g2;
           Gu[c][DIM - 1] = u2;
@@ -924,7 +935,7 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
       for (int c = 0; c < DIM; ++c) {
         Px[q][c] = P[c][0];
 #pragma unroll
-        for (int J = 1; J < DIM; ++J) flux[cl][c][J - 1][p] = P[c][J];
+        for (int J = 1; J < DIM; ++J) flux[FX(c, J - 1, q, t)] = P[c][J];
       }
     }
     __syncthreads();
@@ -936,15 +947,12 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
       for (int c = 0; c < DIM; ++c) {
         T s = T(0);
 #pragma unroll
-        for (int j = 0; j < N; ++j) s = fma(tD[j][q], Px[j][c], s);
+        for (int j = 0; j < N; ++j) s = fma(a.b.D[j][q], Px[j][c], s);
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
-          const int pj = DIM == 3 ? q + N * (j + N * l2) : q + N * j;
-          s = fma(tD[j][l1], flux[cl][c][0][pj], s);
-        }
+        for (int j = 0; j < N; ++j) s = fma(tD[j][l1], flux[FX(c, 0, q, ly + j)], s);
         if (DIM == 3) {
 #pragma unroll
-          for (int j = 0; j < N; ++j) s = fma(tD[j][l2], flux[cl][c][DIM - 2][q + N * (l1 + N * j)], s);
+          for (int j = 0; j < N; ++j) s = fma(tD[j][l2], flux[FX(c, DIM - 2, q, lz + N * j)], s);
         }
         Wq[q][c] = s;
       }
@@ -954,7 +962,7 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
 #pragma unroll
       for (int q = 0; q < N; ++q)
 #pragma unroll
-        for (int c = 0; c < DIM; ++c) buf1[cl][c][q + N * l] = Wq[q][c];
+        for (int c = 0; c < DIM; ++c) buf1[B(c, q, t)] = Wq[q][c];
       __syncthreads();
 #pragma unroll
       for (int q = 0; q < N; ++q)
@@ -962,8 +970,8 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
         for (int c = 0; c < DIM; ++c) {  // z: (q1 = l1, a2 = l2)
           T sz = T(0);
 #pragma unroll
-          for (int j = 0; j < N; ++j) sz = fma(tS[j][l2], buf1[cl][c][q + N * (l1 + N * j)], sz);
-          buf0[cl][c][q + N * l] = sz;
+          for (int j = 0; j < N; ++j) sz = fma(tS[j][l2], buf1[B(c, q, lz + N * j)], sz);
+          buf0[B(c, q, t)] = sz;
         }
       __syncthreads();
 #pragma unroll
@@ -972,14 +980,14 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
         for (int c = 0; c < DIM; ++c) {  // y: (a1 = l1, a2 = l2)
           T sy = T(0);
 #pragma unroll
-          for (int j = 0; j < N; ++j) sy = fma(tS[j][l1], buf0[cl][c][q + N * (j + N * l2)], sy);
+          for (int j = 0; j < N; ++j) sy = fma(tS[j][l1], buf0[B(c, q, ly + j)], sy);
           Yb[q][c] = sy;
         }
     } else {
 #pragma unroll
       for (int q = 0; q < N; ++q)
 #pragma unroll
-        for (int c = 0; c < DIM; ++c) buf0[cl][c][q + N * l] = Wq[q][c];
+        for (int c = 0; c < DIM; ++c) buf0[B(c, q, t)] = Wq[q][c];
       __syncthreads();
 #pragma unroll
       for (int q = 0; q < N; ++q)
@@ -987,7 +995,7 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
         for (int c = 0; c < DIM; ++c) {
           T sy = T(0);
 #pragma unroll
-          for (int j = 0; j < N; ++j) sy = fma(tS[j][l1], buf0[cl][c][q + N * j], sy);
+          for (int j = 0; j < N; ++j) sy = fma(tS[j][l1], buf0[B(c, q, ly + j)], sy);
           Yb[q][c] = sy;
         }
     }
@@ -999,7 +1007,7 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
           if ((cms[a0] >> c) & 1u) continue;
           T s = T(0);
 #pragma unroll
-          for (int j = 0; j < N; ++j) s = fma(tS[j][a0], Yb[j][c], s);
+          for (int j = 0; j < N; ++j) s = fma(a.b.S[j][a0], Yb[j][c], s);
           atomicAdd(&a.y[(node0 + a0) * DIM + c], vec_out(s));
         }
     }

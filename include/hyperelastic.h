@@ -155,9 +155,11 @@ typedef struct {
                                arithmetic on the FP32 pipe (about 48 significant bits; the applied inverse
                                and the matrix-vector product are FP64) */
   int kernel_form;          /* [-1] tangent-action kernel: 0 = one thread per (cell, Gauss point), 1 = one
-                               thread per x-line of a cell, -1 = autotuned: the first linearisation of each
-                               (dim, degree, variant, precision, mesh size) times both on the level's own
-                               cache and keeps the faster (process-wide; when the environment variable
+                               thread per x-line of a cell, 2 = as 1 on a persistent grid whose thread
+                               blocks copy their next cache chunk in while finishing the current one (FP32;
+                               runs as 1 in the other precisions), -1 = autotuned: the first linearisation
+                               of each (dim, degree, variant, precision, mesh size) times the forms on the
+                               level's own cache and keeps the fastest (process-wide; when the environment variable
                                HY_TUNE_FILE names a file, the decisions are read from it at the first tuning
                                and it is rewritten, as a JSON array, with every new decision) */
   hy_dtype fine_dtype;      /* [HY_F64] tangent action of the finest level inside the solver (outer CG, and the

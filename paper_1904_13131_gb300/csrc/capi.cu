@@ -960,7 +960,7 @@ hy_status autotune_level(hy_ctx* ctx, int l) {
   HY_CK(cudaEventCreate(&ev.a));
   HY_CK(cudaEventCreate(&ev.b));
   cudaEvent_t e0 = ev.a, e1 = ev.b;
-  // FP32 also has the persistent double-buffered line form
+  // FP32 also has the persistent line form (next cache chunk copied in under the current block's work)
   const int nforms = std::is_same<T, float>::value ? 3 : 2;
   float best[3] = {1e30f, 1e30f, 1e30f};
   for (int form = 0; form < nforms; ++form) {

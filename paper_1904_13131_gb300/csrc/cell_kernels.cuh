@@ -700,9 +700,11 @@ __device__ __forceinline__ void apply_point_body(const CellArgs<T>& a, const int
 // memory, and gather and scatter touch one contiguous run of (k+1)*dim values. The y and z sweeps exchange
 // values through shared memory, the thread playing the line (q0 varies; q1 = l1, q2 = l2) of each stage.
 // Same arithmetic, variants and Dirichlet treatment as apply_kernel.
-// PERSIST: the thread block loops over the cell blocks blk0, blk0 + step, ... with the cache chunks in
-// two shared-memory stages -- the bulk copy of the next chunk runs while the current one is used (tables
-// are loaded once per thread block). Otherwise the thread block processes the one cell block blk0.
+// PERSIST: the thread block loops over the cell blocks blk0, blk0 + step, ... with one shared-memory
+// stage of the cache: the bulk copy of the next chunk is issued as soon as the Gauss-point work has read
+// the current one, so it runs under the transposed sweeps, the scatter, the next gather and the forward
+// sweeps (tables are loaded once per thread block). Otherwise the thread block processes the one cell
+// block blk0.
 template <int DIM, int N, int VAR, typename T, bool PERSIST = false>
 __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int blk0, const int step) {
   constexpr int NPT = ipow(N, DIM);
@@ -722,22 +724,20 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
   __shared__ T buf0[NB], buf1[NB];
   __shared__ T ubuf0[NBU], ubuf1[NBU];
   __shared__ T flux[DIM * (DIM - 1) * N * TL];  // (c, J - 1, q, i) at ((c (DIM-1) + J - 1) N + q) TL + i
-  __shared__ __align__(8) unsigned long long bar[2];
+  __shared__ __align__(8) unsigned long long bar;
   extern __shared__ __align__(128) unsigned char dyn_smem[];
-  T* const cs0 = reinterpret_cast<T*>(dyn_smem);
+  T* const cs = reinterpret_cast<T*>(dyn_smem);
   const int t = threadIdx.x;
   // STAGE: the block's cache chunk streams into shared memory with one bulk copy (measured faster for
   // T4 than reading the cache straight from global memory at the Gauss points, with or without an L2
   // prefetch of the chunks ahead of use).
   constexpr bool STAGE = HY_LINE_STAGE;
-  constexpr int NST = (PERSIST && STAGE && NV > 0) ? 2 : 1;  // shared-memory stages of the cache
   constexpr unsigned CHUNK = (unsigned)(NV * BS * sizeof(T));
   const int nb = PERSIST ? (a.g.ncells + CB - 1) / CB : blk0 + 1;
   if (STAGE && NV > 0 && t == 0) {
-    mbar_init(&bar[0], 1);
-    if (NST == 2) mbar_init(&bar[1], 1);
+    mbar_init(&bar, 1);
     if (blk0 < nb) {
-      bulk_load(cs0, a.cache + (size_t)blk0 * NV * BS, CHUNK, &bar[0]);
+      bulk_load(cs, a.cache + (size_t)blk0 * NV * BS, CHUNK, &bar);
       if (!PERSIST) prefetch_chunk<NV, BS, CB>(a, blk0);
     }
   }
@@ -772,14 +772,7 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
   auto FX = [](int c, int J, int q, int i) { return ((c * (DIM - 1) + J) * N + q) * TL + i; };
   int it = 0;
   for (int blk = blk0; blk < nb; blk += step, ++it) {
-    const int st = NST == 2 ? (it & 1) : 0;
-    T* const cs = cs0 + (size_t)st * NV * BS;
     const T* cg = a.cache + (size_t)blk * NV * BS;
-    if (NST == 2 && t == 0 && blk + step < nb) {
-      // the other stage was last read in the previous iteration, before its closing barrier
-      fence_proxy_async();
-      bulk_load(cs0 + (size_t)(st ^ 1) * NV * BS, a.cache + (size_t)(blk + step) * NV * BS, CHUNK, &bar[st ^ 1]);
-    }
     const int cell = blk * CB + cl;
     const bool active = cell < a.g.ncells;
     const int m = a.g.m;
@@ -883,12 +876,11 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
       }
     __syncthreads();
     if (STAGE && NV > 0) {
-      const unsigned parity = NST == 2 ? ((it >> 1) & 1) : 0;
-      const bool ok = mbar_wait(&bar[st], parity);
-      if (__syncthreads_or(!ok)) {  // a copy never completed: flag it, let the copies in flight land, leave
+      const unsigned parity = it & 1;  // the it-th copy completes phase it of the barrier
+      const bool ok = mbar_wait(&bar, parity);
+      if (__syncthreads_or(!ok)) {  // the copy never completed: flag it, give it one more bounded wait, leave
         if (t == 0) atomicOr(a.err, ERRBIT_TIMEOUT);
-        mbar_wait(&bar[st], parity);
-        if (NST == 2 && blk + step < nb) mbar_wait(&bar[st ^ 1], ((it + 1) >> 1) & 1);
+        mbar_wait(&bar, parity);
         return;
       }
     }
@@ -939,6 +931,11 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
       }
     }
     __syncthreads();
+    if (PERSIST && STAGE && NV > 0 && t == 0 && blk + step < nb) {
+      // every thread has read this chunk (barrier above): refill the stage with the next one
+      fence_proxy_async();
+      bulk_load(cs, a.cache + (size_t)(blk + step) * NV * BS, CHUNK, &bar);
+    }
     // transposed derivatives summed over the directions: x from registers, y/z from shared memory
     T Wq[N][DIM];
 #pragma unroll
@@ -1048,7 +1045,7 @@ apply_line_kernel(const CellArgs<T> a) {
   apply_line_body<DIM, N, VAR, T>(a, blockIdx.x, 1);
 }
 
-// persistent: gridDim.x thread blocks loop over all cell blocks, two cache stages
+// persistent: gridDim.x thread blocks loop over all cell blocks, the next chunk copied in early
 template <int DIM, int N, int VAR, typename T>
 __global__ void __launch_bounds__(layout_cells<T>(DIM, N) * ipow(N, DIM - 1))
 apply_line_persist_kernel(const CellArgs<T> a) {

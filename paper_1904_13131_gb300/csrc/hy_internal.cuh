@@ -101,8 +101,8 @@ __host__ __device__ constexpr int layout_row(int dim, int n) {
 }
 
 // Kernel forms of the tangent action: thread per (cell, Gauss point); thread per x-line of a cell; the line
-// form as a persistent grid with the cache double-buffered in shared memory (FP32 only: elsewhere it
-// runs as FORM_LINE).
+// form as a persistent grid whose blocks copy their next cache chunk in while they finish the current one
+// (FP32 only: elsewhere it runs as FORM_LINE).
 enum KernelForm { FORM_POINT = 0, FORM_LINE = 1, FORM_LINE_PERSIST = 2 };
 
 // Device-side error word bits.

@@ -260,6 +260,111 @@ def solve_latency(torch, api, inputs, dev):
     return out
 
 
+def f32_steady_state(torch, api, inputs, dev, hbm):
+    """The FP32 action in steady state: 64^3 Q2 (6.4M dofs; caches of 0.5-1 GB, far larger than L2), ten
+    back-to-back applications per timing, best of three; T4 and T2 with the tuned kernel form."""
+    k, m = 2, 64
+    pr = inputs.problem(3, k, m, n_levels=1, top=0)
+    n = inputs.n_dofs(3, k, m)
+    nqp = m**3 * (k + 1) ** 3
+    u = torch.tensor(inputs.smooth_field(3, k, m, seed=0), device=dev)
+    x = torch.tensor(inputs.gaussian_vector(n, seed=1), device=dev).float()
+    y = torch.empty_like(x)
+    out = {"workload": "64^3 Q2 inclusion cube (6,440,067 dofs), u = 0.05 smooth field, FP32 cache and vectors"}
+    for var in ("T4", "T2"):
+        with api.Context(dev.index) as c:
+            c.setup_problem(pr)
+            c.set_solver_params(coarse_eig_iters=5)
+            c.set_displacement(u, var, level_dtype=1)
+            for _ in range(3):
+                c.apply_tangent(x, y, dtype=1)
+            best = 1e30
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(10):
+                    c.apply_tangent(x, y, dtype=1)
+                e1.record()
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1) / 10)
+            gbs = bytes_per_apply(var, 4, nqp, n) / (best * 1e-3) / 1e9
+            out[var] = {"ms": best, "gdofs": n / (best * 1e-3) / 1e9, "gbs": gbs, "hbm_frac": gbs / hbm,
+                        "form": FORMS[c.kernel_form(-1, 1)], "algorithmic_bytes": bytes_per_apply(var, 4, nqp, n)}
+    return out
+
+
+def newton_summary(rep):
+    lat = np.array(rep["solve_ms"])
+    return {"solve_p50_ms": float(np.percentile(lat, 50)), "solve_p99_ms": float(np.percentile(lat, 99)),
+            "solves": rep["n_solves"], "cg_iterations_median": int(np.median(rep["solve_cg_iterations"])),
+            "cg_iterations_max": rep["cg_iterations_max"], "newton_iterations": rep["newton_iterations"],
+            "newton_total_ms": rep["total_ms"], "setup_ms_total": rep["setup_ms_total"]}
+
+
+def config_study(torch, api, inputs, dev):
+    """The large workloads: (a) the 3D degree sweep Q1-Q4 at 6.4M-51M dofs, full Newton solve under 10%
+    compression in 5 load steps, GMG down to a 2^3-4^3 coarse level, CG rtol 1e-8, in the paper's mode (FP64
+    V-cycle, Chebyshev coarse solve) and in the fastest mode (FP32 V-cycle with T2 level operators, exact
+    coarse inverse where the coarsest level has at most 6000 dofs, double-float finest-level action for
+    degrees 1-2); (b) mixed precision on the 64^3 Q2 inclusion cube, load step by load step: displacement
+    difference between the FP64 and the mixed-precision Newton states, and the CG iterations of both."""
+    out = {}
+    sweep = [(1, 128, 6), (2, 64, 5), (3, 48, 5), (4, 32, 4), (2, 128, 6)]
+    for k, m, L in sweep:
+        pr = inputs.problem(3, k, m, n_levels=L, top=inputs.normal_top_mask(3))
+        n = inputs.n_dofs(3, k, m)
+        fv = [[0.0] * 3 for _ in range(6)]
+        fv[5][2] = -0.1
+        coarse_exact = inputs.n_dofs(3, k, m >> (L - 1)) <= 6000 and k <= 3
+        modes = [("fastest", 1, 2 if coarse_exact else 0, api.FF if k <= 2 else api.F64, api.VARIANTS["T2"])]
+        if n < 20_000_000:
+            modes.insert(0, ("paper_fp64", 0, 0, api.F64, -1))
+        row = {"dofs": n, "levels": L, "coarse_m": m >> (L - 1)}
+        sols = {}
+        with api.Context(dev.index) as c:
+            c.setup_problem(pr)
+            for name, ldt, coarse, fine, lvar in modes:
+                c.set_solver_params(coarse_solver=coarse, fine_dtype=fine, level_variant=lvar)
+                u = torch.zeros(n, dtype=torch.float64, device=dev)
+                rep = c.newton_solve(u, api.Context.newton_params(level_dtype=ldt, face_values=fv))
+                row[name] = newton_summary(rep)
+                row[name]["coarse_solver"] = ["chebyshev", "exact_fp64", "exact_ff"][coarse]
+                row[name]["fine_dtype"] = "ff" if fine == api.FF else "f64"
+                row[name]["solves_per_s"] = 1e3 / row[name]["solve_p50_ms"]
+                sols[name] = u
+        if len(sols) == 2:
+            row["fastest_vs_paper_rel_l2"] = float(torch.linalg.norm(sols["fastest"] - sols["paper_fp64"]) /
+                                                   torch.linalg.norm(sols["paper_fp64"]))
+        del sols
+        out[f"Q{k}_{m}^3"] = row
+        print(json.dumps({"config_progress": f"Q{k}_{m}^3"}), file=sys.stderr, flush=True)
+    # (b) mixed precision per load step on 64^3 Q2 (5 levels, FP64 Chebyshev coarse solve in both)
+    k, m, L, steps = 2, 64, 5, 5
+    pr = inputs.problem(3, k, m, n_levels=L, top=inputs.normal_top_mask(3))
+    n = inputs.n_dofs(3, k, m)
+    per_step = []
+    with api.Context(dev.index) as c:
+        c.setup_problem(pr)
+        u64 = torch.zeros(n, dtype=torch.float64, device=dev)
+        u32 = torch.zeros_like(u64)
+        for s in range(1, steps + 1):
+            fv = [[0.0] * 3 for _ in range(6)]
+            fv[5][2] = -0.1 * s / steps
+            r64 = c.newton_solve(u64, api.Context.newton_params(load_steps=1, level_dtype=0, face_values=fv))
+            r32 = c.newton_solve(u32, api.Context.newton_params(load_steps=1, level_dtype=1, face_values=fv))
+            per_step.append({"step": s, "mixed_vs_fp64_rel_l2": float(torch.linalg.norm(u32 - u64) / torch.linalg.norm(u64)),
+                             "cg_iterations_fp64": r64["cg_iterations_total"], "cg_iterations_mixed": r32["cg_iterations_total"],
+                             "newton_iterations_fp64": r64["newton_iterations"][0],
+                             "newton_iterations_mixed": r32["newton_iterations"][0],
+                             "solve_p50_ms_fp64": float(np.percentile(r64["solve_ms"], 50)),
+                             "solve_p50_ms_mixed": float(np.percentile(r32["solve_ms"], 50))})
+    out["mixed_per_load_step_64^3_Q2"] = per_step
+    out["note"] = ("paper_fp64: FP64 V-cycle, Chebyshev coarse to 1e-3 (Sec. 7); fastest: FP32 V-cycle with T2 level "
+                   "operators, exact coarse inverse (double-float Gauss-Jordan) where the coarsest level allows, "
+                   "double-float finest-level action for degrees 1-2; Newton under 10% compression in 5 load steps")
+    return out
+
+
 def serve_bench(api, inputs, dev, n_req, seed=0, max_active=8, budget_gb=160):
     """Serving (continuous batching): a seeded stream of uneven solve requests (2D 32^2-256^2 and 3D 8^3-48^3,
     Q1-Q3, stiffness ratio 2-100, radius 0.1-0.35, compression 2-15 %, 5 load steps). Baseline: the same
@@ -457,12 +562,14 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--only", default=None, help="profile mode: VARIANT:f64|f32, a few applications of one kernel")
     ap.add_argument("--form", type=int, default=-1, help="profile mode: kernel form (0 point, 1 line, -1 tuned)")
+    ap.add_argument("--m", type=int, default=M, help="profile mode: cells per direction of the Q2 cube")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--serve-requests", type=int, default=12, help="requests in the serving section (0 = skip)")
     ap.add_argument("--serve-only", action="store_true")
     ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the work-list batch section")
     ap.add_argument("--batch-only", action="store_true")
     ap.add_argument("--solve-only", action="store_true")
+    ap.add_argument("--configs", action="store_true", help="the degree sweep at 6-51M dofs and the 64^3 mixed study")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -484,9 +591,10 @@ def main():
     stream = torch.cuda.current_stream(dev)
     if args.only:
         var, dt = args.only.split(":")
-        pr = inputs.problem(DIM, K, M, n_levels=1, top=0)
-        u = torch.tensor(inputs.smooth_field(DIM, K, M, seed=0), device=dev)
-        x = torch.tensor(inputs.gaussian_vector(inputs.n_dofs(DIM, K, M), seed=1), device=dev)
+        mo = args.m
+        pr = inputs.problem(DIM, K, mo, n_levels=1, top=0)
+        u = torch.tensor(inputs.smooth_field(DIM, K, mo, seed=0), device=dev)
+        x = torch.tensor(inputs.gaussian_vector(inputs.n_dofs(DIM, K, mo), seed=1), device=dev)
         code = {"f64": 0, "f32": 1, "ff": 2}[dt]
         with api.Context(dev.index) as c:
             c.setup_problem(pr)
@@ -498,6 +606,9 @@ def main():
                 c.apply_tangent(xin, y, dtype=code)
             torch.cuda.synchronize()
         print(json.dumps({"only": args.only, "reps": args.reps}))
+        return
+    if args.configs:
+        print(json.dumps({"configs": config_study(torch, api, inputs, dev)}), flush=True)
         return
     if args.solve_only:
         print(json.dumps({"solve": solve_latency(torch, api, inputs, dev)}), flush=True)
@@ -565,6 +676,7 @@ def main():
         second_law[v] = {"f64_ms": t, "f64_gdofs": n / (t * 1e-3) / 1e9}
         ctxs[v].set_material_law(api.LAW_LOG2)
         ctxs[v].set_displacement(u, v, level_dtype=1)
+    steady = f32_steady_state(torch, api, inputs, dev, hbm)
     # curved (isoparametric) cells through T4 and T2: M = J^{-1} F^{-1} and the weights w det(dX/dxi) are
     # folded into the cache, so the applies should cost what they cost on the lattice
     curved = {}
@@ -649,7 +761,8 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": int(launches_timed),
-                "per_variant_ms_f64": per_var_ms, "variants": variants, "second_law": second_law, "curved": curved, "solve": solve,
+                "per_variant_ms_f64": per_var_ms, "variants": variants, "second_law": second_law, "curved": curved,
+                "f32_steady_state_64cube": steady, "solve": solve,
                 "serve": serve, "batch": batch,
                 "wall_s_timed_region": wall, "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src}
         print(json.dumps(line), flush=True)

@@ -231,25 +231,29 @@ class Problem:
         y_{a,c} += w_q h^d grad(N_a e_c) : Q = w_q h^d sum_j g_a,j Q_cj.
         With constrained=True, x is read as zero on constrained dofs and y_c = x_c there.
         """
-        d = self.dim
         xin = np.where(self.constrained, 0.0, x) if constrained else np.asarray(x, dtype=float)
         y = np.zeros(self.n_dofs)
         for cells in self._chunks():
-            F = self.deformation(u, cells)
-            mu, lam = self._qp_params(cells)
-            tau = material.kirchhoff(F, mu, lam, self.law)
-            JC = material.spatial_tangent(F, mu, lam, self.law)
-            Finv = np.linalg.inv(F)
-            gx = np.einsum("KqiJ,KqJj->Kqij", self.grad_at_qp(xin, cells), Finv)
-            gxs = 0.5 * (gx + np.swapaxes(gx, -1, -2))
-            Q = np.einsum("Kqim,Kqmj->Kqij", gx, tau) + np.einsum("Kqijkl,Kqkl->Kqij", JC, gxs)
-            ga = self._g(F, cells)
-            _, wdV = self._geom(cells)
-            yK = np.einsum("Kqaj,Kqcj,Kq->Kac", ga, Q, wdV)
-            np.add.at(y, self.cell_dofs[cells].reshape(-1), yK.reshape(-1))
+            self.apply_cells(u, xin, cells, y)
         if constrained:
             y[self.constrained] = x[self.constrained]
         return y
+
+    def apply_cells(self, u, xin, cells, y):
+        """Adds the contributions of the given cells to y (the loop body of apply; xin already has the
+        constrained entries zeroed if they are to be read as zero)."""
+        F = self.deformation(u, cells)
+        mu, lam = self._qp_params(cells)
+        tau = material.kirchhoff(F, mu, lam, self.law)
+        JC = material.spatial_tangent(F, mu, lam, self.law)
+        Finv = np.linalg.inv(F)
+        gx = np.einsum("KqiJ,KqJj->Kqij", self.grad_at_qp(xin, cells), Finv)
+        gxs = 0.5 * (gx + np.swapaxes(gx, -1, -2))
+        Q = np.einsum("Kqim,Kqmj->Kqij", gx, tau) + np.einsum("Kqijkl,Kqkl->Kqij", JC, gxs)
+        ga = self._g(F, cells)
+        _, wdV = self._geom(cells)
+        yK = np.einsum("Kqaj,Kqcj,Kq->Kac", ga, Q, wdV)
+        np.add.at(y, self.cell_dofs[cells].reshape(-1), yK.reshape(-1))
 
     def diagonal(self, u):
         """diag of the constrained tangent, summed element by element (1 on constrained dofs)."""

@@ -2,6 +2,9 @@
 
 * 3D 32^3 Q2 tangent application (823,875 dofs) in the launch configuration the benchmark times: every
   output of every variant against the oracle's element-by-element application (FP64 1e-12, FP32 2e-6).
+* The largest mesh of the degree sweep, 128^3 Q2 (50,923,779 dofs): the tangent action (T4 and NC in FP64, T4
+  in FP32, tuned kernel forms) against the oracle at seeded sample dofs, each evaluated by the oracle from
+  the cells that contain its node (1e-12 / 2e-6).
 * Degree sweep Q1-Q4 of the 3D Newton solve under 10 % compression in 5 load steps: against the oracle's
   Newton on reduced meshes (1e-8), and at 64^3 Q2 (6.4M dofs) by properties that hold at any size: the FP64,
   mixed-precision and exact-coarse solves converge to the same displacement (1e-8).
@@ -52,6 +55,48 @@ def test_config2_full_size_apply_every_output(torch):
             ctx.set_displacement(ud, var, level_dtype=1)
             assert rel(ctx.apply_tangent(xd).cpu().numpy(), y_ref) < 1e-12, var
             assert rel(ctx.apply_tangent(xd.float(), dtype=1).cpu().numpy(), y_ref) < 2e-6, var
+
+
+def cells_of_node(k, m, idx):
+    """Cells (x-fastest index) whose closure holds the lattice node with multi-index idx."""
+    per_axis = []
+    for i in idx:
+        cs = {min(i // k, m - 1)}
+        if i % k == 0 and i > 0:
+            cs.add(i // k - 1)
+        per_axis.append(sorted(cs))
+    return [c0 + m * (c1 + m * c2) for c2 in per_axis[2] for c1 in per_axis[1] for c0 in per_axis[0]]
+
+
+def test_config3_largest_mesh_sampled_outputs(torch):
+    dim, k, m = 3, 2, 128
+    pr = inputs.problem(dim, k, m, top=0)
+    P = Problem(dim, k, m, pr["ids"][0], pr["mu"], pr["lam"], pr["masks"])
+    assert P.n_dofs == 50_923_779
+    u = inputs.smooth_field(dim, k, m, seed=0)
+    x = inputs.gaussian_vector(P.n_dofs, seed=1)
+    L = k * m + 1
+    rng = np.random.default_rng(7)
+    # random dofs plus dofs on the clamped bottom face, a cell corner and the last node
+    dofs = np.concatenate([rng.choice(P.n_dofs, 300, replace=False), [0, 5, dim * (L * L + L + 1) * 2 + 2,
+                                                                       P.n_dofs - 1]])
+    cells = sorted({c for d in dofs for c in cells_of_node(k, m, ((d // dim) % L, (d // dim // L) % L,
+                                                                   d // dim // (L * L)))})
+    y_ref = np.zeros(P.n_dofs)
+    P.apply_cells(u, np.where(P.constrained, 0.0, x), np.array(cells), y_ref)
+    ref = np.where(P.constrained[dofs], x[dofs], y_ref[dofs])
+    assert P.constrained[dofs].any() and not P.constrained[dofs].all()
+    ud, xd = torch.tensor(u, device="cuda"), torch.tensor(x, device="cuda")
+    del u, y_ref
+    with context(pr) as ctx:
+        ctx.set_solver_params(coarse_eig_iters=5)
+        for var in ("T4", "NC"):
+            ctx.set_displacement(ud, var, level_dtype=1 if var == "T4" else 0)
+            y = ctx.apply_tangent(xd)[torch.tensor(dofs, device="cuda")].cpu().numpy()
+            assert rel(y, ref) < 1e-12, (var, rel(y, ref))
+            if var == "T4":
+                y32 = ctx.apply_tangent(xd.float(), dtype=1)[torch.tensor(dofs, device="cuda")].cpu().numpy()
+                assert rel(y32, ref) < 2e-6, rel(y32, ref)
 
 
 @pytest.mark.parametrize("k,m,L", [(1, 8, 3), (2, 4, 2), (3, 4, 2), (4, 2, 2)])

@@ -108,6 +108,15 @@ hy_status hy_set_material_law(hy_ctx *ctx, int law);
  * Takes effect at the next hy_set_displacement (and for hy_residual at once). */
 hy_status hy_set_geometry(hy_ctx *ctx, const double *X_dev);
 
+/* Failure-path check of the bounded device waits (no counterpart in the paper). Every wait of the
+ * tangent-action kernels on a bulk copy is bounded by GPU wall time (4 s) and a poll count; when one
+ * gives up, the kernel flags the context's error word, lets its copies land and returns, and the next
+ * synchronising call reports HY_ERR_TIMEOUT. This call runs one thread block whose wait can never
+ * complete (nothing arrives on its barrier), with the wall-time bound limit_s in [1e-3, 10] seconds.
+ * It returns HY_ERR_TIMEOUT once the wait has given up, with the error word cleared and the context
+ * usable; HY_ERR_STATE before hy_mesh_setup; HY_ERR_ARG for limit_s out of range. */
+hy_status hy_check_bounded_wait(hy_ctx *ctx, double limit_s);
+
 /* Linearisation point (Sec. 6). u_dev: fine-level FP64 displacement (device). The displacement is
  * carried down to every level by nodal interpolation and each level's Gauss-point cache is built
  * for `variant` from FP64 kinematics (F, J, ln J). level_dtype = HY_F32 selects the mixed-precision

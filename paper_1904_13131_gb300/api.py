@@ -29,7 +29,8 @@ EXPORTED = ("hy_create", "hy_destroy", "hy_status_str", "hy_last_error", "hy_mes
             "hy_server_create", "hy_server_destroy", "hy_server_submit", "hy_server_poll", "hy_server_wait",
             "hy_server_release", "hy_server_stats_get", "hy_kernel_form", "hy_batch_create", "hy_batch_destroy",
             "hy_batch_last_error", "hy_batch_apply", "hy_batch_pcg", "hy_batch_kernel_launches",
-            "hy_batch_kernel_form", "hy_set_material_law", "hy_face_load", "hy_set_geometry")
+            "hy_batch_kernel_form", "hy_set_material_law", "hy_face_load", "hy_set_geometry",
+            "hy_check_bounded_wait")
 
 
 class HyError(RuntimeError):
@@ -118,6 +119,7 @@ def load_library(path: str = LIB_PATH):
         "hy_set_material_law": [vp, i32],
         "hy_face_load": [vp, ctypes.c_void_p, vp],
         "hy_set_geometry": [vp, vp],
+        "hy_check_bounded_wait": [vp, ctypes.c_double],
         "hy_ctx_bytes": [vp, ctypes.POINTER(i64)],
         "hy_batch_create": [ctypes.POINTER(vp), ctypes.POINTER(vp), i32],
         "hy_batch_destroy": [vp],
@@ -218,6 +220,11 @@ class Context:
         """Curved cells: X the finest level's nodal coordinates (n_dofs FP64 values on the device, interleaved
         like a displacement), or None for the uniform lattice."""
         self._ck(self.lib.hy_set_geometry(self.h, None if X is None else self._vec(X, self.num_dofs(), F64)))
+
+    def check_bounded_wait(self, limit_s=0.2):
+        """Runs the failure-path check of the bounded device waits; raises HyError (HY_ERR_TIMEOUT) once the
+        never-completing wait has given up, as it must."""
+        self._ck(self.lib.hy_check_bounded_wait(self.h, float(limit_s)))
 
     def set_material_law(self, law):
         """0 (LAW_LOG2): the paper's lambda ln^2 J; 1 (LAW_J2): lambda/4 (J^2 - 1 - 2 ln J)."""

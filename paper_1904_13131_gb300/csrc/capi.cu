@@ -2228,6 +2228,15 @@ hy_status hy_set_geometry(hy_ctx* ctx, const double* X) {
   return HY_OK;
 }
 
+hy_status hy_check_bounded_wait(hy_ctx* ctx, double limit_s) {
+  if (!ctx) return HY_ERR_ARG;
+  if (!ctx->d_err) return fail(ctx, HY_ERR_STATE, "check_bounded_wait: no mesh");
+  if (!(limit_s >= 1e-3 && limit_s <= 10.0)) return fail(ctx, HY_ERR_ARG, "check_bounded_wait: limit_s outside [1e-3, 10]");
+  launch_bounded_wait_check(ctx->d_err, (unsigned long long)(limit_s * 1e9), ctx->stream);
+  HY_TRY(check_launch(ctx, 1));
+  return check_error_word(ctx, "check_bounded_wait");
+}
+
 hy_status hy_set_material_law(hy_ctx* ctx, int law) {
   if (!ctx) return HY_ERR_ARG;
   if (law != HY_LAW_LOG2 && law != HY_LAW_J2) return fail(ctx, HY_ERR_ARG, "unknown material law");

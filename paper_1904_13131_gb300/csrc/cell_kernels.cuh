@@ -86,9 +86,17 @@ __device__ __forceinline__ void prefetch_chunk(const CellArgs<T>& a, int blk) {
   const long long pb = (long long)blk + a.pf;
   if (pb < nb) prefetch_l2(a.cache + (size_t)pb * NV * BS, (unsigned)(NV * BS * sizeof(T)));
 }
-// Wait for phase `parity` of the barrier with a bounded number of polls; false if it never completed.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for phase `parity` of the barrier; false if it did not complete within limit_ns of GPU wall time
+// (checked every 64 polls) or MBAR_POLL_LIMIT polls.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity,
+                                          unsigned long long limit_ns = MBAR_WAIT_NS) {
   const unsigned a = smem_u32(bar);
+  const unsigned long long t0 = global_ns();
   for (unsigned it = 0; it < MBAR_POLL_LIMIT; ++it) {
     unsigned done;
     asm volatile(
@@ -97,6 +105,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
+    if ((it & 63u) == 63u && global_ns() - t0 > limit_ns) return false;
   }
   return false;
 }

@@ -108,8 +108,9 @@ enum KernelForm { FORM_POINT = 0, FORM_LINE = 1, FORM_LINE_PERSIST = 2 };
 // Device-side error word bits.
 enum : unsigned { ERRBIT_JNEG = 1u, ERRBIT_NAN = 2u, ERRBIT_TIMEOUT = 4u, ERRBIT_NONSPD = 8u };
 
-// Upper bound on mbarrier polls before a wait gives up (each try_wait may suspend the thread briefly,
-// so this is seconds, far above any real copy time).
+// A bounded mbarrier wait gives up after MBAR_WAIT_NS of GPU wall time (the global timer) or
+// MBAR_POLL_LIMIT polls, whichever comes first: seconds, far above any real copy time.
 constexpr unsigned MBAR_POLL_LIMIT = 1u << 24;
+constexpr unsigned long long MBAR_WAIT_NS = 4000000000ull;
 
 }  // namespace hy

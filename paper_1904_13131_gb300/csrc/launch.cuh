@@ -123,6 +123,8 @@ void launch_eig_beta(double* s, double* hist, int it, int iters, cudaStream_t st
 // converged, not_spd}); op 0 alpha, 1 convergence test, 2 beta
 constexpr int PCG_SCALARS = 16;  // stride of one problem's scalars
 void launch_pcg_scalar(double* s, int op, cudaStream_t st);
+// one thread block whose bounded mbarrier wait can never complete: sets ERRBIT_TIMEOUT in *err after limit_ns
+void launch_bounded_wait_check(unsigned* err, unsigned long long limit_ns, cudaStream_t st);
 // r = b - t
 template <typename T> void launch_sub(const T* b, const T* t, T* r, long long n, cudaStream_t st);
 // f += t * int_face N_a dA on face `face` (0..2 dim-1: -x, +x, -y, +y, -z, +z); FaceLoad carries the traction t

@@ -455,4 +455,18 @@ template void launch_convert<float, double>(const float*, double*, long long, cu
 template void launch_prep_out_list<double>(const CellArgs<double>*, int, int, long long, cudaStream_t);
 template void launch_prep_out_list<float>(const CellArgs<float>*, int, int, long long, cudaStream_t);
 template void launch_prep_out_list<ff>(const CellArgs<ff>*, int, int, long long, cudaStream_t);
+// One thread block waits on an mbarrier that nothing arrives on: the bounded wait has to give up by itself
+// after limit_ns and flag ERRBIT_TIMEOUT. A check of the failure path that every bulk-copy wait takes.
+__global__ void bounded_wait_check_kernel(unsigned* err, unsigned long long limit_ns) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  const bool ok = mbar_wait(&bar, 0, limit_ns);
+  if (!ok && threadIdx.x == 0) atomicOr(err, ERRBIT_TIMEOUT);
+}
+
+void launch_bounded_wait_check(unsigned* err, unsigned long long limit_ns, cudaStream_t st) {
+  bounded_wait_check_kernel<<<1, 32, 0, st>>>(err, limit_ns);
+}
+
 }  // namespace hy

@@ -164,6 +164,31 @@ def test_inverted_element_reports_jneg(torch):
         assert torch.count_nonzero(ok).item() == 0
 
 
+def test_bounded_wait_gives_up_and_context_stays_usable(torch):
+    """A bulk-copy wait that can never complete (nothing arrives on the barrier) gives up by itself after its
+    wall-time bound: HY_ERR_TIMEOUT, then the same context applies the tangent correctly."""
+    import time
+    from paper_1904_13131_gb300.api import HyError
+    dim, k, m = 3, 2, 3
+    pr = problem(dim, k, m)
+    P = oracle_level(pr)
+    u = inputs.smooth_field(dim, k, m, seed=3)
+    x = inputs.gaussian_vector(P.n_dofs, seed=4)
+    with context(pr) as ctx:
+        for limit in (0.05, 0.3):
+            t0 = time.perf_counter()
+            with pytest.raises(HyError) as e:
+                ctx.check_bounded_wait(limit)
+            assert e.value.status == "HY_ERR_TIMEOUT"
+            assert time.perf_counter() - t0 < 5.0
+        with pytest.raises(HyError) as e:
+            ctx.check_bounded_wait(60.0)
+        assert e.value.status == "HY_ERR_ARG"
+        ctx.set_displacement(torch.tensor(u, device="cuda"), "T4")
+        y = ctx.apply_tangent(torch.tensor(x, device="cuda")).cpu().numpy()
+        assert rel(y, P.apply(u, x)) < 1e-12
+
+
 def test_argument_errors(torch):
     from paper_1904_13131_gb300.api import Context, HyError
     with Context(0) as ctx:

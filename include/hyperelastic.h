@@ -223,10 +223,16 @@ typedef struct {
   double face_traction[6][3]; /* final dead traction per face (reference configuration, per unit reference
                                  area), reached in the same increments; [0] = none. The paper loads its
                                  benchmark this way (Sec. 7); the tangent is unchanged by a dead load. */
+  int first_step;            /* [0 = 1] checkpoint / resume: run load steps first_step .. last_step of the
+                                load_steps increments only. u_inout_dev then holds on entry the converged
+                                state after step first_step - 1 (zero for step 1); a solve stopped after a
+                                step and resumed from its u (saved anywhere, in any context of the same
+                                problem) continues the same load path. */
+  int last_step;             /* [0 = load_steps] */
 } hy_newton_params;
 
 typedef struct {
-  int load_steps_done;
+  int load_steps_done;        /* the last load step completed (an absolute step number) */
   int newton_iterations[64];  /* per load step (first 64 steps) */
   int cg_iterations_total;
   int cg_iterations_max;
@@ -342,6 +348,9 @@ typedef struct {
   hy_newton_params newton;        /* load path, tolerances, variant, V-cycle precision */
   hy_solver_params solver;
   int law;                        /* hy_law of the material */
+  const double *u_start;          /* HOST, NULL = zero: the start state (n_dofs values, copied at submit);
+                                     with newton.first_step > 1 it re-admits a checkpoint, e.g. the u of an
+                                     earlier request that stopped at newton.last_step */
 } hy_request;
 
 typedef struct {

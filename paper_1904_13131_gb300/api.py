@@ -50,7 +50,8 @@ class NewtonParams(ctypes.Structure):
     _fields_ = [("load_steps", ctypes.c_int), ("max_newton", ctypes.c_int), ("newton_rtol", ctypes.c_double),
                 ("newton_atol", ctypes.c_double), ("cg_rtol", ctypes.c_double), ("cg_max_iter", ctypes.c_int),
                 ("variant", ctypes.c_int), ("level_dtype", ctypes.c_int),
-                ("face_values", (ctypes.c_double * 3) * 6), ("face_traction", (ctypes.c_double * 3) * 6)]
+                ("face_values", (ctypes.c_double * 3) * 6), ("face_traction", (ctypes.c_double * 3) * 6),
+                ("first_step", ctypes.c_int), ("last_step", ctypes.c_int)]
 
 
 class NewtonReport(ctypes.Structure):
@@ -65,7 +66,8 @@ class Request(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("degree", ctypes.c_int), ("cells_per_dir", ctypes.c_int),
                 ("n_levels", ctypes.c_int), ("face_masks", ctypes.c_uint32 * 6), ("cell_mat_levels", ctypes.c_void_p),
                 ("mu", ctypes.POINTER(ctypes.c_double)), ("lambda_", ctypes.POINTER(ctypes.c_double)),
-                ("n_mat", ctypes.c_int), ("newton", NewtonParams), ("solver", SolverParams), ("law", ctypes.c_int)]
+                ("n_mat", ctypes.c_int), ("newton", NewtonParams), ("solver", SolverParams), ("law", ctypes.c_int),
+                ("u_start", ctypes.POINTER(ctypes.c_double))]
 
 
 class ServerStats(ctypes.Structure):
@@ -524,8 +526,10 @@ class Server:
     def __exit__(self, *a):
         self.close()
 
-    def submit(self, problem: dict, newton: NewtonParams, solver: SolverParams | None = None, law: int = 0) -> int:
-        """problem: an inputs.problem(...) bundle (ids of every level, coarsest first); law: a hy_law."""
+    def submit(self, problem: dict, newton: NewtonParams, solver: SolverParams | None = None, law: int = 0,
+               u_start=None) -> int:
+        """problem: an inputs.problem(...) bundle (ids of every level, coarsest first); law: a hy_law; u_start:
+        host start state (a checkpoint, with newton.first_step > 1), None = zero."""
         if solver is None:
             solver = SolverParams(4, 1, 0.6, 1.2, 30, 0, 1e-3, 0, -1, 0, -1)
         ids = np.ascontiguousarray(np.concatenate([np.asarray(i, dtype=np.uint8) for i in problem["ids"]]))
@@ -542,6 +546,11 @@ class Server:
         r.newton = newton
         r.solver = solver
         r.law = int(law)
+        if u_start is not None:
+            u_start = np.ascontiguousarray(u_start, dtype=np.float64)
+            if u_start.size != r.dim * (r.degree * r.cells_per_dir + 1) ** r.dim:
+                raise ValueError("u_start has the wrong length")
+            r.u_start = u_start.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         t = ctypes.c_uint64()
         st = self.lib.hy_server_submit(self.h, ctypes.byref(r), ctypes.byref(t))
         if st != 0:

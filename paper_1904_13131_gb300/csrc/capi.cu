@@ -15,6 +15,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/hyperelastic.h"
 #include "cell_kernels.cuh"
 #include "launch.cuh"
@@ -22,6 +24,15 @@
 using namespace hy;
 
 namespace {
+
+// Named NVTX range over a solver phase (linearisation, PCG, V-cycle, Newton load step) for profilers and
+// tracers; without a tool attached, push and pop return at once.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 // ---------------------------------------------------------------------------------------------
 // 1D Q_k element tables from their definitions: Legendre recurrences for the GLL points (roots of
@@ -1008,6 +1019,7 @@ struct PhaseTimer {
 };
 
 hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
+  const Range range("set_displacement");
   if (ctx->nlev == 0) return fail(ctx, HY_ERR_STATE, "mesh not set up");
   PhaseTimer pt(ctx);
   for (int l = 0; l < ctx->nlev; ++l)
@@ -1790,6 +1802,7 @@ hy_status pcg_graph(hy_ctx* ctx, const double* b, double* x_out, double rtol, in
 }
 
 hy_status pcg(hy_ctx* ctx, const double* b, double* x, double rtol, int max_iter, int* its_out) {
+  const Range range("pcg");
   return ctx->use_graphs ? pcg_graph(ctx, b, x, rtol, max_iter, its_out) : pcg_host(ctx, b, x, rtol, max_iter, its_out);
 }
 
@@ -2120,6 +2133,7 @@ hy_status hy_residual(hy_ctx* ctx, const double* u, double* r) {
   if (ctx->nlev == 0) return fail(ctx, HY_ERR_STATE, "mesh not set up");
   if (!ctx->lev[ctx->nlev - 1].mat_set) return fail(ctx, HY_ERR_STATE, "material not set");
   HY_CK(cudaSetDevice(ctx->device));
+  const Range range("residual");
   HY_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
   HY_TRY(residual(ctx, u, r));
   return check_error_word(ctx, "residual");
@@ -2147,6 +2161,7 @@ hy_status hy_gmg_vcycle(hy_ctx* ctx, const double* r, double* z) {
   if (!ctx || !r || !z) return HY_ERR_ARG;
   if (!ctx->state_ok) return fail(ctx, HY_ERR_STATE, "set_displacement first");
   HY_CK(cudaSetDevice(ctx->device));
+  const Range range("gmg_vcycle");
   return vcycle_top(ctx, r, z);
 }
 
@@ -2310,7 +2325,12 @@ hy_status hy_newton_solve(hy_ctx* ctx, const hy_newton_params* p, double* u, hy_
   if (!ctx || !p || !u) return HY_ERR_ARG;
   if (p->load_steps < 1 || p->max_newton < 1 || !(p->newton_rtol > 0) || !(p->cg_rtol > 0) || p->cg_max_iter < 1)
     return fail(ctx, HY_ERR_ARG, "newton parameters out of range");
+  const int s_first = p->first_step > 0 ? p->first_step : 1;
+  const int s_last = p->last_step > 0 ? p->last_step : p->load_steps;
+  if (p->first_step < 0 || p->last_step < 0 || s_first > s_last || s_last > p->load_steps)
+    return fail(ctx, HY_ERR_ARG, "newton: need 1 <= first_step <= last_step <= load_steps");
   if (ctx->nlev == 0) return fail(ctx, HY_ERR_STATE, "mesh not set up");
+  const Range range_solve("hy_newton_solve");
   HY_CK(cudaSetDevice(ctx->device));
   hy_newton_report rl;
   std::memset(&rl, 0, sizeof(rl));
@@ -2325,7 +2345,8 @@ hy_status hy_newton_solve(hy_ctx* ctx, const hy_newton_params* p, double* u, hy_
   auto ms_since = [](clk::time_point t0) { return std::chrono::duration<double, std::milli>(clk::now() - t0).count(); };
   const clk::time_point t_start = clk::now();
   hy_status st = HY_OK;
-  for (int s = 1; s <= p->load_steps && st == HY_OK; ++s) {
+  for (int s = s_first; s <= s_last && st == HY_OK; ++s) {
+    const Range range_step("load step");
     const double factor = (double)s / p->load_steps;
     double ref = -1.0;
     int its = 0;

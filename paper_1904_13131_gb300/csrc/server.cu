@@ -42,6 +42,7 @@ struct Req {
   std::string err;
   hy_newton_report rep{};
   std::vector<double> u;
+  std::vector<double> u_start;  // empty: start from zero
   Clock::time_point t_submit, t_start, t_end;
 };
 
@@ -87,9 +88,12 @@ void run_request(Req& r, int device, cudaStream_t st) {
   int64_t n = 0;
   if (s == HY_OK) s = hy_num_dofs(ctx, -1, &n);
   if (s == HY_OK) {
-    if (cudaMallocAsync((void**)&u, sizeof(double) * n, st) != cudaSuccess ||
-        cudaMemsetAsync(u, 0, sizeof(double) * n, st) != cudaSuccess)
+    if (cudaMallocAsync((void**)&u, sizeof(double) * n, st) != cudaSuccess)
       s = HY_ERR_OOM;
+    else if ((r.u_start.empty() ? cudaMemsetAsync(u, 0, sizeof(double) * n, st)
+                                : cudaMemcpyAsync(u, r.u_start.data(), sizeof(double) * n, cudaMemcpyHostToDevice,
+                                                  st)) != cudaSuccess)
+      s = HY_ERR_CUDA;
   }
   if (s == HY_OK) s = hy_newton_solve(ctx, &r.np, u, &r.rep);
   if (s == HY_OK) {
@@ -202,7 +206,9 @@ hy_status hy_server_submit(hy_server* sv, const hy_request* q, uint64_t* ticket)
   hy_status s = hy_footprint(r->dim, r->degree, r->m, r->nlev, q->newton.variant, q->newton.level_dtype, &q->solver,
                              r->fm, &bytes);
   if (s != HY_OK) return s;
-  r->bytes = bytes + (int64_t)sizeof(double) * r->dim * (int64_t)std::pow(r->degree * r->m + 1.0, r->dim);  // + u
+  const int64_t n_u = r->dim * (int64_t)std::llround(std::pow(r->degree * r->m + 1.0, r->dim));
+  r->bytes = bytes + (int64_t)sizeof(double) * n_u;  // + u
+  if (q->u_start) r->u_start.assign(q->u_start, q->u_start + n_u);
   if (r->bytes > sv->budget) return HY_ERR_OOM;  // could never be admitted
   {
     std::lock_guard<std::mutex> lock(sv->mu);

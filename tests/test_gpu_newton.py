@@ -74,3 +74,44 @@ def test_config1_newton_exact_coarse_matches_oracle(torch, config1_reference):
         rep = ctx.newton_solve(u, Context.newton_params(level_dtype=1, face_values=face_values(2, -0.1)))
     assert rep["load_steps_done"] == 5
     assert rel(u.cpu().numpy(), u_ref) < 1e-8
+
+
+def test_checkpoint_and_resume_continue_the_load_path(torch):
+    """Checkpoint / resume at load-step granularity: load steps 1-2 in one context, the displacement saved to
+    the host, steps 3-5 from it in a fresh context (and through the solve server) reach the one-shot
+    solution (1e-10); the reports count absolute steps."""
+    from paper_1904_13131_gb300.api import Context, HyError, Server, SolverParams
+    dim, k, m, L = 3, 2, 4, 2
+    pr = inputs.problem(dim, k, m, n_levels=L, top=inputs.normal_top_mask(dim))
+    fv = [[0.0] * 3 for _ in range(6)]
+    fv[5][2] = -0.1
+    n = inputs.n_dofs(dim, k, m)
+    with context(pr) as c:
+        u_full = torch.zeros(n, dtype=torch.float64, device="cuda")
+        c.newton_solve(u_full, Context.newton_params(level_dtype=1, face_values=fv))
+        with pytest.raises(HyError) as e:
+            c.newton_solve(torch.zeros_like(u_full), Context.newton_params(face_values=fv, first_step=4, last_step=3))
+        assert e.value.status == "HY_ERR_ARG"
+        u = torch.zeros_like(u_full)
+        rep = c.newton_solve(u, Context.newton_params(level_dtype=1, face_values=fv, last_step=2))
+        assert rep["load_steps_done"] == 2 and rep["newton_iterations"][2:] == [0, 0, 0]
+    checkpoint = u.cpu().numpy()
+    with context(pr) as c:
+        u = torch.tensor(checkpoint, device="cuda")
+        rep = c.newton_solve(u, Context.newton_params(level_dtype=1, face_values=fv, first_step=3))
+        assert rep["load_steps_done"] == 5 and rep["newton_iterations"][:2] == [0, 0]
+        assert min(rep["newton_iterations"][2:]) > 0
+    ref = u_full.cpu().numpy()
+    assert rel(u.cpu().numpy(), ref) < 1e-10
+    solver = SolverParams(4, 1, 0.6, 1.2, 30, 0, 1e-3, 1, -1, 0, -1)
+    with Server(0, budget_bytes=4 << 30, max_active=2) as sv:
+        t1 = sv.submit(pr, Context.newton_params(level_dtype=1, face_values=fv, last_step=2), solver)
+        sv.wait(t1, 600.0)
+        r1 = sv.poll(t1, want_u=True)
+        assert r1["state"] == 2 and r1["report"]["load_steps_done"] == 2
+        t2 = sv.submit(pr, Context.newton_params(level_dtype=1, face_values=fv, first_step=3), solver,
+                       u_start=r1["u"])
+        sv.wait(t2, 600.0)
+        r2 = sv.poll(t2, want_u=True)
+        assert r2["state"] == 2 and r2["report"]["load_steps_done"] == 5
+    assert rel(r2["u"], ref) < 1e-10

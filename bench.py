@@ -569,6 +569,7 @@ def main():
     ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the work-list batch section")
     ap.add_argument("--batch-only", action="store_true")
     ap.add_argument("--solve-only", action="store_true")
+    ap.add_argument("--vcycle", action="store_true", help="profile mode: V-cycles of the 32^3 Q2 hierarchy")
     ap.add_argument("--configs", action="store_true", help="the degree sweep at 6-51M dofs and the 64^3 mixed study")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -606,6 +607,31 @@ def main():
                 c.apply_tangent(xin, y, dtype=code)
             torch.cuda.synchronize()
         print(json.dumps({"only": args.only, "reps": args.reps}))
+        return
+    if args.vcycle:
+        # profile mode: V-cycles of the 32^3 Q2 hierarchy (4 levels) in the fastest mode; the first call
+        # captures the graph, then args.reps timed replays
+        pr = inputs.problem(DIM, K, M, n_levels=4, top=inputs.normal_top_mask(DIM))
+        with api.Context(dev.index) as c:
+            c.setup_problem(pr)
+            c.set_solver_params(coarse_solver=2, fine_dtype=api.FF, level_variant=api.VARIANTS["T2"])
+            c.set_displacement(torch.tensor(inputs.smooth_field(DIM, K, M, seed=0, amplitude=0.02), device=dev),
+                               "T4", level_dtype=1)
+            b = torch.tensor(inputs.gaussian_vector(c.num_dofs(), seed=1), device=dev)
+            z = torch.empty_like(b)
+            n0 = c.kernel_launches()
+            c.gmg_vcycle(b, z)
+            torch.cuda.synchronize()
+            per = c.kernel_launches() - n0
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.reps):
+                c.gmg_vcycle(b, z)
+            e1.record(stream)
+            e1.synchronize()
+            print(json.dumps({"vcycle_ms": e0.elapsed_time(e1) / args.reps, "reps": args.reps,
+                              "kernels_per_vcycle": per,
+                              "forms_f32": [c.kernel_form(level, 1) for level in range(4)]}))
         return
     if args.configs:
         print(json.dumps({"configs": config_study(torch, api, inputs, dev)}), flush=True)

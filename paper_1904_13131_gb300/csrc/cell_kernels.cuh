@@ -17,10 +17,6 @@
 
 #include "hy_internal.cuh"
 
-#ifndef HY_LINE_STAGE
-#define HY_LINE_STAGE 1
-#endif
-
 namespace hy {
 
 template <typename T>
@@ -737,13 +733,12 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
   extern __shared__ __align__(128) unsigned char dyn_smem[];
   T* const cs = reinterpret_cast<T*>(dyn_smem);
   const int t = threadIdx.x;
-  // STAGE: the block's cache chunk streams into shared memory with one bulk copy (measured faster for
-  // T4 than reading the cache straight from global memory at the Gauss points, with or without an L2
-  // prefetch of the chunks ahead of use).
-  constexpr bool STAGE = HY_LINE_STAGE;
+  // The block's cache chunk streams into shared memory with one bulk copy (measured faster for T4 than
+  // reading the cache straight from global memory at the Gauss points, with or without an L2 prefetch of
+  // the chunks ahead of use).
   constexpr unsigned CHUNK = (unsigned)(NV * BS * sizeof(T));
   const int nb = PERSIST ? (a.g.ncells + CB - 1) / CB : blk0 + 1;
-  if (STAGE && NV > 0 && t == 0) {
+  if (NV > 0 && t == 0) {
     mbar_init(&bar, 1);
     if (blk0 < nb) {
       bulk_load(cs, a.cache + (size_t)blk0 * NV * BS, CHUNK, &bar);
@@ -781,7 +776,6 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
   auto FX = [](int c, int J, int q, int i) { return ((c * (DIM - 1) + J) * N + q) * TL + i; };
   int it = 0;
   for (int blk = blk0; blk < nb; blk += step, ++it) {
-    const T* cg = a.cache + (size_t)blk * NV * BS;
     const int cell = blk * CB + cl;
     const bool active = cell < a.g.ncells;
     const int m = a.g.m;
@@ -884,7 +878,7 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
         if (NEED_U) vub[NEED_U ? B(c, q, t) : 0] = VU[q][c];
       }
     __syncthreads();
-    if (STAGE && NV > 0) {
+    if (NV > 0) {
       const unsigned parity = it & 1;  // the it-th copy completes phase it of the barrier
       const bool ok = mbar_wait(&bar, parity);
       if (__syncthreads_or(!ok)) {  // the copy never completed: flag it, give it one more bounded wait, leave
@@ -893,7 +887,7 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
         return;
       }
     }
-    const T* cq = STAGE ? cs : cg;
+    const T* cq = cs;
     const T (*Dd)[MAXN] = PHYS ? tDh : tD;
     const int id = active ? a.mat[cell] : 0;
     T Px[N][DIM];
@@ -940,7 +934,7 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
       }
     }
     __syncthreads();
-    if (PERSIST && STAGE && NV > 0 && t == 0 && blk + step < nb) {
+    if (PERSIST && NV > 0 && t == 0 && blk + step < nb) {
       // every thread has read this chunk (barrier above): refill the stage with the next one
       fence_proxy_async();
       bulk_load(cs, a.cache + (size_t)(blk + step) * NV * BS, CHUNK, &bar);

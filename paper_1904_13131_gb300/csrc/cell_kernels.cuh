@@ -616,11 +616,15 @@ __device__ __forceinline__ void apply_point_body(const CellArgs<T>& a, const int
   __shared__ Smem<DIM, N, T, CB> s;
   __shared__ __align__(8) unsigned long long bar;
   extern __shared__ __align__(128) unsigned char dyn_smem[];
-  T* cs = reinterpret_cast<T*>(dyn_smem);  // this block's cache chunk [NV][BS]
-  if (NV > 0 && threadIdx.x == 0) {
+  // This block's cache chunk [NV][BS]: staged in shared memory by a bulk copy, except in double-float,
+  // whose FP32-pipe-bound work gains more from the occupancy that a 70 KB chunk would cost; there the
+  // Gauss-point work reads it from global memory, coalesced (thread i reads entry i of every row).
+  constexpr bool STAGE = !std::is_same<T, ff>::value;
+  const T* cs = STAGE ? reinterpret_cast<const T*>(dyn_smem) : a.cache + (size_t)blk * NV * BS;
+  if (STAGE && NV > 0 && threadIdx.x == 0) {
     // the chunk streams in (TMA bulk copy) while the block gathers x and runs the forward sweeps
     mbar_init(&bar, 1);
-    bulk_load(cs, a.cache + (size_t)blk * NV * BS, (unsigned)(NV * BS * sizeof(T)), &bar);
+    bulk_load(dyn_smem, a.cache + (size_t)blk * NV * BS, (unsigned)(NV * BS * sizeof(T)), &bar);
     prefetch_chunk<NV, BS, CB>(a, blk);
   }
   load_tables<DIM, N>(s, a);
@@ -671,7 +675,7 @@ __device__ __forceinline__ void apply_point_body(const CellArgs<T>& a, const int
     if (!HOIST) kD.rows(PHYS ? s.Dh : s.D, pt);
     grad_coef<DIM, N>(src[0], pt, kD, G);  // Grad x (FC) or d x / d xi (T4, T2: M holds F^{-1}/h)
   }
-  if (NV > 0) {
+  if (STAGE && NV > 0) {
     const bool ok = mbar_wait(&bar, 0);
     if (__syncthreads_or(!ok)) {  // the copy never completed: flag it, give it one more bounded wait, leave
       if (threadIdx.x == 0) atomicOr(a.err, ERRBIT_TIMEOUT);
@@ -1038,6 +1042,22 @@ apply_kernel(const CellArgs<T> a) {
 template <int DIM, int N, int VAR, typename T>
 __global__ void __launch_bounds__(layout_cells<T>(DIM, N) * ipow(N, DIM))
 apply_list_kernel(const CellArgs<T>* __restrict__ list, const int* __restrict__ start, int count) {
+  const int p = work_item(start, count, blockIdx.x);
+  apply_point_body<DIM, N, VAR, T>(list[p], blockIdx.x - start[p]);
+}
+
+// The point form in double-float stages no cache chunk and asks for three resident blocks per SM (register
+// limit 85). The other precisions keep the compiler's default register budget; an explicit minimum of one
+// block would let it take up to 152 registers for FP64 NC and fall to one block per SM.
+template <int DIM, int N, int VAR, typename T>
+__global__ void __launch_bounds__(layout_cells<T>(DIM, N) * ipow(N, DIM), 3)
+apply_kernel_ff(const CellArgs<T> a) {
+  apply_point_body<DIM, N, VAR, T>(a, blockIdx.x);
+}
+
+template <int DIM, int N, int VAR, typename T>
+__global__ void __launch_bounds__(layout_cells<T>(DIM, N) * ipow(N, DIM), 3)
+apply_list_kernel_ff(const CellArgs<T>* __restrict__ list, const int* __restrict__ start, int count) {
   const int p = work_item(start, count, blockIdx.x);
   apply_point_body<DIM, N, VAR, T>(list[p], blockIdx.x - start[p]);
 }

@@ -409,6 +409,9 @@ def serve_bench(api, inputs, dev, n_req, seed=0, max_active=8, budget_gb=160):
         failed = sum(r["state"] != 2 for r in res)
         out = {"solves_per_s": (len(reqs) - failed) / makespan, "p50_ms": float(np.percentile(lat, 50)),
                "p99_ms": float(np.percentile(lat, 99)), "makespan_s": makespan, "failed": failed,
+               "failed_requests": [dict(id=q["id"], status=r["status"], dim=q["dim"], k=q["k"], m=q["m"],
+                                        ratio=q["ratio"], compression=q["compression"])
+                                   for q, r in zip(reqs, res) if r["state"] != 2],
                "bytes_peak_gb": stats["bytes_peak"] / 1e9, "max_active": max_act}
         return out, [r["u"] for r in res]
 

@@ -356,6 +356,11 @@ typedef struct {
 typedef struct {
   int64_t submitted, completed, failed, active, queued;
   int64_t bytes_in_use, bytes_peak, budget;
+  int64_t retried;  /* solves run again with the coarsest level dropped: a solve that fails only on a
+                       coarsest-level tangent that is not positive definite (a coarse mesh that does not
+                       resolve the inclusion, Sec. 6) reruns from its start state with one level fewer, while
+                       two levels remain and the budget holds the larger coarse level (Chebyshev coarse
+                       solve when it exceeds the dense-inverse limit) */
 } hy_server_stats;
 
 hy_status hy_server_create(hy_server **out, int device, int64_t hbm_budget_bytes, int max_active);

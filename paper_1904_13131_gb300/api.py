@@ -72,7 +72,7 @@ class Request(ctypes.Structure):
 
 class ServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "active", "queued", "bytes_in_use",
-                                              "bytes_peak", "budget")]
+                                              "bytes_peak", "budget", "retried")]
 
 
 _lib = None
@@ -241,11 +241,15 @@ class Context:
                                           lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(mu)))
 
     def setup_problem(self, problem: dict, n_levels: int | None = None):
-        """mesh_setup + set_material on every level from an inputs.problem(...) bundle."""
-        L = len(problem["levels_m"]) if n_levels is None else n_levels
+        """mesh_setup + set_material on every level from an inputs.problem(...) bundle; n_levels (at most the
+        bundle's) keeps the finest n_levels of its hierarchy."""
+        nb = len(problem["levels_m"])
+        L = nb if n_levels is None else n_levels
+        if not 1 <= L <= nb:
+            raise ValueError(f"n_levels must lie in [1, {nb}]")
         self.mesh_setup(problem["dim"], problem["k"], problem["m"], L, problem["masks"])
         for l in range(L):
-            self.set_material(l, problem["ids"][l], problem["mu"], problem["lam"])
+            self.set_material(l, problem["ids"][nb - L + l], problem["mu"], problem["lam"])
 
     # ---- state / operators ----------------------------------------------------------------------
     def set_displacement(self, u, variant="T4", level_dtype=F64):

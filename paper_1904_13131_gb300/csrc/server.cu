@@ -9,6 +9,11 @@
 // Newton solve and releases it when done, at which point the next request is admitted. Requests that
 // arrive while others run therefore join them on the device: their kernels overlap through the
 // concurrent streams. Latency is measured from submission to completion.
+//
+// A solve that fails only because its coarsest level's tangent is not positive definite (a coarse mesh
+// that does not resolve the inclusion, under a large load) is run again from its start state with that
+// level dropped, as long as two levels remain and the budget has room for the larger coarse level.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -43,6 +48,7 @@ struct Req {
   hy_newton_report rep{};
   std::vector<double> u;
   std::vector<double> u_start;  // empty: start from zero
+  int dropped = 0;              // coarsest levels dropped after an indefinite coarse tangent
   Clock::time_point t_submit, t_start, t_end;
 };
 
@@ -58,7 +64,7 @@ struct hy_server {
   std::unordered_map<uint64_t, std::unique_ptr<Req>> reqs;
   int64_t in_use = 0, peak = 0;
   int active = 0;
-  int64_t submitted = 0, completed = 0, failed = 0;
+  int64_t submitted = 0, completed = 0, failed = 0, retried = 0;
   bool stop = false;
   uint64_t next_id = 1;
   std::vector<std::thread> workers;
@@ -72,17 +78,26 @@ long long level_cells(const Req& r, int l) {
   return c;
 }
 
-// One request on the worker's stream: context, hierarchy, materials, Newton solve, result to host.
-void run_request(Req& r, int device, cudaStream_t st) {
+// One attempt of a request on the worker's stream with its `drop` coarsest levels left out: context,
+// hierarchy, materials, Newton solve, result to host. *coarse_indefinite tells whether it failed on a
+// coarsest-level tangent that is not positive definite.
+hy_status run_attempt(Req& r, int drop, int device, cudaStream_t st, bool* coarse_indefinite) {
+  *coarse_indefinite = false;
   hy_ctx* ctx = nullptr;
   double* u = nullptr;
+  const int nlev = r.nlev - drop;
+  hy_solver_params sp = r.sp;
   hy_status s = hy_create(&ctx, device, st);
-  if (s == HY_OK) s = hy_mesh_setup(ctx, r.dim, r.degree, r.m, r.nlev, r.fm);
-  if (s == HY_OK) s = hy_set_solver_params(ctx, &r.sp);
+  if (s == HY_OK) s = hy_mesh_setup(ctx, r.dim, r.degree, r.m, nlev, r.fm);
+  int64_t n_coarse = 0;
+  if (s == HY_OK) s = hy_num_dofs(ctx, 0, &n_coarse);
+  if (s == HY_OK && drop > 0 && n_coarse > 6000) sp.coarse_solver = 0;  // beyond the dense inverse: Chebyshev
+  if (s == HY_OK) s = hy_set_solver_params(ctx, &sp);
   if (s == HY_OK) s = hy_set_material_law(ctx, r.law);
   size_t off = 0;
-  for (int l = 0; l < r.nlev && s == HY_OK; ++l) {
-    s = hy_set_material(ctx, l, r.mats.data() + off, r.mu.data(), r.lam.data(), (int)r.mu.size());
+  for (int l = 0; l < drop; ++l) off += (size_t)level_cells(r, l);
+  for (int l = drop; l < r.nlev && s == HY_OK; ++l) {
+    s = hy_set_material(ctx, l - drop, r.mats.data() + off, r.mu.data(), r.lam.data(), (int)r.mu.size());
     off += (size_t)level_cells(r, l);
   }
   int64_t n = 0;
@@ -102,11 +117,49 @@ void run_request(Req& r, int device, cudaStream_t st) {
         cudaStreamSynchronize(st) != cudaSuccess)
       s = HY_ERR_CUDA;
   }
-  if (s != HY_OK) r.err = ctx ? hy_last_error(ctx) : "context creation failed";
+  if (s != HY_OK) {
+    r.err = ctx ? hy_last_error(ctx) : "context creation failed";
+    *coarse_indefinite = s == HY_ERR_NOCONV && r.err.rfind("coarsest-level tangent is not positive definite", 0) == 0;
+  }
   if (u) cudaFreeAsync(u, st);
   hy_destroy(ctx);
   cudaStreamSynchronize(st);
-  r.status = s;
+  return s;
+}
+
+// Device bytes of the request with `drop` coarsest levels left out (the coarse solver as run_attempt
+// picks it), or -1.
+int64_t attempt_bytes(const Req& r, int drop) {
+  const int nlev = r.nlev - drop;
+  hy_solver_params sp = r.sp;
+  const long long mc = (long long)r.m >> (nlev - 1);
+  const double nc = r.dim * std::pow(r.degree * (double)mc + 1.0, r.dim);
+  if (drop > 0 && nc > 6000.0) sp.coarse_solver = 0;
+  int64_t bytes = 0;
+  if (hy_footprint(r.dim, r.degree, r.m, nlev, r.np.variant, r.np.level_dtype, &sp, r.fm, &bytes) != HY_OK) return -1;
+  return bytes + (int64_t)sizeof(double) * r.dim * (int64_t)std::llround(std::pow(r.degree * r.m + 1.0, r.dim));
+}
+
+void run_request(hy_server* sv, Req& r, cudaStream_t st) {
+  for (int drop = 0;; ++drop) {
+    bool coarse_indefinite = false;
+    r.status = run_attempt(r, drop, sv->device, st, &coarse_indefinite);
+    r.dropped = drop;
+    if (!coarse_indefinite || r.nlev - drop <= 2) return;
+    // retry with the coarsest level dropped if the budget has room for it
+    const int64_t need = attempt_bytes(r, drop + 1);
+    if (need < 0) return;
+    {
+      std::lock_guard<std::mutex> lock(sv->mu);
+      const int64_t extra = std::max<int64_t>(0, need - r.bytes);
+      if (sv->in_use + extra > sv->budget) return;
+      sv->in_use += extra;
+      sv->peak = std::max(sv->peak, sv->in_use);
+      r.bytes += extra;
+      sv->retried++;
+    }
+    r.rep = hy_newton_report{};
+  }
 }
 
 void worker_loop(hy_server* sv) {
@@ -130,7 +183,7 @@ void worker_loop(hy_server* sv) {
       r->t_start = Clock::now();
     }
     sv->cv_work.notify_all();  // the next head may fit as well
-    run_request(*r, sv->device, st);
+    run_request(sv, *r, st);
     {
       std::lock_guard<std::mutex> lock(sv->mu);
       sv->in_use -= r->bytes;
@@ -274,6 +327,7 @@ hy_status hy_server_stats_get(hy_server* sv, hy_server_stats* st) {
   st->bytes_in_use = sv->in_use;
   st->bytes_peak = sv->peak;
   st->budget = sv->budget;
+  st->retried = sv->retried;
   return HY_OK;
 }
 

@@ -80,3 +80,35 @@ def test_admission_respects_the_budget():
         with pytest.raises(HyError) as e:
             s.submit(request_problem(big), newton(big, level_dtype=1))
         assert e.value.status == "HY_ERR_OOM"
+
+
+def test_indefinite_coarse_level_is_retried_with_one_level_fewer():
+    """A 3D Q1 48^3 request with a small 85x-stiff inclusion under 14.6 % compression: on the 3^3 coarsest
+    mesh its tangent turns indefinite in load step 2 (HY_ERR_NOCONV from the V-cycle). The server runs it
+    again with the coarsest level dropped (6^3) and the request completes, with the solution of a direct
+    4-level solve (1e-8)."""
+    torch = require_gpu()
+    from paper_1904_13131_gb300.api import Context, HyError, Server, SolverParams
+    q = {"dim": 3, "k": 1, "m": 48, "levels": 5, "ratio": 84.58656300151284, "radius": 0.13719100305812448,
+         "compression": 0.14644174579698413}
+    pr = request_problem(q)
+    solver = SolverParams(4, 1, 0.6, 1.2, 30, 0, 1e-3, 1, -1, 0, -1)
+    with context(pr) as c:  # the 5-level hierarchy fails on its coarsest level
+        c.set_solver_params(coarse_solver=1)
+        u = torch.zeros(c.num_dofs(), dtype=torch.float64, device="cuda")
+        with pytest.raises(HyError) as e:
+            c.newton_solve(u, newton(q, level_dtype=1))
+        assert e.value.status == "HY_ERR_NOCONV"
+    q4 = dict(q, levels=4)
+    with context(request_problem(q4)) as c:  # the same problem on 4 levels (48 -> 6)
+        c.set_solver_params(coarse_solver=1)
+        u4 = torch.zeros(c.num_dofs(), dtype=torch.float64, device="cuda")
+        c.newton_solve(u4, newton(q, level_dtype=1))
+    with Server(0, budget_bytes=8 << 30, max_active=1) as sv:
+        t = sv.submit(pr, newton(q, level_dtype=1), solver)
+        sv.wait(t, 600.0)
+        r = sv.poll(t, want_u=True)
+        st = sv.stats()
+    assert r["state"] == 2 and st["retried"] == 1 and st["failed"] == 0
+    ref = u4.cpu().numpy()
+    assert np.linalg.norm(r["u"] - ref) / np.linalg.norm(ref) < 1e-8

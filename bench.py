@@ -293,6 +293,19 @@ def f32_steady_state(torch, api, inputs, dev, hbm):
     return out
 
 
+def whole_job_rate(torch, dist, local_ms, units_per_rank, device):
+    """Whole-job throughput of N replicas: the units all ranks processed over the slowest rank's timed region
+    (max over ranks), in units per second; returns (rate, slowest ms). dist: torch.distributed or None."""
+    t = float(local_ms)
+    world = 1
+    if dist is not None:
+        tt = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+        world = dist.get_world_size()
+    return units_per_rank * world / (t * 1e-3), t
+
+
 def newton_summary(rep):
     lat = np.array(rep["solve_ms"])
     return {"solve_p50_ms": float(np.percentile(lat, 50)), "solve_p99_ms": float(np.percentile(lat, 99)),
@@ -667,12 +680,8 @@ def main():
         dist.barrier()
     wall = time.perf_counter() - t_wall
     clocks = clk.stop()
-    total_ms = float(ms.sum())
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = 3 * n * args.steps * world / (total_ms * 1e-3) / 1e9
+    rate, total_ms = whole_job_rate(torch, dist, float(ms.sum()), 3 * n * args.steps, dev)
+    value = rate / 1e9
     per_var_ms = {v: float(np.median(ms[:, i])) for i, v in enumerate(VARIANTS)}
 
     # ---- per-variant FP64 / FP32 throughput (untimed for the headline) ---------------------------
@@ -756,8 +765,8 @@ def main():
         e1.synchronize()
         if it >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
-    e2e_total = float(np.sum(e2e_ms))
-    e2e = {"value": 3 * n * len(e2e_ms) * world / (e2e_total * 1e-3) / 1e9, "unit": UNIT,
+    e2e_rate, _ = whole_job_rate(torch, dist, float(np.sum(e2e_ms)), 3 * n * len(e2e_ms), dev)
+    e2e = {"value": e2e_rate / 1e9, "unit": UNIT,
            "h2d_bytes_per_step": int(x.numel() * 8), "d2h_bytes_per_step": int(3 * n * 8)}
 
     solve = None

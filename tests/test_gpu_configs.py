@@ -19,6 +19,7 @@ from oracle.newton import newton_solve
 from paper_1904_13131_gb300 import inputs
 
 from .gpu_util import context, rel, require_gpu
+from .mesh_util import cells_of_node
 
 pytestmark = pytest.mark.gpu
 
@@ -55,17 +56,6 @@ def test_config2_full_size_apply_every_output(torch):
             ctx.set_displacement(ud, var, level_dtype=1)
             assert rel(ctx.apply_tangent(xd).cpu().numpy(), y_ref) < 1e-12, var
             assert rel(ctx.apply_tangent(xd.float(), dtype=1).cpu().numpy(), y_ref) < 2e-6, var
-
-
-def cells_of_node(k, m, idx):
-    """Cells (x-fastest index) whose closure holds the lattice node with multi-index idx."""
-    per_axis = []
-    for i in idx:
-        cs = {min(i // k, m - 1)}
-        if i % k == 0 and i > 0:
-            cs.add(i // k - 1)
-        per_axis.append(sorted(cs))
-    return [c0 + m * (c1 + m * c2) for c2 in per_axis[2] for c1 in per_axis[1] for c0 in per_axis[0]]
 
 
 def test_config3_largest_mesh_sampled_outputs(torch):

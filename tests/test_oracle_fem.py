@@ -246,3 +246,28 @@ def test_element_apply_and_diagonal_match_assembled(dim, k, m):
     A = p.tangent(u)
     np.testing.assert_allclose(p.apply(u, x), A @ x, atol=1e-13 * np.abs(A @ x).max())
     np.testing.assert_allclose(p.diagonal(u), A.diagonal(), atol=1e-14 * abs(A).max())
+
+
+@pytest.mark.parametrize("k,m", [(1, 4), (2, 3), (3, 2)])
+def test_sampled_action_from_the_cells_of_each_node(k, m):
+    """The sampled-output check of the largest meshes: y at a dof from only the cells holding its node
+    (apply_cells) equals the full element-by-element action there; the cell lists match a brute-force
+    search of the connectivity."""
+    from paper_1904_13131_gb300 import inputs
+
+    from .mesh_util import cells_of_node
+    pr = inputs.problem(3, k, m, top=0)
+    P = Problem(3, k, m, pr["ids"][0], pr["mu"], pr["lam"], pr["masks"])
+    L = k * m + 1
+    for node in range(P.n_nodes):
+        idx = (node % L, (node // L) % L, node // (L * L))
+        assert sorted(cells_of_node(k, m, idx)) == np.nonzero((P.cell_nodes == node).any(axis=1))[0].tolist()
+    u = inputs.smooth_field(3, k, m, seed=0)
+    x = inputs.gaussian_vector(P.n_dofs, 1)
+    full = P.apply(u, x)
+    dofs = np.arange(0, P.n_dofs, 7)
+    cells = sorted({c for d in dofs for c in cells_of_node(k, m, ((d // 3) % L, (d // 3 // L) % L, d // 3 // (L * L)))})
+    y = np.zeros(P.n_dofs)
+    P.apply_cells(u, np.where(P.constrained, 0.0, x), np.array(cells), y)
+    sampled = np.where(P.constrained[dofs], x[dofs], y[dofs])
+    np.testing.assert_allclose(sampled, full[dofs], rtol=1e-13, atol=1e-13 * np.abs(full).max())

@@ -66,7 +66,10 @@ typedef enum { HY_T4 = 0, HY_T2 = 1, HY_FC = 2, HY_SC = 3, HY_NC = 4 } hy_varian
 hy_status hy_create(hy_ctx **out, int device, void *cuda_stream);
 /* Free every device buffer the context owns. NULL is accepted. */
 void hy_destroy(hy_ctx *ctx);
+/* Name of a status code ("HY_OK", ..., "HY_ERR_UNKNOWN" for other values); a static string. */
 const char *hy_status_str(hy_status s);
+/* Message of the context's most recent failed call (empty if none failed yet; a later success does not
+ * clear it); owned by the context, valid until its next call. NULL context: "null context". */
 const char *hy_last_error(const hy_ctx *ctx);
 
 /* Mesh and level hierarchy (Sec. 6: a hierarchy of uniformly refined meshes; Sec. 3: Q_k space).
@@ -183,7 +186,10 @@ typedef struct {
                                the preconditioner beyond rounding. */
 } hy_solver_params;
 
+/* Replace the context's solver parameters (copied); they take effect at the next hy_set_displacement.
+ * HY_ERR_ARG for a value out of the ranges above. */
 hy_status hy_set_solver_params(hy_ctx *ctx, const hy_solver_params *p);
+/* Copy the context's current solver parameters (the defaults above before any hy_set_solver_params). */
 hy_status hy_get_solver_params(const hy_ctx *ctx, hy_solver_params *p);
 
 /* Estimates held by the context after set_displacement: lmax of level `level` (levels >= 1), and
@@ -203,6 +209,7 @@ hy_status hy_level_displacement(const hy_ctx *ctx, int level, double *u_dev);
 /* Transfers between level l-1 (coarse) and l (fine), constrained entries zeroed (Sec. 6):
  * fine += P coarse (prolongate_add) and coarse = P^T fine (restrict). dtype as for the level. */
 hy_status hy_prolongate_add(hy_ctx *ctx, int fine_level, const void *coarse_dev, void *fine_dev, hy_dtype dtype);
+/* (restrict: see above) */
 hy_status hy_restrict(hy_ctx *ctx, int fine_level, const void *fine_dev, void *coarse_dev, hy_dtype dtype);
 
 /* Preconditioned CG (FP64) on the finest level: A~ x = b with the V-cycle preconditioner, zero
@@ -245,6 +252,7 @@ typedef struct {
   double total_ms;            /* whole call */
 } hy_newton_report;
 
+/* Fill p with the defaults in brackets above (zero tractions and prescribed values). */
 void hy_newton_default_params(hy_newton_params *p);
 /* Solve for the equilibrium displacement: u_inout_dev (fine FP64, device) holds the start state on
  * entry (its constrained values are overwritten by the load path) and the solution on return; on
@@ -310,7 +318,9 @@ typedef struct hy_batch hy_batch;
 /* Group count distinct contexts (same device, dimension and degree, mesh set up). HY_ERR_ARG for an
  * empty, oversized, mixed or repeated list; HY_ERR_STATE for a context without a mesh. */
 hy_status hy_batch_create(hy_batch **out, hy_ctx *const *ctxs, int count);
+/* Free the batch's graphs, streams and buffers (the contexts stay). NULL is accepted. */
 void hy_batch_destroy(hy_batch *b);
+/* Message of the batch's most recent failed call; owned by the batch. NULL batch: "null batch". */
 const char *hy_batch_last_error(const hy_batch *b);
 
 /* y_i = A~_i x_i on the finest level of every context i, in one list launch (as hy_apply_tangent,
@@ -363,6 +373,8 @@ typedef struct {
                        solve when it exceeds the dense-inverse limit) */
 } hy_server_stats;
 
+/* Start a server on `device` with `max_active` workers (1..64), admitting requests while their summed
+ * footprints stay within hbm_budget_bytes. HY_ERR_ARG for a bad device, budget or worker count. */
 hy_status hy_server_create(hy_server **out, int device, int64_t hbm_budget_bytes, int max_active);
 /* Running requests finish; queued ones are dropped. */
 void hy_server_destroy(hy_server *s);
@@ -376,6 +388,7 @@ hy_status hy_server_poll(hy_server *s, uint64_t ticket, int *state, hy_newton_re
 hy_status hy_server_wait(hy_server *s, uint64_t ticket, double timeout_s);
 /* Forget a finished request (frees its host copy of the solution). */
 hy_status hy_server_release(hy_server *s, uint64_t ticket);
+/* Counters and device bytes of the server (a consistent snapshot). */
 hy_status hy_server_stats_get(hy_server *s, hy_server_stats *st);
 
 #ifdef __cplusplus

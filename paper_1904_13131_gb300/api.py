@@ -34,12 +34,14 @@ EXPORTED = ("hy_create", "hy_destroy", "hy_status_str", "hy_last_error", "hy_mes
 
 
 class HyError(RuntimeError):
+    """A failed C-ABI call: .status is the hy_status name ("HY_ERR_ARG", ...), the message the library's."""
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
         self.status = STATUS.get(status, str(status))
 
 
 class SolverParams(ctypes.Structure):
+    """ctypes mirror of hy_solver_params (include/hyperelastic.h)."""
     _fields_ = [("cheb_degree", ctypes.c_int), ("cheb_sweeps", ctypes.c_int), ("cheb_lo", ctypes.c_double),
                 ("cheb_hi", ctypes.c_double), ("eig_iters", ctypes.c_int), ("coarse_eig_iters", ctypes.c_int),
                 ("coarse_reduction", ctypes.c_double), ("coarse_solver", ctypes.c_int), ("kernel_form", ctypes.c_int),
@@ -47,6 +49,7 @@ class SolverParams(ctypes.Structure):
 
 
 class NewtonParams(ctypes.Structure):
+    """ctypes mirror of hy_newton_params (include/hyperelastic.h)."""
     _fields_ = [("load_steps", ctypes.c_int), ("max_newton", ctypes.c_int), ("newton_rtol", ctypes.c_double),
                 ("newton_atol", ctypes.c_double), ("cg_rtol", ctypes.c_double), ("cg_max_iter", ctypes.c_int),
                 ("variant", ctypes.c_int), ("level_dtype", ctypes.c_int),
@@ -55,6 +58,7 @@ class NewtonParams(ctypes.Structure):
 
 
 class NewtonReport(ctypes.Structure):
+    """ctypes mirror of hy_newton_report (include/hyperelastic.h)."""
     _fields_ = [("load_steps_done", ctypes.c_int), ("newton_iterations", ctypes.c_int * 64),
                 ("cg_iterations_total", ctypes.c_int), ("cg_iterations_max", ctypes.c_int),
                 ("final_residual", ctypes.c_double), ("backtracks", ctypes.c_int), ("n_solves", ctypes.c_int),
@@ -63,6 +67,7 @@ class NewtonReport(ctypes.Structure):
 
 
 class Request(ctypes.Structure):
+    """ctypes mirror of hy_request (include/hyperelastic.h)."""
     _fields_ = [("dim", ctypes.c_int), ("degree", ctypes.c_int), ("cells_per_dir", ctypes.c_int),
                 ("n_levels", ctypes.c_int), ("face_masks", ctypes.c_uint32 * 6), ("cell_mat_levels", ctypes.c_void_p),
                 ("mu", ctypes.POINTER(ctypes.c_double)), ("lambda_", ctypes.POINTER(ctypes.c_double)),
@@ -71,6 +76,7 @@ class Request(ctypes.Structure):
 
 
 class ServerStats(ctypes.Structure):
+    """ctypes mirror of hy_server_stats (include/hyperelastic.h)."""
     _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "active", "queued", "bytes_in_use",
                                               "bytes_peak", "budget", "retried")]
 
@@ -175,6 +181,7 @@ class Context:
         self.dim = self.degree = self.m = self.n_levels = None
 
     def close(self):
+        """hy_destroy; idempotent."""
         if getattr(self, "h", None):
             self.lib.hy_destroy(self.h)
             self.h = None
@@ -203,17 +210,20 @@ class Context:
         return _ptr(t)
 
     def empty(self, level=-1, dtype=F64):
+        """An uninitialised device vector of a level's dofs (FP64; FP32 for dtype=F32)."""
         torch = self._torch
         return torch.empty(self.num_dofs(level), dtype=torch.float32 if dtype == F32 else torch.float64,
                            device=self.device)
 
     # ---- mesh / material -------------------------------------------------------------------------
     def mesh_setup(self, dim, degree, cells_per_dir, n_levels, face_masks):
+        """hy_mesh_setup: dim 2|3, degree 1-4, cells per direction, levels; face_masks[2*dim] per face."""
         fm = (ctypes.c_uint32 * (2 * dim))(*[int(x) for x in face_masks[: 2 * dim]])
         self._ck(self.lib.hy_mesh_setup(self.h, dim, degree, cells_per_dir, n_levels, fm))
         self.dim, self.degree, self.m, self.n_levels = dim, degree, cells_per_dir, n_levels
 
     def num_dofs(self, level=-1):
+        """hy_num_dofs of a level (-1 = finest)."""
         n = ctypes.c_int64()
         self._ck(self.lib.hy_num_dofs(self.h, level, ctypes.byref(n)))
         return n.value
@@ -233,6 +243,7 @@ class Context:
         self._ck(self.lib.hy_set_material_law(self.h, int(law)))
 
     def set_material(self, level, cell_mat, mu, lam):
+        """hy_set_material of one level: per-cell material ids (uint8, x fastest), per-id mu and lambda."""
         ids = np.ascontiguousarray(cell_mat, dtype=np.uint8)
         mu = np.ascontiguousarray(mu, dtype=np.float64)
         lam = np.ascontiguousarray(lam, dtype=np.float64)
@@ -253,10 +264,13 @@ class Context:
 
     # ---- state / operators ----------------------------------------------------------------------
     def set_displacement(self, u, variant="T4", level_dtype=F64):
+        """hy_set_displacement: linearise every level about u (finest, FP64 on the device) in the given
+        variant; level_dtype=F32 builds the mixed-precision V-cycle."""
         self._ck(self.lib.hy_set_displacement(self.h, self._vec(u, self.num_dofs(), F64), VARIANTS[variant],
                                               level_dtype))
 
     def apply_tangent(self, x, y=None, dtype=F64):
+        """hy_apply_tangent: y = A(u) x on the finest level in dtype (F64, F32 or FF); returns y."""
         n = self.num_dofs()
         if y is None:
             y = self.empty(-1, dtype)
@@ -264,6 +278,7 @@ class Context:
         return y
 
     def vmult(self, level, x, y=None, dtype=F64):
+        """hy_vmult: y = A_l x on level `level`; returns y."""
         n = self.num_dofs(level)
         if y is None:
             y = self.empty(level, dtype)
@@ -271,6 +286,7 @@ class Context:
         return y
 
     def residual(self, u, r=None):
+        """hy_residual: r = R(u) in FP64, zero on constrained dofs; returns r."""
         n = self.num_dofs()
         if r is None:
             r = self.empty()
@@ -278,11 +294,13 @@ class Context:
         return r
 
     def diagonal(self, level=-1, dtype=F64):
+        """hy_diagonal: the diagonal of a level's tangent (1 on constrained dofs)."""
         d = self.empty(level, dtype)
         self._ck(self.lib.hy_diagonal(self.h, level, self._vec(d, self.num_dofs(level), dtype), dtype))
         return d
 
     def gmg_vcycle(self, r, z=None):
+        """hy_gmg_vcycle: z = V r, one V-cycle on the finest level; returns z."""
         n = self.num_dofs()
         if z is None:
             z = self.empty()
@@ -290,6 +308,8 @@ class Context:
         return z
 
     def set_solver_params(self, **kw):
+        """hy_set_solver_params with the named hy_solver_params fields changed (level_variant also by
+        variant name)."""
         p = self.get_solver_params()
         for k, v in kw.items():
             if k == "level_variant" and isinstance(v, str):
@@ -298,36 +318,43 @@ class Context:
         self._ck(self.lib.hy_set_solver_params(self.h, ctypes.byref(p)))
 
     def get_solver_params(self):
+        """hy_get_solver_params as a SolverParams structure."""
         p = SolverParams()
         self._ck(self.lib.hy_get_solver_params(self.h, ctypes.byref(p)))
         return p
 
     def level_info(self, level):
+        """hy_level_info: lmax of a level and, for the coarsest, its Chebyshev interval and degree."""
         lm, lo, hi, dg = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
         self._ck(self.lib.hy_level_info(self.h, level, ctypes.byref(lm), ctypes.byref(lo), ctypes.byref(hi),
                                         ctypes.byref(dg)))
         return {"lmax": lm.value, "coarse_lo": lo.value, "coarse_hi": hi.value, "coarse_degree": dg.value}
 
     def set_level_info(self, level, lmax=0.0, coarse_lo=0.0, coarse_hi=0.0):
+        """hy_set_level_info: impose the eigenvalue estimates of a level instead of computing them."""
         self._ck(self.lib.hy_set_level_info(self.h, level, lmax, coarse_lo, coarse_hi))
 
     def kernel_form(self, level=-1, dtype=F64):
+        """hy_kernel_form: the tangent-action kernel form of a level and precision (-1: no cache)."""
         f = ctypes.c_int()
         self._ck(self.lib.hy_kernel_form(self.h, level, dtype, ctypes.byref(f)))
         return f.value
 
     def level_displacement(self, level):
+        """hy_level_displacement: the displacement carried down to a level (FP64)."""
         u = self.empty(level)
         self._ck(self.lib.hy_level_displacement(self.h, level, self._vec(u, self.num_dofs(level), F64)))
         return u
 
     def prolongate_add(self, fine_level, coarse, fine, dtype=F64):
+        """hy_prolongate_add: fine += P coarse (levels fine_level - 1 -> fine_level); returns fine."""
         fl = fine_level if fine_level >= 0 else self.n_levels + fine_level
         self._ck(self.lib.hy_prolongate_add(self.h, fl, self._vec(coarse, self.num_dofs(fl - 1), dtype),
                                             self._vec(fine, self.num_dofs(fl), dtype), dtype))
         return fine
 
     def restrict(self, fine_level, fine, coarse=None, dtype=F64):
+        """hy_restrict: coarse = P^T fine; returns coarse."""
         fl = fine_level if fine_level >= 0 else self.n_levels + fine_level
         if coarse is None:
             coarse = self.empty(fl - 1, dtype)
@@ -336,6 +363,7 @@ class Context:
         return coarse
 
     def pcg(self, b, x=None, rtol=1e-8, max_iter=1000):
+        """hy_pcg: V-cycle-preconditioned CG from zero to ||r|| <= rtol ||b||; returns (x, iterations)."""
         n = self.num_dofs()
         if x is None:
             x = self.empty()
@@ -346,6 +374,8 @@ class Context:
 
     @staticmethod
     def newton_params(**kw):
+        """hy_newton_default_params with the named fields changed: face_values and face_traction as
+        [face][component] lists, variant by name."""
         p = NewtonParams()
         load_library().hy_newton_default_params(ctypes.byref(p))
         face_values = kw.pop("face_values", None)
@@ -373,6 +403,8 @@ class Context:
         return f
 
     def newton_solve(self, u, params: NewtonParams):
+        """hy_newton_solve: u (finest, FP64 on the device) in and out; returns the report as a dict and
+        raises HyError on failure (u then holds the last accepted iterate)."""
         rep = NewtonReport()
         st = self.lib.hy_newton_solve(self.h, ctypes.byref(params), self._vec(u, self.num_dofs(), F64),
                                       ctypes.byref(rep))
@@ -387,17 +419,20 @@ class Context:
         return report
 
     def dot(self, a, b):
+        """hy_dot: FP64 dot product of two finest-level vectors in a fixed summation order."""
         n = a.numel()
         out = ctypes.c_double()
         self._ck(self.lib.hy_dot(self.h, self._vec(a, n, F64), self._vec(b, n, F64), n, ctypes.byref(out)))
         return out.value
 
     def bytes(self):
+        """hy_ctx_bytes: device bytes the context owns."""
         b = ctypes.c_int64()
         self._ck(self.lib.hy_ctx_bytes(self.h, ctypes.byref(b)))
         return b.value
 
     def kernel_launches(self):
+        """hy_kernel_launches: kernels the context has launched so far."""
         c = ctypes.c_int64()
         self._ck(self.lib.hy_kernel_launches(self.h, ctypes.byref(c)))
         return c.value
@@ -455,6 +490,7 @@ class Batch:
         self.h = h
 
     def close(self):
+        """hy_batch_destroy; idempotent (the contexts stay)."""
         if getattr(self, "h", None):
             self.lib.hy_batch_destroy(self.h)
             self.h = None
@@ -481,6 +517,7 @@ class Batch:
         return (ctypes.c_void_p * len(ts))(*[c._vec(t, c.num_dofs(), dtype).value for c, t in zip(self.contexts, ts)])
 
     def apply(self, xs, ys=None, dtype=F64):
+        """hy_batch_apply: ys[i] = A_i xs[i] for every context in one list launch; returns ys."""
         if ys is None:
             ys = [c.empty(-1, dtype) for c in self.contexts]
         self._ck(self.lib.hy_batch_apply(self.h, self._vecs(xs, dtype), self._vecs(ys, dtype), dtype))
@@ -497,11 +534,13 @@ class Batch:
         return xs, list(its), list(sts)
 
     def kernel_launches(self):
+        """hy_batch_kernel_launches: kernels the batch has launched so far."""
         v = ctypes.c_int64()
         self._ck(self.lib.hy_batch_kernel_launches(self.h, ctypes.byref(v)))
         return v.value
 
     def kernel_form(self, dtype=F64):
+        """hy_batch_kernel_form: the list launch's kernel form for a precision (-1: not chosen yet)."""
         v = ctypes.c_int()
         self._ck(self.lib.hy_batch_kernel_form(self.h, dtype, ctypes.byref(v)))
         return v.value
@@ -520,6 +559,7 @@ class Server:
         self._steps = {}
 
     def close(self):
+        """hy_server_destroy: running requests finish, queued ones are dropped; idempotent."""
         if getattr(self, "h", None):
             self.lib.hy_server_destroy(self.h)
             self.h = None
@@ -563,6 +603,8 @@ class Server:
         return t.value
 
     def poll(self, ticket, want_u=False):
+        """hy_server_poll: {"state": 0 queued | 1 running | 2 done | 3 failed, "status"} plus, once finished,
+        the report, the latency and (want_u, done) the solution on the host."""
         state, rep, lat = ctypes.c_int(), NewtonReport(), ctypes.c_double()
         steps, n = self._steps[ticket]
         u = np.empty(n) if want_u else None
@@ -575,14 +617,17 @@ class Server:
         return out
 
     def wait(self, ticket, timeout_s=600.0):
+        """hy_server_wait: block until the request has finished; HyError (HY_ERR_TIMEOUT) after timeout_s."""
         st = self.lib.hy_server_wait(self.h, ticket, timeout_s)
         if st != 0:
             raise HyError(st, "hy_server_wait")
 
     def release(self, ticket):
+        """hy_server_release: forget a finished request."""
         self.lib.hy_server_release(self.h, ticket)
 
     def stats(self):
+        """hy_server_stats_get as a dict."""
         s = ServerStats()
         st = self.lib.hy_server_stats_get(self.h, ctypes.byref(s))
         if st != 0:

@@ -278,7 +278,8 @@ hy_status hy_dot(hy_ctx *ctx, const double *a_dev, const double *b_dev, int64_t 
  * 128 KiB per device, held until the process exits); n > HY_DOT_NOALLOC_MAX_N returns HY_ERR_ARG.
  * The first call on each device looks up that array's device address, so make it before any stream
  * capture. All calls share the array: calls that overlap on the GPU (different streams without
- * ordering) race; serialise them. The summation order is fixed, so repeated calls agree bitwise. */
+ * ordering) race; serialise them. The summation order is fixed, so repeated calls agree bitwise. The
+ * calling thread's current device is the same after the call as before it. */
 #define HY_DOT_NOALLOC_MAX_N (16384LL * 4096LL) /* 67,108,864 elements */
 hy_status hy_dot_noalloc(int device, void *cuda_stream, const double *a_dev, const double *b_dev, int64_t n,
                          double *result);

@@ -5,7 +5,8 @@ A(u) du = -F(u), on the free dofs with scipy's sparse direct solver. Readings of
 silent: displacement-driven loading in S equal steps; the prescribed increment of a
 step is lifted into the first linear solve (du_c given, A_ff du_f = -R_f - A_fc du_c); the step
 converges when ||R_free|| <= max(rtol * ||first right-hand side||, atol); a step that makes J <= 0
-is halved up to 5 times before the solve reports failure.
+at a Gauss point (Sec. 2.1 requires J > 0) is halved up to 5 times before the solve reports failure
+(reading O15). The report lists, per load step, how many halvings each accepted Newton update took.
 """
 from __future__ import annotations
 
@@ -25,12 +26,13 @@ def newton_solve(prob: Problem, u_final_bc, load_steps=5, rtol=1e-10, atol=1e-14
     u = np.zeros(prob.n_dofs) if u0 is None else np.array(u0, dtype=float)
     cons = prob.constrained
     free = prob.free
-    report = {"iterations": [], "residuals": []}
+    report = {"iterations": [], "residuals": [], "halvings": []}
     for s in range(1, load_steps + 1):
         target = np.where(cons, (s / load_steps) * np.asarray(u_final_bc, dtype=float), 0.0)
         ref = None
         its = 0
         res_hist = []
+        halv = []
         while True:
             du0 = np.where(cons, target - u, 0.0)
             R = prob.residual_raw(u)
@@ -54,15 +56,17 @@ def newton_solve(prob: Problem, u_final_bc, load_steps=5, rtol=1e-10, atol=1e-14
             else:
                 du = du0 + linear_solve(prob, u, rhs)
             step = 1.0
-            for _ in range(6):
+            for h in range(6):
                 trial = u + step * du
                 if prob.min_jacobian(trial) > 0:
                     break
                 step *= 0.5
             else:
                 raise FloatingPointError("J <= 0 after 5 halvings")
+            halv.append(h)
             u = trial
             its += 1
         report["iterations"].append(its)
         report["residuals"].append(res_hist)
+        report["halvings"].append(halv)
     return u, report

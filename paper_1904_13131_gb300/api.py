@@ -442,11 +442,22 @@ DOT_NOALLOC_MAX_N = 16384 * 4096
 
 
 def dot_noalloc(a, b, device: int = 0, stream=None) -> float:
-    """a . b through hy_dot_noalloc: no context and no device allocation (see include/hyperelastic.h)."""
+    """a . b through hy_dot_noalloc: no context and no device allocation (see include/hyperelastic.h).
+    a and b must be contiguous float64 tensors of equal length on cuda:device (ValueError otherwise,
+    before anything reaches the GPU)."""
     import torch
+    dev = torch.device("cuda", device)
+    for name, t in (("a", a), ("b", b)):
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous torch.float64 tensor")
+    if a.numel() != b.numel():
+        raise ValueError(f"a and b differ in length ({a.numel()} vs {b.numel()})")
+    for name, t in (("a", a), ("b", b)):
+        if t.device != dev:
+            raise ValueError(f"{name} is on {t.device}, not on {dev}")
     lib = load_library()
     if stream is None:
-        stream = torch.cuda.current_stream(torch.device("cuda", device))
+        stream = torch.cuda.current_stream(dev)
     out = ctypes.c_double()
     st = lib.hy_dot_noalloc(device, ctypes.c_void_p(stream.cuda_stream), _ptr(a), _ptr(b), a.numel(), ctypes.byref(out))
     if st != 0:

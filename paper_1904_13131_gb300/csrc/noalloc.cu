@@ -81,12 +81,10 @@ hy_status scratch_address(int device, double** out) {
 
 }  // namespace
 
-extern "C" hy_status hy_dot_noalloc(int device, void* cuda_stream, const double* a_dev, const double* b_dev,
-                                    int64_t n, double* result) {
-  if (!a_dev || !b_dev || !result || n < 0) return HY_ERR_ARG;
-  if (n > HY_DOT_NOALLOC_MAX_N) return HY_ERR_ARG;  // the partial sums would not fit the fixed array
-  if (device < 0 || device >= NA_MAX_DEVICES) return HY_ERR_ARG;
-  if (cudaSetDevice(device) != cudaSuccess) return HY_ERR_CUDA;
+namespace {
+
+hy_status dot_noalloc_on_current(int device, void* cuda_stream, const double* a_dev, const double* b_dev,
+                                 int64_t n, double* result) {
   if (n == 0) {
     *result = 0.0;
     return HY_OK;
@@ -103,4 +101,21 @@ extern "C" hy_status hy_dot_noalloc(int device, void* cuda_stream, const double*
     return HY_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return HY_ERR_CUDA;
   return HY_OK;
+}
+
+}  // namespace
+
+// The call makes `device` current for its own launches and gives the calling thread back the device
+// that was current on entry, on every return path.
+extern "C" hy_status hy_dot_noalloc(int device, void* cuda_stream, const double* a_dev, const double* b_dev,
+                                    int64_t n, double* result) {
+  if (!a_dev || !b_dev || !result || n < 0) return HY_ERR_ARG;
+  if (n > HY_DOT_NOALLOC_MAX_N) return HY_ERR_ARG;  // the partial sums would not fit the fixed array
+  if (device < 0 || device >= NA_MAX_DEVICES) return HY_ERR_ARG;
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess) return HY_ERR_CUDA;
+  if (prev != device && cudaSetDevice(device) != cudaSuccess) return HY_ERR_CUDA;
+  const hy_status st = dot_noalloc_on_current(device, cuda_stream, a_dev, b_dev, n, result);
+  if (prev != device && cudaSetDevice(prev) != cudaSuccess) return st == HY_OK ? HY_ERR_CUDA : st;
+  return st;
 }

@@ -115,3 +115,64 @@ def test_checkpoint_and_resume_continue_the_load_path(torch):
         r2 = sv.poll(t2, want_u=True)
         assert r2["state"] == 2 and r2["report"]["load_steps_done"] == 5
     assert rel(r2["u"], ref) < 1e-10
+
+
+def uniaxial_setup(dim, k, m, L):
+    """Homogeneous body (mu = 1, nu = 0.3), bottom clamped, side faces held in their normal component, top free."""
+    masks = [0] * (2 * dim)
+    for a in range(dim - 1):
+        masks[2 * a] = masks[2 * a + 1] = 1 << a
+    masks[2 * (dim - 1)] = (1 << dim) - 1
+    mu, lam = inputs.material_table(1.0)
+    ms = inputs.level_sizes(m, L)
+    pr = {"dim": dim, "k": k, "m": m, "levels_m": ms, "ids": [np.zeros(ml**dim, np.uint8) for ml in ms],
+          "mu": mu, "lam": lam, "masks": masks}
+    return pr
+
+
+def traction_top(dim, t):
+    tr = np.zeros((6, 3))
+    tr[2 * dim - 1][dim - 1] = -t
+    return tr
+
+
+@pytest.mark.parametrize("dim,k,m,L", [(2, 1, 4, 2), (2, 2, 4, 2), (3, 1, 4, 2), (3, 2, 4, 2)])
+@pytest.mark.parametrize("t", [7.5, 12.0])
+def test_newton_step_halving_matches_oracle(torch, dim, k, m, L, t):
+    """Reading O15 (J > 0, Sec. 2.1) on the GPU: one load step of a compressive dead traction whose first
+    Newton update would fold every cell. The GMG-CG Newton halves it as often as the oracle does (one
+    halving for t = 7.5, two for t = 12; counted in the report's backtracks) and converges to the oracle's
+    solution (1e-8)."""
+    from paper_1904_13131_gb300.api import Context
+    pr = uniaxial_setup(dim, k, m, L)
+    P = oracle_level(pr)
+    tr = traction_top(dim, t)
+    u_ref, rep_ref = newton_solve(P, np.zeros(P.n_dofs), load_steps=1, f_ext=P.face_load(tr[: 2 * dim, :dim]))
+    with context(pr) as ctx:
+        for ldt in (0, 1):
+            u = torch.zeros(ctx.num_dofs(), dtype=torch.float64, device="cuda")
+            rep = ctx.newton_solve(u, Context.newton_params(load_steps=1, level_dtype=ldt, face_traction=tr))
+            assert rep["load_steps_done"] == 1
+            assert rep["backtracks"] == sum(rep_ref["halvings"][0]) == (1 if t == 7.5 else 2)
+            assert abs(rep["newton_iterations"][0] - rep_ref["iterations"][0]) <= 1
+            assert rel(u.cpu().numpy(), u_ref) < 1e-8, (ldt, rel(u.cpu().numpy(), u_ref))
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_newton_reports_jneg_after_five_halvings(torch, dim):
+    """t = 200: every halving down to 1/32 of the first update still folds the cells. The solve returns
+    HY_ERR_JNEG (the oracle raises), leaves u at the last accepted iterate (zero), and the context stays
+    usable: the next solve on it succeeds."""
+    from paper_1904_13131_gb300.api import Context, HyError
+    pr = uniaxial_setup(dim, 1, 4, 2)
+    P = oracle_level(pr)
+    with pytest.raises(FloatingPointError):
+        newton_solve(P, np.zeros(P.n_dofs), load_steps=1, f_ext=P.face_load(traction_top(dim, 200.0)[: 2 * dim, :dim]))
+    with context(pr) as ctx:
+        u = torch.zeros(ctx.num_dofs(), dtype=torch.float64, device="cuda")
+        with pytest.raises(HyError) as e:
+            ctx.newton_solve(u, Context.newton_params(load_steps=1, face_traction=traction_top(dim, 200.0)))
+        assert e.value.status == "HY_ERR_JNEG"
+        assert float(u.abs().max()) == 0.0
+        rep = ctx.newton_solve(u, Context.newton_params(load_steps=1, face_traction=traction_top(dim, 7.5)))
+        assert rep["load_steps_done"] == 1 and rep["backtracks"] == 1

@@ -1,11 +1,13 @@
-"""The solve server: admission by device footprint, continuous batching, and results that do not
-depend on what else is running (each request alone vs in the mix agree to 1e-10 relative)."""
+"""The solve server: admission by device footprint, continuous batching, results that do not depend on
+what else is running (each request alone vs in the mix agree to 1e-10 relative), and served results that
+match the oracle's Newton (1e-8 relative in displacement), the coarse-level retry included."""
 import numpy as np
 import pytest
 
+from oracle.newton import newton_solve
 from paper_1904_13131_gb300 import inputs
 
-from .gpu_util import context, require_gpu
+from .gpu_util import context, oracle_level, rel, require_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -112,3 +114,43 @@ def test_indefinite_coarse_level_is_retried_with_one_level_fewer():
     assert r["state"] == 2 and st["retried"] == 1 and st["failed"] == 0
     ref = u4.cpu().numpy()
     assert np.linalg.norm(r["u"] - ref) / np.linalg.norm(ref) < 1e-8
+
+
+# Served together (four at a time) in mixed precision with the exact FP64 coarse inverse. The last request
+# (3D Q1 12^3, a 60x stiff inclusion of radius 0.12, 10 % compression) has a 3^3 coarsest level whose
+# carried-down tangent turns indefinite during the load path (oracle: smallest eigenvalue -0.61 on the free
+# coarse dofs, while the 6^3 level stays positive definite), so the server reruns it with that level dropped.
+ORACLE_MIX = [{"dim": 2, "k": 2, "m": 16, "levels": 3, "ratio": 10.0, "radius": 0.25, "compression": 0.1},
+              {"dim": 3, "k": 1, "m": 8, "levels": 3, "ratio": 30.0, "radius": 0.2, "compression": 0.05},
+              {"dim": 2, "k": 3, "m": 8, "levels": 3, "ratio": 3.0, "radius": 0.3, "compression": 0.12},
+              {"dim": 3, "k": 2, "m": 4, "levels": 2, "ratio": 80.0, "radius": 0.3, "compression": 0.08},
+              {"dim": 3, "k": 1, "m": 12, "levels": 3, "ratio": 60.0, "radius": 0.12, "compression": 0.1}]
+
+
+def oracle_solution(q):
+    """The oracle's Newton (sparse direct solves, Sec. 3) on the request's problem, 5 load steps."""
+    pr = request_problem(q)
+    P = oracle_level(pr)
+    dim, k, m = q["dim"], q["k"], q["m"]
+    X = inputs.node_coords(dim, k, m)
+    ubc = np.zeros((P.n_nodes, dim))
+    ubc[np.isclose(X[:, dim - 1], 1.0), dim - 1] = -q["compression"]
+    u, _ = newton_solve(P, ubc.reshape(-1), load_steps=5)
+    return u
+
+
+def test_served_results_match_the_oracle():
+    require_gpu()
+    from paper_1904_13131_gb300.api import Server, SolverParams
+    solver = SolverParams(4, 1, 0.6, 1.2, 30, 0, 1e-3, 1, -1, 0, -1)  # exact coarse solve, FP64 inverse
+    with Server(0, budget_bytes=8 << 30, max_active=4) as sv:
+        tickets = [sv.submit(request_problem(q), newton(q, level_dtype=1), solver) for q in ORACLE_MIX]
+        for t in tickets:
+            sv.wait(t, 600.0)
+        served = [sv.poll(t, want_u=True) for t in tickets]
+        st = sv.stats()
+    assert st["completed"] == len(ORACLE_MIX) and st["failed"] == 0 and st["retried"] == 1
+    for q, r in zip(ORACLE_MIX, served):
+        assert r["state"] == 2, (q, r)
+        err = rel(r["u"], oracle_solution(q))
+        assert err < 1e-8, (q, err)

@@ -70,3 +70,20 @@ def test_footprint_is_host_arithmetic(lib):
     assert b64 - api.footprint(3, 2, 32, 4, level_variant="T2") == saved
     with pytest.raises(api.HyError):
         api.footprint(3, 5, 32, 4)
+
+
+def test_dot_noalloc_checks_its_inputs_before_the_gpu():
+    """The binding of the allocation-free dot product refuses a second vector of another length, another
+    dtype, a non-contiguous view or a tensor off the device before anything is launched (the kernel
+    itself would read past the end of the shorter vector)."""
+    torch = pytest.importorskip("torch")
+    from paper_1904_13131_gb300 import api
+    a = torch.zeros(10, dtype=torch.float64)
+    with pytest.raises(ValueError, match="length"):
+        api.dot_noalloc(a, torch.zeros(9, dtype=torch.float64))
+    with pytest.raises(ValueError, match="float64"):
+        api.dot_noalloc(a, torch.zeros(10, dtype=torch.float32))
+    with pytest.raises(ValueError, match="contiguous"):
+        api.dot_noalloc(a, torch.zeros(20, dtype=torch.float64)[::2])
+    with pytest.raises(ValueError, match="not on cuda:0"):
+        api.dot_noalloc(a, torch.zeros(10, dtype=torch.float64))

@@ -3,7 +3,10 @@
 Collected last on purpose (file name): it must pass both alone in a fresh process and after the rest
 of the GPU suite. It calls the C ABI directly and checks the result against hy_dot, the context-based
 entry point, within the relative tolerance of the other FP64 tests (1e-12), on two calls in a row --
-the second call reuses the library's fixed scratch array that the first one left filled.
+the second call reuses the library's fixed scratch array that the first one left filled. It also checks
+what the entry point exists for: after a warm-up call (which looks up the array's address), repeated calls
+leave the device's free memory exactly where it was, so nothing was allocated, and the calling thread's
+current device is unchanged.
 """
 import ctypes
 
@@ -45,6 +48,24 @@ def test_dot_noalloc_matches_context_dot_twice():
         assert lib.hy_dot_noalloc(0, stream, ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()), 0,
                                   ctypes.byref(out)) == 0
         assert out.value == 0.0
+
+
+def test_dot_noalloc_allocates_nothing():
+    torch = require_gpu()
+    from paper_1904_13131_gb300 import api
+    n = 3 * 4096 * 5 + 17
+    a = torch.tensor(inputs.gaussian_vector(n, 21), device="cuda")
+    b = torch.tensor(inputs.gaussian_vector(n, 22), device="cuda")
+    ref = api.dot_noalloc(a, b)  # warm-up: the first call on the device looks up the scratch address
+    torch.cuda.synchronize()
+    dev_before = torch.cuda.current_device()
+    free_before, _ = torch.cuda.mem_get_info()
+    for _ in range(20):
+        assert api.dot_noalloc(a, b) == ref
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after == free_before
+    assert torch.cuda.current_device() == dev_before
 
 
 def test_dot_noalloc_rejects_oversize():

@@ -72,11 +72,37 @@ def bytes_per_apply(var, dtype_bytes, nqp, ndofs, dim=3):
     return nvals * nqp * dtype_bytes + vec
 
 
-# DRAM bytes (read + write) per launch from one ncu capture of the 32^3 Q2 workload (profiles/*_ncu.md);
-# a kernel that changed since its capture maps to None.
-NCU_TRAFFIC = {
-    ("NC", "double", "apply_kernel"): 19_644_416,   # profiles/apply_nc_f64_32cube_q2_ncu.md
-}
+# Algorithmic FP64 flops per dof of one 3D Q2 application, the per-unit figures of the scope table's
+# measurement row: sum factorisation 8 d^2 n^(d+1) per cell, about 250 flops per Gauss point of
+# quadrature work for the caching variants, and for NC in addition the gradient of the displacement
+# (4 d^2 n^(d+1) per cell) and about 150 flops per Gauss point of kinematics.
+SCOPE_FLOPS_PER_DOF = {"T4": 530.0, "NC": 830.0}
+
+
+def kernel_source_sha():
+    """sha256 of the tangent-action kernel source; a capture taken on other source no longer applies."""
+    import hashlib
+    with open(os.path.join(ROOT, "paper_1904_13131_gb300", "csrc", "cell_kernels.cuh"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def captured_traffic(kernel):
+    """DRAM bytes (read + write) per launch of `kernel` from a committed ncu summary under profiles/ that
+    names it on a 'traffic:' line together with the sha256 of the kernel source it was captured on:
+        traffic: <kernel> <bytes per launch> <source sha256>
+    None when no summary has it for the current source."""
+    import glob
+    sha = kernel_source_sha()
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*"))):
+        try:
+            lines = open(path).read().splitlines()
+        except (OSError, UnicodeDecodeError):
+            continue
+        for line in lines:
+            parts = line.strip().strip("`").split()
+            if len(parts) == 4 and parts[0] == "traffic:" and parts[1] == kernel and parts[3] == sha:
+                return int(parts[2])
+    return None
 
 
 def peaks():
@@ -527,39 +553,208 @@ def batch_bench(torch, api, inputs, dev, stream, n_apply=64, n_solve=16, reps=20
     return out
 
 
-def cpu_oracle_rate(seconds=10.0):
-    """Oracle element-by-element application on the same problem at 16^3 Q2 (1/8 of the cells)."""
+# ---- the CPU oracle on the host cores (cpu_baseline and the reference arm) -----------------------------
+# The oracle's element-by-element action (oracle.fem.Problem.apply, Eq. mf_vmult) as it stands, spread over
+# a pool of host processes: each process runs the oracle's own per-chunk loop body (Problem.apply_cells)
+# over a contiguous range of cells into its own slot of a shared result array, and the parent adds the
+# slots and applies the Dirichlet rows exactly as Problem.apply does. The pool is started with "spawn"
+# (never forked from a process that has touched the GPU).
+_W = {}
+
+
+def _oracle_worker_init(m, x_name, y_name, slots):
+    from multiprocessing import shared_memory
+
     from oracle.fem import Problem
     from paper_1904_13131_gb300 import inputs
-    m = 16
+    pr = inputs.problem(DIM, K, m, n_levels=1, top=0)
+    P = Problem(DIM, K, m, pr["ids"][0], pr["mu"], pr["lam"], pr["masks"])
+    _W["P"], _W["u"] = P, inputs.smooth_field(DIM, K, m, seed=0)
+    _W["shx"] = shared_memory.SharedMemory(name=x_name)
+    _W["shy"] = shared_memory.SharedMemory(name=y_name)
+    _W["x"] = np.ndarray((P.n_dofs,), dtype=np.float64, buffer=_W["shx"].buf)
+    _W["y"] = np.ndarray((slots, P.n_dofs), dtype=np.float64, buffer=_W["shy"].buf)
+
+
+def _oracle_worker_apply(task):
+    slot, lo, hi = task
+    P, y = _W["P"], _W["y"][slot]
+    y[:] = 0.0
+    for c in range(lo, hi, P.chunk):
+        P.apply_cells(_W["u"], _W["x"], np.arange(c, min(c + P.chunk, hi)), y)
+    return hi - lo
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+class OraclePool:
+    """The oracle's tangent action on the m^3 Q2 inclusion cube (the apply workload's problem) over
+    `workers` spawned host processes."""
+
+    def __init__(self, m=M, workers=None):
+        import multiprocessing as mp
+        from multiprocessing import shared_memory
+
+        from oracle.fem import Problem
+        from paper_1904_13131_gb300 import inputs
+        self.workers = workers or host_cores()
+        pr = inputs.problem(DIM, K, m, n_levels=1, top=0)
+        self.P = Problem(DIM, K, m, pr["ids"][0], pr["mu"], pr["lam"], pr["masks"])
+        self.n, self.ncells = self.P.n_dofs, m**DIM
+        self.shx = shared_memory.SharedMemory(create=True, size=8 * self.n)
+        self.shy = shared_memory.SharedMemory(create=True, size=8 * self.n * self.workers)
+        self.x = np.ndarray((self.n,), dtype=np.float64, buffer=self.shx.buf)
+        self.y = np.ndarray((self.workers, self.n), dtype=np.float64, buffer=self.shy.buf)
+        self.pool = mp.get_context("spawn").Pool(self.workers, initializer=_oracle_worker_init,
+                                                 initargs=(m, self.shx.name, self.shy.name, self.workers))
+
+    def apply(self, x, n_cells=None):
+        """y = A(u) x over the first n_cells cells (default all), Dirichlet rows as Problem.apply."""
+        nc = self.ncells if n_cells is None else n_cells
+        cons = self.P.constrained
+        self.x[:] = np.where(cons, 0.0, x)
+        bounds = np.linspace(0, nc, self.workers + 1).astype(int)
+        self.pool.map(_oracle_worker_apply, [(i, int(bounds[i]), int(bounds[i + 1])) for i in range(self.workers)])
+        y = self.y.sum(axis=0)
+        if nc == self.ncells:
+            y[cons] = np.asarray(x)[cons]
+        return y
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
+        for sh in (self.shx, self.shy):
+            sh.close()
+            sh.unlink()
+
+
+def cpu_matrix_based(m=12):
+    """The paper's matrix-based comparator (Sec. 4) with the oracle on one host core: assembly of the
+    sparse tangent (Problem.tangent_raw) and its CSR SpMV (scipy), on an m^3 Q2 sample of the problem."""
+    from oracle.fem import Problem
+    from paper_1904_13131_gb300 import inputs
     pr = inputs.problem(DIM, K, m, n_levels=1, top=0)
     P = Problem(DIM, K, m, pr["ids"][0], pr["mu"], pr["lam"], pr["masks"])
     u = inputs.smooth_field(DIM, K, m, seed=0)
     x = inputs.gaussian_vector(P.n_dofs, seed=1)
-    n_done, t0 = 0, time.perf_counter()
-    while True:
-        P.apply(u, x)
-        n_done += 1
+    t0 = time.perf_counter()
+    A = P.tangent_raw(u)
+    t_asm = time.perf_counter() - t0
+    ts = []
+    for _ in range(10):
+        t0 = time.perf_counter()
+        A @ x
+        ts.append(time.perf_counter() - t0)
+    t_spmv = float(np.median(ts))
+    return {"sample": f"{m}^3 Q2 ({P.n_dofs} dofs, {A.nnz} nonzeros), one core",
+            "assembly_s": t_asm, "assembly_s_per_cell": t_asm / m**DIM,
+            "csr_spmv_ms": t_spmv * 1e3, "csr_spmv_gdofs": P.n_dofs / t_spmv / 1e9,
+            "csr_bytes_per_spmv": int(A.nnz * 12 + (A.shape[0] + 1) * 4 + 2 * A.shape[0] * 8)}
+
+
+def cpu_newton_config1():
+    """The oracle's Newton (sparse direct solves) on the 2D 16^2 Q2 inclusion problem, 5 load steps."""
+    from oracle.fem import Problem
+    from oracle.newton import newton_solve
+    from paper_1904_13131_gb300 import inputs
+    dim, k, m = 2, 2, 16
+    pr = inputs.problem(dim, k, m, top=inputs.normal_top_mask(dim))
+    P = Problem(dim, k, m, pr["ids"][0], pr["mu"], pr["lam"], pr["masks"])
+    X = inputs.node_coords(dim, k, m)
+    ubc = np.zeros((P.n_nodes, dim))
+    ubc[np.isclose(X[:, 1], 1.0), 1] = -0.1
+    t0 = time.perf_counter()
+    _, rep = newton_solve(P, ubc.reshape(-1), load_steps=5)
+    return {"problem": "2D 16^2 Q2 inclusion, top -0.1 in 5 load steps (2,178 dofs), one core",
+            "seconds": time.perf_counter() - t0, "newton_iterations": rep["iterations"]}
+
+
+def cpu_baseline(x):
+    """cpu_baseline of the GPU arm: the oracle's action on the full apply workload over all host cores
+    (one warm-up application, then one step = the three variants' applications, which the oracle computes
+    alike), plus the matrix-based comparator and a Newton solve of the oracle on one core each."""
+    pool = OraclePool(M)
+    try:
+        pool.apply(x)
+        t0 = time.perf_counter()
+        for _ in VARIANTS:
+            pool.apply(x)
         el = time.perf_counter() - t0
-        if el >= seconds:
-            break
-    # dofs per second on the sample, scaled to the full workload by cells (same cost per cell)
-    cells_ratio = (M / m) ** DIM
-    full_dofs = inputs.n_dofs(DIM, K, M)
-    t_full = el / n_done * cells_ratio
-    return full_dofs / t_full / 1e9, n_done, el, f"oracle apply on the 16^3 Q2 sample ({P.n_dofs} dofs, " \
-        f"{m**DIM} cells = 1/{int(cells_ratio)} of the workload), {n_done} applications in {el:.1f} s, scaled by cells"
+    finally:
+        pool.close()
+    rate = 3 * inputs_ndofs() / el / 1e9
+    return {"value": rate, "unit": UNIT, "cores": pool.workers, "kind": "oracle",
+            "sample": f"the full workload (32^3 Q2, {inputs_ndofs()} dofs), one step = {len(VARIANTS)} "
+                      f"element-by-element applications of the oracle in {el:.1f} s, after one warm-up "
+                      f"application; {pool.workers} spawned host processes",
+            "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+            "matrix_based": cpu_matrix_based(), "newton": cpu_newton_config1()}
 
 
-def run_reference(args, rank, world):
+def run_reference(args, rank, world, budget_s=150.0):
+    """The reference arm: the oracle as it stands, on the host cores, stepping through the same workload
+    (one step = the three applications). If full steps would not fit the time budget, every step applies
+    the oracle to the same leading fraction of the cells and counts only those cells' dofs."""
     if rank != 0:
         return
-    rate, n, el, sample = cpu_oracle_rate(seconds=max(5.0, 2.0 * (args.steps + args.warmup)))
+    from paper_1904_13131_gb300 import inputs
+    x = inputs.gaussian_vector(inputs_ndofs(), seed=1)
+    pool = OraclePool(M)
+    try:
+        t0 = time.perf_counter()
+        for _ in VARIANTS:
+            pool.apply(x)
+        t_full = time.perf_counter() - t0
+        n_cells = pool.ncells
+        if (args.steps + args.warmup - 1) * t_full > budget_s:
+            frac = max(budget_s / ((args.steps + args.warmup - 1) * t_full), 1.0 / 64)
+            n_cells = max(1, int(pool.ncells * frac))
+        for _ in range(args.warmup - 1):
+            for _ in VARIANTS:
+                pool.apply(x, n_cells)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for _ in VARIANTS:
+                pool.apply(x, n_cells)
+        el = time.perf_counter() - t0
+    finally:
+        pool.close()
+    units = len(VARIANTS) * inputs_ndofs() * n_cells / pool.ncells * args.steps
+    rate = units / el / 1e9
+    sample = (f"{args.steps} steps of {len(VARIANTS)} element-by-element applications of the oracle over "
+              f"{n_cells} of the {pool.ncells} cells of the 32^3 Q2 workload ({n_cells / pool.ncells:.3f} of it; "
+              f"dofs counted in proportion) in {el:.1f} s after {args.warmup} warm-up steps; "
+              f"{pool.workers} spawned host processes")
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 3 * inputs_ndofs() / (rate * 1e9) * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)", "cells_per_step": n_cells},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": pool.workers, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model()},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -575,7 +770,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-solve", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--only", default=None, help="profile mode: VARIANT:f64|f32, a few applications of one kernel")
     ap.add_argument("--form", type=int, default=-1, help="profile mode: kernel form (0 point, 1 line, -1 tuned)")
     ap.add_argument("--m", type=int, default=M, help="profile mode: cells per direction of the Q2 cube")
@@ -731,15 +926,26 @@ def main():
         ctxs[v].set_geometry(None)
         ctxs[v].set_displacement(u, v, level_dtype=1)
     del Xc
-    # dominant kernel of the step: the slowest variant's FP64 apply (FP64-pipe bound)
+    # dominant kernel of the step: the slowest variant's FP64 apply (FP64-pipe bound). achieved = the scope
+    # table's algorithmic flops per dof x dofs per launch / event time; the count of the kernel's own
+    # arithmetic (flops_per_qp, FMA = 2) is reported beside it
     dom = max(per_var_ms, key=per_var_ms.get)
-    ach = flops_per_qp(dom) * nqp / (per_var_ms[dom] * 1e-3) / 1e12
+    t_dom = per_var_ms[dom] * 1e-3
     kname = "apply_line_kernel" if ctxs[dom].kernel_form(-1, 0) == 1 else "apply_kernel"
-    roofline = {"bound": "alu", "kernel": f"{kname}<3,3,{dom},double>", "achieved": ach, "peak": fp64_peak,
-                "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": NCU_TRAFFIC.get((dom, "double", kname)),
+    kfull = f"{kname}<3,3,{dom},double>"
+    scope = SCOPE_FLOPS_PER_DOF.get(dom)
+    alg = scope * n if scope else flops_per_qp(dom) * nqp
+    ach = alg / t_dom / 1e12
+    roofline = {"bound": "alu", "kernel": kfull, "achieved": ach, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": captured_traffic(kfull),
                 "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                 "peak_source": "FP64 pipe: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (derived, nominal 1.25 TFLOP/s)",
-                "algorithmic_flops_per_launch": flops_per_qp(dom) * nqp}
+                "algorithmic_flops_per_launch": alg,
+                "flops_per_dof": scope if scope else flops_per_qp(dom) * nqp / n,
+                "kernel_count_flops_per_launch": flops_per_qp(dom) * nqp,
+                "kernel_count_frac": flops_per_qp(dom) * nqp / t_dom / 1e12 / fp64_peak,
+                "algorithmic_bytes_per_launch": bytes_per_apply(dom, 8, nqp, n),
+                "kernel_source_sha256": kernel_source_sha()}
 
     # ---- end to end through the public API: pinned host x -> device, 3 applies, results -> host ----
     # each result goes to the host on a copy stream while the next variant computes
@@ -793,9 +999,8 @@ def main():
             batch = {"error": str(e)}
 
     cpu = None
-    if rank == 0 and world == 1:
-        rate, nd, el, sample = cpu_oracle_rate(args.cpu_seconds)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(x.cpu().numpy())
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

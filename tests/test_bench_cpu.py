@@ -78,3 +78,26 @@ def test_reference_arm_prints_on_rank_0_only():
                 "e2e"):
         assert key in d
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_oracle_pool_reproduces_the_oracle_action():
+    """The host-parallel timing harness of the oracle (bench.OraclePool) adds up exactly what the oracle's
+    own Problem.apply computes, on the same problem, over the whole mesh and over a leading sample of cells."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+
+    import bench
+    from paper_1904_13131_gb300 import inputs
+    m = 4
+    pool = bench.OraclePool(m, workers=3)
+    try:
+        x = inputs.gaussian_vector(pool.n, seed=1)
+        u = inputs.smooth_field(bench.DIM, bench.K, m, seed=0)
+        ref = pool.P.apply(u, x)
+        np.testing.assert_allclose(pool.apply(x), ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+        part = np.zeros(pool.n)
+        xin = np.where(pool.P.constrained, 0.0, x)
+        pool.P.apply_cells(u, xin, np.arange(40), part)
+        np.testing.assert_allclose(pool.apply(x, 40), part, rtol=0, atol=1e-13 * np.abs(part).max())
+    finally:
+        pool.close()

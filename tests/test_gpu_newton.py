@@ -118,11 +118,14 @@ def test_checkpoint_and_resume_continue_the_load_path(torch):
 
 
 def uniaxial_setup(dim, k, m, L):
-    """Homogeneous body (mu = 1, nu = 0.3), bottom clamped, side faces held in their normal component, top free."""
+    """Homogeneous body (mu = 1, nu = 0.3), bottom clamped, side faces held in their normal component, the top
+    face held laterally (free along its normal): uniaxial strain, with a positive definite tangent along the
+    whole compressed path, as CG and the Chebyshev coarse solve need."""
     masks = [0] * (2 * dim)
     for a in range(dim - 1):
         masks[2 * a] = masks[2 * a + 1] = 1 << a
     masks[2 * (dim - 1)] = (1 << dim) - 1
+    masks[2 * (dim - 1) + 1] = (1 << (dim - 1)) - 1
     mu, lam = inputs.material_table(1.0)
     ms = inputs.level_sizes(m, L)
     pr = {"dim": dim, "k": k, "m": m, "levels_m": ms, "ids": [np.zeros(ml**dim, np.uint8) for ml in ms],

@@ -42,12 +42,15 @@ def test_config1_newton_converges_quadratically():
 
 
 def uniaxial_masks(dim):
-    """Bottom clamped, every side face constrained in its own normal component, top free: a homogeneous
-    body under a normal traction on the top then deforms in uniaxial strain, F = diag(1, .., 1, s)."""
+    """Bottom clamped, every side face constrained in its own normal component, the top face held laterally
+    and free along its normal: a homogeneous body under a normal traction on the top then deforms in
+    uniaxial strain, F = diag(1, .., 1, s). (With the top free laterally as well, the compressed block's
+    tangent turns indefinite -- a surface instability -- before s = 0.5, which every halved step reaches.)"""
     masks = [0] * (2 * dim)
     for a in range(dim - 1):
         masks[2 * a] = masks[2 * a + 1] = 1 << a
     masks[2 * (dim - 1)] = (1 << dim) - 1
+    masks[2 * (dim - 1) + 1] = (1 << (dim - 1)) - 1
     return masks
 
 

@@ -404,13 +404,15 @@ def config_study(torch, api, inputs, dev):
     return out
 
 
-def serve_bench(api, inputs, dev, n_req, seed=0, max_active=8, budget_gb=160):
+def serve_bench(api, inputs, dev, n_req, seed=0, max_active=8, budget_gb=160, seq_every=1, poisson=True):
     """Serving (continuous batching): a seeded stream of uneven solve requests (2D 32^2-256^2 and 3D 8^3-48^3,
     Q1-Q3, stiffness ratio 2-100, radius 0.1-0.35, compression 2-15 %, 5 load steps). Baseline: the same
-    requests solved one at a time with plain FP64 (FP64 V-cycle, Chebyshev coarse solve). Served: up to
-    `max_active` resident solves, mixed-precision V-cycle, exact coarse solve with the double-float inverse,
-    double-float finest-level action and diagonals for degrees 1-2; closed loop (all at t=0) for peak
-    solves/s, and Poisson arrivals at twice the baseline rate for p50/p99 latency."""
+    requests solved one at a time with plain FP64 (FP64 V-cycle, Chebyshev coarse solve); with seq_every > 1
+    only every seq_every-th request is solved that way and the baseline rate is that subset's (stated in the
+    result). Served: up to `max_active` resident solves, mixed-precision V-cycle, exact coarse solve with the
+    double-float inverse, double-float finest-level action and diagonals for degrees 1-2; closed loop (all at
+    t=0) for peak solves/s, once with independent per-request solves and once with the outer CG solves fused
+    across requests (hy_server_set_batching); Poisson arrivals at twice the baseline rate for p50/p99."""
     reqs = inputs.serving_requests(n_req, seed)
 
     def problem(q):
@@ -428,12 +430,12 @@ def serve_bench(api, inputs, dev, n_req, seed=0, max_active=8, budget_gb=160):
         return api.SolverParams(4, 1, 0.6, 1.2, 30, 0, 1e-3, 2 if (ff and coarse) else coarse, -1, fine,
                                api.VARIANTS["T2"] if ff else -1)
 
-    def run(max_act, ldt, coarse, arrivals=None, ff=False):
+    def run(subset, max_act, ldt, coarse, arrivals=None, ff=False, batching=False):
         out = {}
-        with api.Server(dev.index, budget_bytes=budget_gb << 30, max_active=max_act) as sv:
+        with api.Server(dev.index, budget_bytes=budget_gb << 30, max_active=max_act, batching=batching) as sv:
             t0 = time.perf_counter()
             tickets = []
-            for q in reqs:
+            for q in subset:
                 if arrivals is not None:
                     delay = arrivals[q["id"]] - (time.perf_counter() - t0)
                     if delay > 0:
@@ -446,29 +448,48 @@ def serve_bench(api, inputs, dev, n_req, seed=0, max_active=8, budget_gb=160):
             stats = sv.stats()
         lat = np.array([r["latency_ms"] for r in res])
         failed = sum(r["state"] != 2 for r in res)
-        out = {"solves_per_s": (len(reqs) - failed) / makespan, "p50_ms": float(np.percentile(lat, 50)),
-               "p99_ms": float(np.percentile(lat, 99)), "makespan_s": makespan, "failed": failed,
+        out = {"requests": len(subset), "solves_per_s": (len(subset) - failed) / makespan,
+               "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+               "makespan_s": makespan, "failed": failed,
                "failed_requests": [dict(id=q["id"], status=r["status"], dim=q["dim"], k=q["k"], m=q["m"],
                                         ratio=q["ratio"], compression=q["compression"])
-                                   for q, r in zip(reqs, res) if r["state"] != 2],
-               "bytes_peak_gb": stats["bytes_peak"] / 1e9, "max_active": max_act}
-        return out, [r["u"] for r in res]
+                                   for q, r in zip(subset, res) if r["state"] != 2],
+               "bytes_peak_gb": stats["bytes_peak"] / 1e9, "max_active": max_act, "retried": stats["retried"]}
+        if batching:
+            out.update(batched_solves=stats["batched_solves"], batch_runs=stats["batch_runs"],
+                       mean_solves_per_batch=stats["batched_solves"] / max(1, stats["batch_runs"]))
+        return out, {q["id"]: r["u"] for q, r in zip(subset, res)}
 
-    seq, u_seq = run(1, 0, 0)
+    sub = reqs[::seq_every]
+    seq, u_seq = run(sub, 1, 0, 0)
+    if seq_every > 1:
+        seq["subset"] = f"every {seq_every}th request ({len(sub)} of {n_req}); the baseline rate is this subset's"
     rate = 2.0 * seq["solves_per_s"]
-    rng = np.random.default_rng(seed + 1)
-    arr, t = {}, 0.0
-    for q in reqs:
-        t += float(rng.exponential(1.0 / rate))
-        arr[q["id"]] = t
-    peak, u_peak = run(max_active, 1, 1, ff=True)
-    poisson, u_srv = run(max_active, 1, 1, arrivals=arr, ff=True)
-    err = max(float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(u_srv, u_seq) if a is not None and b is not None)
-    return {"requests": n_req, "seed": seed, "sequential_fp64": seq, "served_closed_loop": peak,
-            "served_poisson": dict(poisson, arrival_rate_per_s=rate),
-            "speedup_solves_per_s": peak["solves_per_s"] / seq["solves_per_s"],
-            "max_rel_l2_served_vs_fp64": err,
-            "mix": [(q["dim"], q["k"], q["m"]) for q in reqs]}
+    peak, u_peak = run(reqs, max_active, 1, 1, ff=True)
+    fused, u_fused = run(reqs, max_active, 1, 1, ff=True, batching=True)
+    out = {"requests": n_req, "seed": seed, "sequential_fp64": seq, "served_closed_loop": peak,
+           "served_closed_loop_batched": fused,
+           "speedup_solves_per_s": peak["solves_per_s"] / seq["solves_per_s"],
+           "speedup_solves_per_s_batched": fused["solves_per_s"] / seq["solves_per_s"],
+           "mix": [(q["dim"], q["k"], q["m"]) for q in reqs]}
+
+    def max_err(us):
+        errs = [float(np.linalg.norm(us[i] - u_seq[i]) / np.linalg.norm(u_seq[i])) for i in u_seq
+                if us.get(i) is not None and u_seq[i] is not None]
+        return max(errs) if errs else None
+
+    out["max_rel_l2_served_vs_fp64"] = max_err(u_peak)
+    out["max_rel_l2_batched_vs_fp64"] = max_err(u_fused)
+    if poisson:
+        rng = np.random.default_rng(seed + 1)
+        arr, t = {}, 0.0
+        for q in reqs:
+            t += float(rng.exponential(1.0 / rate))
+            arr[q["id"]] = t
+        best_batched = fused["solves_per_s"] > peak["solves_per_s"]
+        poi, _ = run(reqs, max_active, 1, 1, arrivals=arr, ff=True, batching=best_batched)
+        out["served_poisson"] = dict(poi, arrival_rate_per_s=rate, batching=best_batched)
+    return out
 
 
 def batch_bench(torch, api, inputs, dev, stream, n_apply=64, n_solve=16, reps=20):
@@ -777,6 +798,9 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--serve-requests", type=int, default=12, help="requests in the serving section (0 = skip)")
     ap.add_argument("--serve-only", action="store_true")
+    ap.add_argument("--serve-seq-every", type=int, default=1,
+                    help="sequential FP64 baseline on every n-th request only (long streams)")
+    ap.add_argument("--no-serve-poisson", dest="serve_poisson", action="store_false")
     ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the work-list batch section")
     ap.add_argument("--batch-only", action="store_true")
     ap.add_argument("--solve-only", action="store_true")
@@ -854,7 +878,8 @@ def main():
         print(json.dumps({"batch": batch_bench(torch, api, inputs, dev, stream)}), flush=True)
         return
     if args.serve_only:
-        print(json.dumps({"serve": serve_bench(api, inputs, dev, args.serve_requests)}), flush=True)
+        print(json.dumps({"serve": serve_bench(api, inputs, dev, args.serve_requests, seq_every=args.serve_seq_every,
+                                               poisson=args.serve_poisson)}), flush=True)
         return
     pr, u, x, ctxs = setup_contexts(torch, api, inputs, dev)
     n = inputs.n_dofs(DIM, K, M)

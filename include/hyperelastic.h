@@ -372,11 +372,25 @@ typedef struct {
                        resolve the inclusion, Sec. 6) reruns from its start state with one level fewer, while
                        two levels remain and the budget holds the larger coarse level (Chebyshev coarse
                        solve when it exceeds the dense-inverse limit) */
+  int64_t batched_solves; /* batched serving: outer linear solves that went through the batcher */
+  int64_t batch_runs;     /* batched serving: work-list batches run (batched_solves / batch_runs = the mean
+                             number of solves fused per batch) */
 } hy_server_stats;
 
 /* Start a server on `device` with `max_active` workers (1..64), admitting requests while their summed
  * footprints stay within hbm_budget_bytes. HY_ERR_ARG for a bad device, budget or worker count. */
 hy_status hy_server_create(hy_server **out, int device, int64_t hbm_budget_bytes, int max_active);
+/* Batched serving (call before the first submit; HY_ERR_STATE afterwards or when already enabled). Not a
+ * step of the paper: it fuses the paper's matrix-free operator action (Eq. mf_vmult) and its GMG-
+ * preconditioned CG (Secs. 6-7) across requests. Each worker still linearises its own request on its own
+ * stream, but its outer CG solves go to a batcher, which waits until every running Newton solve has a
+ * solve waiting or window_ms (0..1000) has passed since the oldest arrived, groups the waiting solves by
+ * dimension, degree, cache variants, finest-level precision, CG tolerance and cap, and runs every group as
+ * one work-list batch (hy_batch_pcg: one graph replay per PCG iteration with ONE kernel launch for the
+ * finest-level tangent actions of all members and their V-cycles as concurrent branches). Groups of
+ * different degree run side by side. Results are those of the requests' own PCG (the same arithmetic per
+ * problem). HY_ERR_ARG for a bad window. */
+hy_status hy_server_set_batching(hy_server *s, int enable, double window_ms);
 /* Running requests finish; queued ones are dropped. */
 void hy_server_destroy(hy_server *s);
 /* Copies the request and returns at once. HY_ERR_OOM if its footprint exceeds the whole budget. */

@@ -30,7 +30,7 @@ EXPORTED = ("hy_create", "hy_destroy", "hy_status_str", "hy_last_error", "hy_mes
             "hy_server_release", "hy_server_stats_get", "hy_kernel_form", "hy_batch_create", "hy_batch_destroy",
             "hy_batch_last_error", "hy_batch_apply", "hy_batch_pcg", "hy_batch_kernel_launches",
             "hy_batch_kernel_form", "hy_set_material_law", "hy_face_load", "hy_set_geometry",
-            "hy_check_bounded_wait")
+            "hy_check_bounded_wait", "hy_server_set_batching")
 
 
 class HyError(RuntimeError):
@@ -78,7 +78,7 @@ class Request(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     """ctypes mirror of hy_server_stats (include/hyperelastic.h)."""
     _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "active", "queued", "bytes_in_use",
-                                              "bytes_peak", "budget", "retried")]
+                                              "bytes_peak", "budget", "retried", "batched_solves", "batch_runs")]
 
 
 _lib = None
@@ -145,6 +145,7 @@ def load_library(path: str = LIB_PATH):
         "hy_server_wait": [vp, ctypes.c_uint64, dbl],
         "hy_server_release": [vp, ctypes.c_uint64],
         "hy_server_stats_get": [vp, ctypes.POINTER(ServerStats)],
+        "hy_server_set_batching": [vp, i32, dbl],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -560,7 +561,8 @@ class Batch:
 class Server:
     """hy_server: continuous batching of independent Newton solves on one GPU (see include/hyperelastic.h)."""
 
-    def __init__(self, device=0, budget_bytes=64 << 30, max_active=4):
+    def __init__(self, device=0, budget_bytes=64 << 30, max_active=4, batching=False, window_ms=2.0):
+        """hy_server_create, then hy_server_set_batching when batching (fused outer CG solves)."""
         self.lib = load_library()
         h = ctypes.c_void_p()
         st = self.lib.hy_server_create(ctypes.byref(h), device, int(budget_bytes), max_active)
@@ -568,6 +570,11 @@ class Server:
             raise HyError(st, "hy_server_create")
         self.h = h
         self._steps = {}
+        if batching:
+            st = self.lib.hy_server_set_batching(self.h, 1, float(window_ms))
+            if st != 0:
+                self.close()
+                raise HyError(st, "hy_server_set_batching")
 
     def close(self):
         """hy_server_destroy: running requests finish, queued ones are dropped; idempotent."""

@@ -20,6 +20,7 @@
 #include "../../include/hyperelastic.h"
 #include "cell_kernels.cuh"
 #include "launch.cuh"
+#include "serve_internal.h"
 
 using namespace hy;
 
@@ -245,6 +246,9 @@ struct hy_ctx {
   double* h_pcg_scal = nullptr;
   long long vc_nodes = 0;
   std::vector<std::pair<void*, size_t>> allocs;
+  // replacement of the outer PCG inside hy_newton_solve (the solve server's batched solves), or null
+  hy_linear_solve_hook solve_hook = nullptr;
+  void* solve_user = nullptr;
 };
 
 namespace {
@@ -2395,7 +2399,8 @@ hy_status hy_newton_solve(hy_ctx* ctx, const hy_newton_params* p, double* u, hy_
       int cg_its = 0;
       HY_CK(cudaStreamSynchronize(ctx->stream));
       const clk::time_point t_solve = clk::now();
-      st = pcg(ctx, rhs, du, p->cg_rtol, p->cg_max_iter, &cg_its);
+      st = ctx->solve_hook ? ctx->solve_hook(ctx->solve_user, ctx, rhs, du, p->cg_rtol, p->cg_max_iter, &cg_its)
+                           : pcg(ctx, rhs, du, p->cg_rtol, p->cg_max_iter, &cg_its);
       HY_CK(cudaStreamSynchronize(ctx->stream));
       if (rl.n_solves < 256) {
         rl.solve_ms[rl.n_solves] = ms_since(t_solve);
@@ -2620,3 +2625,76 @@ hy_status hy_batch_kernel_form(const hy_batch* b, hy_dtype dtype, int* form) {
 }
 
 }  // extern "C"
+
+// ---- internal interface of the solve server (serve_internal.h) ----------------------------------
+void hy_ctx_set_solve_hook(hy_ctx* ctx, hy_linear_solve_hook hook, void* user) {
+  if (!ctx) return;
+  ctx->solve_hook = hook;
+  ctx->solve_user = user;
+}
+
+long long hy_ctx_batch_key(const hy_ctx* c) {
+  if (!c || c->nlev == 0) return -1;
+  const Level& L = c->lev[c->nlev - 1];
+  const bool ff_action = c->sp.fine_dtype == HY_FF && L.hasff;
+  long long key = c->dim;
+  key = key * 8 + c->n;
+  for (int d = 0; d < 3; ++d) key = key * 8 + (L.var[d] + 1);
+  return key * 2 + (ff_action ? 1 : 0);
+}
+
+hy_status hy_batch_create_empty(hy_batch** out, int device, int capacity) {
+  if (!out || capacity < 1 || capacity > HY_BATCH_MAX) return HY_ERR_ARG;
+  *out = nullptr;
+  if (cudaSetDevice(device) != cudaSuccess) return HY_ERR_CUDA;
+  hy_batch* b = new (std::nothrow) hy_batch();
+  if (!b) return HY_ERR_OOM;
+  b->device = device;
+  b->branch.assign(capacity, nullptr);
+  b->ev.assign(capacity, nullptr);
+  bool ok = cudaStreamCreateWithFlags(&b->s0, cudaStreamNonBlocking) == cudaSuccess;
+  for (int i = 0; i < capacity && ok; ++i)
+    ok = cudaStreamCreateWithFlags(&b->branch[i], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->ev[i], cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+       cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming) == cudaSuccess &&
+       cudaEventCreateWithFlags(&b->ev_upload, cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->d_list, BATCH_ARG_BYTES * capacity) == cudaSuccess &&
+       cudaMalloc((void**)&b->d_start, sizeof(int) * (capacity + 1)) == cudaSuccess &&
+       cudaMalloc((void**)&b->d_scal, sizeof(double) * PCG_SCALARS * capacity) == cudaSuccess &&
+       cudaMallocHost(&b->h_list, BATCH_ARG_BYTES * capacity) == cudaSuccess &&
+       cudaMallocHost((void**)&b->h_start, sizeof(int) * (capacity + 1)) == cudaSuccess &&
+       cudaMallocHost((void**)&b->h_scal_in, sizeof(double) * PCG_SCALARS * capacity) == cudaSuccess &&
+       cudaMallocHost((void**)&b->h_scal_out, sizeof(double) * PCG_SCALARS * capacity) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    batch_free(b);
+    return HY_ERR_OOM;
+  }
+  *out = b;
+  return HY_OK;
+}
+
+// New members: the uploaded argument list no longer describes them, and the list launch takes the kernel
+// form that the autotuner chose for the largest member's finest level (it dominates the launch).
+hy_status hy_batch_bind(hy_batch* b, hy_ctx* const* ctxs, int count) {
+  if (!b || !ctxs || count < 1 || count > (int)b->branch.size()) return HY_ERR_ARG;
+  for (int i = 0; i < count; ++i) {
+    if (!ctxs[i] || ctxs[i]->nlev == 0) return HY_ERR_STATE;
+    if (ctxs[i]->device != b->device || ctxs[i]->dim != ctxs[0]->dim || ctxs[i]->n != ctxs[0]->n)
+      return HY_ERR_ARG;
+  }
+  HB_CK(cudaSetDevice(b->device));
+  HB_CK(cudaEventSynchronize(b->ev_upload));  // the pinned staging of the previous members is free
+  b->ctx.assign(ctxs, ctxs + count);
+  b->dim = ctxs[0]->dim;
+  b->n = ctxs[0]->n;
+  b->up_dt = -1;
+  b->up_x.clear();
+  b->up_y.clear();
+  const hy_ctx* big = ctxs[0];
+  for (int i = 1; i < count; ++i)
+    if (ctxs[i]->lev[ctxs[i]->nlev - 1].ndofs > big->lev[big->nlev - 1].ndofs) big = ctxs[i];
+  for (int d = 0; d < 3; ++d) b->form[d] = big->lev[big->nlev - 1].form[d];
+  return HY_OK;
+}

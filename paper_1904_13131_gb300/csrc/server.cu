@@ -13,6 +13,17 @@
 // A solve that fails only because its coarsest level's tangent is not positive definite (a coarse mesh
 // that does not resolve the inclusion, under a large load) is run again from its start state with that
 // level dropped, as long as two levels remain and the budget has room for the larger coarse level.
+//
+// Batched solves (hy_server_set_batching): the linear solves of the running Newton iterations are fused
+// across requests. Each worker still linearises its own request (state, diagonals, eigenvalue estimates,
+// V-cycle graph) on its own stream, but hands its outer preconditioned CG to a batcher thread and waits.
+// The batcher collects the solves that are waiting -- until every running Newton solve has one waiting, or
+// for at most the batching window after the oldest arrived -- groups them by (dimension, degree, cache
+// variants, finest-level precision, CG tolerance and cap) and advances each group as one work-list batch:
+// per PCG iteration one CUDA-graph replay, in which ONE kernel launch applies the finest-level tangents of
+// all members and the members' V-cycles run as concurrent branches (hy_batch_pcg). Groups of different
+// degree cannot share a launch (the kernel's shared-memory layout, threads per block and registers are
+// those of its degree) and run side by side on their own batches instead.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -23,10 +34,12 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <unordered_map>
 #include <vector>
 
 #include "../../include/hyperelastic.h"
+#include "serve_internal.h"
 
 namespace {
 
@@ -52,6 +65,19 @@ struct Req {
   Clock::time_point t_submit, t_start, t_end;
 };
 
+// One outer linear solve handed to the batcher by a worker's Newton iteration.
+struct SolveJob {
+  hy_ctx* ctx = nullptr;
+  const double* rhs = nullptr;
+  double* x = nullptr;
+  double rtol = 0.0;
+  int max_iter = 0;
+  int iterations = 0;
+  hy_status status = HY_OK;
+  bool done = false;
+  Clock::time_point t_queued;
+};
+
 }  // namespace
 
 struct hy_server {
@@ -68,6 +94,16 @@ struct hy_server {
   bool stop = false;
   uint64_t next_id = 1;
   std::vector<std::thread> workers;
+  // batched solves
+  bool batching = false;
+  double window_ms = 2.0;
+  int in_newton = 0;                 // workers inside a Newton solve (potential batch members)
+  std::deque<SolveJob*> jobs;        // waiting for the batcher
+  std::condition_variable cv_jobs, cv_jobs_done;
+  bool stop_batcher = false;
+  std::thread batcher;
+  std::vector<hy_batch*> batches;    // one per group that can run at once, created on first use
+  int64_t batched_solves = 0, batch_runs = 0;
 };
 
 namespace {
@@ -81,7 +117,26 @@ long long level_cells(const Req& r, int l) {
 // One attempt of a request on the worker's stream with its `drop` coarsest levels left out: context,
 // hierarchy, materials, Newton solve, result to host. *coarse_indefinite tells whether it failed on a
 // coarsest-level tangent that is not positive definite.
-hy_status run_attempt(Req& r, int drop, int device, cudaStream_t st, bool* coarse_indefinite) {
+// The solve hook of a batching server: queue the solve for the batcher and wait for its result.
+hy_status batched_solve(void* user, hy_ctx* ctx, const double* rhs, double* x, double rtol, int max_iter,
+                        int* iterations) {
+  hy_server* sv = static_cast<hy_server*>(user);
+  SolveJob job;
+  job.ctx = ctx;
+  job.rhs = rhs;
+  job.x = x;
+  job.rtol = rtol;
+  job.max_iter = max_iter;
+  std::unique_lock<std::mutex> lock(sv->mu);
+  job.t_queued = Clock::now();
+  sv->jobs.push_back(&job);
+  sv->cv_jobs.notify_all();
+  sv->cv_jobs_done.wait(lock, [&] { return job.done; });
+  *iterations = job.iterations;
+  return job.status;
+}
+
+hy_status run_attempt(hy_server* sv, Req& r, int drop, int device, cudaStream_t st, bool* coarse_indefinite) {
   *coarse_indefinite = false;
   hy_ctx* ctx = nullptr;
   double* u = nullptr;
@@ -110,7 +165,20 @@ hy_status run_attempt(Req& r, int drop, int device, cudaStream_t st, bool* coars
                                                   st)) != cudaSuccess)
       s = HY_ERR_CUDA;
   }
+  const bool counted = s == HY_OK && sv->batching;
+  if (counted) {
+    hy_ctx_set_solve_hook(ctx, batched_solve, sv);
+    std::lock_guard<std::mutex> lock(sv->mu);
+    sv->in_newton++;
+  }
   if (s == HY_OK) s = hy_newton_solve(ctx, &r.np, u, &r.rep);
+  if (counted) {
+    {
+      std::lock_guard<std::mutex> lock(sv->mu);
+      sv->in_newton--;
+    }
+    sv->cv_jobs.notify_all();  // the batcher may now have every running solve waiting
+  }
   if (s == HY_OK) {
     r.u.resize((size_t)n);
     if (cudaMemcpyAsync(r.u.data(), u, sizeof(double) * n, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -143,7 +211,7 @@ int64_t attempt_bytes(const Req& r, int drop) {
 void run_request(hy_server* sv, Req& r, cudaStream_t st) {
   for (int drop = 0;; ++drop) {
     bool coarse_indefinite = false;
-    r.status = run_attempt(r, drop, sv->device, st, &coarse_indefinite);
+    r.status = run_attempt(sv, r, drop, sv->device, st, &coarse_indefinite);
     r.dropped = drop;
     if (!coarse_indefinite || r.nlev - drop <= 2) return;
     // retry with the coarsest level dropped if the budget has room for it
@@ -159,6 +227,80 @@ void run_request(hy_server* sv, Req& r, cudaStream_t st) {
       sv->retried++;
     }
     r.rep = hy_newton_report{};
+  }
+}
+
+// Advance one group of waiting solves (same batch key, tolerance and cap) as one work-list batch.
+void run_group(hy_server* sv, hy_batch* b, std::vector<SolveJob*>& g) {
+  const int cnt = (int)g.size();
+  std::vector<hy_ctx*> ctxs(cnt);
+  std::vector<const double*> rhs(cnt);
+  std::vector<double*> xs(cnt);
+  std::vector<int> its(cnt, 0);
+  std::vector<hy_status> sts(cnt, HY_OK);
+  for (int i = 0; i < cnt; ++i) {
+    ctxs[i] = g[i]->ctx;
+    rhs[i] = g[i]->rhs;
+    xs[i] = g[i]->x;
+  }
+  hy_status st = hy_batch_bind(b, ctxs.data(), cnt);
+  if (st == HY_OK) st = hy_batch_pcg(b, rhs.data(), xs.data(), g[0]->rtol, g[0]->max_iter, its.data(), sts.data());
+  for (int i = 0; i < cnt; ++i) {
+    g[i]->iterations = its[i];
+    g[i]->status = st != HY_OK ? st : sts[i];
+  }
+  (void)sv;
+}
+
+void batcher_loop(hy_server* sv) {
+  cudaSetDevice(sv->device);
+  std::unique_lock<std::mutex> lock(sv->mu);
+  for (;;) {
+    sv->cv_jobs.wait(lock, [&] { return sv->stop_batcher || !sv->jobs.empty(); });
+    if (sv->jobs.empty()) break;  // stop_batcher, nothing left
+    // gather: until every running Newton solve has a solve waiting, or the window after the oldest closes
+    const auto deadline = sv->jobs.front()->t_queued + std::chrono::duration_cast<Clock::duration>(
+                                                            std::chrono::duration<double, std::milli>(sv->window_ms));
+    sv->cv_jobs.wait_until(lock, deadline, [&] { return (int)sv->jobs.size() >= sv->in_newton; });
+    std::vector<SolveJob*> take(sv->jobs.begin(), sv->jobs.end());
+    sv->jobs.clear();
+    lock.unlock();
+    // groups of one batch key, tolerance and cap
+    std::vector<std::vector<SolveJob*>> groups;
+    std::vector<std::tuple<long long, double, int>> keys;
+    for (SolveJob* j : take) {
+      const auto key = std::make_tuple(hy_ctx_batch_key(j->ctx), j->rtol, j->max_iter);
+      size_t gi = 0;
+      while (gi < keys.size() && keys[gi] != key) ++gi;
+      if (gi == keys.size()) {
+        keys.push_back(key);
+        groups.emplace_back();
+      }
+      groups[gi].push_back(j);
+    }
+    while (sv->batches.size() < groups.size()) {
+      hy_batch* b = nullptr;
+      if (hy_batch_create_empty(&b, sv->device, sv->max_active) != HY_OK) break;
+      sv->batches.push_back(b);
+    }
+    if (sv->batches.size() < groups.size()) {
+      for (SolveJob* j : take) j->status = HY_ERR_OOM;
+    } else if (groups.size() == 1) {
+      run_group(sv, sv->batches[0], groups[0]);
+    } else {  // groups of different degree (or dimension, variant, precision) side by side
+      std::vector<std::thread> th;
+      for (size_t gi = 0; gi < groups.size(); ++gi)
+        th.emplace_back([sv, gi, &groups]() {
+          cudaSetDevice(sv->device);
+          run_group(sv, sv->batches[gi], groups[gi]);
+        });
+      for (auto& t : th) t.join();
+    }
+    lock.lock();
+    sv->batched_solves += (int64_t)take.size();
+    sv->batch_runs += (int64_t)groups.size();
+    for (SolveJob* j : take) j->done = true;
+    sv->cv_jobs_done.notify_all();
   }
 }
 
@@ -229,7 +371,29 @@ void hy_server_destroy(hy_server* sv) {
   sv->cv_work.notify_all();
   sv->cv_done.notify_all();
   for (auto& t : sv->workers) t.join();
+  if (sv->batcher.joinable()) {  // after the workers: their last solves may still need it
+    {
+      std::lock_guard<std::mutex> lock(sv->mu);
+      sv->stop_batcher = true;
+    }
+    sv->cv_jobs.notify_all();
+    sv->batcher.join();
+  }
+  cudaSetDevice(sv->device);
+  for (hy_batch* b : sv->batches) hy_batch_destroy(b);
   delete sv;
+}
+
+hy_status hy_server_set_batching(hy_server* sv, int enable, double window_ms) {
+  if (!sv || !(window_ms >= 0.0) || window_ms > 1000.0) return HY_ERR_ARG;
+  std::lock_guard<std::mutex> lock(sv->mu);
+  if (sv->submitted > 0 || sv->batching) return HY_ERR_STATE;
+  sv->window_ms = window_ms;
+  if (enable) {
+    sv->batching = true;
+    sv->batcher = std::thread(batcher_loop, sv);
+  }
+  return HY_OK;
 }
 
 hy_status hy_server_submit(hy_server* sv, const hy_request* q, uint64_t* ticket) {
@@ -328,6 +492,8 @@ hy_status hy_server_stats_get(hy_server* sv, hy_server_stats* st) {
   st->bytes_peak = sv->peak;
   st->budget = sv->budget;
   st->retried = sv->retried;
+  st->batched_solves = sv->batched_solves;
+  st->batch_runs = sv->batch_runs;
   return HY_OK;
 }
 

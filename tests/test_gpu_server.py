@@ -154,3 +154,55 @@ def test_served_results_match_the_oracle():
         assert r["state"] == 2, (q, r)
         err = rel(r["u"], oracle_solution(q))
         assert err < 1e-8, (q, err)
+
+
+def test_batched_serving_matches_the_oracle():
+    """Batched serving: the outer CG solves of the running Newton iterations are fused across requests
+    (one list launch for the finest-level actions of a group per PCG iteration). The served results still
+    match the oracle's Newton (1e-8), the coarse-level retry included, and some solves were fused."""
+    require_gpu()
+    from paper_1904_13131_gb300.api import Server, SolverParams
+    solver = SolverParams(4, 1, 0.6, 1.2, 30, 0, 1e-3, 1, -1, 0, -1)
+    mix = ORACLE_MIX + [dict(ORACLE_MIX[1], ratio=12.0), dict(ORACLE_MIX[1], radius=0.3, compression=0.08)]
+    with Server(0, budget_bytes=8 << 30, max_active=len(mix), batching=True, window_ms=20.0) as sv:
+        tickets = [sv.submit(request_problem(q), newton(q, level_dtype=1), solver) for q in mix]
+        for t in tickets:
+            sv.wait(t, 600.0)
+        served = [sv.poll(t, want_u=True) for t in tickets]
+        st = sv.stats()
+    assert st["completed"] == len(mix) and st["failed"] == 0 and st["retried"] == 1
+    assert st["batched_solves"] >= sum(r["report"]["n_solves"] for r in served)
+    assert st["batch_runs"] < st["batched_solves"]  # solves were fused
+    for q, r in zip(mix, served):
+        err = rel(r["u"], oracle_solution(q))
+        assert err < 1e-8, (q, err)
+
+
+def test_batched_and_independent_serving_agree():
+    """The same requests served with fused solves and with independent per-request solves agree (1e-10)."""
+    require_gpu()
+    from paper_1904_13131_gb300.api import Server
+    out = []
+    for batching in (False, True):
+        with Server(0, budget_bytes=8 << 30, max_active=4, batching=batching) as s:
+            tickets = [s.submit(request_problem(q), newton(q, level_dtype=1)) for q in SMALL]
+            for t in tickets:
+                s.wait(t)
+            out.append([s.poll(t, want_u=True) for t in tickets])
+            st = s.stats()
+        assert st["completed"] == len(SMALL) and st["failed"] == 0
+    for a, b in zip(*out):
+        assert np.linalg.norm(b["u"] - a["u"]) <= 1e-10 * np.linalg.norm(a["u"])
+        assert b["report"]["newton_iterations"] == a["report"]["newton_iterations"]
+
+
+def test_batching_is_set_before_the_first_request():
+    require_gpu()
+    from paper_1904_13131_gb300.api import HyError, Server
+    with Server(0, budget_bytes=1 << 30, max_active=2) as s:
+        lib = s.lib
+        assert lib.hy_server_set_batching(s.h, 1, -1.0) == 1  # HY_ERR_ARG: bad window
+        assert lib.hy_server_set_batching(s.h, 1, 1.0) == 0
+        assert lib.hy_server_set_batching(s.h, 1, 1.0) == 2  # HY_ERR_STATE: already on
+    with pytest.raises(HyError):
+        Server(0, budget_bytes=1 << 30, max_active=2, batching=True, window_ms=5000.0)

@@ -923,33 +923,39 @@ def main():
             "f64_form": FORMS[ctxs[v].kernel_form(-1, 0)], "f32_form": FORMS[ctxs[v].kernel_form(-1, 1)],
             "ff_form": FORMS[ctxs[v].kernel_form(-1, 2)],
         }
-    # the second volumetric function (law 1) through the caching variants T4 and T2 in FP64
-    second_law = {}
-    for v in ("T4", "T2"):
-        ctxs[v].set_material_law(api.LAW_J2)
+    # the second volumetric function (law 1) and curved (isoparametric) cells through every variant in FP64
+    # and FP32: T4 and T2 fold both into their cached state, so their applies should cost what they cost on
+    # the lattice; FC, SC and NC run their general build (the reference map of every Gauss point read from
+    # the cache, the law chosen at run time), which has no double-float action
+    def relinearise(v, law=None, X=None, restore=False):
+        general_ff = v in ("FC", "SC", "NC")
+        if law is not None:
+            ctxs[v].set_material_law(law)
+        if X is not None or restore:
+            ctxs[v].set_geometry(X)
+        ctxs[v].set_solver_params(fine_dtype=api.FF if (restore or not general_ff) else api.F64)
         ctxs[v].set_displacement(u, v, level_dtype=1)
-    msl, _, _ = time_applies(torch, ctxs, ["T4", "T2"], x, 0, 5, 2, flush, stream)
-    for i, v in enumerate(("T4", "T2")):
-        t = float(np.median(msl[:, i]))
-        second_law[v] = {"f64_ms": t, "f64_gdofs": n / (t * 1e-3) / 1e9}
-        ctxs[v].set_material_law(api.LAW_LOG2)
-        ctxs[v].set_displacement(u, v, level_dtype=1)
-    steady = f32_steady_state(torch, api, inputs, dev, hbm)
-    # curved (isoparametric) cells through T4 and T2: M = J^{-1} F^{-1} and the weights w det(dX/dxi) are
-    # folded into the cache, so the applies should cost what they cost on the lattice
-    curved = {}
+
+    second_law, curved = {}, {}
+    for v in ALL_VARIANTS:
+        relinearise(v, law=api.LAW_J2)
+    msl64, _, _ = time_applies(torch, ctxs, ALL_VARIANTS, x, 0, 5, 2, flush, stream)
+    msl32, _, _ = time_applies(torch, ctxs, ALL_VARIANTS, x, 1, 5, 2, flush, stream)
+    for i, v in enumerate(ALL_VARIANTS):
+        t64, t32 = float(np.median(msl64[:, i])), float(np.median(msl32[:, i]))
+        second_law[v] = {"f64_ms": t64, "f64_gdofs": n / (t64 * 1e-3) / 1e9, "f32_ms": t32,
+                         "f32_gdofs": n / (t32 * 1e-3) / 1e9}
+        relinearise(v, law=api.LAW_LOG2, restore=True)
     Xc = torch.tensor(inputs.curved_coords(DIM, K, M).reshape(-1), device=dev)
-    for v in ("T4", "T2"):
-        ctxs[v].set_geometry(Xc)
-        ctxs[v].set_displacement(u, v, level_dtype=1)
-    msc64, _, _ = time_applies(torch, ctxs, ["T4", "T2"], x, 0, 5, 2, flush, stream)
-    msc32, _, _ = time_applies(torch, ctxs, ["T4", "T2"], x, 1, 5, 2, flush, stream)
-    for i, v in enumerate(("T4", "T2")):
+    for v in ALL_VARIANTS:
+        relinearise(v, X=Xc)
+    msc64, _, _ = time_applies(torch, ctxs, ALL_VARIANTS, x, 0, 5, 2, flush, stream)
+    msc32, _, _ = time_applies(torch, ctxs, ALL_VARIANTS, x, 1, 5, 2, flush, stream)
+    for i, v in enumerate(ALL_VARIANTS):
         t64, t32 = float(np.median(msc64[:, i])), float(np.median(msc32[:, i]))
         curved[v] = {"f64_ms": t64, "f64_gdofs": n / (t64 * 1e-3) / 1e9, "f32_ms": t32,
                      "f32_gdofs": n / (t32 * 1e-3) / 1e9}
-        ctxs[v].set_geometry(None)
-        ctxs[v].set_displacement(u, v, level_dtype=1)
+        relinearise(v, restore=True)
     del Xc
     # dominant kernel of the step: the slowest variant's FP64 apply (FP64-pipe bound). achieved = the scope
     # table's algorithmic flops per dof x dofs per launch / event time; the count of the kernel's own

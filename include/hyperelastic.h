@@ -93,9 +93,12 @@ hy_status hy_set_material(hy_ctx *ctx, int level, const uint8_t *cell_mat, const
  * HY_LAW_J2: U = lambda/4 (J^2 - 1 - 2 ln J). With p = J U'(J) both give tau = mu b - (mu - p) I and
  * J*C = 2 (mu - p) S + J p'(J) I (x) I. The law enters where the Gauss-point state is formed (the state
  * build, residual, diagonal and dense coarse assembly), so it goes through the caching variants T4 and
- * T2 unchanged; the recomputing variants FC, SC and NC keep the paper's law (hy_set_displacement returns
- * HY_ERR_UNSUPPORTED for them, also as level_variant, under HY_LAW_J2). Takes effect at the next
- * hy_set_displacement (and for hy_residual at once). HY_ERR_ARG for another value. */
+ * T2 unchanged. The recomputing variants FC, SC and NC form the state in every application: under
+ * HY_LAW_J2 they run their general build, which evaluates the volumetric function chosen at run time
+ * (and reads the reference map of every Gauss point from the cache: d^2 + 1 more cached values per point,
+ * see hy_set_geometry). The double-float action of FC/SC/NC has no general build (HY_ERR_UNSUPPORTED with
+ * fine_dtype = HY_FF). Takes effect at the next hy_set_displacement (and for hy_residual at once).
+ * HY_ERR_ARG for another value. */
 typedef enum { HY_LAW_LOG2 = 0, HY_LAW_J2 = 1 } hy_law;
 hy_status hy_set_material_law(hy_ctx *ctx, int law);
 
@@ -105,9 +108,14 @@ hy_status hy_set_material_law(hy_ctx *ctx, int law);
  * displacement down (Sec. 6). Gradients use dxi/dX = (dX/dxi)^{-1} and the volume weights w_q det(dX/dxi)
  * at every Gauss point. The map enters where the Gauss-point state is formed (state build, residual,
  * diagonal, dense coarse assembly), so it goes through the caching variants T4 and T2 with unchanged
- * applications; FC, SC and NC return HY_ERR_UNSUPPORTED from hy_set_displacement. Dead tractions keep the
+ * applications. FC, SC and NC (the paper's Algorithm 1 is SC) run their general build on curved cells: the
+ * state build caches the inverse Jacobian dxi/dX and the weight w_q det(dX/dxi) of every Gauss point (as
+ * the paper's matrix-free operators keep the mapping data of curved cells per quadrature point), d^2 + 1
+ * values beside the variant's own; the application maps its unit-cell gradients with them. Not with the
+ * double-float action (HY_ERR_UNSUPPORTED with fine_dtype = HY_FF). Dead tractions keep the
  * reference measure of the lattice faces (exact for maps that keep the faces in place). NULL returns to
- * the uniform lattice. The coordinates take sum over levels of n_dofs(l) * 8 bytes beyond hy_footprint.
+ * the uniform lattice. The coordinates take sum over levels of n_dofs(l) * 8 bytes beyond hy_footprint,
+ * and so do the extra cached values of FC/SC/NC.
  * Takes effect at the next hy_set_displacement (and for hy_residual at once). */
 hy_status hy_set_geometry(hy_ctx *ctx, const double *X_dev);
 

@@ -1031,11 +1031,13 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
   if (var < 0 || var > 4) return fail(ctx, HY_ERR_ARG, "variant out of range");
   if (ctx->sp.fine_dtype == HY_FF && ctx->n > 3)
     return fail(ctx, HY_ERR_UNSUPPORTED, "the double-float action is built for degrees 1-2");
-  if (ctx->law != HY_LAW_LOG2 &&
-      (var >= VAR_FC || (ctx->sp.level_variant >= VAR_FC)))
-    return fail(ctx, HY_ERR_UNSUPPORTED, "the second law goes through the caching variants T4 and T2");
-  if (ctx->curved && (var >= VAR_FC || (ctx->sp.level_variant >= VAR_FC)))
-    return fail(ctx, HY_ERR_UNSUPPORTED, "curved cells go through the caching variants T4 and T2");
+  // Curved cells or the second law: FC, SC and NC run their general builds (the reference map per Gauss
+  // point in the cache, the volumetric function chosen at run time); T4 and T2 fold both into their state.
+  const bool general = ctx->curved || ctx->law != HY_LAW_LOG2;
+  auto build_of = [general](int v) { return (general && v >= VAR_FC && v <= VAR_NC) ? v - VAR_FC + VAR_FCG : v; };
+  if (general && ctx->sp.fine_dtype == HY_FF && var >= VAR_FC)
+    return fail(ctx, HY_ERR_UNSUPPORTED,
+                "the double-float action of FC/SC/NC is built for the lattice and the paper's law only");
   ctx->state_ok = false;
   drop_graph(ctx);
   ctx->var = var;
@@ -1069,8 +1071,8 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
     L.form[0] = L.form[1] = L.form[2] = -1;
     // the finest level's FP64 and double-float caches serve the outer CG: the given variant; the V-cycle's
     // level operators (every cache below the finest, and its FP32 cache) take the level variant
-    const int lvar = ctx->sp.level_variant >= 0 ? ctx->sp.level_variant : var;
-    L.var[0] = l == top ? var : lvar;
+    const int lvar = build_of(ctx->sp.level_variant >= 0 ? ctx->sp.level_variant : var);
+    L.var[0] = l == top ? build_of(var) : lvar;
     L.var[1] = lvar;
     L.var[2] = var;
     if (need64) {
@@ -2450,6 +2452,14 @@ hy_status hy_dot(hy_ctx* ctx, const double* a, const double* b, int64_t n, doubl
 // hy_set_displacement (requested sizes; the allocator's own rounding comes on top).
 hy_status hy_footprint(int dim, int degree, int m, int n_levels, hy_variant variant, hy_dtype level_dtype,
                        const hy_solver_params* sp, const uint32_t* face_masks, int64_t* bytes) {
+  return hy_footprint_general(dim, degree, m, n_levels, variant, level_dtype, sp, face_masks, false, bytes);
+}
+
+}  // extern "C"
+
+hy_status hy_footprint_general(int dim, int degree, int m, int n_levels, hy_variant variant, hy_dtype level_dtype,
+                               const hy_solver_params* sp, const uint32_t* face_masks, bool general,
+                               int64_t* bytes) {
   if (!bytes || (dim != 2 && dim != 3) || degree < 1 || degree > 4 || m < 1 || n_levels < 1) return HY_ERR_ARG;
   const int coarse_solver = sp ? sp->coarse_solver : 0;
   const hy_dtype fine_dtype = sp ? sp->fine_dtype : HY_F64;
@@ -2491,8 +2501,10 @@ hy_status hy_footprint(int dim, int degree, int m, int n_levels, hy_variant vari
     const bool need64 = (l == top) || (l == 0) || !mixed;
     const bool need32 = mixed && (l > 0 || l == top);
     const int cb64 = layout_cells<double>(dim, n), cb32 = layout_cells<float>(dim, n);
-    const int lvar = level_variant >= 0 ? level_variant : (int)variant;  // as set_displacement assigns them
-    const int var64 = l == top ? (int)variant : lvar;
+    // as set_displacement assigns them
+    auto build_of = [general](int v) { return (general && v >= VAR_FC && v <= VAR_NC) ? v - VAR_FC + VAR_FCG : v; };
+    const int lvar = build_of(level_variant >= 0 ? level_variant : (int)variant);
+    const int var64 = l == top ? build_of((int)variant) : lvar;
     const size_t clen64 = std::max<size_t>(1, (size_t)cache_values(var64, dim) * layout_row<double>(dim, n) *
                                                   (size_t)((nc[l] + cb64 - 1) / cb64));
     const size_t clen32 = std::max<size_t>(1, (size_t)cache_values(lvar, dim) * layout_row<float>(dim, n) *
@@ -2530,6 +2542,8 @@ hy_status hy_footprint(int dim, int degree, int m, int n_levels, hy_variant vari
   *bytes = (int64_t)total;
   return HY_OK;
 }
+
+extern "C" {
 
 hy_status hy_ctx_bytes(const hy_ctx* ctx, int64_t* bytes) {
   if (!ctx || !bytes) return HY_ERR_ARG;

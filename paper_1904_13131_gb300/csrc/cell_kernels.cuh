@@ -428,9 +428,10 @@ __device__ __forceinline__ T neo_hooke_state(const T F[DIM][DIM], T mu, T lam, i
 // the unit-cell shape gradients is P~ = Q' adj^T, Q' = g' tau' + c1' sym(g') + c2' tr(g') I, where
 // g' = Grad x adj, tau' = kappa tau, c1' = 2 kappa (mu - 2 lambda ln J), c2' = 2 kappa lambda -- the same
 // quantity as W/h (g tau + JC : sym g) F^{-T} with g = Grad x F^{-1}.
-template <int DIM, typename T>
+// LAW: the volumetric function is the material's (law 0 or 1, chosen at run time) instead of the paper's.
+template <int DIM, typename T, bool LAW = false>
 __device__ __forceinline__ void neo_hooke_adj(const T F[DIM][DIM], T mu, T lam, T Wh, bool have_c, T c_in,
-                                              T adj[DIM][DIM], T tau[nsym(DIM)], T& c1, T& c2) {
+                                              T adj[DIM][DIM], T tau[nsym(DIM)], T& c1, T& c2, int law = 0) {
   T J;
   if (DIM == 3) {
     adj[0][0] = F[1][1] * F[2][2] - F[1][2] * F[2][1];
@@ -453,7 +454,15 @@ __device__ __forceinline__ void neo_hooke_adj(const T F[DIM][DIM], T mu, T lam, 
   T rho;
   rho = rcp_rn(J);
   const T kappa = Wh * rho * rho;
-  const T c = have_c ? c_in : mu - T(2) * lam * log(J);
+  T c, jdp;
+  if (LAW) {
+    T pv;
+    volumetric(J, lam, law, pv, jdp);
+    c = have_c ? c_in : mu - pv;
+  } else {
+    c = have_c ? c_in : mu - T(2) * lam * log(J);
+    jdp = T(2) * lam;
+  }
   const T kmu = kappa * mu, kc = kappa * c;
 #pragma unroll
   for (int a = 0; a < nsym(DIM); ++a) {
@@ -464,7 +473,7 @@ __device__ __forceinline__ void neo_hooke_adj(const T F[DIM][DIM], T mu, T lam, 
     tau[a] = (i == j) ? fma(kmu, bij, -kc) : kmu * bij;
   }
   c1 = T(2) * kc;
-  c2 = T(2) * kappa * lam;
+  c2 = kappa * jdp;
 }
 
 // Material part for the neo-Hooke action (Eq. simplified_action): S = c1 sym(g) + c2 tr(g) I.
@@ -541,10 +550,15 @@ struct CellLoc {
 //   T4: P~ = (g tau~ + JC~ : sym g) M^T, g = G M with M = F^{-1}/h, tau~, JC~ cached   (Algorithm 3)
 //   T2: the same with JC~ : s = c1~ s + c2~ tr(s) I                                     (Algorithm 2)
 //   FC/SC/NC: the state recomputed from F (cached, or I + Grad u), with g' = Grad x adj F (Algorithm 1 for SC).
+//   FCG/SCG/NCG (curved cells, either law): G and Gu are unit-cell derivatives, mapped by the cached
+//   inverse Jacobian invJ; the cached weight W replaces W/h, and the flux is mapped back, P~ = P invJ^T.
 template <int DIM, int VAR, typename T>
 __device__ __forceinline__ void qp_flux(const T G[DIM][DIM], const T Gu[DIM][DIM], const T* __restrict__ cs, int st,
-                                        int qg, bool active, int id, const T* mu, const T* lam, T Wh, T P[DIM][DIM]) {
+                                        int qg, bool active, int id, const T* mu, const T* lam, T Wh, T P[DIM][DIM],
+                                        int law = 0) {
   constexpr int NS = nsym(DIM);
+  constexpr int BV = base_variant(VAR);
+  constexpr bool GEN = is_general(VAR);
   T M[DIM][DIM], tau[NS], Sv[NS], g[DIM][DIM];
   if (VAR == VAR_T4 || VAR == VAR_T2) {
 #pragma unroll
@@ -578,22 +592,57 @@ __device__ __forceinline__ void qp_flux(const T G[DIM][DIM], const T Gu[DIM][DIM
       nh_action<DIM>(g, c1, c2, Sv);
     }
   } else {
+    // the reference map of this point (general build): invJ rows after the variant's own, then W
+    constexpr int GOFF = cache_values(BV, DIM);
+    T Ji[DIM][DIM], Gx[DIM][DIM], W = Wh;
+    if (GEN) {
+#pragma unroll
+      for (int i = 0; i < DIM * DIM; ++i)
+        Ji[i / DIM][i % DIM] = active ? cs[(GOFF + i) * st + qg] : (i % (DIM + 1) == 0 ? T(1) : T(0));
+      W = active ? cs[(GOFF + DIM * DIM) * st + qg] : T(0);
+      matmul<DIM>(G, Ji, Gx);
+    }
     T F[DIM][DIM];
-    if (VAR == VAR_FC) {
+    if (BV == VAR_FC) {
 #pragma unroll
       for (int i = 0; i < DIM * DIM; ++i)
         F[i / DIM][i % DIM] = active ? cs[i * st + qg] : (i % (DIM + 1) == 0 ? T(1) : T(0));
     } else {
+      T Gp[DIM][DIM];
+      if (GEN) {
+        matmul<DIM>(Gu, Ji, Gp);
+      } else {
+#pragma unroll
+        for (int i = 0; i < DIM * DIM; ++i) Gp[i / DIM][i % DIM] = Gu[i / DIM][i % DIM];
+      }
 #pragma unroll
       for (int i = 0; i < DIM; ++i)
 #pragma unroll
-        for (int J = 0; J < DIM; ++J) F[i][J] = (i == J) ? T(1) + Gu[i][J] : Gu[i][J];
+        for (int J = 0; J < DIM; ++J) F[i][J] = (i == J) ? T(1) + Gp[i][J] : Gp[i][J];
     }
-    const T cin = (VAR == VAR_SC && active) ? cs[qg] : T(0);
+    const T cin = (BV == VAR_SC && active) ? cs[qg] : T(0);
     T c1, c2;
-    neo_hooke_adj<DIM>(F, mu[id], lam[id], Wh, VAR == VAR_SC, cin, M, tau, c1, c2);  // M = adj
-    matmul<DIM>(G, M, g);
+    neo_hooke_adj<DIM, T, GEN>(F, mu[id], lam[id], W, BV == VAR_SC, cin, M, tau, c1, c2, law);  // M = adj
+    if (GEN) {
+      matmul<DIM>(Gx, M, g);
+    } else {
+      matmul<DIM>(G, M, g);
+    }
     nh_action<DIM>(g, c1, c2, Sv);
+    if (GEN) {
+      T Pp[DIM][DIM];
+      finish_flux<DIM>(g, tau, Sv, M, Pp);
+#pragma unroll
+      for (int c = 0; c < DIM; ++c)
+#pragma unroll
+        for (int J = 0; J < DIM; ++J) {
+          T v = Pp[c][0] * Ji[J][0];
+#pragma unroll
+          for (int K = 1; K < DIM; ++K) v = fma(Pp[c][K], Ji[J][K], v);
+          P[c][J] = v;
+        }
+      return;
+    }
   }
   finish_flux<DIM>(g, tau, Sv, M, P);
 }
@@ -610,7 +659,8 @@ __device__ __forceinline__ void apply_point_body(const CellArgs<T>& a, const int
   constexpr int NPT = ipow(N, DIM);
   constexpr int CB = layout_cells<T>(DIM, N);
   constexpr int NS = nsym(DIM);
-  constexpr bool NEED_U = (VAR == VAR_NC || VAR == VAR_SC);
+  constexpr int BV = base_variant(VAR);
+  constexpr bool NEED_U = (BV == VAR_NC || BV == VAR_SC);
   constexpr int NV = cache_values(VAR, DIM);
   constexpr int BS = layout_row<T>(DIM, N);
   __shared__ Smem<DIM, N, T, CB> s;
@@ -649,7 +699,8 @@ __device__ __forceinline__ void apply_point_body(const CellArgs<T>& a, const int
   __syncthreads();
   // coefficient rows of this thread's lines: loaded once (FP32) or before each stage (FP64)
   constexpr bool HOIST = false;
-  constexpr bool PHYS = (VAR == VAR_FC || NEED_U);  // derivatives in physical units (D / h)
+  // derivatives in physical units (D / h) on the lattice; the general build maps unit-cell ones itself
+  constexpr bool PHYS = (BV == VAR_FC || NEED_U) && !is_general(VAR);
   LineCoef<DIM, N, T> kS, kD, kSt, kDt;
   if (HOIST) {
     kS.rows(s.S, pt);
@@ -664,7 +715,7 @@ __device__ __forceinline__ void apply_point_body(const CellArgs<T>& a, const int
     T* src[2] = {b0, bp};
     T* dst[2] = {b1, bp + DIM * NPT};
     sweeps_forward_coef<DIM, N, 2>(src, dst, pt, kS);  // both fields in the same stages
-    if (!HOIST) kD.rows(s.Dh, pt);
+    if (!HOIST) kD.rows(PHYS ? s.Dh : s.D, pt);
     grad_coef<DIM, N>(src[0], pt, kD, G);   // physical gradients: Grad x, Grad u
     grad_coef<DIM, N>(src[1], pt, kD, Gu);
     __syncthreads();  // bp is overwritten with the fluxes below
@@ -685,7 +736,8 @@ __device__ __forceinline__ void apply_point_body(const CellArgs<T>& a, const int
   }
   // quadrature-point work
   T P[DIM][DIM];
-  qp_flux<DIM, VAR>(G, Gu, cs, BS, threadIdx.x, active, active ? a.mat[cell] : 0, s.mu, s.lam, s.Wh[pt.p], P);
+  qp_flux<DIM, VAR>(G, Gu, cs, BS, threadIdx.x, active, active ? a.mat[cell] : 0, s.mu, s.lam, s.Wh[pt.p], P,
+                    a.mt.law);
 #pragma unroll
   for (int c = 0; c < DIM; ++c)
 #pragma unroll
@@ -721,8 +773,9 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
   constexpr int CB = layout_cells<T>(DIM, N);
   constexpr int TL = CB * NLC;  // line threads of the block
   constexpr int K = N - 1;
-  constexpr bool NEED_U = (VAR == VAR_NC || VAR == VAR_SC);
-  constexpr bool PHYS = (VAR == VAR_FC || NEED_U);
+  constexpr int BV = base_variant(VAR);
+  constexpr bool NEED_U = (BV == VAR_NC || BV == VAR_SC);
+  constexpr bool PHYS = (BV == VAR_FC || NEED_U) && !is_general(VAR);
   constexpr int NV = cache_values(VAR, DIM);
   constexpr int BS = layout_row<T>(DIM, N);
   // Line buffers, component- and Gauss-index-major: entry (c, q, line i of the block) at (c N + q) TL + i,
@@ -929,7 +982,7 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
         }
       }
       T P[DIM][DIM];
-      qp_flux<DIM, VAR>(G, Gu, cq, BS, cl * NPT + p, active, id, tmu, tlam, tWh[p], P);
+      qp_flux<DIM, VAR>(G, Gu, cq, BS, cl * NPT + p, active, id, tmu, tlam, tWh[p], P, a.mt.law);
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
         Px[q][c] = P[c][0];
@@ -1252,13 +1305,22 @@ qp_state_kernel(const CellArgs<double> a, T* __restrict__ out) {
           ++idx;
         }
     }
-  } else if (VAR == VAR_FC) {
+  } else if (base_variant(VAR) == VAR_FC) {
 #pragma unroll
     for (int i = 0; i < DIM * DIM; ++i) out[i * st + qg] = T(F[i / DIM][i % DIM]);
-  } else if (VAR == VAR_SC) {
+  } else if (base_variant(VAR) == VAR_SC) {
     double pv, jdp;
     volumetric(J, lam, a.mt.law, pv, jdp);
     out[qg] = T(mu - pv);
+  }
+  if (is_general(VAR)) {  // the reference map of the point: invJ (I/h on the lattice), then w_q det(dX/dxi)
+    constexpr int GOFF = cache_values(base_variant(VAR), DIM);
+#pragma unroll
+    for (int i = 0; i < DIM * DIM; ++i) {
+      const int r = i / DIM, c = i % DIM;
+      out[(GOFF + i) * st + qg] = T(curved ? invJ[r][c] : (r == c ? inv_h : 0.0));
+    }
+    out[(GOFF + DIM * DIM) * st + qg] = T(curved ? wdet : s.W[pt.p]);
   }
 }
 

@@ -18,11 +18,21 @@ constexpr int MAXMAT = 16;   // materials per level
 
 // Sizes of the per-Gauss-point caches of the tangent variants (Algorithms 1-3 and the two
 // cached/recomputed variants), as a function of dim.
-enum Variant { VAR_T4 = 0, VAR_T2 = 1, VAR_FC = 2, VAR_SC = 3, VAR_NC = 4 };
+//   The variants that form the state inside the action (FC, SC, NC) come in two builds. The plain one
+// assumes the uniform lattice (1/h and w_q h^d as constants) and the paper's volumetric function. The
+// general one (FCG, SCG, NCG) reads the reference map of its Gauss point from the cache -- the inverse
+// Jacobian d xi / d X (dim^2 values) and the volume weight w_q det(dX/dxi), as the paper's matrix-free
+// operators keep the mapping data of curved cells per quadrature point -- and evaluates the material's
+// volumetric function chosen at run time: curved cells and the second law. (Index 5 is VAR_NONE, the
+// state kernel that only checks J.)
+enum Variant { VAR_T4 = 0, VAR_T2 = 1, VAR_FC = 2, VAR_SC = 3, VAR_NC = 4, VAR_FCG = 6, VAR_SCG = 7, VAR_NCG = 8 };
 
+__host__ __device__ constexpr bool is_general(int var) { return var >= VAR_FCG; }
+__host__ __device__ constexpr int base_variant(int var) { return is_general(var) ? var - VAR_FCG + VAR_FC : var; }
 __host__ __device__ constexpr int nsym(int dim) { return dim == 3 ? 6 : 3; }
 __host__ __device__ constexpr int cache_values(int var, int dim) {
-  return var == VAR_T4 ? dim * dim + nsym(dim) + nsym(dim) * (nsym(dim) + 1) / 2
+  return is_general(var) ? cache_values(base_variant(var), dim) + dim * dim + 1
+       : var == VAR_T4 ? dim * dim + nsym(dim) + nsym(dim) * (nsym(dim) + 1) / 2
        : var == VAR_T2 ? dim * dim + nsym(dim) + 2
        : var == VAR_FC ? dim * dim
        : var == VAR_SC ? 1

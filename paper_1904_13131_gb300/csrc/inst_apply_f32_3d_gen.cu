@@ -1,0 +1,9 @@
+// Tangent-action kernels, float, dim 3, degrees 1-4: the general builds of FC, SC and NC (the reference
+// map per Gauss point from the cache, the volumetric function chosen at run time), one problem or a
+// work list.
+#define INST_DIM 3
+#define INST_T float
+#define INST_GEN 1
+#define INST_NAME apply_fn_f32_3d_gen
+#define INST_LIST_NAME apply_list_fn_f32_3d_gen
+#include "inst_apply.inc"

@@ -27,33 +27,40 @@ void launch_diag(const CellArgs<double>& a, cudaStream_t st) {
 }
 }  // namespace
 
+// indexed by Variant (0-4, VAR_NONE = 5, the general builds 6-8; double-float has no general build)
 #define HY_SROW(D, N, T)                                                                                   \
   { launch_state<D, N, VAR_T4, T>, launch_state<D, N, VAR_T2, T>, launch_state<D, N, VAR_FC, T>,           \
-    launch_state<D, N, VAR_SC, T>, launch_state<D, N, VAR_NC, T>, launch_state<D, N, VAR_NONE, T> }
+    launch_state<D, N, VAR_SC, T>, launch_state<D, N, VAR_NC, T>, launch_state<D, N, VAR_NONE, T>,         \
+    launch_state<D, N, VAR_FCG, T>, launch_state<D, N, VAR_SCG, T>, launch_state<D, N, VAR_NCG, T> }
+#define HY_SROW_FF(D, N)                                                                                   \
+  { launch_state<D, N, VAR_T4, ff>, launch_state<D, N, VAR_T2, ff>, launch_state<D, N, VAR_FC, ff>,         \
+    launch_state<D, N, VAR_SC, ff>, launch_state<D, N, VAR_NC, ff>, launch_state<D, N, VAR_NONE, ff>,       \
+    nullptr, nullptr, nullptr }
 
 StateFn<double> state_fn_f64(int dim, int n, int var) {
-  static const StateFn<double> t2[4][6] = {HY_SROW(2, 2, double), HY_SROW(2, 3, double), HY_SROW(2, 4, double),
+  static const StateFn<double> t2[4][9] = {HY_SROW(2, 2, double), HY_SROW(2, 3, double), HY_SROW(2, 4, double),
                                            HY_SROW(2, 5, double)};
-  static const StateFn<double> t3[4][6] = {HY_SROW(3, 2, double), HY_SROW(3, 3, double), HY_SROW(3, 4, double),
+  static const StateFn<double> t3[4][9] = {HY_SROW(3, 2, double), HY_SROW(3, 3, double), HY_SROW(3, 4, double),
                                            HY_SROW(3, 5, double)};
-  if (n < 2 || n > 5 || var < 0 || var > 5) return nullptr;
+  if (n < 2 || n > 5 || var < 0 || var > 8) return nullptr;
   return dim == 2 ? t2[n - 2][var] : dim == 3 ? t3[n - 2][var] : nullptr;
 }
 StateFn<float> state_fn_f32(int dim, int n, int var) {
-  static const StateFn<float> t2[4][6] = {HY_SROW(2, 2, float), HY_SROW(2, 3, float), HY_SROW(2, 4, float),
+  static const StateFn<float> t2[4][9] = {HY_SROW(2, 2, float), HY_SROW(2, 3, float), HY_SROW(2, 4, float),
                                           HY_SROW(2, 5, float)};
-  static const StateFn<float> t3[4][6] = {HY_SROW(3, 2, float), HY_SROW(3, 3, float), HY_SROW(3, 4, float),
+  static const StateFn<float> t3[4][9] = {HY_SROW(3, 2, float), HY_SROW(3, 3, float), HY_SROW(3, 4, float),
                                           HY_SROW(3, 5, float)};
-  if (n < 2 || n > 5 || var < 0 || var > 5) return nullptr;
+  if (n < 2 || n > 5 || var < 0 || var > 8) return nullptr;
   return dim == 2 ? t2[n - 2][var] : dim == 3 ? t3[n - 2][var] : nullptr;
 }
 StateFn<ff> state_fn_ff(int dim, int n, int var) {
-  static const StateFn<ff> t2[4][6] = {HY_SROW(2, 2, ff), HY_SROW(2, 3, ff), HY_SROW(2, 4, ff), HY_SROW(2, 5, ff)};
-  static const StateFn<ff> t3[4][6] = {HY_SROW(3, 2, ff), HY_SROW(3, 3, ff), HY_SROW(3, 4, ff), HY_SROW(3, 5, ff)};
-  if (n < 2 || n > 5 || var < 0 || var > 5) return nullptr;
+  static const StateFn<ff> t2[4][9] = {HY_SROW_FF(2, 2), HY_SROW_FF(2, 3), HY_SROW_FF(2, 4), HY_SROW_FF(2, 5)};
+  static const StateFn<ff> t3[4][9] = {HY_SROW_FF(3, 2), HY_SROW_FF(3, 3), HY_SROW_FF(3, 4), HY_SROW_FF(3, 5)};
+  if (n < 2 || n > 5 || var < 0 || var > 8) return nullptr;
   return dim == 2 ? t2[n - 2][var] : dim == 3 ? t3[n - 2][var] : nullptr;
 }
 #undef HY_SROW
+#undef HY_SROW_FF
 
 CellFn<double> residual_fn(int dim, int n) {
   static const CellFn<double> t[2][4] = {{launch_residual<2, 2>, launch_residual<2, 3>, launch_residual<2, 4>,

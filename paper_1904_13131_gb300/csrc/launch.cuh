@@ -26,16 +26,21 @@ template <typename T>
 inline int apply_cells_per_block(int dim, int n) { return layout_cells<T>(dim, n); }
 
 // n = degree + 1 in 2..5; var in Variant; returns nullptr for unsupported combinations. The kernels of
-// degrees 1-2 (n <= 3) and 3-4 live in separate translation units (_lo, _hi) that compile in parallel.
+// degrees 1-2 (n <= 3) and 3-4 live in separate translation units (_lo, _hi) that compile in parallel, and
+// so do the general builds of FC, SC, NC (_gen).
 #define HY_APPLY_TABLES(P, TAG, D)                                                                      \
   ApplyFn<P> apply_fn_##TAG##_##D##_lo(int n, int var);                                              \
   ApplyFn<P> apply_fn_##TAG##_##D##_hi(int n, int var);                                              \
+  ApplyFn<P> apply_fn_##TAG##_##D##_gen(int n, int var);                                             \
   ApplyListFn<P> apply_list_fn_##TAG##_##D##_lo(int n, int var);                                     \
   ApplyListFn<P> apply_list_fn_##TAG##_##D##_hi(int n, int var);                                     \
+  ApplyListFn<P> apply_list_fn_##TAG##_##D##_gen(int n, int var);                                    \
   inline ApplyFn<P> apply_fn_##TAG##_##D(int n, int var) {                                           \
+    if (is_general(var)) return apply_fn_##TAG##_##D##_gen(n, var);                                  \
     return n <= 3 ? apply_fn_##TAG##_##D##_lo(n, var) : apply_fn_##TAG##_##D##_hi(n, var);             \
   }                                                                                                \
   inline ApplyListFn<P> apply_list_fn_##TAG##_##D(int n, int var) {                                  \
+    if (is_general(var)) return apply_list_fn_##TAG##_##D##_gen(n, var);                             \
     return n <= 3 ? apply_list_fn_##TAG##_##D##_lo(n, var) : apply_list_fn_##TAG##_##D##_hi(n, var);   \
   }
 HY_APPLY_TABLES(double, f64, 2d)

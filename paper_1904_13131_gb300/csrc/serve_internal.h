@@ -20,3 +20,9 @@ long long hy_ctx_batch_key(const hy_ctx* ctx);
 // (1..capacity contexts of one device, dimension and degree) before each hy_batch_pcg / hy_batch_apply.
 hy_status hy_batch_create_empty(hy_batch** out, int device, int capacity);
 hy_status hy_batch_bind(hy_batch* b, hy_ctx* const* ctxs, int count);
+
+// hy_footprint with `general` set: the bytes when FC, SC and NC run their general builds (curved cells or
+// a volumetric function other than the paper's), whose caches add dim^2 + 1 values per Gauss point.
+hy_status hy_footprint_general(int dim, int degree, int m, int n_levels, hy_variant variant, hy_dtype level_dtype,
+                               const hy_solver_params* sp, const uint32_t* face_masks, bool general,
+                               int64_t* bytes);

@@ -204,7 +204,9 @@ int64_t attempt_bytes(const Req& r, int drop) {
   const double nc = r.dim * std::pow(r.degree * (double)mc + 1.0, r.dim);
   if (drop > 0 && nc > 6000.0) sp.coarse_solver = 0;
   int64_t bytes = 0;
-  if (hy_footprint(r.dim, r.degree, r.m, nlev, r.np.variant, r.np.level_dtype, &sp, r.fm, &bytes) != HY_OK) return -1;
+  if (hy_footprint_general(r.dim, r.degree, r.m, nlev, r.np.variant, r.np.level_dtype, &sp, r.fm,
+                           r.law != HY_LAW_LOG2, &bytes) != HY_OK)
+    return -1;
   return bytes + (int64_t)sizeof(double) * r.dim * (int64_t)std::llround(std::pow(r.degree * r.m + 1.0, r.dim));
 }
 
@@ -420,8 +422,8 @@ hy_status hy_server_submit(hy_server* sv, const hy_request* q, uint64_t* ticket)
   if (q->law != HY_LAW_LOG2 && q->law != HY_LAW_J2) return HY_ERR_ARG;
   r->law = q->law;
   int64_t bytes = 0;
-  hy_status s = hy_footprint(r->dim, r->degree, r->m, r->nlev, q->newton.variant, q->newton.level_dtype, &q->solver,
-                             r->fm, &bytes);
+  hy_status s = hy_footprint_general(r->dim, r->degree, r->m, r->nlev, q->newton.variant, q->newton.level_dtype,
+                                     &q->solver, r->fm, q->law != HY_LAW_LOG2, &bytes);
   if (s != HY_OK) return s;
   const int64_t n_u = r->dim * (int64_t)std::llround(std::pow(r->degree * r->m + 1.0, r->dim));
   r->bytes = bytes + (int64_t)sizeof(double) * n_u;  // + u

@@ -1,12 +1,14 @@
-"""Curved (isoparametric) cells through the caching variants.
+"""Curved (isoparametric) cells through every variant.
 
 Parity with the oracle's isoparametric Problem on the seeded curved geometry (inputs.curved_coords): the
-tangent action of T4 and T2 in FP64 (1e-12), FP32 (2e-6) and double-float (1e-12); the residual and the
-diagonal (1e-12); Newton with FP64 and mixed V-cycles and the exact coarse inverse (1e-8). The curved
-result differs from the lattice one (checked). A V-cycle with the exact coarse inverse matches the
-oracle's hierarchy with the coordinates carried down by nodal interpolation (1e-10), which pins the
-coarse-level geometry and the dense coarse assembly on curved cells. The recomputing variants refuse
-curved cells.
+tangent action of all five variants in FP64 (1e-12) and FP32 (2e-6), both kernel forms -- T4 and T2 fold
+the map into their cached state, FC, SC (the paper's Algorithm 1) and NC run their general build, which
+reads the inverse Jacobian and weight of each Gauss point from the cache -- and of T4/T2 in double-float
+(1e-12); the residual and the diagonal (1e-12); Newton with FP64 and mixed V-cycles and the exact coarse
+inverse (1e-8), through T4 and SC. The curved result differs from the lattice one (checked). A V-cycle
+with the exact coarse inverse matches the oracle's hierarchy with the coordinates carried down by nodal
+interpolation (1e-10), which pins the coarse-level geometry and the dense coarse assembly on curved cells.
+The double-float action has no general build of FC/SC/NC and refuses them.
 """
 import numpy as np
 import pytest
@@ -44,13 +46,16 @@ def test_apply_residual_diagonal_on_curved_cells(torch, dim, k, m):
     with context(pr) as ctx:
         ctx.set_geometry(torch.tensor(X.reshape(-1), device="cuda"))
         assert rel(ctx.residual(ud).cpu().numpy(), P.residual(u)) < 1e-12
-        ctx.set_solver_params(coarse_eig_iters=5, fine_dtype=FF if k <= 2 else 0)
-        for var in ("T4", "T2"):
-            ctx.set_displacement(ud, var, level_dtype=1)
-            assert rel(ctx.apply_tangent(xd).cpu().numpy(), y_ref) < 1e-12, var
-            assert rel(ctx.apply_tangent(xd.float(), dtype=1).cpu().numpy(), y_ref) < 2e-6, var
-            if k <= 2:
-                assert rel(ctx.apply_tangent(xd, dtype=FF).cpu().numpy(), y_ref) < 1e-12, var
+        for var in ("T4", "T2", "FC", "SC", "NC"):
+            for form in (0, 1):
+                ff = k <= 2 and var in ("T4", "T2")
+                ctx.set_solver_params(coarse_eig_iters=5, fine_dtype=FF if ff else 0, kernel_form=form)
+                ctx.set_displacement(ud, var, level_dtype=1)
+                assert rel(ctx.apply_tangent(xd).cpu().numpy(), y_ref) < 1e-12, (var, form)
+                assert rel(ctx.apply_tangent(xd.float(), dtype=1).cpu().numpy(), y_ref) < 2e-6, (var, form)
+                if ff:
+                    assert rel(ctx.apply_tangent(xd, dtype=FF).cpu().numpy(), y_ref) < 1e-12, (var, form)
+        ctx.set_solver_params(kernel_form=-1)
         assert rel(ctx.diagonal().cpu().numpy(), P.diagonal(u)) < 1e-12
         ctx.set_geometry(None)  # back to the lattice
         ctx.set_displacement(ud, "T4")
@@ -77,8 +82,9 @@ def test_vcycle_on_curved_cells(torch, dim, k, m, L):
     assert rel(z, H.vcycle(bb)) < 1e-10
 
 
+@pytest.mark.parametrize("variant", ["T4", "SC"])
 @pytest.mark.parametrize("dim,k,m,L", [(2, 2, 8, 3), (3, 2, 4, 2)])
-def test_newton_on_curved_cells(torch, dim, k, m, L):
+def test_newton_on_curved_cells(torch, dim, k, m, L, variant):
     from paper_1904_13131_gb300.api import Context
     pr = problem(dim, k, m, n_levels=L)
     X = inputs.curved_coords(dim, k, m)
@@ -94,19 +100,24 @@ def test_newton_on_curved_cells(torch, dim, k, m, L):
         for ldt, coarse in ((0, 0), (1, 1)):
             ctx.set_solver_params(coarse_solver=coarse)
             u = torch.zeros(ctx.num_dofs(), dtype=torch.float64, device="cuda")
-            rep = ctx.newton_solve(u, Context.newton_params(load_steps=3, level_dtype=ldt, face_values=fv))
+            rep = ctx.newton_solve(u, Context.newton_params(load_steps=3, level_dtype=ldt, face_values=fv,
+                                                            variant=variant))
             assert rep["load_steps_done"] == 3
             assert rel(u.cpu().numpy(), u_ref) < 1e-8, (ldt, coarse)
 
 
-def test_recomputing_variants_refuse_curved_cells(torch):
-    from paper_1904_13131_gb300.api import HyError
+def test_double_float_refuses_the_general_builds(torch):
+    from paper_1904_13131_gb300.api import FF, HyError
     dim, k, m = 2, 1, 2
     pr = problem(dim, k, m)
     with context(pr) as ctx:
         ctx.set_geometry(torch.tensor(inputs.curved_coords(dim, k, m).reshape(-1), device="cuda"))
         u = torch.zeros(ctx.num_dofs(), dtype=torch.float64, device="cuda")
+        ctx.set_solver_params(fine_dtype=FF)
         for var in ("FC", "SC", "NC"):
             with pytest.raises(HyError) as e:
                 ctx.set_displacement(u, var)
             assert e.value.status == "HY_ERR_UNSUPPORTED"
+        ctx.set_solver_params(fine_dtype=0)
+        for var in ("FC", "SC", "NC"):
+            ctx.set_displacement(u, var)

@@ -53,8 +53,8 @@ def test_apply_residual_diagonal_second_law(torch, dim, k, m):
                 assert rel(ctx.apply_tangent(xd.float(), dtype=1).cpu().numpy(), y_ref) < 2e-6, (var, form)
                 if ff:
                     assert rel(ctx.apply_tangent(xd, dtype=FF).cpu().numpy(), y_ref) < 1e-12, (var, form)
-        ctx.set_solver_params(kernel_form=-1)
         assert rel(ctx.diagonal().cpu().numpy(), P.diagonal(u)) < 1e-12
+        ctx.set_solver_params(kernel_form=-1)
 
 
 @pytest.mark.parametrize("variant", ["T4", "NC"])

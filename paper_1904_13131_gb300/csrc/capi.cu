@@ -188,6 +188,11 @@ struct Level {
   int* d_cidx = nullptr;      // dof -> compact index or -1
   long long nfree = 0;
   double* d_Aresult = nullptr;  // whichever of the pair holds the inverse
+  // the eigenvalue estimate's iterations as an executable graph, replayed while every argument its kernels
+  // were captured with (the signature) is unchanged
+  cudaGraphExec_t eig_exec = nullptr;
+  std::vector<unsigned char> eig_sig;
+  long long eig_nodes = 0;
 };
 
 struct Transfer {  // level l-1 (coarse) <-> l (fine); the same 1D tables act along every axis
@@ -246,6 +251,11 @@ struct hy_ctx {
   double* h_pcg_scal = nullptr;
   long long vc_nodes = 0;
   std::vector<std::pair<void*, size_t>> allocs;
+  // the exact coarse inverse is built on a side stream, overlapping the rest of the linearisation
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_side_fork = nullptr, ev_side_join = nullptr;
+  unsigned* h_err_side = nullptr;  // pinned: the side stream's error word, read after the join
+  bool side_pending = false;
   // replacement of the outer PCG inside hy_newton_solve (the solve server's batched solves), or null
   hy_linear_solve_hook solve_hook = nullptr;
   void* solve_user = nullptr;
@@ -318,7 +328,11 @@ void drop_graph(hy_ctx* ctx) {
 }
 
 void free_mesh(hy_ctx* ctx) {
+  if (ctx->side) cudaStreamSynchronize(ctx->side);  // a coarse setup in flight uses the level buffers
+  ctx->side_pending = false;
   drop_graph(ctx);
+  for (Level& L : ctx->lev)
+    if (L.eig_exec) cudaGraphExecDestroy(L.eig_exec);
   for (auto& a : ctx->allocs) cudaFreeAsync(a.first, ctx->stream);
   ctx->allocs.clear();
   ctx->bytes = 0;
@@ -655,38 +669,7 @@ hy_status vcycle_top(hy_ctx* ctx, const double* r, double* z) {
   return HY_OK;
 }
 
-// Record the work `body` issues on ctx->stream into a CUDA graph (captured on the private capture stream),
-// then launch it once on ctx->stream, where stream order places it after the work queued before. Kernel
-// counts recorded during the capture stand for the launch.
 constexpr int EIG_GRAPH_MAX_ITERS = 64;
-template <typename F>
-hy_status run_captured(hy_ctx* ctx, F&& body) {
-  if (!ctx->cap_stream) HY_CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
-  cudaStream_t saved = ctx->stream;
-  ctx->stream = ctx->cap_stream;
-  cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) {
-    ctx->stream = saved;
-    return fail(ctx, HY_ERR_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
-  }
-  const hy_status st = body();
-  cudaGraph_t g = nullptr;
-  e = cudaStreamEndCapture(ctx->cap_stream, &g);
-  ctx->stream = saved;
-  if (st != HY_OK || e != cudaSuccess) {
-    if (g) cudaGraphDestroy(g);
-    if (st != HY_OK) return st;
-    return fail(ctx, HY_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
-  }
-  cudaGraphExec_t ex = nullptr;
-  e = cudaGraphInstantiate(&ex, g, 0);
-  cudaGraphDestroy(g);
-  if (e != cudaSuccess) return fail(ctx, HY_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
-  e = cudaGraphLaunch(ex, ctx->stream);
-  cudaGraphExecDestroy(ex);  // destruction waits for nothing: the launched work completes on its own
-  if (e != cudaSuccess) return fail(ctx, HY_ERR_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
-  return HY_OK;
-}
 
 // Ritz extremes of D^{-1} A~ on level l from `iters` Jacobi-PCG iterations (Lanczos tridiagonal from
 // the CG coefficients), start vector from SplitMix64 with seed l, constrained entries zero (Sec. 7).
@@ -722,12 +705,71 @@ hy_status eig_estimate(hy_ctx* ctx, int l, int iters, double& lmin, double& lmax
     return check_launch(ctx, 9);
   };
   if (ctx->use_graphs && iters <= EIG_GRAPH_MAX_ITERS) {
-    // a short run (the smoother estimates) is captured whole and launched as one CUDA graph: once the
-    // device-side stop flag is set the remaining iterations change nothing
-    HY_TRY(run_captured(ctx, [&]() -> hy_status {
-      for (int it = 0; it < iters; ++it) HY_TRY(iteration(it));
-      return HY_OK;
-    }));
+    // A short run (the smoother estimates) is one CUDA graph: once the device-side stop flag is set the
+    // remaining iterations change nothing. The graph is kept per level and replayed at later
+    // linearisations as long as the arguments of its kernels are the same (the signature below: the
+    // action's kernel arguments, form and precision, the vectors, scalars, iteration count).
+    std::vector<unsigned char> sig;
+    auto add = [&sig](const void* v, size_t bytes) {
+      const unsigned char* b = static_cast<const unsigned char*>(v);
+      sig.insert(sig.end(), b, b + bytes);
+    };
+    const bool ff_top = std::is_same<T, double>::value && l == ctx->nlev - 1 && ctx->sp.fine_dtype == HY_FF && L.hasff;
+    if (ff_top) {
+      CellArgs<ff> ca = cell_args<ff>(ctx, L);
+      ca.cache = cache_of<ff>(L);
+      ca.ubar = ubar_of<ff>(L);
+      add(&ca, sizeof(ca));
+      add(&L.form[2], sizeof(int));
+      add(&L.var[2], sizeof(int));
+    } else {
+      CellArgs<T> ca = cell_args<T>(ctx, L);
+      ca.cache = cache_of<T>(L);
+      ca.ubar = ubar_of<T>(L);
+      add(&ca, sizeof(ca));
+      add(&L.form[prec_index<T>()], sizeof(int));
+      add(&L.var[prec_index<T>()], sizeof(int));
+    }
+    const void* ptrs[9] = {r, z, q, p, dinv, sc, hist, ctx->d_partials, ctx->d_err};
+    add(ptrs, sizeof(ptrs));
+    add(&iters, sizeof(iters));
+    add(&ctx->prefetch, sizeof(ctx->prefetch));
+    const int ptag = prec_index<T>() + (ff_top ? 8 : 0);
+    add(&ptag, sizeof(ptag));
+    if (!L.eig_exec || sig != L.eig_sig) {
+      if (L.eig_exec) cudaGraphExecDestroy(L.eig_exec);
+      L.eig_exec = nullptr;
+      if (!ctx->cap_stream) HY_CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+      cudaStream_t saved = ctx->stream;
+      const long long l0 = ctx->launches;
+      ctx->stream = ctx->cap_stream;
+      cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) {
+        ctx->stream = saved;
+        return fail(ctx, HY_ERR_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+      }
+      hy_status st = HY_OK;
+      for (int it = 0; it < iters && st == HY_OK; ++it) st = iteration(it);
+      cudaGraph_t g = nullptr;
+      e = cudaStreamEndCapture(ctx->cap_stream, &g);
+      ctx->stream = saved;
+      L.eig_nodes = ctx->launches - l0;
+      ctx->launches = l0;
+      if (st != HY_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        if (st != HY_OK) return st;
+        return fail(ctx, HY_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+      }
+      e = cudaGraphInstantiate(&L.eig_exec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        L.eig_exec = nullptr;
+        return fail(ctx, HY_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+      }
+      L.eig_sig.swap(sig);
+    }
+    HY_CK(cudaGraphLaunch(L.eig_exec, ctx->stream));
+    ctx->launches += L.eig_nodes;
   } else {
     for (int it = 0; it < iters; ++it) {
       HY_TRY(iteration(it));
@@ -857,19 +899,41 @@ hy_status coarse_direct_setup(hy_ctx* ctx) {
   ctx->coarse_deg = 0;
   ctx->coarse_spd = true;
   if (n == 0) return HY_OK;
-  HY_CK(cudaMemsetAsync(C.d_Ainv, 0, sizeof(double) * n * n, ctx->stream));
+  // Assembly and inversion go to the side stream, after the work queued so far on the context's stream
+  // (the carried-down coarse displacement): they need nothing else of the linearisation and overlap its
+  // state builds, diagonals and eigenvalue estimates. coarse_direct_finish joins them.
+  if (!ctx->side) {
+    HY_CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+    HY_CK(cudaEventCreateWithFlags(&ctx->ev_side_fork, cudaEventDisableTiming));
+    HY_CK(cudaEventCreateWithFlags(&ctx->ev_side_join, cudaEventDisableTiming));
+    HY_CK(cudaMallocHost((void**)&ctx->h_err_side, sizeof(unsigned)));
+  }
+  HY_CK(cudaEventRecord(ctx->ev_side_fork, ctx->stream));
+  HY_CK(cudaStreamWaitEvent(ctx->side, ctx->ev_side_fork, 0));
+  unsigned* err = ctx->d_err + 1;
+  HY_CK(cudaMemsetAsync(C.d_Ainv, 0, sizeof(double) * n * n, ctx->side));
+  HY_CK(cudaMemsetAsync(err, 0, sizeof(unsigned), ctx->side));
   CellArgs<double> a = cell_args<double>(ctx, C);
   a.u64 = C.d_u64;
-  launch_assemble_dense(ctx->dim, ctx->n, a, C.d_Ainv, n, C.d_cidx, ctx->stream);
+  a.err = err;
+  launch_assemble_dense(ctx->dim, ctx->n, a, C.d_Ainv, n, C.d_cidx, ctx->side);
   HY_TRY(check_launch(ctx, 1));
-  HY_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
   const bool ff_arith = ctx->sp.coarse_solver == 2;
-  C.d_Aresult = launch_gj_invert(C.d_Ainv, C.d_Awork, n, C.d_inv_piv, ctx->d_err, ff_arith, ctx->stream);
+  C.d_Aresult = launch_gj_invert(C.d_Ainv, C.d_Awork, n, C.d_inv_piv, err, ff_arith, ctx->side);
   HY_TRY(check_launch(ctx, (int)(3 * ((n + 31) / 32)) + (ff_arith ? 2 : 0)));
-  unsigned h = 0;
-  HY_CK(cudaMemcpyAsync(&h, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
-  HY_CK(cudaStreamSynchronize(ctx->stream));
-  HY_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
+  HY_CK(cudaMemcpyAsync(ctx->h_err_side, err, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->side));
+  HY_CK(cudaEventRecord(ctx->ev_side_join, ctx->side));
+  ctx->side_pending = true;
+  return HY_OK;
+}
+
+// Join the coarse setup of the side stream: the context's stream waits for it, and its error word decides.
+hy_status coarse_direct_finish(hy_ctx* ctx) {
+  if (!ctx->side_pending) return HY_OK;
+  ctx->side_pending = false;
+  HY_CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_side_join, 0));
+  HY_CK(cudaEventSynchronize(ctx->ev_side_join));
+  const unsigned h = *ctx->h_err_side;
   if (h & (ERRBIT_JNEG | ERRBIT_NAN)) return fail(ctx, HY_ERR_JNEG, "coarse level: J <= 0 at a Gauss point");
   ctx->coarse_spd = !(h & ERRBIT_NONSPD);
   return HY_OK;
@@ -1060,6 +1124,9 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
                         ctx->stream));
   for (int l = top; l >= 1; --l) HY_TRY(interpolate_down(ctx, l));
   pt.mark("carry down");
+  hy_status coarse_st = HY_OK;
+  if (ctx->sp.coarse_solver >= 1) coarse_st = coarse_direct_setup(ctx);  // runs on the side stream
+  if (coarse_st != HY_OK) return coarse_st;
   HY_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
   const unsigned long long one_bits = 0x7FF0000000000000ULL;  // +inf
   HY_CK(cudaMemcpyAsync(ctx->d_jmin, &one_bits, sizeof(one_bits), cudaMemcpyHostToDevice, ctx->stream));
@@ -1128,7 +1195,7 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
   }
   pt.mark("smoother eig");
   if (ctx->sp.coarse_solver >= 1) {
-    HY_TRY(coarse_direct_setup(ctx));
+    HY_TRY(coarse_direct_finish(ctx));
   } else {
     const long long nfree = ctx->coarse_nfree;
     int it = ctx->sp.coarse_eig_iters > 0 ? (int)std::min<long long>(nfree, ctx->sp.coarse_eig_iters) : (int)nfree;
@@ -1877,9 +1944,14 @@ void hy_destroy(hy_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
+  if (ctx->side) cudaStreamSynchronize(ctx->side);
   free_mesh(ctx);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
+  if (ctx->ev_side_fork) cudaEventDestroy(ctx->ev_side_fork);
+  if (ctx->ev_side_join) cudaEventDestroy(ctx->ev_side_join);
   if (ctx->h_pcg_scal) cudaFreeHost(ctx->h_pcg_scal);
+  if (ctx->h_err_side) cudaFreeHost(ctx->h_err_side);
   delete ctx;
 }
 
@@ -2061,14 +2133,14 @@ hy_status hy_mesh_setup(hy_ctx* ctx, int dim, int degree, int m, int n_levels, c
   HY_TRY(dalloc(ctx, &ctx->tmp32a, tmp_len));
   HY_TRY(dalloc(ctx, &ctx->tmp32b, tmp_len));
   HY_TRY(dalloc(ctx, &ctx->tmp32c, tmp_len));
-  HY_TRY(dalloc(ctx, &ctx->d_err, 1));
+  HY_TRY(dalloc(ctx, &ctx->d_err, 2));  // [0] the context's stream, [1] the side stream of the coarse setup
   HY_TRY(dalloc(ctx, &ctx->d_jmin, 1));
   HY_TRY(dalloc(ctx, &ctx->d_partials, DOT_BLOCKS));
   HY_TRY(dalloc(ctx, &ctx->d_scal, 4));
   HY_TRY(dalloc(ctx, &ctx->d_face, 18));
   HY_TRY(dalloc(ctx, &ctx->d_eig_scal, 8 + PCG_SCALARS));
   for (int i = 0; i < 12; ++i) HY_TRY(dalloc(ctx, &ctx->f64[i], ctx->lev[n_levels - 1].ndofs));
-  HY_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
+  HY_CK(cudaMemsetAsync(ctx->d_err, 0, 2 * sizeof(unsigned), ctx->stream));
   HY_CK(cudaStreamSynchronize(ctx->stream));
   return HY_OK;
 }
@@ -2494,7 +2566,7 @@ hy_status hy_footprint_general(int dim, int degree, int m, int n_levels, hy_vari
     tmp_len = std::max(tmp_len, inter);
   }
   total += 2 * al(tmp_len, 8) + 3 * al(tmp_len, 4);
-  total += al(1, 4) + al(1, 8) + al(DOT_BLOCKS, 8) + al(4, 8) + al(18, 8) + al(8 + PCG_SCALARS, 8);
+  total += al(2, 4) + al(1, 8) + al(DOT_BLOCKS, 8) + al(4, 8) + al(18, 8) + al(8 + PCG_SCALARS, 8);
   total += 12 * al(nd[n_levels - 1], 8);
   const int top = n_levels - 1;
   for (int l = 0; l < n_levels; ++l) {

@@ -192,6 +192,15 @@ typedef struct {
                                hy_set_displacement, else a hy_variant. The variants are implementations of
                                one operator (Sec. 5): a cheaper one speeds up the smoother without changing
                                the preconditioner beyond rounding. */
+  double setup_reuse;       /* [0 = off] reuse of the V-cycle's setup across linearisations: when the
+                               coarsest level's carried-down displacement differs from the one of the last
+                               full setup by at most setup_reuse (relative, Euclidean norm), hy_set_displacement
+                               keeps that setup's eigenvalue estimates (smoother ranges, Chebyshev coarse
+                               bounds) and exact coarse inverse; the level caches, diagonals and the V-cycle
+                               graph are rebuilt as always. The V-cycle stays a fixed SPD preconditioner of
+                               the current tangent, so the outer CG converges to the same tolerance; only its
+                               iteration count can change. Not in the paper, which sets up every
+                               linearisation. */
 } hy_solver_params;
 
 /* Replace the context's solver parameters (copied); they take effect at the next hy_set_displacement.
@@ -258,6 +267,7 @@ typedef struct {
   double solve_ms[256];       /* host wall time of each PCG solve (stream synchronised) */
   double setup_ms_total;      /* time spent linearising (caches, diagonals, eigenvalue estimates) */
   double total_ms;            /* whole call */
+  int setups_reused;          /* linearisations that kept the previous V-cycle setup (solver setup_reuse) */
 } hy_newton_report;
 
 /* Fill p with the defaults in brackets above (zero tractions and prescribed values). */

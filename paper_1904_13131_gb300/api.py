@@ -45,7 +45,7 @@ class SolverParams(ctypes.Structure):
     _fields_ = [("cheb_degree", ctypes.c_int), ("cheb_sweeps", ctypes.c_int), ("cheb_lo", ctypes.c_double),
                 ("cheb_hi", ctypes.c_double), ("eig_iters", ctypes.c_int), ("coarse_eig_iters", ctypes.c_int),
                 ("coarse_reduction", ctypes.c_double), ("coarse_solver", ctypes.c_int), ("kernel_form", ctypes.c_int),
-                ("fine_dtype", ctypes.c_int), ("level_variant", ctypes.c_int)]
+                ("fine_dtype", ctypes.c_int), ("level_variant", ctypes.c_int), ("setup_reuse", ctypes.c_double)]
 
 
 class NewtonParams(ctypes.Structure):
@@ -63,7 +63,7 @@ class NewtonReport(ctypes.Structure):
                 ("cg_iterations_total", ctypes.c_int), ("cg_iterations_max", ctypes.c_int),
                 ("final_residual", ctypes.c_double), ("backtracks", ctypes.c_int), ("n_solves", ctypes.c_int),
                 ("solve_cg_iterations", ctypes.c_int * 256), ("solve_ms", ctypes.c_double * 256),
-                ("setup_ms_total", ctypes.c_double), ("total_ms", ctypes.c_double)]
+                ("setup_ms_total", ctypes.c_double), ("total_ms", ctypes.c_double), ("setups_reused", ctypes.c_int)]
 
 
 class Request(ctypes.Structure):
@@ -415,7 +415,7 @@ class Context:
                   "final_residual": rep.final_residual, "backtracks": rep.backtracks,
                   "n_solves": rep.n_solves, "solve_cg_iterations": list(rep.solve_cg_iterations[: min(rep.n_solves, 256)]),
                   "solve_ms": list(rep.solve_ms[: min(rep.n_solves, 256)]), "setup_ms_total": rep.setup_ms_total,
-                  "total_ms": rep.total_ms}
+                  "total_ms": rep.total_ms, "setups_reused": rep.setups_reused}
         self._ck(st)
         return report
 
@@ -484,7 +484,7 @@ def _report_dict(rep, steps):
     return {"load_steps_done": rep.load_steps_done, "newton_iterations": list(rep.newton_iterations[:steps]),
             "cg_iterations_total": rep.cg_iterations_total, "cg_iterations_max": rep.cg_iterations_max,
             "final_residual": rep.final_residual, "n_solves": rep.n_solves, "total_ms": rep.total_ms,
-            "setup_ms_total": rep.setup_ms_total}
+            "setup_ms_total": rep.setup_ms_total, "setups_reused": rep.setups_reused}
 
 
 class Batch:

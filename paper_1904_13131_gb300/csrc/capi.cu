@@ -213,7 +213,7 @@ struct hy_ctx {
   Basis1D<double> b64{};
   Basis1D<float> b32{};
   Basis1D<ff> bff{};
-  hy_solver_params sp{4, 1, 0.6, 1.2, 30, 0, 1e-3, 0, -1, HY_F64, -1};
+  hy_solver_params sp{4, 1, 0.6, 1.2, 30, 0, 1e-3, 0, -1, HY_F64, -1, 0.0};
   int var = -1;
   int law = 0;  // volumetric function of the neo-Hooke law (hy_set_material_law)
   bool curved = false;  // a curved reference geometry is set (hy_set_geometry)
@@ -256,6 +256,12 @@ struct hy_ctx {
   cudaEvent_t ev_side_fork = nullptr, ev_side_join = nullptr;
   unsigned* h_err_side = nullptr;  // pinned: the side stream's error word, read after the join
   bool side_pending = false;
+  // reuse of the V-cycle setup (solver parameter setup_reuse): the coarsest level's displacement at the
+  // last full setup, and whether that setup is still valid for this mesh, material and parameters
+  double* d_usetup = nullptr;
+  double* d_udiff = nullptr;
+  bool setup_valid = false;
+  bool last_setup_reused = false;
   // replacement of the outer PCG inside hy_newton_solve (the solve server's batched solves), or null
   hy_linear_solve_hook solve_hook = nullptr;
   void* solve_user = nullptr;
@@ -346,6 +352,8 @@ void free_mesh(hy_ctx* ctx) {
   ctx->d_eig_scal = nullptr;
   ctx->d_eig_hist = nullptr;
   ctx->eig_hist_len = 0;
+  ctx->d_usetup = ctx->d_udiff = nullptr;
+  ctx->setup_valid = false;
   ctx->tmp64a = ctx->tmp64b = nullptr;
   ctx->tmp32a = ctx->tmp32b = ctx->tmp32c = nullptr;
   for (auto& p : ctx->f64) p = nullptr;
@@ -1124,8 +1132,22 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
                         ctx->stream));
   for (int l = top; l >= 1; --l) HY_TRY(interpolate_down(ctx, l));
   pt.mark("carry down");
+  // Setup reuse (setup_reuse > 0): keep the last full setup's eigenvalue estimates and coarse inverse while
+  // the coarsest level's displacement stays within the tolerance of the one they were computed for.
+  bool reuse = false;
+  if (ctx->sp.setup_reuse > 0.0 && ctx->setup_valid) {
+    Level& C = ctx->lev[0];
+    launch_sub<double>(C.d_u64, ctx->d_usetup, ctx->d_udiff, C.ndofs, ctx->stream);
+    HY_TRY(check_launch(ctx, 1));
+    double dd = 0.0, uu = 0.0;
+    HY_TRY(dot<double>(ctx, ctx->d_udiff, ctx->d_udiff, C.ndofs, &dd));
+    HY_TRY(dot<double>(ctx, C.d_u64, C.d_u64, C.ndofs, &uu));
+    reuse = std::sqrt(dd) <= ctx->sp.setup_reuse * std::sqrt(uu);
+  }
+  ctx->setup_valid = false;
+  ctx->last_setup_reused = reuse;
   hy_status coarse_st = HY_OK;
-  if (ctx->sp.coarse_solver >= 1) coarse_st = coarse_direct_setup(ctx);  // runs on the side stream
+  if (ctx->sp.coarse_solver >= 1 && !reuse) coarse_st = coarse_direct_setup(ctx);  // runs on the side stream
   if (coarse_st != HY_OK) return coarse_st;
   HY_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
   const unsigned long long one_bits = 0x7FF0000000000000ULL;  // +inf
@@ -1187,14 +1209,16 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
   }
   pt.mark("autotune");
   // eigenvalue estimates (level precision of the V-cycle)
-  for (int l = 1; l < ctx->nlev; ++l) {
+  for (int l = 1; l < ctx->nlev && !reuse; ++l) {
     double lmin, lmax;
     if (level_f32(ctx, l)) HY_TRY(eig_estimate<float>(ctx, l, ctx->sp.eig_iters, lmin, lmax));
     else HY_TRY(eig_estimate<double>(ctx, l, ctx->sp.eig_iters, lmin, lmax));
     ctx->lev[l].lmax = lmax;
   }
   pt.mark("smoother eig");
-  if (ctx->sp.coarse_solver >= 1) {
+  if (reuse) {
+    // the last full setup's coarse inverse or Chebyshev coarse bounds stay
+  } else if (ctx->sp.coarse_solver >= 1) {
     HY_TRY(coarse_direct_finish(ctx));
   } else {
     const long long nfree = ctx->coarse_nfree;
@@ -1207,7 +1231,7 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
   }
   // The Chebyshev coarse solver needs an SPD coarsest level; an indefinite one (a tangent about an
   // unstable state) is reported when the V-cycle is used, not here, so that applications still work.
-  if (ctx->sp.coarse_solver < 1) {
+  if (ctx->sp.coarse_solver < 1 && !reuse) {
     ctx->coarse_spd = ctx->coarse_lo > 0.0;
     ctx->coarse_deg = 0;
     if (ctx->coarse_spd) {
@@ -1220,6 +1244,11 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
     for (int l = 1; l < ctx->nlev; ++l) std::fprintf(stderr, "[hy] level %d lmax %.6e\n", l, ctx->lev[l].lmax);
     std::fprintf(stderr, "[hy] coarse lo %.6e hi %.6e degree %d\n", ctx->coarse_lo, ctx->coarse_hi, ctx->coarse_deg);
   }
+  if (!reuse) {  // this full setup is the reference of later reuse
+    HY_CK(cudaMemcpyAsync(ctx->d_usetup, ctx->lev[0].d_u64, sizeof(double) * ctx->lev[0].ndofs,
+                          cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  ctx->setup_valid = true;
   ctx->state_ok = true;
   return HY_OK;
 }
@@ -2139,6 +2168,8 @@ hy_status hy_mesh_setup(hy_ctx* ctx, int dim, int degree, int m, int n_levels, c
   HY_TRY(dalloc(ctx, &ctx->d_scal, 4));
   HY_TRY(dalloc(ctx, &ctx->d_face, 18));
   HY_TRY(dalloc(ctx, &ctx->d_eig_scal, 8 + PCG_SCALARS));
+  HY_TRY(dalloc(ctx, &ctx->d_usetup, ctx->lev[0].ndofs));
+  HY_TRY(dalloc(ctx, &ctx->d_udiff, ctx->lev[0].ndofs));
   for (int i = 0; i < 12; ++i) HY_TRY(dalloc(ctx, &ctx->f64[i], ctx->lev[n_levels - 1].ndofs));
   HY_CK(cudaMemsetAsync(ctx->d_err, 0, 2 * sizeof(unsigned), ctx->stream));
   HY_CK(cudaStreamSynchronize(ctx->stream));
@@ -2178,6 +2209,7 @@ hy_status hy_set_material(hy_ctx* ctx, int level, const uint8_t* cell_mat, const
   }
   L.mat_set = true;
   ctx->state_ok = false;
+  ctx->setup_valid = false;
   return HY_OK;
 }
 
@@ -2249,10 +2281,11 @@ hy_status hy_set_solver_params(hy_ctx* ctx, const hy_solver_params* p) {
       p->kernel_form < -1 || p->kernel_form > 2 || (p->fine_dtype != HY_F64 && p->fine_dtype != HY_FF) ||
       p->level_variant < -1 || p->level_variant > 4 ||
       p->eig_iters < 1 || p->coarse_eig_iters < 0 || !(p->coarse_reduction > 0 && p->coarse_reduction < 1) ||
-      p->coarse_solver < 0 || p->coarse_solver > 2)
+      p->coarse_solver < 0 || p->coarse_solver > 2 || !(p->setup_reuse >= 0.0))
     return fail(ctx, HY_ERR_ARG, "solver parameters out of range");
   ctx->sp = *p;
   ctx->state_ok = false;
+  ctx->setup_valid = false;
   drop_graph(ctx);
   return HY_OK;
 }
@@ -2306,6 +2339,7 @@ hy_status hy_set_geometry(hy_ctx* ctx, const double* X) {
   if (ctx->nlev == 0) return fail(ctx, HY_ERR_STATE, "mesh not set up");
   HY_CK(cudaSetDevice(ctx->device));
   ctx->state_ok = false;
+  ctx->setup_valid = false;
   drop_graph(ctx);
   if (!X) {
     ctx->curved = false;
@@ -2335,6 +2369,7 @@ hy_status hy_set_material_law(hy_ctx* ctx, int law) {
   if (law != HY_LAW_LOG2 && law != HY_LAW_J2) return fail(ctx, HY_ERR_ARG, "unknown material law");
   ctx->law = law;
   ctx->state_ok = false;
+  ctx->setup_valid = false;
   drop_graph(ctx);
   return HY_OK;
 }
@@ -2456,6 +2491,7 @@ hy_status hy_newton_solve(hy_ctx* ctx, const hy_newton_params* p, double* u, hy_
       if ((st = set_displacement(ctx, u, (int)p->variant, p->level_dtype == HY_F32)) != HY_OK) break;
       HY_CK(cudaStreamSynchronize(ctx->stream));
       rl.setup_ms_total += ms_since(t_setup);
+      if (ctx->last_setup_reused) rl.setups_reused++;
       // rhs = -R - Z A du0 (lifting of the prescribed increment into the first solve)
       HY_CK(cudaMemcpyAsync(rhs, R, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
       if (lift2 > 0.0) {
@@ -2567,6 +2603,7 @@ hy_status hy_footprint_general(int dim, int degree, int m, int n_levels, hy_vari
   }
   total += 2 * al(tmp_len, 8) + 3 * al(tmp_len, 4);
   total += al(2, 4) + al(1, 8) + al(DOT_BLOCKS, 8) + al(4, 8) + al(18, 8) + al(8 + PCG_SCALARS, 8);
+  total += 2 * al(nd[0], 8);  // coarsest-level displacement of the last full setup, and a difference
   total += 12 * al(nd[n_levels - 1], 8);
   const int top = n_levels - 1;
   for (int l = 0; l < n_levels; ++l) {

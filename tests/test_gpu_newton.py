@@ -179,3 +179,24 @@ def test_newton_reports_jneg_after_five_halvings(torch, dim):
         assert float(u.abs().max()) == 0.0
         rep = ctx.newton_solve(u, Context.newton_params(load_steps=1, face_traction=traction_top(dim, 7.5)))
         assert rep["load_steps_done"] == 1 and rep["backtracks"] == 1
+
+
+@pytest.mark.parametrize("coarse", [0, 1])
+def test_setup_reuse_keeps_the_solution(torch, config1_reference, coarse):
+    """Solver parameter setup_reuse: linearisations whose coarsest-level displacement moved little since the
+    last full setup keep its eigenvalue estimates and coarse solve. The preconditioner changes, the Newton
+    solution does not (1e-8 against the oracle), and some setups were reused."""
+    pr, u_ref, rep_ref = config1_reference
+    from paper_1904_13131_gb300.api import Context
+    with context(pr) as ctx:
+        ctx.set_solver_params(coarse_solver=coarse)
+        u0 = torch.zeros(ctx.num_dofs(), dtype=torch.float64, device="cuda")
+        rep0 = ctx.newton_solve(u0, Context.newton_params(level_dtype=1, face_values=face_values(2, -0.1)))
+        ctx.set_solver_params(coarse_solver=coarse, setup_reuse=0.05)
+        u = torch.zeros(ctx.num_dofs(), dtype=torch.float64, device="cuda")
+        rep = ctx.newton_solve(u, Context.newton_params(level_dtype=1, face_values=face_values(2, -0.1)))
+    assert rep0["setups_reused"] == 0 and rep["setups_reused"] > 0
+    assert rep["load_steps_done"] == 5
+    assert rel(u.cpu().numpy(), u_ref) < 1e-8
+    assert rep["newton_iterations"] == rep0["newton_iterations"]
+    assert rep["cg_iterations_max"] <= rep0["cg_iterations_max"] + 5

@@ -940,6 +940,7 @@ def main():
         ctxs[v].set_solver_params(fine_dtype=api.FF if (restore or not general_ff) else api.F64)
         ctxs[v].set_displacement(u, v, level_dtype=1)
 
+    steady = f32_steady_state(torch, api, inputs, dev, hbm)
     second_law, curved = {}, {}
     for v in ALL_VARIANTS:
         relinearise(v, law=api.LAW_J2)

@@ -736,8 +736,7 @@ __device__ __forceinline__ void apply_point_body(const CellArgs<T>& a, const int
   }
   // quadrature-point work
   T P[DIM][DIM];
-  qp_flux<DIM, VAR>(G, Gu, cs, BS, cache_slot<T>(DIM, N, cl, pt.p), active, active ? a.mat[cell] : 0, s.mu, s.lam,
-                    s.Wh[pt.p], P,
+  qp_flux<DIM, VAR>(G, Gu, cs, BS, threadIdx.x, active, active ? a.mat[cell] : 0, s.mu, s.lam, s.Wh[pt.p], P,
                     a.mt.law);
 #pragma unroll
   for (int c = 0; c < DIM; ++c)
@@ -826,15 +825,10 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
     tlam[i] = a.mt.lam[i];
   }
   const T xh = PHYS ? T(a.g.inv_h) : T(1);  // x derivatives: D from the arguments, scaled once
-  // Thread t plays line l = (l1, l2) of cell cl with t = l * CB + cl: the threads of a warp take the same
-  // line of consecutive cells, whose x-runs of nodes are adjacent in the lattice, so that the gather and
-  // the scatter-add of a warp touch a few contiguous segments instead of one line of the lattice per
-  // thread (measured: 26 sectors per global request with the cell-major mapping). Line (j1, j2) of this
-  // cell is thread (j1 + N j2) CB + cl.
-  const int cl = t % CB, l = t / CB;
+  const int cl = t / NLC, l = t % NLC;
   const int l1 = l % N, l2 = DIM == 3 ? l / N : 0;
-  const int ly = N * l2 * CB + cl;  // line of this cell with y index 0 and this thread's z index (step CB in y)
-  const int lz = l1 * CB + cl;      // line of this cell with this thread's y index and z index 0 (step N CB in z)
+  const int ly = cl * NLC + N * l2;  // line of this cell with y index 0 and this thread's z index
+  const int lz = cl * NLC + l1;      // line of this cell with this thread's y index and z index 0
   auto B = [](int c, int q, int i) { return (c * N + q) * TL + i; };
   auto FX = [](int c, int J, int q, int i) { return ((c * (DIM - 1) + J) * N + q) * TL + i; };
   int it = 0;
@@ -893,8 +887,8 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
           T sx = T(0), su = T(0);
 #pragma unroll
           for (int j = 0; j < N; ++j) {
-            sx = fma(tS[l1][j], buf0[B(c, q, ly + j * CB)], sx);
-            if (NEED_U) su = fma(tS[l1][j], ubuf0[NEED_U ? B(c, q, ly + j * CB) : 0], su);
+            sx = fma(tS[l1][j], buf0[B(c, q, ly + j)], sx);
+            if (NEED_U) su = fma(tS[l1][j], ubuf0[NEED_U ? B(c, q, ly + j) : 0], su);
           }
           buf1[B(c, q, t)] = sx;
           if (NEED_U) ubuf1[NEED_U ? B(c, q, t) : 0] = su;
@@ -908,8 +902,8 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
           T sx = T(0), su = T(0);
 #pragma unroll
           for (int j = 0; j < N; ++j) {
-            sx = fma(tS[l2][j], buf1[B(c, q, lz + N * CB * j)], sx);
-            if (NEED_U) su = fma(tS[l2][j], ubuf1[NEED_U ? B(c, q, lz + N * CB * j) : 0], su);
+            sx = fma(tS[l2][j], buf1[B(c, q, lz + N * j)], sx);
+            if (NEED_U) su = fma(tS[l2][j], ubuf1[NEED_U ? B(c, q, lz + N * j) : 0], su);
           }
           V[q][c] = sx;
           VU[q][c] = su;
@@ -922,8 +916,8 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
           T sx = T(0), su = T(0);
 #pragma unroll
           for (int j = 0; j < N; ++j) {
-            sx = fma(tS[l1][j], buf0[B(c, q, ly + j * CB)], sx);
-            if (NEED_U) su = fma(tS[l1][j], ubuf0[NEED_U ? B(c, q, ly + j * CB) : 0], su);
+            sx = fma(tS[l1][j], buf0[B(c, q, ly + j)], sx);
+            if (NEED_U) su = fma(tS[l1][j], ubuf0[NEED_U ? B(c, q, ly + j) : 0], su);
           }
           V[q][c] = sx;
           VU[q][c] = su;
@@ -971,8 +965,8 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
         T g1 = T(0), u1 = T(0);
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-          g1 = fma(Dd[l1][j], vb[B(c, q, ly + j * CB)], g1);
-          if (NEED_U) u1 = fma(Dd[l1][j], vub[NEED_U ? B(c, q, ly + j * CB) : 0], u1);
+          g1 = fma(Dd[l1][j], vb[B(c, q, ly + j)], g1);
+          if (NEED_U) u1 = fma(Dd[l1][j], vub[NEED_U ? B(c, q, ly + j) : 0], u1);
         }
         G[c][1] = g1;
         Gu[c][1] = u1;
@@ -980,15 +974,15 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
           T g2 = T(0), u2 = T(0);
 #pragma unroll
           for (int j = 0; j < N; ++j) {
-            g2 = fma(Dd[l2][j], vb[B(c, q, lz + N * CB * j)], g2);
-            if (NEED_U) u2 = fma(Dd[l2][j], vub[NEED_U ? B(c, q, lz + N * CB * j) : 0], u2);
+            g2 = fma(Dd[l2][j], vb[B(c, q, lz + N * j)], g2);
+            if (NEED_U) u2 = fma(Dd[l2][j], vub[NEED_U ? B(c, q, lz + N * j) : 0], u2);
           }
           G[c][DIM - 1] = g2;
           Gu[c][DIM - 1] = u2;
         }
       }
       T P[DIM][DIM];
-      qp_flux<DIM, VAR>(G, Gu, cq, BS, cache_slot<T>(DIM, N, cl, p), active, id, tmu, tlam, tWh[p], P, a.mt.law);
+      qp_flux<DIM, VAR>(G, Gu, cq, BS, cl * NPT + p, active, id, tmu, tlam, tWh[p], P, a.mt.law);
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
         Px[q][c] = P[c][0];
@@ -1012,10 +1006,10 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
 #pragma unroll
         for (int j = 0; j < N; ++j) s = fma(a.b.D[j][q], Px[j][c], s);
 #pragma unroll
-        for (int j = 0; j < N; ++j) s = fma(tD[j][l1], flux[FX(c, 0, q, ly + j * CB)], s);
+        for (int j = 0; j < N; ++j) s = fma(tD[j][l1], flux[FX(c, 0, q, ly + j)], s);
         if (DIM == 3) {
 #pragma unroll
-          for (int j = 0; j < N; ++j) s = fma(tD[j][l2], flux[FX(c, DIM - 2, q, lz + N * CB * j)], s);
+          for (int j = 0; j < N; ++j) s = fma(tD[j][l2], flux[FX(c, DIM - 2, q, lz + N * j)], s);
         }
         Wq[q][c] = s;
       }
@@ -1033,7 +1027,7 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
         for (int c = 0; c < DIM; ++c) {  // z: (q1 = l1, a2 = l2)
           T sz = T(0);
 #pragma unroll
-          for (int j = 0; j < N; ++j) sz = fma(tS[j][l2], buf1[B(c, q, lz + N * CB * j)], sz);
+          for (int j = 0; j < N; ++j) sz = fma(tS[j][l2], buf1[B(c, q, lz + N * j)], sz);
           buf0[B(c, q, t)] = sz;
         }
       __syncthreads();
@@ -1043,7 +1037,7 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
         for (int c = 0; c < DIM; ++c) {  // y: (a1 = l1, a2 = l2)
           T sy = T(0);
 #pragma unroll
-          for (int j = 0; j < N; ++j) sy = fma(tS[j][l1], buf0[B(c, q, ly + j * CB)], sy);
+          for (int j = 0; j < N; ++j) sy = fma(tS[j][l1], buf0[B(c, q, ly + j)], sy);
           Yb[q][c] = sy;
         }
     } else {
@@ -1058,7 +1052,7 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
         for (int c = 0; c < DIM; ++c) {
           T sy = T(0);
 #pragma unroll
-          for (int j = 0; j < N; ++j) sy = fma(tS[j][l1], buf0[B(c, q, ly + j * CB)], sy);
+          for (int j = 0; j < N; ++j) sy = fma(tS[j][l1], buf0[B(c, q, ly + j)], sy);
           Yb[q][c] = sy;
         }
     }
@@ -1286,7 +1280,7 @@ qp_state_kernel(const CellArgs<double> a, T* __restrict__ out) {
   constexpr int NVO = cache_values(VAR, DIM);
   constexpr int CBL = layout_cells<T>(DIM, N);
   constexpr int BS = layout_row<T>(DIM, N);
-  const long long qg = (long long)(cell / CBL) * NVO * BS + cache_slot<T>(DIM, N, cell % CBL, pt.p);
+  const long long qg = (long long)(cell / CBL) * NVO * BS + (cell % CBL) * NPT + pt.p;
   constexpr long long st = BS;
   if (VAR == VAR_T4 || VAR == VAR_T2) {
 #pragma unroll

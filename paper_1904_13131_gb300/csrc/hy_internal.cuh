@@ -109,15 +109,6 @@ template <typename T>
 __host__ __device__ constexpr int layout_row(int dim, int n) {
   return (layout_cells<T>(dim, n) * ipow(n, dim) + 3) / 4 * 4;
 }
-// Entry of (local cell, Gauss point q) within a value row of a block's chunk. FP64 and double-float, read
-// by one thread per (cell, point) in cell-major thread order: cell-major. FP32, read mostly by the line
-// form, whose warps take the same line of consecutive cells: point-major, so that those reads fall in
-// consecutive shared-memory banks for every degree (cell-major rows would put them NPT apart: 8- to
-// 32-way bank conflicts for the even NPT of degrees 1 and 3).
-template <typename T>
-__host__ __device__ constexpr int cache_slot(int dim, int n, int cell_local, int q) {
-  return sizeof(T) == 4 ? q * layout_cells<T>(dim, n) + cell_local : cell_local * ipow(n, dim) + q;
-}
 
 // Kernel forms of the tangent action: thread per (cell, Gauss point); thread per x-line of a cell; the line
 // form as a persistent grid whose blocks copy their next cache chunk in while they finish the current one

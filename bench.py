@@ -809,6 +809,9 @@ def main():
     ap.add_argument("--batch-only", action="store_true")
     ap.add_argument("--solve-only", action="store_true")
     ap.add_argument("--vcycle", action="store_true", help="profile mode: V-cycles of the 32^3 Q2 hierarchy")
+    ap.add_argument("--profile-all", action="store_true",
+                    help="profile mode: one application of every variant in FP64, then FP32, tuned forms, inside "
+                         "the NVTX range 'measure' (ncu --nvtx --nvtx-include measure/)")
     ap.add_argument("--configs", action="store_true", help="the degree sweep at 6-51M dofs and the 64^3 mixed study")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -846,6 +849,25 @@ def main():
                 c.apply_tangent(xin, y, dtype=code)
             torch.cuda.synchronize()
         print(json.dumps({"only": args.only, "reps": args.reps}))
+        return
+    if args.profile_all:
+        # profile mode: the workload's contexts (caches of every precision, tuned kernel forms), then one
+        # application per (precision, variant) inside an NVTX range that ncu can select
+        _, _, x, ctxs = setup_contexts(torch, api, inputs, dev)
+        x32 = x.float()
+        y64, y32 = torch.empty_like(x), torch.empty_like(x32)
+        torch.cuda.synchronize()
+        forms = {}
+        torch.cuda.nvtx.range_push("measure")
+        for dt, xin, y in ((0, x, y64), (1, x32, y32)):
+            for v in ALL_VARIANTS:
+                ctxs[v].apply_tangent(xin, y, dtype=dt)
+                forms[f"{v}:{'f64' if dt == 0 else 'f32'}"] = FORMS[ctxs[v].kernel_form(-1, dt)]
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        for c in ctxs.values():
+            c.close()
+        print(json.dumps({"profile_all": forms}))
         return
     if args.vcycle:
         # profile mode: V-cycles of the 32^3 Q2 hierarchy (4 levels) in the fastest mode; the first call

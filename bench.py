@@ -341,10 +341,14 @@ def newton_summary(rep):
     return {"solve_p50_ms": float(np.percentile(lat, 50)), "solve_p99_ms": float(np.percentile(lat, 99)),
             "solves": rep["n_solves"], "cg_iterations_median": int(np.median(rep["solve_cg_iterations"])),
             "cg_iterations_max": rep["cg_iterations_max"], "newton_iterations": rep["newton_iterations"],
-            "newton_total_ms": rep["total_ms"], "setup_ms_total": rep["setup_ms_total"]}
+            "newton_total_ms": rep["total_ms"], "setup_ms_total": rep["setup_ms_total"],
+            "setups_reused": rep["setups_reused"]}
 
 
-def config_study(torch, api, inputs, dev):
+DEFAULT_SWEEP = [(1, 128, 6), (1, 256, 7), (2, 64, 5), (2, 128, 6), (3, 48, 5), (3, 64, 5), (4, 32, 4), (4, 64, 5)]
+
+
+def config_study(torch, api, inputs, dev, sweep=None, paper_max_dofs=60_000_000, mixed_study=True):
     """The large workloads: (a) the 3D degree sweep Q1-Q4 at 6.4M-51M dofs, full Newton solve under 10%
     compression in 5 load steps, GMG down to a 2^3-4^3 coarse level, CG rtol 1e-8, in the paper's mode (FP64
     V-cycle, Chebyshev coarse solve) and in the fastest mode (FP32 V-cycle with T2 level operators, exact
@@ -352,27 +356,27 @@ def config_study(torch, api, inputs, dev):
     degrees 1-2); (b) mixed precision on the 64^3 Q2 inclusion cube, load step by load step: displacement
     difference between the FP64 and the mixed-precision Newton states, and the CG iterations of both."""
     out = {}
-    sweep = [(1, 128, 6), (2, 64, 5), (3, 48, 5), (4, 32, 4), (2, 128, 6)]
-    for k, m, L in sweep:
+    for k, m, L in (sweep or DEFAULT_SWEEP):
         pr = inputs.problem(3, k, m, n_levels=L, top=inputs.normal_top_mask(3))
         n = inputs.n_dofs(3, k, m)
         fv = [[0.0] * 3 for _ in range(6)]
         fv[5][2] = -0.1
         coarse_exact = inputs.n_dofs(3, k, m >> (L - 1)) <= 6000 and k <= 3
-        modes = [("fastest", 1, 2 if coarse_exact else 0, api.FF if k <= 2 else api.F64, api.VARIANTS["T2"])]
-        if n < 20_000_000:
-            modes.insert(0, ("paper_fp64", 0, 0, api.F64, -1))
+        modes = [("fastest", 1, 2 if coarse_exact else 0, api.FF if k <= 2 else api.F64, api.VARIANTS["T2"], 0.05)]
+        if n <= paper_max_dofs:
+            modes.insert(0, ("paper_fp64", 0, 0, api.F64, -1, 0.0))
         row = {"dofs": n, "levels": L, "coarse_m": m >> (L - 1)}
         sols = {}
         with api.Context(dev.index) as c:
             c.setup_problem(pr)
-            for name, ldt, coarse, fine, lvar in modes:
-                c.set_solver_params(coarse_solver=coarse, fine_dtype=fine, level_variant=lvar)
+            for name, ldt, coarse, fine, lvar, reuse in modes:
+                c.set_solver_params(coarse_solver=coarse, fine_dtype=fine, level_variant=lvar, setup_reuse=reuse)
                 u = torch.zeros(n, dtype=torch.float64, device=dev)
                 rep = c.newton_solve(u, api.Context.newton_params(level_dtype=ldt, face_values=fv))
                 row[name] = newton_summary(rep)
                 row[name]["coarse_solver"] = ["chebyshev", "exact_fp64", "exact_ff"][coarse]
                 row[name]["fine_dtype"] = "ff" if fine == api.FF else "f64"
+                row[name]["setup_reuse"] = reuse
                 row[name]["solves_per_s"] = 1e3 / row[name]["solve_p50_ms"]
                 sols[name] = u
         if len(sols) == 2:
@@ -381,6 +385,8 @@ def config_study(torch, api, inputs, dev):
         del sols
         out[f"Q{k}_{m}^3"] = row
         print(json.dumps({"config_progress": f"Q{k}_{m}^3"}), file=sys.stderr, flush=True)
+    if not mixed_study:
+        return out
     # (b) mixed precision per load step on 64^3 Q2 (5 levels, FP64 Chebyshev coarse solve in both)
     k, m, L, steps = 2, 64, 5, 5
     pr = inputs.problem(3, k, m, n_levels=L, top=inputs.normal_top_mask(3))
@@ -813,6 +819,8 @@ def main():
                     help="profile mode: one application of every variant in FP64, then FP32, tuned forms, inside "
                          "the NVTX range 'measure' (ncu --nvtx --nvtx-include measure/)")
     ap.add_argument("--configs", action="store_true", help="the degree sweep at 6-51M dofs and the 64^3 mixed study")
+    ap.add_argument("--sweep", default=None,
+                    help="--configs: meshes as degree:cells:levels,... (default: all eight), no mixed study")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -895,7 +903,9 @@ def main():
                               "forms_f32": [c.kernel_form(level, 1) for level in range(4)]}))
         return
     if args.configs:
-        print(json.dumps({"configs": config_study(torch, api, inputs, dev)}), flush=True)
+        sweep = [tuple(int(v) for v in item.split(":")) for item in args.sweep.split(",")] if args.sweep else None
+        print(json.dumps({"configs": config_study(torch, api, inputs, dev, sweep=sweep, mixed_study=sweep is None)}),
+              flush=True)
         return
     if args.solve_only:
         print(json.dumps({"solve": solve_latency(torch, api, inputs, dev)}), flush=True)

@@ -352,8 +352,8 @@ def config_study(torch, api, inputs, dev, sweep=None, paper_max_dofs=60_000_000,
     """The large workloads: (a) the 3D degree sweep Q1-Q4 at 6.4M-51M dofs, full Newton solve under 10%
     compression in 5 load steps, GMG down to a 2^3-4^3 coarse level, CG rtol 1e-8, in the paper's mode (FP64
     V-cycle, Chebyshev coarse solve) and in the fastest mode (FP32 V-cycle with T2 level operators, exact
-    coarse inverse where the coarsest level has at most 6000 dofs, double-float finest-level action for
-    degrees 1-2); (b) mixed precision on the 64^3 Q2 inclusion cube, load step by load step: displacement
+    coarse inverse where the coarsest level has at most 6000 dofs, double-float finest-level action, setup
+    reuse at 5 %); (b) mixed precision on the 64^3 Q2 inclusion cube, load step by load step: displacement
     difference between the FP64 and the mixed-precision Newton states, and the CG iterations of both."""
     out = {}
     for k, m, L in (sweep or DEFAULT_SWEEP):
@@ -362,7 +362,7 @@ def config_study(torch, api, inputs, dev, sweep=None, paper_max_dofs=60_000_000,
         fv = [[0.0] * 3 for _ in range(6)]
         fv[5][2] = -0.1
         coarse_exact = inputs.n_dofs(3, k, m >> (L - 1)) <= 6000 and k <= 3
-        modes = [("fastest", 1, 2 if coarse_exact else 0, api.FF if k <= 2 else api.F64, api.VARIANTS["T2"], 0.05)]
+        modes = [("fastest", 1, 2 if coarse_exact else 0, api.FF, api.VARIANTS["T2"], 0.05)]
         if n <= paper_max_dofs:
             modes.insert(0, ("paper_fp64", 0, 0, api.F64, -1, 0.0))
         row = {"dofs": n, "levels": L, "coarse_m": m >> (L - 1)}
@@ -435,8 +435,8 @@ def serve_bench(api, inputs, dev, n_req, seed=0, max_active=8, budget_gb=160, se
         return api.Context.newton_params(face_values=fv, level_dtype=ldt)
 
     def solver(q, coarse, ff):
-        # ff: double-float coarse inverse, and double-float finest-level action where built (degrees 1-2)
-        fine = api.FF if ff and q["k"] <= 2 else api.F64
+        # ff: double-float coarse inverse and double-float finest-level action
+        fine = api.FF if ff else api.F64
         return api.SolverParams(4, 1, 0.6, 1.2, 30, 0, 1e-3, 2 if (ff and coarse) else coarse, -1, fine,
                                api.VARIANTS["T2"] if ff else -1)
 

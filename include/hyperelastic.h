@@ -184,9 +184,10 @@ typedef struct {
                                and it is rewritten, as a JSON array, with every new decision) */
   hy_dtype fine_dtype;      /* [HY_F64] tangent action of the finest level inside the solver (outer CG, and the
                                finest level of an FP64 V-cycle): HY_F64, or HY_FF to build a double-float
-                               cache of the finest level at hy_set_displacement and use it there (degrees
-                               1-2; HY_ERR_UNSUPPORTED from hy_set_displacement otherwise); HY_FF also sums
-                               the level diagonals' (node, Gauss point) pairs in double-float */
+                               cache of the finest level at hy_set_displacement and use it there (every
+                               degree; with curved cells or the second law only for T4/T2: the general
+                               builds of FC/SC/NC have no double-float action); HY_FF also sums the level
+                               diagonals' (node, Gauss point) pairs in double-float */
   int level_variant;        /* [-1] tangent variant of the V-cycle's level operators (every level below the
                                finest, and the finest level's FP32 cache): -1 = the variant given to
                                hy_set_displacement, else a hy_variant. The variants are implementations of

@@ -1101,8 +1101,6 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
   for (int l = 0; l < ctx->nlev; ++l)
     if (!ctx->lev[l].mat_set) return fail(ctx, HY_ERR_STATE, "material not set on level " + std::to_string(l));
   if (var < 0 || var > 4) return fail(ctx, HY_ERR_ARG, "variant out of range");
-  if (ctx->sp.fine_dtype == HY_FF && ctx->n > 3)
-    return fail(ctx, HY_ERR_UNSUPPORTED, "the double-float action is built for degrees 1-2");
   // Curved cells or the second law: FC, SC and NC run their general builds (the reference map per Gauss
   // point in the cache, the volumetric function chosen at run time); T4 and T2 fold both into their state.
   const bool general = ctx->curved || ctx->law != HY_LAW_LOG2;

@@ -3,6 +3,6 @@
 #define INST_DIM 2
 #define INST_T ff
 #define INST_VAR VAR_NC
-#define INST_NAME apply_fn_ff_2d_v4
-#define INST_LIST_NAME apply_list_fn_ff_2d_v4
+#define INST_NAME apply_fn_ff_2d_v4_lo
+#define INST_LIST_NAME apply_list_fn_ff_2d_v4_lo
 #include "inst_apply.inc"

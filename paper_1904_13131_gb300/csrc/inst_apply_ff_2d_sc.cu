@@ -3,6 +3,6 @@
 #define INST_DIM 2
 #define INST_T ff
 #define INST_VAR VAR_SC
-#define INST_NAME apply_fn_ff_2d_v3
-#define INST_LIST_NAME apply_list_fn_ff_2d_v3
+#define INST_NAME apply_fn_ff_2d_v3_lo
+#define INST_LIST_NAME apply_list_fn_ff_2d_v3_lo
 #include "inst_apply.inc"

@@ -1,0 +1,9 @@
+// Tangent-action kernels, double-float (FP64 vectors, FP32-pipe arithmetic), dim 3, degrees 3-4, variant
+// FC, one problem or a work list (one translation unit per variant and degree pair).
+#define INST_DIM 3
+#define INST_T ff
+#define INST_VAR VAR_FC
+#define INST_N0 4
+#define INST_NAME apply_fn_ff_3d_v2_hi
+#define INST_LIST_NAME apply_list_fn_ff_3d_v2_hi
+#include "inst_apply.inc"

@@ -3,6 +3,6 @@
 #define INST_DIM 3
 #define INST_T ff
 #define INST_VAR VAR_T4
-#define INST_NAME apply_fn_ff_3d_v0
-#define INST_LIST_NAME apply_list_fn_ff_3d_v0
+#define INST_NAME apply_fn_ff_3d_v0_lo
+#define INST_LIST_NAME apply_list_fn_ff_3d_v0_lo
 #include "inst_apply.inc"

@@ -47,18 +47,25 @@ HY_APPLY_TABLES(double, f64, 2d)
 HY_APPLY_TABLES(double, f64, 3d)
 HY_APPLY_TABLES(float, f32, 2d)
 HY_APPLY_TABLES(float, f32, 3d)
-// double-float: degrees 1-2 (n = 2, 3), one translation unit per (dim, variant)
+// double-float: one translation unit per (dim, variant) for degrees 1-2 (_lo) and per (dim, variant) for
+// degrees 3-4 (_hi)
+#define HY_FF_VAR(D, V)                                                                            \
+  ApplyFn<ff> apply_fn_ff_##D##_v##V##_lo(int n);                                                  \
+  ApplyFn<ff> apply_fn_ff_##D##_v##V##_hi(int n);                                                  \
+  ApplyListFn<ff> apply_list_fn_ff_##D##_v##V##_lo(int n);                                         \
+  ApplyListFn<ff> apply_list_fn_ff_##D##_v##V##_hi(int n);                                         \
+  inline ApplyFn<ff> apply_fn_ff_##D##_v##V(int n) {                                               \
+    return n <= 3 ? apply_fn_ff_##D##_v##V##_lo(n) : apply_fn_ff_##D##_v##V##_hi(n);                \
+  }                                                                                                \
+  inline ApplyListFn<ff> apply_list_fn_ff_##D##_v##V(int n) {                                      \
+    return n <= 3 ? apply_list_fn_ff_##D##_v##V##_lo(n) : apply_list_fn_ff_##D##_v##V##_hi(n);      \
+  }
 #define HY_FF_TABLES(D)                                                                            \
-  ApplyFn<ff> apply_fn_ff_##D##_v0(int n);                                                         \
-  ApplyFn<ff> apply_fn_ff_##D##_v1(int n);                                                         \
-  ApplyFn<ff> apply_fn_ff_##D##_v2(int n);                                                         \
-  ApplyFn<ff> apply_fn_ff_##D##_v3(int n);                                                         \
-  ApplyFn<ff> apply_fn_ff_##D##_v4(int n);                                                         \
-  ApplyListFn<ff> apply_list_fn_ff_##D##_v0(int n);                                                \
-  ApplyListFn<ff> apply_list_fn_ff_##D##_v1(int n);                                                \
-  ApplyListFn<ff> apply_list_fn_ff_##D##_v2(int n);                                                \
-  ApplyListFn<ff> apply_list_fn_ff_##D##_v3(int n);                                                \
-  ApplyListFn<ff> apply_list_fn_ff_##D##_v4(int n);                                                \
+  HY_FF_VAR(D, 0)                                                                                  \
+  HY_FF_VAR(D, 1)                                                                                  \
+  HY_FF_VAR(D, 2)                                                                                  \
+  HY_FF_VAR(D, 3)                                                                                  \
+  HY_FF_VAR(D, 4)                                                                                  \
   inline ApplyFn<ff> apply_fn_ff_##D(int n, int var) {                                             \
     switch (var) {                                                                                 \
       case 0: return apply_fn_ff_##D##_v0(n);                                                      \
@@ -82,6 +89,7 @@ HY_APPLY_TABLES(float, f32, 3d)
 HY_FF_TABLES(2d)
 HY_FF_TABLES(3d)
 #undef HY_FF_TABLES
+#undef HY_FF_VAR
 #undef HY_APPLY_TABLES
 StateFn<double> state_fn_f64(int dim, int n, int var);   // var VAR_NONE: J check only
 StateFn<float> state_fn_f32(int dim, int n, int var);

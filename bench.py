@@ -410,7 +410,7 @@ def config_study(torch, api, inputs, dev, sweep=None, paper_max_dofs=60_000_000,
     out["mixed_per_load_step_64^3_Q2"] = per_step
     out["note"] = ("paper_fp64: FP64 V-cycle, Chebyshev coarse to 1e-3 (Sec. 7); fastest: FP32 V-cycle with T2 level "
                    "operators, exact coarse inverse (double-float Gauss-Jordan) where the coarsest level allows, "
-                   "double-float finest-level action for degrees 1-2; Newton under 10% compression in 5 load steps")
+                   "double-float finest-level action, setup reuse at 5 %; Newton under 10% compression in 5 load steps")
     return out
 
 
@@ -420,7 +420,7 @@ def serve_bench(api, inputs, dev, n_req, seed=0, max_active=8, budget_gb=160, se
     requests solved one at a time with plain FP64 (FP64 V-cycle, Chebyshev coarse solve); with seq_every > 1
     only every seq_every-th request is solved that way and the baseline rate is that subset's (stated in the
     result). Served: up to `max_active` resident solves, mixed-precision V-cycle, exact coarse solve with the
-    double-float inverse, double-float finest-level action and diagonals for degrees 1-2; closed loop (all at
+    double-float inverse, double-float finest-level action and diagonals; closed loop (all at
     t=0) for peak solves/s, once with independent per-request solves and once with the outer CG solves fused
     across requests (hy_server_set_batching); Poisson arrivals at twice the baseline rate for p50/p99."""
     reqs = inputs.serving_requests(n_req, seed)

@@ -41,7 +41,7 @@ ALL_VARIANTS = ("T4", "T2", "FC", "SC", "NC")
 WORKLOAD = "3D neo-Hookean unit cube, spherical inclusion r=0.25 10x, 32^3 Q2 (823,875 dofs), FP64 tangent apply x {T4, FC, NC}"
 
 
-FORMS = {-1: None, 0: "point", 1: "line", 2: "line_persistent"}
+FORMS = {-1: None, 0: "point", 1: "line", 2: "line_persistent", 3: "plane"}
 
 
 def flops_per_qp(var, dim=3, n=3):

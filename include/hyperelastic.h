@@ -177,7 +177,9 @@ typedef struct {
   int kernel_form;          /* [-1] tangent-action kernel: 0 = one thread per (cell, Gauss point), 1 = one
                                thread per x-line of a cell, 2 = as 1 on a persistent grid whose thread
                                blocks copy their next cache chunk in while finishing the current one (FP32;
-                               runs as 1 in the other precisions), -1 = autotuned: the first linearisation
+                               runs as 1 in the other precisions), 3 = one thread per z-plane of a cell, only
+                               the z direction exchanged through shared memory (FP32 in 3D, degrees 1-2;
+                               runs as 1 elsewhere), -1 = autotuned: the first linearisation
                                of each (dim, degree, variant, precision, mesh size) times the forms on the
                                level's own cache and keeps the fastest (process-wide; when the environment variable
                                HY_TUNE_FILE names a file, the decisions are read from it at the first tuning
@@ -217,7 +219,8 @@ hy_status hy_level_info(const hy_ctx *ctx, int level, double *lmax, double *coar
 /* Override the estimates (levels >= 1: lmax; level 0: lo, hi), e.g. to mirror another solver. */
 hy_status hy_set_level_info(hy_ctx *ctx, int level, double lmax, double coarse_lo, double coarse_hi);
 
-/* Tangent-action kernel form used on a level for a precision (0 point, 1 line; see kernel_form), or -1
+/* Tangent-action kernel form used on a level for a precision (0 point, 1 line, 2 persistent line, 3 plane;
+ * see kernel_form), or -1
  * when that level has no cache of that precision. */
 hy_status hy_kernel_form(const hy_ctx *ctx, int level, hy_dtype dtype, int *form);
 

@@ -34,7 +34,8 @@ def nvcc() -> str:
 def sources():
     """The translation units, longest compiles first (3D, then double-float, kernel units)."""
     def cost(f):
-        return (0 if "3d" in f and ("_hi" in f or "_ff_" in f) else 1 if "3d" in f else 2 if "inst" in f else 3, f)
+        return (0 if "f32_3d" in f else 1 if "3d" in f and ("_hi" in f or "_ff_" in f) else 2 if "3d" in f
+                else 3 if "inst" in f else 4, f)
     return [os.path.join(CSRC, f) for f in sorted((f for f in os.listdir(CSRC) if f.endswith(".cu")), key=cost)]
 
 

@@ -956,8 +956,8 @@ using TuneKey = std::tuple<int, int, int, int, int>;
 std::mutex g_tune_mu;
 std::map<TuneKey, int> g_tune;
 bool g_tune_loaded = false;
-const char* const kVarNames[5] = {"T4", "T2", "FC", "SC", "NC"};
-const char* const kFormNames[3] = {"point", "line", "line_persistent"};
+const char* const kVarNames[9] = {"T4", "T2", "FC", "SC", "NC", "none", "FCG", "SCG", "NCG"};
+const char* const kFormNames[4] = {"point", "line", "line_persistent", "plane"};
 const char* const kPrecNames[3] = {"f64", "f32", "ff"};
 
 int name_index(const char* s, const char* const* names, int n) {
@@ -981,7 +981,7 @@ void tune_load_locked() {
                           "\"cells_log2\": %d, \"threads_per_cell\": \"%23[^\"]\"",
                     &d, &k, var, prec, &b, form) != 6)
       continue;  // the brackets and anything unrecognised
-    const int v = name_index(var, kVarNames, 5), fm = name_index(form, kFormNames, 3);
+    const int v = name_index(var, kVarNames, 9), fm = name_index(form, kFormNames, 4);
     const int p = name_index(prec, kPrecNames, 3);
     if (v >= 0 && fm >= 0 && p >= 0) g_tune[TuneKey{d, k, v, p, b}] = fm;
   }
@@ -1048,8 +1048,9 @@ hy_status autotune_level(hy_ctx* ctx, int l) {
   HY_CK(cudaEventCreate(&ev.b));
   cudaEvent_t e0 = ev.a, e1 = ev.b;
   // FP32 also has the persistent line form (next cache chunk copied in under the current block's work)
-  const int nforms = std::is_same<T, float>::value ? 3 : 2;
-  float best[3] = {1e30f, 1e30f, 1e30f};
+  // and, in 3D, the plane form
+  const int nforms = std::is_same<T, float>::value ? (ctx->dim == 3 && ctx->n <= PLANE_MAX_N ? 4 : 3) : 2;
+  float best[4] = {1e30f, 1e30f, 1e30f, 1e30f};
   for (int form = 0; form < nforms; ++form) {
     L.form[dt] = form;
     HY_TRY(vmult<T>(ctx, l, x, y));
@@ -1071,9 +1072,11 @@ hy_status autotune_level(hy_ctx* ctx, int l) {
     if (best[form] < best[choice]) choice = form;
   L.form[dt] = choice;
   if (ctx->verbose)
-    std::fprintf(stderr, "[hy] autotune dim %d k %d var %d %s cells 2^%d: point %.3f ms, line %.3f ms, persistent %.3f ms -> %s\n",
+    std::fprintf(stderr,
+                 "[hy] autotune dim %d k %d var %d %s cells 2^%d: point %.3f ms, line %.3f ms, persistent %.3f ms, "
+                 "plane %.3f ms -> %s\n",
                  ctx->dim, ctx->k, L.var[dt], kPrecNames[dt], bucket, best[0], best[1], nforms > 2 ? best[2] : 0.f,
-                 kFormNames[choice]);
+                 nforms > 3 ? best[3] : 0.f, kFormNames[choice]);
   std::lock_guard<std::mutex> lock(g_tune_mu);
   if (g_tune.emplace(key, choice).second) tune_save_locked();
   return HY_OK;
@@ -1386,7 +1389,6 @@ hy_status bfail(hy_batch* b, hy_status s, const std::string& msg) {
                                         std::string(#call) + ": " + cudaGetErrorString(e_));              \
   } while (0)
 
-constexpr int BATCH_MAX = 1024;
 constexpr size_t BATCH_ARG_BYTES = sizeof(CellArgs<double>) > sizeof(CellArgs<float>) ? sizeof(CellArgs<double>)
                                                                                       : sizeof(CellArgs<float>);
 
@@ -2276,7 +2278,7 @@ hy_status hy_gmg_vcycle(hy_ctx* ctx, const double* r, double* z) {
 hy_status hy_set_solver_params(hy_ctx* ctx, const hy_solver_params* p) {
   if (!ctx || !p) return HY_ERR_ARG;
   if (p->cheb_degree < 1 || p->cheb_sweeps < 1 || !(p->cheb_lo > 0) || !(p->cheb_hi > p->cheb_lo) ||
-      p->kernel_form < -1 || p->kernel_form > 2 || (p->fine_dtype != HY_F64 && p->fine_dtype != HY_FF) ||
+      p->kernel_form < -1 || p->kernel_form > 3 || (p->fine_dtype != HY_F64 && p->fine_dtype != HY_FF) ||
       p->level_variant < -1 || p->level_variant > 4 ||
       p->eig_iters < 1 || p->coarse_eig_iters < 0 || !(p->coarse_reduction > 0 && p->coarse_reduction < 1) ||
       p->coarse_solver < 0 || p->coarse_solver > 2 || !(p->setup_reuse >= 0.0))

@@ -1072,6 +1072,252 @@ __device__ __forceinline__ void apply_line_body(const CellArgs<T>& a, const int 
   }
 }
 
+// ------------------------------------------------------------------------------------------------
+// Tangent action, one thread per z-plane of a cell (3D, FP32). The thread holds the (k+1)^2 nodes of its
+// node plane a2 = l2, then the (k+1)^2 Gauss points of Gauss plane q2 = l2, in registers: interpolation,
+// derivatives and their transposes along x and y need no shared memory, and only the z direction exchanges
+// values between the k+1 threads of a cell through shared memory -- four exchanges of (k+1)^2 d values per
+// thread (the z sweep, the z derivative, the z part of the flux, the transposed z sweep), about 60 % of the
+// shared-memory traffic of the line form. Same arithmetic, variants, cache layout and Dirichlet treatment as
+// apply_kernel. The transposed x and y derivatives are accumulated Gauss point by Gauss point.
+// Built for degrees 1-2 (n <= PLANE_MAX_N): at higher degrees a plane is 16-25 nodes per component, too many
+// registers; the line form serves those.
+constexpr int PLANE_MAX_N = 3;
+template <int N, int VAR, typename T>
+__device__ __forceinline__ void apply_plane_body(const CellArgs<T>& a, const int blk) {
+  constexpr int DIM = 3;
+  constexpr int NPT = N * N * N;
+  constexpr int NP = N * N;  // nodes or Gauss points of a plane
+  constexpr int CB = layout_cells<T>(DIM, N);
+  constexpr int TP = CB * N;  // plane threads of the block
+  constexpr int K = N - 1;
+  constexpr int BV = base_variant(VAR);
+  constexpr bool NEED_U = (BV == VAR_NC || BV == VAR_SC);
+  constexpr bool PHYS = (BV == VAR_FC || NEED_U) && !is_general(VAR);
+  constexpr int NV = cache_values(VAR, DIM);
+  constexpr int BS = layout_row<T>(DIM, N);
+  // exchange buffers: entry (component c, point r of the plane, plane thread t) at (c NP + r) TP + t
+  constexpr int NB = DIM * NP * TP;
+  constexpr int NBU = NEED_U ? NB : 1;
+  __shared__ T tD[MAXN][MAXN], tS[MAXN][MAXN], tWh[NPT], tmu[MAXMAT], tlam[MAXMAT];
+  __shared__ T xb0[NB], xb1[NB];
+  __shared__ T ub0[NBU], ub1[NBU];
+  __shared__ __align__(8) unsigned long long bar;
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
+  T* const cs = reinterpret_cast<T*>(dyn_smem);
+  const int t = threadIdx.x;
+  constexpr unsigned CHUNK = (unsigned)(NV * BS * sizeof(T));
+  if (NV > 0 && t == 0) {
+    // the block's cache chunk streams in (bulk copy) under the gather and the forward sweeps
+    mbar_init(&bar, 1);
+    bulk_load(cs, a.cache + (size_t)blk * NV * BS, CHUNK, &bar);
+  }
+  for (int i = t; i < MAXN * MAXN; i += blockDim.x) {
+    tS[i / MAXN][i % MAXN] = a.b.S[i / MAXN][i % MAXN];
+    tD[i / MAXN][i % MAXN] = a.b.D[i / MAXN][i % MAXN];
+  }
+  for (int i = t; i < NPT; i += blockDim.x) {
+    const int q0 = i % N, q1 = (i / N) % N, q2 = i / NP;
+    const T hd = T(a.g.h) * T(a.g.h) * T(a.g.h);
+    tWh[i] = a.b.w[q0] * a.b.w[q1] * a.b.w[q2] * hd * T(a.g.inv_h);
+  }
+  for (int i = t; i < MAXMAT; i += blockDim.x) {
+    tmu[i] = a.mt.mu[i];
+    tlam[i] = a.mt.lam[i];
+  }
+  const int cl = t / N, l2 = t % N;  // plane l2 of cell cl: the k+1 threads of a cell are adjacent
+  const int zb = cl * N;             // plane thread of this cell with plane index 0
+  const int cell = blk * CB + cl;
+  const bool active = cell < a.g.ncells;
+  const int m = a.g.m;
+  const int cc = active ? cell : 0;
+  const int c0 = cc % m, c1 = (cc / m) % m, c2 = cc / (m * m);
+  const int i2 = K * c2 + l2;
+  const T sh = PHYS ? T(a.g.inv_h) : T(1);
+  auto XB = [](int c, int r, int i) { return (c * NP + r) * TP + i; };
+  // gather the node plane a2 = l2 (x read as zero on constrained dofs)
+  uint32_t cms[NP];
+  T V[NP][DIM], VU[NEED_U ? NP : 1][DIM];
+#pragma unroll
+  for (int a1 = 0; a1 < N; ++a1)
+#pragma unroll
+    for (int a0 = 0; a0 < N; ++a0) {
+      const int r = a0 + N * a1;
+      const int i0 = K * c0 + a0, i1 = K * c1 + a1;
+      cms[r] = node_cmask<DIM>(a.g, i0, i1, i2);
+      const long long node = i0 + (long long)a.g.L * (i1 + (long long)a.g.L * i2);
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        V[r][c] = (active && !((cms[r] >> c) & 1u)) ? vec_in<T>(a.x[node * DIM + c]) : T(0);
+        if (NEED_U) VU[NEED_U ? r : 0][c] = active ? vec_in<T>(a.ubar[node * DIM + c]) : T(0);
+      }
+    }
+  // x, then y interpolation in registers: values at (q0, q1) of node plane l2
+  {
+    T X[NP][DIM], XU[NEED_U ? NP : 1][DIM];
+#pragma unroll
+    for (int a1 = 0; a1 < N; ++a1)
+#pragma unroll
+      for (int q0 = 0; q0 < N; ++q0)
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+          T sx = T(0), su = T(0);
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            sx = fma(a.b.S[q0][j], V[j + N * a1][c], sx);
+            if (NEED_U) su = fma(a.b.S[q0][j], VU[NEED_U ? j + N * a1 : 0][c], su);
+          }
+          X[q0 + N * a1][c] = sx;
+          if (NEED_U) XU[NEED_U ? q0 + N * a1 : 0][c] = su;
+        }
+#pragma unroll
+    for (int q1 = 0; q1 < N; ++q1)
+#pragma unroll
+      for (int q0 = 0; q0 < N; ++q0)
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+          T sx = T(0), su = T(0);
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            sx = fma(a.b.S[q1][j], X[q0 + N * j][c], sx);
+            if (NEED_U) su = fma(a.b.S[q1][j], XU[NEED_U ? q0 + N * j : 0][c], su);
+          }
+          xb0[XB(c, q0 + N * q1, t)] = sx;
+          if (NEED_U) ub0[NEED_U ? XB(c, q0 + N * q1, t) : 0] = su;
+        }
+  }
+  __syncthreads();
+  // z interpolation: this thread's Gauss plane q2 = l2 from the k+1 node planes of its cell
+#pragma unroll
+  for (int r = 0; r < NP; ++r)
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      T sx = T(0), su = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        sx = fma(tS[l2][j], xb0[XB(c, r, zb + j)], sx);
+        if (NEED_U) su = fma(tS[l2][j], ub0[NEED_U ? XB(c, r, zb + j) : 0], su);
+      }
+      V[r][c] = sx;
+      if (NEED_U) VU[NEED_U ? r : 0][c] = su;
+    }
+#pragma unroll
+  for (int r = 0; r < NP; ++r)
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      xb1[XB(c, r, t)] = V[r][c];
+      if (NEED_U) ub1[NEED_U ? XB(c, r, t) : 0] = VU[NEED_U ? r : 0][c];
+    }
+  __syncthreads();
+  if (NV > 0) {
+    const bool ok = mbar_wait(&bar, 0);
+    if (__syncthreads_or(!ok)) {  // the copy never completed: flag it, give it one more bounded wait, leave
+      if (t == 0) atomicOr(a.err, ERRBIT_TIMEOUT);
+      mbar_wait(&bar, 0);
+      return;
+    }
+  }
+  // Gauss-point work on plane l2; the transposed x and y derivatives accumulate in W, the z part of the
+  // flux goes to shared memory
+  const int id = active ? a.mat[cell] : 0;
+  T W[NP][DIM];
+#pragma unroll
+  for (int r = 0; r < NP; ++r)
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) W[r][c] = T(0);
+#pragma unroll
+  for (int q1 = 0; q1 < N; ++q1)
+#pragma unroll
+    for (int q0 = 0; q0 < N; ++q0) {
+      const int r = q0 + N * q1;
+      const int p = r + NP * l2;
+      T G[DIM][DIM], Gu[DIM][DIM];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        T gx = T(0), gy = T(0), gz = T(0), ux = T(0), uy = T(0), uz = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          gx = fma(a.b.D[q0][j], V[j + N * q1][c], gx);
+          gy = fma(a.b.D[q1][j], V[q0 + N * j][c], gy);
+          gz = fma(tD[l2][j], xb1[XB(c, r, zb + j)], gz);
+          if (NEED_U) {
+            ux = fma(a.b.D[q0][j], VU[NEED_U ? j + N * q1 : 0][c], ux);
+            uy = fma(a.b.D[q1][j], VU[NEED_U ? q0 + N * j : 0][c], uy);
+            uz = fma(tD[l2][j], ub1[NEED_U ? XB(c, r, zb + j) : 0], uz);
+          }
+        }
+        G[c][0] = gx * sh;
+        G[c][1] = gy * sh;
+        G[c][2] = gz * sh;
+        Gu[c][0] = ux * sh;
+        Gu[c][1] = uy * sh;
+        Gu[c][2] = uz * sh;
+      }
+      T P[DIM][DIM];
+      qp_flux<DIM, VAR>(G, Gu, cs, BS, cl * NPT + p, active, id, tmu, tlam, tWh[p], P, a.mt.law);
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          W[j + N * q1][c] = fma(a.b.D[q0][j], P[c][0], W[j + N * q1][c]);
+          W[q0 + N * j][c] = fma(a.b.D[q1][j], P[c][1], W[q0 + N * j][c]);
+        }
+        xb0[XB(c, r, t)] = P[c][2];
+      }
+    }
+  __syncthreads();
+  // the z part of the transposed derivatives: Gauss plane l2 collects from the k+1 planes of its cell
+#pragma unroll
+  for (int r = 0; r < NP; ++r)
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      T s = W[r][c];
+#pragma unroll
+      for (int j = 0; j < N; ++j) s = fma(tD[j][l2], xb0[XB(c, r, zb + j)], s);
+      xb1[XB(c, r, t)] = s;
+    }
+  __syncthreads();
+  // transposed z interpolation (node plane l2), then y and x in registers
+#pragma unroll
+  for (int r = 0; r < NP; ++r)
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      T s = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) s = fma(tS[j][l2], xb1[XB(c, r, zb + j)], s);
+      W[r][c] = s;
+    }
+  T Y[NP][DIM];
+#pragma unroll
+  for (int a1 = 0; a1 < N; ++a1)
+#pragma unroll
+    for (int q0 = 0; q0 < N; ++q0)
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        T s = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) s = fma(a.b.S[j][a1], W[q0 + N * j][c], s);
+        Y[q0 + N * a1][c] = s;
+      }
+  if (active) {
+#pragma unroll
+    for (int a1 = 0; a1 < N; ++a1)
+#pragma unroll
+      for (int a0 = 0; a0 < N; ++a0) {
+        const int r = a0 + N * a1;
+        const long long node = (K * c0 + a0) + (long long)a.g.L * ((K * c1 + a1) + (long long)a.g.L * i2);
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+          if ((cms[r] >> c) & 1u) continue;
+          T s = T(0);
+#pragma unroll
+          for (int j = 0; j < N; ++j) s = fma(a.b.S[j][a0], Y[j + N * a1][c], s);
+          atomicAdd(&a.y[node * DIM + c], vec_out(s));
+        }
+      }
+  }
+}
+
 // ---- kernels: one problem (arguments by value), or a work list of problems in one launch ----------
 // Work list: problem p owns the thread blocks start[p] .. start[p+1]-1 of the grid (start[count] = grid
 // size); each problem's arguments are read from global memory. The problems share dim, degree, variant
@@ -1119,6 +1365,19 @@ template <int DIM, int N, int VAR, typename T>
 __global__ void __launch_bounds__(layout_cells<T>(DIM, N) * ipow(N, DIM - 1))
 apply_line_kernel(const CellArgs<T> a) {
   apply_line_body<DIM, N, VAR, T>(a, blockIdx.x, 1);
+}
+
+template <int N, int VAR, typename T>
+__global__ void __launch_bounds__(layout_cells<T>(3, N) * N)
+apply_plane_kernel(const CellArgs<T> a) {
+  apply_plane_body<N, VAR, T>(a, blockIdx.x);
+}
+
+template <int N, int VAR, typename T>
+__global__ void __launch_bounds__(layout_cells<T>(3, N) * N)
+apply_plane_list_kernel(const CellArgs<T>* __restrict__ list, const int* __restrict__ start, int count) {
+  const int p = work_item(start, count, blockIdx.x);
+  apply_plane_body<N, VAR, T>(list[p], blockIdx.x - start[p]);
 }
 
 // persistent: gridDim.x thread blocks loop over all cell blocks, the next chunk copied in early

@@ -112,8 +112,9 @@ __host__ __device__ constexpr int layout_row(int dim, int n) {
 
 // Kernel forms of the tangent action: thread per (cell, Gauss point); thread per x-line of a cell; the line
 // form as a persistent grid whose blocks copy their next cache chunk in while they finish the current one
-// (FP32 only: elsewhere it runs as FORM_LINE).
-enum KernelForm { FORM_POINT = 0, FORM_LINE = 1, FORM_LINE_PERSIST = 2 };
+// (FP32 only: elsewhere it runs as FORM_LINE); thread per z-plane of a cell (FP32 in 3D only: elsewhere it
+// runs as FORM_LINE).
+enum KernelForm { FORM_POINT = 0, FORM_LINE = 1, FORM_LINE_PERSIST = 2, FORM_PLANE = 3 };
 
 // Device-side error word bits.
 enum : unsigned { ERRBIT_JNEG = 1u, ERRBIT_NAN = 2u, ERRBIT_TIMEOUT = 4u, ERRBIT_NONSPD = 8u };

@@ -31,16 +31,20 @@ inline int apply_cells_per_block(int dim, int n) { return layout_cells<T>(dim, n
 #define HY_APPLY_TABLES(P, TAG, D)                                                                      \
   ApplyFn<P> apply_fn_##TAG##_##D##_lo(int n, int var);                                              \
   ApplyFn<P> apply_fn_##TAG##_##D##_hi(int n, int var);                                              \
-  ApplyFn<P> apply_fn_##TAG##_##D##_gen(int n, int var);                                             \
+  ApplyFn<P> apply_fn_##TAG##_##D##_gen_lo(int n, int var);                                          \
+  ApplyFn<P> apply_fn_##TAG##_##D##_gen_hi(int n, int var);                                          \
   ApplyListFn<P> apply_list_fn_##TAG##_##D##_lo(int n, int var);                                     \
   ApplyListFn<P> apply_list_fn_##TAG##_##D##_hi(int n, int var);                                     \
-  ApplyListFn<P> apply_list_fn_##TAG##_##D##_gen(int n, int var);                                    \
+  ApplyListFn<P> apply_list_fn_##TAG##_##D##_gen_lo(int n, int var);                                 \
+  ApplyListFn<P> apply_list_fn_##TAG##_##D##_gen_hi(int n, int var);                                 \
   inline ApplyFn<P> apply_fn_##TAG##_##D(int n, int var) {                                           \
-    if (is_general(var)) return apply_fn_##TAG##_##D##_gen(n, var);                                  \
+    if (is_general(var))                                                                           \
+      return n <= 3 ? apply_fn_##TAG##_##D##_gen_lo(n, var) : apply_fn_##TAG##_##D##_gen_hi(n, var);    \
     return n <= 3 ? apply_fn_##TAG##_##D##_lo(n, var) : apply_fn_##TAG##_##D##_hi(n, var);             \
   }                                                                                                \
   inline ApplyListFn<P> apply_list_fn_##TAG##_##D(int n, int var) {                                  \
-    if (is_general(var)) return apply_list_fn_##TAG##_##D##_gen(n, var);                             \
+    if (is_general(var))                                                                           \
+      return n <= 3 ? apply_list_fn_##TAG##_##D##_gen_lo(n, var) : apply_list_fn_##TAG##_##D##_gen_hi(n, var); \
     return n <= 3 ? apply_list_fn_##TAG##_##D##_lo(n, var) : apply_list_fn_##TAG##_##D##_hi(n, var);   \
   }
 HY_APPLY_TABLES(double, f64, 2d)

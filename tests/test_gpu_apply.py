@@ -33,9 +33,9 @@ def test_apply_all_variants_fp64_fp32(torch, dim, k, m):
     xd = torch.tensor(x, device="cuda")
     xf = xd.float()
     with context(pr) as ctx:
-        # one thread per (cell, Gauss point); one thread per x-line of a cell; the persistent double-buffered
-        # line form (FP32; the line form elsewhere)
-        for form in (0, 1, 2):
+        # one thread per (cell, Gauss point); one thread per x-line of a cell; the persistent line form (FP32;
+        # the line form elsewhere); one thread per z-plane of a cell (FP32 in 3D; the line form elsewhere)
+        for form in (0, 1, 2, 3):
             ctx.set_solver_params(kernel_form=form)
             for var in VARIANTS:
                 ctx.set_displacement(ud, var, level_dtype=1)  # builds the FP64 and the FP32 fine cache

@@ -414,7 +414,8 @@ def config_study(torch, api, inputs, dev, sweep=None, paper_max_dofs=60_000_000,
     return out
 
 
-def serve_bench(api, inputs, dev, n_req, seed=0, max_active=8, budget_gb=160, seq_every=1, poisson=True):
+def serve_bench(api, inputs, dev, n_req, seed=0, max_active=8, budget_gb=160, seq_every=1, poisson=True,
+                rate=None):
     """Serving (continuous batching): a seeded stream of uneven solve requests (2D 32^2-256^2 and 3D 8^3-48^3,
     Q1-Q3, stiffness ratio 2-100, radius 0.1-0.35, compression 2-15 %, 5 load steps). Baseline: the same
     requests solved one at a time with plain FP64 (FP64 V-cycle, Chebyshev coarse solve); with seq_every > 1
@@ -422,7 +423,8 @@ def serve_bench(api, inputs, dev, n_req, seed=0, max_active=8, budget_gb=160, se
     result). Served: up to `max_active` resident solves, mixed-precision V-cycle, exact coarse solve with the
     double-float inverse, double-float finest-level action and diagonals; closed loop (all at
     t=0) for peak solves/s, once with independent per-request solves and once with the outer CG solves fused
-    across requests (hy_server_set_batching); Poisson arrivals at twice the baseline rate for p50/p99."""
+    across requests (hy_server_set_batching); Poisson arrivals at twice the baseline rate (or `rate` per
+    second) for p50/p99."""
     reqs = inputs.serving_requests(n_req, seed)
 
     def problem(q):
@@ -474,7 +476,7 @@ def serve_bench(api, inputs, dev, n_req, seed=0, max_active=8, budget_gb=160, se
     seq, u_seq = run(sub, 1, 0, 0)
     if seq_every > 1:
         seq["subset"] = f"every {seq_every}th request ({len(sub)} of {n_req}); the baseline rate is this subset's"
-    rate = 2.0 * seq["solves_per_s"]
+    rate = 2.0 * seq["solves_per_s"] if rate is None else rate
     peak, u_peak = run(reqs, max_active, 1, 1, ff=True)
     fused, u_fused = run(reqs, max_active, 1, 1, ff=True, batching=True)
     out = {"requests": n_req, "seed": seed, "sequential_fp64": seq, "served_closed_loop": peak,
@@ -811,6 +813,8 @@ def main():
     ap.add_argument("--serve-seq-every", type=int, default=1,
                     help="sequential FP64 baseline on every n-th request only (long streams)")
     ap.add_argument("--no-serve-poisson", dest="serve_poisson", action="store_false")
+    ap.add_argument("--serve-rate", type=float, default=None,
+                    help="Poisson arrival rate per second (default: twice the sequential baseline's solves/s)")
     ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the work-list batch section")
     ap.add_argument("--batch-only", action="store_true")
     ap.add_argument("--solve-only", action="store_true")
@@ -915,7 +919,7 @@ def main():
         return
     if args.serve_only:
         print(json.dumps({"serve": serve_bench(api, inputs, dev, args.serve_requests, seq_every=args.serve_seq_every,
-                                               poisson=args.serve_poisson)}), flush=True)
+                                               poisson=args.serve_poisson, rate=args.serve_rate)}), flush=True)
         return
     pr, u, x, ctxs = setup_contexts(torch, api, inputs, dev)
     n = inputs.n_dofs(DIM, K, M)

@@ -233,7 +233,8 @@ def solve_latency(torch, api, inputs, dev):
                 ("mixed_exact_coarse_fp64_inverse_t2_levels", 1, 1, 0, api.VARIANTS["T2"], 0.0),
                 ("mixed_exact_coarse_ff", 1, 2, 2, -1, 0.0),
                 ("mixed_exact_coarse_ff_t2_levels", 1, 2, 2, api.VARIANTS["T2"], 0.0),
-                ("mixed_exact_coarse_ff_t2_levels_setup_reuse", 1, 2, 2, api.VARIANTS["T2"], 0.05)):
+                ("mixed_exact_coarse_ff_t2_levels_setup_reuse", 1, 2, 2, api.VARIANTS["T2"], 0.05),
+                ("mixed_fp64_coarse_inverse_ff_t2_levels_setup_reuse", 1, 1, 2, api.VARIANTS["T2"], 0.05)):
             c.set_solver_params(coarse_solver=coarse, fine_dtype=fine, level_variant=lvar, setup_reuse=reuse)
             u = torch.zeros(inputs.n_dofs(DIM, K, M), dtype=torch.float64, device=dev)
             rep = c.newton_solve(u, api.Context.newton_params(level_dtype=ldt, face_values=fv))
@@ -285,7 +286,9 @@ def solve_latency(torch, api, inputs, dev):
                              "double-float (about 48 bits) and double-float finest-level action in the outer CG; "
                              "_t2_levels: the V-cycle's level operators in the T2 variant; _setup_reuse: "
                              "eigenvalue estimates and coarse inverse kept while the coarse displacement moved "
-                             "less than 5 % since the last full setup")
+                             "less than 5 % since the last full setup; mixed_fp64_coarse_inverse_*: the fastest "
+                             "mode with the coarse inverse in FP64 (the FP64 coarse solve of the mixed-precision "
+                             "pattern) instead of double-float")
     out["workload"] = "32^3 Q2 (823,875 dofs), 10% compression in 5 load steps, 4 levels, CG rtol 1e-8, T4"
     return out
 

@@ -928,7 +928,7 @@ hy_status coarse_direct_setup(hy_ctx* ctx) {
   HY_TRY(check_launch(ctx, 1));
   const bool ff_arith = ctx->sp.coarse_solver == 2;
   C.d_Aresult = launch_gj_invert(C.d_Ainv, C.d_Awork, n, C.d_inv_piv, err, ff_arith, ctx->side);
-  HY_TRY(check_launch(ctx, (int)(3 * ((n + 31) / 32)) + (ff_arith ? 2 : 0)));
+  HY_TRY(check_launch(ctx, (int)(3 * ((n + 31) / 32)) + 1 + (ff_arith ? 2 : 0)));
   HY_CK(cudaMemcpyAsync(ctx->h_err_side, err, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->side));
   HY_CK(cudaEventRecord(ctx->ev_side_join, ctx->side));
   ctx->side_pending = true;

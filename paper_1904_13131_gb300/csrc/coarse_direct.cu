@@ -253,8 +253,21 @@ void launch_assemble_dense(int dim, int n, const CellArgs<double>& a, double* A,
 // the block form of b consecutive single-pivot steps; every element of A is read and written once per b
 // pivots instead of once per pivot. The element type E is double, or double-float (ff: the same passes on
 // the FP32 pipe, about 48 significant bits, the reciprocal of each pivot taken in FP64).
+// Symmetry: A is SPD, and after any number of passes an entry (i, j) equals (j, i) when i and j are both
+// eliminated (i, j < k0) or both not, and -(j, i) when exactly one is (the eliminated block holds the
+// inverse of the leading block, the rest its Schur complement, the cross blocks are negatives of each
+// other's transposes). So every pass reads and writes the upper triangle only, which halves the update, and
+// the final inverse (all eliminated: symmetric) is mirrored once.
 namespace {
 constexpr int GJB = 32;
+
+// Entry (p, q) of the current matrix from its upper triangle (before the pass over [k0, k0 + b)).
+template <typename E>
+__device__ __forceinline__ E sym_get(const E* __restrict__ A, int n, int k0, int p, int q) {
+  if (p <= q) return A[(long long)p * n + q];
+  const E v = A[(long long)q * n + p];
+  return ((p < k0) != (q < k0)) ? -v : v;
+}
 
 __device__ __forceinline__ double gj_recip(double p) { return 1.0 / p; }
 __device__ __forceinline__ ff gj_recip(ff p) { return rcp_rn(p); }
@@ -268,7 +281,7 @@ __global__ void gjb_diag(const E* __restrict__ A, int n, int k0, int b, E* __res
   __shared__ E w[GJB][GJB + 1];
   __shared__ E rk[GJB], ck[GJB];
   const int t = threadIdx.x;
-  for (int idx = t; idx < b * b; idx += blockDim.x) w[idx / b][idx % b] = A[(long long)(k0 + idx / b) * n + k0 + idx % b];
+  for (int idx = t; idx < b * b; idx += blockDim.x) w[idx / b][idx % b] = sym_get(A, n, k0, k0 + idx / b, k0 + idx % b);
   __syncthreads();
   for (int k = 0; k < b; ++k) {
     const E p = w[k][k];
@@ -299,8 +312,8 @@ __global__ void __launch_bounds__(256) gjb_panels(const E* __restrict__ A, int n
   for (int idx = t; idx < b * b; idx += 256) w[idx / b][idx % b] = W[idx];
   const int j = blockIdx.x * 8 + jy;
   const bool inb = j < n && r < b;
-  colv[jy][r] = inb ? A[(long long)(k0 + r) * n + j] : E(0);  // A_Kj
-  rowv[jy][r] = inb ? A[(long long)j * n + k0 + r] : E(0);    // A_jK
+  colv[jy][r] = inb ? sym_get(A, n, k0, k0 + r, j) : E(0);  // A_Kj
+  rowv[jy][r] = inb ? sym_get(A, n, k0, j, k0 + r) : E(0);  // A_jK
   __syncthreads();
   if (!inb) return;
   E y = E(0), x = E(0);
@@ -320,12 +333,13 @@ __global__ void __launch_bounds__(256) gjb_update(const E* __restrict__ A, E* __
                                                   const E* __restrict__ X) {
   __shared__ E sA[64][GJB + 1];
   __shared__ E sY[GJB][64 + 1];
+  if (blockIdx.x < blockIdx.y) return;  // upper triangle of tiles only
   const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
   const int t = threadIdx.x;
   for (int idx = t; idx < 64 * GJB; idx += 256) {
     const int r = idx / GJB, m = idx % GJB;
     const int i = i0 + r;
-    sA[r][m] = (i < n && m < b) ? A[(long long)i * n + k0 + m] : E(0);
+    sA[r][m] = (i < n && m < b) ? sym_get(A, n, k0, i, k0 + m) : E(0);
     const int mm = idx / 64, c = idx % 64;
     const int j = j0 + c;
     sY[mm][c] = (j < n && mm < b) ? Y[(long long)mm * n + j] : E(0);
@@ -356,13 +370,24 @@ __global__ void __launch_bounds__(256) gjb_update(const E* __restrict__ A, E* __
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const int j = j0 + tc + c;
-      if (j >= n) continue;
+      if (j >= n || j < i) continue;  // the upper triangle
       const bool jK = j >= k0 && j < k0 + b;
       E v;
       if (iK) v = jK ? W[(i - k0) * b + (j - k0)] : Y[(long long)(i - k0) * n + j];
       else v = jK ? -X[(long long)i * b + (j - k0)] : A[(long long)i * n + j] - acc[a][c];
       B[(long long)i * n + j] = v;
     }
+  }
+}
+
+// lower triangle <- upper triangle (the symmetric inverse after the last pass)
+template <typename E>
+__global__ void mirror_lower(E* A, int n) {
+  const long long total = (long long)n * n;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / n), j = (int)(idx % n);
+    if (i > j) A[idx] = A[(long long)j * n + i];
   }
 }
 
@@ -379,6 +404,7 @@ E* gj_passes(E* A, E* B, long long n, E* work, unsigned* err, cudaStream_t st) {
     gjb_update<E><<<grid, 256, 0, st>>>(A, B, (int)n, (int)k0, b, W, Y, X);
     std::swap(A, B);
   }
+  mirror_lower<E><<<(int)std::min<long long>((n * n + 255) / 256, 152LL * 16), 256, 0, st>>>(A, (int)n);
   return A;
 }
 

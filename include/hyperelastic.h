@@ -407,7 +407,8 @@ hy_status hy_server_create(hy_server **out, int device, int64_t hbm_budget_bytes
  * preconditioned CG (Secs. 6-7) across requests. Each worker still linearises its own request on its own
  * stream, but its outer CG solves go to a batcher, which waits until every running Newton solve has a
  * solve waiting or window_ms (0..1000) has passed since the oldest arrived, groups the waiting solves by
- * dimension, degree, cache variants, finest-level precision, CG tolerance and cap, and runs every group as
+ * dimension, degree, cache variants, finest-level precision, CG tolerance and cap and size (within a factor
+ * of 4 in dofs: a batch returns when its slowest member has converged), and runs every group as
  * one work-list batch (hy_batch_pcg: one graph replay per PCG iteration with ONE kernel launch for the
  * finest-level tangent actions of all members and their V-cycles as concurrent branches). Groups of
  * different degree run side by side. Results are those of the requests' own PCG (the same arithmetic per

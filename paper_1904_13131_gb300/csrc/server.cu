@@ -267,11 +267,19 @@ void batcher_loop(hy_server* sv) {
     std::vector<SolveJob*> take(sv->jobs.begin(), sv->jobs.end());
     sv->jobs.clear();
     lock.unlock();
-    // groups of one batch key, tolerance and cap
+    // groups of one batch key, tolerance, cap and size class: a batch returns when its slowest member has
+    // converged, so members within a factor of 4 in dofs are fused and the others run side by side
     std::vector<std::vector<SolveJob*>> groups;
-    std::vector<std::tuple<long long, double, int>> keys;
+    std::vector<std::tuple<long long, double, int, int>> keys;
     for (SolveJob* j : take) {
-      const auto key = std::make_tuple(hy_ctx_batch_key(j->ctx), j->rtol, j->max_iter);
+      int64_t nd = 1;
+      hy_num_dofs(j->ctx, -1, &nd);
+      int size_class = 0;
+      while (nd > 1) {
+        nd >>= 2;
+        ++size_class;
+      }
+      const auto key = std::make_tuple(hy_ctx_batch_key(j->ctx), j->rtol, j->max_iter, size_class);
       size_t gi = 0;
       while (gi < keys.size() && keys[gi] != key) ++gi;
       if (gi == keys.size()) {

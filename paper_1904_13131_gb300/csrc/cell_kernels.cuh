@@ -1335,14 +1335,12 @@ __device__ __forceinline__ int work_item(const int* __restrict__ start, int coun
 template <int DIM, int N, int VAR, typename T>
 __global__ void __launch_bounds__(layout_cells<T>(DIM, N) * ipow(N, DIM))
 apply_kernel(const CellArgs<T> a) {
-  pdl_enter();
   apply_point_body<DIM, N, VAR, T>(a, blockIdx.x);
 }
 
 template <int DIM, int N, int VAR, typename T>
 __global__ void __launch_bounds__(layout_cells<T>(DIM, N) * ipow(N, DIM))
 apply_list_kernel(const CellArgs<T>* __restrict__ list, const int* __restrict__ start, int count) {
-  pdl_enter();
   const int p = work_item(start, count, blockIdx.x);
   apply_point_body<DIM, N, VAR, T>(list[p], blockIdx.x - start[p]);
 }
@@ -1353,14 +1351,12 @@ apply_list_kernel(const CellArgs<T>* __restrict__ list, const int* __restrict__ 
 template <int DIM, int N, int VAR, typename T>
 __global__ void __launch_bounds__(layout_cells<T>(DIM, N) * ipow(N, DIM), 3)
 apply_kernel_ff(const CellArgs<T> a) {
-  pdl_enter();
   apply_point_body<DIM, N, VAR, T>(a, blockIdx.x);
 }
 
 template <int DIM, int N, int VAR, typename T>
 __global__ void __launch_bounds__(layout_cells<T>(DIM, N) * ipow(N, DIM), 3)
 apply_list_kernel_ff(const CellArgs<T>* __restrict__ list, const int* __restrict__ start, int count) {
-  pdl_enter();
   const int p = work_item(start, count, blockIdx.x);
   apply_point_body<DIM, N, VAR, T>(list[p], blockIdx.x - start[p]);
 }
@@ -1368,21 +1364,18 @@ apply_list_kernel_ff(const CellArgs<T>* __restrict__ list, const int* __restrict
 template <int DIM, int N, int VAR, typename T>
 __global__ void __launch_bounds__(layout_cells<T>(DIM, N) * ipow(N, DIM - 1))
 apply_line_kernel(const CellArgs<T> a) {
-  pdl_enter();
   apply_line_body<DIM, N, VAR, T>(a, blockIdx.x, 1);
 }
 
 template <int N, int VAR, typename T>
 __global__ void __launch_bounds__(layout_cells<T>(3, N) * N)
 apply_plane_kernel(const CellArgs<T> a) {
-  pdl_enter();
   apply_plane_body<N, VAR, T>(a, blockIdx.x);
 }
 
 template <int N, int VAR, typename T>
 __global__ void __launch_bounds__(layout_cells<T>(3, N) * N)
 apply_plane_list_kernel(const CellArgs<T>* __restrict__ list, const int* __restrict__ start, int count) {
-  pdl_enter();
   const int p = work_item(start, count, blockIdx.x);
   apply_plane_body<N, VAR, T>(list[p], blockIdx.x - start[p]);
 }
@@ -1391,14 +1384,12 @@ apply_plane_list_kernel(const CellArgs<T>* __restrict__ list, const int* __restr
 template <int DIM, int N, int VAR, typename T>
 __global__ void __launch_bounds__(layout_cells<T>(DIM, N) * ipow(N, DIM - 1))
 apply_line_persist_kernel(const CellArgs<T> a) {
-  pdl_enter();
   apply_line_body<DIM, N, VAR, T, true>(a, blockIdx.x, gridDim.x);
 }
 
 template <int DIM, int N, int VAR, typename T>
 __global__ void __launch_bounds__(layout_cells<T>(DIM, N) * ipow(N, DIM - 1))
 apply_line_list_kernel(const CellArgs<T>* __restrict__ list, const int* __restrict__ start, int count) {
-  pdl_enter();
   const int p = work_item(start, count, blockIdx.x);
   apply_line_body<DIM, N, VAR, T>(list[p], blockIdx.x - start[p], 1);
 }
@@ -1501,7 +1492,6 @@ __device__ __forceinline__ void premultiply(const double invJ[DIM][DIM], double 
 template <int DIM, int N, int VAR, typename T>
 __global__ void __launch_bounds__(cells_per_block(DIM, N) * ipow(N, DIM))
 qp_state_kernel(const CellArgs<double> a, T* __restrict__ out) {
-  pdl_enter();
   constexpr int NPT = ipow(N, DIM);
   constexpr int CB = cells_per_block(DIM, N);
   constexpr int NS = nsym(DIM);
@@ -1599,7 +1589,6 @@ qp_state_kernel(const CellArgs<double> a, T* __restrict__ out) {
 template <int DIM, int N>
 __global__ void __launch_bounds__(cells_per_block(DIM, N) * ipow(N, DIM))
 residual_kernel(const CellArgs<double> a) {
-  pdl_enter();
   constexpr int NPT = ipow(N, DIM);
   constexpr int CB = cells_per_block(DIM, N);
   constexpr int NS = nsym(DIM);
@@ -1671,7 +1660,6 @@ residual_kernel(const CellArgs<double> a) {
 template <int DIM, int N, typename E>
 __global__ void __launch_bounds__(cells_per_block(DIM, N) * ipow(N, DIM))
 diag_kernel(const CellArgs<double> a) {
-  pdl_enter();
   constexpr int NPT = ipow(N, DIM);
   constexpr int CB = cells_per_block(DIM, N);
   constexpr int NS = nsym(DIM);

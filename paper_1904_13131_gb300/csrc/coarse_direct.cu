@@ -16,7 +16,6 @@ namespace {
 template <int DIM, int N>
 __global__ void assemble_dense_kernel(const CellArgs<double> a, double* __restrict__ Aout, long long nfree,
                                       const int* __restrict__ cidx) {
-  pdl_enter();
   constexpr int NPT = ipow(N, DIM);
   constexpr int NS = nsym(DIM);
   constexpr int NR = NPT * DIM;
@@ -220,14 +219,13 @@ void launch_assemble(const CellArgs<double>& a, double* A, long long nfree, cons
     attr = true;
   }
   const int threads = NPT * DIM < 256 ? 256 : ((NPT * DIM + 31) / 32) * 32;
-  pdl_launch(assemble_dense_kernel<DIM, N>, a.g.ncells, threads, dyn, st, a, A, nfree, cidx);
+  assemble_dense_kernel<DIM, N><<<a.g.ncells, threads, dyn, st>>>(a, A, nfree, cidx);
 }
 
 // x = A b on the free dofs (one warp per row, fixed summation order); b and x are full level vectors
 // indexed through free_idx, whose constrained entries stay zero.
 __global__ void dense_gemv(const double* __restrict__ A, const double* __restrict__ b, double* __restrict__ x,
                            long long n, const int* __restrict__ free_idx) {
-  pdl_enter();
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32;
   const int lane = threadIdx.x % 32;
   if (warp >= n) return;
@@ -280,7 +278,6 @@ __device__ __forceinline__ bool gj_positive(ff p) { return p.hi > 0.f; }
 // pivot <= 0.
 template <typename E>
 __global__ void gjb_diag(const E* __restrict__ A, int n, int k0, int b, E* __restrict__ W, unsigned* err) {
-  pdl_enter();
   __shared__ E w[GJB][GJB + 1];
   __shared__ E rk[GJB], ck[GJB];
   const int t = threadIdx.x;
@@ -309,7 +306,6 @@ __global__ void gjb_diag(const E* __restrict__ A, int n, int k0, int b, E* __res
 template <typename E>
 __global__ void __launch_bounds__(256) gjb_panels(const E* __restrict__ A, int n, int k0, int b,
                                                   const E* __restrict__ W, E* __restrict__ Y, E* __restrict__ X) {
-  pdl_enter();
   __shared__ E w[GJB][GJB + 1];
   __shared__ E colv[8][GJB + 1], rowv[8][GJB + 1];
   const int r = threadIdx.x, jy = threadIdx.y, t = jy * GJB + r;
@@ -335,7 +331,6 @@ template <typename E>
 __global__ void __launch_bounds__(256) gjb_update(const E* __restrict__ A, E* __restrict__ B, int n, int k0, int b,
                                                   const E* __restrict__ W, const E* __restrict__ Y,
                                                   const E* __restrict__ X) {
-  pdl_enter();
   __shared__ E sA[64][GJB + 1];
   __shared__ E sY[GJB][64 + 1];
   if (blockIdx.x < blockIdx.y) return;  // upper triangle of tiles only
@@ -388,7 +383,6 @@ __global__ void __launch_bounds__(256) gjb_update(const E* __restrict__ A, E* __
 // lower triangle <- upper triangle (the symmetric inverse after the last pass)
 template <typename E>
 __global__ void mirror_lower(E* A, int n) {
-  pdl_enter();
   const long long total = (long long)n * n;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -405,23 +399,21 @@ E* gj_passes(E* A, E* B, long long n, E* work, unsigned* err, cudaStream_t st) {
   const dim3 grid((unsigned)((n + 63) / 64), (unsigned)((n + 63) / 64));
   for (long long k0 = 0; k0 < n; k0 += GJB) {
     const int b = (int)std::min<long long>(GJB, n - k0);
-    pdl_launch(gjb_diag<E>, 1, 256, 0, st, A, (int)n, (int)k0, b, W, err);
-    pdl_launch(gjb_panels<E>, (unsigned)((n + 7) / 8), dim3(GJB, 8), 0, st, A, (int)n, (int)k0, b, W, Y, X);
-    pdl_launch(gjb_update<E>, grid, 256, 0, st, A, B, (int)n, (int)k0, b, W, Y, X);
+    gjb_diag<E><<<1, 256, 0, st>>>(A, (int)n, (int)k0, b, W, err);
+    gjb_panels<E><<<(unsigned)((n + 7) / 8), dim3(GJB, 8), 0, st>>>(A, (int)n, (int)k0, b, W, Y, X);
+    gjb_update<E><<<grid, 256, 0, st>>>(A, B, (int)n, (int)k0, b, W, Y, X);
     std::swap(A, B);
   }
-  pdl_launch(mirror_lower<E>, (int)std::min<long long>((n * n + 255) / 256, 152LL * 16), 256, 0, st, A, (int)n);
+  mirror_lower<E><<<(int)std::min<long long>((n * n + 255) / 256, 152LL * 16), 256, 0, st>>>(A, (int)n);
   return A;
 }
 
 // in place: the n2 doubles of a become double-float pairs, or back
 __global__ void split_to_ff(double* a, long long n2) {
-  pdl_enter();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x)
     reinterpret_cast<ff*>(a)[i] = ff_from(a[i]);
 }
 __global__ void join_from_ff(double* a, long long n2) {
-  pdl_enter();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x)
     a[i] = vec_out(reinterpret_cast<const ff*>(a)[i]);
 }
@@ -436,16 +428,16 @@ double* launch_gj_invert(double* A, double* B, long long n, double* work, unsign
   if (!ff_arith) return gj_passes<double>(A, B, n, work, err, st);
   const long long n2 = n * n;
   const int grid = (int)std::min<long long>((n2 + 255) / 256, 152LL * 16);
-  pdl_launch(split_to_ff, grid, 256, 0, st, A, n2);
+  split_to_ff<<<grid, 256, 0, st>>>(A, n2);
   ff* r = gj_passes<ff>(reinterpret_cast<ff*>(A), reinterpret_cast<ff*>(B), n, reinterpret_cast<ff*>(work), err, st);
   double* out = reinterpret_cast<double*>(r);
-  pdl_launch(join_from_ff, grid, 256, 0, st, out, n2);
+  join_from_ff<<<grid, 256, 0, st>>>(out, n2);
   return out;
 }
 
 void launch_dense_gemv(const double* A, const double* b, double* x, long long n, const int* free_idx, cudaStream_t st) {
   const long long threads = n * 32;
-  pdl_launch(dense_gemv, (int)((threads + 255) / 256), 256, 0, st, A, b, x, n, free_idx);
+  dense_gemv<<<(int)((threads + 255) / 256), 256, 0, st>>>(A, b, x, n, free_idx);
 }
 
 }  // namespace hy

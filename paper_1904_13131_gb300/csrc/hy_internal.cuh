@@ -7,39 +7,11 @@
 // runs of (k+1)*dim values, so no index array is stored.
 #pragma once
 #include <cstdint>
-#include <utility>
 #include <cuda_runtime.h>
 
 #include "ff.cuh"
 
 namespace hy {
-
-// Programmatic dependent launch. Every kernel of the library is launched with pdl_launch and starts with
-// pdl_enter(): it lets the next kernel of the stream be launched as soon as all of its own thread blocks are
-// running, then waits until the kernel ahead of it in the stream has completed and its results are visible.
-// Only the launch latency between dependent kernels is hidden (the V-cycle, CG and smoother chains are
-// dozens of short dependent kernels); no kernel reads anything of its predecessor before the wait. Launched
-// without the attribute (or after a copy), both instructions are no-ops.
-__device__ __forceinline__ void pdl_enter() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-
-template <typename... KArgs, typename... Args>
-inline void pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
-                       Args&&... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
-}
 
 constexpr int MAXN = 5;      // polynomial degree <= 4
 constexpr int MAXMAT = 16;   // materials per level

@@ -9,21 +9,21 @@ void launch_state(const CellArgs<double>& a, T* out, cudaStream_t st) {
   constexpr int CB = cells_per_block(DIM, N);
   constexpr int NPT = ipow(N, DIM);
   const int grid = (a.g.ncells + CB - 1) / CB;
-  pdl_launch(qp_state_kernel<DIM, N, VAR, T>, grid, CB * NPT, 0, st, a, out);
+  qp_state_kernel<DIM, N, VAR, T><<<grid, CB * NPT, 0, st>>>(a, out);
 }
 template <int DIM, int N>
 void launch_residual(const CellArgs<double>& a, cudaStream_t st) {
   constexpr int CB = cells_per_block(DIM, N);
   constexpr int NPT = ipow(N, DIM);
   const int grid = (a.g.ncells + CB - 1) / CB;
-  pdl_launch(residual_kernel<DIM, N>, grid, CB * NPT, 0, st, a);
+  residual_kernel<DIM, N><<<grid, CB * NPT, 0, st>>>(a);
 }
 template <int DIM, int N, typename E>
 void launch_diag(const CellArgs<double>& a, cudaStream_t st) {
   constexpr int CB = cells_per_block(DIM, N);
   constexpr int NPT = ipow(N, DIM);
   const int grid = (a.g.ncells + CB - 1) / CB;
-  pdl_launch(diag_kernel<DIM, N, E>, grid, CB * NPT, 0, st, a);
+  diag_kernel<DIM, N, E><<<grid, CB * NPT, 0, st>>>(a);
 }
 }  // namespace
 

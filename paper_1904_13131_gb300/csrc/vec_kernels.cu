@@ -30,7 +30,6 @@ __device__ __forceinline__ uint32_t cmask_of(const Geom& g, long long node) {
 
 template <typename T, int DIM>
 __global__ void prep_out_kernel(const T* __restrict__ x, T* __restrict__ y, long long n_nodes, Geom g) {
-  pdl_enter();
   for (long long nd = blockIdx.x * (long long)blockDim.x + threadIdx.x; nd < n_nodes; nd += (long long)gridDim.x * blockDim.x) {
     const uint32_t cm = cmask_of<DIM>(g, nd);
 #pragma unroll
@@ -41,7 +40,6 @@ __global__ void prep_out_kernel(const T* __restrict__ x, T* __restrict__ y, long
 // prep_out of every problem of a work list: blockIdx.y = problem, x and y and the lattice from its arguments
 template <typename T, int DIM>
 __global__ void prep_out_list_kernel(const CellArgs<T>* __restrict__ list) {
-  pdl_enter();
   const CellArgs<T>& a = list[blockIdx.y];
   const long long n_nodes = (long long)a.g.L * a.g.L * (DIM == 3 ? a.g.L : 1);
   for (long long nd = blockIdx.x * (long long)blockDim.x + threadIdx.x; nd < n_nodes; nd += (long long)gridDim.x * blockDim.x) {
@@ -57,7 +55,6 @@ __global__ void prep_out_list_kernel(const CellArgs<T>* __restrict__ list) {
 // the cell it ends (if any), with w1[i] the integral of basis function i over the unit interval.
 template <int DIM>
 __global__ void face_load_kernel(double* __restrict__ f, Geom g, int axis, int side, FaceLoad fl) {
-  pdl_enter();
   const long long L = g.L;
   const long long nface = DIM == 3 ? L * L : L;
   const int K = fl.k;
@@ -88,7 +85,6 @@ __global__ void face_load_kernel(double* __restrict__ f, Geom g, int axis, int s
 
 template <typename T, int DIM>
 __global__ void set_constrained_kernel(T* __restrict__ y, long long n_nodes, Geom g, T val) {
-  pdl_enter();
   for (long long nd = blockIdx.x * (long long)blockDim.x + threadIdx.x; nd < n_nodes; nd += (long long)gridDim.x * blockDim.x) {
     const uint32_t cm = cmask_of<DIM>(g, nd);
     if (cm) {
@@ -102,7 +98,6 @@ __global__ void set_constrained_kernel(T* __restrict__ y, long long n_nodes, Geo
 template <int DIM>
 __global__ void lift_kernel(const double* __restrict__ u, double* __restrict__ du0, double factor,
                             const double* __restrict__ fv, long long n_nodes, Geom g) {
-  pdl_enter();
   for (long long nd = blockIdx.x * (long long)blockDim.x + threadIdx.x; nd < n_nodes; nd += (long long)gridDim.x * blockDim.x) {
     const int i[3] = {(int)(nd % g.L), (int)((nd / g.L) % g.L), DIM == 3 ? (int)(nd / ((long long)g.L * g.L)) : 0};
 #pragma unroll
@@ -122,35 +117,30 @@ __global__ void lift_kernel(const double* __restrict__ u, double* __restrict__ d
 
 template <typename T>
 __global__ void invert_kernel(const double* __restrict__ d, T* __restrict__ dinv, long long n) {
-  pdl_enter();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     dinv[i] = T(1.0 / d[i]);
 }
 
 template <typename TA, typename TB>
 __global__ void convert_kernel(const TA* __restrict__ a, TB* __restrict__ b, long long n) {
-  pdl_enter();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     b[i] = TB(a[i]);
 }
 
 template <typename T>
 __global__ void axpby_kernel(T a, const T* x, T b, T* y, long long n) {
-  pdl_enter();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     y[i] = a * x[i] + b * y[i];
 }
 
 template <typename T>
 __global__ void xpay_kernel(const T* __restrict__ x, T a, const T* y, T* z, long long n) {
-  pdl_enter();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     z[i] = x[i] + a * y[i];
 }
 
 template <typename T>
 __global__ void mul_kernel(const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ z, long long n) {
-  pdl_enter();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     z[i] = a[i] * b[i];
 }
@@ -158,7 +148,6 @@ __global__ void mul_kernel(const T* __restrict__ a, const T* __restrict__ b, T* 
 // SplitMix64 (Steele, Lea & Flood 2014) at counter i + 1, top 53 bits mapped to [-1, 1).
 template <typename T>
 __global__ void splitmix_kernel(T* __restrict__ out, long long n, unsigned long long seed) {
-  pdl_enter();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     unsigned long long z = seed + (unsigned long long)(i + 1) * 0x9E3779B97F4A7C15ULL;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
@@ -170,7 +159,6 @@ __global__ void splitmix_kernel(T* __restrict__ out, long long n, unsigned long 
 
 template <typename T>
 __global__ void sub_kernel(const T* __restrict__ b, const T* __restrict__ t, T* __restrict__ r, long long n) {
-  pdl_enter();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     r[i] = b[i] - t[i];
 }
@@ -181,7 +169,6 @@ template <typename T, int PREP>
 __global__ void cheb_init_kernel(const T* __restrict__ b, T* __restrict__ t, const T* __restrict__ dinv,
                                  T* __restrict__ r, T* __restrict__ d, T* __restrict__ x, T inv_theta, bool x0_zero,
                                  long long n, Geom g) {
-  pdl_enter();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const T ri = x0_zero ? b[i] : b[i] - t[i];
     const T di = dinv[i] * ri * inv_theta;
@@ -195,7 +182,6 @@ __global__ void cheb_init_kernel(const T* __restrict__ b, T* __restrict__ t, con
 template <typename T, int PREP>
 __global__ void cheb_step_kernel(T* __restrict__ t, const T* __restrict__ dinv, T* __restrict__ r,
                                  T* __restrict__ d, T* __restrict__ x, T cd, T cr, long long n, Geom g) {
-  pdl_enter();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const T ri = r[i] - t[i];
     const T di = cd * d[i] + cr * dinv[i] * ri;
@@ -211,14 +197,12 @@ __global__ void cheb_step_kernel(T* __restrict__ t, const T* __restrict__ dinv, 
 template <typename T>
 __global__ void axpy_dev_kernel(const double* __restrict__ alpha, double sign, const T* __restrict__ x, T* y,
                                 long long n) {
-  pdl_enter();
   const T a = T(sign * alpha[0]);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     y[i] += a * x[i];
 }
 template <typename T>
 __global__ void xpay_dev_kernel(const T* __restrict__ x, const double* __restrict__ beta, const T* y, T* z, long long n) {
-  pdl_enter();
   const T b = T(beta[0]);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     z[i] = x[i] + b * y[i];
@@ -227,7 +211,6 @@ __global__ void xpay_dev_kernel(const T* __restrict__ x, const double* __restric
 // Scalars of one CG step of the eigenvalue estimate, kept on the device. s = {rz, rz0, pq, rzn, alpha,
 // beta, stopped, count}; hist = alpha[iters] followed by beta[iters].
 __global__ void eig_alpha_kernel(double* s, double* hist, int it) {
-  pdl_enter();
   const bool stopped = s[6] != 0.0;
   const double alpha = stopped ? 0.0 : s[0] / s[2];
   s[4] = alpha;
@@ -238,7 +221,6 @@ __global__ void eig_alpha_kernel(double* s, double* hist, int it) {
 // op 1: converged = sqrt(rr) <= tol; op 2: beta = rzn / rz, rz = rzn. Once converged or not_spd is set it
 // stays set and alpha = beta = 0: later iterations of a finished problem leave x and r unchanged.
 __global__ void pcg_scalar_kernel(double* s, int op) {
-  pdl_enter();
   const bool finished = s[7] != 0.0 || s[8] != 0.0;
   if (op == 0) {
     const double pq = s[1];
@@ -262,7 +244,6 @@ __global__ void pcg_scalar_kernel(double* s, int op) {
   }
 }
 __global__ void eig_beta_kernel(double* s, double* hist, int it, int iters) {
-  pdl_enter();
   if (s[6] != 0.0) {
     s[5] = 0.0;
     return;
@@ -280,7 +261,6 @@ __global__ void eig_beta_kernel(double* s, double* hist, int it, int iters) {
 template <typename T>
 __global__ void dot_partial_kernel(const T* __restrict__ a, const T* __restrict__ b, long long n,
                                    double* __restrict__ partials) {
-  pdl_enter();
   __shared__ double sh[TPB];
   double s = 0.0;
   for (long long i = blockIdx.x * (long long)TPB + threadIdx.x; i < n; i += (long long)DOT_BLOCKS * TPB)
@@ -295,7 +275,6 @@ __global__ void dot_partial_kernel(const T* __restrict__ a, const T* __restrict_
 }
 
 __global__ void dot_final_kernel(const double* __restrict__ partials, double* __restrict__ out) {
-  pdl_enter();
   __shared__ double sh[TPB];
   double s = 0.0;
   for (int i = threadIdx.x; i < DOT_BLOCKS; i += TPB) s += partials[i];
@@ -312,7 +291,6 @@ template <typename T, int DIM>
 __global__ void sweep_kernel(const T* __restrict__ in, T* __restrict__ out, int Li0, int Li1, int Lo0, int Lo1,
                              int Lo2, int axis, const int* __restrict__ start, const T* __restrict__ w, int E,
                              bool add, bool use_mask_in, Geom gin, bool use_mask_out, Geom gout) {
-  pdl_enter();
   const long long n_out = (long long)Lo0 * Lo1 * (DIM == 3 ? Lo2 : 1) * DIM;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n_out;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -339,8 +317,8 @@ __global__ void sweep_kernel(const T* __restrict__ in, T* __restrict__ out, int 
 
 template <typename T>
 void launch_prep_out(const T* x, T* y, long long n_nodes, int dim, const Geom& g, cudaStream_t st) {
-  if (dim == 2) pdl_launch(prep_out_kernel<T, 2>, grid_for(n_nodes), TPB, 0, st, x, y, n_nodes, g);
-  else pdl_launch(prep_out_kernel<T, 3>, grid_for(n_nodes), TPB, 0, st, x, y, n_nodes, g);
+  if (dim == 2) prep_out_kernel<T, 2><<<grid_for(n_nodes), TPB, 0, st>>>(x, y, n_nodes, g);
+  else prep_out_kernel<T, 3><<<grid_for(n_nodes), TPB, 0, st>>>(x, y, n_nodes, g);
 }
 template <typename T>
 void launch_prep_out_list(const CellArgs<T>* list, int count, int dim, long long max_nodes, cudaStream_t st) {
@@ -350,91 +328,91 @@ void launch_prep_out_list(const CellArgs<T>* list, int count, int dim, long long
   if (gx > cap) gx = cap;
   if (gx < 1) gx = 1;
   const dim3 grid((unsigned)gx, (unsigned)count);
-  if (dim == 2) pdl_launch(prep_out_list_kernel<T, 2>, grid, TPB, 0, st, list);
-  else pdl_launch(prep_out_list_kernel<T, 3>, grid, TPB, 0, st, list);
+  if (dim == 2) prep_out_list_kernel<T, 2><<<grid, TPB, 0, st>>>(list);
+  else prep_out_list_kernel<T, 3><<<grid, TPB, 0, st>>>(list);
 }
 template <typename T>
 void launch_zero_constrained(T* y, long long n_nodes, int dim, const Geom& g, cudaStream_t st) {
-  if (dim == 2) pdl_launch(set_constrained_kernel<T, 2>, grid_for(n_nodes), TPB, 0, st, y, n_nodes, g, T(0));
-  else pdl_launch(set_constrained_kernel<T, 3>, grid_for(n_nodes), TPB, 0, st, y, n_nodes, g, T(0));
+  if (dim == 2) set_constrained_kernel<T, 2><<<grid_for(n_nodes), TPB, 0, st>>>(y, n_nodes, g, T(0));
+  else set_constrained_kernel<T, 3><<<grid_for(n_nodes), TPB, 0, st>>>(y, n_nodes, g, T(0));
 }
 template <typename T>
 void launch_set_constrained_one(T* y, long long n_nodes, int dim, const Geom& g, cudaStream_t st) {
-  if (dim == 2) pdl_launch(set_constrained_kernel<T, 2>, grid_for(n_nodes), TPB, 0, st, y, n_nodes, g, T(1));
-  else pdl_launch(set_constrained_kernel<T, 3>, grid_for(n_nodes), TPB, 0, st, y, n_nodes, g, T(1));
+  if (dim == 2) set_constrained_kernel<T, 2><<<grid_for(n_nodes), TPB, 0, st>>>(y, n_nodes, g, T(1));
+  else set_constrained_kernel<T, 3><<<grid_for(n_nodes), TPB, 0, st>>>(y, n_nodes, g, T(1));
 }
 template <typename T>
 void launch_invert(const double* d, T* dinv, long long n, cudaStream_t st) {
-  pdl_launch(invert_kernel<T>, grid_for(n), TPB, 0, st, d, dinv, n);
+  invert_kernel<T><<<grid_for(n), TPB, 0, st>>>(d, dinv, n);
 }
 template <typename TA, typename TB>
 void launch_convert(const TA* a, TB* b, long long n, cudaStream_t st) {
-  pdl_launch(convert_kernel<TA, TB>, grid_for(n), TPB, 0, st, a, b, n);
+  convert_kernel<TA, TB><<<grid_for(n), TPB, 0, st>>>(a, b, n);
 }
 template <typename T>
 void launch_axpby(T a, const T* x, T b, T* y, long long n, cudaStream_t st) {
-  pdl_launch(axpby_kernel<T>, grid_for(n), TPB, 0, st, a, x, b, y, n);
+  axpby_kernel<T><<<grid_for(n), TPB, 0, st>>>(a, x, b, y, n);
 }
 template <typename T>
 void launch_xpay(const T* x, T a, const T* y, T* z, long long n, cudaStream_t st) {
-  pdl_launch(xpay_kernel<T>, grid_for(n), TPB, 0, st, x, a, y, z, n);
+  xpay_kernel<T><<<grid_for(n), TPB, 0, st>>>(x, a, y, z, n);
 }
 template <typename T>
 void launch_mul(const T* a, const T* b, T* z, long long n, cudaStream_t st) {
-  pdl_launch(mul_kernel<T>, grid_for(n), TPB, 0, st, a, b, z, n);
+  mul_kernel<T><<<grid_for(n), TPB, 0, st>>>(a, b, z, n);
 }
 template <typename T>
 void launch_splitmix(T* out, long long n, unsigned long long seed, cudaStream_t st) {
-  pdl_launch(splitmix_kernel<T>, grid_for(n), TPB, 0, st, out, n, seed);
+  splitmix_kernel<T><<<grid_for(n), TPB, 0, st>>>(out, n, seed);
 }
 template <typename T>
 void launch_axpy_dev(const double* alpha, double sign, const T* x, T* y, long long n, cudaStream_t st) {
-  pdl_launch(axpy_dev_kernel<T>, grid_for(n), TPB, 0, st, alpha, sign, x, y, n);
+  axpy_dev_kernel<T><<<grid_for(n), TPB, 0, st>>>(alpha, sign, x, y, n);
 }
 template <typename T>
 void launch_xpay_dev(const T* x, const double* beta, const T* y, T* z, long long n, cudaStream_t st) {
-  pdl_launch(xpay_dev_kernel<T>, grid_for(n), TPB, 0, st, x, beta, y, z, n);
+  xpay_dev_kernel<T><<<grid_for(n), TPB, 0, st>>>(x, beta, y, z, n);
 }
-void launch_pcg_scalar(double* s, int op, cudaStream_t st) { pdl_launch(pcg_scalar_kernel, 1, 1, 0, st, s, op); }
-void launch_eig_alpha(double* s, double* hist, int it, cudaStream_t st) { pdl_launch(eig_alpha_kernel, 1, 1, 0, st, s, hist, it); }
+void launch_pcg_scalar(double* s, int op, cudaStream_t st) { pcg_scalar_kernel<<<1, 1, 0, st>>>(s, op); }
+void launch_eig_alpha(double* s, double* hist, int it, cudaStream_t st) { eig_alpha_kernel<<<1, 1, 0, st>>>(s, hist, it); }
 void launch_eig_beta(double* s, double* hist, int it, int iters, cudaStream_t st) {
-  pdl_launch(eig_beta_kernel, 1, 1, 0, st, s, hist, it, iters);
+  eig_beta_kernel<<<1, 1, 0, st>>>(s, hist, it, iters);
 }
 template <typename T>
 void launch_sub(const T* b, const T* t, T* r, long long n, cudaStream_t st) {
-  pdl_launch(sub_kernel<T>, grid_for(n), TPB, 0, st, b, t, r, n);
+  sub_kernel<T><<<grid_for(n), TPB, 0, st>>>(b, t, r, n);
 }
 template <typename T>
 void launch_cheb_init(const T* b, T* t, const T* dinv, T* r, T* d, T* x, T inv_theta, bool x0_zero, long long n,
                       const Geom* prep, int dim, cudaStream_t st) {
   const Geom g = prep ? *prep : Geom{};
-  if (!prep) pdl_launch(cheb_init_kernel<T, 0>, grid_for(n), TPB, 0, st, b, t, dinv, r, d, x, inv_theta, x0_zero, n, g);
-  else if (dim == 2) pdl_launch(cheb_init_kernel<T, 2>, grid_for(n), TPB, 0, st, b, t, dinv, r, d, x, inv_theta, x0_zero, n, g);
-  else pdl_launch(cheb_init_kernel<T, 3>, grid_for(n), TPB, 0, st, b, t, dinv, r, d, x, inv_theta, x0_zero, n, g);
+  if (!prep) cheb_init_kernel<T, 0><<<grid_for(n), TPB, 0, st>>>(b, t, dinv, r, d, x, inv_theta, x0_zero, n, g);
+  else if (dim == 2) cheb_init_kernel<T, 2><<<grid_for(n), TPB, 0, st>>>(b, t, dinv, r, d, x, inv_theta, x0_zero, n, g);
+  else cheb_init_kernel<T, 3><<<grid_for(n), TPB, 0, st>>>(b, t, dinv, r, d, x, inv_theta, x0_zero, n, g);
 }
 template <typename T>
 void launch_cheb_step(T* t, const T* dinv, T* r, T* d, T* x, T cd, T cr, long long n, const Geom* prep, int dim,
                       cudaStream_t st) {
   const Geom g = prep ? *prep : Geom{};
-  if (!prep) pdl_launch(cheb_step_kernel<T, 0>, grid_for(n), TPB, 0, st, t, dinv, r, d, x, cd, cr, n, g);
-  else if (dim == 2) pdl_launch(cheb_step_kernel<T, 2>, grid_for(n), TPB, 0, st, t, dinv, r, d, x, cd, cr, n, g);
-  else pdl_launch(cheb_step_kernel<T, 3>, grid_for(n), TPB, 0, st, t, dinv, r, d, x, cd, cr, n, g);
+  if (!prep) cheb_step_kernel<T, 0><<<grid_for(n), TPB, 0, st>>>(t, dinv, r, d, x, cd, cr, n, g);
+  else if (dim == 2) cheb_step_kernel<T, 2><<<grid_for(n), TPB, 0, st>>>(t, dinv, r, d, x, cd, cr, n, g);
+  else cheb_step_kernel<T, 3><<<grid_for(n), TPB, 0, st>>>(t, dinv, r, d, x, cd, cr, n, g);
 }
 void launch_face_load(double* f, int dim, const Geom& g, int face, const FaceLoad& fl, cudaStream_t st) {
   const long long L = g.L;
   const long long nface = dim == 3 ? L * L : L;
-  if (dim == 2) pdl_launch(face_load_kernel<2>, grid_for(nface), TPB, 0, st, f, g, face / 2, face % 2, fl);
-  else pdl_launch(face_load_kernel<3>, grid_for(nface), TPB, 0, st, f, g, face / 2, face % 2, fl);
+  if (dim == 2) face_load_kernel<2><<<grid_for(nface), TPB, 0, st>>>(f, g, face / 2, face % 2, fl);
+  else face_load_kernel<3><<<grid_for(nface), TPB, 0, st>>>(f, g, face / 2, face % 2, fl);
 }
 void launch_lift(const double* u, double* du0, double factor, const double* fv, long long n_nodes, int dim,
                  const Geom& g, cudaStream_t st) {
-  if (dim == 2) pdl_launch(lift_kernel<2>, grid_for(n_nodes), TPB, 0, st, u, du0, factor, fv, n_nodes, g);
-  else pdl_launch(lift_kernel<3>, grid_for(n_nodes), TPB, 0, st, u, du0, factor, fv, n_nodes, g);
+  if (dim == 2) lift_kernel<2><<<grid_for(n_nodes), TPB, 0, st>>>(u, du0, factor, fv, n_nodes, g);
+  else lift_kernel<3><<<grid_for(n_nodes), TPB, 0, st>>>(u, du0, factor, fv, n_nodes, g);
 }
 template <typename T>
 void launch_dot(const T* a, const T* b, long long n, double* partials, double* out, cudaStream_t st) {
-  pdl_launch(dot_partial_kernel<T>, DOT_BLOCKS, TPB, 0, st, a, b, n, partials);
-  pdl_launch(dot_final_kernel, 1, TPB, 0, st, partials, out);
+  dot_partial_kernel<T><<<DOT_BLOCKS, TPB, 0, st>>>(a, b, n, partials);
+  dot_final_kernel<<<1, TPB, 0, st>>>(partials, out);
 }
 template <typename T>
 void launch_sweep(const T* in, T* out, int dim, const int Lin[3], const int Lout[3], int axis, const int* start,
@@ -443,10 +421,10 @@ void launch_sweep(const T* in, T* out, int dim, const int Lin[3], const int Lout
   Geom gi = mask_in ? *mask_in : Geom{};
   Geom go = mask_out ? *mask_out : Geom{};
   if (dim == 2)
-    pdl_launch(sweep_kernel<T, 2>, grid_for(n_out), TPB, 0, st, in, out, Lin[0], Lin[1], Lout[0], Lout[1], Lout[2], axis,
+    sweep_kernel<T, 2><<<grid_for(n_out), TPB, 0, st>>>(in, out, Lin[0], Lin[1], Lout[0], Lout[1], Lout[2], axis,
                                                         start, w, E, add, mask_in != nullptr, gi, mask_out != nullptr, go);
   else
-    pdl_launch(sweep_kernel<T, 3>, grid_for(n_out), TPB, 0, st, in, out, Lin[0], Lin[1], Lout[0], Lout[1], Lout[2], axis,
+    sweep_kernel<T, 3><<<grid_for(n_out), TPB, 0, st>>>(in, out, Lin[0], Lin[1], Lout[0], Lout[1], Lout[2], axis,
                                                         start, w, E, add, mask_in != nullptr, gi, mask_out != nullptr, go);
 }
 

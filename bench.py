@@ -244,7 +244,7 @@ def solve_latency(torch, api, inputs, dev):
                          "cg_iterations_max": rep["cg_iterations_max"], "newton_iterations": rep["newton_iterations"],
                          "newton_total_ms": rep["total_ms"], "setup_ms_total": rep["setup_ms_total"],
                          "setup_fraction": rep["setup_ms_total"] / rep["total_ms"],
-                         "setups_reused": rep["setups_reused"],
+                         "setups_reused": rep["setups_reused"], "setup_phase_ms": rep["setup_phase_ms"],
                          "coarse_degree": c.level_info(0)["coarse_degree"]}
             sols[name] = u.cpu().numpy()
     for name in sols:

@@ -272,6 +272,11 @@ typedef struct {
   double setup_ms_total;      /* time spent linearising (caches, diagonals, eigenvalue estimates) */
   double total_ms;            /* whole call */
   int setups_reused;          /* linearisations that kept the previous V-cycle setup (solver setup_reuse) */
+  double setup_phase_ms[6];   /* device time of the linearisations' phases, summed: carry the displacement
+                                 down; Gauss-point states and diagonals; kernel-form autotuning; smoother
+                                 eigenvalue estimates; coarse setup on the context's stream (the wait for the
+                                 exact inverse, or the coarse eigenvalue estimate); and, measured on the side
+                                 stream where it overlaps the others, the exact coarse inverse itself */
 } hy_newton_report;
 
 /* Fill p with the defaults in brackets above (zero tractions and prescribed values). */

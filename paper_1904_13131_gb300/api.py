@@ -18,6 +18,9 @@ STATUS = {0: "HY_OK", 1: "HY_ERR_ARG", 2: "HY_ERR_STATE", 3: "HY_ERR_OOM", 4: "H
           6: "HY_ERR_NOCONV", 7: "HY_ERR_TIMEOUT", 8: "HY_ERR_UNSUPPORTED"}
 VARIANTS = {"T4": 0, "T2": 1, "FC": 2, "SC": 3, "NC": 4}
 LAW_LOG2, LAW_J2 = 0, 1  # hy_law
+# the linearisation phases of hy_newton_report.setup_phase_ms
+SETUP_PHASES = ("carry_down", "state_and_diagonal", "autotune", "smoother_eigenvalues", "coarse_setup_wait",
+                "coarse_inverse_side_stream")
 F64, F32, FF = 0, 1, 2  # hy_dtype; FF: double-float action on FP64 vectors
 
 # every symbol the header declares (checked by the CPU test suite)
@@ -63,7 +66,8 @@ class NewtonReport(ctypes.Structure):
                 ("cg_iterations_total", ctypes.c_int), ("cg_iterations_max", ctypes.c_int),
                 ("final_residual", ctypes.c_double), ("backtracks", ctypes.c_int), ("n_solves", ctypes.c_int),
                 ("solve_cg_iterations", ctypes.c_int * 256), ("solve_ms", ctypes.c_double * 256),
-                ("setup_ms_total", ctypes.c_double), ("total_ms", ctypes.c_double), ("setups_reused", ctypes.c_int)]
+                ("setup_ms_total", ctypes.c_double), ("total_ms", ctypes.c_double), ("setups_reused", ctypes.c_int),
+                ("setup_phase_ms", ctypes.c_double * 6)]
 
 
 class Request(ctypes.Structure):
@@ -415,7 +419,8 @@ class Context:
                   "final_residual": rep.final_residual, "backtracks": rep.backtracks,
                   "n_solves": rep.n_solves, "solve_cg_iterations": list(rep.solve_cg_iterations[: min(rep.n_solves, 256)]),
                   "solve_ms": list(rep.solve_ms[: min(rep.n_solves, 256)]), "setup_ms_total": rep.setup_ms_total,
-                  "total_ms": rep.total_ms, "setups_reused": rep.setups_reused}
+                  "total_ms": rep.total_ms, "setups_reused": rep.setups_reused,
+                  "setup_phase_ms": dict(zip(SETUP_PHASES, rep.setup_phase_ms))}
         self._ck(st)
         return report
 

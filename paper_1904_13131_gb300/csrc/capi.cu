@@ -24,6 +24,8 @@
 
 using namespace hy;
 
+constexpr int SETUP_PHASES = 5;  // carry down, state + diagonal, autotune, smoother estimates, coarse setup
+
 namespace {
 
 // Named NVTX range over a solver phase (linearisation, PCG, V-cycle, Newton load step) for profilers and
@@ -253,7 +255,11 @@ struct hy_ctx {
   std::vector<std::pair<void*, size_t>> allocs;
   // the exact coarse inverse is built on a side stream, overlapping the rest of the linearisation
   cudaStream_t side = nullptr;
-  cudaEvent_t ev_side_fork = nullptr, ev_side_join = nullptr;
+  cudaEvent_t ev_side_fork = nullptr, ev_side_join = nullptr, ev_side_start = nullptr;
+  bool side_timed = false;
+  // phase events of the last linearisation (PhaseTimer)
+  cudaEvent_t ev_phase[6] = {};
+  int phases_recorded = 0;
   unsigned* h_err_side = nullptr;  // pinned: the side stream's error word, read after the join
   bool side_pending = false;
   // reuse of the V-cycle setup (solver parameter setup_reuse): the coarsest level's displacement at the
@@ -913,11 +919,14 @@ hy_status coarse_direct_setup(hy_ctx* ctx) {
   if (!ctx->side) {
     HY_CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
     HY_CK(cudaEventCreateWithFlags(&ctx->ev_side_fork, cudaEventDisableTiming));
-    HY_CK(cudaEventCreateWithFlags(&ctx->ev_side_join, cudaEventDisableTiming));
+    HY_CK(cudaEventCreate(&ctx->ev_side_join));
+    HY_CK(cudaEventCreate(&ctx->ev_side_start));
     HY_CK(cudaMallocHost((void**)&ctx->h_err_side, sizeof(unsigned)));
   }
   HY_CK(cudaEventRecord(ctx->ev_side_fork, ctx->stream));
   HY_CK(cudaStreamWaitEvent(ctx->side, ctx->ev_side_fork, 0));
+  HY_CK(cudaEventRecord(ctx->ev_side_start, ctx->side));
+  ctx->side_timed = true;
   unsigned* err = ctx->d_err + 1;
   HY_CK(cudaMemsetAsync(C.d_Ainv, 0, sizeof(double) * n * n, ctx->side));
   HY_CK(cudaMemsetAsync(err, 0, sizeof(unsigned), ctx->side));
@@ -1083,11 +1092,27 @@ hy_status autotune_level(hy_ctx* ctx, int l) {
 }
 
 // Verbose phase timer of set_displacement (synchronises the stream, so only when HY_VERBOSE=1).
+// Phase events of set_displacement: recorded on the context's stream at the start and after each phase (no
+// synchronisation); setup_phases_ms reads them once the stream has been synchronised. With HY_VERBOSE=1 each
+// phase is also synchronised and printed.
 struct PhaseTimer {
   hy_ctx* ctx;
+  int next = 0;
   std::chrono::steady_clock::time_point t;
-  explicit PhaseTimer(hy_ctx* c) : ctx(c), t(std::chrono::steady_clock::now()) {}
+  explicit PhaseTimer(hy_ctx* c) : ctx(c), t(std::chrono::steady_clock::now()) {
+    if (!ctx->ev_phase[0])
+      for (cudaEvent_t& e : ctx->ev_phase) cudaEventCreate(&e);
+    ctx->phases_recorded = 0;
+    record();
+  }
+  void record() {
+    if (next < SETUP_PHASES + 1 && cudaEventRecord(ctx->ev_phase[next], ctx->stream) == cudaSuccess) {
+      ++next;
+      ctx->phases_recorded = next;
+    }
+  }
   void mark(const char* what) {
+    record();
     if (!ctx->verbose) return;
     cudaStreamSynchronize(ctx->stream);
     const auto now = std::chrono::steady_clock::now();
@@ -1096,6 +1121,21 @@ struct PhaseTimer {
     t = now;
   }
 };
+
+// Device time of the phases of the last set_displacement (the stream must have reached its end): carry down,
+// state and diagonal, autotune, smoother eigenvalue estimates, coarse setup (the join of the exact inverse or
+// the coarse eigenvalue estimate), then the side stream's exact coarse inverse itself (0 if none).
+void setup_phases_ms(hy_ctx* ctx, double out[SETUP_PHASES + 1]) {
+  for (int i = 0; i <= SETUP_PHASES; ++i) out[i] = 0.0;
+  for (int i = 0; i + 1 < ctx->phases_recorded; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->ev_phase[i], ctx->ev_phase[i + 1]) == cudaSuccess) out[i] = ms;
+  }
+  if (ctx->side_timed) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->ev_side_start, ctx->ev_side_join) == cudaSuccess) out[SETUP_PHASES] = ms;
+  }
+}
 
 hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
   const Range range("set_displacement");
@@ -1147,6 +1187,7 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
   }
   ctx->setup_valid = false;
   ctx->last_setup_reused = reuse;
+  ctx->side_timed = false;
   hy_status coarse_st = HY_OK;
   if (ctx->sp.coarse_solver >= 1 && !reuse) coarse_st = coarse_direct_setup(ctx);  // runs on the side stream
   if (coarse_st != HY_OK) return coarse_st;
@@ -1979,6 +2020,9 @@ void hy_destroy(hy_ctx* ctx) {
   if (ctx->side) cudaStreamDestroy(ctx->side);
   if (ctx->ev_side_fork) cudaEventDestroy(ctx->ev_side_fork);
   if (ctx->ev_side_join) cudaEventDestroy(ctx->ev_side_join);
+  if (ctx->ev_side_start) cudaEventDestroy(ctx->ev_side_start);
+  for (cudaEvent_t e : ctx->ev_phase)
+    if (e) cudaEventDestroy(e);
   if (ctx->h_pcg_scal) cudaFreeHost(ctx->h_pcg_scal);
   if (ctx->h_err_side) cudaFreeHost(ctx->h_err_side);
   delete ctx;
@@ -2492,6 +2536,11 @@ hy_status hy_newton_solve(hy_ctx* ctx, const hy_newton_params* p, double* u, hy_
       HY_CK(cudaStreamSynchronize(ctx->stream));
       rl.setup_ms_total += ms_since(t_setup);
       if (ctx->last_setup_reused) rl.setups_reused++;
+      {
+        double ph[SETUP_PHASES + 1];
+        setup_phases_ms(ctx, ph);
+        for (int i = 0; i <= SETUP_PHASES; ++i) rl.setup_phase_ms[i] += ph[i];
+      }
       // rhs = -R - Z A du0 (lifting of the prescribed increment into the first solve)
       HY_CK(cudaMemcpyAsync(rhs, R, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
       if (lift2 > 0.0) {

@@ -1655,25 +1655,35 @@ residual_kernel(const CellArgs<double> a) {
 // Diagonal of the tangent, d += diag A(u). For node a and component c:
 //   A_{ac,ac} = sum_q W [ g_a . tau . g_a + c1 (|g_a|^2 + g_{a,c}^2)/2 + c2 g_{a,c}^2 ],  g_a = F^{-T} Grad N_a,
 // the geometric and material parts of Eq. algebraic_tangent with the action of Eq. simplified_action.
-// The Gauss-point state is FP64; the O((k+1)^(2 dim)) sum over (node, point) pairs runs in E: double, or
-// double-float (the FP32 pipe, about 48 significant bits).
+//   With r = grad_xi N_a(q) the reference gradient and g_a = M^T r (M: the point's map, carrying 1/h or, on
+// curved cells, the inverse Jacobian), the entry is a quadratic form in r,
+//   A_{ac,ac} = sum_q sum_{J,L} r_J r_L K^c_{JL}(q),   K^c = M (tau + c1/2 I) M^T + (c1/2 + c2) m_c m_c^T,
+// m_c the column c of M (weights folded into tau, c1, c2). On the tensor-product element r_J r_L is a
+// product of one 1D factor per direction -- S^2, S S' or S'^2 (S the nodal basis at the Gauss points, S' its
+// derivative) as the direction occurs 0, 1 or 2 times in (J, L) -- so the sum over q factorises into dim 1D
+// contractions per (J, L) pair and component: (k+1)^(dim+1) multiply-adds per field and cell instead of the
+// (k+1)^(2 dim) of a sum over (node, point) pairs.
+//   One thread per (cell, Gauss point) forms the FP64 state and K^c; per component c the NS fields K^c_{JL}
+// (J <= L, the off-diagonal pairs doubled) go to shared memory in E and are contracted along x, y (and z)
+// by the same threads, which end as (cell, node) and hold the entry. E is double, or double-float (the
+// FP32 pipe, about 48 significant bits).
 template <int DIM, int N, typename E>
 __global__ void __launch_bounds__(cells_per_block(DIM, N) * ipow(N, DIM))
 diag_kernel(const CellArgs<double> a) {
   constexpr int NPT = ipow(N, DIM);
   constexpr int CB = cells_per_block(DIM, N);
   constexpr int NS = nsym(DIM);
-  __shared__ Smem<DIM, N, double> s;
-  __shared__ E Sd[MAXN][MAXN];
-  __shared__ E st[CB][NS + 2][NPT];
   static_assert(sizeof(E) == sizeof(double), "E values reuse double buffers");
+  static_assert(NS <= DIM * DIM && NS <= 2 * DIM, "the fields fit the flux and displacement buffers");
+  __shared__ Smem<DIM, N, double> s;
+  __shared__ E tab[3][MAXN][MAXN];  // tab[k][q][a] = S[q][a]^(2-k) S'[q][a]^k
   load_tables<DIM, N>(s, a);
-  // S in E in the (here unused) Dh table
-  E(*Se)[MAXN] = reinterpret_cast<E(*)[MAXN]>(&s.Dh[0][0]);
-  __syncthreads();
   if (threadIdx.x < MAXN * MAXN) {
-    Sd[threadIdx.x / MAXN][threadIdx.x % MAXN] = E(a.b.Sd[threadIdx.x / MAXN][threadIdx.x % MAXN]);
-    Se[threadIdx.x / MAXN][threadIdx.x % MAXN] = E(a.b.S[threadIdx.x / MAXN][threadIdx.x % MAXN]);
+    const int q = threadIdx.x / MAXN, n = threadIdx.x % MAXN;
+    const double sv = a.b.S[q][n], dv = a.b.Sd[q][n];
+    tab[0][q][n] = E(sv * sv);
+    tab[1][q][n] = E(sv * dv);
+    tab[2][q][n] = E(dv * dv);
   }
   const int cl = threadIdx.x / NPT;
   const Pt<DIM, N> pt(threadIdx.x % NPT);
@@ -1682,7 +1692,7 @@ diag_kernel(const CellArgs<double> a) {
   const CellLoc<DIM, N> loc(a.g, active ? cell : 0, pt);
   double* b0 = &s.b0[cl][0][0];
   double* b1 = &s.b1[cl][0][0];
-  double* bp = &s.bp[cl][0][0];
+  __syncthreads();
 #pragma unroll
   for (int c = 0; c < DIM; ++c) b0[c * NPT + pt.p] = active ? a.u64[(long long)loc.node * DIM + c] : 0.0;
   __syncthreads();
@@ -1707,49 +1717,97 @@ diag_kernel(const CellArgs<double> a) {
   neo_hooke_state<DIM>(F, s.mu[id], s.lam[id], a.mt.law, curved ? wdet : s.W[pt.p], curved ? 1.0 : inv_h, false, 0.0,
                        M, tau, c1, c2);
   if (curved) premultiply<DIM>(invJ, M);
-  // per-point state to shared memory in E: M (DIM^2 rows, in the flux buffer), tau, c1, c2 (NS + 2 rows)
-  E(*Me)[DIM * DIM][NPT] = reinterpret_cast<E(*)[DIM * DIM][NPT]>(&s.bp[0][0][0]);
-#pragma unroll
-  for (int i = 0; i < DIM * DIM; ++i) Me[cl][i][pt.p] = E(M[i / DIM][i % DIM]);
-#pragma unroll
-  for (int i = 0; i < NS; ++i) st[cl][i][pt.p] = E(tau[i]);
-  st[cl][NS][pt.p] = E(c1);
-  st[cl][NS + 1][pt.p] = E(c2);
-  __syncthreads();
-  // thread now plays node a = pt.p
-  E dsum[DIM];
-#pragma unroll
-  for (int c = 0; c < DIM; ++c) dsum[c] = E(0);
-  for (int q = 0; q < NPT; ++q) {
-    const int q0 = q % N, q1 = (q / N) % N, q2 = DIM == 3 ? q / (N * N) : 0;
-    E gr[DIM];  // d N_a / d xi at q
-    const E s0 = Se[q0][pt.pc[0]], s1 = Se[q1][pt.pc[1]];
-    const E s2 = DIM == 3 ? Se[q2][pt.pc[2]] : E(1);
-    gr[0] = Sd[q0][pt.pc[0]] * s1 * s2;
-    gr[1] = s0 * Sd[q1][pt.pc[1]] * s2;
-    if (DIM == 3) gr[DIM - 1] = s0 * s1 * Sd[q2][pt.pc[2]];
-    E ga[DIM];
-#pragma unroll
-    for (int j = 0; j < DIM; ++j) {
-      E acc = gr[0] * Me[cl][0 * DIM + j][q];
-#pragma unroll
-      for (int J = 1; J < DIM; ++J) acc = fma(gr[J], Me[cl][J * DIM + j][q], acc);
-      ga[j] = acc;
-    }
-    E geo = E(0), nrm = E(0);
+  // G = M (tau + c1/2 I) M^T (upper triangle) and kappa = c1/2 + c2
+  double G[NS];
+  {
+    double T[DIM][DIM];
 #pragma unroll
     for (int al = 0; al < NS; ++al) {
-      const int i = vi<DIM>(al), j = vj<DIM>(al);
-      const E gij = ga[i] * ga[j];
-      geo = fma(i == j ? gij : gij + gij, st[cl][al][q], geo);
+      T[vi<DIM>(al)][vj<DIM>(al)] = tau[al];
+      T[vj<DIM>(al)][vi<DIM>(al)] = tau[al];
     }
 #pragma unroll
-    for (int j = 0; j < DIM; ++j) nrm = fma(ga[j], ga[j], nrm);
-    const E hc1 = E(0.5) * st[cl][NS][q], qc2 = st[cl][NS + 1][q];
+    for (int i = 0; i < DIM; ++i) T[i][i] += 0.5 * c1;
+    double MT[DIM][DIM];
 #pragma unroll
-    for (int c = 0; c < DIM; ++c) {
-      const E gc2 = ga[c] * ga[c];
-      dsum[c] = dsum[c] + (geo + fma(hc1, nrm + gc2, qc2 * gc2));
+    for (int J = 0; J < DIM; ++J)
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) {
+        double acc = M[J][0] * T[0][j];
+#pragma unroll
+        for (int i = 1; i < DIM; ++i) acc = fma(M[J][i], T[i][j], acc);
+        MT[J][j] = acc;
+      }
+#pragma unroll
+    for (int al = 0; al < NS; ++al) {
+      const int J = vi<DIM>(al), L = vj<DIM>(al);
+      double acc = MT[J][0] * M[L][0];
+#pragma unroll
+      for (int j = 1; j < DIM; ++j) acc = fma(MT[J][j], M[L][j], acc);
+      G[al] = acc;
+    }
+  }
+  const double kappa = 0.5 * c1 + c2;
+  // field buffers: A = the first NS rows of the cell's flux buffer, B = its two displacement buffers
+  E(*A)[DIM * DIM][NPT] = reinterpret_cast<E(*)[DIM * DIM][NPT]>(&s.bp[0][0][0]);
+  E(*B0)[DIM][NPT] = reinterpret_cast<E(*)[DIM][NPT]>(&s.b0[0][0][0]);
+  E(*B1)[DIM][NPT] = reinterpret_cast<E(*)[DIM][NPT]>(&s.b1[0][0][0]);
+  auto Bf = [&](int f, int p) -> E& { return f < DIM ? B0[cl][f][p] : B1[cl][f - DIM][p]; };
+  // the 1D factor of pair al along direction d: how often d occurs in (vi, vj)
+  auto fac = [](int al, int d) { return (vi<DIM>(al) == d ? 1 : 0) + (vj<DIM>(al) == d ? 1 : 0); };
+  E dsum[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    __syncthreads();  // the buffers are free: the state reads (c = 0) or the last sweep (c > 0) are done
+#pragma unroll
+    for (int al = 0; al < NS; ++al) {
+      const int J = vi<DIM>(al), L = vj<DIM>(al);
+      const double k = fma(kappa * M[J][c], M[L][c], G[al]);
+      A[cl][al][pt.p] = active ? E(J == L ? k : 2.0 * k) : E(0);
+    }
+    __syncthreads();
+    // x: (q0, q1, q2) -> (a0, q1, q2), A -> B
+    {
+      const int a0 = pt.pc[0], base = pt.base(0);
+#pragma unroll
+      for (int al = 0; al < NS; ++al) {
+        const int f = fac(al, 0);
+        E acc = tab[f][0][a0] * A[cl][al][base];
+#pragma unroll
+        for (int q = 1; q < N; ++q) acc = fma(tab[f][q][a0], A[cl][al][base + q], acc);
+        Bf(al, pt.p) = acc;
+      }
+    }
+    __syncthreads();
+    // y: (a0, q1, q2) -> (a0, a1, q2), B -> A; in 2D the last sweep, summed over the pairs
+    {
+      const int a1 = pt.pc[1], base = pt.base(1);
+      E tot = E(0);
+#pragma unroll
+      for (int al = 0; al < NS; ++al) {
+        const int f = fac(al, 1);
+        E acc = tab[f][0][a1] * Bf(al, base);
+#pragma unroll
+        for (int q = 1; q < N; ++q) acc = fma(tab[f][q][a1], Bf(al, base + q * N), acc);
+        if (DIM == 3) A[cl][al][pt.p] = acc;
+        else tot = tot + acc;
+      }
+      if (DIM == 2) dsum[c] = tot;
+    }
+    if (DIM == 3) {
+      __syncthreads();
+      // z: (a0, a1, q2) -> (a0, a1, a2), summed over the pairs
+      const int a2 = pt.pc[2], base = pt.base(2);
+      E tot = E(0);
+#pragma unroll
+      for (int al = 0; al < NS; ++al) {
+        const int f = fac(al, 2);
+        E acc = tab[f][0][a2] * A[cl][al][base];
+#pragma unroll
+        for (int q = 1; q < N; ++q) acc = fma(tab[f][q][a2], A[cl][al][base + q * N * N], acc);
+        tot = tot + acc;
+      }
+      dsum[c] = tot;
     }
   }
   if (active) {

@@ -336,10 +336,15 @@ __global__ void __launch_bounds__(256) gjb_update(const E* __restrict__ A, E* __
   if (blockIdx.x < blockIdx.y) return;  // upper triangle of tiles only
   const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
   const int t = threadIdx.x;
+  // A_iK of the tile's rows: stored in row i where i < k0 (consecutive threads take consecutive m), and as
+  // row K's entries (A_Ki, the same or the negated value) where i >= k0 (consecutive threads take consecutive i)
+  const bool rows_eliminated = i0 + 64 <= k0;
   for (int idx = t; idx < 64 * GJB; idx += 256) {
-    const int r = idx / GJB, m = idx % GJB;
+    const int r = rows_eliminated ? idx / GJB : idx % 64, m = rows_eliminated ? idx % GJB : idx / 64;
     const int i = i0 + r;
     sA[r][m] = (i < n && m < b) ? sym_get(A, n, k0, i, k0 + m) : E(0);
+  }
+  for (int idx = t; idx < 64 * GJB; idx += 256) {
     const int mm = idx / 64, c = idx % 64;
     const int j = j0 + c;
     sY[mm][c] = (j < n && mm < b) ? Y[(long long)mm * n + j] : E(0);

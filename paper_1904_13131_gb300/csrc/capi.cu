@@ -172,6 +172,9 @@ struct Level {
   float* d_c32 = nullptr;
   size_t c64_len = 0, c32_len = 0;
   bool has64 = false, has32 = false;
+  // the finest level's FP64 cache is allocated but built at its first use: with a double-float finest
+  // action (fine_dtype) the solver itself never reads it
+  bool lazy64 = false;
   double* d_diag = nullptr;
   double* d_dinv64 = nullptr;
   float* d_dinv32 = nullptr;
@@ -195,6 +198,7 @@ struct Level {
   cudaGraphExec_t eig_exec = nullptr;
   std::vector<unsigned char> eig_sig;
   long long eig_nodes = 0;
+  double* d_eigbuf = nullptr;  // this level's smoother estimate: scalars, coefficient history, dot partials
 };
 
 struct Transfer {  // level l-1 (coarse) <-> l (fine); the same 1D tables act along every axis
@@ -256,6 +260,10 @@ struct hy_ctx {
   // the exact coarse inverse is built on a side stream, overlapping the rest of the linearisation
   cudaStream_t side = nullptr;
   cudaEvent_t ev_side_fork = nullptr, ev_side_join = nullptr, ev_side_start = nullptr;
+  // streams (and their end events) on which the levels' smoother estimates run side by side
+  std::vector<cudaStream_t> eig_st;
+  std::vector<cudaEvent_t> eig_ev;
+  cudaEvent_t ev_eig_fork = nullptr;
   bool side_timed = false;
   // phase events of the last linearisation (PhaseTimer)
   cudaEvent_t ev_phase[6] = {};
@@ -341,6 +349,8 @@ void drop_graph(hy_ctx* ctx) {
 
 void free_mesh(hy_ctx* ctx) {
   if (ctx->side) cudaStreamSynchronize(ctx->side);  // a coarse setup in flight uses the level buffers
+  for (cudaStream_t st : ctx->eig_st)
+    if (st) cudaStreamSynchronize(st);
   ctx->side_pending = false;
   drop_graph(ctx);
   for (Level& L : ctx->lev)
@@ -421,10 +431,15 @@ ApplyFn<ff> apply_fn(hy_ctx* ctx, ff*, int var) {
 // y = A~ x on level l in precision T (x zero on constrained dofs on read, y = x there). The vectors are
 // of type vec_t<T> (FP64 for the double-float action).
 // prepared: y already holds (constrained ? x : 0) (written by the kernel that produced x).
+hy_status ensure_fp64_cache(hy_ctx* ctx, int l);
+
 template <typename T>
 hy_status vmult(hy_ctx* ctx, int l, const vec_t<T>* x, vec_t<T>* y, bool constrained_in = true, bool prepared = false) {
   using V = vec_t<T>;
   Level& L = ctx->lev[l];
+  if constexpr (std::is_same<T, double>::value) {
+    if (L.lazy64) HY_TRY(ensure_fp64_cache(ctx, l));
+  }
   if (!has_cache<T>(L)) return fail(ctx, HY_ERR_STATE, "no Gauss-point cache of this precision on this level");
   CellArgs<T> a = cell_args<T>(ctx, L);
   a.x = x;
@@ -684,38 +699,53 @@ hy_status vcycle_top(hy_ctx* ctx, const double* r, double* z) {
 }
 
 constexpr int EIG_GRAPH_MAX_ITERS = 64;
+// per level: 8 scalars, the alpha and beta history of a graph-length run, the dot partial sums
+constexpr int EIG_BUF_LEN = 8 + 2 * EIG_GRAPH_MAX_ITERS + DOT_BLOCKS;
 
-// Ritz extremes of D^{-1} A~ on level l from `iters` Jacobi-PCG iterations (Lanczos tridiagonal from
-// the CG coefficients), start vector from SplitMix64 with seed l, constrained entries zero (Sec. 7).
+// Device buffers of one eigenvalue-estimate run.
+struct EigBufs {
+  double* sc;        // {rz, rz0, pq, rzn, alpha, beta, stopped, count}
+  double* hist;      // alpha history [iters], then beta history [iters]; follows sc contiguously
+  double* partials;  // dot partial sums
+};
+EigBufs ctx_eig_bufs(hy_ctx* ctx) { return {ctx->d_eig_scal, ctx->d_eig_hist, ctx->d_partials}; }
+EigBufs level_eig_bufs(Level& L) {
+  return {L.d_eigbuf, L.d_eigbuf + 8, L.d_eigbuf + 8 + 2 * EIG_GRAPH_MAX_ITERS};
+}
+
+// Enqueues `iters` Jacobi-PCG iterations on level l (Ritz values of D^{-1} A~ come from their coefficients),
+// start vector from SplitMix64 with seed l, constrained entries zero (Sec. 7), on the context's current
+// stream. A run of at most EIG_GRAPH_MAX_ITERS iterations with graphs enabled is enqueued without any host
+// synchronisation; a longer one looks at the device-side stop flag now and then.
 template <typename T>
-hy_status eig_estimate(hy_ctx* ctx, int l, int iters, double& lmin, double& lmax) {
+hy_status eig_enqueue(hy_ctx* ctx, int l, int iters, const EigBufs& eb) {
   Level& L = ctx->lev[l];
   T* r = wvec<T>(L, 2);
   T* z = wvec<T>(L, 3);
   T* q = wvec<T>(L, 4);
   T* p = wvec<T>(L, 1);
   const T* dinv = dinv_of<T>(L);
-  if ((long long)ctx->eig_hist_len < 2LL * iters) return fail(ctx, HY_ERR_STATE, "eigenvalue history too short");
-  double* sc = ctx->d_eig_scal;  // {rz, rz0, pq, rzn, alpha, beta, stopped, count}
-  double* hist = ctx->d_eig_hist;
+  double* sc = eb.sc;
+  double* hist = eb.hist;
+  double* part = eb.partials;
   launch_splitmix<T>(r, L.ndofs, (unsigned long long)l, ctx->stream);
   launch_zero_constrained<T>(r, L.nnodes, ctx->dim, L.g, ctx->stream);
   launch_mul<T>(dinv, r, z, L.ndofs, ctx->stream);
   HY_CK(cudaMemcpyAsync(p, z, sizeof(T) * L.ndofs, cudaMemcpyDeviceToDevice, ctx->stream));
   HY_CK(cudaMemsetAsync(sc, 0, sizeof(double) * 8, ctx->stream));
-  launch_dot<T>(r, z, L.ndofs, ctx->d_partials, sc + 0, ctx->stream);  // rz
+  launch_dot<T>(r, z, L.ndofs, part, sc + 0, ctx->stream);  // rz
   HY_CK(cudaMemcpyAsync(sc + 1, sc + 0, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));  // rz0
   HY_TRY(check_launch(ctx, 5));
   // CG iterations with every scalar on the device; the coefficient history comes back once at the end
   auto iteration = [&](int it) -> hy_status {
     HY_TRY(level_apply<T>(ctx, l, p, q));
-    launch_dot<T>(p, q, L.ndofs, ctx->d_partials, sc + 2, ctx->stream);  // pq
+    launch_dot<T>(p, q, L.ndofs, part, sc + 2, ctx->stream);  // pq
     launch_eig_alpha(sc, hist, it, ctx->stream);
-    launch_axpy_dev<T>(sc + 4, -1.0, q, r, L.ndofs, ctx->stream);        // r -= alpha q
-    launch_mul<T>(dinv, r, z, L.ndofs, ctx->stream);                     // z = D^{-1} r
-    launch_dot<T>(r, z, L.ndofs, ctx->d_partials, sc + 3, ctx->stream);  // rzn
+    launch_axpy_dev<T>(sc + 4, -1.0, q, r, L.ndofs, ctx->stream);  // r -= alpha q
+    launch_mul<T>(dinv, r, z, L.ndofs, ctx->stream);               // z = D^{-1} r
+    launch_dot<T>(r, z, L.ndofs, part, sc + 3, ctx->stream);       // rzn
     launch_eig_beta(sc, hist, it, iters, ctx->stream);
-    launch_xpay_dev<T>(z, sc + 5, p, p, L.ndofs, ctx->stream);           // p = z + beta p
+    launch_xpay_dev<T>(z, sc + 5, p, p, L.ndofs, ctx->stream);     // p = z + beta p
     return check_launch(ctx, 9);
   };
   if (ctx->use_graphs && iters <= EIG_GRAPH_MAX_ITERS) {
@@ -744,7 +774,7 @@ hy_status eig_estimate(hy_ctx* ctx, int l, int iters, double& lmin, double& lmax
       add(&L.form[prec_index<T>()], sizeof(int));
       add(&L.var[prec_index<T>()], sizeof(int));
     }
-    const void* ptrs[9] = {r, z, q, p, dinv, sc, hist, ctx->d_partials, ctx->d_err};
+    const void* ptrs[9] = {r, z, q, p, dinv, sc, hist, part, ctx->d_err};
     add(ptrs, sizeof(ptrs));
     add(&iters, sizeof(iters));
     add(&ctx->prefetch, sizeof(ctx->prefetch));
@@ -795,12 +825,13 @@ hy_status eig_estimate(hy_ctx* ctx, int l, int iters, double& lmin, double& lmax
       }
     }
   }
-  double hs[8];
-  std::vector<double> hh((size_t)2 * iters);
-  HY_CK(cudaMemcpyAsync(hs, sc, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
-  HY_CK(cudaMemcpyAsync(hh.data(), hist, sizeof(double) * 2 * iters, cudaMemcpyDeviceToHost, ctx->stream));
-  HY_CK(cudaStreamSynchronize(ctx->stream));
-  // iterations taken: up to and including the one whose residual met the stop test
+  return HY_OK;
+}
+
+// Extreme Ritz values from a finished run's scalars hs (8) and coefficient history hh (alpha [iters], then
+// beta [iters]): the Lanczos tridiagonal of the CG coefficients, over the iterations taken up to and
+// including the one whose residual met the stop test.
+hy_status eig_extremes(hy_ctx* ctx, const double* hs, const double* hh, int iters, double& lmin, double& lmax) {
   int m = (int)hs[7];
   if (hs[6] == 0.0) m = iters;
   if (m == 0) return fail(ctx, HY_ERR_STATE, "eigenvalue estimate: no iterations");
@@ -810,6 +841,74 @@ hy_status eig_estimate(hy_ctx* ctx, int l, int iters, double& lmin, double& lmax
     if (j + 1 < m) off[j] = std::sqrt(hh[iters + j]) / hh[j];
   }
   tridiag_extremes(diag, off, lmin, lmax);
+  return HY_OK;
+}
+
+// One run on the context's stream with the context's buffers, waited for.
+template <typename T>
+hy_status eig_estimate(hy_ctx* ctx, int l, int iters, double& lmin, double& lmax) {
+  if ((long long)ctx->eig_hist_len < 2LL * iters) return fail(ctx, HY_ERR_STATE, "eigenvalue history too short");
+  const EigBufs eb = ctx_eig_bufs(ctx);
+  HY_TRY(eig_enqueue<T>(ctx, l, iters, eb));
+  double hs[8];
+  std::vector<double> hh((size_t)2 * iters);
+  HY_CK(cudaMemcpyAsync(hs, eb.sc, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
+  HY_CK(cudaMemcpyAsync(hh.data(), eb.hist, sizeof(double) * 2 * iters, cudaMemcpyDeviceToHost, ctx->stream));
+  HY_CK(cudaStreamSynchronize(ctx->stream));
+  return eig_extremes(ctx, hs, hh.data(), iters, lmin, lmax);
+}
+
+// The smoother estimates of every level above the coarsest (the level precision of the V-cycle). A level's
+// run reads only its own tangent and diagonal and writes only its own vectors and buffers, so with graphs
+// the runs go side by side, each on a stream of its own: one fork, one join and one host synchronisation
+// for all levels. Otherwise they run one after another.
+hy_status smoother_eig_estimates(hy_ctx* ctx) {
+  const int nl = ctx->nlev, iters = ctx->sp.eig_iters;
+  if (!ctx->use_graphs || iters > EIG_GRAPH_MAX_ITERS) {
+    for (int l = 1; l < nl; ++l) {
+      double lmin, lmax;
+      if (level_f32(ctx, l)) HY_TRY(eig_estimate<float>(ctx, l, iters, lmin, lmax));
+      else HY_TRY(eig_estimate<double>(ctx, l, iters, lmin, lmax));
+      ctx->lev[l].lmax = lmax;
+    }
+    return HY_OK;
+  }
+  if (nl < 2) return HY_OK;
+  while ((int)ctx->eig_st.size() < nl) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    HY_CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    ctx->eig_st.push_back(st);
+    HY_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    ctx->eig_ev.push_back(ev);
+  }
+  if (!ctx->ev_eig_fork) HY_CK(cudaEventCreateWithFlags(&ctx->ev_eig_fork, cudaEventDisableTiming));
+  HY_CK(cudaEventRecord(ctx->ev_eig_fork, ctx->stream));
+  cudaStream_t main = ctx->stream;
+  hy_status st = HY_OK;
+  for (int l = 1; l < nl; ++l) {
+    HY_CK(cudaStreamWaitEvent(ctx->eig_st[l], ctx->ev_eig_fork, 0));
+    ctx->stream = ctx->eig_st[l];
+    if (st == HY_OK)
+      st = level_f32(ctx, l) ? eig_enqueue<float>(ctx, l, iters, level_eig_bufs(ctx->lev[l]))
+                             : eig_enqueue<double>(ctx, l, iters, level_eig_bufs(ctx->lev[l]));
+    ctx->stream = main;
+    // joined even after a failure, so that nothing of the run outlives the call
+    HY_CK(cudaEventRecord(ctx->eig_ev[l], ctx->eig_st[l]));
+    HY_CK(cudaStreamWaitEvent(main, ctx->eig_ev[l], 0));
+  }
+  if (st != HY_OK) return st;
+  const size_t per = 8 + 2 * (size_t)iters;  // scalars, then the history that follows them
+  std::vector<double> h((size_t)nl * per);
+  for (int l = 1; l < nl; ++l)
+    HY_CK(cudaMemcpyAsync(h.data() + l * per, ctx->lev[l].d_eigbuf, sizeof(double) * per, cudaMemcpyDeviceToHost,
+                          main));
+  HY_CK(cudaStreamSynchronize(main));
+  for (int l = 1; l < nl; ++l) {
+    double lmin, lmax;
+    HY_TRY(eig_extremes(ctx, h.data() + l * per, h.data() + l * per + 8, iters, lmin, lmax));
+    ctx->lev[l].lmax = lmax;
+  }
   return HY_OK;
 }
 
@@ -834,8 +933,10 @@ template <> size_t& cache_len<double>(Level& L) { return L.c64_len; }
 template <> size_t& cache_len<float>(Level& L) { return L.c32_len; }
 template <> size_t& cache_len<ff>(Level& L) { return L.cff_len; }
 
+// Allocates level l's cache of element type TOUT for variant var and, unless only_allocate, launches the
+// state kernel that fills it.
 template <typename TOUT>
-hy_status build_cache(hy_ctx* ctx, int l, int var) {
+hy_status build_cache(hy_ctx* ctx, int l, int var, bool only_allocate = false) {
   Level& L = ctx->lev[l];
   const int cb = layout_cells<TOUT>(ctx->dim, ctx->n);
   const size_t nblocks = (size_t)((L.g.ncells + cb - 1) / cb);
@@ -848,6 +949,7 @@ hy_status build_cache(hy_ctx* ctx, int l, int var) {
     HY_TRY(dalloc(ctx, &buf, len));
     cur = len;
   }
+  if (only_allocate) return HY_OK;
   CellArgs<double> a = cell_args<double>(ctx, L);
   a.u64 = L.d_u64;
   StateFn<TOUT> fn;
@@ -917,7 +1019,10 @@ hy_status coarse_direct_setup(hy_ctx* ctx) {
   // (the carried-down coarse displacement): they need nothing else of the linearisation and overlap its
   // state builds, diagonals and eigenvalue estimates. coarse_direct_finish joins them.
   if (!ctx->side) {
-    HY_CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+    // the longest chain of the linearisation: its blocks go first, the main stream's work fills in around them
+    int lo = 0, hi = 0;
+    HY_CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    HY_CK(cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, hi));
     HY_CK(cudaEventCreateWithFlags(&ctx->ev_side_fork, cudaEventDisableTiming));
     HY_CK(cudaEventCreate(&ctx->ev_side_join));
     HY_CK(cudaEventCreate(&ctx->ev_side_start));
@@ -1091,6 +1196,21 @@ hy_status autotune_level(hy_ctx* ctx, int l) {
   return HY_OK;
 }
 
+// Builds the finest level's deferred FP64 cache (and picks its kernel form) on the first FP64 action that
+// needs it. Not inside a stream capture: the build synchronises with the host.
+hy_status ensure_fp64_cache(hy_ctx* ctx, int l) {
+  Level& L = ctx->lev[l];
+  if (!L.lazy64) return HY_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  HY_CK(cudaStreamIsCapturing(ctx->stream, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return fail(ctx, HY_ERR_STATE, "FP64 cache needed inside a capture");
+  HY_TRY(build_cache<double>(ctx, l, L.var[0]));
+  HY_TRY(check_error_word(ctx, "FP64 state build"));
+  L.lazy64 = false;
+  L.has64 = true;
+  return autotune_level<double>(ctx, l);
+}
+
 // Verbose phase timer of set_displacement (synchronises the stream, so only when HY_VERBOSE=1).
 // Phase events of set_displacement: recorded on the context's stream at the start and after each phase (no
 // synchronisation); setup_phases_ms reads them once the stream has been synchronised. With HY_VERBOSE=1 each
@@ -1198,7 +1318,7 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
     Level& L = ctx->lev[l];
     const bool need64 = (l == top) || (l == 0) || !mixed;
     const bool need32 = mixed && (l > 0 || l == top);
-    L.has64 = L.has32 = L.hasff = false;
+    L.has64 = L.has32 = L.hasff = L.lazy64 = false;
     L.form[0] = L.form[1] = L.form[2] = -1;
     // the finest level's FP64 and double-float caches serve the outer CG: the given variant; the V-cycle's
     // level operators (every cache below the finest, and its FP32 cache) take the level variant
@@ -1206,7 +1326,10 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
     L.var[0] = l == top ? build_of(var) : lvar;
     L.var[1] = lvar;
     L.var[2] = var;
-    if (need64) {
+    if (need64 && l == top && l > 0 && ctx->sp.fine_dtype == HY_FF) {
+      HY_TRY(build_cache<double>(ctx, l, L.var[0], true));
+      L.lazy64 = true;
+    } else if (need64) {
       HY_TRY(build_cache<double>(ctx, l, L.var[0]));
       L.has64 = true;
     }
@@ -1251,12 +1374,7 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
   }
   pt.mark("autotune");
   // eigenvalue estimates (level precision of the V-cycle)
-  for (int l = 1; l < ctx->nlev && !reuse; ++l) {
-    double lmin, lmax;
-    if (level_f32(ctx, l)) HY_TRY(eig_estimate<float>(ctx, l, ctx->sp.eig_iters, lmin, lmax));
-    else HY_TRY(eig_estimate<double>(ctx, l, ctx->sp.eig_iters, lmin, lmax));
-    ctx->lev[l].lmax = lmax;
-  }
+  if (!reuse) HY_TRY(smoother_eig_estimates(ctx));
   pt.mark("smoother eig");
   if (reuse) {
     // the last full setup's coarse inverse or Chebyshev coarse bounds stay
@@ -1691,6 +1809,9 @@ hy_status batch_apply(hy_batch* b, const void* const* x, void* const* y) {
   for (int i = 0; i < cnt; ++i) {
     hy_ctx* c = b->ctx[i];
     const Level& L = c->lev[c->nlev - 1];
+    if constexpr (std::is_same<T, double>::value) {
+      if (L.lazy64 && ensure_fp64_cache(c, c->nlev - 1) != HY_OK) return bfail(b, HY_ERR_STATE, "batch: " + c->err);
+    }
     if (!has_cache<T>(L)) return bfail(b, HY_ERR_STATE, "batch: a context has no finest-level cache of this precision");
     if (!x[i] || !y[i] || x[i] == y[i]) return bfail(b, HY_ERR_ARG, "batch: null or aliased vectors");
     R[i] = i;
@@ -1751,11 +1872,14 @@ hy_status batch_pcg(hy_batch* b, const double* const* rhs, double* const* xs, do
     }
     R.push_back(i);
   }
-  HY_TRY(join_in(b));
-  hy_status result = HY_OK;
   // the finest-level action of the outer CG: double-float when every problem asks for it (fine_dtype)
   bool use_ff = true;
   for (hy_ctx* c : b->ctx) use_ff = use_ff && c->sp.fine_dtype == HY_FF && c->lev[c->nlev - 1].hasff;
+  if (!use_ff)
+    for (int i : R)
+      if (ensure_fp64_cache(b->ctx[i], b->ctx[i]->nlev - 1) != HY_OK) return bfail(b, HY_ERR_STATE, "batch: " + b->ctx[i]->err);
+  HY_TRY(join_in(b));
+  hy_status result = HY_OK;
   if (!R.empty()) {
     std::vector<const void*> ps, qs;
     for (int i : R) {
@@ -2021,6 +2145,11 @@ void hy_destroy(hy_ctx* ctx) {
   if (ctx->ev_side_fork) cudaEventDestroy(ctx->ev_side_fork);
   if (ctx->ev_side_join) cudaEventDestroy(ctx->ev_side_join);
   if (ctx->ev_side_start) cudaEventDestroy(ctx->ev_side_start);
+  for (cudaStream_t st : ctx->eig_st)
+    if (st) cudaStreamDestroy(st);
+  for (cudaEvent_t e : ctx->eig_ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->ev_eig_fork) cudaEventDestroy(ctx->ev_eig_fork);
   for (cudaEvent_t e : ctx->ev_phase)
     if (e) cudaEventDestroy(e);
   if (ctx->h_pcg_scal) cudaFreeHost(ctx->h_pcg_scal);
@@ -2212,6 +2341,7 @@ hy_status hy_mesh_setup(hy_ctx* ctx, int dim, int degree, int m, int n_levels, c
   HY_TRY(dalloc(ctx, &ctx->d_scal, 4));
   HY_TRY(dalloc(ctx, &ctx->d_face, 18));
   HY_TRY(dalloc(ctx, &ctx->d_eig_scal, 8 + PCG_SCALARS));
+  for (int l = 1; l < n_levels; ++l) HY_TRY(dalloc(ctx, &ctx->lev[l].d_eigbuf, EIG_BUF_LEN));
   HY_TRY(dalloc(ctx, &ctx->d_usetup, ctx->lev[0].ndofs));
   HY_TRY(dalloc(ctx, &ctx->d_udiff, ctx->lev[0].ndofs));
   for (int i = 0; i < 12; ++i) HY_TRY(dalloc(ctx, &ctx->f64[i], ctx->lev[n_levels - 1].ndofs));
@@ -2544,7 +2674,9 @@ hy_status hy_newton_solve(hy_ctx* ctx, const hy_newton_params* p, double* u, hy_
       // rhs = -R - Z A du0 (lifting of the prescribed increment into the first solve)
       HY_CK(cudaMemcpyAsync(rhs, R, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
       if (lift2 > 0.0) {
-        HY_TRY(vmult<double>(ctx, ctx->nlev - 1, du0, t, false));
+        // in the finest-level action of the outer CG (double-float when fine_dtype asks for it)
+        if (ctx->sp.fine_dtype == HY_FF && ctx->lev[ctx->nlev - 1].hasff) HY_TRY(vmult<ff>(ctx, ctx->nlev - 1, du0, t, false));
+        else HY_TRY(vmult<double>(ctx, ctx->nlev - 1, du0, t, false));
         launch_axpby<double>(-1.0, t, -1.0, rhs, n, ctx->stream);  // rhs = -A du0 - R
       } else {
         launch_axpby<double>(0.0, R, -1.0, rhs, n, ctx->stream);   // rhs = -R
@@ -2652,6 +2784,7 @@ hy_status hy_footprint_general(int dim, int degree, int m, int n_levels, hy_vari
   }
   total += 2 * al(tmp_len, 8) + 3 * al(tmp_len, 4);
   total += al(2, 4) + al(1, 8) + al(DOT_BLOCKS, 8) + al(4, 8) + al(18, 8) + al(8 + PCG_SCALARS, 8);
+  total += (size_t)(n_levels - 1) * al(EIG_BUF_LEN, 8);  // the smoother estimates' per-level buffers
   total += 2 * al(nd[0], 8);  // coarsest-level displacement of the last full setup, and a difference
   total += 12 * al(nd[n_levels - 1], 8);
   const int top = n_levels - 1;

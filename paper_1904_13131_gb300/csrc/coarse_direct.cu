@@ -9,7 +9,8 @@
 namespace hy {
 namespace {
 
-// One block per cell, one thread per row (node a, component c) of the element matrix.
+// One block per cell; the work items are the cell's node pairs (a, b), each forming a DIM x DIM block of
+// the element matrix:
 //   A_{ac,be} = sum_q W [ d_ce g_a.tau.g_b + c1/2 (d_ce g_a.g_b + g_{a,e} g_{b,c}) + c2 g_{a,c} g_{b,e} ]
 // with g_a = F^{-T} Grad N_a: the geometric and material parts of Eq. algebraic_tangent with the
 // neo-Hooke action of Eq. simplified_action (c1 = 2(mu - 2 lambda ln J), c2 = 2 lambda, W = w_q h^d).
@@ -180,32 +181,52 @@ __global__ void assemble_dense_kernel(const CellArgs<double> a, double* __restri
     }
   }
   __syncthreads();
-  // one (row, column) pair of the element matrix per work item
-  for (int item = t; item < NR * NR; item += blockDim.x) {
-    const int row = item / NR, col = item % NR;
-    if (cons[row] || cons[col]) continue;
-    const int an = row / DIM, c = row % DIM, bn = col / DIM, e = col % DIM;
-    double acc = 0.0;
+  // one node pair (a, b) per work item: its DIM x DIM block of the element matrix,
+  //   A_{ac,be} = sum_q [ d_ce g_b.(tau + c1/2 I).g_a + c1/2 g_{a,e} g_{b,c} + c2 g_{a,c} g_{b,e} ].
+  // Only the upper triangle of the free-dof matrix is assembled (the Gauss-Jordan passes read nothing else):
+  // the lattice numbers a cell's nodes in the order of its local nodes, so the pairs with a > b lie below
+  // the diagonal and are skipped, and those with a = b keep c <= e.
+  for (int item = t; item < NPT * NPT; item += blockDim.x) {
+    const int an = item / NPT, bn = item % NPT;
+    if (an > bn) continue;
+    double acc[DIM][DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c)
+#pragma unroll
+      for (int e = 0; e < DIM; ++e) acc[c][e] = 0.0;
     for (int q = 0; q < NPT; ++q) {
-      const double* ga = &Gq[(an * NPT + q) * DIM];
-      const double* gb = &Gq[(bn * NPT + q) * DIM];
-      double v = 0.0;
-      if (c == e) {
-        double geo = 0.0, dotab = 0.0;
+      double ga[DIM], gb[DIM];
 #pragma unroll
-        for (int al = 0; al < NS; ++al) {
-          const int i = vi<DIM>(al), j = vj<DIM>(al);
-          geo = fma(tq[al][q], (i == j) ? ga[i] * gb[i] : ga[i] * gb[j] + ga[j] * gb[i], geo);
-        }
-#pragma unroll
-        for (int j = 0; j < DIM; ++j) dotab = fma(ga[j], gb[j], dotab);
-        v = geo + 0.5 * c1q[q] * dotab;
+      for (int j = 0; j < DIM; ++j) {
+        ga[j] = Gq[(an * NPT + q) * DIM + j];
+        gb[j] = Gq[(bn * NPT + q) * DIM + j];
       }
-      v = fma(0.5 * c1q[q], ga[e] * gb[c], v);
-      v = fma(c2q[q], ga[c] * gb[e], v);
-      acc += v;
+      const double hc1 = 0.5 * c1q[q], c2 = c2q[q];
+      double geo = 0.0, dotab = 0.0;
+#pragma unroll
+      for (int al = 0; al < NS; ++al) {
+        const int i = vi<DIM>(al), j = vj<DIM>(al);
+        geo = fma(tq[al][q], (i == j) ? ga[i] * gb[i] : ga[i] * gb[j] + ga[j] * gb[i], geo);
+      }
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) dotab = fma(ga[j], gb[j], dotab);
+      const double sdiag = fma(hc1, dotab, geo);
+#pragma unroll
+      for (int c = 0; c < DIM; ++c)
+#pragma unroll
+        for (int e = 0; e < DIM; ++e) {
+          double v = fma(hc1, ga[e] * gb[c], c == e ? sdiag : 0.0);
+          acc[c][e] += fma(c2, ga[c] * gb[e], v);
+        }
     }
-    atomicAdd(&Aout[(long long)cidx[gdof[row]] * nfree + cidx[gdof[col]]], acc);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c)
+#pragma unroll
+      for (int e = 0; e < DIM; ++e) {
+        const int row = an * DIM + c, col = bn * DIM + e;
+        if (cons[row] || cons[col] || (an == bn && c > e)) continue;
+        atomicAdd(&Aout[(long long)cidx[gdof[row]] * nfree + cidx[gdof[col]]], acc[c][e]);
+      }
   }
 }
 
@@ -275,21 +296,25 @@ __device__ __forceinline__ bool gj_positive(double p) { return p > 0.0; }
 __device__ __forceinline__ bool gj_positive(ff p) { return p.hi > 0.f; }
 
 // W = A_KK^{-1} by single-pivot Gauss-Jordan on the b x b block in shared memory (one block); flags a
-// pivot <= 0.
+// pivot <= 0. The pivot's reciprocal (an FP64 operation, on a pipe of 2 lanes per clock per SM) is taken by
+// the first warp alone, which also forms the pivot row and column; all warps then update the block.
 template <typename E>
 __global__ void gjb_diag(const E* __restrict__ A, int n, int k0, int b, E* __restrict__ W, unsigned* err) {
   __shared__ E w[GJB][GJB + 1];
   __shared__ E rk[GJB], ck[GJB];
+  static_assert(GJB == 32, "the first warp forms a pivot row of GJB entries");
   const int t = threadIdx.x;
   for (int idx = t; idx < b * b; idx += blockDim.x) w[idx / b][idx % b] = sym_get(A, n, k0, k0 + idx / b, k0 + idx % b);
   __syncthreads();
   for (int k = 0; k < b; ++k) {
-    const E p = w[k][k];
-    if (t == 0 && !gj_positive(p)) atomicOr(err, ERRBIT_NONSPD);
-    const E ip = gj_recip(p);
-    if (t < b) {
-      rk[t] = (t == k ? E(1) : w[k][t]) * ip;
-      ck[t] = w[t][k];
+    if (t < 32) {
+      const E p = w[k][k];
+      if (t == 0 && !gj_positive(p)) atomicOr(err, ERRBIT_NONSPD);
+      const E ip = gj_recip(p);
+      if (t < b) {
+        rk[t] = (t == k ? E(1) : w[k][t]) * ip;
+        ck[t] = w[t][k];
+      }
     }
     __syncthreads();
     for (int idx = t; idx < b * b; idx += blockDim.x) {

@@ -104,8 +104,8 @@ def test_autotuned_form_is_recorded_and_reused(torch):
 
 @pytest.mark.parametrize("dim,k,m", [(2, 2, 7), (3, 2, 3), (3, 3, 2), (2, 4, 3), (3, 4, 2)])
 def test_residual_and_diagonal(torch, dim, k, m):
-    """Residual in FP64; the diagonal's (node, point) pair sums in FP64 and, with fine_dtype = FF, in
-    double-float (degrees 1-2 build the double-float action too; the diagonal has both for every degree)."""
+    """Residual in FP64; the sum-factorised diagonal (per (J, L) pair and component, one 1D contraction per
+    direction) in FP64 and, with fine_dtype = FF, in double-float."""
     from paper_1904_13131_gb300.api import FF
     pr = problem(dim, k, m)
     P = oracle_level(pr)
@@ -115,13 +115,34 @@ def test_residual_and_diagonal(torch, dim, k, m):
         r = ctx.residual(ud).cpu().numpy()
         ctx.set_displacement(ud, "T4")
         d = ctx.diagonal().cpu().numpy()
-        if k <= 2:
-            ctx.set_solver_params(fine_dtype=FF)
-            ctx.set_displacement(ud, "T4")
-            dff = ctx.diagonal().cpu().numpy()
-            assert rel(dff, P.diagonal(u)) < 1e-12
+        ctx.set_solver_params(fine_dtype=FF)
+        ctx.set_displacement(ud, "T4")
+        dff = ctx.diagonal().cpu().numpy()
+        assert rel(dff, P.diagonal(u)) < 1e-12
     assert rel(r, P.residual(u)) < 1e-12
     assert rel(d, P.diagonal(u)) < 1e-12
+
+
+def test_deferred_fp64_cache_under_double_float(torch):
+    """With a double-float finest action the finest FP64 cache is built at its first FP64 use (no kernel
+    form before it), and that action then matches the oracle; the double-float action needs no FP64 cache."""
+    from paper_1904_13131_gb300.api import F64, FF
+    dim, k, m = 3, 2, 4
+    pr = problem(dim, k, m, n_levels=2)
+    P = oracle_level(pr)
+    u = inputs.smooth_field(dim, k, m, seed=12)
+    x = inputs.gaussian_vector(P.n_dofs, seed=13)
+    y_ref = P.apply(u, x)
+    ud, xd = torch.tensor(u, device="cuda"), torch.tensor(x, device="cuda")
+    with context(pr) as ctx:
+        ctx.set_solver_params(fine_dtype=FF)
+        for var in ("T4", "NC"):
+            ctx.set_displacement(ud, var)
+            assert ctx.kernel_form(-1, F64) == -1 and ctx.kernel_form(-1, FF) >= 0
+            assert rel(ctx.apply_tangent(xd, dtype=FF).cpu().numpy(), y_ref) < 1e-12
+            assert ctx.kernel_form(-1, F64) == -1
+            assert rel(ctx.apply_tangent(xd, dtype=F64).cpu().numpy(), y_ref) < 1e-12
+            assert ctx.kernel_form(-1, F64) >= 0
 
 
 def test_zero_state_and_zero_vector(torch):

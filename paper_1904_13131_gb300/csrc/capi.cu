@@ -1338,7 +1338,24 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
       L.hasff = true;
     }
     if (need32) {
-      HY_TRY(build_cache<float>(ctx, l, L.var[1]));
+      // The finest level's FP32 cache comes from its double-float or FP64 cache of the same state where the
+      // variants allow (the same variant, or T2 from T4): one state evaluation instead of two.
+      const bool from_ff = L.hasff, from64 = !from_ff && L.has64;
+      const int vs = from_ff ? L.var[2] : L.var[0], vd = L.var[1];
+      const bool t4_to_t2 = vs == VAR_T4 && vd == VAR_T2;
+      // (A variant that caches nothing needs no FP32 build at all: the other build has checked J.)
+      if (l == top && (from_ff || from64) && (vs == vd || t4_to_t2)) {
+        HY_TRY(build_cache<float>(ctx, l, vd, true));
+        if (cache_values(vd, ctx->dim) > 0) {
+          launch_derive_f32(ctx->dim, ctx->n, from_ff,
+                            from_ff ? (const void*)cache_of<ff>(L) : (const void*)cache_of<double>(L),
+                            cache_values(vs, ctx->dim), cache_buf<float>(L), cache_values(vd, ctx->dim), t4_to_t2,
+                            L.g.ncells, ctx->stream);
+          HY_TRY(check_launch(ctx, 1));
+        }
+      } else {
+        HY_TRY(build_cache<float>(ctx, l, L.var[1]));
+      }
       if (!L.d_u32) HY_TRY(dalloc(ctx, &L.d_u32, L.ndofs));
       launch_convert<double, float>(L.d_u64, L.d_u32, L.ndofs, ctx->stream);
       HY_TRY(check_launch(ctx, 1));

@@ -25,7 +25,58 @@ void launch_diag(const CellArgs<double>& a, cudaStream_t st) {
   const int grid = (a.g.ncells + CB - 1) / CB;
   diag_kernel<DIM, N, E><<<grid, CB * NPT, 0, st>>>(a);
 }
+
+__device__ __forceinline__ float to_f32(double v) { return (float)v; }
+__device__ __forceinline__ float to_f32(ff v) { return v.hi; }
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(ff v) { return (double)v.hi + (double)v.lo; }
+
+// One thread per (cell, Gauss point): the FP32 cache entries of the point from the FP64 or double-float
+// cache of the same state, each in its own cell-block layout. The same variant rounds every value to FP32 (the
+// leading float of a double-float value is the FP64 value rounded to FP32), so the result equals what the
+// FP32 state kernel writes. T2 from T4 keeps M and tau~ and recovers c1~ = JC~_0000 - JC~_0011 and
+// c2~ = JC~_0011 (JC~ = c1~ S + c2~ I (x) I, Voigt entries (0, 0) and (0, 1)) in FP64 before rounding.
+template <int DIM, int N, typename TS>
+__global__ void derive_f32_kernel(const TS* __restrict__ src, int nvs, float* __restrict__ dst, int nvd, bool t4_to_t2,
+                                  int ncells) {
+  constexpr int NPT = ipow(N, DIM);
+  constexpr int CBS = layout_cells<TS>(DIM, N), BSS = layout_row<TS>(DIM, N);
+  constexpr int CBD = layout_cells<float>(DIM, N), BSD = layout_row<float>(DIM, N);
+  constexpr int NM = DIM * DIM + nsym(DIM);  // M and tau~
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= (long long)ncells * NPT) return;
+  const int cell = (int)(i / NPT), p = (int)(i % NPT);
+  const TS* s = src + (long long)(cell / CBS) * nvs * BSS + (cell % CBS) * NPT + p;
+  float* d = dst + (long long)(cell / CBD) * nvd * BSD + (cell % CBD) * NPT + p;
+  if (!t4_to_t2) {
+    for (int v = 0; v < nvd; ++v) d[(long long)v * BSD] = to_f32(s[(long long)v * BSS]);
+    return;
+  }
+#pragma unroll
+  for (int v = 0; v < NM; ++v) d[(long long)v * BSD] = to_f32(s[(long long)v * BSS]);
+  const double k00 = to_f64(s[(long long)NM * BSS]), k01 = to_f64(s[(long long)(NM + 1) * BSS]);
+  d[(long long)NM * BSD] = (float)(k00 - k01);
+  d[(long long)(NM + 1) * BSD] = (float)k01;
+}
+
+template <int DIM, int N>
+void launch_derive(bool src_ff, const void* src, int nvs, float* dst, int nvd, bool t4_to_t2, int ncells,
+                   cudaStream_t st) {
+  const long long total = (long long)ncells * ipow(N, DIM);
+  const int grid = (int)((total + 255) / 256);
+  if (src_ff) derive_f32_kernel<DIM, N, ff><<<grid, 256, 0, st>>>(static_cast<const ff*>(src), nvs, dst, nvd, t4_to_t2, ncells);
+  else derive_f32_kernel<DIM, N, double><<<grid, 256, 0, st>>>(static_cast<const double*>(src), nvs, dst, nvd, t4_to_t2, ncells);
+}
 }  // namespace
+
+void launch_derive_f32(int dim, int n, bool src_ff, const void* src, int nvs, float* dst, int nvd, bool t4_to_t2,
+                       int ncells, cudaStream_t st) {
+  using Fn = void (*)(bool, const void*, int, float*, int, bool, int, cudaStream_t);
+  static const Fn t[2][4] = {{launch_derive<2, 2>, launch_derive<2, 3>, launch_derive<2, 4>, launch_derive<2, 5>},
+                             {launch_derive<3, 2>, launch_derive<3, 3>, launch_derive<3, 4>, launch_derive<3, 5>}};
+  if (n < 2 || n > 5 || dim < 2 || dim > 3 || ncells <= 0) return;
+  t[dim - 2][n - 2](src_ff, src, nvs, dst, nvd, t4_to_t2, ncells, st);
+}
 
 // indexed by Variant (0-4, VAR_NONE = 5, the general builds 6-8; double-float has no general build)
 #define HY_SROW(D, N, T)                                                                                   \

@@ -98,6 +98,10 @@ HY_FF_TABLES(3d)
 StateFn<double> state_fn_f64(int dim, int n, int var);   // var VAR_NONE: J check only
 StateFn<float> state_fn_f32(int dim, int n, int var);
 StateFn<ff> state_fn_ff(int dim, int n, int var);
+// FP32 cache (nvd values per Gauss point) of a level derived from its FP64 (src_ff false) or double-float
+// cache (nvs values) of the same state: the same variant, or T2 from T4 (t4_to_t2).
+void launch_derive_f32(int dim, int n, bool src_ff, const void* src, int nvs, float* dst, int nvd, bool t4_to_t2,
+                       int ncells, cudaStream_t st);
 CellFn<double> residual_fn(int dim, int n);
 // diagonal: the sum over (node, Gauss point) pairs in FP64, or in double-float (ff_arith)
 CellFn<double> diag_fn(int dim, int n, bool ff_arith);

@@ -145,6 +145,26 @@ def test_deferred_fp64_cache_under_double_float(torch):
             assert ctx.kernel_form(-1, F64) >= 0
 
 
+@pytest.mark.parametrize("dim,k,m", [(2, 3, 6), (3, 2, 4)])
+def test_finest_fp32_cache_from_the_high_precision_cache(torch, dim, k, m):
+    """The finest level's FP32 cache of a mixed-precision hierarchy is taken from its FP64 or double-float
+    cache of the same state (the same variant rounded, or T2 from T4); its FP32 action matches the oracle."""
+    from paper_1904_13131_gb300.api import F32, F64, FF
+    pr = problem(dim, k, m, n_levels=2)
+    P = oracle_level(pr)
+    u = inputs.smooth_field(dim, k, m, seed=21)
+    x = inputs.gaussian_vector(P.n_dofs, seed=22)
+    y_ref = P.apply(u, x)
+    ud, xd = torch.tensor(u, device="cuda"), torch.tensor(x, device="cuda").float()
+    with context(pr) as ctx:
+        for fine, var, lvar in ((F64, "T4", -1), (FF, "T4", -1), (FF, "T4", "T2"), (F64, "T4", "T2"),
+                                (FF, "T2", -1), (F64, "SC", -1), (FF, "NC", -1), (F64, "FC", "FC")):
+            ctx.set_solver_params(fine_dtype=fine, level_variant=lvar)
+            ctx.set_displacement(ud, var, level_dtype=1)
+            y = ctx.apply_tangent(xd, dtype=F32).double().cpu().numpy()
+            assert rel(y, y_ref) < 2e-6, (fine, var, lvar, rel(y, y_ref))
+
+
 def test_zero_state_and_zero_vector(torch):
     """u = 0 gives R = 0 exactly; x = 0 gives y = 0 exactly (degenerate inputs)."""
     pr = problem(3, 2, 3)

@@ -295,16 +295,24 @@ __device__ __forceinline__ ff gj_recip(ff p) { return rcp_rn(p); }
 __device__ __forceinline__ bool gj_positive(double p) { return p > 0.0; }
 __device__ __forceinline__ bool gj_positive(ff p) { return p.hi > 0.f; }
 
-// W = A_KK^{-1} by single-pivot Gauss-Jordan on the b x b block in shared memory (one block); flags a
-// pivot <= 0. The pivot's reciprocal (an FP64 operation, on a pipe of 2 lanes per clock per SM) is taken by
-// the first warp alone, which also forms the pivot row and column; all warps then update the block.
+// W = A_KK^{-1} by single-pivot Gauss-Jordan on the b x b block in shared memory (one block of 256
+// threads); flags a pivot <= 0. The pivot's reciprocal (an FP64 operation, on a pipe of 2 lanes per clock
+// per SM) is taken by the first warp alone, which also forms the pivot row and column; then every thread
+// updates the four entries (i, j), i = t / 32 + 8 r, j = t mod 32, of the GJB x GJB index space (no integer
+// division: this loop is the sequential chain of the whole inversion).
 template <typename E>
-__global__ void gjb_diag(const E* __restrict__ A, int n, int k0, int b, E* __restrict__ W, unsigned* err) {
+__global__ void __launch_bounds__(256) gjb_diag(const E* __restrict__ A, int n, int k0, int b, E* __restrict__ W,
+                                                unsigned* err) {
   __shared__ E w[GJB][GJB + 1];
   __shared__ E rk[GJB], ck[GJB];
-  static_assert(GJB == 32, "the first warp forms a pivot row of GJB entries");
+  static_assert(GJB == 32, "one warp forms a pivot row; a thread's column is its lane");
   const int t = threadIdx.x;
-  for (int idx = t; idx < b * b; idx += blockDim.x) w[idx / b][idx % b] = sym_get(A, n, k0, k0 + idx / b, k0 + idx % b);
+  const int j = t & 31, i0 = t >> 5;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = i0 + 8 * r;
+    if (i < b && j < b) w[i][j] = sym_get(A, n, k0, k0 + i, k0 + j);
+  }
   __syncthreads();
   for (int k = 0; k < b; ++k) {
     if (t < 32) {
@@ -317,13 +325,21 @@ __global__ void gjb_diag(const E* __restrict__ A, int n, int k0, int b, E* __res
       }
     }
     __syncthreads();
-    for (int idx = t; idx < b * b; idx += blockDim.x) {
-      const int i = idx / b, j = idx % b;
-      w[i][j] = (i == k) ? rk[j] : (j == k ? E(0) : w[i][j]) - ck[i] * rk[j];
+    if (j < b) {
+      const E rkj = rk[j];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int i = i0 + 8 * r;
+        if (i < b) w[i][j] = (i == k) ? rkj : (j == k ? E(0) : w[i][j]) - ck[i] * rkj;
+      }
     }
     __syncthreads();
   }
-  for (int idx = t; idx < b * b; idx += blockDim.x) W[idx] = w[idx / b][idx % b];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = i0 + 8 * r;
+    if (i < b && j < b) W[i * b + j] = w[i][j];
+  }
 }
 
 // Y = W A_K: (b x n) and X = A_:K W (n x b). Thread (r, jy) of a 32 x 8 block computes Y_rj and X_jr for
@@ -349,6 +365,32 @@ __global__ void __launch_bounds__(256) gjb_panels(const E* __restrict__ A, int n
   Y[(long long)r * n + j] = y;
   X[(long long)j * b + r] = x;
 }
+
+// Accumulator of the update's dot products. FP64: a fused multiply-add chain. Double-float: the dot product
+// of Ogita, Rump and Oishi ("Accurate sum and dot product", 2005, Dot2) with double-word operands -- the
+// leading product split exactly by FMA, the leading sums by TwoSum, all error terms (and the cross products
+// of the low words) gathered in one float -- normalised once at the end: 12 FP32 operations per term instead
+// of the 15 of a double-float multiply-add, the same order of accuracy for the 32 terms of a pass.
+template <typename E> struct DotAcc;
+template <> struct DotAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x, double y) { s = fma(x, y, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct DotAcc<ff> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(ff x, ff y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, e));
+    const float s = __fadd_rn(hi, p);
+    const float bp = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+  }
+  __device__ __forceinline__ ff value() const { return two_sum(hi, lo); }  // |lo| may exceed |hi| after cancellation
+};
 
 // B_ij = A_ij - sum_m A_im Y_mj (i, j outside K); rows K take Y (W on the diagonal block), columns K
 // take -X. 64 x 64 output tile per block, 4 x 4 per thread, the A_:K and Y panels staged in shared memory.
@@ -376,11 +418,7 @@ __global__ void __launch_bounds__(256) gjb_update(const E* __restrict__ A, E* __
   }
   __syncthreads();
   const int tr = (t / 16) * 4, tc = (t % 16) * 4;
-  E acc[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) acc[a][c] = E(0);
+  DotAcc<E> acc[4][4];
   for (int m = 0; m < b; ++m) {
     E av[4], yv[4];
 #pragma unroll
@@ -390,7 +428,7 @@ __global__ void __launch_bounds__(256) gjb_update(const E* __restrict__ A, E* __
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[a][c] = fma(av[a], yv[c], acc[a][c]);
+      for (int c = 0; c < 4; ++c) acc[a][c].add(av[a], yv[c]);
   }
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
@@ -404,7 +442,7 @@ __global__ void __launch_bounds__(256) gjb_update(const E* __restrict__ A, E* __
       const bool jK = j >= k0 && j < k0 + b;
       E v;
       if (iK) v = jK ? W[(i - k0) * b + (j - k0)] : Y[(long long)(i - k0) * n + j];
-      else v = jK ? -X[(long long)i * b + (j - k0)] : A[(long long)i * n + j] - acc[a][c];
+      else v = jK ? -X[(long long)i * b + (j - k0)] : A[(long long)i * n + j] - acc[a][c].value();
       B[(long long)i * n + j] = v;
     }
   }

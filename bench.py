@@ -353,30 +353,37 @@ DEFAULT_SWEEP = [(1, 128, 6), (1, 256, 7), (2, 64, 5), (2, 128, 6), (3, 48, 5), 
 
 def config_study(torch, api, inputs, dev, sweep=None, paper_max_dofs=60_000_000, mixed_study=True):
     """The large workloads: (a) the 3D degree sweep Q1-Q4 at 6.4M-51M dofs, full Newton solve under 10%
-    compression in 5 load steps, GMG down to a 2^3-4^3 coarse level, CG rtol 1e-8, in the paper's mode (FP64
-    V-cycle, Chebyshev coarse solve) and in the fastest mode (FP32 V-cycle with T2 level operators, exact
-    coarse inverse where the coarsest level has at most 6000 dofs, double-float finest-level action, setup
-    reuse at 5 %); (b) mixed precision on the 64^3 Q2 inclusion cube, load step by load step: displacement
+    compression in 5 load steps, CG rtol 1e-8, in the paper's mode (FP64 V-cycle down to a 3^3-4^3 coarse
+    level, Chebyshev coarse solve) and in the fastest mode (FP32 V-cycle with T2 level operators, coarsened
+    further where needed to a level of at most 6000 dofs that is inverted exactly in double-float,
+    double-float finest-level action, setup reuse at 5 %); (b) mixed precision on the 64^3 Q2 inclusion cube, load step by load step: displacement
     difference between the FP64 and the mixed-precision Newton states, and the CG iterations of both."""
     out = {}
     for k, m, L in (sweep or DEFAULT_SWEEP):
-        pr = inputs.problem(3, k, m, n_levels=L, top=inputs.normal_top_mask(3))
         n = inputs.n_dofs(3, k, m)
         fv = [[0.0] * 3 for _ in range(6)]
         fv[5][2] = -0.1
-        coarse_exact = inputs.n_dofs(3, k, m >> (L - 1)) <= 6000 and k <= 3
-        modes = [("fastest", 1, 2 if coarse_exact else 0, api.FF, api.VARIANTS["T2"], 0.05)]
+        # the fastest mode coarsens further (halving an even cell count) until its coarsest level can be
+        # inverted exactly (at most 6000 dofs): 2^3 for Q3 64^3 and Q4
+        Lf = L
+        while inputs.n_dofs(3, k, m >> (Lf - 1)) > 6000 and (m >> (Lf - 1)) % 2 == 0 and (m >> (Lf - 1)) >= 4:
+            Lf += 1
+        coarse_exact = inputs.n_dofs(3, k, m >> (Lf - 1)) <= 6000
+        modes = [("fastest", Lf, 1, 2 if coarse_exact else 0, api.FF, api.VARIANTS["T2"], 0.05)]
         if n <= paper_max_dofs:
-            modes.insert(0, ("paper_fp64", 0, 0, api.F64, -1, 0.0))
+            modes.insert(0, ("paper_fp64", L, 0, 0, api.F64, -1, 0.0))
         row = {"dofs": n, "levels": L, "coarse_m": m >> (L - 1)}
         sols = {}
-        with api.Context(dev.index) as c:
-            c.setup_problem(pr)
-            for name, ldt, coarse, fine, lvar, reuse in modes:
+        for name, levels, ldt, coarse, fine, lvar, reuse in modes:
+            pr = inputs.problem(3, k, m, n_levels=levels, top=inputs.normal_top_mask(3))
+            with api.Context(dev.index) as c:
+                c.setup_problem(pr)
                 c.set_solver_params(coarse_solver=coarse, fine_dtype=fine, level_variant=lvar, setup_reuse=reuse)
                 u = torch.zeros(n, dtype=torch.float64, device=dev)
                 rep = c.newton_solve(u, api.Context.newton_params(level_dtype=ldt, face_values=fv))
                 row[name] = newton_summary(rep)
+                row[name]["levels"] = levels
+                row[name]["coarse_m"] = m >> (levels - 1)
                 row[name]["coarse_solver"] = ["chebyshev", "exact_fp64", "exact_ff"][coarse]
                 row[name]["fine_dtype"] = "ff" if fine == api.FF else "f64"
                 row[name]["setup_reuse"] = reuse
@@ -828,6 +835,7 @@ def main():
     ap.add_argument("--configs", action="store_true", help="the degree sweep at 6-51M dofs and the 64^3 mixed study")
     ap.add_argument("--sweep", default=None,
                     help="--configs: meshes as degree:cells:levels,... (default: all eight), no mixed study")
+    ap.add_argument("--fastest-only", action="store_true", help="--configs: the fastest mode alone")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -911,7 +919,8 @@ def main():
         return
     if args.configs:
         sweep = [tuple(int(v) for v in item.split(":")) for item in args.sweep.split(",")] if args.sweep else None
-        print(json.dumps({"configs": config_study(torch, api, inputs, dev, sweep=sweep, mixed_study=sweep is None)}),
+        print(json.dumps({"configs": config_study(torch, api, inputs, dev, sweep=sweep, mixed_study=sweep is None,
+                                                   paper_max_dofs=0 if args.fastest_only else 60_000_000)}),
               flush=True)
         return
     if args.solve_only:

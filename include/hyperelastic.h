@@ -170,8 +170,8 @@ typedef struct {
   double coarse_reduction;  /* [1e-3] residual reduction of the coarse Chebyshev solve */
   int coarse_solver;        /* [0] 0 = Chebyshev as a solver (Sec. 7); 1 = exact: the coarsest tangent
                                assembled densely and inverted (Gauss-Jordan) once per linearisation,
-                               applied as one matrix-vector product (coarsest level <= 6000 dofs;
-                               degrees 1-3 in 3D, 1-4 in 2D); 2 = as 1 with the inversion in double-float
+                               applied as one matrix-vector product (coarsest level <= 6000 dofs,
+                               any degree); 2 = as 1 with the inversion in double-float
                                arithmetic on the FP32 pipe (about 48 significant bits; the applied inverse
                                and the matrix-vector product are FP64) */
   int kernel_form;          /* [-1] tangent-action kernel: 0 = one thread per (cell, Gauss point), 1 = one

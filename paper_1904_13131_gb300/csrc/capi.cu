@@ -978,8 +978,6 @@ hy_status check_error_word(hy_ctx* ctx, const char* where) {
 hy_status coarse_direct_setup(hy_ctx* ctx) {
   Level& C = ctx->lev[0];
   if (C.ndofs > 6000) return fail(ctx, HY_ERR_UNSUPPORTED, "exact coarse solve needs a coarsest level of at most 6000 dofs");
-  if (ctx->dim == 3 && ctx->k == 4)
-    return fail(ctx, HY_ERR_UNSUPPORTED, "exact coarse solve is built for degrees 1-3 in 3D (1-4 in 2D)");
   if (!C.d_Ainv) {
     // free-dof numbering of the coarsest level (host, from the face masks)
     std::vector<int> cidx(C.ndofs, -1), fidx;

@@ -14,7 +14,10 @@ namespace {
 //   A_{ac,be} = sum_q W [ d_ce g_a.tau.g_b + c1/2 (d_ce g_a.g_b + g_{a,e} g_{b,c}) + c2 g_{a,c} g_{b,e} ]
 // with g_a = F^{-T} Grad N_a: the geometric and material parts of Eq. algebraic_tangent with the
 // neo-Hooke action of Eq. simplified_action (c1 = 2(mu - 2 lambda ln J), c2 = 2 lambda, W = w_q h^d).
-template <int DIM, int N>
+// CH = 0: one block per cell, g_a(q) of every node of the cell in shared memory. CH > 0 (elements whose
+// table NPT^2 DIM doubles exceeds shared memory: Q4 in 3D): the block (cell, blockIdx.y) holds g_a(q) for the
+// CH nodes a of its chunk only; thread b forms g_b(q) itself and accumulates the pairs (a, b) of the chunk.
+template <int DIM, int N, int CH>
 __global__ void assemble_dense_kernel(const CellArgs<double> a, double* __restrict__ Aout, long long nfree,
                                       const int* __restrict__ cidx) {
   constexpr int NPT = ipow(N, DIM);
@@ -27,7 +30,7 @@ __global__ void assemble_dense_kernel(const CellArgs<double> a, double* __restri
   __shared__ double Mq[DIM * DIM][NPT], tq[NS][NPT], c1q[NPT], c2q[NPT];
   __shared__ long long gdof[NR];
   __shared__ unsigned char cons[NR];
-  extern __shared__ double Gq[];  // [NPT][NPT][DIM]
+  extern __shared__ double Gq[];  // [NPT or CH][NPT][DIM]
   __shared__ double mu_s, lam_s;
   const int t = threadIdx.x;
   const int cell = blockIdx.x;
@@ -159,9 +162,13 @@ __global__ void assemble_dense_kernel(const CellArgs<double> a, double* __restri
     c2q[t] = c2;
   }
   __syncthreads();
-  // g_a(q) = F^{-T} Grad N_a at every (node, point) pair of the cell, once, in shared memory
-  for (int item = t; item < NPT * NPT; item += blockDim.x) {
-    const int an = item / NPT, q = item % NPT;
+  // g_a(q) = F^{-T} Grad N_a at every (node, point) pair of the cell (of the chunk), once, in shared memory
+  constexpr int NA = CH > 0 ? CH : NPT;  // nodes a in the table
+  const int a0 = CH > 0 ? (int)blockIdx.y * CH : 0;
+  for (int item = t; item < NA * NPT; item += blockDim.x) {
+    const int al = item / NPT, q = item % NPT;
+    const int an = a0 + al;
+    if (an >= NPT) continue;
     const int apc[3] = {an % N, (an / N) % N, DIM == 3 ? an / (N * N) : 0};
     const int qc[3] = {q % N, (q / N) % N, DIM == 3 ? q / (N * N) : 0};
     double gr[DIM];
@@ -177,70 +184,147 @@ __global__ void assemble_dense_kernel(const CellArgs<double> a, double* __restri
       double sa = 0.0;
 #pragma unroll
       for (int J = 0; J < DIM; ++J) sa = fma(gr[J], Mq[J * DIM + j][q], sa);
-      Gq[(an * NPT + q) * DIM + j] = sa;
+      Gq[(al * NPT + q) * DIM + j] = sa;
     }
   }
   __syncthreads();
-  // one node pair (a, b) per work item: its DIM x DIM block of the element matrix,
-  //   A_{ac,be} = sum_q [ d_ce g_b.(tau + c1/2 I).g_a + c1/2 g_{a,e} g_{b,c} + c2 g_{a,c} g_{b,e} ].
-  // Only the upper triangle of the free-dof matrix is assembled (the Gauss-Jordan passes read nothing else):
-  // the lattice numbers a cell's nodes in the order of its local nodes, so the pairs with a > b lie below
-  // the diagonal and are skipped, and those with a = b keep c <= e.
-  for (int item = t; item < NPT * NPT; item += blockDim.x) {
-    const int an = item / NPT, bn = item % NPT;
-    if (an > bn) continue;
-    double acc[DIM][DIM];
-#pragma unroll
-    for (int c = 0; c < DIM; ++c)
-#pragma unroll
-      for (int e = 0; e < DIM; ++e) acc[c][e] = 0.0;
-    for (int q = 0; q < NPT; ++q) {
-      double ga[DIM], gb[DIM];
-#pragma unroll
-      for (int j = 0; j < DIM; ++j) {
-        ga[j] = Gq[(an * NPT + q) * DIM + j];
-        gb[j] = Gq[(bn * NPT + q) * DIM + j];
-      }
-      const double hc1 = 0.5 * c1q[q], c2 = c2q[q];
-      double geo = 0.0, dotab = 0.0;
-#pragma unroll
-      for (int al = 0; al < NS; ++al) {
-        const int i = vi<DIM>(al), j = vj<DIM>(al);
-        geo = fma(tq[al][q], (i == j) ? ga[i] * gb[i] : ga[i] * gb[j] + ga[j] * gb[i], geo);
-      }
-#pragma unroll
-      for (int j = 0; j < DIM; ++j) dotab = fma(ga[j], gb[j], dotab);
-      const double sdiag = fma(hc1, dotab, geo);
-#pragma unroll
+  if constexpr (CH == 0) {
+    // one node pair (a, b) per work item: its DIM x DIM block of the element matrix,
+    //   A_{ac,be} = sum_q [ d_ce g_b.(tau + c1/2 I).g_a + c1/2 g_{a,e} g_{b,c} + c2 g_{a,c} g_{b,e} ].
+    // Only the upper triangle of the free-dof matrix is assembled (the Gauss-Jordan passes read nothing else):
+    // the lattice numbers a cell's nodes in the order of its local nodes, so the pairs with a > b lie below
+    // the diagonal and are skipped, and those with a = b keep c <= e.
+    for (int item = t; item < NPT * NPT; item += blockDim.x) {
+      const int an = item / NPT, bn = item % NPT;
+      if (an > bn) continue;
+      double acc[DIM][DIM];
+  #pragma unroll
       for (int c = 0; c < DIM; ++c)
-#pragma unroll
+  #pragma unroll
+        for (int e = 0; e < DIM; ++e) acc[c][e] = 0.0;
+      for (int q = 0; q < NPT; ++q) {
+        double ga[DIM], gb[DIM];
+  #pragma unroll
+        for (int j = 0; j < DIM; ++j) {
+          ga[j] = Gq[(an * NPT + q) * DIM + j];
+          gb[j] = Gq[(bn * NPT + q) * DIM + j];
+        }
+        const double hc1 = 0.5 * c1q[q], c2 = c2q[q];
+        double geo = 0.0, dotab = 0.0;
+  #pragma unroll
+        for (int al = 0; al < NS; ++al) {
+          const int i = vi<DIM>(al), j = vj<DIM>(al);
+          geo = fma(tq[al][q], (i == j) ? ga[i] * gb[i] : ga[i] * gb[j] + ga[j] * gb[i], geo);
+        }
+  #pragma unroll
+        for (int j = 0; j < DIM; ++j) dotab = fma(ga[j], gb[j], dotab);
+        const double sdiag = fma(hc1, dotab, geo);
+  #pragma unroll
+        for (int c = 0; c < DIM; ++c)
+  #pragma unroll
+          for (int e = 0; e < DIM; ++e) {
+            double v = fma(hc1, ga[e] * gb[c], c == e ? sdiag : 0.0);
+            acc[c][e] += fma(c2, ga[c] * gb[e], v);
+          }
+      }
+  #pragma unroll
+      for (int c = 0; c < DIM; ++c)
+  #pragma unroll
         for (int e = 0; e < DIM; ++e) {
-          double v = fma(hc1, ga[e] * gb[c], c == e ? sdiag : 0.0);
-          acc[c][e] += fma(c2, ga[c] * gb[e], v);
+          const int row = an * DIM + c, col = bn * DIM + e;
+          if (cons[row] || cons[col] || (an == bn && c > e)) continue;
+          atomicAdd(&Aout[(long long)cidx[gdof[row]] * nfree + cidx[gdof[col]]], acc[c][e]);
         }
     }
+  } else {
+    // thread b: g_b(q) from the tables and M, then the pairs (a, b), a of the chunk, a <= b
+    const int bn = t;
+    if (bn < NPT) {
+      const int bpc[3] = {bn % N, (bn / N) % N, DIM == 3 ? bn / (N * N) : 0};
+      double acc[CH][DIM][DIM];
 #pragma unroll
-    for (int c = 0; c < DIM; ++c)
+      for (int al = 0; al < CH; ++al)
 #pragma unroll
-      for (int e = 0; e < DIM; ++e) {
-        const int row = an * DIM + c, col = bn * DIM + e;
-        if (cons[row] || cons[col] || (an == bn && c > e)) continue;
-        atomicAdd(&Aout[(long long)cidx[gdof[row]] * nfree + cidx[gdof[col]]], acc[c][e]);
+        for (int c = 0; c < DIM; ++c)
+#pragma unroll
+          for (int e = 0; e < DIM; ++e) acc[al][c][e] = 0.0;
+      for (int q = 0; q < NPT; ++q) {
+        const int qc[3] = {q % N, (q / N) % N, DIM == 3 ? q / (N * N) : 0};
+        double gr[DIM], gb[DIM];
+#pragma unroll
+        for (int J = 0; J < DIM; ++J) {
+          double v = 1.0;
+#pragma unroll
+          for (int i = 0; i < DIM; ++i) v *= (i == J ? Sd : S)[qc[i]][bpc[i]];
+          gr[J] = v;
+        }
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) {
+          double sb = 0.0;
+#pragma unroll
+          for (int J = 0; J < DIM; ++J) sb = fma(gr[J], Mq[J * DIM + j][q], sb);
+          gb[j] = sb;
+        }
+        const double hc1 = 0.5 * c1q[q], c2 = c2q[q];
+#pragma unroll
+        for (int al = 0; al < CH; ++al) {
+          if (a0 + al > bn) continue;  // below the diagonal (or past the last node)
+          double ga[DIM];
+#pragma unroll
+          for (int j = 0; j < DIM; ++j) ga[j] = Gq[(al * NPT + q) * DIM + j];
+          double geo = 0.0, dotab = 0.0;
+#pragma unroll
+          for (int be = 0; be < NS; ++be) {
+            const int i = vi<DIM>(be), j = vj<DIM>(be);
+            geo = fma(tq[be][q], (i == j) ? ga[i] * gb[i] : ga[i] * gb[j] + ga[j] * gb[i], geo);
+          }
+#pragma unroll
+          for (int j = 0; j < DIM; ++j) dotab = fma(ga[j], gb[j], dotab);
+          const double sdiag = fma(hc1, dotab, geo);
+#pragma unroll
+          for (int c = 0; c < DIM; ++c)
+#pragma unroll
+            for (int e = 0; e < DIM; ++e) {
+              double v = fma(hc1, ga[e] * gb[c], c == e ? sdiag : 0.0);
+              acc[al][c][e] += fma(c2, ga[c] * gb[e], v);
+            }
+        }
       }
+#pragma unroll
+      for (int al = 0; al < CH; ++al) {
+        const int an = a0 + al;
+        if (an > bn) continue;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c)
+#pragma unroll
+          for (int e = 0; e < DIM; ++e) {
+            const int row = an * DIM + c, col = bn * DIM + e;
+            if (cons[row] || cons[col] || (an == bn && c > e)) continue;
+            atomicAdd(&Aout[(long long)cidx[gdof[row]] * nfree + cidx[gdof[col]]], acc[al][c][e]);
+          }
+      }
+    }
   }
 }
 
 template <int DIM, int N>
 void launch_assemble(const CellArgs<double>& a, double* A, long long nfree, const int* cidx, cudaStream_t st) {
   constexpr int NPT = ipow(N, DIM);
-  constexpr size_t dyn = sizeof(double) * NPT * NPT * DIM;  // up to 375 KB for Q4 3D: capped below
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(assemble_dense_kernel<DIM, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    attr = true;
+  constexpr size_t full = sizeof(double) * NPT * NPT * DIM;  // the whole table: 375 KB for Q4 3D
+  if constexpr (full <= 160 * 1024) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(assemble_dense_kernel<DIM, N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)full);
+      attr = true;
+    }
+    const int threads = NPT * DIM < 256 ? 256 : ((NPT * DIM + 31) / 32) * 32;
+    assemble_dense_kernel<DIM, N, 0><<<a.g.ncells, threads, full, st>>>(a, A, nfree, cidx);
+  } else {
+    constexpr int CH = 5;
+    constexpr size_t dyn = sizeof(double) * CH * NPT * DIM;
+    const dim3 grid((unsigned)a.g.ncells, (unsigned)((NPT + CH - 1) / CH));
+    assemble_dense_kernel<DIM, N, CH><<<grid, ((NPT + 31) / 32) * 32, dyn, st>>>(a, A, nfree, cidx);
   }
-  const int threads = NPT * DIM < 256 ? 256 : ((NPT * DIM + 31) / 32) * 32;
-  assemble_dense_kernel<DIM, N><<<a.g.ncells, threads, dyn, st>>>(a, A, nfree, cidx);
 }
 
 // x = A b on the free dofs (one warp per row, fixed summation order); b and x are full level vectors

@@ -122,7 +122,7 @@ def test_indefinite_coarse_level_is_reported_by_the_vcycle(torch):
 
 
 @pytest.mark.parametrize("coarse", [1, 2])
-@pytest.mark.parametrize("dim,k,m,L", [(2, 2, 8, 3), (3, 2, 4, 2), (3, 1, 8, 3)])
+@pytest.mark.parametrize("dim,k,m,L", [(2, 2, 8, 3), (3, 2, 4, 2), (3, 1, 8, 3), (3, 4, 4, 2), (3, 3, 4, 2)])
 def test_exact_coarse_vcycle(torch, dim, k, m, L, coarse):
     """Option: the coarsest level solved exactly (dense inverse; coarse = 2 inverts in double-float)
     instead of by Chebyshev."""

@@ -1364,7 +1364,15 @@ hy_status set_displacement(hy_ctx* ctx, const double* u, int var, bool mixed) {
     CellArgs<double> a = cell_args<double>(ctx, L);
     a.u64 = L.d_u64;
     a.y = L.d_diag;
-    CellFn<double> dfn = diag_fn(ctx->dim, ctx->n, ctx->sp.fine_dtype == HY_FF);
+    // the state from the level's T4/T2 cache in the diagonal's arithmetic where there is one, else evaluated
+    const bool ffa = ctx->sp.fine_dtype == HY_FF;
+    const int cvar = ffa ? L.var[2] : L.var[0];
+    const bool cached = (ffa ? L.hasff : L.has64) && (cvar == VAR_T4 || cvar == VAR_T2);
+    CellFn<double> dfn = diag_fn(ctx->dim, ctx->n, ffa);
+    if (cached) {
+      a.cache = ffa ? reinterpret_cast<const double*>(cache_of<ff>(L)) : cache_of<double>(L);
+      dfn = diag_cached_fn(ctx->dim, ctx->n, ffa, cvar);
+    }
     dfn(a, ctx->stream);
     launch_set_constrained_one<double>(L.d_diag, L.nnodes, ctx->dim, L.g, ctx->stream);
     HY_TRY(check_launch(ctx, 2));

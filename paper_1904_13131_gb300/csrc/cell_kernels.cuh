@@ -1667,7 +1667,12 @@ residual_kernel(const CellArgs<double> a) {
 // (J <= L, the off-diagonal pairs doubled) go to shared memory in E and are contracted along x, y (and z)
 // by the same threads, which end as (cell, node) and hold the entry. E is double, or double-float (the
 // FP32 pipe, about 48 significant bits).
-template <int DIM, int N, typename E>
+//   SRC = 0 evaluates the state from the displacement. SRC = 1 (T4) or 2 (T2) reads M, tau~, c1~, c2~ of the
+// point from the level's cache of that variant in element type E (the same cell blocks as this kernel): the
+// values the state kernel wrote, with c1~ = JC~_0000 - JC~_0011 and c2~ = JC~_0011 for T4.
+__device__ __forceinline__ double cached_double(double v) { return v; }
+__device__ __forceinline__ double cached_double(ff v) { return (double)v.hi + (double)v.lo; }
+template <int DIM, int N, typename E, int SRC = 0>
 __global__ void __launch_bounds__(cells_per_block(DIM, N) * ipow(N, DIM))
 diag_kernel(const CellArgs<double> a) {
   constexpr int NPT = ipow(N, DIM);
@@ -1690,33 +1695,55 @@ diag_kernel(const CellArgs<double> a) {
   const int cell = blockIdx.x * CB + cl;
   const bool active = cell < a.g.ncells;
   const CellLoc<DIM, N> loc(a.g, active ? cell : 0, pt);
-  double* b0 = &s.b0[cl][0][0];
-  double* b1 = &s.b1[cl][0][0];
   __syncthreads();
-#pragma unroll
-  for (int c = 0; c < DIM; ++c) b0[c * NPT + pt.p] = active ? a.u64[(long long)loc.node * DIM + c] : 0.0;
-  __syncthreads();
-  const double* V = interp_forward<DIM, N, DIM>(b0, b1, pt, s.S);
-  double Gu[DIM][DIM];
-  colloc_grad<DIM, N>(V, pt, s.D, Gu);
-  const bool curved = a.X64 != nullptr;
-  double invJ[DIM][DIM], wdet = 0.0;
-  if (curved) qp_geometry<DIM, N>(a, s, loc, pt, active, b0, b1, invJ, wdet);
-  const double inv_h = a.g.inv_h;
-  double F[DIM][DIM];
-  if (curved) {
-    deformation_curved<DIM>(Gu, invJ, F);
-  } else {
-#pragma unroll
-    for (int i = 0; i < DIM; ++i)
-#pragma unroll
-      for (int J = 0; J < DIM; ++J) F[i][J] = (i == J ? 1.0 : 0.0) + Gu[i][J] * inv_h;
-  }
-  const int id = active ? a.mat[cell] : 0;
   double M[DIM][DIM], tau[NS], c1, c2;
-  neo_hooke_state<DIM>(F, s.mu[id], s.lam[id], a.mt.law, curved ? wdet : s.W[pt.p], curved ? 1.0 : inv_h, false, 0.0,
-                       M, tau, c1, c2);
-  if (curved) premultiply<DIM>(invJ, M);
+  if constexpr (SRC == 0) {
+    double* b0 = &s.b0[cl][0][0];
+    double* b1 = &s.b1[cl][0][0];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) b0[c * NPT + pt.p] = active ? a.u64[(long long)loc.node * DIM + c] : 0.0;
+    __syncthreads();
+    const double* V = interp_forward<DIM, N, DIM>(b0, b1, pt, s.S);
+    double Gu[DIM][DIM];
+    colloc_grad<DIM, N>(V, pt, s.D, Gu);
+    const bool curved = a.X64 != nullptr;
+    double invJ[DIM][DIM], wdet = 0.0;
+    if (curved) qp_geometry<DIM, N>(a, s, loc, pt, active, b0, b1, invJ, wdet);
+    const double inv_h = a.g.inv_h;
+    double F[DIM][DIM];
+    if (curved) {
+      deformation_curved<DIM>(Gu, invJ, F);
+    } else {
+#pragma unroll
+      for (int i = 0; i < DIM; ++i)
+#pragma unroll
+        for (int J = 0; J < DIM; ++J) F[i][J] = (i == J ? 1.0 : 0.0) + Gu[i][J] * inv_h;
+    }
+    const int id = active ? a.mat[cell] : 0;
+    neo_hooke_state<DIM>(F, s.mu[id], s.lam[id], a.mt.law, curved ? wdet : s.W[pt.p], curved ? 1.0 : inv_h, false,
+                         0.0, M, tau, c1, c2);
+    if (curved) premultiply<DIM>(invJ, M);
+  } else {
+    static_assert(SRC == 1 || SRC == 2, "T4 or T2 cache");
+    constexpr int NV = cache_values(SRC == 1 ? VAR_T4 : VAR_T2, DIM);
+    constexpr int BS = layout_row<E>(DIM, N);
+    constexpr int NM = DIM * DIM + NS;
+    static_assert(layout_cells<E>(DIM, N) == CB, "the cache's cell blocks are this kernel's");
+    const E* cq = reinterpret_cast<const E*>(a.cache) + (size_t)blockIdx.x * NV * BS + cl * NPT + pt.p;
+    auto rd = [&](int v) { return active ? cached_double(cq[(size_t)v * BS]) : 0.0; };
+#pragma unroll
+    for (int i = 0; i < DIM * DIM; ++i) M[i / DIM][i % DIM] = rd(i);
+#pragma unroll
+    for (int al = 0; al < NS; ++al) tau[al] = rd(DIM * DIM + al);
+    if (SRC == 1) {
+      const double k00 = rd(NM), k01 = rd(NM + 1);
+      c2 = k01;
+      c1 = k00 - k01;
+    } else {
+      c1 = rd(NM);
+      c2 = rd(NM + 1);
+    }
+  }
   // G = M (tau + c1/2 I) M^T (upper triangle) and kappa = c1/2 + c2
   double G[NS];
   {

@@ -18,12 +18,12 @@ void launch_residual(const CellArgs<double>& a, cudaStream_t st) {
   const int grid = (a.g.ncells + CB - 1) / CB;
   residual_kernel<DIM, N><<<grid, CB * NPT, 0, st>>>(a);
 }
-template <int DIM, int N, typename E>
+template <int DIM, int N, typename E, int SRC = 0>
 void launch_diag(const CellArgs<double>& a, cudaStream_t st) {
   constexpr int CB = cells_per_block(DIM, N);
   constexpr int NPT = ipow(N, DIM);
   const int grid = (a.g.ncells + CB - 1) / CB;
-  diag_kernel<DIM, N, E><<<grid, CB * NPT, 0, st>>>(a);
+  diag_kernel<DIM, N, E, SRC><<<grid, CB * NPT, 0, st>>>(a);
 }
 
 __device__ __forceinline__ float to_f32(double v) { return (float)v; }
@@ -130,4 +130,14 @@ CellFn<double> diag_fn(int dim, int n, bool ff_arith) {
   if (n < 2 || n > 5 || dim < 2 || dim > 3) return nullptr;
   return t[ff_arith ? 1 : 0][dim - 2][n - 2];
 }
+#define HY_DROW(E, S)                                                                                              \
+  {{launch_diag<2, 2, E, S>, launch_diag<2, 3, E, S>, launch_diag<2, 4, E, S>, launch_diag<2, 5, E, S>},          \
+   {launch_diag<3, 2, E, S>, launch_diag<3, 3, E, S>, launch_diag<3, 4, E, S>, launch_diag<3, 5, E, S>}}
+CellFn<double> diag_cached_fn(int dim, int n, bool ff_arith, int var) {
+  static const CellFn<double> t[2][2][2][4] = {{HY_DROW(double, 1), HY_DROW(double, 2)},
+                                               {HY_DROW(ff, 1), HY_DROW(ff, 2)}};
+  if (n < 2 || n > 5 || dim < 2 || dim > 3 || (var != VAR_T4 && var != VAR_T2)) return nullptr;
+  return t[ff_arith ? 1 : 0][var == VAR_T4 ? 0 : 1][dim - 2][n - 2];
+}
+#undef HY_DROW
 }  // namespace hy

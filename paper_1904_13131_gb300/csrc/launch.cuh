@@ -105,6 +105,9 @@ void launch_derive_f32(int dim, int n, bool src_ff, const void* src, int nvs, fl
 CellFn<double> residual_fn(int dim, int n);
 // diagonal: the sum over (node, Gauss point) pairs in FP64, or in double-float (ff_arith)
 CellFn<double> diag_fn(int dim, int n, bool ff_arith);
+// The diagonal with the Gauss-point state read from the level's T4 or T2 cache (a.cache) in the diagonal's
+// element type (double-float when ff_arith) instead of evaluated from the displacement.
+CellFn<double> diag_cached_fn(int dim, int n, bool ff_arith, int var);
 
 constexpr int VAR_NONE = 5;
 

@@ -105,22 +105,23 @@ def test_autotuned_form_is_recorded_and_reused(torch):
 @pytest.mark.parametrize("dim,k,m", [(2, 2, 7), (3, 2, 3), (3, 3, 2), (2, 4, 3), (3, 4, 2)])
 def test_residual_and_diagonal(torch, dim, k, m):
     """Residual in FP64; the sum-factorised diagonal (per (J, L) pair and component, one 1D contraction per
-    direction) in FP64 and, with fine_dtype = FF, in double-float."""
+    direction) in FP64 and, with fine_dtype = FF, in double-float, its state read from the T4 or T2 cache or
+    (NC) evaluated from the displacement."""
     from paper_1904_13131_gb300.api import FF
     pr = problem(dim, k, m)
     P = oracle_level(pr)
     u = inputs.smooth_field(dim, k, m, seed=3)
     ud = torch.tensor(u, device="cuda")
+    d_ref = P.diagonal(u)
     with context(pr) as ctx:
         r = ctx.residual(ud).cpu().numpy()
-        ctx.set_displacement(ud, "T4")
-        d = ctx.diagonal().cpu().numpy()
-        ctx.set_solver_params(fine_dtype=FF)
-        ctx.set_displacement(ud, "T4")
-        dff = ctx.diagonal().cpu().numpy()
-        assert rel(dff, P.diagonal(u)) < 1e-12
+        for fine in (0, FF):
+            ctx.set_solver_params(fine_dtype=fine)
+            for var in ("T4", "T2", "NC"):
+                ctx.set_displacement(ud, var)
+                d = ctx.diagonal().cpu().numpy()
+                assert rel(d, d_ref) < 1e-12, (fine, var, rel(d, d_ref))
     assert rel(r, P.residual(u)) < 1e-12
-    assert rel(d, P.diagonal(u)) < 1e-12
 
 
 def test_deferred_fp64_cache_under_double_float(torch):

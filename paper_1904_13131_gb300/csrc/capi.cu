@@ -499,8 +499,10 @@ template <> double* tmp_of<double>(hy_ctx* c, int i) { return i == 0 ? c->tmp64a
 template <> float* tmp_of<float>(hy_ctx* c, int i) { return i == 0 ? c->tmp32a : c->tmp32b; }
 
 // fine += P coarse (fine level l), constrained coarse entries read as zero, constrained fine rows zero.
+// prep (or null): the last sweep also writes prep = (constrained ? new fine : 0), ready for an application
+// of the new fine vector.
 template <typename T>
-hy_status prolongate_add(hy_ctx* ctx, int l, const T* coarse, T* fine) {
+hy_status prolongate_add(hy_ctx* ctx, int l, const T* coarse, T* fine, T* prep = nullptr) {
   Transfer& t = ctx->tr[l];
   const int d = ctx->dim;
   int Lin[3] = {t.Lc, t.Lc, t.Lc};
@@ -511,16 +513,17 @@ hy_status prolongate_add(hy_ctx* ctx, int l, const T* coarse, T* fine) {
     const bool last = ax == d - 1;
     T* dst = last ? fine : tmp_of<T>(ctx, ax & 1);
     launch_sweep<T>(src, dst, d, Lin, Lout, ax, t.d_pstart, pw_of<T>(t), t.Ep, last, ax == 0 ? &ctx->lev[l - 1].g : nullptr,
-                    last ? &ctx->lev[l].g : nullptr, ctx->stream);
+                    last ? &ctx->lev[l].g : nullptr, ctx->stream, nullptr, last ? prep : nullptr);
     src = dst;
     Lin[ax] = t.Lf;
   }
   return check_launch(ctx, d);
 }
 
-// coarse = P^T fine (fine level l), with the same constraint masks.
+// coarse = P^T fine (fine level l), with the same constraint masks; with fine_minus, of fine - fine_minus
+// (the residual formed inside the first sweep).
 template <typename T>
-hy_status restrict_to(hy_ctx* ctx, int l, const T* fine, T* coarse) {
+hy_status restrict_to(hy_ctx* ctx, int l, const T* fine, T* coarse, const T* fine_minus = nullptr) {
   Transfer& t = ctx->tr[l];
   const int d = ctx->dim;
   int Lin[3] = {t.Lf, t.Lf, t.Lf};
@@ -531,7 +534,7 @@ hy_status restrict_to(hy_ctx* ctx, int l, const T* fine, T* coarse) {
     const bool last = ax == d - 1;
     T* dst = last ? coarse : tmp_of<T>(ctx, ax & 1);
     launch_sweep<T>(src, dst, d, Lin, Lout, ax, t.d_rstart, rw_of<T>(t), t.Er, false, ax == 0 ? &ctx->lev[l].g : nullptr,
-                    last ? &ctx->lev[l - 1].g : nullptr, ctx->stream);
+                    last ? &ctx->lev[l - 1].g : nullptr, ctx->stream, ax == 0 ? fine_minus : nullptr);
     src = dst;
     Lin[ax] = t.Lc;
   }
@@ -561,9 +564,12 @@ hy_status interpolate_down(hy_ctx* ctx, int l) {
 }
 
 // Chebyshev iteration of the given degree on [lo, hi] for A~ x = b on level l (Saad, Alg. 12.1),
-// Jacobi preconditioned; x0_zero starts from zero. Uses the level's r, d, t vectors.
+// Jacobi preconditioned; x0_zero starts from zero. Uses the level's r, d, t vectors. t_ready: t already holds
+// (constrained ? x : 0), the output of the first application prepared; prep_x: the last update leaves t so
+// prepared for an application of the final x.
 template <typename T>
-hy_status chebyshev(hy_ctx* ctx, int l, const T* b, T* x, bool x0_zero, int degree, double lo, double hi) {
+hy_status chebyshev(hy_ctx* ctx, int l, const T* b, T* x, bool x0_zero, int degree, double lo, double hi,
+                    bool t_ready = false, bool prep_x = false) {
   Level& L = ctx->lev[l];
   T* r = wvec<T>(L, 2);
   T* dd = wvec<T>(L, 3);
@@ -572,16 +578,18 @@ hy_status chebyshev(hy_ctx* ctx, int l, const T* b, T* x, bool x0_zero, int degr
   const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
   const double sigma = theta / delta;
   double rho = 1.0 / sigma;
-  if (!x0_zero) HY_TRY(level_apply<T>(ctx, l, x, t));
-  // each update also prepares t for the next application of d (no separate prep_out launch)
-  launch_cheb_init<T>(b, t, dinv, r, dd, x, T(1.0 / theta), x0_zero, L.ndofs, degree > 1 ? &L.g : nullptr, ctx->dim,
-                      ctx->stream);
+  if (!x0_zero) HY_TRY(level_apply<T>(ctx, l, x, t, t_ready));
+  // each update also prepares t for the next application of d, or after the last one of x (no separate
+  // prep_out launch)
+  launch_cheb_init<T>(b, t, dinv, r, dd, x, T(1.0 / theta), x0_zero, L.ndofs, degree > 1 || prep_x ? &L.g : nullptr,
+                      ctx->dim, ctx->stream, degree == 1 && prep_x);
   HY_TRY(check_launch(ctx, 1));
   for (int j = 1; j < degree; ++j) {
     HY_TRY(level_apply<T>(ctx, l, dd, t, true));
     const double rho_new = 1.0 / (2.0 * sigma - rho);
+    const bool last = j + 1 == degree;
     launch_cheb_step<T>(t, dinv, r, dd, x, T(rho_new * rho), T(2.0 * rho_new / delta), L.ndofs,
-                        j + 1 < degree ? &L.g : nullptr, ctx->dim, ctx->stream);
+                        !last || prep_x ? &L.g : nullptr, ctx->dim, ctx->stream, last && prep_x);
     HY_TRY(check_launch(ctx, 1));
     rho = rho_new;
   }
@@ -599,30 +607,32 @@ hy_status vcycle_typed(hy_ctx* ctx, int l) {
   T* b = wvec<T>(L, 0);
   T* x = wvec<T>(L, 1);
   const double lo = ctx->sp.cheb_lo * L.lmax, hi = ctx->sp.cheb_hi * L.lmax;
-  for (int s = 0; s < ctx->sp.cheb_sweeps; ++s) HY_TRY(chebyshev<T>(ctx, l, b, x, s == 0, ctx->sp.cheb_degree, lo, hi));
+  // Every smoothing sweep leaves t prepared for the application of its x that follows it (the next sweep's
+  // first one, or the residual's), and the prolongation leaves t prepared for the post-smoother's first one.
+  for (int s = 0; s < ctx->sp.cheb_sweeps; ++s)
+    HY_TRY(chebyshev<T>(ctx, l, b, x, s == 0, ctx->sp.cheb_degree, lo, hi, s > 0, true));
   T* t = wvec<T>(L, 4);
-  T* r = wvec<T>(L, 2);
-  HY_TRY(level_apply<T>(ctx, l, x, t));
-  launch_sub<T>(b, t, r, L.ndofs, ctx->stream);
-  HY_TRY(check_launch(ctx, 1));
+  HY_TRY(level_apply<T>(ctx, l, x, t, true));
+  // the residual b - t is formed inside the restriction's first sweep
   Level& C = ctx->lev[l - 1];
   const bool cf32 = level_f32(ctx, l - 1);
   if ((sizeof(T) == 4) == cf32) {
-    HY_TRY(restrict_to<T>(ctx, l, r, wvec<T>(C, 0)));
+    HY_TRY(restrict_to<T>(ctx, l, b, wvec<T>(C, 0), t));
   } else {  // float fine level above the FP64 coarsest level
-    HY_TRY(restrict_to<T>(ctx, l, r, (T*)ctx->tmp32c));
+    HY_TRY(restrict_to<T>(ctx, l, b, (T*)ctx->tmp32c, t));
     launch_convert<float, double>((const float*)ctx->tmp32c, C.w64[0], C.ndofs, ctx->stream);
     HY_TRY(check_launch(ctx, 1));
   }
   HY_TRY(vcycle_level(ctx, l - 1));
   if ((sizeof(T) == 4) == cf32) {
-    HY_TRY(prolongate_add<T>(ctx, l, wvec<T>(C, 1), x));
+    HY_TRY(prolongate_add<T>(ctx, l, wvec<T>(C, 1), x, t));
   } else {
     launch_convert<double, float>(C.w64[1], ctx->tmp32c, C.ndofs, ctx->stream);
     HY_TRY(check_launch(ctx, 1));
-    HY_TRY(prolongate_add<T>(ctx, l, (const T*)ctx->tmp32c, x));
+    HY_TRY(prolongate_add<T>(ctx, l, (const T*)ctx->tmp32c, x, t));
   }
-  for (int s = 0; s < ctx->sp.cheb_sweeps; ++s) HY_TRY(chebyshev<T>(ctx, l, b, x, false, ctx->sp.cheb_degree, lo, hi));
+  for (int s = 0; s < ctx->sp.cheb_sweeps; ++s)
+    HY_TRY(chebyshev<T>(ctx, l, b, x, false, ctx->sp.cheb_degree, lo, hi, true, s + 1 < ctx->sp.cheb_sweeps));
   return HY_OK;
 }
 

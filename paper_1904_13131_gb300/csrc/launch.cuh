@@ -127,12 +127,13 @@ template <typename T> void launch_axpby(T a, const T* x, T b, T* y, long long n,
 template <typename T> void launch_xpay(const T* x, T a, const T* y, T* z, long long n, cudaStream_t st);
 // Chebyshev: first step. r = b (x0 zero) or r = b - t; d = dinv*r*inv_theta; x = d (x0 zero) or x += d.
 // prep (the level geometry, or null): also t = (constrained ? d : 0), the next application's output
-// prepared as launch_prep_out would.
+// prepared as launch_prep_out would -- or, with prep_x, prepared for an application of the new x.
 template <typename T> void launch_cheb_init(const T* b, T* t, const T* dinv, T* r, T* d, T* x, T inv_theta,
-                                            bool x0_zero, long long n, const Geom* prep, int dim, cudaStream_t st);
+                                            bool x0_zero, long long n, const Geom* prep, int dim, cudaStream_t st,
+                                            bool prep_x = false);
 // Chebyshev: later step. r -= t; d = cd*d + cr*dinv*r; x += d; prep as above
 template <typename T> void launch_cheb_step(T* t, const T* dinv, T* r, T* d, T* x, T cd, T cr, long long n,
-                                            const Geom* prep, int dim, cudaStream_t st);
+                                            const Geom* prep, int dim, cudaStream_t st, bool prep_x = false);
 // z = a * b (elementwise)
 template <typename T> void launch_mul(const T* a, const T* b, T* z, long long n, cudaStream_t st);
 // out[i] = SplitMix64 uniform on [-1, 1) at counter i (seeded)
@@ -166,10 +167,13 @@ void launch_lift(const double* u, double* du0, double factor, const double* face
 constexpr int DOT_BLOCKS = 304;
 template <typename T> void launch_dot(const T* a, const T* b, long long n, double* partials, double* out,
                                       cudaStream_t st);
-// separable 1D transfer sweep along `axis`: out(i with i_axis = o) = sum_e w[o*E+e] in(i with i_axis = start[o]+e)
+// separable 1D transfer sweep along `axis`: out(i with i_axis = o) = sum_e w[o*E+e] in(i with i_axis = start[o]+e).
+// in_minus (or null): the input is in - in_minus. prep (or null): also prep = (masked out ? new out : 0), the
+// output of an application of `out` prepared as launch_prep_out would.
 template <typename T>
 void launch_sweep(const T* in, T* out, int dim, const int Lin[3], const int Lout[3], int axis, const int* start,
-                  const T* w, int E, bool add_to_out, const Geom* mask_in, const Geom* mask_out, cudaStream_t st);
+                  const T* w, int E, bool add_to_out, const Geom* mask_in, const Geom* mask_out, cudaStream_t st,
+                  const T* in_minus = nullptr, T* prep = nullptr);
 
 // ---- exact coarsest-level solve (coarse_direct.cu) ----------------------------------------------
 // dense tangent of a level on its free dofs (cidx: dof -> compact index or -1), accumulated into A

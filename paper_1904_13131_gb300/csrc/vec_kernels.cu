@@ -168,27 +168,29 @@ __global__ void sub_kernel(const T* __restrict__ b, const T* __restrict__ t, T* 
 template <typename T, int PREP>
 __global__ void cheb_init_kernel(const T* __restrict__ b, T* __restrict__ t, const T* __restrict__ dinv,
                                  T* __restrict__ r, T* __restrict__ d, T* __restrict__ x, T inv_theta, bool x0_zero,
-                                 long long n, Geom g) {
+                                 long long n, Geom g, bool prep_x) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const T ri = x0_zero ? b[i] : b[i] - t[i];
     const T di = dinv[i] * ri * inv_theta;
     r[i] = ri;
     d[i] = di;
-    x[i] = x0_zero ? di : x[i] + di;
-    if constexpr (PREP > 0) t[i] = ((cmask_of<PREP>(g, i / PREP) >> (i % PREP)) & 1u) ? di : T(0);
+    const T xi = x0_zero ? di : x[i] + di;
+    x[i] = xi;
+    if constexpr (PREP > 0) t[i] = ((cmask_of<PREP>(g, i / PREP) >> (i % PREP)) & 1u) ? (prep_x ? xi : di) : T(0);
   }
 }
 
 template <typename T, int PREP>
 __global__ void cheb_step_kernel(T* __restrict__ t, const T* __restrict__ dinv, T* __restrict__ r,
-                                 T* __restrict__ d, T* __restrict__ x, T cd, T cr, long long n, Geom g) {
+                                 T* __restrict__ d, T* __restrict__ x, T cd, T cr, long long n, Geom g, bool prep_x) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const T ri = r[i] - t[i];
     const T di = cd * d[i] + cr * dinv[i] * ri;
     r[i] = ri;
     d[i] = di;
-    x[i] += di;
-    if constexpr (PREP > 0) t[i] = ((cmask_of<PREP>(g, i / PREP) >> (i % PREP)) & 1u) ? di : T(0);
+    const T xi = x[i] + di;
+    x[i] = xi;
+    if constexpr (PREP > 0) t[i] = ((cmask_of<PREP>(g, i / PREP) >> (i % PREP)) & 1u) ? (prep_x ? xi : di) : T(0);
   }
 }
 
@@ -288,9 +290,10 @@ __global__ void dot_final_kernel(const double* __restrict__ partials, double* __
 }
 
 template <typename T, int DIM>
-__global__ void sweep_kernel(const T* __restrict__ in, T* __restrict__ out, int Li0, int Li1, int Lo0, int Lo1,
-                             int Lo2, int axis, const int* __restrict__ start, const T* __restrict__ w, int E,
-                             bool add, bool use_mask_in, Geom gin, bool use_mask_out, Geom gout) {
+__global__ void sweep_kernel(const T* __restrict__ in, const T* __restrict__ in_minus, T* __restrict__ out,
+                             T* __restrict__ prep, int Li0, int Li1, int Lo0, int Lo1, int Lo2, int axis,
+                             const int* __restrict__ start, const T* __restrict__ w, int E, bool add, bool use_mask_in,
+                             Geom gin, bool use_mask_out, Geom gout) {
   const long long n_out = (long long)Lo0 * Lo1 * (DIM == 3 ? Lo2 : 1) * DIM;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n_out;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -304,12 +307,16 @@ __global__ void sweep_kernel(const T* __restrict__ in, T* __restrict__ out, int 
       o[axis] = s0 + e;
       const long long ni = o[0] + (long long)Li0 * (o[1] + (long long)Li1 * o[2]);
       T v = in[ni * DIM + c];
+      if (in_minus) v = v - in_minus[ni * DIM + c];
       if (use_mask_in && ((node_cmask<DIM>(gin, o[0], o[1], o[2]) >> c) & 1u)) v = T(0);
       acc = fma(w[(long long)oa * E + e], v, acc);
     }
     o[axis] = oa;
-    if (use_mask_out && ((node_cmask<DIM>(gout, o[0], o[1], o[2]) >> c) & 1u)) acc = T(0);
-    out[idx] = add ? out[idx] + acc : acc;
+    const bool masked = use_mask_out && ((node_cmask<DIM>(gout, o[0], o[1], o[2]) >> c) & 1u);
+    if (masked) acc = T(0);
+    const T v = add ? out[idx] + acc : acc;
+    out[idx] = v;
+    if (prep) prep[idx] = masked ? v : T(0);
   }
 }
 
@@ -384,19 +391,20 @@ void launch_sub(const T* b, const T* t, T* r, long long n, cudaStream_t st) {
 }
 template <typename T>
 void launch_cheb_init(const T* b, T* t, const T* dinv, T* r, T* d, T* x, T inv_theta, bool x0_zero, long long n,
-                      const Geom* prep, int dim, cudaStream_t st) {
+                      const Geom* prep, int dim, cudaStream_t st, bool prep_x) {
   const Geom g = prep ? *prep : Geom{};
-  if (!prep) cheb_init_kernel<T, 0><<<grid_for(n), TPB, 0, st>>>(b, t, dinv, r, d, x, inv_theta, x0_zero, n, g);
-  else if (dim == 2) cheb_init_kernel<T, 2><<<grid_for(n), TPB, 0, st>>>(b, t, dinv, r, d, x, inv_theta, x0_zero, n, g);
-  else cheb_init_kernel<T, 3><<<grid_for(n), TPB, 0, st>>>(b, t, dinv, r, d, x, inv_theta, x0_zero, n, g);
+  if (!prep) cheb_init_kernel<T, 0><<<grid_for(n), TPB, 0, st>>>(b, t, dinv, r, d, x, inv_theta, x0_zero, n, g, prep_x);
+  else if (dim == 2)
+    cheb_init_kernel<T, 2><<<grid_for(n), TPB, 0, st>>>(b, t, dinv, r, d, x, inv_theta, x0_zero, n, g, prep_x);
+  else cheb_init_kernel<T, 3><<<grid_for(n), TPB, 0, st>>>(b, t, dinv, r, d, x, inv_theta, x0_zero, n, g, prep_x);
 }
 template <typename T>
 void launch_cheb_step(T* t, const T* dinv, T* r, T* d, T* x, T cd, T cr, long long n, const Geom* prep, int dim,
-                      cudaStream_t st) {
+                      cudaStream_t st, bool prep_x) {
   const Geom g = prep ? *prep : Geom{};
-  if (!prep) cheb_step_kernel<T, 0><<<grid_for(n), TPB, 0, st>>>(t, dinv, r, d, x, cd, cr, n, g);
-  else if (dim == 2) cheb_step_kernel<T, 2><<<grid_for(n), TPB, 0, st>>>(t, dinv, r, d, x, cd, cr, n, g);
-  else cheb_step_kernel<T, 3><<<grid_for(n), TPB, 0, st>>>(t, dinv, r, d, x, cd, cr, n, g);
+  if (!prep) cheb_step_kernel<T, 0><<<grid_for(n), TPB, 0, st>>>(t, dinv, r, d, x, cd, cr, n, g, prep_x);
+  else if (dim == 2) cheb_step_kernel<T, 2><<<grid_for(n), TPB, 0, st>>>(t, dinv, r, d, x, cd, cr, n, g, prep_x);
+  else cheb_step_kernel<T, 3><<<grid_for(n), TPB, 0, st>>>(t, dinv, r, d, x, cd, cr, n, g, prep_x);
 }
 void launch_face_load(double* f, int dim, const Geom& g, int face, const FaceLoad& fl, cudaStream_t st) {
   const long long L = g.L;
@@ -416,16 +424,19 @@ void launch_dot(const T* a, const T* b, long long n, double* partials, double* o
 }
 template <typename T>
 void launch_sweep(const T* in, T* out, int dim, const int Lin[3], const int Lout[3], int axis, const int* start,
-                  const T* w, int E, bool add, const Geom* mask_in, const Geom* mask_out, cudaStream_t st) {
+                  const T* w, int E, bool add, const Geom* mask_in, const Geom* mask_out, cudaStream_t st,
+                  const T* in_minus, T* prep) {
   long long n_out = (long long)Lout[0] * Lout[1] * (dim == 3 ? Lout[2] : 1) * dim;
   Geom gi = mask_in ? *mask_in : Geom{};
   Geom go = mask_out ? *mask_out : Geom{};
   if (dim == 2)
-    sweep_kernel<T, 2><<<grid_for(n_out), TPB, 0, st>>>(in, out, Lin[0], Lin[1], Lout[0], Lout[1], Lout[2], axis,
-                                                        start, w, E, add, mask_in != nullptr, gi, mask_out != nullptr, go);
+    sweep_kernel<T, 2><<<grid_for(n_out), TPB, 0, st>>>(in, in_minus, out, prep, Lin[0], Lin[1], Lout[0], Lout[1],
+                                                        Lout[2], axis, start, w, E, add, mask_in != nullptr, gi,
+                                                        mask_out != nullptr, go);
   else
-    sweep_kernel<T, 3><<<grid_for(n_out), TPB, 0, st>>>(in, out, Lin[0], Lin[1], Lout[0], Lout[1], Lout[2], axis,
-                                                        start, w, E, add, mask_in != nullptr, gi, mask_out != nullptr, go);
+    sweep_kernel<T, 3><<<grid_for(n_out), TPB, 0, st>>>(in, in_minus, out, prep, Lin[0], Lin[1], Lout[0], Lout[1],
+                                                        Lout[2], axis, start, w, E, add, mask_in != nullptr, gi,
+                                                        mask_out != nullptr, go);
 }
 
 #define HY_INST(T)                                                                                              \
@@ -441,11 +452,12 @@ void launch_sweep(const T* in, T* out, int dim, const int Lin[3], const int Lout
   template void launch_xpay_dev<T>(const T*, const double*, const T*, T*, long long, cudaStream_t);             \
   template void launch_splitmix<T>(T*, long long, unsigned long long, cudaStream_t);                            \
   template void launch_cheb_init<T>(const T*, T*, const T*, T*, T*, T*, T, bool, long long, const Geom*, int,     \
-                                    cudaStream_t);                                                              \
-  template void launch_cheb_step<T>(T*, const T*, T*, T*, T*, T, T, long long, const Geom*, int, cudaStream_t);   \
+                                    cudaStream_t, bool);                                                        \
+  template void launch_cheb_step<T>(T*, const T*, T*, T*, T*, T, T, long long, const Geom*, int, cudaStream_t,     \
+                                    bool);                                                                      \
   template void launch_dot<T>(const T*, const T*, long long, double*, double*, cudaStream_t);                   \
   template void launch_sweep<T>(const T*, T*, int, const int*, const int*, int, const int*, const T*, int, bool, \
-                                const Geom*, const Geom*, cudaStream_t);
+                                const Geom*, const Geom*, cudaStream_t, const T*, T*);
 HY_INST(double)
 HY_INST(float)
 #undef HY_INST

@@ -227,17 +227,19 @@ def solve_latency(torch, api, inputs, dev):
     out, sols = {}, {}
     with api.Context(dev.index) as c:
         c.setup_problem(pr)
-        for name, ldt, coarse, fine, lvar, reuse in (
-                ("fp64", 0, 0, 0, -1, 0.0), ("mixed", 1, 0, 0, -1, 0.0),
-                ("mixed_exact_coarse", 1, 1, 0, -1, 0.0),
-                ("mixed_exact_coarse_fp64_inverse_t2_levels", 1, 1, 0, api.VARIANTS["T2"], 0.0),
-                ("mixed_exact_coarse_ff", 1, 2, 2, -1, 0.0),
-                ("mixed_exact_coarse_ff_t2_levels", 1, 2, 2, api.VARIANTS["T2"], 0.0),
-                ("mixed_exact_coarse_ff_t2_levels_setup_reuse", 1, 2, 2, api.VARIANTS["T2"], 0.05),
-                ("mixed_fp64_coarse_inverse_ff_t2_levels_setup_reuse", 1, 1, 2, api.VARIANTS["T2"], 0.05)):
+        t2 = api.VARIANTS["T2"]
+        for name, ldt, coarse, fine, lvar, reuse, var in (
+                ("fp64", 0, 0, 0, -1, 0.0, "T4"), ("mixed", 1, 0, 0, -1, 0.0, "T4"),
+                ("mixed_exact_coarse", 1, 1, 0, -1, 0.0, "T4"),
+                ("mixed_exact_coarse_fp64_inverse_t2_levels", 1, 1, 0, t2, 0.0, "T4"),
+                ("mixed_exact_coarse_ff", 1, 2, 2, -1, 0.0, "T4"),
+                ("mixed_exact_coarse_ff_t2_levels", 1, 2, 2, t2, 0.0, "T4"),
+                ("mixed_exact_coarse_ff_t2_levels_setup_reuse", 1, 2, 2, t2, 0.05, "T4"),
+                ("mixed_fp64_coarse_inverse_ff_t2_levels_setup_reuse", 1, 1, 2, t2, 0.05, "T4"),
+                ("mixed_exact_coarse_ff_t2_everywhere", 1, 2, 2, t2, 0.0, "T2")):
             c.set_solver_params(coarse_solver=coarse, fine_dtype=fine, level_variant=lvar, setup_reuse=reuse)
             u = torch.zeros(inputs.n_dofs(DIM, K, M), dtype=torch.float64, device=dev)
-            rep = c.newton_solve(u, api.Context.newton_params(level_dtype=ldt, face_values=fv))
+            rep = c.newton_solve(u, api.Context.newton_params(level_dtype=ldt, face_values=fv, variant=var))
             lat = np.array(rep["solve_ms"])
             out[name] = {"solve_p50_ms": float(np.percentile(lat, 50)), "solve_p99_ms": float(np.percentile(lat, 99)),
                          "solves": rep["n_solves"], "cg_iterations_median": int(np.median(rep["solve_cg_iterations"])),
@@ -288,8 +290,10 @@ def solve_latency(torch, api, inputs, dev):
                              "eigenvalue estimates and coarse inverse kept while the coarse displacement moved "
                              "less than 5 % since the last full setup; mixed_fp64_coarse_inverse_*: the fastest "
                              "mode with the coarse inverse in FP64 (the FP64 coarse solve of the mixed-precision "
-                             "pattern) instead of double-float")
-    out["workload"] = "32^3 Q2 (823,875 dofs), 10% compression in 5 load steps, 4 levels, CG rtol 1e-8, T4"
+                             "pattern) instead of double-float; _t2_everywhere: the outer CG's finest-level action "
+                             "in T2 as well (Algorithm 2)")
+    out["workload"] = ("32^3 Q2 (823,875 dofs), 10% compression in 5 load steps, 4 levels, CG rtol 1e-8, T4 for "
+                       "the outer CG unless the mode says otherwise")
     return out
 
 

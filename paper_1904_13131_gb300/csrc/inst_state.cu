@@ -1,5 +1,5 @@
 // Gauss-point state build, residual and diagonal kernels (all dims and degrees).
-#include "cell_kernels.cuh"
+#include "setup_kernels.cuh"
 #include "launch.cuh"
 
 namespace hy {
